@@ -1,0 +1,736 @@
+/*
+ * Oracle for BDD-based min-marginal averaging on 0-1 ILPs (Lange & Swoboda, "Efficient
+ * Message Passing for 0-1 ILPs with Binary Decision Diagrams").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Plain, slow, single-threaded FP64 C.  Only the test suite, the
+ * package smoke check and the benchmark's CPU-baseline leg load this file's library.  It
+ * shares no code, header, table or helper with the CUDA library.
+ *
+ * What it computes, in the paper's notation:
+ *   - BP / ILP form (Sec. 3, Def. 1 and Ex. 1): one subproblem per constraint row j, index
+ *     set I_j = { i : a_ji != 0 }, feasible set X_j = { x : a_j x (<=,=,>=) b_j }.
+ *   - One reduced, ordered, non-skipping BDD per row (Sec. 5.1, Def. 4 and the remark after
+ *     Prop. 2), built by reducing reachable partial coefficient sums bottom-up: the node of a
+ *     partial sum s at layer l is the pair (node of s, node of s + a_l) at layer l+1; equal
+ *     pairs are one node, the pair (bot, bot) is bot.  Nodes of a layer are numbered by their
+ *     smallest partial sum (canonical order; the paper leaves node order open).
+ *   - Arc costs theta (Sec. 5.3): 1-arc of a layer-i node costs lambda^j_i, 0-arc costs 0.
+ *   - Forward / backward update steps (Alg. 2, Alg. 3) with m_fwd(root) = 0,
+ *     m_bwd(top) = 0, m_bwd(bot) = +inf; arc marginals and min-marginals (eqs. arc-marginal
+ *     and marginal-aggregation).
+ *   - Schedule S: Alg. 1 (min-marginal averaging, forward then backward over the variables,
+ *     lambda initialised to c_i/|J_i|), with min-marginals taken from a full dynamic
+ *     programme over the BDD at every visit, and the Prop. 1 gain checked per update.
+ *   - Schedule P: the parallel-across-BDDs form with deferred averaging: within a sweep every
+ *     BDD runs its layers in order using the incremental steps of Sec. 5.4 (forward: update
+ *     step then aggregate; backward: aggregate then update step); the averaging share
+ *     P_i/|J_i| of the previous sweep is added to lambda when its layer is visited, lambda
+ *     moves by -omega*(m1 - m0), and the pending sum P_i = sum omega*(m1 - m0) is formed
+ *     after the sweep.
+ *   - Lower bound: sum_j E^j(lambda^j) + sum_i min(0, c_i - sum_j lambda^j_i) (the y-slack
+ *     form of the dual derivation, Appendix A.1), which equals eq. (D)'s objective when
+ *     sum_j lambda^j_i = c_i.
+ *   - Solution counts (Appendix C.1, Table 3, counting column).
+ * Readings where the paper is silent: a min-marginal that is +inf (a row that forces x_i)
+ * gives the difference 0; a variable in no row contributes min(0, c_i) to the bound; an empty
+ * row is dropped when 0 (sense) b holds and is infeasible otherwise.
+ */
+#include <limits.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TOP (-1)
+#define ORC_BOT (-2)
+
+enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_EINFEASIBLE = -2, ORC_ETOOBIG = -3, ORC_ENOMEM = -4 };
+
+/* ------------------------------------------------------------------------------------ */
+/* growable arrays                                                                        */
+/* ------------------------------------------------------------------------------------ */
+typedef struct { int *p; long long n, cap; } ivec;
+typedef struct { long long *p; long long n, cap; } lvec;
+
+static int iv_push(ivec *v, int x) {
+  if (v->n == v->cap) {
+    long long nc = v->cap ? 2 * v->cap : 256;
+    int *q = (int *)realloc(v->p, (size_t)nc * sizeof(int));
+    if (!q) return -1;
+    v->p = q; v->cap = nc;
+  }
+  v->p[v->n++] = x;
+  return 0;
+}
+static int lv_push(lvec *v, long long x) {
+  if (v->n == v->cap) {
+    long long nc = v->cap ? 2 * v->cap : 256;
+    long long *q = (long long *)realloc(v->p, (size_t)nc * sizeof(long long));
+    if (!q) return -1;
+    v->p = q; v->cap = nc;
+  }
+  v->p[v->n++] = x;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* oracle state                                                                           */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+  int n, m, nb;
+  long long nnz, O, N;
+  int max_depth, max_width;
+  /* per BDD (in ascending row order) */
+  int *bdd_row, *bdd_k;
+  long long *bdd_occ0;      /* [nb+1] first occurrence; occurrence o = bdd_occ0[b] + layer */
+  /* per occurrence (BDD-major, layer-minor) */
+  int *occ_var, *occ_bdd, *occ_layer;
+  long long *occ_csr;       /* position of the coefficient in the input CSR arrays */
+  long long *occ_node0;     /* [O+1] first node of the layer; nodes are BDD-major, layer-major */
+  /* per node */
+  int *lo, *hi;             /* local id in the next layer of the same BDD, or TOP / BOT */
+  long long *minsum;        /* smallest partial sum of the node's class */
+  /* per variable */
+  long long *var_ptr, *var_occ; /* occurrences of each variable in ascending row order */
+  int *deg;
+  double *c;
+  double empty_const;       /* sum over variables in no row of min(0, c_i) */
+  /* dual state and messages */
+  double *lam, *P, *delta, *share, *fm, *bm;
+  /* scratch for the definitional dynamic programmes */
+  double *sfm, *sbm;
+  /* worst check violations seen: [monotone drop, invariant, incremental mm, prop-1 gain,
+   * negative gain] */
+  double worst[5];
+} oracle_t;
+
+void orc_free(void *vh) {
+  oracle_t *h = (oracle_t *)vh;
+  if (!h) return;
+  free(h->bdd_row); free(h->bdd_k); free(h->bdd_occ0);
+  free(h->occ_var); free(h->occ_bdd); free(h->occ_layer); free(h->occ_csr); free(h->occ_node0);
+  free(h->lo); free(h->hi); free(h->minsum);
+  free(h->var_ptr); free(h->var_occ); free(h->deg); free(h->c);
+  free(h->lam); free(h->P); free(h->delta); free(h->share); free(h->fm); free(h->bm);
+  free(h->sfm); free(h->sbm);
+  free(h);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* BDD construction by reduction of reachable partial sums                                */
+/* ------------------------------------------------------------------------------------ */
+typedef struct { int col, val; long long pos; } entry_t;
+
+static int cmp_entry(const void *a, const void *b) {
+  const entry_t *x = (const entry_t *)a, *y = (const entry_t *)b;
+  return (x->col > y->col) - (x->col < y->col);
+}
+
+static int sat(long long s, int sense, long long b) {
+  if (sense < 0) return s <= b;
+  if (sense > 0) return s >= b;
+  return s == b;
+}
+
+/* index of s in the sorted array S[0..len) (s is known to be present) */
+static long long find_sum(const long long *S, long long len, long long s) {
+  long long lo = 0, hi = len - 1;
+  while (lo < hi) {
+    long long mid = (lo + hi) / 2;
+    if (S[mid] < s) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+#define SUM_CAP (1LL << 24)
+
+/* Builds the BDD of one row and appends its nodes / occurrences.  Returns ORC_OK,
+ * ORC_EINFEASIBLE (no feasible point), ORC_ETOOBIG or ORC_ENOMEM. */
+static int build_row(const entry_t *e, int k, long long b, int sense, int row,
+                     ivec *bdd_row, ivec *bdd_k, ivec *occ_var, lvec *occ_csr, lvec *occ_node0,
+                     ivec *lo, ivec *hi, lvec *minsum) {
+  int rc = ORC_OK;
+  long long **S = (long long **)calloc((size_t)k + 1, sizeof(long long *));
+  long long *len = (long long *)calloc((size_t)k + 1, sizeof(long long));
+  int **cls = (int **)calloc((size_t)k + 1, sizeof(int *));
+  /* nodes of each layer, collected bottom-up, emitted top-down */
+  ivec *Llo = (ivec *)calloc((size_t)k, sizeof(ivec));
+  ivec *Lhi = (ivec *)calloc((size_t)k, sizeof(ivec));
+  lvec *Lmin = (lvec *)calloc((size_t)k, sizeof(lvec));
+  if (!S || !len || !cls || !Llo || !Lhi || !Lmin) { rc = ORC_ENOMEM; goto done; }
+
+  /* top-down: reachable partial sums S_l (sorted, distinct) */
+  S[0] = (long long *)malloc(sizeof(long long));
+  if (!S[0]) { rc = ORC_ENOMEM; goto done; }
+  S[0][0] = 0; len[0] = 1;
+  for (int l = 0; l < k; ++l) {
+    long long a = e[l].val, n0 = len[l];
+    if (2 * n0 > SUM_CAP) { rc = ORC_ETOOBIG; goto done; }
+    long long *out = (long long *)malloc((size_t)(2 * n0) * sizeof(long long));
+    if (!out) { rc = ORC_ENOMEM; goto done; }
+    long long i = 0, j = 0, t = 0;
+    while (i < n0 || j < n0) {  /* merge S_l and S_l + a */
+      long long x = i < n0 ? S[l][i] : LLONG_MAX;
+      long long y = j < n0 ? S[l][j] + a : LLONG_MAX;
+      long long v;
+      if (x <= y) { v = x; ++i; if (x == y) ++j; } else { v = y; ++j; }
+      if (t == 0 || out[t - 1] != v) out[t++] = v;
+    }
+    S[l + 1] = out; len[l + 1] = t;
+  }
+  /* bottom-up: classes.  Layer k holds the terminal outcome of each complete sum. */
+  cls[k] = (int *)malloc((size_t)len[k] * sizeof(int));
+  if (!cls[k]) { rc = ORC_ENOMEM; goto done; }
+  for (long long t = 0; t < len[k]; ++t) cls[k][t] = sat(S[k][t], sense, b) ? ORC_TOP : ORC_BOT;
+  for (int l = k - 1; l >= 0; --l) {
+    long long a = e[l].val, nl = len[l];
+    cls[l] = (int *)malloc((size_t)nl * sizeof(int));
+    /* open-addressing table: (lo, hi) pair -> node id */
+    long long cap = 16;
+    while (cap < 2 * nl) cap <<= 1;
+    unsigned long long *keys = (unsigned long long *)malloc((size_t)cap * sizeof(unsigned long long));
+    int *ids = (int *)malloc((size_t)cap * sizeof(int));
+    if (!cls[l] || !keys || !ids) { free(keys); free(ids); rc = ORC_ENOMEM; goto done; }
+    for (long long t = 0; t < cap; ++t) keys[t] = ~0ULL;
+    int next_id = 0;
+    for (long long t = 0; t < nl; ++t) {   /* ascending s: ids come out in min-sum order */
+      long long s = S[l][t];
+      int c0 = cls[l + 1][find_sum(S[l + 1], len[l + 1], s)];
+      int c1 = cls[l + 1][find_sum(S[l + 1], len[l + 1], s + a)];
+      if (c0 == ORC_BOT && c1 == ORC_BOT) { cls[l][t] = ORC_BOT; continue; }
+      unsigned long long key = ((unsigned long long)(unsigned)(c0 + 2) << 32) | (unsigned)(c1 + 2);
+      unsigned long long hsh = key * 0x9E3779B97F4A7C15ULL;
+      long long slot = (long long)(hsh >> 20) & (cap - 1);
+      while (keys[slot] != ~0ULL && keys[slot] != key) slot = (slot + 1) & (cap - 1);
+      if (keys[slot] == ~0ULL) {
+        keys[slot] = key; ids[slot] = next_id++;
+        if (iv_push(&Llo[l], c0) || iv_push(&Lhi[l], c1) || lv_push(&Lmin[l], s)) {
+          free(keys); free(ids); rc = ORC_ENOMEM; goto done;
+        }
+      }
+      cls[l][t] = ids[slot];
+    }
+    free(keys); free(ids);
+  }
+  if (cls[0][0] == ORC_BOT) { rc = ORC_EINFEASIBLE; goto done; }
+  /* emit */
+  if (iv_push(bdd_row, row) || iv_push(bdd_k, k)) { rc = ORC_ENOMEM; goto done; }
+  for (int l = 0; l < k; ++l) {
+    long long nodes_before = lo->n;
+    if (iv_push(occ_var, e[l].col) || lv_push(occ_csr, e[l].pos) || lv_push(occ_node0, nodes_before)) {
+      rc = ORC_ENOMEM; goto done;
+    }
+    for (long long t = 0; t < Llo[l].n; ++t)
+      if (iv_push(lo, Llo[l].p[t]) || iv_push(hi, Lhi[l].p[t]) || lv_push(minsum, Lmin[l].p[t])) {
+        rc = ORC_ENOMEM; goto done;
+      }
+  }
+done:
+  if (S) for (int l = 0; l <= k; ++l) free(S[l]);
+  if (cls) for (int l = 0; l <= k; ++l) free(cls[l]);
+  if (Llo) for (int l = 0; l < k; ++l) { free(Llo[l].p); free(Lhi[l].p); free(Lmin[l].p); }
+  free(S); free(len); free(cls); free(Llo); free(Lhi); free(Lmin);
+  return rc;
+}
+
+/* Builds all BDDs.  status: ORC_* code; failed_row: the row that made it fail (or -1). */
+void *orc_build(int n, int m, const long long *row_ptr, const int *col, const int *val,
+                const int *b, const signed char *sense, const double *c, int *status,
+                int *failed_row) {
+  *status = ORC_OK; *failed_row = -1;
+  if (n < 0 || m < 0) { *status = ORC_EINVAL; return NULL; }
+  for (int i = 0; i < n; ++i)
+    if (!isfinite(c[i])) { *status = ORC_EINVAL; return NULL; }
+  oracle_t *h = (oracle_t *)calloc(1, sizeof(oracle_t));
+  if (!h) { *status = ORC_ENOMEM; return NULL; }
+  h->n = n; h->m = m; h->nnz = m ? row_ptr[m] : 0;
+  ivec bdd_row = {0}, bdd_k = {0}, occ_var = {0}, lo = {0}, hi = {0};
+  lvec occ_csr = {0}, occ_node0 = {0}, minsum = {0};
+  int rc = ORC_OK;
+  for (int j = 0; j < m && rc == ORC_OK; ++j) {
+    long long s = row_ptr[j], e = row_ptr[j + 1];
+    if (e < s || sense[j] < -1 || sense[j] > 1) { rc = ORC_EINVAL; *failed_row = j; break; }
+    int k = 0;
+    entry_t *ent = (entry_t *)malloc((size_t)(e - s + 1) * sizeof(entry_t));
+    if (!ent) { rc = ORC_ENOMEM; break; }
+    for (long long t = s; t < e; ++t) {
+      if (col[t] < 0 || col[t] >= n) { rc = ORC_EINVAL; break; }
+      if (val[t] == 0) continue;            /* zero coefficients are not in I_j */
+      ent[k].col = col[t]; ent[k].val = val[t]; ent[k].pos = t; ++k;
+    }
+    if (rc == ORC_OK) {
+      qsort(ent, (size_t)k, sizeof(entry_t), cmp_entry);
+      for (int t = 1; t < k; ++t)
+        if (ent[t].col == ent[t - 1].col) rc = ORC_EINVAL;   /* duplicate (j, i) */
+    }
+    if (rc == ORC_OK) {
+      if (k == 0) {
+        if (!sat(0, sense[j], b[j])) rc = ORC_EINFEASIBLE;
+      } else {
+        rc = build_row(ent, k, b[j], sense[j], j, &bdd_row, &bdd_k, &occ_var, &occ_csr,
+                       &occ_node0, &lo, &hi, &minsum);
+      }
+    }
+    if (rc != ORC_OK) *failed_row = j;
+    free(ent);
+  }
+  h->bdd_row = bdd_row.p; h->bdd_k = bdd_k.p; h->occ_var = occ_var.p; h->occ_csr = occ_csr.p;
+  h->lo = lo.p; h->hi = hi.p; h->minsum = minsum.p;
+  h->nb = (int)bdd_row.n; h->O = occ_var.n; h->N = lo.n;
+  if (rc != ORC_OK) { free(occ_node0.p); orc_free(h); *status = rc; return NULL; }
+  if (lv_push(&occ_node0, h->N)) { free(occ_node0.p); orc_free(h); *status = ORC_ENOMEM; return NULL; }
+  h->occ_node0 = occ_node0.p;
+
+  long long O = h->O, N = h->N;
+  h->bdd_occ0 = (long long *)malloc((size_t)(h->nb + 1) * sizeof(long long));
+  h->occ_bdd = (int *)malloc((size_t)(O + 1) * sizeof(int));
+  h->occ_layer = (int *)malloc((size_t)(O + 1) * sizeof(int));
+  h->var_ptr = (long long *)calloc((size_t)n + 1, sizeof(long long));
+  h->var_occ = (long long *)malloc((size_t)(O + 1) * sizeof(long long));
+  h->deg = (int *)calloc((size_t)n + 1, sizeof(int));
+  h->c = (double *)malloc((size_t)(n + 1) * sizeof(double));
+  h->lam = (double *)calloc((size_t)O + 1, sizeof(double));
+  h->delta = (double *)calloc((size_t)O + 1, sizeof(double));
+  h->P = (double *)calloc((size_t)n + 1, sizeof(double));
+  h->share = (double *)calloc((size_t)n + 1, sizeof(double));
+  h->fm = (double *)calloc((size_t)N + 1, sizeof(double));
+  h->bm = (double *)calloc((size_t)N + 1, sizeof(double));
+  h->sfm = (double *)calloc((size_t)N + 1, sizeof(double));
+  h->sbm = (double *)calloc((size_t)N + 1, sizeof(double));
+  if (!h->bdd_occ0 || !h->occ_bdd || !h->occ_layer || !h->var_ptr || !h->var_occ || !h->deg ||
+      !h->c || !h->lam || !h->delta || !h->P || !h->share || !h->fm || !h->bm || !h->sfm ||
+      !h->sbm) {
+    orc_free(h); *status = ORC_ENOMEM; return NULL;
+  }
+  long long o = 0;
+  h->max_depth = 0; h->max_width = 0;
+  for (int bb = 0; bb < h->nb; ++bb) {
+    h->bdd_occ0[bb] = o;
+    if (h->bdd_k[bb] > h->max_depth) h->max_depth = h->bdd_k[bb];
+    for (int l = 0; l < h->bdd_k[bb]; ++l, ++o) {
+      h->occ_bdd[o] = bb; h->occ_layer[o] = l;
+      int w = (int)(h->occ_node0[o + 1] - h->occ_node0[o]);
+      if (w > h->max_width) h->max_width = w;
+    }
+  }
+  h->bdd_occ0[h->nb] = o;
+  for (long long t = 0; t < O; ++t) h->deg[h->occ_var[t]]++;
+  for (int i = 0; i < n; ++i) h->var_ptr[i + 1] = h->var_ptr[i] + h->deg[i];
+  {
+    long long *fill = (long long *)malloc((size_t)(n + 1) * sizeof(long long));
+    if (!fill) { orc_free(h); *status = ORC_ENOMEM; return NULL; }
+    memcpy(fill, h->var_ptr, (size_t)(n + 1) * sizeof(long long));
+    for (long long t = 0; t < O; ++t) h->var_occ[fill[h->occ_var[t]]++] = t;  /* ascending row */
+    free(fill);
+  }
+  h->empty_const = 0.0;
+  for (int i = 0; i < n; ++i) {
+    h->c[i] = c[i];
+    if (h->deg[i] == 0 && c[i] < 0) h->empty_const += c[i];
+  }
+  return h;
+}
+
+void orc_sizes(void *vh, long long out[8]) {
+  oracle_t *h = (oracle_t *)vh;
+  out[0] = h->n; out[1] = h->m; out[2] = h->nb; out[3] = h->O; out[4] = h->N;
+  out[5] = h->max_depth; out[6] = h->max_width; out[7] = h->nnz;
+}
+
+/* Canonical export: BDDs in ascending row order; occurrences BDD-major, layer-minor; nodes
+ * BDD-major, layer-major, canonical order inside a layer; lo/hi are next-layer local ids. */
+void orc_export(void *vh, int *bdd_row, int *bdd_depth, int *occ_var, long long *occ_csr,
+                int *occ_width, int *lo, int *hi, long long *minsum) {
+  oracle_t *h = (oracle_t *)vh;
+  for (int b = 0; b < h->nb; ++b) { bdd_row[b] = h->bdd_row[b]; bdd_depth[b] = h->bdd_k[b]; }
+  for (long long o = 0; o < h->O; ++o) {
+    occ_var[o] = h->occ_var[o];
+    occ_csr[o] = h->occ_csr[o];
+    occ_width[o] = (int)(h->occ_node0[o + 1] - h->occ_node0[o]);
+  }
+  for (long long v = 0; v < h->N; ++v) {
+    lo[v] = h->lo[v]; hi[v] = h->hi[v];
+    if (minsum) minsum[v] = h->minsum[v];
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* dynamic programmes (Alg. 2 / Alg. 3, eqs. arc-marginal and marginal-aggregation)       */
+/* ------------------------------------------------------------------------------------ */
+/* backward message of the target t of an arc leaving layer o (t is a local id in o+1) */
+static double bval(const oracle_t *h, const double *bm, long long o, int t) {
+  if (t == ORC_TOP) return 0.0;
+  if (t == ORC_BOT) return INFINITY;
+  return bm[h->occ_node0[o + 1] + t];
+}
+
+/* Full forward programme of BDD b into fm: m_fwd(root) = 0, then for every layer the min
+ * over in-arcs (each arc relaxed once). */
+static void dp_forward(const oracle_t *h, int b, const double *lam, double *fm) {
+  long long o0 = h->bdd_occ0[b];
+  int k = h->bdd_k[b];
+  fm[h->occ_node0[o0]] = 0.0;
+  for (int l = 1; l < k; ++l) {
+    long long o = o0 + l;
+    for (long long v = h->occ_node0[o]; v < h->occ_node0[o + 1]; ++v) fm[v] = INFINITY;
+    for (long long u = h->occ_node0[o - 1]; u < h->occ_node0[o]; ++u) {
+      if (h->lo[u] >= 0) {
+        long long v = h->occ_node0[o] + h->lo[u];
+        if (fm[u] < fm[v]) fm[v] = fm[u];
+      }
+      if (h->hi[u] >= 0) {
+        long long v = h->occ_node0[o] + h->hi[u];
+        double x = fm[u] + lam[o - 1];
+        if (x < fm[v]) fm[v] = x;
+      }
+    }
+  }
+}
+
+/* backward update step (Alg. 3) for the nodes of occurrence o */
+static void bwd_step(const oracle_t *h, long long o, double lam_o, double *bm) {
+  for (long long u = h->occ_node0[o]; u < h->occ_node0[o + 1]; ++u) {
+    double a0 = bval(h, bm, o, h->lo[u]);
+    double a1 = lam_o + bval(h, bm, o, h->hi[u]);
+    if (h->hi[u] == ORC_BOT) a1 = INFINITY;
+    bm[u] = a0 < a1 ? a0 : a1;
+  }
+}
+
+/* Full backward programme of BDD b into bm; returns E^j = m_bwd(root). */
+static double dp_backward(const oracle_t *h, int b, const double *lam, double *bm) {
+  long long o0 = h->bdd_occ0[b];
+  for (int l = h->bdd_k[b] - 1; l >= 0; --l) bwd_step(h, o0 + l, lam[o0 + l], bm);
+  return bm[h->occ_node0[o0]];
+}
+
+/* min-marginals of occurrence o from fm (its layer) and bm (next layer) */
+static void aggregate(const oracle_t *h, long long o, double lam_o, const double *fm,
+                      const double *bm, double *m0, double *m1) {
+  double a = INFINITY, c1 = INFINITY;
+  for (long long u = h->occ_node0[o]; u < h->occ_node0[o + 1]; ++u) {
+    if (h->lo[u] != ORC_BOT) {
+      double x = fm[u] + bval(h, bm, o, h->lo[u]);
+      if (x < a) a = x;
+    }
+    if (h->hi[u] != ORC_BOT) {
+      double x = fm[u] + lam_o + bval(h, bm, o, h->hi[u]);
+      if (x < c1) c1 = x;
+    }
+  }
+  *m0 = a; *m1 = c1;
+}
+
+/* Definitional min-marginals of occurrence o under lam: full programmes on scratch arrays. */
+static void minmarg_full(oracle_t *h, long long o, const double *lam, double *m0, double *m1) {
+  int b = h->occ_bdd[o];
+  dp_forward(h, b, lam, h->sfm);
+  dp_backward(h, b, lam, h->sbm);
+  aggregate(h, o, lam[o], h->sfm, h->sbm, m0, m1);
+}
+
+static double energy(oracle_t *h, int b, const double *lam) {
+  return dp_backward(h, b, lam, h->sbm);
+}
+
+/* y-slack lower bound for the current lam and pending P (fresh programmes) */
+double orc_bound(void *vh) {
+  oracle_t *h = (oracle_t *)vh;
+  double lb = h->empty_const;
+  for (int b = 0; b < h->nb; ++b) lb += energy(h, b, h->lam);
+  for (int i = 0; i < h->n; ++i)
+    if (h->deg[i] > 0 && h->P[i] < 0) lb += h->P[i];
+  return lb;
+}
+
+static double mm_diff(double m0, double m1) {
+  return (isinf(m0) || isinf(m1)) ? 0.0 : m1 - m0;
+}
+
+static double rel(double err, double scale) {
+  return fabs(err) / (1.0 > fabs(scale) ? 1.0 : fabs(scale));
+}
+
+static void note(double *w, double v) { if (v > *w) *w = v; }
+
+/* ------------------------------------------------------------------------------------ */
+/* initialisation                                                                         */
+/* ------------------------------------------------------------------------------------ */
+/* lambda^j_i = c_i / |J_i| (Alg. 1 initialisation), P = 0, then a full backward programme
+ * so that every backward message is valid (precondition of Prop. 3). */
+void orc_init_dual(void *vh) {
+  oracle_t *h = (oracle_t *)vh;
+  for (long long o = 0; o < h->O; ++o) h->lam[o] = h->c[h->occ_var[o]] / h->deg[h->occ_var[o]];
+  for (int i = 0; i < h->n; ++i) h->P[i] = 0.0;
+  for (int b = 0; b < h->nb; ++b) dp_backward(h, b, h->lam, h->bm);
+  for (int t = 0; t < 5; ++t) h->worst[t] = 0.0;
+}
+
+void orc_worst(void *vh, double out[5]) {
+  oracle_t *h = (oracle_t *)vh;
+  for (int t = 0; t < 5; ++t) out[t] = h->worst[t];
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* schedule P: parallel across BDDs, deferred averaging                                   */
+/* ------------------------------------------------------------------------------------ */
+static void check_invariant(oracle_t *h) {
+  for (int i = 0; i < h->n; ++i) {
+    if (h->deg[i] == 0) continue;
+    double s = h->P[i], scale = fabs(h->c[i]) + fabs(h->P[i]);
+    for (long long t = h->var_ptr[i]; t < h->var_ptr[i + 1]; ++t) {
+      s += h->lam[h->var_occ[t]];
+      scale += fabs(h->lam[h->var_occ[t]]);
+    }
+    note(&h->worst[1], rel(s - h->c[i], scale));
+  }
+}
+
+static void form_pending(oracle_t *h) {
+  for (int i = 0; i < h->n; ++i) {
+    double s = 0.0;
+    for (long long t = h->var_ptr[i]; t < h->var_ptr[i + 1]; ++t) s += h->delta[h->var_occ[t]];
+    h->P[i] = s;
+  }
+}
+
+static void take_share(oracle_t *h) {
+  for (int i = 0; i < h->n; ++i) h->share[i] = h->deg[i] ? h->P[i] / h->deg[i] : 0.0;
+}
+
+static void sweep_forward(oracle_t *h, double omega, int check) {
+  take_share(h);
+  for (int b = 0; b < h->nb; ++b) {
+    long long o0 = h->bdd_occ0[b];
+    int k = h->bdd_k[b];
+    h->fm[h->occ_node0[o0]] = 0.0;
+    for (int l = 0; l < k; ++l) {
+      long long o = o0 + l;
+      if (l > 0) {  /* Alg. 2 for the nodes of layer l */
+        for (long long v = h->occ_node0[o]; v < h->occ_node0[o + 1]; ++v) h->fm[v] = INFINITY;
+        for (long long u = h->occ_node0[o - 1]; u < h->occ_node0[o]; ++u) {
+          if (h->lo[u] >= 0) {
+            long long v = h->occ_node0[o] + h->lo[u];
+            if (h->fm[u] < h->fm[v]) h->fm[v] = h->fm[u];
+          }
+          if (h->hi[u] >= 0) {
+            long long v = h->occ_node0[o] + h->hi[u];
+            double x = h->fm[u] + h->lam[o - 1];
+            if (x < h->fm[v]) h->fm[v] = x;
+          }
+        }
+      }
+      h->lam[o] += h->share[h->occ_var[o]];
+      double m0, m1;
+      aggregate(h, o, h->lam[o], h->fm, h->bm, &m0, &m1);
+      if (check) {
+        double r0, r1;
+        minmarg_full(h, o, h->lam, &r0, &r1);
+        if (isinf(r0) != isinf(m0) || isinf(r1) != isinf(m1)) note(&h->worst[2], INFINITY);
+        if (!isinf(r0)) note(&h->worst[2], rel(r0 - m0, r0));
+        if (!isinf(r1)) note(&h->worst[2], rel(r1 - m1, r1));
+      }
+      double d = omega * mm_diff(m0, m1);
+      h->lam[o] -= d;
+      h->delta[o] = d;
+    }
+  }
+  form_pending(h);
+}
+
+static void sweep_backward(oracle_t *h, double omega, int check) {
+  take_share(h);
+  for (int b = 0; b < h->nb; ++b) {
+    long long o0 = h->bdd_occ0[b];
+    for (int l = h->bdd_k[b] - 1; l >= 0; --l) {
+      long long o = o0 + l;
+      h->lam[o] += h->share[h->occ_var[o]];
+      double m0, m1;
+      aggregate(h, o, h->lam[o], h->fm, h->bm, &m0, &m1);
+      if (check) {
+        double r0, r1;
+        minmarg_full(h, o, h->lam, &r0, &r1);
+        if (isinf(r0) != isinf(m0) || isinf(r1) != isinf(m1)) note(&h->worst[2], INFINITY);
+        if (!isinf(r0)) note(&h->worst[2], rel(r0 - m0, r0));
+        if (!isinf(r1)) note(&h->worst[2], rel(r1 - m1, r1));
+      }
+      double d = omega * mm_diff(m0, m1);
+      h->lam[o] -= d;
+      h->delta[o] = d;
+      bwd_step(h, o, h->lam[o], h->bm);  /* Alg. 3 with the updated lambda */
+    }
+  }
+  form_pending(h);
+}
+
+/* bound from the current messages: valid right after a backward sweep */
+static double bound_after_backward(const oracle_t *h) {
+  double lb = h->empty_const;
+  for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];
+  for (int i = 0; i < h->n; ++i)
+    if (h->deg[i] > 0 && h->P[i] < 0) lb += h->P[i];
+  return lb;
+}
+
+/* iters iterations (forward sweep, backward sweep) of schedule P.  trace[t] = bound after
+ * iteration t.  check: invariant, incremental-vs-definitional min-marginals and a fresh bound
+ * after every sweep (monotonicity), recorded in orc_worst(). */
+int orc_run_parallel(void *vh, int iters, double omega, int check, double *trace) {
+  oracle_t *h = (oracle_t *)vh;
+  double prev = check ? orc_bound(h) : 0.0;
+  for (int it = 0; it < iters; ++it) {
+    sweep_forward(h, omega, check);
+    if (check) {
+      check_invariant(h);
+      double lb = orc_bound(h);
+      note(&h->worst[0], rel(prev - lb, lb) * (prev > lb ? 1.0 : 0.0));
+      prev = lb;
+    }
+    sweep_backward(h, omega, check);
+    double lb = bound_after_backward(h);
+    if (check) {
+      check_invariant(h);
+      double fresh = orc_bound(h);
+      note(&h->worst[2], rel(fresh - lb, fresh));
+      note(&h->worst[0], rel(prev - fresh, fresh) * (prev > fresh ? 1.0 : 0.0));
+      prev = fresh;
+    }
+    if (trace) trace[it] = lb;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* schedule S: Alg. 1 with definitional min-marginals                                     */
+/* ------------------------------------------------------------------------------------ */
+static void visit_variable(oracle_t *h, int i, int check, double *m0s, double *m1s) {
+  long long s = h->var_ptr[i], e = h->var_ptr[i + 1];
+  int J = (int)(e - s);
+  if (J == 0) return;
+  double S = 0.0, neg = 0.0, before = 0.0;
+  int finite = 1;
+  for (long long t = s; t < e; ++t) {
+    long long o = h->var_occ[t];
+    minmarg_full(h, o, h->lam, &m0s[t - s], &m1s[t - s]);
+    if (isinf(m0s[t - s]) || isinf(m1s[t - s])) finite = 0;
+    double d = mm_diff(m0s[t - s], m1s[t - s]);
+    S += d;
+    if (d < 0) neg += d;
+    if (check) before += energy(h, h->occ_bdd[o], h->lam);
+  }
+  for (long long t = s; t < e; ++t) {  /* eq. (mma-update) */
+    long long o = h->var_occ[t];
+    h->lam[o] += -mm_diff(m0s[t - s], m1s[t - s]) + S / J;
+  }
+  if (check) {
+    double after = 0.0;
+    for (long long t = s; t < e; ++t) after += energy(h, h->occ_bdd[h->var_occ[t]], h->lam);
+    double gain = after - before;
+    double scale = fabs(before) + fabs(S) + fabs(neg);
+    if (finite) note(&h->worst[3], rel(gain - ((S < 0 ? S : 0.0) - neg), scale));
+    if (gain < 0) note(&h->worst[4], rel(gain, scale));
+  }
+}
+
+/* iters iterations of Alg. 1 (forward pass over i = 0..n-1, backward pass over n-1..0),
+ * trace[t] = sum_j E^j after iteration t.  Requires each variable to lie in distinct rows
+ * only once (true by construction). */
+int orc_run_sequential(void *vh, int iters, int check, double *trace) {
+  oracle_t *h = (oracle_t *)vh;
+  int maxJ = 1;
+  for (int i = 0; i < h->n; ++i) if (h->deg[i] > maxJ) maxJ = h->deg[i];
+  double *m0s = (double *)malloc((size_t)maxJ * sizeof(double));
+  double *m1s = (double *)malloc((size_t)maxJ * sizeof(double));
+  if (!m0s || !m1s) { free(m0s); free(m1s); return ORC_ENOMEM; }
+  for (int i = 0; i < h->n; ++i) h->P[i] = 0.0;
+  double prev = orc_bound(h);
+  for (int it = 0; it < iters; ++it) {
+    for (int i = 0; i < h->n; ++i) visit_variable(h, i, check, m0s, m1s);
+    for (int i = h->n - 1; i >= 0; --i) visit_variable(h, i, check, m0s, m1s);
+    double lb = orc_bound(h);
+    if (check) {
+      check_invariant(h);
+      note(&h->worst[0], rel(prev - lb, lb) * (prev > lb ? 1.0 : 0.0));
+    }
+    prev = lb;
+    if (trace) trace[it] = lb;
+  }
+  /* leave messages consistent with lambda */
+  for (int b = 0; b < h->nb; ++b) dp_backward(h, b, h->lam, h->bm);
+  free(m0s); free(m1s);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* state access (arrays indexed by position in the input CSR; zero coefficients get 0)    */
+/* ------------------------------------------------------------------------------------ */
+/* lambda per coefficient; fold != 0 adds the pending share P_i/|J_i|, so that the returned
+ * multipliers satisfy sum_j lambda^j_i = c_i. */
+void orc_get_lambda(void *vh, int fold, double *out) {
+  oracle_t *h = (oracle_t *)vh;
+  for (long long t = 0; t < h->nnz; ++t) out[t] = 0.0;
+  for (long long o = 0; o < h->O; ++o) {
+    int i = h->occ_var[o];
+    out[h->occ_csr[o]] = h->lam[o] + (fold ? h->P[i] / h->deg[i] : 0.0);
+  }
+}
+
+void orc_get_pending(void *vh, double *P) {
+  oracle_t *h = (oracle_t *)vh;
+  for (int i = 0; i < h->n; ++i) P[i] = h->P[i];
+}
+
+/* Sets lambda (per CSR position) and P (NULL = 0), then recomputes backward messages. */
+void orc_set_state(void *vh, const double *lam, const double *P) {
+  oracle_t *h = (oracle_t *)vh;
+  for (long long o = 0; o < h->O; ++o) h->lam[o] = lam[h->occ_csr[o]];
+  for (int i = 0; i < h->n; ++i) h->P[i] = P ? P[i] : 0.0;
+  for (int b = 0; b < h->nb; ++b) dp_backward(h, b, h->lam, h->bm);
+}
+
+/* Definitional min-marginals (full forward and backward programmes, then eq.
+ * marginal-aggregation) for the current lambda, or lambda + P/|J| when fold != 0. */
+void orc_min_marginals(void *vh, int fold, double *m0, double *m1) {
+  oracle_t *h = (oracle_t *)vh;
+  double *lam = (double *)malloc((size_t)(h->O + 1) * sizeof(double));
+  if (!lam) return;
+  for (long long o = 0; o < h->O; ++o) {
+    int i = h->occ_var[o];
+    lam[o] = h->lam[o] + (fold ? h->P[i] / h->deg[i] : 0.0);
+  }
+  for (long long t = 0; t < h->nnz; ++t) { m0[t] = 0.0; m1[t] = 0.0; }
+  for (int b = 0; b < h->nb; ++b) {
+    dp_forward(h, b, lam, h->sfm);
+    dp_backward(h, b, lam, h->sbm);
+    for (int l = 0; l < h->bdd_k[b]; ++l) {
+      long long o = h->bdd_occ0[b] + l;
+      aggregate(h, o, lam[o], h->sfm, h->sbm, &m0[h->occ_csr[o]], &m1[h->occ_csr[o]]);
+    }
+  }
+  free(lam);
+}
+
+/* Per-BDD energies E^j(lambda^j) (min over X_j) and solution counts |X_j| (Table 3's counting
+ * algebra: count(v) = count(v0) + count(v1), count(top) = 1, count(bot) = 0). */
+void orc_energies(void *vh, double *E) {
+  oracle_t *h = (oracle_t *)vh;
+  for (int b = 0; b < h->nb; ++b) E[b] = energy(h, b, h->lam);
+}
+
+void orc_counts(void *vh, double *counts) {
+  oracle_t *h = (oracle_t *)vh;
+  for (int b = 0; b < h->nb; ++b) {
+    long long o0 = h->bdd_occ0[b];
+    for (int l = h->bdd_k[b] - 1; l >= 0; --l) {
+      long long o = o0 + l;
+      for (long long u = h->occ_node0[o]; u < h->occ_node0[o + 1]; ++u) {
+        double x = 0.0;
+        int t0 = h->lo[u], t1 = h->hi[u];
+        x += t0 == ORC_TOP ? 1.0 : (t0 == ORC_BOT ? 0.0 : h->sfm[h->occ_node0[o + 1] + t0]);
+        x += t1 == ORC_TOP ? 1.0 : (t1 == ORC_BOT ? 0.0 : h->sfm[h->occ_node0[o + 1] + t1]);
+        h->sfm[u] = x;
+      }
+    }
+    counts[b] = h->sfm[h->occ_node0[o0]];
+  }
+}

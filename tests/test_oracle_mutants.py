@@ -1,0 +1,102 @@
+"""Planted mistakes: copies of oracle.c with one plausible error each must fail the pins.
+
+Each mutant is a textual edit of a copy of the oracle source, compiled on the CPU into a
+temporary directory; the original oracle is untouched.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from instances import SENSE_EQ, SENSE_GE, SENSE_LE, random_ilp
+from instances.generators import _from_rows
+from oracle import Oracle, OracleError, load_variant
+from tests import bruteforce as bf
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "oracle.c")
+
+MUTANTS = {
+    # min-marginal difference with the wrong sign
+    "sign": ("return (isinf(m0) || isinf(m1)) ? 0.0 : m1 - m0;",
+             "return (isinf(m0) || isinf(m1)) ? 0.0 : m0 - m1;"),
+    # deferred averaging share never applied in the forward sweep
+    "drop_share": ("        }\n      }\n      h->lam[o] += h->share[h->occ_var[o]];",
+                   "        }\n      }\n"),
+    # forward update step charges the 1-arc with the wrong layer's multiplier
+    "fwd_index": ("            double x = h->fm[u] + h->lam[o - 1];\n            if (x < h->fm[v]) h->fm[v] = x;\n          }\n        }\n      }\n      h->lam[o]",
+                  "            double x = h->fm[u] + h->lam[o];\n            if (x < h->fm[v]) h->fm[v] = x;\n          }\n        }\n      }\n      h->lam[o]"),
+    # BDD builder swaps the 0- and 1-successor
+    "swap_arcs": ("iv_push(&Llo[l], c0) || iv_push(&Lhi[l], c1)",
+                  "iv_push(&Llo[l], c1) || iv_push(&Lhi[l], c0)"),
+    # backward step drops the 1-arc cost
+    "bwd_theta": ("double a1 = lam_o + bval(h, bm, o, h->hi[u]);",
+                  "double a1 = bval(h, bm, o, h->hi[u]);"),
+    # bound forgets the slack term of the y-variables
+    "bound_slack": ("  for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];\n  for (int i = 0; i < h->n; ++i)\n    if (h->deg[i] > 0 && h->P[i] < 0) lb += h->P[i];",
+                    "  for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];"),
+}
+
+
+def _compile(tmp_path, name):
+    src = open(SRC).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / f"lib{name}.so"
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", str(so), str(path), "-lm"])
+    return load_variant(str(so))
+
+
+def _pins_hold(lib) -> bool:
+    """A compact battery of the pins: enumeration of BDDs and min-marginals, the parallel
+    schedule's checks, and weak duality against brute force."""
+    rng = np.random.default_rng(7)
+    for t in range(12):
+        k = int(rng.integers(2, 9))
+        vals = rng.integers(1, 4, size=k) * rng.choice([-1, 1], size=k)
+        sense = [SENSE_LE, SENSE_EQ, SENSE_GE][t % 3]
+        x0 = rng.integers(0, 2, size=k)
+        b = int(vals @ x0)
+        lam = rng.normal(size=k)
+        inst = _from_rows("r", k, [(np.arange(k), vals, b, sense)], np.zeros(k, np.float32))
+        try:
+            o = Oracle(inst, lib=lib)
+        except OracleError:
+            return False
+        layers = bf.split_bdds(o.canonical())[0]
+        feas = bf.row_feasible(vals, b, sense)
+        acc = np.array([bf.walk(layers, x)[0] for x in bf.assignments(k)])
+        if not np.array_equal(acc, feas):
+            return False
+        o.set_state(lam)
+        m0, m1 = o.min_marginals(fold=False)
+        em0, em1, _, _ = bf.min_marginals_enum(vals, b, sense, lam)
+        if not (np.allclose(m0, em0, atol=1e-12) and np.allclose(m1, em1, atol=1e-12)):
+            return False
+    for seed in range(3):
+        inst = random_ilp(n=14, m=10, max_row_vars=6, seed=500 + seed)
+        opt = bf.ilp_optimum(inst)
+        o = Oracle(inst, lib=lib)
+        tr = o.run_parallel(15, omega=0.5, check=True)
+        w = o.worst()
+        if w["incremental_mm"] > 1e-10 or w["invariant"] > 1e-12 or w["monotone_drop"] > 1e-12:
+            return False
+        if tr.max() > opt + 1e-9:
+            return False
+    return True
+
+
+def test_original_passes_battery():
+    from oracle import _load
+    assert _pins_hold(_load())
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    lib = _compile(tmp_path, name)
+    assert not _pins_hold(lib), f"planted mistake '{name}' passed every pin"
