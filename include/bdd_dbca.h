@@ -1,0 +1,142 @@
+/*
+ * bdd_dbca.h -- C ABI of the GB300 library for BDD-based dual block coordinate ascent on
+ * 0-1 integer linear programs (Lange & Swoboda, "Efficient Message Passing for 0-1 ILPs with
+ * Binary Decision Diagrams").
+ *
+ * Problem (Sec. 3, Def. 1 and Ex. 1):  min c.x  s.t.  a_j.x (<=, =, >=) b_j for every row j,
+ * x in {0,1}^n.  Each row becomes one subproblem with index set I_j = { i : a_ji != 0 } and
+ * one reduced, ordered BDD (Sec. 5.1, Def. 4).  The library maximises the Lagrangean dual
+ * (Sec. 3.1, eq. D) over multipliers lambda^j_i, one per nonzero coefficient ("occurrence"),
+ * by min-marginal averaging (Sec. 3.2, eq. mma-update) with BDD shortest-path messages
+ * (Sec. 5.3, Alg. 2 and Alg. 3; Sec. 5.4 incremental form), parallel across BDDs with the
+ * averaging share of each sweep applied in the next sweep, damped by omega.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a status (BDD_OK or a negative BDD_E* code).  No call throws.
+ *   - Inputs are copied; the caller keeps ownership of every array it passes.  Outputs go to
+ *     caller-allocated arrays (host arrays unless the name ends in _device).
+ *   - Per-coefficient arrays (lambda, mm0, mm1) are indexed by position in the caller's CSR
+ *     arrays (col/val).  Positions whose coefficient is 0 are not occurrences (Ex. 1 drops
+ *     them) and receive 0.
+ *   - One solver handle must not be used from two host threads at once.
+ *   - Device calls run on the solver's stream unless a stream is passed; results are
+ *     stream-ordered.  Host-array calls synchronise before returning.
+ */
+#ifndef BDD_DBCA_H
+#define BDD_DBCA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bdd_solver bdd_solver; /* opaque; created by bdd_build, released by bdd_free */
+
+enum {
+  BDD_OK = 0,
+  BDD_EINVAL = -1,      /* malformed input: bad sizes / indices, duplicate (row, column), NaN/Inf cost, bad option */
+  BDD_EINFEASIBLE = -2, /* a row has no 0-1 solution (see bdd_last_failed_row) */
+  BDD_ETOOBIG = -3,     /* a BDD or the instance exceeds max_width / max_nodes or 32-bit indexing */
+  BDD_ENOMEM = -4,      /* host allocation failed or max_device_bytes would be exceeded */
+  BDD_ECUDA = -5,       /* a CUDA runtime call failed (no device, launch failure, ...) */
+  BDD_ETIMEOUT = -6,    /* reserved: a bounded device-side wait gave up */
+  BDD_EDEVICE = -7,     /* a device-side check failed */
+  BDD_ESTATE = -8       /* the call needs device state but the solver was built host-only */
+};
+
+#define BDD_SIZES_LEN 12
+
+/* Options for bdd_build.  Fill with bdd_default_options, then change fields. */
+typedef struct {
+  float omega;                /* damping of the min-marginal difference, in (0, 1]; default 0.5 */
+  int max_width;              /* largest allowed BDD layer width; default 1 << 20 */
+  long long max_nodes;        /* largest allowed total node count; default 2^31 - 1 */
+  long long max_device_bytes; /* cap on device memory of the solver, 0 = no cap */
+  int host_only;              /* 0: normal.  1: compile BDDs on the host only (no GPU needed);
+                                 2: also build the device slab layout, kept in host memory.  With
+                                 1 or 2 only bdd_sizes, bdd_export_canonical and bdd_free may be
+                                 called (others return BDD_ESTATE); with 2 the export reads the
+                                 slab layout back, as it does from the device */
+  int device;                 /* CUDA device ordinal; -1 = the current device (default) */
+  void *stream;               /* cudaStream_t for all device work; NULL = a stream the solver owns */
+} bdd_options;
+
+void bdd_default_options(bdd_options *opt);
+
+/* Compiles one BDD per row and, unless host_only, uploads the layer-major slabs to the GPU and
+ * initialises lambda^j_i = c_i / |J_i| (Alg. 1 initialisation) followed by one backward pass
+ * (Prop. 3 precondition).
+ *   n, m:     number of variables and rows
+ *   row_ptr:  int64[m+1] CSR row pointers; col: int32[nnz] in [0, n); val: int32[nnz]
+ *   b:        int32[m] right-hand sides; sense: int8[m], -1 (<=), 0 (=), +1 (>=)
+ *   c:        float32[n] objective (finite)
+ *   opt:      NULL = defaults
+ *   out:      receives the solver, or NULL on error
+ * Rows with no nonzero are dropped when 0 (sense) b holds and are infeasible otherwise. */
+int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int *val,
+              const int *b, const signed char *sense, const float *c, const bdd_options *opt,
+              bdd_solver **out);
+
+/* Row id that made the last failing bdd_build of this host thread fail (-1 if none). */
+int bdd_last_failed_row(void);
+
+/* Runs n_iter iterations (forward sweep, then backward sweep; Alg. 1's forward and backward
+ * pass) and copies results to host arrays:
+ *   lower_bound: double[1], the y-slack bound after the last iteration (Appendix A.1 dual
+ *                derivation; equals eq. D's objective once the pending share is folded)
+ *   lambda:      float[nnz] or NULL; multipliers with the pending share folded in, so that
+ *                sum_j lambda^j_i = c_i up to rounding
+ *   mm0, mm1:    float[nnz] or NULL; min-marginals (Sec. 3.2 eq. min-marginals) at those
+ *                multipliers, from a full forward and backward pass
+ * n_iter = 0 only evaluates the outputs.  Solver state (multipliers, pending sums) after
+ * the call is the same whether outputs are requested or not. */
+int bdd_iterate(bdd_solver *h, int n_iter, double *lower_bound, float *lambda, float *mm0,
+                float *mm1);
+
+/* Device form of bdd_iterate: all pointers are device pointers, each may be NULL.
+ *   d_bound_trace: double[n_iter], bound after every iteration
+ *   d_lambda, d_mm0, d_mm1: float[nnz] as in bdd_iterate
+ *   stream: cudaStream_t to order the work on (NULL = the solver's stream)
+ * Returns after enqueueing; nothing is synchronised. */
+int bdd_iterate_device(bdd_solver *h, int n_iter, double *d_bound_trace, float *d_lambda,
+                       float *d_mm0, float *d_mm1, void *stream);
+
+/* Same iterations as bdd_iterate_device, launched kernel by kernel with CUDA events between
+ * the kernels, for measurement.  kernel_ms[4] receives the summed device time of the forward
+ * sweeps, the reductions after them, the backward sweeps and the reductions (with the bound)
+ * after them; synchronises before returning.  kernel_ms: host double[4]. */
+int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms);
+
+/* Replaces c and restarts: lambda = c/|J_i|, pending sums 0, one backward pass.  c: float[n],
+ * host. */
+int bdd_set_costs(bdd_solver *h, const float *c);
+
+/* Sizes: out[0] n, [1] m, [2] BDDs, [3] occurrences (nonzeros kept), [4] nodes, [5] max depth,
+ * [6] max width, [7] nnz, [8] device bytes held, [9] warp tiles, [10] block tiles,
+ * [11] kernel launches per iteration. */
+int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]);
+
+/* Canonical form of the BDDs, read back from the device slabs (or the host copy when built
+ * host_only): BDDs in ascending row order; occurrences BDD-major, layer-minor; nodes
+ * BDD-major, layer-major and, inside a layer, in ascending order of the smallest partial
+ * coefficient sum that reaches them.  lo/hi are node ids inside the next layer of the same
+ * BDD, or -1 (top) / -2 (bot).  Array sizes: bdd_row, bdd_depth [BDDs]; occ_var, occ_csr,
+ * occ_width [occurrences]; lo, hi [nodes].  occ_csr is the CSR position of the coefficient. */
+int bdd_export_canonical(const bdd_solver *h, int *bdd_row, int *bdd_depth, int *occ_var,
+                         long long *occ_csr, int *occ_width, int *lo, int *hi);
+
+/* Dual state: lambda without the pending share (float[nnz], CSR positions) and the pending
+ * sums P_i (float[n]).  bdd_set_state also recomputes the backward messages. */
+int bdd_get_state(const bdd_solver *h, float *lambda, float *pending);
+int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending);
+
+/* Text for a status code (static storage). */
+const char *bdd_strerror(int code);
+
+/* Releases the solver and its device memory; NULL is ignored. */
+void bdd_free(bdd_solver *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BDD_DBCA_H */

@@ -1,0 +1,197 @@
+"""ctypes binding of the C ABI (include/bdd_dbca.h).  Argument marshalling only: every step
+of the method runs in the CUDA library.  There is no fallback: if the library is missing or
+fails to load, loading raises.
+
+Functions keep the C names.  Device buffers and streams may come from PyTorch: pass
+``tensor.data_ptr()`` and ``torch.cuda.current_stream().cuda_stream``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+BDD_OK, BDD_EINVAL, BDD_EINFEASIBLE, BDD_ETOOBIG, BDD_ENOMEM = 0, -1, -2, -3, -4
+BDD_ECUDA, BDD_ETIMEOUT, BDD_EDEVICE, BDD_ESTATE = -5, -6, -7, -8
+BDD_SIZES_LEN = 12
+
+EXPORTED = [
+    "bdd_default_options", "bdd_build", "bdd_last_failed_row", "bdd_iterate", "bdd_iterate_device",
+    "bdd_iterate_profiled",
+    "bdd_set_costs", "bdd_sizes", "bdd_export_canonical", "bdd_get_state", "bdd_set_state",
+    "bdd_strerror", "bdd_free",
+]
+
+
+class bdd_options(C.Structure):
+    _fields_ = [("omega", C.c_float), ("max_width", C.c_int), ("max_nodes", C.c_longlong),
+                ("max_device_bytes", C.c_longlong), ("host_only", C.c_int), ("device", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+class BDDError(RuntimeError):
+    def __init__(self, code: int, where: str, row: int = -1):
+        msg = f"{where}: {strerror(code)} (status {code})"
+        if row >= 0:
+            msg += f", row {row}"
+        super().__init__(msg)
+        self.code, self.row = code, row
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    P = C.POINTER
+    vp, i32, i64, f32, f64 = C.c_void_p, C.c_int, C.c_longlong, C.c_float, C.c_double
+    lib.bdd_default_options.argtypes = [P(bdd_options)]
+    lib.bdd_default_options.restype = None
+    lib.bdd_build.argtypes = [i32, i32, P(i64), P(i32), P(i32), P(i32), P(C.c_byte), P(f32),
+                              P(bdd_options), P(vp)]
+    lib.bdd_last_failed_row.argtypes = []
+    lib.bdd_iterate.argtypes = [vp, i32, P(f64), P(f32), P(f32), P(f32)]
+    lib.bdd_iterate_device.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    lib.bdd_iterate_profiled.argtypes = [vp, i32, P(f64)]
+    lib.bdd_set_costs.argtypes = [vp, P(f32)]
+    lib.bdd_sizes.argtypes = [vp, P(i64)]
+    lib.bdd_export_canonical.argtypes = [vp, P(i32), P(i32), P(i32), P(i64), P(i32), P(i32), P(i32)]
+    lib.bdd_get_state.argtypes = [vp, P(f32), P(f32)]
+    lib.bdd_set_state.argtypes = [vp, P(f32), P(f32)]
+    lib.bdd_strerror.argtypes = [i32]
+    lib.bdd_strerror.restype = C.c_char_p
+    lib.bdd_free.argtypes = [vp]
+    lib.bdd_free.restype = None
+    if path == LIB:
+        _lib = lib
+    return lib
+
+
+def _ptr(a, t):
+    return None if a is None else a.ctypes.data_as(C.POINTER(t))
+
+
+def strerror(code: int) -> str:
+    return load().bdd_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != BDD_OK:
+        raise BDDError(rc, where)
+
+
+def bdd_default_options() -> bdd_options:
+    opt = bdd_options()
+    load().bdd_default_options(C.byref(opt))
+    return opt
+
+
+def bdd_build(n, m, row_ptr, col, val, b, sense, c, opt: bdd_options | None = None) -> int:
+    """Returns the solver handle (an int); raises BDDError with the failing row on error."""
+    lib = load()
+    row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    val = np.ascontiguousarray(val, np.int32)
+    b = np.ascontiguousarray(b, np.int32)
+    sense = np.ascontiguousarray(sense, np.int8)
+    c = np.ascontiguousarray(c, np.float32)
+    h = C.c_void_p()
+    rc = lib.bdd_build(int(n), int(m), _ptr(row_ptr, C.c_longlong), _ptr(col, C.c_int),
+                       _ptr(val, C.c_int), _ptr(b, C.c_int), _ptr(sense, C.c_byte),
+                       _ptr(c, C.c_float), C.byref(opt) if opt is not None else None, C.byref(h))
+    if rc != BDD_OK:
+        raise BDDError(rc, "bdd_build", lib.bdd_last_failed_row())
+    return h.value
+
+
+def bdd_last_failed_row() -> int:
+    return load().bdd_last_failed_row()
+
+
+def bdd_sizes(h) -> np.ndarray:
+    out = np.zeros(BDD_SIZES_LEN, np.int64)
+    _check(load().bdd_sizes(h, _ptr(out, C.c_longlong)), "bdd_sizes")
+    return out
+
+
+def bdd_iterate(h, n_iter: int, lam: bool = False, mm: bool = False):
+    """Host form: returns (lower_bound, lambda or None, mm0 or None, mm1 or None)."""
+    s = bdd_sizes(h)
+    nnz = int(s[7])
+    lb = np.zeros(1, np.float64)
+    lam_a = np.zeros(max(nnz, 1), np.float32) if lam else None
+    m0 = np.zeros(max(nnz, 1), np.float32) if mm else None
+    m1 = np.zeros(max(nnz, 1), np.float32) if mm else None
+    _check(load().bdd_iterate(h, int(n_iter), _ptr(lb, C.c_double), _ptr(lam_a, C.c_float),
+                              _ptr(m0, C.c_float), _ptr(m1, C.c_float)), "bdd_iterate")
+    cut = (lambda a: None if a is None else a[:nnz])
+    return float(lb[0]), cut(lam_a), cut(m0), cut(m1)
+
+
+def bdd_iterate_device(h, n_iter: int, d_bound_trace=0, d_lambda=0, d_mm0=0, d_mm1=0, stream=0):
+    """Device form: pointer arguments are integers (e.g. tensor.data_ptr()), 0 for none."""
+    _check(load().bdd_iterate_device(h, int(n_iter), d_bound_trace or None, d_lambda or None,
+                                     d_mm0 or None, d_mm1 or None, stream or None),
+           "bdd_iterate_device")
+
+
+def bdd_iterate_profiled(h, n_iter: int) -> np.ndarray:
+    """Summed device milliseconds of [forward sweeps, reductions, backward sweeps, reductions
+    with bound] over n_iter iterations launched kernel by kernel."""
+    ms = np.zeros(4, np.float64)
+    _check(load().bdd_iterate_profiled(h, int(n_iter), _ptr(ms, C.c_double)), "bdd_iterate_profiled")
+    return ms
+
+
+def bdd_set_costs(h, c):
+    c = np.ascontiguousarray(c, np.float32)
+    _check(load().bdd_set_costs(h, _ptr(c, C.c_float)), "bdd_set_costs")
+
+
+def bdd_export_canonical(h) -> dict:
+    s = bdd_sizes(h)
+    nb, O, N = int(s[2]), int(s[3]), int(s[4])
+    out = dict(bdd_row=np.zeros(max(nb, 1), np.int32), bdd_depth=np.zeros(max(nb, 1), np.int32),
+               occ_var=np.zeros(max(O, 1), np.int32), occ_csr=np.zeros(max(O, 1), np.int64),
+               occ_width=np.zeros(max(O, 1), np.int32), lo=np.zeros(max(N, 1), np.int32),
+               hi=np.zeros(max(N, 1), np.int32))
+    _check(load().bdd_export_canonical(
+        h, _ptr(out["bdd_row"], C.c_int), _ptr(out["bdd_depth"], C.c_int),
+        _ptr(out["occ_var"], C.c_int), _ptr(out["occ_csr"], C.c_longlong),
+        _ptr(out["occ_width"], C.c_int), _ptr(out["lo"], C.c_int), _ptr(out["hi"], C.c_int)),
+        "bdd_export_canonical")
+    sizes = dict(bdd_row=nb, bdd_depth=nb, occ_var=O, occ_csr=O, occ_width=O, lo=N, hi=N)
+    return {k: v[: sizes[k]] for k, v in out.items()}
+
+
+def bdd_get_state(h):
+    s = bdd_sizes(h)
+    lam = np.zeros(max(int(s[7]), 1), np.float32)
+    P = np.zeros(max(int(s[0]), 1), np.float32)
+    _check(load().bdd_get_state(h, _ptr(lam, C.c_float), _ptr(P, C.c_float)), "bdd_get_state")
+    return lam[: int(s[7])], P[: int(s[0])]
+
+
+def bdd_set_state(h, lam, P=None):
+    lam = np.ascontiguousarray(lam, np.float32)
+    P = None if P is None else np.ascontiguousarray(P, np.float32)
+    _check(load().bdd_set_state(h, _ptr(lam, C.c_float), _ptr(P, C.c_float)), "bdd_set_state")
+
+
+def bdd_strerror(code: int) -> str:
+    return strerror(code)
+
+
+def bdd_free(h):
+    if h:
+        load().bdd_free(h)

@@ -1,0 +1,725 @@
+// C ABI of the library (include/bdd_dbca.h): solver object, device slabs, the captured
+// iteration loop, outputs and state access.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bdd_dbca.h"
+#include "internal.h"
+
+using namespace bdd;
+
+namespace {
+
+thread_local int g_failed_row = -1;
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+#define CK(x)                                   \
+  do {                                          \
+    if ((x) != cudaSuccess) {                   \
+      cudaGetLastError();                       \
+      return BDD_ECUDA;                         \
+    }                                           \
+  } while (0)
+
+#define RC(x)                                   \
+  do {                                          \
+    int rc_ = (x);                              \
+    if (rc_ != 0) return rc_;                   \
+  } while (0)
+
+constexpr int kGraphIters = 8;  // iterations per captured graph
+
+}  // namespace
+
+struct bdd_solver {
+  // sizes
+  int n = 0, m = 0;
+  long long nnz = 0, nb = 0, O = 0, N = 0;
+  int max_depth = 0, max_width = 0;
+  bool host_only = false;
+  HostBDDs host;                 // kept only for host_only solvers
+  bool host_layout = false;      // host_only == 2: the slab layout is kept in host memory
+  Layout layout;
+  // host metadata of the device layout
+  std::vector<int> bdd_perm;     // sorted position -> canonical BDD index
+  std::vector<int> canon_row;    // canonical BDD index -> row
+  std::vector<int> tile_occ0, tile_bdd0, tile_nbdd;
+  int class_tile_off[kWarpClasses + 2] = {0};
+  int n_warp_tiles = 0, n_block_tiles = 0, block_buf = 0;
+  std::vector<int> var_deg;
+  std::vector<float> c;
+  double empty_const = 0.0;
+  // device
+  int device = -1;
+  float omega = 0.5f;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  bool own_stream = false;
+  long long max_device_bytes = 0, device_bytes = 0;
+  std::vector<void *> allocs;
+  int *d_occ_node_off = nullptr, *d_occ_var = nullptr;
+  long long *d_occ_csr = nullptr;
+  int2 *d_lohi = nullptr;
+  float *d_fm = nullptr, *d_bm = nullptr, *d_lam = nullptr, *d_delta = nullptr;
+  float *d_share = nullptr, *d_P = nullptr, *d_c = nullptr;
+  int *d_bdd_depth = nullptr;
+  float *d_bdd_E = nullptr;
+  int *d_tile_occ0 = nullptr, *d_tile_bdd0 = nullptr, *d_tile_nbdd = nullptr;
+  int *d_var_ptr = nullptr, *d_var_occ = nullptr;
+  double *d_partial = nullptr, *d_trace = nullptr;
+  unsigned *d_ticket = nullptr;
+  int *d_iter = nullptr;
+  int trace_cap = 0;
+  float *d_out_lam = nullptr, *d_out_m0 = nullptr, *d_out_m1 = nullptr;
+  int grid_sweep = 0, n_warp_blocks = 0, grid_reduce = 1;
+  size_t smem = 0;
+  cudaGraphExec_t g_many = nullptr, g_one = nullptr;
+
+  ~bdd_solver() {
+    if (g_many) cudaGraphExecDestroy(g_many);
+    if (g_one) cudaGraphExecDestroy(g_one);
+    for (void *p : allocs) cudaFree(p);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+
+  template <class Tp>
+  int alloc(Tp **p, long long count) {
+    size_t bytes = (size_t)std::max<long long>(count, 1) * sizeof(Tp);
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (max_device_bytes > 0 && device_bytes + (long long)bytes > max_device_bytes) return BDD_ENOMEM;
+    void *q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return BDD_ENOMEM;
+    }
+    allocs.push_back(q);
+    device_bytes += (long long)bytes;
+    *p = (Tp *)q;
+    return BDD_OK;
+  }
+
+  SweepParams sweep_params(float *out_m0 = nullptr, float *out_m1 = nullptr) const {
+    SweepParams p;
+    p.occ_node_off = d_occ_node_off;
+    p.occ_var = d_occ_var;
+    p.occ_csr = d_occ_csr;
+    p.lohi = d_lohi;
+    p.fm = d_fm;
+    p.bm = d_bm;
+    p.lam = d_lam;
+    p.delta = d_delta;
+    p.share = d_share;
+    p.bdd_depth = d_bdd_depth;
+    p.bdd_E = d_bdd_E;
+    p.tile_occ0 = d_tile_occ0;
+    p.tile_bdd0 = d_tile_bdd0;
+    p.tile_nbdd = d_tile_nbdd;
+    p.out_m0 = out_m0;
+    p.out_m1 = out_m1;
+    for (int c = 0; c < kWarpClasses + 2; ++c) p.class_tile_off[c] = class_tile_off[c];
+    p.n_warp_blocks = n_warp_blocks;
+    p.block_buf = block_buf;
+    p.omega = omega;
+    return p;
+  }
+
+  ReduceParams reduce_params() const {
+    ReduceParams r;
+    r.var_ptr = d_var_ptr;
+    r.var_occ = d_var_occ;
+    r.delta = d_delta;
+    r.P = d_P;
+    r.share = d_share;
+    r.bdd_E = d_bdd_E;
+    r.partial = d_partial;
+    r.ticket = d_ticket;
+    r.iter_ctr = d_iter;
+    r.trace = d_trace;
+    r.trace_cap = trace_cap;
+    r.n = n;
+    r.nb = (int)nb;
+    r.empty_const = empty_const;
+    return r;
+  }
+
+  int sweep(bool fwd, int mode, cudaStream_t s, float *m0 = nullptr, float *m1 = nullptr) {
+    return sweep_launch(fwd, mode, sweep_params(m0, m1), grid_sweep, s) ? BDD_ECUDA : BDD_OK;
+  }
+
+  int reduce(bool recompute, bool bound, cudaStream_t s) {
+    return reduce_launch(recompute, bound, reduce_params(), grid_reduce, s) ? BDD_ECUDA : BDD_OK;
+  }
+
+  // one iteration: forward sweep, reduction, backward sweep, reduction + bound
+  int enqueue_iteration(cudaStream_t s) {
+    RC(sweep(true, kUpdate, s));
+    RC(reduce(true, false, s));
+    RC(sweep(false, kUpdate, s));
+    RC(reduce(true, true, s));
+    return BDD_OK;
+  }
+
+  int capture(int iters, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = BDD_OK;
+    for (int t = 0; t < iters && rc == BDD_OK; ++t) rc = enqueue_iteration(cap_stream);
+    cudaError_t e = cudaStreamEndCapture(cap_stream, &g);
+    if (rc != BDD_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return rc != BDD_OK ? rc : BDD_ECUDA;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return BDD_OK;
+  }
+
+  void drop_graphs() {
+    if (g_many) cudaGraphExecDestroy(g_many);
+    if (g_one) cudaGraphExecDestroy(g_one);
+    g_many = g_one = nullptr;
+  }
+
+  int ensure_trace(int need) {
+    if (need <= trace_cap) return BDD_OK;
+    int cap = std::max(need, std::max(1024, 2 * trace_cap));
+    double *t = nullptr;
+    RC(alloc(&t, cap));
+    d_trace = t;  // the previous buffer stays owned by `allocs` until the solver is freed
+    trace_cap = cap;
+    drop_graphs();  // graphs bake in the trace pointer
+    return BDD_OK;
+  }
+
+  int ensure_outputs() {
+    if (!d_out_lam) RC(alloc(&d_out_lam, nnz));
+    if (!d_out_m0) RC(alloc(&d_out_m0, nnz));
+    if (!d_out_m1) RC(alloc(&d_out_m1, nnz));
+    return BDD_OK;
+  }
+
+  // lambda^j_i = c_i/|J_i|, P = 0, then backward messages (and E^j) for that lambda
+  int restart(cudaStream_t s) {
+    if (O > 0 && init_lambda_launch(d_occ_var, d_var_ptr, d_c, d_lam, (int)O, s)) return BDD_ECUDA;
+    CK(cudaMemsetAsync(d_P, 0, sizeof(float) * std::max(n, 1), s));
+    CK(cudaMemsetAsync(d_share, 0, sizeof(float) * std::max(n, 1), s));
+    CK(cudaMemsetAsync(d_delta, 0, sizeof(float) * std::max<long long>(O, 1), s));
+    return sweep(false, kMessages, s);
+  }
+
+  // min-marginals and folded multipliers for the current state; leaves the state unchanged
+  int output_pass(cudaStream_t s, float *lam_out, float *m0, float *m1) {
+    const size_t bytes = sizeof(float) * (size_t)nnz;
+    if (lam_out) {
+      if (nnz) CK(cudaMemsetAsync(lam_out, 0, bytes, s));
+      if (O && scatter_lambda_launch(d_lam, d_share, d_occ_var, d_occ_csr, lam_out, (int)O, true, s))
+        return BDD_ECUDA;
+    }
+    if (m0 || m1) {
+      if (!m0 || !m1) RC(ensure_outputs());
+      float *o0 = m0 ? m0 : d_out_m0, *o1 = m1 ? m1 : d_out_m1;
+      if (nnz) {
+        CK(cudaMemsetAsync(o0, 0, bytes, s));
+        CK(cudaMemsetAsync(o1, 0, bytes, s));
+      }
+      RC(sweep(true, kFolded, s));
+      RC(sweep(false, kFolded, s, o0, o1));
+      RC(sweep(false, kMessages, s));  // backward messages of the unfolded multipliers again
+    }
+    return BDD_OK;
+  }
+};
+
+namespace {
+
+template <class Tp>
+int upload(bdd_solver *h, Tp **d, const std::vector<Tp> &v) {
+  RC(h->alloc(d, (long long)v.size()));
+  if (!v.empty()) CK(cudaMemcpy(*d, v.data(), v.size() * sizeof(Tp), cudaMemcpyHostToDevice));
+  return BDD_OK;
+}
+
+int setup_device(bdd_solver *h, const Layout &L, const float *c) {
+  h->bdd_perm = L.bdd_perm;
+  h->tile_occ0 = L.tile_occ0;
+  h->tile_bdd0 = L.tile_bdd0;
+  h->tile_nbdd = L.tile_nbdd;
+  for (int t = 0; t < kWarpClasses + 2; ++t) h->class_tile_off[t] = L.class_tile_off[t];
+  h->n_warp_tiles = L.n_warp_tiles;
+  h->n_block_tiles = L.n_block_tiles;
+  h->block_buf = ((L.max_block_width + 3) / 4) * 4;
+  h->n_warp_blocks = (L.n_warp_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  h->grid_sweep = h->n_warp_blocks + L.n_block_tiles;
+  const int range = std::max<long long>(h->n, h->nb) > 0 ? (int)std::max<long long>(h->n, h->nb) : 1;
+  h->grid_reduce = std::max(1, std::min((range + kReduceThreads - 1) / kReduceThreads, 152 * 8));
+  h->smem = (2 * kWarpsPerBlock + 2 * (size_t)h->block_buf) * sizeof(float);
+  if (h->smem > 48 * 1024 && sweep_set_smem(h->smem)) return BDD_ECUDA;
+
+  // device memory estimate against the cap, before allocating anything
+  const long long O = h->O, N = h->N, nb = h->nb, n = h->n;
+  const long long ntiles = (long long)L.tile_bdd0.size();
+  long long need = (O + 1) * 4 + O * 4 + O * 8 + N * 8 + 2 * N * 4 + 2 * O * 4 + 3 * (long long)n * 4 +
+                   nb * 8 + 3 * ntiles * 4 + (n + 1) * 4 + O * 4 + h->grid_reduce * 8 + 1024 * 8;
+  if (h->max_device_bytes > 0 && need > h->max_device_bytes) return BDD_ENOMEM;
+
+  RC(upload(h, &h->d_occ_node_off, L.occ_node_off));
+  RC(upload(h, &h->d_occ_var, L.occ_var));
+  RC(upload(h, &h->d_occ_csr, L.occ_csr));
+  {
+    int *tmp = nullptr;
+    RC(upload(h, &tmp, L.lohi));
+    h->d_lohi = reinterpret_cast<int2 *>(tmp);
+  }
+  RC(h->alloc(&h->d_fm, N));
+  RC(h->alloc(&h->d_bm, N));
+  RC(h->alloc(&h->d_lam, O));
+  RC(h->alloc(&h->d_delta, O));
+  RC(h->alloc(&h->d_share, n));
+  RC(h->alloc(&h->d_P, n));
+  RC(h->alloc(&h->d_c, n));
+  RC(upload(h, &h->d_bdd_depth, L.bdd_depth));
+  RC(h->alloc(&h->d_bdd_E, nb));
+  RC(upload(h, &h->d_tile_occ0, L.tile_occ0));
+  RC(upload(h, &h->d_tile_bdd0, L.tile_bdd0));
+  RC(upload(h, &h->d_tile_nbdd, L.tile_nbdd));
+  RC(upload(h, &h->d_var_ptr, L.var_ptr));
+  RC(upload(h, &h->d_var_occ, L.var_occ));
+  RC(h->alloc(&h->d_partial, h->grid_reduce));
+  RC(h->alloc(&h->d_ticket, 1));
+  RC(h->alloc(&h->d_iter, 1));
+  CK(cudaMemset(h->d_ticket, 0, sizeof(unsigned)));
+  CK(cudaMemset(h->d_iter, 0, sizeof(int)));
+  RC(h->ensure_trace(1024));
+  if (n) CK(cudaMemcpy(h->d_c, c, sizeof(float) * n, cudaMemcpyHostToDevice));
+  RC(h->restart(h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BDD_OK;
+}
+
+bool finite_costs(const float *c, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(c[i])) return false;
+  return true;
+}
+
+double empty_constant(const std::vector<int> &deg, const float *c, int n) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i)
+    if (deg[i] == 0 && c[i] < 0.f) s += (double)c[i];
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bdd_default_options(bdd_options *opt) {
+  if (!opt) return;
+  opt->omega = 0.5f;
+  opt->max_width = 1 << 20;
+  opt->max_nodes = 2147483647LL;
+  opt->max_device_bytes = 0;
+  opt->host_only = 0;
+  opt->device = -1;
+  opt->stream = nullptr;
+}
+
+int bdd_last_failed_row(void) { return g_failed_row; }
+
+int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int *val, const int *b,
+              const signed char *sense, const float *c, const bdd_options *opt_in, bdd_solver **out) {
+  g_failed_row = -1;
+  if (!out) return BDD_EINVAL;
+  *out = nullptr;
+  bdd_options opt;
+  bdd_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (n < 0 || m < 0 || (m > 0 && (!row_ptr || !b || !sense)) || (n > 0 && !c)) return BDD_EINVAL;
+  if (!(opt.omega > 0.f && opt.omega <= 1.f) || opt.max_width < 1 || opt.max_nodes < 1) return BDD_EINVAL;
+  if (m > 0 && row_ptr[0] != 0) return BDD_EINVAL;
+  for (int j = 0; j < m; ++j)
+    if (row_ptr[j + 1] < row_ptr[j]) {
+      g_failed_row = j;
+      return BDD_EINVAL;
+    }
+  const long long nnz = m ? row_ptr[m] : 0;
+  if (nnz > 0 && (!col || !val)) return BDD_EINVAL;
+  if (!finite_costs(c, n)) return BDD_EINVAL;
+
+  bdd_solver *h = new (std::nothrow) bdd_solver();
+  if (!h) return BDD_ENOMEM;
+  h->n = n;
+  h->m = m;
+  h->nnz = nnz;
+  h->omega = opt.omega;
+  if (opt.host_only < 0 || opt.host_only > 2) {
+    delete h;
+    return BDD_EINVAL;
+  }
+  h->host_only = opt.host_only != 0;
+  h->host_layout = opt.host_only == 2;
+  h->max_device_bytes = opt.max_device_bytes;
+  int failed = -1, rc;
+  try {
+    rc = compile_bdds(n, m, row_ptr, col, val, b, sense, opt.max_width, opt.max_nodes, &h->host, &failed);
+  } catch (const std::bad_alloc &) {
+    rc = BDD_ENOMEM;
+  }
+  if (rc != BDD_OK) {
+    g_failed_row = failed;
+    delete h;
+    return rc;
+  }
+  HostBDDs &H = h->host;
+  h->nb = H.nb();
+  h->O = H.O();
+  h->N = H.N();
+  h->max_depth = H.max_depth;
+  h->max_width = H.max_width;
+  h->canon_row = H.bdd_row;
+  h->var_deg.assign(n, 0);
+  for (int v : H.occ_var) h->var_deg[v]++;
+  h->c.assign(c, c + n);
+  h->empty_const = empty_constant(h->var_deg, c, n);
+  if (h->host_only && !h->host_layout) {
+    *out = h;
+    return BDD_OK;
+  }
+  Layout L;
+  try {
+    rc = build_layout(H, &L);
+  } catch (const std::bad_alloc &) {
+    rc = BDD_ENOMEM;
+  }
+  if (rc != BDD_OK) {
+    delete h;
+    return rc;
+  }
+  if (h->host_layout) {
+    h->bdd_perm = L.bdd_perm;
+    h->tile_occ0 = L.tile_occ0;
+    h->tile_bdd0 = L.tile_bdd0;
+    h->tile_nbdd = L.tile_nbdd;
+    for (int t = 0; t < kWarpClasses + 2; ++t) h->class_tile_off[t] = L.class_tile_off[t];
+    h->n_warp_tiles = L.n_warp_tiles;
+    h->n_block_tiles = L.n_block_tiles;
+    h->layout = std::move(L);
+    *out = h;
+    return BDD_OK;
+  }
+  H = HostBDDs();  // the device slabs are the only copy from here on
+  {
+    DeviceGuard dg(opt.device);
+    if (!dg.ok) {
+      delete h;
+      return BDD_ECUDA;
+    }
+    cudaGetDevice(&h->device);
+    if (opt.stream) {
+      h->stream = (cudaStream_t)opt.stream;
+    } else if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return BDD_ECUDA;
+    } else {
+      h->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return BDD_ECUDA;
+    }
+    rc = setup_device(h, L, c);
+  }
+  if (rc != BDD_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return BDD_OK;
+}
+
+int bdd_iterate_device(bdd_solver *h, int n_iter, double *d_bound_trace, float *d_lambda, float *d_mm0,
+                       float *d_mm1, void *stream) {
+  if (!h || n_iter < 0) return BDD_EINVAL;
+  if (h->host_only) return BDD_ESTATE;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return BDD_ECUDA;
+  cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+  RC(h->ensure_trace(n_iter + 1));
+  if (n_iter > 0) {
+    if (!h->g_one) RC(h->capture(1, &h->g_one));
+    if (!h->g_many && n_iter >= kGraphIters) RC(h->capture(kGraphIters, &h->g_many));
+  }
+  CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
+  int left = n_iter;
+  while (left >= kGraphIters) {
+    CK(cudaGraphLaunch(h->g_many, s));
+    left -= kGraphIters;
+  }
+  for (; left > 0; --left) CK(cudaGraphLaunch(h->g_one, s));
+  if (d_bound_trace && n_iter > 0)
+    CK(cudaMemcpyAsync(d_bound_trace, h->d_trace, sizeof(double) * n_iter, cudaMemcpyDeviceToDevice, s));
+  return h->output_pass(s, d_lambda, d_mm0, d_mm1);
+}
+
+int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms) {
+  if (!h || n_iter < 0 || !kernel_ms) return BDD_EINVAL;
+  if (h->host_only) return BDD_ESTATE;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return BDD_ECUDA;
+  cudaStream_t s = h->stream;
+  for (int t = 0; t < 4; ++t) kernel_ms[t] = 0.0;
+  RC(h->ensure_trace(n_iter + 1));
+  CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
+  const int kBatch = 256;  // iterations per batch of recorded events
+  std::vector<cudaEvent_t> ev(5 * kBatch, nullptr);
+  int rc = BDD_OK;
+  for (auto &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) rc = BDD_ECUDA;
+  for (int done = 0; done < n_iter && rc == BDD_OK;) {
+    const int cnt = std::min(kBatch, n_iter - done);
+    for (int t = 0; t < cnt && rc == BDD_OK; ++t) {
+      cudaEvent_t *e = &ev[5 * t];
+      if (cudaEventRecord(e[0], s) != cudaSuccess) rc = BDD_ECUDA;
+      if (rc == BDD_OK) rc = h->sweep(true, kUpdate, s);
+      if (rc == BDD_OK && cudaEventRecord(e[1], s) != cudaSuccess) rc = BDD_ECUDA;
+      if (rc == BDD_OK) rc = h->reduce(true, false, s);
+      if (rc == BDD_OK && cudaEventRecord(e[2], s) != cudaSuccess) rc = BDD_ECUDA;
+      if (rc == BDD_OK) rc = h->sweep(false, kUpdate, s);
+      if (rc == BDD_OK && cudaEventRecord(e[3], s) != cudaSuccess) rc = BDD_ECUDA;
+      if (rc == BDD_OK) rc = h->reduce(true, true, s);
+      if (rc == BDD_OK && cudaEventRecord(e[4], s) != cudaSuccess) rc = BDD_ECUDA;
+    }
+    if (rc == BDD_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = BDD_ECUDA;
+    for (int t = 0; t < cnt && rc == BDD_OK; ++t)
+      for (int k = 0; k < 4; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[5 * t + k], ev[5 * t + k + 1]) != cudaSuccess) rc = BDD_ECUDA;
+        kernel_ms[k] += ms;
+      }
+    done += cnt;
+  }
+  for (auto &e : ev)
+    if (e) cudaEventDestroy(e);
+  if (rc != BDD_OK) cudaGetLastError();
+  return rc;
+}
+
+int bdd_iterate(bdd_solver *h, int n_iter, double *lower_bound, float *lambda, float *mm0, float *mm1) {
+  if (!h || n_iter < 0) return BDD_EINVAL;
+  if (h->host_only) return BDD_ESTATE;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return BDD_ECUDA;
+  cudaStream_t s = h->stream;
+  if (lambda || mm0 || mm1) RC(h->ensure_outputs());
+  RC(bdd_iterate_device(h, n_iter, nullptr, lambda ? h->d_out_lam : nullptr, mm0 ? h->d_out_m0 : nullptr,
+                        mm1 ? h->d_out_m1 : nullptr, s));
+  if (lower_bound && n_iter == 0) {
+    CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
+    RC(h->reduce(false, true, s));
+  }
+  const size_t bytes = sizeof(float) * (size_t)h->nnz;
+  if (lambda && bytes) CK(cudaMemcpyAsync(lambda, h->d_out_lam, bytes, cudaMemcpyDeviceToHost, s));
+  if (mm0 && bytes) CK(cudaMemcpyAsync(mm0, h->d_out_m0, bytes, cudaMemcpyDeviceToHost, s));
+  if (mm1 && bytes) CK(cudaMemcpyAsync(mm1, h->d_out_m1, bytes, cudaMemcpyDeviceToHost, s));
+  if (lower_bound) {
+    const int last = n_iter > 0 ? n_iter - 1 : 0;
+    CK(cudaMemcpyAsync(lower_bound, h->d_trace + last, sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return BDD_OK;
+}
+
+int bdd_set_costs(bdd_solver *h, const float *c) {
+  if (!h || (h->n > 0 && !c)) return BDD_EINVAL;
+  if (!finite_costs(c, h->n)) return BDD_EINVAL;
+  h->c.assign(c, c + h->n);
+  h->empty_const = empty_constant(h->var_deg, c, h->n);
+  if (h->host_only) return BDD_OK;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return BDD_ECUDA;
+  if (h->n) CK(cudaMemcpyAsync(h->d_c, c, sizeof(float) * h->n, cudaMemcpyHostToDevice, h->stream));
+  h->drop_graphs();  // the bound constant is baked into the captured reductions
+  RC(h->restart(h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BDD_OK;
+}
+
+int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]) {
+  if (!h || !out) return BDD_EINVAL;
+  out[0] = h->n;
+  out[1] = h->m;
+  out[2] = h->nb;
+  out[3] = h->O;
+  out[4] = h->N;
+  out[5] = h->max_depth;
+  out[6] = h->max_width;
+  out[7] = h->nnz;
+  out[8] = h->device_bytes;
+  out[9] = h->n_warp_tiles;
+  out[10] = h->n_block_tiles;
+  out[11] = h->host_only ? 0 : 4;
+  return BDD_OK;
+}
+
+int bdd_export_canonical(const bdd_solver *h, int *bdd_row, int *bdd_depth, int *occ_var, long long *occ_csr,
+                         int *occ_width, int *lo, int *hi) {
+  if (!h || !bdd_row || !bdd_depth || !occ_var || !occ_csr || !occ_width || !lo || !hi) return BDD_EINVAL;
+  if (h->host_only && !h->host_layout) {
+    const HostBDDs &H = h->host;
+    std::copy(H.bdd_row.begin(), H.bdd_row.end(), bdd_row);
+    std::copy(H.bdd_depth.begin(), H.bdd_depth.end(), bdd_depth);
+    std::copy(H.occ_var.begin(), H.occ_var.end(), occ_var);
+    std::copy(H.occ_csr.begin(), H.occ_csr.end(), occ_csr);
+    std::copy(H.occ_width.begin(), H.occ_width.end(), occ_width);
+    std::copy(H.lo.begin(), H.lo.end(), lo);
+    std::copy(H.hi.begin(), H.hi.end(), hi);
+    return BDD_OK;
+  }
+  // read the slabs back (from the device, or the host copy of the layout) and undo the tiles
+  const long long O = h->O, N = h->N, nb = h->nb;
+  std::vector<int> off(O + 1), var(O), depth(nb), lohi(2 * N);
+  std::vector<long long> csr(O);
+  if (h->host_layout) {
+    const Layout &L = h->layout;
+    off = L.occ_node_off;
+    var = L.occ_var;
+    csr = L.occ_csr;
+    depth = L.bdd_depth;
+    lohi = L.lohi;
+  } else {
+    DeviceGuard dg(h->device);
+    if (!dg.ok) return BDD_ECUDA;
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(off.data(), h->d_occ_node_off, sizeof(int) * (O + 1), cudaMemcpyDeviceToHost));
+    if (O) {
+      CK(cudaMemcpy(var.data(), h->d_occ_var, sizeof(int) * O, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(csr.data(), h->d_occ_csr, sizeof(long long) * O, cudaMemcpyDeviceToHost));
+    }
+    if (nb) CK(cudaMemcpy(depth.data(), h->d_bdd_depth, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+    if (N) CK(cudaMemcpy(lohi.data(), h->d_lohi, sizeof(int) * 2 * N, cudaMemcpyDeviceToHost));
+  }
+  // device occurrence of (sorted BDD s, layer l), by the tile rule the kernels use
+  std::vector<std::vector<int>> occ_of(nb);
+  for (size_t t = 0; t < h->tile_bdd0.size(); ++t) {
+    int o = h->tile_occ0[t];
+    const int b0 = h->tile_bdd0[t], nt = h->tile_nbdd[t];
+    for (int q = 0; q < nt; ++q) occ_of[b0 + q].assign(depth[b0 + q], -1);
+    for (int l = 0; l < depth[b0]; ++l)
+      for (int q = 0; q < nt && depth[b0 + q] > l; ++q) occ_of[b0 + q][l] = o++;
+  }
+  std::vector<int> sorted_of_canon(nb);
+  for (long long s = 0; s < nb; ++s) sorted_of_canon[h->bdd_perm[s]] = (int)s;
+  long long co = 0, cn = 0;
+  for (long long cb = 0; cb < nb; ++cb) {
+    const int s = sorted_of_canon[cb];
+    bdd_row[cb] = h->canon_row[cb];
+    bdd_depth[cb] = depth[s];
+    for (int l = 0; l < depth[s]; ++l, ++co) {
+      const int o = occ_of[s][l];
+      if (o < 0 || o >= O) return BDD_EDEVICE;
+      const int w = off[o + 1] - off[o];
+      occ_var[co] = var[o];
+      occ_csr[co] = csr[o];
+      occ_width[co] = w;
+      const int next0 = l + 1 < depth[s] ? off[occ_of[s][l + 1]] : 0;
+      for (int q = 0; q < w; ++q, ++cn) {
+        if (cn >= N) return BDD_EDEVICE;
+        const int g0 = lohi[2 * (off[o] + q)], g1 = lohi[2 * (off[o] + q) + 1];
+        lo[cn] = g0 >= 0 ? g0 - next0 : g0;
+        hi[cn] = g1 >= 0 ? g1 - next0 : g1;
+      }
+    }
+  }
+  return BDD_OK;
+}
+
+int bdd_get_state(const bdd_solver *h_in, float *lambda, float *pending) {
+  bdd_solver *h = const_cast<bdd_solver *>(h_in);
+  if (!h) return BDD_EINVAL;
+  if (h->host_only) return BDD_ESTATE;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return BDD_ECUDA;
+  cudaStream_t s = h->stream;
+  if (lambda) {
+    RC(h->ensure_outputs());
+    if (h->nnz) CK(cudaMemsetAsync(h->d_out_lam, 0, sizeof(float) * h->nnz, s));
+    if (h->O && scatter_lambda_launch(h->d_lam, h->d_share, h->d_occ_var, h->d_occ_csr, h->d_out_lam,
+                                      (int)h->O, false, s))
+      return BDD_ECUDA;
+    if (h->nnz) CK(cudaMemcpyAsync(lambda, h->d_out_lam, sizeof(float) * h->nnz, cudaMemcpyDeviceToHost, s));
+  }
+  if (pending && h->n) CK(cudaMemcpyAsync(pending, h->d_P, sizeof(float) * h->n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return BDD_OK;
+}
+
+int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending) {
+  if (!h || !lambda) return BDD_EINVAL;
+  if (h->host_only) return BDD_ESTATE;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return BDD_ECUDA;
+  cudaStream_t s = h->stream;
+  RC(h->ensure_outputs());
+  if (h->nnz) CK(cudaMemcpyAsync(h->d_out_lam, lambda, sizeof(float) * h->nnz, cudaMemcpyHostToDevice, s));
+  if (h->O && gather_lambda_launch(h->d_out_lam, h->d_occ_csr, h->d_lam, (int)h->O, s)) return BDD_ECUDA;
+  if (h->n) {
+    if (pending)
+      CK(cudaMemcpyAsync(h->d_P, pending, sizeof(float) * h->n, cudaMemcpyHostToDevice, s));
+    else
+      CK(cudaMemsetAsync(h->d_P, 0, sizeof(float) * h->n, s));
+    if (share_from_pending_launch(h->d_var_ptr, h->d_P, h->d_share, h->n, s)) return BDD_ECUDA;
+  }
+  RC(h->sweep(false, kMessages, s));
+  CK(cudaStreamSynchronize(s));
+  return BDD_OK;
+}
+
+const char *bdd_strerror(int code) {
+  switch (code) {
+    case BDD_OK: return "ok";
+    case BDD_EINVAL: return "invalid argument or malformed instance";
+    case BDD_EINFEASIBLE: return "a constraint row has no 0-1 solution";
+    case BDD_ETOOBIG: return "a BDD or the instance exceeds the size limits";
+    case BDD_ENOMEM: return "out of host or device memory (or over max_device_bytes)";
+    case BDD_ECUDA: return "CUDA runtime error";
+    case BDD_ETIMEOUT: return "device-side wait gave up";
+    case BDD_EDEVICE: return "device-side check failed";
+    case BDD_ESTATE: return "solver was built host-only";
+    default: return "unknown status";
+  }
+}
+
+void bdd_free(bdd_solver *h) {
+  if (!h) return;
+  if (h->host_only) {
+    delete h;
+    return;
+  }
+  DeviceGuard dg(h->device);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,340 @@
+// Host BDD compiler and device slab layout.
+//
+// compile_bdds: one reduced, ordered, non-skipping BDD per constraint row (Sec. 5.1, Def. 4;
+// the paper builds them with the threshold method it cites, in O(N log W), Sec. 5.2).  This
+// compiler is threshold-based: with the suffix-sum set T_l = { a_l y_l + ... + a_{k-1} y_{k-1} }
+// of the variables still to come, two partial sums s, s' at layer l have the same feasible
+// completions iff they select the same part of T_l:
+//   a.x <= b : the number of t in T_l with t <= b - s,
+//   a.x >= b : the number of t in T_l with t >= b - s,
+//   a.x == b : the position of b - s in T_l (if present),
+// and 0 means "no completion" (the false terminal).  Nodes of layer l are the distinct nonzero
+// keys among the reachable partial sums, numbered in ascending order of their smallest
+// reachable partial sum (the canonical order of the library's exports).  Each node keeps one
+// representative sum; its 0-/1-successors are the keys of s and s + a_l at layer l+1.
+//
+// build_layout: turns the canonical BDDs into the tile-grouped, layer-major slabs the sweep
+// kernels read.
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cstring>
+#include <thread>
+
+#include "bdd_dbca.h"
+#include "internal.h"
+
+namespace bdd {
+namespace {
+
+constexpr long long kSumCap = 1LL << 22;  // largest suffix / prefix sum set per layer
+
+struct Scratch {
+  std::vector<int> order;
+  std::vector<long long> a, pos;
+  std::vector<int> cols;
+  std::vector<std::vector<long long>> T, S, rep;
+  std::vector<std::vector<int>> id_of_key;
+};
+
+struct Chunk {
+  std::vector<int> bdd_row, bdd_depth, occ_var, occ_width, lo, hi;
+  std::vector<long long> occ_csr;
+  int status = BDD_OK;
+  int failed_row = -1;
+};
+
+inline bool sat(long long s, int sense, long long b) {
+  return sense < 0 ? s <= b : (sense > 0 ? s >= b : s == b);
+}
+
+// out = sorted distinct union of A and A + a
+void merge_shift(const std::vector<long long> &A, long long a, std::vector<long long> &out) {
+  out.clear();
+  out.reserve(2 * A.size());
+  size_t i = 0, j = 0, n = A.size();
+  while (i < n || j < n) {
+    long long x = i < n ? A[i] : LLONG_MAX;
+    long long y = j < n ? A[j] + a : LLONG_MAX;
+    long long v;
+    if (x < y) {
+      v = x; ++i;
+    } else if (y < x) {
+      v = y; ++j;
+    } else {
+      v = x; ++i; ++j;
+    }
+    if (out.empty() || out.back() != v) out.push_back(v);
+  }
+}
+
+inline int key_of(const std::vector<long long> &T, long long s, long long b, int sense) {
+  long long r = b - s;
+  if (sense < 0) return (int)(std::upper_bound(T.begin(), T.end(), r) - T.begin());
+  if (sense > 0) return (int)(T.end() - std::lower_bound(T.begin(), T.end(), r));
+  auto it = std::lower_bound(T.begin(), T.end(), r);
+  return (it != T.end() && *it == r) ? (int)(it - T.begin()) + 1 : 0;
+}
+
+int compile_row(int j, const long long *row_ptr, const int *col, const int *val, int n,
+                long long b, int sense, int max_width, Scratch &sc, Chunk &out) {
+  long long s0 = row_ptr[j], e0 = row_ptr[j + 1];
+  if (e0 < s0 || sense < -1 || sense > 1) return BDD_EINVAL;
+  sc.order.clear();
+  for (long long t = s0; t < e0; ++t) {
+    if (col[t] < 0 || col[t] >= n) return BDD_EINVAL;
+    if (val[t] != 0) sc.order.push_back((int)(t - s0));
+  }
+  std::sort(sc.order.begin(), sc.order.end(),
+            [&](int x, int y) { return col[s0 + x] < col[s0 + y]; });
+  const int k = (int)sc.order.size();
+  sc.a.resize(k);
+  sc.pos.resize(k);
+  sc.cols.resize(k);
+  for (int l = 0; l < k; ++l) {
+    long long t = s0 + sc.order[l];
+    sc.a[l] = val[t];
+    sc.pos[l] = t;
+    sc.cols[l] = col[t];
+    if (l > 0 && sc.cols[l] == sc.cols[l - 1]) return BDD_EINVAL;  // duplicate (j, i)
+  }
+  if (k == 0) return sat(0, sense, b) ? BDD_OK : BDD_EINFEASIBLE;
+  if ((int)sc.T.size() < k + 1) {
+    sc.T.resize(k + 1);
+    sc.S.resize(k + 1);
+    sc.rep.resize(k + 1);
+    sc.id_of_key.resize(k + 1);
+  }
+  // suffix sums T_l (l = k .. 0)
+  sc.T[k].assign(1, 0);
+  for (int l = k - 1; l >= 0; --l) {
+    merge_shift(sc.T[l + 1], sc.a[l], sc.T[l]);
+    if ((long long)sc.T[l].size() > kSumCap) return BDD_ETOOBIG;
+  }
+  // reachable prefix sums S_l (l = 0 .. k-1)
+  sc.S[0].assign(1, 0);
+  for (int l = 0; l + 1 < k; ++l) {
+    merge_shift(sc.S[l], sc.a[l], sc.S[l + 1]);
+    if ((long long)sc.S[l + 1].size() > kSumCap) return BDD_ETOOBIG;
+  }
+  // nodes: distinct nonzero keys, numbered in ascending order of their smallest sum
+  for (int l = 0; l < k; ++l) {
+    std::vector<int> &ids = sc.id_of_key[l];
+    ids.assign(sc.T[l].size() + 1, -1);
+    sc.rep[l].clear();
+    for (long long s : sc.S[l]) {
+      int key = key_of(sc.T[l], s, b, sense);
+      if (key == 0 || ids[key] >= 0) continue;
+      ids[key] = (int)sc.rep[l].size();
+      sc.rep[l].push_back(s);
+    }
+    if (sc.rep[l].empty()) return BDD_EINFEASIBLE;  // no feasible completion of the root
+    if ((long long)sc.rep[l].size() > max_width) return BDD_ETOOBIG;
+  }
+  // emit arcs
+  out.bdd_row.push_back(j);
+  out.bdd_depth.push_back(k);
+  for (int l = 0; l < k; ++l) {
+    out.occ_var.push_back(sc.cols[l]);
+    out.occ_csr.push_back(sc.pos[l]);
+    out.occ_width.push_back((int)sc.rep[l].size());
+    for (long long s : sc.rep[l]) {
+      int lo, hi;
+      if (l == k - 1) {
+        lo = sat(s, sense, b) ? kTop : kBot;
+        hi = sat(s + sc.a[l], sense, b) ? kTop : kBot;
+      } else {
+        int k0 = key_of(sc.T[l + 1], s, b, sense);
+        int k1 = key_of(sc.T[l + 1], s + sc.a[l], b, sense);
+        lo = k0 ? sc.id_of_key[l + 1][k0] : kBot;
+        hi = k1 ? sc.id_of_key[l + 1][k1] : kBot;
+      }
+      out.lo.push_back(lo);
+      out.hi.push_back(hi);
+    }
+  }
+  return BDD_OK;
+}
+
+}  // namespace
+
+int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const int *val,
+                 const int *b, const signed char *sense, int max_width, long long max_nodes,
+                 HostBDDs *H, int *failed_row) {
+  *failed_row = -1;
+  const int rows_per_chunk = 2048;
+  const int nchunks = (m + rows_per_chunk - 1) / rows_per_chunk;
+  std::vector<Chunk> chunks(nchunks);
+  std::atomic<int> next(0);
+  unsigned hw = std::thread::hardware_concurrency();
+  int nthreads = (int)std::max(1u, std::min(hw ? hw : 1u, 64u));
+  nthreads = std::min(nthreads, std::max(1, nchunks));
+  auto worker = [&]() {
+    Scratch sc;
+    for (;;) {
+      int cidx = next.fetch_add(1);
+      if (cidx >= nchunks) break;
+      Chunk &ch = chunks[cidx];
+      int r0 = cidx * rows_per_chunk, r1 = std::min(m, r0 + rows_per_chunk);
+      for (int j = r0; j < r1; ++j) {
+        int rc = compile_row(j, row_ptr, col, val, n, b[j], sense[j], max_width, sc, ch);
+        if (rc != BDD_OK) {
+          ch.status = rc;
+          ch.failed_row = j;
+          break;
+        }
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto &th : pool) th.join();
+  for (auto &ch : chunks)
+    if (ch.status != BDD_OK) {
+      *failed_row = ch.failed_row;
+      return ch.status;
+    }
+  // concatenate in row order
+  size_t nb = 0, O = 0, N = 0;
+  for (auto &ch : chunks) {
+    nb += ch.bdd_row.size();
+    O += ch.occ_var.size();
+    N += ch.lo.size();
+  }
+  if ((long long)N > max_nodes || N >= (size_t)INT_MAX || O >= (size_t)INT_MAX) return BDD_ETOOBIG;
+  H->n = n;
+  H->m = m;
+  H->nnz = m ? row_ptr[m] : 0;
+  H->bdd_row.reserve(nb);
+  H->bdd_depth.reserve(nb);
+  H->occ_var.reserve(O);
+  H->occ_csr.reserve(O);
+  H->occ_width.reserve(O);
+  H->lo.reserve(N);
+  H->hi.reserve(N);
+  for (auto &ch : chunks) {
+    H->bdd_row.insert(H->bdd_row.end(), ch.bdd_row.begin(), ch.bdd_row.end());
+    H->bdd_depth.insert(H->bdd_depth.end(), ch.bdd_depth.begin(), ch.bdd_depth.end());
+    H->occ_var.insert(H->occ_var.end(), ch.occ_var.begin(), ch.occ_var.end());
+    H->occ_csr.insert(H->occ_csr.end(), ch.occ_csr.begin(), ch.occ_csr.end());
+    H->occ_width.insert(H->occ_width.end(), ch.occ_width.begin(), ch.occ_width.end());
+    H->lo.insert(H->lo.end(), ch.lo.begin(), ch.lo.end());
+    H->hi.insert(H->hi.end(), ch.hi.begin(), ch.hi.end());
+    ch = Chunk();  // release the chunk's memory as soon as it is copied
+  }
+  H->bdd_occ0.assign(nb + 1, 0);
+  for (size_t t = 0; t < nb; ++t) {
+    H->bdd_occ0[t + 1] = H->bdd_occ0[t] + H->bdd_depth[t];
+    H->max_depth = std::max(H->max_depth, H->bdd_depth[t]);
+  }
+  H->occ_node0.assign(O + 1, 0);
+  for (size_t o = 0; o < O; ++o) {
+    H->occ_node0[o + 1] = H->occ_node0[o] + H->occ_width[o];
+    H->max_width = std::max(H->max_width, H->occ_width[o]);
+  }
+  return BDD_OK;
+}
+
+int build_layout(const HostBDDs &H, Layout *L) {
+  const long long nb = H.nb(), O = H.O(), N = H.N();
+  // class of each BDD from its widest layer
+  std::vector<int> cls(nb);
+  for (long long b = 0; b < nb; ++b) {
+    int w = 0;
+    for (long long o = H.bdd_occ0[b]; o < H.bdd_occ0[b + 1]; ++o) w = std::max(w, H.occ_width[o]);
+    int c = 0;
+    while ((1 << c) < w && c < kWarpClasses) ++c;
+    if (w > 32) c = kWarpClasses;
+    if (c == kWarpClasses && w > kMaxBlockTileWidth) return BDD_ETOOBIG;
+    cls[b] = c;
+  }
+  // stable counting sort by (class, depth descending); ties keep ascending row order
+  const int D = H.max_depth;
+  const int nkeys = (kWarpClasses + 1) * (D + 1);
+  std::vector<long long> cnt(nkeys + 1, 0);
+  auto key = [&](long long b) { return cls[b] * (D + 1) + (D - H.bdd_depth[b]); };
+  for (long long b = 0; b < nb; ++b) cnt[key(b) + 1]++;
+  for (int t = 0; t < nkeys; ++t) cnt[t + 1] += cnt[t];
+  L->bdd_perm.assign(nb, 0);
+  for (long long b = 0; b < nb; ++b) L->bdd_perm[cnt[key(b)]++] = (int)b;
+  L->n_sorted = (int)nb;
+  L->bdd_depth.resize(nb);
+  for (long long s = 0; s < nb; ++s) L->bdd_depth[s] = H.bdd_depth[L->bdd_perm[s]];
+  // tiles
+  L->tile_occ0.clear();
+  L->tile_bdd0.clear();
+  L->tile_nbdd.clear();
+  long long s = 0;
+  for (int c = 0; c <= kWarpClasses; ++c) {
+    L->class_tile_off[c] = (int)L->tile_bdd0.size();
+    const int G = c < kWarpClasses ? (32 >> c) : 1;
+    while (s < nb && cls[L->bdd_perm[s]] == c) {
+      long long e = s;
+      while (e < nb && e - s < G && cls[L->bdd_perm[e]] == c) ++e;
+      L->tile_bdd0.push_back((int)s);
+      L->tile_nbdd.push_back((int)(e - s));
+      s = e;
+    }
+  }
+  L->class_tile_off[kWarpClasses + 1] = (int)L->tile_bdd0.size();
+  L->n_warp_tiles = L->class_tile_off[kWarpClasses];
+  L->n_block_tiles = L->class_tile_off[kWarpClasses + 1] - L->class_tile_off[kWarpClasses];
+  // occurrences and nodes in tile order
+  const long long ntiles = (long long)L->tile_bdd0.size();
+  L->tile_occ0.resize(ntiles);
+  L->occ_of_canon.assign(O, -1);
+  L->occ_node_off.assign(O + 1, 0);
+  L->occ_var.assign(O, 0);
+  L->occ_csr.assign(O, 0);
+  std::vector<long long> node_of_canon_occ(O, 0);  // device first node of each canonical occurrence
+  long long dev_o = 0, dev_node = 0;
+  L->max_block_width = 0;
+  for (long long t = 0; t < ntiles; ++t) {
+    L->tile_occ0[t] = (int)dev_o;
+    const int b0 = L->tile_bdd0[t], nt = L->tile_nbdd[t];
+    const int dmax = L->bdd_depth[b0];  // first BDD of a tile is the deepest
+    for (int l = 0; l < dmax; ++l) {
+      for (int q = 0; q < nt; ++q) {
+        const int cb = L->bdd_perm[b0 + q];
+        if (H.bdd_depth[cb] <= l) break;  // depths are non-increasing inside the tile
+        const long long co = H.bdd_occ0[cb] + l;
+        L->occ_of_canon[co] = (int)dev_o;
+        L->occ_node_off[dev_o] = (int)dev_node;
+        L->occ_var[dev_o] = H.occ_var[co];
+        L->occ_csr[dev_o] = H.occ_csr[co];
+        node_of_canon_occ[co] = dev_node;
+        dev_node += H.occ_width[co];
+        if (cls[cb] == kWarpClasses) L->max_block_width = std::max(L->max_block_width, H.occ_width[co]);
+        ++dev_o;
+      }
+    }
+  }
+  L->occ_node_off[O] = (int)dev_node;
+  if (dev_o != O || dev_node != N) return BDD_EINVAL;
+  // successors as global device node ids
+  L->lohi.assign(2 * N, 0);
+  for (long long b = 0; b < nb; ++b) {
+    for (long long co = H.bdd_occ0[b]; co < H.bdd_occ0[b + 1]; ++co) {
+      const bool last = co + 1 == H.bdd_occ0[b + 1];
+      const long long next0 = last ? 0 : node_of_canon_occ[co + 1];
+      const long long d0 = node_of_canon_occ[co];
+      for (int q = 0; q < H.occ_width[co]; ++q) {
+        const long long cn = H.occ_node0[co] + q;
+        const int lo = H.lo[cn], hi = H.hi[cn];
+        L->lohi[2 * (d0 + q)] = lo >= 0 ? (int)(next0 + lo) : lo;
+        L->lohi[2 * (d0 + q) + 1] = hi >= 0 ? (int)(next0 + hi) : hi;
+      }
+    }
+  }
+  // variable -> occurrences (ascending row, i.e. canonical occurrence order)
+  L->var_ptr.assign(H.n + 1, 0);
+  for (long long co = 0; co < O; ++co) L->var_ptr[H.occ_var[co] + 1]++;
+  for (int i = 0; i < H.n; ++i) L->var_ptr[i + 1] += L->var_ptr[i];
+  L->var_occ.assign(O, 0);
+  std::vector<int> fill(L->var_ptr.begin(), L->var_ptr.end() - 1);
+  for (long long co = 0; co < O; ++co) L->var_occ[fill[H.occ_var[co]]++] = L->occ_of_canon[co];
+  return BDD_OK;
+}
+
+}  // namespace bdd

@@ -1,0 +1,135 @@
+// Internal declarations shared by the host compiler, the layout builder, the kernels and the
+// C ABI.  Not installed; the public interface is include/bdd_dbca.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+namespace bdd {
+
+constexpr int kTop = -1;   // arc into the true terminal
+constexpr int kBot = -2;   // arc into the false terminal
+constexpr int kNone = -3;  // no arc (lane without a node)
+
+// Canonical host form of all BDDs (Sec. 5.1, Def. 4): BDDs in ascending row order;
+// occurrences (row j, variable i) BDD-major, layer-minor; nodes BDD-major, layer-major,
+// ascending smallest partial sum inside a layer; lo/hi are ids inside the next layer.
+struct HostBDDs {
+  int n = 0, m = 0;
+  long long nnz = 0;
+  std::vector<int> bdd_row, bdd_depth;
+  std::vector<long long> bdd_occ0;   // [nb+1]
+  std::vector<int> occ_var;          // [O]
+  std::vector<long long> occ_csr;    // [O]
+  std::vector<int> occ_width;        // [O]
+  std::vector<long long> occ_node0;  // [O+1]
+  std::vector<int> lo, hi;           // [N]
+  int max_depth = 0, max_width = 0;
+  long long nb() const { return (long long)bdd_row.size(); }
+  long long O() const { return (long long)occ_var.size(); }
+  long long N() const { return (long long)lo.size(); }
+};
+
+// Compiles every row (threshold counting over suffix-sum sets; see compile.cpp).
+// Returns a BDD_* status; *failed_row is the row that failed, or -1.
+int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const int *val,
+                 const int *b, const signed char *sense, int max_width, long long max_nodes,
+                 HostBDDs *out, int *failed_row);
+
+// Team classes of the sweep kernels.  Class c < kWarpClasses: a team of T = 1 << c lanes per
+// BDD (lane t holds node t of the current layer), 32 / T BDDs per warp ("warp tile").
+// Class kWarpClasses: one thread block per BDD ("block tile").
+constexpr int kWarpClasses = 6;
+constexpr int kBlockThreads = 128;
+constexpr int kWarpsPerBlock = kBlockThreads / 32;
+constexpr int kMaxBlockTileWidth = 12288;  // two float layer buffers in shared memory
+
+// Device slab layout (host staging copy).  Occurrences are grouped by tile; inside a warp
+// tile they are layer-major (layer l of every tile BDD still alive at l, in tile order; the
+// tile's BDDs are sorted by depth, longest first, so the BDDs alive at l are a prefix).  Nodes
+// follow their occurrence.  Successors are global node indices or kTop / kBot.
+struct Layout {
+  int n_sorted = 0;                    // BDDs in sorted (device) order
+  std::vector<int> bdd_perm;           // sorted position -> canonical BDD index
+  std::vector<int> bdd_depth;          // [nb] sorted order
+  std::vector<int> occ_node_off;       // [O+1]
+  std::vector<int> occ_var;            // [O]
+  std::vector<long long> occ_csr;      // [O]
+  std::vector<int> lohi;               // [2N] interleaved lo, hi
+  std::vector<int> tile_occ0, tile_bdd0, tile_nbdd;  // per tile
+  int class_tile_off[kWarpClasses + 2] = {0};        // tiles of class c: [off[c], off[c+1])
+  int n_warp_tiles = 0, n_block_tiles = 0;
+  int max_block_width = 0;
+  std::vector<int> var_ptr;            // [n+1]
+  std::vector<int> var_occ;            // [O] device occurrence ids, ascending row per variable
+  std::vector<int> occ_of_canon;       // canonical occurrence -> device occurrence
+};
+
+int build_layout(const HostBDDs &H, Layout *L);
+
+// Kernel parameter blocks (passed by value).
+struct SweepParams {
+  const int *occ_node_off;
+  const int *occ_var;
+  const long long *occ_csr;
+  const int2 *lohi;
+  float *fm;
+  float *bm;
+  float *lam;
+  float *delta;
+  const float *share;
+  const int *bdd_depth;
+  float *bdd_E;
+  const int *tile_occ0;
+  const int *tile_bdd0;
+  const int *tile_nbdd;
+  float *out_m0;
+  float *out_m1;
+  int class_tile_off[kWarpClasses + 2];
+  int n_warp_blocks;
+  int block_buf;  // floats per shared-memory layer buffer of a block tile
+  float omega;
+};
+
+struct ReduceParams {
+  const int *var_ptr;
+  const int *var_occ;
+  const float *delta;
+  float *P;
+  float *share;
+  const float *bdd_E;
+  double *partial;
+  unsigned int *ticket;
+  int *iter_ctr;
+  double *trace;
+  int trace_cap;
+  int n;
+  int nb;
+  double empty_const;
+};
+
+// Sweep modes.
+enum SweepMode : int {
+  kUpdate = 0,   // add the pending share, take min-marginals, move lambda, record delta
+  kMessages = 1, // messages only (no share, no update); backward form also records E^j
+  kFolded = 2,   // messages and min-marginals at lambda + share, nothing stored but messages
+};
+
+// Launch wrappers (kernels.cu).  All enqueue on `stream` and return the launch status.
+int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStream_t stream);
+int reduce_launch(bool recompute, bool bound, const ReduceParams &p, int grid, cudaStream_t stream);
+int init_lambda_launch(const int *occ_var, const int *var_ptr, const float *c, float *lam, int O,
+                       cudaStream_t stream);
+int share_from_pending_launch(const int *var_ptr, const float *P, float *share, int n,
+                              cudaStream_t stream);
+int scatter_lambda_launch(const float *lam, const float *share, const int *occ_var,
+                          const long long *occ_csr, float *out, int O, bool fold,
+                          cudaStream_t stream);
+int sweep_set_smem(size_t bytes);
+int gather_lambda_launch(const float *in, const long long *occ_csr, float *lam, int O,
+                         cudaStream_t stream);
+constexpr int kReduceThreads = 256;
+
+}  // namespace bdd

@@ -1,0 +1,73 @@
+"""Convenience wrapper of one solver handle.  Marshalling only; PyTorch (optional) supplies
+device buffers and streams for :meth:`Solver.iterate_device`."""
+from __future__ import annotations
+
+from . import binding as B
+
+# cudaStreamLegacy: the handle of the legacy default stream that PyTorch's default stream
+# reports as 0 (0 itself means "the solver's own stream" in the C ABI)
+LEGACY_DEFAULT_STREAM = 1
+
+
+class Solver:
+    """BDDs of a 0-1 ILP on the GPU.
+
+    ``inst`` needs attributes n, m, row_ptr, col, val, b, sense, c (CSR form; see
+    ``include/bdd_dbca.h``).  ``omega`` damps the min-marginal difference.
+    """
+
+    def __init__(self, inst, omega: float = 0.5, host_only: bool = False, max_device_bytes: int = 0,
+                 device: int = -1, stream: int = 0):
+        opt = B.bdd_default_options()
+        opt.omega = omega
+        opt.host_only = int(host_only)
+        opt.max_device_bytes = int(max_device_bytes)
+        opt.device = int(device)
+        opt.stream = stream or None
+        self.h = B.bdd_build(inst.n, inst.m, inst.row_ptr, inst.col, inst.val, inst.b, inst.sense,
+                             inst.c, opt)
+        s = B.bdd_sizes(self.h)
+        (self.n, self.m, self.nb, self.O, self.N, self.max_depth, self.max_width, self.nnz,
+         self.device_bytes, self.warp_tiles, self.block_tiles, self.launches_per_iter) = map(int, s)
+
+    def close(self):
+        if getattr(self, "h", None):
+            B.bdd_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def iterate(self, n_iter: int, lam: bool = False, mm: bool = False):
+        """Returns (lower bound, lambda, mm0, mm1) as host arrays (None where not requested)."""
+        return B.bdd_iterate(self.h, n_iter, lam=lam, mm=mm)
+
+    def iterate_device(self, n_iter: int, trace=None, lam=None, mm0=None, mm1=None, stream=None):
+        """Tensors (or raw device pointers) for the outputs; stream defaults to PyTorch's
+        current stream, so the work is ordered with PyTorch's work on it."""
+        def ptr(t):
+            if t is None:
+                return 0
+            return t if isinstance(t, int) else t.data_ptr()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+            if stream == 0:
+                stream = LEGACY_DEFAULT_STREAM
+        B.bdd_iterate_device(self.h, n_iter, ptr(trace), ptr(lam), ptr(mm0), ptr(mm1), stream)
+
+    def iterate_profiled(self, n_iter: int):
+        """Per-kernel summed device ms: [forward sweep, reduction, backward sweep, reduction+bound]."""
+        return B.bdd_iterate_profiled(self.h, n_iter)
+
+    def canonical(self) -> dict:
+        return B.bdd_export_canonical(self.h)
+
+    def get_state(self):
+        return B.bdd_get_state(self.h)
+
+    def set_state(self, lam, pending=None):
+        B.bdd_set_state(self.h, lam, pending)
+
+    def set_costs(self, c):
+        B.bdd_set_costs(self.h, c)

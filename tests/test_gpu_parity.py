@@ -1,0 +1,311 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the same seeded
+inputs.
+
+Tolerances (relative with a floor of 1: |a - b| <= tol * max(1, |a|, |b|)):
+  - BDD node / arc arrays read back from the device: bit-exact;
+  - min-marginals for the same FP32 multipliers: 1e-5 (FP32 path sums of at most a few hundred
+    terms of magnitude <= the bound scale);
+  - lower bound after 100 iterations of the deferred-averaging schedule (same omega): 1e-4;
+  - the device bound trace never drops by more than 1e-5 * |bound|.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from instances import (SENSE_LE, config, potts_mrf, random_ilp, sparse_matching, tomography,
+                       tracking)
+from instances.generators import _from_rows
+from oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+MM_TOL = 1e-5
+LB_TOL = 1e-4
+MONO_TOL = 1e-5
+
+
+def close(a, b, tol):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    fin = np.isfinite(a) & np.isfinite(b)
+    assert np.array_equal(np.isfinite(a), np.isfinite(b)), "infinite entries differ"
+    assert np.array_equal(np.sign(a[~fin]), np.sign(b[~fin]))
+    err = np.abs(a[fin] - b[fin]) / np.maximum(1.0, np.maximum(np.abs(a[fin]), np.abs(b[fin])))
+    assert err.size == 0 or err.max() <= tol, f"max rel err {err.max():.3e} > {tol:.1e}"
+
+
+@pytest.fixture(scope="module")
+def lib(cuda_lib):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return cuda_lib
+
+
+def solver(inst, **kw):
+    from paper_2009_00481_gb300 import Solver
+    return Solver(inst, **kw)
+
+
+CASES = {
+    "potts_20x20x3": lambda: config(0),
+    "matching_300x300": lambda: config(1),
+    "matching_small": lambda: sparse_matching(n_left=60, n_right=50, k=6, n_pairs=800, seed=3),
+    "tomography_16": lambda: tomography(side=16, seed=1, unary_sigma=0.05),
+    "tracking_10x40": lambda: tracking(frames=10, dets=40, seed=1),
+    "random_wide": lambda: random_ilp(n=60, m=40, max_row_vars=16, seed=11, coef=3),
+}
+
+
+# ------------------------------------------------------------------------------------------
+# structure
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_device_slabs_bit_exact(lib, name):
+    inst = CASES[name]()
+    want = Oracle(inst).canonical()
+    got = solver(inst).canonical()
+    for key in ["bdd_row", "bdd_depth", "occ_var", "occ_csr", "occ_width", "lo", "hi"]:
+        np.testing.assert_array_equal(got[key], want[key], err_msg=key)
+
+
+def test_device_slabs_full_tomography(lib):
+    inst = config(2)
+    want = Oracle(inst).canonical()
+    got = solver(inst).canonical()
+    for key in ["bdd_row", "bdd_depth", "occ_var", "occ_csr", "occ_width", "lo", "hi"]:
+        np.testing.assert_array_equal(got[key], want[key], err_msg=key)
+
+
+# ------------------------------------------------------------------------------------------
+# min-marginals for the same multipliers (standalone pass)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_min_marginals_same_lambda(lib, name):
+    inst = CASES[name]()
+    rng = np.random.default_rng(5)
+    lam = rng.normal(0, 1, size=inst.nnz).astype(np.float32)
+    lam[inst.val == 0] = 0
+    s = solver(inst)
+    s.set_state(lam)
+    lb, lam_out, m0, m1 = s.iterate(0, lam=True, mm=True)
+    o = Oracle(inst)
+    o.set_state(lam.astype(np.float64))
+    e0, e1 = o.min_marginals(fold=True)
+    close(m0, e0, MM_TOL)
+    close(m1, e1, MM_TOL)
+    np.testing.assert_array_equal(lam_out, lam)  # no pending share: lambda unchanged
+    close([lb], [o.bound()], MM_TOL)
+
+
+def test_min_marginals_with_pending_share(lib):
+    """Outputs fold the pending share P_i/|J_i| into lambda before the pass."""
+    inst = CASES["matching_small"]()
+    rng = np.random.default_rng(8)
+    lam = rng.normal(0, 1, size=inst.nnz).astype(np.float32)
+    P = rng.normal(0, 0.5, size=inst.n).astype(np.float32)
+    s = solver(inst)
+    s.set_state(lam, P)
+    lb, lam_out, m0, m1 = s.iterate(0, lam=True, mm=True)
+    o = Oracle(inst)
+    o.set_state(lam.astype(np.float64), P.astype(np.float64))
+    close(lam_out, o.lam(fold=True), 1e-6)
+    e0, e1 = o.min_marginals(fold=True)
+    close(m0, e0, MM_TOL)
+    close(m1, e1, MM_TOL)
+    close([lb], [o.bound()], MM_TOL)
+
+
+# ------------------------------------------------------------------------------------------
+# iterations: bound trace parity with the oracle's schedule
+# ------------------------------------------------------------------------------------------
+
+def _trace(s, iters):
+    import torch
+    tr = torch.zeros(iters, dtype=torch.float64, device="cuda")
+    s.iterate_device(iters, trace=tr)
+    torch.cuda.synchronize()
+    return tr.cpu().numpy()
+
+
+@pytest.mark.parametrize("omega", [0.5, 1.0])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_bound_trace_parity(lib, name, omega):
+    inst = CASES[name]()
+    iters = 100
+    want = Oracle(inst).run_parallel(iters, omega=omega)
+    got = _trace(solver(inst, omega=omega), iters)
+    close(got[-1:], want[-1:], LB_TOL)
+    close(got[:10], want[:10], LB_TOL)
+    scale = np.maximum(1.0, np.abs(got[1:]))
+    assert np.all(np.diff(got) >= -MONO_TOL * scale), "device bound decreased"
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_bound_parity_workloads_full(lib, k):
+    """Matching 300x300 at its 500 iterations; tracking 50x200 at 50 iterations."""
+    inst = config(k)
+    iters = {1: 500, 3: 50}[k]
+    want = Oracle(inst).run_parallel(iters, omega=0.5)
+    got = _trace(solver(inst), iters)
+    close(got[-1:], want[-1:], LB_TOL)
+    close(got[::25], want[::25], LB_TOL)
+
+
+def test_bound_parity_tomography_full(lib):
+    """64x64 tomography with unary tie-break costs (the all-zero-cost workload sits at a fixed
+    point of the non-smooth method), 100 iterations."""
+    inst = tomography(side=64, seed=0, unary_sigma=0.01)
+    want = Oracle(inst).run_parallel(100, omega=0.5)
+    got = _trace(solver(inst), 100)
+    close(got[-1:], want[-1:], LB_TOL)
+
+
+def test_zero_cost_tomography_stays_at_zero(lib):
+    inst = config(2)
+    got = _trace(solver(inst), 20)
+    assert np.all(got == 0.0)
+
+
+def test_outputs_after_iterations(lib):
+    """lambda folded and min-marginals after 100 iterations match the oracle's; the folded
+    multipliers of each variable sum to c_i."""
+    inst = config(0)
+    s = solver(inst)
+    lb, lam, m0, m1 = s.iterate(100, lam=True, mm=True)
+    o = Oracle(inst)
+    tr = o.run_parallel(100, omega=0.5)
+    close([lb], [tr[-1]], LB_TOL)
+    close(lam, o.lam(fold=True), 2e-4)
+    e0, e1 = o.min_marginals(fold=True)
+    close(m0, e0, 5e-4)
+    close(m1, e1, 5e-4)
+    sums = np.zeros(inst.n)
+    np.add.at(sums, inst.col, lam.astype(np.float64))
+    close(sums, inst.c, 1e-5)
+
+
+# ------------------------------------------------------------------------------------------
+# determinism, state and outputs
+# ------------------------------------------------------------------------------------------
+
+def test_deterministic(lib):
+    inst = config(1)
+    a, b = solver(inst), solver(inst)
+    ta, tb = _trace(a, 60), _trace(b, 60)
+    np.testing.assert_array_equal(ta, tb)
+    la, pa = a.get_state()
+    lb_, pb = b.get_state()
+    np.testing.assert_array_equal(la, lb_)
+    np.testing.assert_array_equal(pa, pb)
+
+
+def test_outputs_leave_state_unchanged(lib):
+    inst = CASES["tomography_16"]()
+    a, b = solver(inst), solver(inst)
+    t1 = _trace(a, 10)
+    a.iterate(0, lam=True, mm=True)
+    t2 = _trace(a, 10)
+    tb = _trace(b, 20)
+    np.testing.assert_array_equal(np.concatenate([t1, t2]), tb)
+
+
+def test_state_roundtrip_resumes_bit_identical(lib):
+    inst = CASES["tracking_10x40"]()
+    a, b = solver(inst), solver(inst)
+    _trace(a, 15)
+    lam, P = a.get_state()
+    b.set_state(lam, P)
+    np.testing.assert_array_equal(_trace(a, 15), _trace(b, 15))
+
+
+def test_set_costs_restarts(lib):
+    inst = config(0)
+    s = solver(inst)
+    t1 = _trace(s, 20)
+    s.set_costs(inst.c)
+    np.testing.assert_array_equal(_trace(s, 20), t1)
+    c2 = (inst.c * 2).astype(np.float32)
+    s.set_costs(c2)
+    inst2 = potts_mrf(20, 20, 3, seed=0)
+    inst2.c = c2
+    close(_trace(s, 20)[-1:], Oracle(inst2).run_parallel(20)[-1:], LB_TOL)
+
+
+def test_host_iterate_matches_device_trace(lib):
+    inst = config(0)
+    a, b = solver(inst), solver(inst)
+    t = _trace(a, 37)
+    lb, _, _, _ = b.iterate(37)
+    assert lb == t[-1]
+
+
+def test_profiled_iterations_match(lib):
+    inst = config(0)
+    a, b = solver(inst), solver(inst)
+    ms = a.iterate_profiled(12)
+    assert ms.shape == (4,) and np.all(ms > 0)
+    lb_a, _, _, _ = a.iterate(0)
+    lb_b = _trace(b, 12)[-1]
+    assert lb_a == lb_b
+
+
+# ------------------------------------------------------------------------------------------
+# edge cases
+# ------------------------------------------------------------------------------------------
+
+def test_empty_instance(lib):
+    inst = _from_rows("empty", 3, [], np.array([1.0, -2.0, -0.5], np.float32))
+    s = solver(inst)
+    lb, lam, m0, m1 = s.iterate(3, lam=True, mm=True)
+    assert lb == pytest.approx(-2.5)
+
+
+def test_unconstrained_variables_and_single_rows(lib):
+    rows = [(np.array([0, 2]), np.array([1, 1]), 1, SENSE_LE), (np.array([2]), np.array([1]), 1, SENSE_LE)]
+    inst = _from_rows("u", 4, rows, np.array([-1.0, -3.0, -2.0, 0.5], np.float32))
+    want = Oracle(inst).run_parallel(30)
+    got = _trace(solver(inst), 30)
+    close(got, want, LB_TOL)
+
+
+def test_wide_block_tiles(lib):
+    """A 300-variable cardinality row has layers up to 150 nodes wide (block tiles with several
+    nodes per thread), plus narrow rows of every warp team size."""
+    rng = np.random.default_rng(3)
+    rows = [(np.arange(300), np.ones(300), 149, SENSE_LE)]
+    for k in [2, 3, 5, 9, 17, 33, 40]:
+        cols = np.sort(rng.choice(300, size=k, replace=False))
+        rows.append((cols, np.ones(k), k // 2, SENSE_LE))
+    c = rng.normal(size=300).astype(np.float32)
+    inst = _from_rows("wide", 300, rows, c)
+    o = Oracle(inst)
+    assert o.max_width > 128
+    s = solver(inst)
+    assert s.block_tiles >= 1
+    np.testing.assert_array_equal(s.canonical()["lo"], o.canonical()["lo"])
+    close(_trace(s, 40), o.run_parallel(40), LB_TOL)
+
+
+def test_forced_variables(lib):
+    """Rows that force variables give +inf min-marginals; the difference is taken as 0."""
+    rows = [(np.array([0, 1]), np.array([1, 1]), 2, 0), (np.array([1, 2]), np.array([1, 1]), 1, SENSE_LE),
+            (np.array([0, 2, 3]), np.array([1, 1, 1]), 2, SENSE_LE)]
+    inst = _from_rows("forced", 4, rows, np.array([1.0, 2.0, -1.0, -0.5], np.float32))
+    s = solver(inst)
+    lb, lam, m0, m1 = s.iterate(0, mm=True)
+    o = Oracle(inst)
+    e0, e1 = o.min_marginals(fold=True)
+    close(m0, e0, MM_TOL)
+    close(m1, e1, MM_TOL)
+    close(_trace(s, 20), o.run_parallel(20), LB_TOL)
+
+
+def test_max_device_bytes(lib):
+    from paper_2009_00481_gb300 import BDDError
+    from paper_2009_00481_gb300.binding import BDD_ENOMEM
+    with pytest.raises(BDDError) as e:
+        solver(config(1), max_device_bytes=1 << 16)
+    assert e.value.code == BDD_ENOMEM

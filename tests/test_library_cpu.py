@@ -1,0 +1,124 @@
+"""CPU checks of the CUDA library: the C ABI loads and exports every declared symbol, and the
+host BDD compiler and slab layout reproduce the oracle's canonical BDDs bit for bit."""
+from __future__ import annotations
+
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from instances import SENSE_EQ, SENSE_LE, config, potts_mrf, random_ilp, tomography, tracking
+from instances.generators import _from_rows
+from oracle import Oracle, OracleError
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(bdd_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(cuda_lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(cuda_lib, name), name
+    from paper_2009_00481_gb300 import EXPORTED
+    assert sorted(EXPORTED) == names
+
+
+def test_strerror_and_defaults(cuda_lib):
+    from paper_2009_00481_gb300 import binding as B
+    assert B.bdd_strerror(0) == "ok"
+    assert "no 0-1 solution" in B.bdd_strerror(-2)
+    opt = B.bdd_default_options()
+    assert abs(opt.omega - 0.5) < 1e-7 and opt.host_only == 0 and opt.device == -1
+
+
+def _lib_canonical(inst, host_only):
+    from paper_2009_00481_gb300 import Solver
+    s = Solver(inst, host_only=host_only)
+    return s, s.canonical()
+
+
+def _assert_same(inst, host_only):
+    o = Oracle(inst)
+    want = o.canonical()
+    s, got = _lib_canonical(inst, host_only)
+    assert (s.nb, s.O, s.N, s.max_depth, s.max_width) == (o.nb, o.O, o.N, o.max_depth, o.max_width)
+    for key in ["bdd_row", "bdd_depth", "occ_var", "occ_csr", "occ_width", "lo", "hi"]:
+        np.testing.assert_array_equal(got[key], want[key], err_msg=key)
+
+
+@pytest.mark.parametrize("host_only", [1, 2])
+@pytest.mark.parametrize("which", ["potts", "matching", "tomography", "tomography_small", "tracking"])
+def test_compiler_bit_exact_workloads(cuda_lib, which, host_only):
+    """Canonical BDD node and arc arrays equal the oracle's (Prop. 2 canonicity makes the two
+    independently built BDDs identical after canonical numbering)."""
+    inst = {"potts": lambda: config(0), "matching": lambda: config(1), "tomography": lambda: config(2),
+            "tomography_small": lambda: tomography(side=12, seed=3, unary_sigma=0.1),
+            "tracking": lambda: tracking(frames=8, dets=30, seed=2)}[which]()
+    _assert_same(inst, host_only)
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_compiler_bit_exact_random(cuda_lib, seed):
+    inst = random_ilp(n=30, m=25, max_row_vars=14, seed=700 + seed, coef=3)
+    _assert_same(inst, 1 + seed % 2)
+
+
+def test_layout_classes(cuda_lib):
+    """Potts rows have width <= 2 (warp tiles of 16 BDDs); tomography projections are wider than
+    32 nodes (one block per BDD)."""
+    from paper_2009_00481_gb300 import Solver
+    s = Solver(config(0), host_only=2)
+    assert s.block_tiles == 0 and s.warp_tiles > 0
+    t = Solver(config(2), host_only=2)
+    assert t.block_tiles > 0 and t.max_width > 32
+
+
+def test_build_errors(cuda_lib):
+    from paper_2009_00481_gb300 import BDDError, Solver
+    from paper_2009_00481_gb300.binding import BDD_EINFEASIBLE, BDD_EINVAL
+    dup = _from_rows("dup", 3, [(np.array([1, 1]), np.array([1, 1]), 1, SENSE_LE)], np.zeros(3, np.float32))
+    with pytest.raises(BDDError) as e:
+        Solver(dup, host_only=1)
+    assert e.value.code == BDD_EINVAL
+    inf = _from_rows("inf", 3, [(np.array([0, 1]), np.array([1, 1]), 1, SENSE_LE),
+                                (np.array([0, 2]), np.array([1, 1]), 3, SENSE_EQ)], np.zeros(3, np.float32))
+    with pytest.raises(BDDError) as e:
+        Solver(inf, host_only=1)
+    assert e.value.code == BDD_EINFEASIBLE and e.value.row == 1
+    with pytest.raises(OracleError) as e2:
+        Oracle(inf)
+    assert e2.value.row == 1
+    nan = _from_rows("nan", 1, [(np.array([0]), np.array([1]), 1, SENSE_LE)], np.array([np.nan], np.float32))
+    with pytest.raises(BDDError) as e:
+        Solver(nan, host_only=1)
+    assert e.value.code == BDD_EINVAL
+    bad_col = _from_rows("col", 2, [(np.array([0, 5]), np.array([1, 1]), 1, SENSE_LE)], np.zeros(2, np.float32))
+    with pytest.raises(BDDError) as e:
+        Solver(bad_col, host_only=1)
+    assert e.value.code == BDD_EINVAL
+    empty = _from_rows("e", 2, [(np.array([], np.int64), np.array([], np.int64), 0, SENSE_LE),
+                                (np.array([0, 1]), np.array([0, 1]), 1, SENSE_EQ)], np.zeros(2, np.float32))
+    s = Solver(empty, host_only=2)
+    assert s.nb == 1 and s.O == 1
+
+
+def test_host_only_refuses_device_calls(cuda_lib):
+    from paper_2009_00481_gb300 import BDDError, Solver
+    from paper_2009_00481_gb300.binding import BDD_ESTATE
+    s = Solver(potts_mrf(3, 3, 2, seed=0), host_only=1)
+    with pytest.raises(BDDError) as e:
+        s.iterate(1)
+    assert e.value.code == BDD_ESTATE
+    with pytest.raises(BDDError) as e:
+        s.get_state()
+    assert e.value.code == BDD_ESTATE
