@@ -20,7 +20,9 @@
  *     them) and receive 0.
  *   - One solver handle must not be used from two host threads at once.
  *   - Device calls run on the solver's stream unless a stream is passed; results are
- *     stream-ordered.  Host-array calls synchronise before returning.
+ *     stream-ordered.  Host-array calls synchronise before returning.  The calls of one
+ *     solver are ordered among themselves even when they use different streams (each call
+ *     waits on an event recorded at the end of the previous one).
  */
 #ifndef BDD_DBCA_H
 #define BDD_DBCA_H

@@ -92,8 +92,10 @@ struct bdd_solver {
   int grid_sweep = 0, n_warp_blocks = 0, grid_reduce = 1;
   size_t smem = 0;
   cudaGraphExec_t g_many = nullptr, g_one = nullptr;
+  cudaEvent_t ev_last = nullptr;  // end of the solver's last enqueued work, on whatever stream
 
   ~bdd_solver() {
+    if (ev_last) cudaEventDestroy(ev_last);
     if (g_many) cudaGraphExecDestroy(g_many);
     if (g_one) cudaGraphExecDestroy(g_one);
     for (void *p : allocs) cudaFree(p);
@@ -159,6 +161,17 @@ struct bdd_solver {
     r.nb = (int)nb;
     r.empty_const = empty_const;
     return r;
+  }
+
+  // Work of one solver may be enqueued on several streams (its own, or one passed per call);
+  // each call first waits for the previous call's work and then marks its own end.
+  int begin(cudaStream_t s) {
+    CK(cudaStreamWaitEvent(s, ev_last, 0));
+    return BDD_OK;
+  }
+  int end(cudaStream_t s) {
+    CK(cudaEventRecord(ev_last, s));
+    return BDD_OK;
   }
 
   int sweep(bool fwd, int mode, cudaStream_t s, float *m0 = nullptr, float *m1 = nullptr) {
@@ -261,6 +274,7 @@ int upload(bdd_solver *h, Tp **d, const std::vector<Tp> &v) {
 }
 
 int setup_device(bdd_solver *h, const Layout &L, const float *c) {
+  CK(cudaEventCreateWithFlags(&h->ev_last, cudaEventDisableTiming));
   h->bdd_perm = L.bdd_perm;
   h->tile_occ0 = L.tile_occ0;
   h->tile_bdd0 = L.tile_bdd0;
@@ -313,6 +327,7 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   RC(h->ensure_trace(1024));
   if (n) CK(cudaMemcpy(h->d_c, c, sizeof(float) * n, cudaMemcpyHostToDevice));
   RC(h->restart(h->stream));
+  RC(h->end(h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return BDD_OK;
 }
@@ -472,6 +487,7 @@ int bdd_iterate_device(bdd_solver *h, int n_iter, double *d_bound_trace, float *
     if (!h->g_one) RC(h->capture(1, &h->g_one));
     if (!h->g_many && n_iter >= kGraphIters) RC(h->capture(kGraphIters, &h->g_many));
   }
+  RC(h->begin(s));
   CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
   int left = n_iter;
   while (left >= kGraphIters) {
@@ -481,7 +497,8 @@ int bdd_iterate_device(bdd_solver *h, int n_iter, double *d_bound_trace, float *
   for (; left > 0; --left) CK(cudaGraphLaunch(h->g_one, s));
   if (d_bound_trace && n_iter > 0)
     CK(cudaMemcpyAsync(d_bound_trace, h->d_trace, sizeof(double) * n_iter, cudaMemcpyDeviceToDevice, s));
-  return h->output_pass(s, d_lambda, d_mm0, d_mm1);
+  RC(h->output_pass(s, d_lambda, d_mm0, d_mm1));
+  return h->end(s);
 }
 
 int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms) {
@@ -492,6 +509,7 @@ int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms) {
   cudaStream_t s = h->stream;
   for (int t = 0; t < 4; ++t) kernel_ms[t] = 0.0;
   RC(h->ensure_trace(n_iter + 1));
+  RC(h->begin(s));
   CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
   const int kBatch = 256;  // iterations per batch of recorded events
   std::vector<cudaEvent_t> ev(5 * kBatch, nullptr);
@@ -524,6 +542,7 @@ int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms) {
   for (auto &e : ev)
     if (e) cudaEventDestroy(e);
   if (rc != BDD_OK) cudaGetLastError();
+  if (rc == BDD_OK) rc = h->end(s);
   return rc;
 }
 
@@ -536,6 +555,7 @@ int bdd_iterate(bdd_solver *h, int n_iter, double *lower_bound, float *lambda, f
   if (lambda || mm0 || mm1) RC(h->ensure_outputs());
   RC(bdd_iterate_device(h, n_iter, nullptr, lambda ? h->d_out_lam : nullptr, mm0 ? h->d_out_m0 : nullptr,
                         mm1 ? h->d_out_m1 : nullptr, s));
+  RC(h->begin(s));
   if (lower_bound && n_iter == 0) {
     CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
     RC(h->reduce(false, true, s));
@@ -548,6 +568,7 @@ int bdd_iterate(bdd_solver *h, int n_iter, double *lower_bound, float *lambda, f
     const int last = n_iter > 0 ? n_iter - 1 : 0;
     CK(cudaMemcpyAsync(lower_bound, h->d_trace + last, sizeof(double), cudaMemcpyDeviceToHost, s));
   }
+  RC(h->end(s));
   CK(cudaStreamSynchronize(s));
   return BDD_OK;
 }
@@ -560,9 +581,11 @@ int bdd_set_costs(bdd_solver *h, const float *c) {
   if (h->host_only) return BDD_OK;
   DeviceGuard dg(h->device);
   if (!dg.ok) return BDD_ECUDA;
+  RC(h->begin(h->stream));
   if (h->n) CK(cudaMemcpyAsync(h->d_c, c, sizeof(float) * h->n, cudaMemcpyHostToDevice, h->stream));
   h->drop_graphs();  // the bound constant is baked into the captured reductions
   RC(h->restart(h->stream));
+  RC(h->end(h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return BDD_OK;
 }
@@ -612,7 +635,7 @@ int bdd_export_canonical(const bdd_solver *h, int *bdd_row, int *bdd_depth, int 
   } else {
     DeviceGuard dg(h->device);
     if (!dg.ok) return BDD_ECUDA;
-    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaEventSynchronize(h->ev_last));
     CK(cudaMemcpy(off.data(), h->d_occ_node_off, sizeof(int) * (O + 1), cudaMemcpyDeviceToHost));
     if (O) {
       CK(cudaMemcpy(var.data(), h->d_occ_var, sizeof(int) * O, cudaMemcpyDeviceToHost));
@@ -663,6 +686,7 @@ int bdd_get_state(const bdd_solver *h_in, float *lambda, float *pending) {
   DeviceGuard dg(h->device);
   if (!dg.ok) return BDD_ECUDA;
   cudaStream_t s = h->stream;
+  RC(h->begin(s));
   if (lambda) {
     RC(h->ensure_outputs());
     if (h->nnz) CK(cudaMemsetAsync(h->d_out_lam, 0, sizeof(float) * h->nnz, s));
@@ -672,6 +696,7 @@ int bdd_get_state(const bdd_solver *h_in, float *lambda, float *pending) {
     if (h->nnz) CK(cudaMemcpyAsync(lambda, h->d_out_lam, sizeof(float) * h->nnz, cudaMemcpyDeviceToHost, s));
   }
   if (pending && h->n) CK(cudaMemcpyAsync(pending, h->d_P, sizeof(float) * h->n, cudaMemcpyDeviceToHost, s));
+  RC(h->end(s));
   CK(cudaStreamSynchronize(s));
   return BDD_OK;
 }
@@ -683,6 +708,7 @@ int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending) {
   if (!dg.ok) return BDD_ECUDA;
   cudaStream_t s = h->stream;
   RC(h->ensure_outputs());
+  RC(h->begin(s));
   if (h->nnz) CK(cudaMemcpyAsync(h->d_out_lam, lambda, sizeof(float) * h->nnz, cudaMemcpyHostToDevice, s));
   if (h->O && gather_lambda_launch(h->d_out_lam, h->d_occ_csr, h->d_lam, (int)h->O, s)) return BDD_ECUDA;
   if (h->n) {
@@ -693,6 +719,7 @@ int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending) {
     if (share_from_pending_launch(h->d_var_ptr, h->d_P, h->d_share, h->n, s)) return BDD_ECUDA;
   }
   RC(h->sweep(false, kMessages, s));
+  RC(h->end(s));
   CK(cudaStreamSynchronize(s));
   return BDD_OK;
 }

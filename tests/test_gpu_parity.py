@@ -234,6 +234,24 @@ def test_set_costs_restarts(lib):
     close(_trace(s, 20)[-1:], Oracle(inst2).run_parallel(20)[-1:], LB_TOL)
 
 
+def test_calls_on_different_streams_are_ordered(lib):
+    """Device iterations enqueued on a PyTorch stream, then host calls on the solver's own
+    stream without any synchronisation in between: the host calls see the finished iterations."""
+    import torch
+    inst = config(1)
+    a, b = solver(inst), solver(inst)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        tr = torch.zeros(40, dtype=torch.float64, device="cuda")
+        a.iterate_device(40, trace=tr)
+    lb_a, lam_a, _, _ = a.iterate(0, lam=True)
+    lb_b, lam_b, _, _ = b.iterate(40, lam=True)
+    torch.cuda.synchronize()
+    assert lb_a == lb_b
+    np.testing.assert_array_equal(lam_a, lam_b)
+    np.testing.assert_array_equal(tr.cpu().numpy()[-1], lb_b)
+
+
 def test_host_iterate_matches_device_trace(lib):
     inst = config(0)
     a, b = solver(inst), solver(inst)
