@@ -131,6 +131,23 @@ int bdd_export_canonical(const bdd_solver *h, int *bdd_row, int *bdd_depth, int 
 int bdd_get_state(const bdd_solver *h, float *lambda, float *pending);
 int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending);
 
+/* Lower bound sum_j E_j + sum_{i: deg_i > 0} min(0, P_i) + empty_const in FP64, from caller
+ * device arrays, without allocating anything.  The paper has no counterpart: it is the bound
+ * reduction of bdd_iterate offered on its own for callers that cannot allocate device memory
+ * (code that runs inside someone else's memory pool or arena, or inside a framework that
+ * forbids cudaMalloc on its hot path), who still own their inputs and output.
+ *   n, nb:  variables and BDDs; max(n, nb) <= 4,194,304, else BDD_ETOOBIG (the scratch limit)
+ *   d_E:    float[nb] per-BDD energies E_j; d_P: float[n] pending sums; d_deg: int32[n] |J_i|
+ *   empty_const: sum of min(0, c_i) over variables in no row
+ *   d_bound: double[1] output; stream: cudaStream_t (NULL = legacy default stream)
+ * Scratch: a static device array of 1025 doubles (8.2 KB) that every GPU loading this library
+ * holds until the process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress), so make the first call on each device before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (e.g. on two streams at
+ * once) race and must be serialised by the caller.  Returns after enqueueing. */
+int bdd_lower_bound_noalloc(int n, int nb, const float *d_E, const float *d_P, const int *d_deg,
+                            double empty_const, double *d_bound, void *stream);
+
 /* Text for a status code (static storage). */
 const char *bdd_strerror(int code);
 

@@ -22,7 +22,7 @@ EXPORTED = [
     "bdd_default_options", "bdd_build", "bdd_last_failed_row", "bdd_iterate", "bdd_iterate_device",
     "bdd_iterate_profiled",
     "bdd_set_costs", "bdd_sizes", "bdd_export_canonical", "bdd_get_state", "bdd_set_state",
-    "bdd_strerror", "bdd_free",
+    "bdd_strerror", "bdd_free", "bdd_lower_bound_noalloc",
 ]
 
 
@@ -72,6 +72,7 @@ def load(path: str | None = None):
     lib.bdd_strerror.restype = C.c_char_p
     lib.bdd_free.argtypes = [vp]
     lib.bdd_free.restype = None
+    lib.bdd_lower_bound_noalloc.argtypes = [i32, i32, vp, vp, vp, f64, vp, vp]
     if path == LIB:
         _lib = lib
     return lib
@@ -186,6 +187,15 @@ def bdd_set_state(h, lam, P=None):
     lam = np.ascontiguousarray(lam, np.float32)
     P = None if P is None else np.ascontiguousarray(P, np.float32)
     _check(load().bdd_set_state(h, _ptr(lam, C.c_float), _ptr(P, C.c_float)), "bdd_set_state")
+
+
+def bdd_lower_bound_noalloc(n: int, nb: int, d_E: int, d_P: int, d_deg: int, empty_const: float,
+                            d_bound: int, stream: int = 0):
+    """Bound reduction into caller device memory with no allocation (pointers are integers,
+    e.g. tensor.data_ptr()).  For callers that cannot allocate device memory."""
+    _check(load().bdd_lower_bound_noalloc(int(n), int(nb), d_E or None, d_P or None, d_deg or None,
+                                          float(empty_const), d_bound or None, stream or None),
+           "bdd_lower_bound_noalloc")
 
 
 def bdd_strerror(code: int) -> str:
