@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--iters", type=int, default=0, help="iterations per step (default: the workload's)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", type=int, default=1, help="1 per-phase graphs (default), 0 persistent kernel")
     return ap.parse_args()
 
 
@@ -55,13 +56,18 @@ def dist_env():
 # ------------------------------------------------------------------------------------------
 def algorithmic_bytes(kind: str, N: int, O: int, n: int, nb: int) -> int:
     if kind in ("fwd", "bwd"):
-        # per node: lo/hi 8 B, fm 4 B, bm 4 B; per occurrence: node offset 4, variable 4,
-        # lambda read+write 8, delta 4, share 4; per BDD: depth (+ root value on bwd)
+        # per node: lo/hi 8 B, fm 4 B, bm 4 B; per occurrence: node offset 4, lambda read+write
+        # 8, share 4, slot 4, difference write 4; per BDD: depth (+ root value on the backward
+        # sweep)
         return 16 * N + 24 * O + (4 if kind == "fwd" else 8) * nb
-    if kind == "red":
-        return 8 * O + 12 * n
-    if kind == "red_bound":
-        return 8 * O + 12 * n + 4 * nb
+    if kind == "pending":
+        # per variable: slot range 4, P write 4; per slot: difference 4, occurrence id 4,
+        # share write 4
+        return 8 * n + 12 * O
+    if kind == "pending_bound":
+        return algorithmic_bytes("pending", N, O, n, nb) + 4 * nb
+    if kind == "iteration":
+        return sum(algorithmic_bytes(k, N, O, n, nb) for k in ("fwd", "pending", "bwd", "pending_bound"))
     raise ValueError(kind)
 
 
@@ -164,7 +170,7 @@ def ours(args):
     inst = config(k)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    s = Solver(inst, omega=0.5, stream=stream.cuda_stream)
+    s = Solver(inst, omega=0.5, stream=stream.cuda_stream, schedule=args.schedule)
     arcs_per_step = 2 * s.N * iters
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     trace = torch.zeros(iters, dtype=torch.float64, device="cuda")
@@ -212,16 +218,27 @@ def ours(args):
     value = world * arcs_per_step / (ms / 1e3)
     tr = trace.cpu().numpy()
 
-    # per-kernel device time (kernel-by-kernel launches with events), for the roofline
+    # roofline of the dominant kernel.  Persistent schedule: the one iteration kernel, timed by
+    # the step's events (one launch per step).  Per-phase schedule: the slowest of the per-phase
+    # kernels, timed kernel by kernel with events.  Both report the per-phase breakdown.
     s.set_costs(inst.c)
     kms = s.iterate_profiled(iters)
-    kinds = ["fwd", "red", "bwd", "red_bound"]
-    dom = int(np.argmax(kms))
-    per_launch_ms = kms[dom] / iters
-    abytes = algorithmic_bytes(kinds[dom], s.N, s.O, s.n, s.nb)
+    kinds = ["fwd", "pending", "bwd", "pending_bound"]
     peak, peak_kind = measured_peaks()
+    iter_bytes = algorithmic_bytes("iteration", s.N, s.O, s.n, s.nb)
+    if s.schedule == 0:
+        kernel_name = "iterate_kernel (persistent, all iterations of a step)"
+        abytes = iter_bytes * iters
+        per_launch_ms = ms
+        launches = args.steps
+    else:
+        dom = int(np.argmax(kms))
+        kernel_name = {"fwd": "sweep_kernel<forward>", "bwd": "sweep_kernel<backward>",
+                       "pending": "pending_kernel", "pending_bound": "pending_kernel<bound>"}[kinds[dom]]
+        abytes = algorithmic_bytes(kinds[dom], s.N, s.O, s.n, s.nb)
+        per_launch_ms = kms[dom] / iters
+        launches = args.steps * iters * 4
     achieved = abytes / (per_launch_ms / 1e3) / 1e9
-    iter_bytes = sum(algorithmic_bytes(kd, s.N, s.O, s.n, s.nb) for kd in kinds)
 
     # end to end through the C ABI with host buffers: build (host compile + upload), iterate,
     # read back the bound, multipliers and min-marginals
@@ -231,7 +248,7 @@ def ours(args):
         for _ in range(args.e2e_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s2 = Solver(inst, omega=0.5)
+            s2 = Solver(inst, omega=0.5, schedule=args.schedule)
             s2.iterate(iters, lam=True, mm=True)
             s2.close()
             times.append(time.perf_counter() - t0)
@@ -263,15 +280,15 @@ def ours(args):
                    f"{iter_bytes / 1e6:.1f} MB per iteration, L2-resident inside a step",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "time_to_bound": ttb,
-        "roofline": {"bound": "hbm", "kernel": {"fwd": "sweep_kernel<forward>", "bwd": "sweep_kernel<backward>",
-                     "red": "reduce_kernel", "red_bound": "reduce_kernel<bound>"}[kinds[dom]],
+        "roofline": {"bound": "hbm", "kernel": kernel_name,
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "algorithmic_bytes_per_launch": abytes, "launch_ms": per_launch_ms,
-                     "kernel_ms_per_iteration": {kd: float(v / iters) for kd, v in zip(kinds, kms)}},
+                     "per_phase_kernel_ms_per_iteration": {kd: float(v / iters) for kd, v in zip(kinds, kms)}},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps * iters * 4,
+        "gpu_launches": launches,
+        "schedule": "persistent" if s.schedule == 0 else "per-phase graphs",
         "clocks": clocks,
         "wall_s": wall,
     }

@@ -60,6 +60,14 @@ typedef struct {
                                  slab layout back, as it does from the device */
   int device;                 /* CUDA device ordinal; -1 = the current device (default) */
   void *stream;               /* cudaStream_t for all device work; NULL = a stream the solver owns */
+  int schedule;               /* 1 (default): per-phase kernels (two sweeps, two pending-sum passes
+                                 per iteration) replayed from CUDA graphs with programmatic
+                                 dependent launch; 0: one persistent cooperative kernel per call
+                                 runs all iterations, four grid barriers per iteration.  Both run
+                                 the same arithmetic; 0 falls back to 1 on devices without
+                                 cooperative launch. */
+  long long spin_limit;       /* polls before a grid-barrier wait gives up (then the call's host
+                                 form returns BDD_ETIMEOUT); default 1 << 26 */
 } bdd_options;
 
 void bdd_default_options(bdd_options *opt);
@@ -90,7 +98,8 @@ int bdd_last_failed_row(void);
  *   mm0, mm1:    float[nnz] or NULL; min-marginals (Sec. 3.2 eq. min-marginals) at those
  *                multipliers, from a full forward and backward pass
  * n_iter = 0 only evaluates the outputs.  Solver state (multipliers, pending sums) after
- * the call is the same whether outputs are requested or not. */
+ * the call is the same whether outputs are requested or not.  Returns BDD_ETIMEOUT if a
+ * grid-barrier wait of this or an earlier device call gave up (see spin_limit). */
 int bdd_iterate(bdd_solver *h, int n_iter, double *lower_bound, float *lambda, float *mm0,
                 float *mm1);
 
@@ -102,10 +111,11 @@ int bdd_iterate(bdd_solver *h, int n_iter, double *lower_bound, float *lambda, f
 int bdd_iterate_device(bdd_solver *h, int n_iter, double *d_bound_trace, float *d_lambda,
                        float *d_mm0, float *d_mm1, void *stream);
 
-/* Same iterations as bdd_iterate_device, launched kernel by kernel with CUDA events between
- * the kernels, for measurement.  kernel_ms[4] receives the summed device time of the forward
- * sweeps, the reductions after them, the backward sweeps and the reductions (with the bound)
- * after them; synchronises before returning.  kernel_ms: host double[4]. */
+/* Same iterations as bdd_iterate_device, run as per-phase kernels launched one by one with CUDA
+ * events between them, for measurement.  kernel_ms[4] receives the summed device time of the
+ * forward sweeps, the pending-sum passes after them, the backward sweeps, and the pending-sum
+ * passes with the FP64 bound after them; synchronises before returning.  kernel_ms: host
+ * double[4]. */
 int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms);
 
 /* Replaces c and restarts: lambda = c/|J_i|, pending sums 0, one backward pass.  c: float[n],
@@ -114,7 +124,7 @@ int bdd_set_costs(bdd_solver *h, const float *c);
 
 /* Sizes: out[0] n, [1] m, [2] BDDs, [3] occurrences (nonzeros kept), [4] nodes, [5] max depth,
  * [6] max width, [7] nnz, [8] device bytes held, [9] warp tiles, [10] block tiles,
- * [11] kernel launches per iteration. */
+ * [11] schedule in use (0 persistent, 1 per-phase graphs). */
 int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]);
 
 /* Canonical form of the BDDs, read back from the device slabs (or the host copy when built

@@ -29,7 +29,7 @@ EXPORTED = [
 class bdd_options(C.Structure):
     _fields_ = [("omega", C.c_float), ("max_width", C.c_int), ("max_nodes", C.c_longlong),
                 ("max_device_bytes", C.c_longlong), ("host_only", C.c_int), ("device", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("schedule", C.c_int), ("spin_limit", C.c_longlong)]
 
 
 class BDDError(RuntimeError):
@@ -147,8 +147,8 @@ def bdd_iterate_device(h, n_iter: int, d_bound_trace=0, d_lambda=0, d_mm0=0, d_m
 
 
 def bdd_iterate_profiled(h, n_iter: int) -> np.ndarray:
-    """Summed device milliseconds of [forward sweeps, reductions, backward sweeps, reductions
-    with bound] over n_iter iterations launched kernel by kernel."""
+    """Summed device milliseconds of [forward sweeps, pending passes, backward sweeps, pending
+    passes with bound] over n_iter iterations launched kernel by kernel."""
     ms = np.zeros(4, np.float64)
     _check(load().bdd_iterate_profiled(h, int(n_iter), _ptr(ms, C.c_double)), "bdd_iterate_profiled")
     return ms

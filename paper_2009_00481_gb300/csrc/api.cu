@@ -79,18 +79,27 @@ struct bdd_solver {
   long long *d_occ_csr = nullptr;
   int2 *d_lohi = nullptr;
   float *d_fm = nullptr, *d_bm = nullptr, *d_lam = nullptr, *d_delta = nullptr;
-  float *d_share = nullptr, *d_P = nullptr, *d_c = nullptr;
+  float *d_P = nullptr, *d_c = nullptr, *d_share_occ = nullptr;
+  int *d_occ_slot = nullptr;
   int *d_bdd_depth = nullptr;
   float *d_bdd_E = nullptr;
   int *d_tile_occ0 = nullptr, *d_tile_bdd0 = nullptr, *d_tile_nbdd = nullptr;
   int *d_var_ptr = nullptr, *d_var_occ = nullptr;
+  // persistent schedule
+  int schedule = 1;
+  long long spin_limit = 1LL << 26;
+  int grid_persist = 0;
+  double *d_part = nullptr;
+  unsigned *d_barrier = nullptr;
+  int *d_error = nullptr;
+  int block_depth_buf = 0;
   double *d_partial = nullptr, *d_trace = nullptr;
   unsigned *d_ticket = nullptr;
   int *d_iter = nullptr;
   int trace_cap = 0;
   float *d_out_lam = nullptr, *d_out_m0 = nullptr, *d_out_m1 = nullptr;
   int grid_sweep = 0, n_warp_blocks = 0, grid_reduce = 1;
-  size_t smem = 0;
+  size_t smem = 0, smem_persist = 0;
   cudaGraphExec_t g_many = nullptr, g_one = nullptr;
   cudaEvent_t ev_last = nullptr;  // end of the solver's last enqueued work, on whatever stream
 
@@ -122,14 +131,14 @@ struct bdd_solver {
   SweepParams sweep_params(float *out_m0 = nullptr, float *out_m1 = nullptr) const {
     SweepParams p;
     p.occ_node_off = d_occ_node_off;
-    p.occ_var = d_occ_var;
     p.occ_csr = d_occ_csr;
     p.lohi = d_lohi;
     p.fm = d_fm;
     p.bm = d_bm;
     p.lam = d_lam;
+    p.occ_slot = d_occ_slot;
     p.delta = d_delta;
-    p.share = d_share;
+    p.share_occ = d_share_occ;
     p.bdd_depth = d_bdd_depth;
     p.bdd_E = d_bdd_E;
     p.tile_occ0 = d_tile_occ0;
@@ -140,17 +149,18 @@ struct bdd_solver {
     for (int c = 0; c < kWarpClasses + 2; ++c) p.class_tile_off[c] = class_tile_off[c];
     p.n_warp_blocks = n_warp_blocks;
     p.block_buf = block_buf;
+    p.block_depth_buf = block_depth_buf;
     p.omega = omega;
     return p;
   }
 
-  ReduceParams reduce_params() const {
-    ReduceParams r;
+  PendingParams pending_params() const {
+    PendingParams r;
     r.var_ptr = d_var_ptr;
     r.var_occ = d_var_occ;
     r.delta = d_delta;
     r.P = d_P;
-    r.share = d_share;
+    r.share_occ = d_share_occ;
     r.bdd_E = d_bdd_E;
     r.partial = d_partial;
     r.ticket = d_ticket;
@@ -178,16 +188,50 @@ struct bdd_solver {
     return sweep_launch(fwd, mode, sweep_params(m0, m1), grid_sweep, s) ? BDD_ECUDA : BDD_OK;
   }
 
-  int reduce(bool recompute, bool bound, cudaStream_t s) {
-    return reduce_launch(recompute, bound, reduce_params(), grid_reduce, s) ? BDD_ECUDA : BDD_OK;
+  int pending(bool bound, cudaStream_t s) {
+    return pending_launch(bound, pending_params(), grid_reduce, s) ? BDD_ECUDA : BDD_OK;
   }
 
-  // one iteration: forward sweep, reduction, backward sweep, reduction + bound
+  // one iteration: forward sweep, pending sums, backward sweep, pending sums and bound
   int enqueue_iteration(cudaStream_t s) {
     RC(sweep(true, kUpdate, s));
-    RC(reduce(true, false, s));
+    RC(pending(false, s));
     RC(sweep(false, kUpdate, s));
-    RC(reduce(true, true, s));
+    RC(pending(true, s));
+    return BDD_OK;
+  }
+
+  int launch_persistent(int n_iter, cudaStream_t s) {
+    IterParams q;
+    q.sp = sweep_params();
+    q.var_ptr = d_var_ptr;
+    q.var_occ = d_var_occ;
+    q.P = d_P;
+    q.share_occ = d_share_occ;
+    q.part = d_part;
+    q.barrier = d_barrier;
+    q.error = d_error;
+    q.trace = d_trace;
+    q.trace_cap = trace_cap;
+    q.n_iter = n_iter;
+    q.n = n;
+    q.empty_const = empty_const;
+    q.spin_limit = spin_limit;
+    CK(cudaMemsetAsync(d_barrier, 0, 2 * sizeof(unsigned), s));
+    return iterate_persistent_launch(q, grid_persist, smem_persist, s) ? BDD_ECUDA : BDD_OK;
+  }
+
+  // a grid-barrier wait of an earlier launch gave up: report once, then clear
+  int take_device_error(cudaStream_t s) {
+    if (!d_error) return BDD_OK;
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, d_error, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (err != 0) {
+      CK(cudaMemsetAsync(d_error, 0, sizeof(int), s));
+      CK(cudaStreamSynchronize(s));
+      return BDD_ETIMEOUT;
+    }
     return BDD_OK;
   }
 
@@ -236,8 +280,8 @@ struct bdd_solver {
   int restart(cudaStream_t s) {
     if (O > 0 && init_lambda_launch(d_occ_var, d_var_ptr, d_c, d_lam, (int)O, s)) return BDD_ECUDA;
     CK(cudaMemsetAsync(d_P, 0, sizeof(float) * std::max(n, 1), s));
-    CK(cudaMemsetAsync(d_share, 0, sizeof(float) * std::max(n, 1), s));
     CK(cudaMemsetAsync(d_delta, 0, sizeof(float) * std::max<long long>(O, 1), s));
+    CK(cudaMemsetAsync(d_share_occ, 0, sizeof(float) * std::max<long long>(O, 1), s));
     return sweep(false, kMessages, s);
   }
 
@@ -246,7 +290,7 @@ struct bdd_solver {
     const size_t bytes = sizeof(float) * (size_t)nnz;
     if (lam_out) {
       if (nnz) CK(cudaMemsetAsync(lam_out, 0, bytes, s));
-      if (O && scatter_lambda_launch(d_lam, d_share, d_occ_var, d_occ_csr, lam_out, (int)O, true, s))
+      if (O && scatter_lambda_launch(d_lam, d_share_occ, d_occ_csr, lam_out, (int)O, true, s))
         return BDD_ECUDA;
     }
     if (m0 || m1) {
@@ -283,12 +327,31 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   h->n_warp_tiles = L.n_warp_tiles;
   h->n_block_tiles = L.n_block_tiles;
   h->block_buf = ((L.max_block_width + 3) / 4) * 4;
+  {
+    int dmax = 0;
+    for (int t = L.class_tile_off[kWarpClasses]; t < L.class_tile_off[kWarpClasses + 1]; ++t)
+      dmax = std::max(dmax, L.bdd_depth[L.tile_bdd0[t]]);
+    h->block_depth_buf = ((dmax + 3) / 4) * 4;
+  }
   h->n_warp_blocks = (L.n_warp_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   h->grid_sweep = h->n_warp_blocks + L.n_block_tiles;
   const int range = std::max<long long>(h->n, h->nb) > 0 ? (int)std::max<long long>(h->n, h->nb) : 1;
   h->grid_reduce = std::max(1, std::min((range + kReduceThreads - 1) / kReduceThreads, 152 * 8));
-  h->smem = (2 * kWarpsPerBlock + 2 * (size_t)h->block_buf) * sizeof(float);
+  h->smem = sweep_smem_bytes(h->block_buf, h->block_depth_buf);
+  h->smem_persist = persist_smem_bytes(h->block_buf, h->block_depth_buf);
   if (h->smem > 48 * 1024 && sweep_set_smem(h->smem)) return BDD_ECUDA;
+  if (h->schedule == 0) {
+    int max_grid = 0;
+    if (iterate_set_smem(h->smem_persist) == 0 && iterate_persistent_max_grid(h->smem_persist, &max_grid) == 0) {
+      // enough blocks for one warp tile per warp and one block tile per 128-thread group
+      const long long need = (L.n_warp_tiles + kPersistWarps - 1) / kPersistWarps +
+                             (L.n_block_tiles + kSubBlocks - 1) / kSubBlocks;
+      h->grid_persist = (int)std::max<long long>(1, std::min<long long>(max_grid, need));
+    } else {
+      cudaGetLastError();
+      h->schedule = 1;  // no cooperative launch (or not enough shared memory) on this device
+    }
+  }
 
   // device memory estimate against the cap, before allocating anything
   const long long O = h->O, N = h->N, nb = h->nb, n = h->n;
@@ -300,6 +363,7 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   RC(upload(h, &h->d_occ_node_off, L.occ_node_off));
   RC(upload(h, &h->d_occ_var, L.occ_var));
   RC(upload(h, &h->d_occ_csr, L.occ_csr));
+  RC(upload(h, &h->d_occ_slot, L.occ_slot));
   {
     int *tmp = nullptr;
     RC(upload(h, &tmp, L.lohi));
@@ -309,7 +373,11 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   RC(h->alloc(&h->d_bm, N));
   RC(h->alloc(&h->d_lam, O));
   RC(h->alloc(&h->d_delta, O));
-  RC(h->alloc(&h->d_share, n));
+  RC(h->alloc(&h->d_share_occ, O));
+  RC(h->alloc(&h->d_part, 2LL * std::max(1, h->grid_persist)));
+  RC(h->alloc(&h->d_barrier, 2));
+  RC(h->alloc(&h->d_error, 1));
+  CK(cudaMemset(h->d_error, 0, sizeof(int)));
   RC(h->alloc(&h->d_P, n));
   RC(h->alloc(&h->d_c, n));
   RC(upload(h, &h->d_bdd_depth, L.bdd_depth));
@@ -358,6 +426,8 @@ void bdd_default_options(bdd_options *opt) {
   opt->host_only = 0;
   opt->device = -1;
   opt->stream = nullptr;
+  opt->schedule = 1;
+  opt->spin_limit = 1LL << 26;
 }
 
 int bdd_last_failed_row(void) { return g_failed_row; }
@@ -388,6 +458,12 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   h->m = m;
   h->nnz = nnz;
   h->omega = opt.omega;
+  h->schedule = opt.schedule;
+  h->spin_limit = opt.spin_limit;
+  if (opt.schedule < 0 || opt.schedule > 1 || opt.spin_limit < 1) {
+    delete h;
+    return BDD_EINVAL;
+  }
   if (opt.host_only < 0 || opt.host_only > 2) {
     delete h;
     return BDD_EINVAL;
@@ -483,18 +559,22 @@ int bdd_iterate_device(bdd_solver *h, int n_iter, double *d_bound_trace, float *
   if (!dg.ok) return BDD_ECUDA;
   cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
   RC(h->ensure_trace(n_iter + 1));
-  if (n_iter > 0) {
+  if (n_iter > 0 && h->schedule == 1) {
     if (!h->g_one) RC(h->capture(1, &h->g_one));
     if (!h->g_many && n_iter >= kGraphIters) RC(h->capture(kGraphIters, &h->g_many));
   }
   RC(h->begin(s));
-  CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
-  int left = n_iter;
-  while (left >= kGraphIters) {
-    CK(cudaGraphLaunch(h->g_many, s));
-    left -= kGraphIters;
+  if (h->schedule == 0) {
+    if (n_iter > 0) RC(h->launch_persistent(n_iter, s));
+  } else {
+    CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
+    int left = n_iter;
+    while (left >= kGraphIters) {
+      CK(cudaGraphLaunch(h->g_many, s));
+      left -= kGraphIters;
+    }
+    for (; left > 0; --left) CK(cudaGraphLaunch(h->g_one, s));
   }
-  for (; left > 0; --left) CK(cudaGraphLaunch(h->g_one, s));
   if (d_bound_trace && n_iter > 0)
     CK(cudaMemcpyAsync(d_bound_trace, h->d_trace, sizeof(double) * n_iter, cudaMemcpyDeviceToDevice, s));
   RC(h->output_pass(s, d_lambda, d_mm0, d_mm1));
@@ -523,11 +603,11 @@ int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms) {
       if (cudaEventRecord(e[0], s) != cudaSuccess) rc = BDD_ECUDA;
       if (rc == BDD_OK) rc = h->sweep(true, kUpdate, s);
       if (rc == BDD_OK && cudaEventRecord(e[1], s) != cudaSuccess) rc = BDD_ECUDA;
-      if (rc == BDD_OK) rc = h->reduce(true, false, s);
+      if (rc == BDD_OK) rc = h->pending(false, s);
       if (rc == BDD_OK && cudaEventRecord(e[2], s) != cudaSuccess) rc = BDD_ECUDA;
       if (rc == BDD_OK) rc = h->sweep(false, kUpdate, s);
       if (rc == BDD_OK && cudaEventRecord(e[3], s) != cudaSuccess) rc = BDD_ECUDA;
-      if (rc == BDD_OK) rc = h->reduce(true, true, s);
+      if (rc == BDD_OK) rc = h->pending(true, s);
       if (rc == BDD_OK && cudaEventRecord(e[4], s) != cudaSuccess) rc = BDD_ECUDA;
     }
     if (rc == BDD_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = BDD_ECUDA;
@@ -558,7 +638,7 @@ int bdd_iterate(bdd_solver *h, int n_iter, double *lower_bound, float *lambda, f
   RC(h->begin(s));
   if (lower_bound && n_iter == 0) {
     CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
-    RC(h->reduce(false, true, s));
+    RC(h->pending(true, s));
   }
   const size_t bytes = sizeof(float) * (size_t)h->nnz;
   if (lambda && bytes) CK(cudaMemcpyAsync(lambda, h->d_out_lam, bytes, cudaMemcpyDeviceToHost, s));
@@ -570,7 +650,7 @@ int bdd_iterate(bdd_solver *h, int n_iter, double *lower_bound, float *lambda, f
   }
   RC(h->end(s));
   CK(cudaStreamSynchronize(s));
-  return BDD_OK;
+  return h->take_device_error(s);
 }
 
 int bdd_set_costs(bdd_solver *h, const float *c) {
@@ -603,7 +683,7 @@ int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]) {
   out[8] = h->device_bytes;
   out[9] = h->n_warp_tiles;
   out[10] = h->n_block_tiles;
-  out[11] = h->host_only ? 0 : 4;
+  out[11] = h->schedule;
   return BDD_OK;
 }
 
@@ -690,8 +770,8 @@ int bdd_get_state(const bdd_solver *h_in, float *lambda, float *pending) {
   if (lambda) {
     RC(h->ensure_outputs());
     if (h->nnz) CK(cudaMemsetAsync(h->d_out_lam, 0, sizeof(float) * h->nnz, s));
-    if (h->O && scatter_lambda_launch(h->d_lam, h->d_share, h->d_occ_var, h->d_occ_csr, h->d_out_lam,
-                                      (int)h->O, false, s))
+    if (h->O && scatter_lambda_launch(h->d_lam, h->d_share_occ, h->d_occ_csr, h->d_out_lam, (int)h->O, false,
+                                      s))
       return BDD_ECUDA;
     if (h->nnz) CK(cudaMemcpyAsync(lambda, h->d_out_lam, sizeof(float) * h->nnz, cudaMemcpyDeviceToHost, s));
   }
@@ -716,7 +796,10 @@ int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending) {
       CK(cudaMemcpyAsync(h->d_P, pending, sizeof(float) * h->n, cudaMemcpyHostToDevice, s));
     else
       CK(cudaMemsetAsync(h->d_P, 0, sizeof(float) * h->n, s));
-    if (share_from_pending_launch(h->d_var_ptr, h->d_P, h->d_share, h->n, s)) return BDD_ECUDA;
+    // slots holding P_i in the first slot of i reproduce P exactly; the pending pass then writes
+    // the shares (and P again, unchanged)
+    if (pending_to_slots_launch(h->d_var_ptr, h->d_P, h->d_delta, h->n, s)) return BDD_ECUDA;
+    RC(h->pending(false, s));
   }
   RC(h->sweep(false, kMessages, s));
   RC(h->end(s));

@@ -332,8 +332,13 @@ int build_layout(const HostBDDs &H, Layout *L) {
   for (long long co = 0; co < O; ++co) L->var_ptr[H.occ_var[co] + 1]++;
   for (int i = 0; i < H.n; ++i) L->var_ptr[i + 1] += L->var_ptr[i];
   L->var_occ.assign(O, 0);
+  L->occ_slot.assign(O, 0);
   std::vector<int> fill(L->var_ptr.begin(), L->var_ptr.end() - 1);
-  for (long long co = 0; co < O; ++co) L->var_occ[fill[H.occ_var[co]]++] = L->occ_of_canon[co];
+  for (long long co = 0; co < O; ++co) {
+    const int k = fill[H.occ_var[co]]++, o = L->occ_of_canon[co];
+    L->var_occ[k] = o;
+    L->occ_slot[o] = k;
+  }
   return BDD_OK;
 }
 

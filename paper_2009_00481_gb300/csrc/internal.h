@@ -40,16 +40,37 @@ int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const i
 
 // Team classes of the sweep kernels.  Class c < kWarpClasses: a team of T = 1 << c lanes per
 // BDD (lane t holds node t of the current layer), 32 / T BDDs per warp ("warp tile").
-// Class kWarpClasses: one thread block per BDD ("block tile").
+// Class kWarpClasses: one 128-thread group per BDD ("block tile").
 constexpr int kWarpClasses = 6;
-constexpr int kBlockThreads = 128;
+constexpr int kBlockThreads = 128;                  // per-phase kernels; block-tile group size
 constexpr int kWarpsPerBlock = kBlockThreads / 32;
-constexpr int kMaxBlockTileWidth = 12288;  // two float layer buffers in shared memory
+constexpr int kPersistThreads = 512;                // persistent kernel: one block per SM
+constexpr int kPersistWarps = kPersistThreads / 32;
+constexpr int kSubBlocks = kPersistThreads / kBlockThreads;
+constexpr int kMaxBlockTileWidth = 12288;           // two float layer buffers in shared memory
+constexpr int kMaxBlockTileDepth = 8192;
+
+// Shared-memory stage of one warp: a window of kWinLayers layers of a warp tile (at most 32
+// occurrences and 32 nodes per layer), plus the node offsets and backward messages of the layer
+// after the window.
+constexpr int kWinLayers = 8;
+constexpr int kWinOcc = 32 * kWinLayers;
+constexpr int kWinNodes = 32 * kWinLayers;
+struct WarpStage {
+  int2 lohi[kWinNodes];
+  float msg[kWinNodes + 32];
+  int off[kWinOcc + 32 + 1];
+  float lam[kWinOcc];
+  float shr[kWinOcc];
+  int slot[kWinOcc];
+};
 
 // Device slab layout (host staging copy).  Occurrences are grouped by tile; inside a warp
 // tile they are layer-major (layer l of every tile BDD still alive at l, in tile order; the
 // tile's BDDs are sorted by depth, longest first, so the BDDs alive at l are a prefix).  Nodes
-// follow their occurrence.  Successors are global node indices or kTop / kBot.
+// follow their occurrence.  Successors are global node indices or kTop / kBot.  Recorded
+// differences live in variable-major "slots": slot k in [var_ptr[i], var_ptr[i+1]) belongs to
+// the occurrences of variable i in ascending row order.
 struct Layout {
   int n_sorted = 0;                    // BDDs in sorted (device) order
   std::vector<int> bdd_perm;           // sorted position -> canonical BDD index
@@ -57,13 +78,14 @@ struct Layout {
   std::vector<int> occ_node_off;       // [O+1]
   std::vector<int> occ_var;            // [O]
   std::vector<long long> occ_csr;      // [O]
+  std::vector<int> occ_slot;           // [O] slot of the occurrence
   std::vector<int> lohi;               // [2N] interleaved lo, hi
   std::vector<int> tile_occ0, tile_bdd0, tile_nbdd;  // per tile
   int class_tile_off[kWarpClasses + 2] = {0};        // tiles of class c: [off[c], off[c+1])
   int n_warp_tiles = 0, n_block_tiles = 0;
   int max_block_width = 0;
   std::vector<int> var_ptr;            // [n+1]
-  std::vector<int> var_occ;            // [O] device occurrence ids, ascending row per variable
+  std::vector<int> var_occ;            // [O] device occurrence of each slot
   std::vector<int> occ_of_canon;       // canonical occurrence -> device occurrence
 };
 
@@ -72,14 +94,14 @@ int build_layout(const HostBDDs &H, Layout *L);
 // Kernel parameter blocks (passed by value).
 struct SweepParams {
   const int *occ_node_off;
-  const int *occ_var;
   const long long *occ_csr;
   const int2 *lohi;
   float *fm;
   float *bm;
   float *lam;
-  float *delta;
-  const float *share;
+  const int *occ_slot;      // slot of each occurrence (variable-major)
+  float *delta;             // differences recorded by a sweep, by slot
+  const float *share_occ;   // pending share P_i / |J_i| of each occurrence's variable
   const int *bdd_depth;
   float *bdd_E;
   const int *tile_occ0;
@@ -89,25 +111,9 @@ struct SweepParams {
   float *out_m1;
   int class_tile_off[kWarpClasses + 2];
   int n_warp_blocks;
-  int block_buf;  // floats per shared-memory layer buffer of a block tile
+  int block_buf;        // floats per shared-memory layer buffer of a block tile
+  int block_depth_buf;  // floats for the per-layer shares of a block tile
   float omega;
-};
-
-struct ReduceParams {
-  const int *var_ptr;
-  const int *var_occ;
-  const float *delta;
-  float *P;
-  float *share;
-  const float *bdd_E;
-  double *partial;
-  unsigned int *ticket;
-  int *iter_ctr;
-  double *trace;
-  int trace_cap;
-  int n;
-  int nb;
-  double empty_const;
 };
 
 // Sweep modes.
@@ -117,17 +123,59 @@ enum SweepMode : int {
   kFolded = 2,   // messages and min-marginals at lambda + share, nothing stored but messages
 };
 
-// Launch wrappers (kernels.cu).  All enqueue on `stream` and return the launch status.
+// Pending pass: P_i = sum of i's slots, stored; share_i = P_i / |J_i| written to each of i's
+// occurrences; optionally the FP64 y-slack bound sum_j E^j + sum_i min(0, P_i) + empty_const,
+// reduced deterministically (per-block partials finished in block order by the last block)
+// into trace[*iter_ctr].
+struct PendingParams {
+  const int *var_ptr;
+  const int *var_occ;
+  const float *delta;
+  float *P;
+  float *share_occ;
+  const float *bdd_E;
+  double *partial;
+  unsigned *ticket;
+  int *iter_ctr;
+  double *trace;
+  int trace_cap;
+  int n;
+  int nb;
+  double empty_const;
+};
+
+// Persistent iteration kernel (one cooperative launch runs n_iter iterations).
+struct IterParams {
+  SweepParams sp;
+  const int *var_ptr;
+  const int *var_occ;
+  float *P;             // pending sums (state)
+  float *share_occ;     // shares written by the pending passes (sp.share_occ, writable)
+  double *part;         // [2][gridDim.x] bound partials: E^j parts, slack parts
+  unsigned *barrier;    // [2] arrival count, generation
+  int *error;           // set to BDD_ETIMEOUT if a barrier wait gives up
+  double *trace;
+  int trace_cap;
+  int n_iter;
+  int n;
+  double empty_const;
+  long long spin_limit;
+};
+
+// Launch wrappers (kernels.cu).  All enqueue on `stream` and return 0 or -5 (launch failure).
+size_t sweep_smem_bytes(int block_buf, int block_depth_buf);
+size_t persist_smem_bytes(int block_buf, int block_depth_buf);
+int sweep_set_smem(size_t bytes);
+int iterate_set_smem(size_t bytes);
 int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStream_t stream);
-int reduce_launch(bool recompute, bool bound, const ReduceParams &p, int grid, cudaStream_t stream);
+int pending_launch(bool bound, const PendingParams &p, int grid, cudaStream_t stream);
+int iterate_persistent_max_grid(size_t smem, int *grid);
+int iterate_persistent_launch(const IterParams &q, int grid, size_t smem, cudaStream_t stream);
 int init_lambda_launch(const int *occ_var, const int *var_ptr, const float *c, float *lam, int O,
                        cudaStream_t stream);
-int share_from_pending_launch(const int *var_ptr, const float *P, float *share, int n,
-                              cudaStream_t stream);
-int scatter_lambda_launch(const float *lam, const float *share, const int *occ_var,
-                          const long long *occ_csr, float *out, int O, bool fold,
-                          cudaStream_t stream);
-int sweep_set_smem(size_t bytes);
+int pending_to_slots_launch(const int *var_ptr, const float *P, float *delta_b, int n, cudaStream_t stream);
+int scatter_lambda_launch(const float *lam, const float *share_occ, const long long *occ_csr, float *out,
+                          int O, bool fold, cudaStream_t stream);
 int gather_lambda_launch(const float *in, const long long *occ_csr, float *lam, int O,
                          cudaStream_t stream);
 constexpr int kReduceThreads = 256;

@@ -1,21 +1,25 @@
-// Sweep, reduction and helper kernels for BDD min-marginal averaging on sm_103a.
+// Sweep, bound and helper kernels for BDD min-marginal averaging on sm_103a.
 //
-// One iteration = forward sweep, per-variable reduction, backward sweep, per-variable
-// reduction with the FP64 lower bound (Sec. 3.2 Alg. 1's forward and backward pass, in the
-// parallel-across-BDDs form: the averaging term of eq. mma-update is formed after a sweep and
-// applied, as share_i = P_i / |J_i|, when the next sweep visits the layer of variable i).
+// One iteration = forward sweep, then backward sweep (Sec. 3.2 Alg. 1's forward and backward
+// pass, in the parallel-across-BDDs form: every BDD runs its layers in order, all BDDs at
+// once; the averaging term of eq. mma-update is applied one sweep late).  Each occurrence
+// records its damped min-marginal difference in a variable-major slot; when the next sweep
+// visits the occurrence it adds share_i = (sum of the variable's slots) / |J_i|, which is the
+// pending sum P_i / |J_i| of the deferred schedule.
 //
-// Sweep kernels walk each BDD's layers in order inside one team of threads; there is no grid
-// synchronisation inside a sweep.  Messages of the current layer stay in registers (warp
-// teams: lane t of a team of T lanes holds node t; the forward step pushes along lo/hi arcs
-// with shuffles, the backward step pulls its successors' messages with one shuffle each) or in
-// shared memory (one block per BDD for layers wider than 32 nodes, forward step by shared-memory
-// atomic minimum).  Forward messages are written for the backward sweep and backward messages
-// for the next forward sweep (Prop. 3: every message stays valid for the layers not yet
-// revisited).
+// Sweeps walk each BDD's layers inside one team of threads with no grid synchronisation inside
+// a sweep.  Warp tiles stage windows of their contiguous slab in shared memory and keep the
+// current layer's messages in registers (lane t of a T-lane team holds node t; the forward step
+// pushes along lo/hi arcs with shuffles, the backward step pulls successors' messages with one
+// shuffle each).  Block tiles (layers wider than 32 nodes) keep two layer buffers in shared
+// memory (forward step by shared-memory atomic minimum).  Forward messages are written for the
+// backward sweep and backward messages for the next forward sweep (Prop. 3: every message
+// stays valid for the layers not yet revisited).
+//
+// Two schedules run this arithmetic: per-phase kernels (forward sweep, backward sweep, bound)
+// replayed from CUDA graphs, and one persistent cooperative kernel per call with two grid
+// barriers per iteration.
 #include <cuda_runtime.h>
-
-#include <cfloat>
 
 #include "internal.h"
 
@@ -30,6 +34,12 @@ __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
 // backward message of an arc target: top -> 0, bot / none -> +inf, node -> bm
 __device__ __forceinline__ float target_bm(const float *__restrict__ bm, int t) {
   if (t >= 0) return bm[t];
+  return t == kTop ? 0.f : inf();
+}
+
+// backward message of an arc target staged at msg[t - base]
+__device__ __forceinline__ float staged_bm(const float *msg, int base, int t) {
+  if (t >= 0) return msg[t - base];
   return t == kTop ? 0.f : inf();
 }
 
@@ -54,180 +64,311 @@ __device__ __forceinline__ float mm_difference(float m0, float m1) {
   return (m0 < inf() && m1 < inf()) ? m1 - m0 : 0.f;
 }
 
-// ---------------------------------------------------------------------------------------
-// warp tiles: T lanes per BDD, 32 / T BDDs per warp
-// ---------------------------------------------------------------------------------------
-template <int T, int MODE>
-__device__ void warp_forward(const SweepParams &p, int tile) {
-  const int lane = threadIdx.x & 31;
-  const int team = lane / T, tl = lane % T, tbase = team * T;
-  const int occ0 = p.tile_occ0[tile];
-  const int bdd = p.tile_bdd0[tile] + team;
-  const bool valid = team < p.tile_nbdd[tile];
-  const int depth = valid ? p.bdd_depth[bdd] : 0;
-  const int maxd = __reduce_max_sync(kFull, depth);
-  int cum = 0;
-  float f_prev = inf(), lam_prev = 0.f;
-  int2 lh_prev = make_int2(kNone, kNone);
-  for (int l = 0; l < maxd; ++l) {
-    const int alive = __popc(__ballot_sync(kFull, tl == 0 && depth > l));
-    const bool active = depth > l;
-    const int o = occ0 + cum + team;
-    int node0 = 0, w = 0;
-    if (active) {
-      node0 = p.occ_node_off[o];
-      w = p.occ_node_off[o + 1] - node0;
-    }
-    const bool has = active && tl < w;
-    // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv
-    float f;
-    if (l == 0) {
-      f = 0.f;
-    } else {
-      const int lo_l = lh_prev.x >= 0 ? lh_prev.x - node0 : kNone;
-      const int hi_l = lh_prev.y >= 0 ? lh_prev.y - node0 : kNone;
-      f = inf();
+// Asynchronous global -> shared copies (cp.async): a warp issues all copies of a stage back to
+// back and waits once, instead of one load round trip per element.  Data written by other
+// blocks of a persistent launch is read only after a grid barrier, whose fences order those
+// writes before these reads.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Programmatic dependent launch: the per-phase kernels are launched so that the next kernel of
+// the chain may start while this one drains; each kernel waits here for its predecessor to
+// complete (and its writes to be visible) before touching any data, and lets its own successor
+// start launching right away.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// barrier of the 128-thread group `group` (named barrier 1 + group; the per-phase kernel's
+// blocks are one such group)
+__device__ __forceinline__ void group_sync(int group) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "r"(kBlockThreads) : "memory");
+}
+
+// Where a sweep records its differences (variable-major slots).
+struct Phase {
+  float *delta;
+};
+
+// Sum of slots [s, e) in ascending order -- the one summation every pending sum uses.  Loads
+// go out eight at a time (independent, through L2: during a persistent launch the slots are
+// written by other blocks); the additions stay in slot order.
+__device__ __forceinline__ float slot_sum(const float *__restrict__ d, int s, int e) {
+  float P = 0.f;
+  for (int k = s; k < e; k += 8) {
+    float v[8];
 #pragma unroll
-      for (int s = 0; s < T; ++s) {
-        const float mf = __shfl_sync(kFull, f_prev, tbase + s);
-        const int ls = __shfl_sync(kFull, lo_l, tbase + s);
-        const int hs = __shfl_sync(kFull, hi_l, tbase + s);
-        if (ls == tl) f = fminf(f, mf);
-        if (hs == tl) f = fminf(f, mf + lam_prev);
-      }
-    }
-    int2 lh = make_int2(kNone, kNone);
-    if (has) {
-      p.fm[node0 + tl] = f;
-      lh = p.lohi[node0 + tl];
-    }
-    float lam = 0.f;
-    if (active) {
-      lam = p.lam[o];
-      if (MODE != kMessages) lam += p.share[p.occ_var[o]];
-    }
-    if (MODE == kUpdate) {
-      // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
-      const float a0 = has ? f + target_bm(p.bm, lh.x) : inf();
-      const float a1 = has ? f + lam + target_bm(p.bm, lh.y) : inf();
-      const float m0 = team_min<T>(a0), m1 = team_min<T>(a1);
-      const float dd = p.omega * mm_difference(m0, m1);
-      lam -= dd;
-      if (active && tl == 0) {
-        p.lam[o] = lam;
-        p.delta[o] = dd;
-      }
-    }
-    f_prev = f;
-    lh_prev = lh;
-    lam_prev = lam;
-    cum += alive;
+    for (int j = 0; j < 8; ++j) v[j] = k + j < e ? __ldcg(d + k + j) : 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k + j < e) P += v[j];
   }
+  return P;
+}
+
+// ---------------------------------------------------------------------------------------
+// warp tiles: T lanes per BDD, 32 / T BDDs per warp.  A tile's slab is contiguous and
+// layer-major, so a window of kWinLayers layers (<= 32 occurrences and <= 32 nodes per layer)
+// is one contiguous range of every array.  Each window is staged into the warp's shared memory
+// with independent coalesced loads before its layers are processed, so the layer recurrence
+// runs on shared memory and registers only.
+// ---------------------------------------------------------------------------------------
+// occurrences of the tile before layer l: sum over the tile's BDDs of min(depth, l)
+__device__ __forceinline__ int occ_before(int lead_depth, int l) {
+  return __reduce_add_sync(kFull, min(lead_depth, l));
+}
+
+template <int MODE>
+__device__ __forceinline__ void stage_occurrences(const SweepParams &p, const Phase &ph, WarpStage &S, int oa,
+                                                  int nob, int nox, double &bacc) {
+  const int lane = threadIdx.x & 31;
+  for (int k = lane; k <= nox; k += 32) cp_async4(&S.off[k], &p.occ_node_off[oa + k]);
+  for (int k = lane; k < nob; k += 32) {
+    cp_async4(&S.lam[k], &p.lam[oa + k]);
+    if (MODE != kMessages)
+      cp_async4(&S.shr[k], &p.share_occ[oa + k]);
+    else
+      S.shr[k] = 0.f;
+    if (MODE == kUpdate) cp_async4(&S.slot[k], &p.occ_slot[oa + k]);
+  }
+  cp_async_wait();
 }
 
 template <int T, int MODE>
-__device__ void warp_backward(const SweepParams &p, int tile) {
+__device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &ph, int tile, WarpStage &S,
+                                             double &bacc) {
   const int lane = threadIdx.x & 31;
   const int team = lane / T, tl = lane % T, tbase = team * T;
   const int occ0 = p.tile_occ0[tile];
   const int bdd = p.tile_bdd0[tile] + team;
   const bool valid = team < p.tile_nbdd[tile];
   const int depth = valid ? p.bdd_depth[bdd] : 0;
+  const int lead_depth = tl == 0 ? depth : 0;
   const int maxd = __reduce_max_sync(kFull, depth);
-  const int total = __reduce_add_sync(kFull, tl == 0 ? depth : 0);
-  int cum_ge = 0;
-  float b_next = inf();
-  int node0_next = 0;
-  for (int l = maxd - 1; l >= 0; --l) {
-    cum_ge += __popc(__ballot_sync(kFull, tl == 0 && depth > l));
-    const bool active = depth > l;
-    const int o = occ0 + total - cum_ge + team;
-    int node0 = 0, w = 0;
-    if (active) {
-      node0 = p.occ_node_off[o];
-      w = p.occ_node_off[o + 1] - node0;
+  float f_prev = inf(), lam_prev = 0.f;
+  int2 lh_prev = make_int2(kNone, kNone);
+  for (int l0 = 0; l0 < maxd; l0 += kWinLayers) {
+    const int l1 = min(l0 + kWinLayers, maxd);
+    const int ca = occ_before(lead_depth, l0), cb = occ_before(lead_depth, l1);
+    const int cx = l1 < maxd ? occ_before(lead_depth, l1 + 1) : cb;
+    const int oa = occ0 + ca, nob = cb - ca, nox = cx - ca;
+    __syncwarp();  // the previous window is no longer read
+    stage_occurrences<MODE>(p, ph, S, oa, nob, nox, bacc);
+    __syncwarp();
+    const int na = S.off[0], nb = S.off[nob];
+    for (int k = lane; k < nb - na; k += 32) cp_async8(&S.lohi[k], &p.lohi[na + k]);
+    if (MODE == kUpdate) {
+      const int nc = S.off[nox];  // through the layer after the window: the arcs' targets
+      for (int k = lane; k < nc - na; k += 32) cp_async4(&S.msg[k], &p.bm[na + k]);
     }
-    const bool has = active && tl < w;
-    int2 lh = make_int2(kNone, kNone);
-    float f = inf();
-    if (has) {
-      lh = p.lohi[node0 + tl];
-      f = p.fm[node0 + tl];
-    }
-    float lam = 0.f;
-    if (active) {
-      lam = p.lam[o];
-      if (MODE != kMessages) lam += p.share[p.occ_var[o]];
-    }
-    // successors' backward messages live on the lanes of this team (layer l + 1)
-    const int s0 = lh.x >= 0 ? lh.x - node0_next : 0;
-    const int s1 = lh.y >= 0 ? lh.y - node0_next : 0;
-    const float g0 = __shfl_sync(kFull, b_next, tbase + (s0 & (T - 1)));
-    const float g1 = __shfl_sync(kFull, b_next, tbase + (s1 & (T - 1)));
-    const float b0 = lh.x >= 0 ? g0 : (lh.x == kTop ? 0.f : inf());
-    const float b1 = lh.y >= 0 ? g1 : (lh.y == kTop ? 0.f : inf());
-    if (MODE != kMessages) {
-      const float m0 = team_min<T>(f + b0), m1 = team_min<T>(f + lam + b1);
+    cp_async_wait();
+    __syncwarp();
+    for (int l = l0; l < l1; ++l) {
+      const bool active = depth > l;
+      const int oi = occ_before(lead_depth, l) - ca + team;
+      int node0 = 0, w = 0;
+      if (active) {
+        node0 = S.off[oi];
+        w = S.off[oi + 1] - node0;
+      }
+      const bool has = active && tl < w;
+      // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv
+      float f;
+      if (l == 0) {
+        f = 0.f;
+      } else {
+        const int lo_l = lh_prev.x >= 0 ? lh_prev.x - node0 : kNone;
+        const int hi_l = lh_prev.y >= 0 ? lh_prev.y - node0 : kNone;
+        f = inf();
+#pragma unroll
+        for (int s = 0; s < T; ++s) {
+          const float mf = __shfl_sync(kFull, f_prev, tbase + s);
+          const int ls = __shfl_sync(kFull, lo_l, tbase + s);
+          const int hs = __shfl_sync(kFull, hi_l, tbase + s);
+          if (ls == tl) f = fminf(f, mf);
+          if (hs == tl) f = fminf(f, mf + lam_prev);
+        }
+      }
+      int2 lh = make_int2(kNone, kNone);
+      if (has) {
+        p.fm[node0 + tl] = f;
+        lh = S.lohi[node0 - na + tl];
+      }
+      float lam = active ? S.lam[oi] + S.shr[oi] : 0.f;
       if (MODE == kUpdate) {
+        // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
+        const float a0 = has ? f + staged_bm(S.msg, na, lh.x) : inf();
+        const float a1 = has ? f + lam + staged_bm(S.msg, na, lh.y) : inf();
+        const float m0 = team_min<T>(a0), m1 = team_min<T>(a1);
         const float dd = p.omega * mm_difference(m0, m1);
         lam -= dd;
         if (active && tl == 0) {
-          p.lam[o] = lam;
-          p.delta[o] = dd;
+          p.lam[oa + oi] = lam;
+          ph.delta[S.slot[oi]] = dd;
         }
-      } else if (active && tl == 0 && p.out_m0) {
-        const long long c = p.occ_csr[o];
-        p.out_m0[c] = m0;
-        p.out_m1[c] = m1;
       }
+      f_prev = f;
+      lh_prev = lh;
+      lam_prev = lam;
     }
-    // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
-    const float bcur = fminf(b0, lam + b1);
-    if (has) p.bm[node0 + tl] = bcur;
-    if (l == 0 && active && tl == 0) p.bdd_E[bdd] = bcur;  // E^j(lambda^j) at the root
-    b_next = bcur;
-    node0_next = node0;
+  }
+}
+
+template <int T, int MODE>
+__device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase &ph, int tile, WarpStage &S,
+                                              double &bacc) {
+  const int lane = threadIdx.x & 31;
+  const int team = lane / T, tl = lane % T, tbase = team * T;
+  const int occ0 = p.tile_occ0[tile];
+  const int bdd = p.tile_bdd0[tile] + team;
+  const bool valid = team < p.tile_nbdd[tile];
+  const int depth = valid ? p.bdd_depth[bdd] : 0;
+  const int lead_depth = tl == 0 ? depth : 0;
+  const int maxd = __reduce_max_sync(kFull, depth);
+  float b_next = inf();
+  int node0_next = 0;
+  for (int l0 = ((maxd - 1) / kWinLayers) * kWinLayers; l0 >= 0; l0 -= kWinLayers) {
+    const int l1 = min(l0 + kWinLayers, maxd);
+    const int ca = occ_before(lead_depth, l0), cb = occ_before(lead_depth, l1);
+    const int oa = occ0 + ca, nob = cb - ca;
+    __syncwarp();
+    stage_occurrences<MODE>(p, ph, S, oa, nob, nob, bacc);
+    __syncwarp();
+    const int na = S.off[0], nb = S.off[nob];
+    for (int k = lane; k < nb - na; k += 32) {
+      cp_async8(&S.lohi[k], &p.lohi[na + k]);
+      cp_async4(&S.msg[k], &p.fm[na + k]);
+    }
+    cp_async_wait();
+    __syncwarp();
+    for (int l = l1 - 1; l >= l0; --l) {
+      const bool active = depth > l;
+      const int oi = occ_before(lead_depth, l) - ca + team;
+      int node0 = 0, w = 0;
+      if (active) {
+        node0 = S.off[oi];
+        w = S.off[oi + 1] - node0;
+      }
+      const bool has = active && tl < w;
+      int2 lh = make_int2(kNone, kNone);
+      float f = inf();
+      if (has) {
+        lh = S.lohi[node0 - na + tl];
+        f = S.msg[node0 - na + tl];
+      }
+      float lam = active ? S.lam[oi] + S.shr[oi] : 0.f;
+      // successors' backward messages live on the lanes of this team (layer l + 1)
+      const int s0 = lh.x >= 0 ? lh.x - node0_next : 0;
+      const int s1 = lh.y >= 0 ? lh.y - node0_next : 0;
+      const float g0 = __shfl_sync(kFull, b_next, tbase + (s0 & (T - 1)));
+      const float g1 = __shfl_sync(kFull, b_next, tbase + (s1 & (T - 1)));
+      const float b0 = lh.x >= 0 ? g0 : (lh.x == kTop ? 0.f : inf());
+      const float b1 = lh.y >= 0 ? g1 : (lh.y == kTop ? 0.f : inf());
+      if (MODE != kMessages) {
+        const float m0 = team_min<T>(f + b0), m1 = team_min<T>(f + lam + b1);
+        if (MODE == kUpdate) {
+          const float dd = p.omega * mm_difference(m0, m1);
+          lam -= dd;
+          if (active && tl == 0) {
+            p.lam[oa + oi] = lam;
+            ph.delta[S.slot[oi]] = dd;
+          }
+        } else if (active && tl == 0 && p.out_m0) {
+          const long long c = p.occ_csr[oa + oi];
+          p.out_m0[c] = m0;
+          p.out_m1[c] = m1;
+        }
+      }
+      // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
+      const float bcur = fminf(b0, lam + b1);
+      if (has) p.bm[node0 + tl] = bcur;
+      if (l == 0 && active && tl == 0) {  // E^j(lambda^j) at the root
+        p.bdd_E[bdd] = bcur;
+        bacc += (double)bcur;
+      }
+      b_next = bcur;
+      node0_next = node0;
+    }
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// block tiles: one block per BDD (layers wider than 32 nodes)
+// block tiles: one 128-thread group per BDD (layers wider than 32 nodes).  `group` selects the
+// named barrier; `gt` is the thread's index inside its group.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ float2 block_min2(float a, float b, float2 *red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+struct GroupSmem {
+  float2 *red;  // [kWarpsPerBlock]
+  float *bufA, *bufB, *shr;
+};
+
+__host__ __device__ __forceinline__ size_t group_floats(int block_buf, int block_depth_buf) {
+  return 2 * kWarpsPerBlock + 2 * (size_t)block_buf + block_depth_buf;
+}
+
+__device__ __forceinline__ GroupSmem group_smem(float *base, const SweepParams &p) {
+  GroupSmem g;
+  g.red = reinterpret_cast<float2 *>(base);
+  g.bufA = base + 2 * kWarpsPerBlock;
+  g.bufB = g.bufA + p.block_buf;
+  g.shr = g.bufB + p.block_buf;
+  return g;
+}
+
+__device__ __forceinline__ float2 group_min2(float a, float b, float2 *red, int group, int gt) {
+  const int lane = gt & 31, warp = gt >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     a = fminf(a, __shfl_xor_sync(kFull, a, off));
     b = fminf(b, __shfl_xor_sync(kFull, b, off));
   }
   if (lane == 0) red[warp] = make_float2(a, b);
-  __syncthreads();
+  group_sync(group);
   float2 r = red[0];
 #pragma unroll
   for (int t = 1; t < kWarpsPerBlock; ++t) {
     r.x = fminf(r.x, red[t].x);
     r.y = fminf(r.y, red[t].y);
   }
-  __syncthreads();  // red may be reused right after
+  group_sync(group);  // red may be reused right after
   return r;
 }
 
+// per-layer shares of a block tile, staged before its layers are processed
 template <int MODE>
-__device__ void block_forward(const SweepParams &p, int tile, float *bufA, float *bufB,
-                              float2 *red) {
+__device__ __forceinline__ void stage_group_shares(const SweepParams &p, int occ0, int depth, float *shr, int gt) {
+  for (int l = gt; l < depth; l += kBlockThreads) {
+    if (MODE != kMessages)
+      cp_async4(&shr[l], &p.share_occ[occ0 + l]);
+    else
+      shr[l] = 0.f;
+  }
+  cp_async_wait();
+}
+
+template <int MODE>
+__device__ __forceinline__ void block_forward(const SweepParams &p, const Phase &ph, int tile, const GroupSmem &g,
+                                              int group, int gt, double &bacc) {
   const int bdd = p.tile_bdd0[tile];
   const int occ0 = p.tile_occ0[tile];
   const int depth = p.bdd_depth[bdd];
-  float *cur = bufA, *nxt = bufB;
-  if (threadIdx.x == 0) cur[0] = 0.f;
-  __syncthreads();
+  float *cur = g.bufA, *nxt = g.bufB;
+  stage_group_shares<MODE>(p, occ0, depth, g.shr, gt);
+  if (gt == 0) cur[0] = 0.f;
+  group_sync(group);
   for (int l = 0; l < depth; ++l) {
     const int o = occ0 + l;
     const int node0 = p.occ_node_off[o], w = p.occ_node_off[o + 1] - node0;
-    float lam = p.lam[o];
-    if (MODE != kMessages) lam += p.share[p.occ_var[o]];
+    float lam = p.lam[o] + g.shr[l];
     float a0 = inf(), a1 = inf();
-    for (int t = threadIdx.x; t < w; t += kBlockThreads) {
+    for (int t = gt; t < w; t += kBlockThreads) {
       const float f = cur[t];
       p.fm[node0 + t] = f;
       if (MODE == kUpdate) {
@@ -237,25 +378,25 @@ __device__ void block_forward(const SweepParams &p, int tile, float *bufA, float
       }
     }
     if (MODE == kUpdate) {
-      const float2 mm = block_min2(a0, a1, red);
+      const float2 mm = group_min2(a0, a1, g.red, group, gt);
       const float dd = p.omega * mm_difference(mm.x, mm.y);
       lam -= dd;
-      if (threadIdx.x == 0) {
+      if (gt == 0) {
         p.lam[o] = lam;
-        p.delta[o] = dd;
+        ph.delta[p.occ_slot[o]] = dd;
       }
     }
     if (l + 1 < depth) {
       const int next0 = node0 + w, wn = p.occ_node_off[o + 2] - next0;
-      for (int t = threadIdx.x; t < wn; t += kBlockThreads) nxt[t] = inf();
-      __syncthreads();
-      for (int t = threadIdx.x; t < w; t += kBlockThreads) {
+      for (int t = gt; t < wn; t += kBlockThreads) nxt[t] = inf();
+      group_sync(group);
+      for (int t = gt; t < w; t += kBlockThreads) {
         const float f = cur[t];
         const int2 lh = p.lohi[node0 + t];
         if (lh.x >= 0) atomic_min_f(&nxt[lh.x - next0], f);
         if (lh.y >= 0) atomic_min_f(&nxt[lh.y - next0], f + lam);
       }
-      __syncthreads();
+      group_sync(group);
       float *tmp = cur;
       cur = nxt;
       nxt = tmp;
@@ -264,21 +405,22 @@ __device__ void block_forward(const SweepParams &p, int tile, float *bufA, float
 }
 
 template <int MODE>
-__device__ void block_backward(const SweepParams &p, int tile, float *bufA, float *bufB,
-                               float2 *red) {
+__device__ __forceinline__ void block_backward(const SweepParams &p, const Phase &ph, int tile, const GroupSmem &g,
+                                               int group, int gt, double &bacc) {
   const int bdd = p.tile_bdd0[tile];
   const int occ0 = p.tile_occ0[tile];
   const int depth = p.bdd_depth[bdd];
-  float *cur = bufA, *nxt = bufB;  // cur: backward messages of layer l + 1
+  float *cur = g.bufA, *nxt = g.bufB;  // cur: backward messages of layer l + 1
+  stage_group_shares<MODE>(p, occ0, depth, g.shr, gt);
+  group_sync(group);
   for (int l = depth - 1; l >= 0; --l) {
     const int o = occ0 + l;
     const int node0 = p.occ_node_off[o], w = p.occ_node_off[o + 1] - node0;
     const int next0 = node0 + w;
-    float lam = p.lam[o];
-    if (MODE != kMessages) lam += p.share[p.occ_var[o]];
+    float lam = p.lam[o] + g.shr[l];
     if (MODE != kMessages) {
       float a0 = inf(), a1 = inf();
-      for (int t = threadIdx.x; t < w; t += kBlockThreads) {
+      for (int t = gt; t < w; t += kBlockThreads) {
         const int2 lh = p.lohi[node0 + t];
         const float f = p.fm[node0 + t];
         const float b0 = lh.x >= 0 ? cur[lh.x - next0] : (lh.x == kTop ? 0.f : inf());
@@ -286,132 +428,285 @@ __device__ void block_backward(const SweepParams &p, int tile, float *bufA, floa
         a0 = fminf(a0, f + b0);
         a1 = fminf(a1, f + lam + b1);
       }
-      const float2 mm = block_min2(a0, a1, red);
+      const float2 mm = group_min2(a0, a1, g.red, group, gt);
       if (MODE == kUpdate) {
         const float dd = p.omega * mm_difference(mm.x, mm.y);
         lam -= dd;
-        if (threadIdx.x == 0) {
+        if (gt == 0) {
           p.lam[o] = lam;
-          p.delta[o] = dd;
+          ph.delta[p.occ_slot[o]] = dd;
         }
-      } else if (threadIdx.x == 0 && p.out_m0) {
+      } else if (gt == 0 && p.out_m0) {
         const long long c = p.occ_csr[o];
         p.out_m0[c] = mm.x;
         p.out_m1[c] = mm.y;
       }
     }
-    for (int t = threadIdx.x; t < w; t += kBlockThreads) {
+    for (int t = gt; t < w; t += kBlockThreads) {
       const int2 lh = p.lohi[node0 + t];
       const float b0 = lh.x >= 0 ? cur[lh.x - next0] : (lh.x == kTop ? 0.f : inf());
       const float b1 = lh.y >= 0 ? cur[lh.y - next0] : (lh.y == kTop ? 0.f : inf());
       const float bcur = fminf(b0, lam + b1);
       p.bm[node0 + t] = bcur;
       nxt[t] = bcur;
-      if (l == 0 && t == 0) p.bdd_E[bdd] = bcur;
+      if (l == 0 && t == 0) {
+        p.bdd_E[bdd] = bcur;
+        bacc += (double)bcur;
+      }
     }
-    __syncthreads();
+    group_sync(group);
     float *tmp = cur;
     cur = nxt;
     nxt = tmp;
   }
 }
 
-}  // namespace
-
-// ---------------------------------------------------------------------------------------
-// kernels
-// ---------------------------------------------------------------------------------------
 template <bool FWD, int MODE>
-__global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams p) {
-  extern __shared__ float smem[];
-  if ((int)blockIdx.x < p.n_warp_blocks) {
-    const int tile = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (tile >= p.class_tile_off[kWarpClasses]) return;  // whole warp leaves together
-    int c = 0;
-    while (tile >= p.class_tile_off[c + 1]) ++c;
-    switch (c) {
+__device__ __forceinline__ void warp_tile(const SweepParams &p, const Phase &ph, int tile, WarpStage &S,
+                                          double &bacc) {
+  int c = 0;
+  while (tile >= p.class_tile_off[c + 1]) ++c;
+  switch (c) {
 #define BDD_TEAM_CASE(C, T)                                   \
   case C:                                                     \
-    if (FWD) warp_forward<T, MODE>(p, tile);                  \
-    else warp_backward<T, MODE>(p, tile);                     \
+    if (FWD) warp_forward<T, MODE>(p, ph, tile, S, bacc);     \
+    else warp_backward<T, MODE>(p, ph, tile, S, bacc);        \
     break;
-      BDD_TEAM_CASE(0, 1)
-      BDD_TEAM_CASE(1, 2)
-      BDD_TEAM_CASE(2, 4)
-      BDD_TEAM_CASE(3, 8)
-      BDD_TEAM_CASE(4, 16)
-      BDD_TEAM_CASE(5, 32)
+    BDD_TEAM_CASE(0, 1)
+    BDD_TEAM_CASE(1, 2)
+    BDD_TEAM_CASE(2, 4)
+    BDD_TEAM_CASE(3, 8)
+    BDD_TEAM_CASE(4, 16)
+    BDD_TEAM_CASE(5, 32)
 #undef BDD_TEAM_CASE
-      default:
-        break;
-    }
-  } else {
-    const int tile = p.class_tile_off[kWarpClasses] + (blockIdx.x - p.n_warp_blocks);
-    if (tile >= p.class_tile_off[kWarpClasses + 1]) return;  // uniform across the block
-    float2 *red = reinterpret_cast<float2 *>(smem);
-    float *bufA = smem + 2 * kWarpsPerBlock;
-    float *bufB = bufA + p.block_buf;
-    if (FWD)
-      block_forward<MODE>(p, tile, bufA, bufB, red);
-    else
-      block_backward<MODE>(p, tile, bufA, bufB, red);
+    default:
+      break;
   }
 }
 
-// Per-variable reduction (the sum in eq. mma-update, deferred): P_i = sum of the recorded
-// differences of i's occurrences in ascending row order, share_i = P_i / |J_i|.  With `bound`,
-// also the FP64 y-slack lower bound sum_j E^j + sum_i min(0, P_i) (+ the constant of variables
-// in no row), reduced deterministically: per-block partials, summed in block order by the last
-// block to finish, written to trace[*iter_ctr].
-template <bool RECOMPUTE, bool BOUND>
-__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const ReduceParams p) {
-  const int range = p.n > p.nb ? p.n : p.nb;
+__device__ __forceinline__ double block_sum(double v, double *red, int nwarps) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nwarps; ++w) s += red[w];
+  __syncthreads();
+  return s;  // on thread 0
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// per-phase kernels
+// ---------------------------------------------------------------------------------------
+template <bool FWD, int MODE>
+__global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams p) {
+  extern __shared__ __align__(16) float smem[];
+  pdl_enter();
+  const Phase ph{p.delta};
+  double bacc = 0.0;
+  if ((int)blockIdx.x < p.n_warp_blocks) {
+    const int tile = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (tile >= p.class_tile_off[kWarpClasses]) return;  // whole warp leaves together
+    warp_tile<FWD, MODE>(p, ph, tile, reinterpret_cast<WarpStage *>(smem)[threadIdx.x >> 5], bacc);
+  } else {
+    const int tile = p.class_tile_off[kWarpClasses] + (blockIdx.x - p.n_warp_blocks);
+    if (tile >= p.class_tile_off[kWarpClasses + 1]) return;  // uniform across the block
+    const GroupSmem g = group_smem(smem, p);
+    if (FWD)
+      block_forward<MODE>(p, ph, tile, g, 0, threadIdx.x, bacc);
+    else
+      block_backward<MODE>(p, ph, tile, g, 0, threadIdx.x, bacc);
+  }
+}
+
+// Pending sums (the sum in eq. mma-update, deferred): P_i = sum of i's slots in ascending
+// order, stored, and share_i = P_i / |J_i| written to each of i's occurrences for the next sweep.
+__device__ __forceinline__ float pending_var(const float *__restrict__ delta, const int *__restrict__ var_ptr,
+                                             const int *__restrict__ var_occ, float *__restrict__ P,
+                                             float *__restrict__ share_occ, int i, bool &has) {
+  const int s = var_ptr[i], e = var_ptr[i + 1];
+  has = e > s;
+  if (!has) return 0.f;
+  const float Pi = slot_sum(delta, s, e);
+  P[i] = Pi;
+  const float share = Pi / (float)(e - s);
+  for (int k = s; k < e; k += 8) {  // occurrence ids eight at a time, then the stores
+    int o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o[j] = k + j < e ? var_occ[k + j] : -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (o[j] >= 0) share_occ[o[j]] = share;
+  }
+  return Pi;
+}
+
+// With `bound`, also the FP64 y-slack lower bound sum_j E^j + sum_i min(0, P_i) (+ the constant
+// of variables in no row): per-block partials summed in a fixed order by the last block to
+// finish, written to trace[*iter_ctr].
+template <bool BOUND>
+__global__ void __launch_bounds__(kReduceThreads) pending_kernel(const PendingParams p) {
+  pdl_enter();
+  const int range = BOUND ? (p.n > p.nb ? p.n : p.nb) : p.n;
   double acc = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < range; i += gridDim.x * blockDim.x) {
     if (i < p.n) {
-      const int s = p.var_ptr[i], e = p.var_ptr[i + 1];
-      float P;
-      if (RECOMPUTE) {
-        P = 0.f;
-        for (int k = s; k < e; ++k) P += p.delta[p.var_occ[k]];
-        p.P[i] = P;
-        p.share[i] = e > s ? P / (float)(e - s) : 0.f;
-      } else {
-        P = p.P[i];
-      }
-      if (BOUND && e > s && P < 0.f) acc += (double)P;
+      bool has;
+      const float Pi = pending_var(p.delta, p.var_ptr, p.var_occ, p.P, p.share_occ, i, has);
+      if (BOUND && has && Pi < 0.f) acc += (double)Pi;
     }
     if (BOUND && i < p.nb) acc += (double)p.bdd_E[i];
   }
   if constexpr (BOUND) {
     __shared__ double red[kReduceThreads / 32];
     __shared__ bool last;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
+    const double blk = block_sum(acc, red, kReduceThreads / 32);
     if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int t = 0; t < kReduceThreads / 32; ++t) s += red[t];
-      p.partial[blockIdx.x] = s;
+      p.partial[blockIdx.x] = blk;
       __threadfence();
-      const unsigned ticket = atomicAdd(p.ticket, 1u);
-      last = ticket == gridDim.x - 1;
+      last = atomicAdd(p.ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {
       __threadfence();
-      double s = p.empty_const;
-      const volatile double *part = p.partial;
-      for (unsigned t = 0; t < gridDim.x; ++t) s += part[t];
-      const int it = *p.iter_ctr;
-      if (it < p.trace_cap) p.trace[it] = s;
-      *p.iter_ctr = it + 1;
-      *p.ticket = 0u;
+      double s = 0.0;
+      for (unsigned t = threadIdx.x; t < gridDim.x; t += blockDim.x) s += __ldcg(&p.partial[t]);
+      s = block_sum(s, red, kReduceThreads / 32);
+      if (threadIdx.x == 0) {
+        const int it = *p.iter_ctr;
+        if (it < p.trace_cap) p.trace[it] = s + p.empty_const;
+        *p.iter_ctr = it + 1;
+        *p.ticket = 0u;
+      }
     }
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// persistent iteration kernel: one cooperative launch runs n_iter iterations, each a forward
+// phase and a backward phase separated by grid barriers; one 512-thread block per SM.  Every
+// tile is owned by the same warp (or 128-thread group) in every phase, so its multipliers and
+// messages never move between SMs; the only data crossing blocks within the launch are the
+// recorded differences (read through L2) and the bound partials.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+// Grid-wide barrier (all blocks are resident: cooperative launch).  The wait is bounded: after
+// spin_limit polls, or once another block has failed, the block records BDD_ETIMEOUT (-6) and
+// every later barrier returns false at once, so the kernel always finishes.
+__device__ bool grid_barrier(const IterParams &q, bool &failed) {
+  __shared__ int s_fail;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int f = failed ? 1 : 0;
+    if (!f) {
+      volatile unsigned *gen = q.barrier + 1;
+      volatile int *err = q.error;
+      const unsigned g = *gen;
+      __threadfence();
+      if (atomicAdd(q.barrier, 1u) == gridDim.x - 1) {
+        atomicExch(q.barrier, 0u);
+        __threadfence();
+        atomicAdd(q.barrier + 1, 1u);
+      } else {
+        long long spins = 0;
+        while (*gen == g) {
+          if (*err != 0 || ++spins > q.spin_limit) {
+            f = 1;
+            atomicExch(q.error, -6);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
+    s_fail = f;
+  }
+  __syncthreads();
+  failed = s_fail != 0;
+  return !failed;
+}
+
+template <bool FWD>
+__device__ __forceinline__ void persistent_phase(const SweepParams &p, float *smem, double &bacc) {
+  const Phase ph{p.delta};
+  const int warp = threadIdx.x >> 5;
+  const int W = gridDim.x * kPersistWarps;
+  const int nwt = p.class_tile_off[kWarpClasses];
+  WarpStage &S = reinterpret_cast<WarpStage *>(smem)[warp];
+  for (int tile = blockIdx.x * kPersistWarps + warp; tile < nwt; tile += W)
+    warp_tile<FWD, kUpdate>(p, ph, tile, S, bacc);
+  const int bt0 = p.class_tile_off[kWarpClasses];
+  const int nbt = p.class_tile_off[kWarpClasses + 1] - bt0;
+  if (nbt > 0) {
+    __syncthreads();  // the warps' stages are reused as group buffers
+    const int group = threadIdx.x / kBlockThreads, gt = threadIdx.x % kBlockThreads;
+    const GroupSmem g = group_smem(smem + group * group_floats(p.block_buf, p.block_depth_buf), p);
+    for (int t = blockIdx.x * kSubBlocks + group; t < nbt; t += gridDim.x * kSubBlocks) {
+      if (FWD)
+        block_forward<kUpdate>(p, ph, bt0 + t, g, group, gt, bacc);
+      else
+        block_backward<kUpdate>(p, ph, bt0 + t, g, group, gt, bacc);
+      group_sync(group);
+    }
+  }
+}
+
+// pending sums and shares of a grid-stride range of variables; returns sum of min(0, P_i)
+__device__ __forceinline__ double persistent_pending(const IterParams &q) {
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q.n; i += gridDim.x * blockDim.x) {
+    bool has;
+    const float Pi = pending_var(q.sp.delta, q.var_ptr, q.var_occ, q.P, q.share_occ, i, has);
+    if (has && Pi < 0.f) acc += (double)Pi;
+  }
+  return acc;
+}
+
+// trace[it] = sum over blocks (in block order) of the E^j partials and the slack partials of
+// iteration it, plus the constant of variables in no row (block 0)
+__device__ void finalize_bound(const IterParams &q, int it, double *red) {
+  const int G = gridDim.x;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) v += __ldcg(q.part + b) + __ldcg(q.part + G + b);
+  const double s = block_sum(v, red, kPersistWarps);
+  if (threadIdx.x == 0 && it < q.trace_cap) q.trace[it] = s + q.empty_const;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kPersistThreads, 1) iterate_kernel(const IterParams q) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ double red[kPersistWarps];
+  const SweepParams &p = q.sp;
+  const int G = gridDim.x;
+  bool failed = false;
+  for (int it = 0; it < q.n_iter; ++it) {
+    double bacc = 0.0;
+    persistent_phase<true>(p, smem, bacc);
+    if (blockIdx.x == 0 && it > 0) finalize_bound(q, it - 1, red);  // partials of it-1 are final
+    if (!grid_barrier(q, failed)) return;
+    persistent_pending(q);
+    if (!grid_barrier(q, failed)) return;
+    bacc = 0.0;
+    persistent_phase<false>(p, smem, bacc);
+    double sum = block_sum(bacc, red, kPersistWarps);
+    if (threadIdx.x == 0) q.part[blockIdx.x] = sum;  // E^j part
+    if (!grid_barrier(q, failed)) return;
+    sum = block_sum(persistent_pending(q), red, kPersistWarps);
+    if (threadIdx.x == 0) q.part[G + blockIdx.x] = sum;  // slack part
+    if (!grid_barrier(q, failed)) return;
+  }
+  if (blockIdx.x == 0 && q.n_iter > 0) finalize_bound(q, q.n_iter - 1, red);
+}
+
+// ---------------------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------------------
 // lambda^j_i = c_i / |J_i| (Alg. 1 initialisation)
 __global__ void init_lambda_kernel(const int *__restrict__ occ_var, const int *__restrict__ var_ptr,
                                    const float *__restrict__ c, float *__restrict__ lam, int O) {
@@ -421,20 +716,21 @@ __global__ void init_lambda_kernel(const int *__restrict__ occ_var, const int *_
   }
 }
 
-__global__ void share_kernel(const int *__restrict__ var_ptr, const float *__restrict__ P,
-                             float *__restrict__ share, int n) {
+// pending sums as slot contents: P_i in the first slot of i, 0 in the others (so the slots
+// sum to P_i exactly)
+__global__ void pending_to_slots_kernel(const int *__restrict__ var_ptr, const float *__restrict__ P,
+                                        float *__restrict__ delta_b, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int d = var_ptr[i + 1] - var_ptr[i];
-    share[i] = d > 0 ? P[i] / (float)d : 0.f;
+    const int s = var_ptr[i], e = var_ptr[i + 1];
+    for (int k = s; k < e; ++k) delta_b[k] = k == s ? P[i] : 0.f;
   }
 }
 
-__global__ void scatter_lambda_kernel(const float *__restrict__ lam, const float *__restrict__ share,
-                                      const int *__restrict__ occ_var,
-                                      const long long *__restrict__ occ_csr, float *__restrict__ out,
-                                      int O, bool fold) {
+__global__ void scatter_lambda_kernel(const float *__restrict__ lam, const float *__restrict__ share_occ,
+                                      const long long *__restrict__ occ_csr, float *__restrict__ out, int O,
+                                      bool fold) {
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < O; o += gridDim.x * blockDim.x)
-    out[occ_csr[o]] = lam[o] + (fold ? share[occ_var[o]] : 0.f);
+    out[occ_csr[o]] = lam[o] + (fold ? share_occ[o] : 0.f);
 }
 
 __global__ void gather_lambda_kernel(const float *__restrict__ in, const long long *__restrict__ occ_csr,
@@ -454,12 +750,40 @@ int grid_for(long long work, int threads) {
   return (int)g;
 }
 int status() { return cudaGetLastError() == cudaSuccess ? 0 : -5; }
+
+template <typename... Args>
+int launch_pdl(void (*kernel)(Args...), int grid, int block, size_t smem, cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...) == cudaSuccess ? 0 : -5;
+}
 }  // namespace
+
+size_t sweep_smem_bytes(int block_buf, int block_depth_buf) {
+  const size_t warp_part = kWarpsPerBlock * sizeof(WarpStage);
+  const size_t group_part = group_floats(block_buf, block_depth_buf) * sizeof(float);
+  return warp_part > group_part ? warp_part : group_part;
+}
+
+size_t persist_smem_bytes(int block_buf, int block_depth_buf) {
+  const size_t warp_part = kPersistWarps * sizeof(WarpStage);
+  const size_t group_part = kSubBlocks * group_floats(block_buf, block_depth_buf) * sizeof(float);
+  return warp_part > group_part ? warp_part : group_part;
+}
 
 int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStream_t stream) {
   if (grid <= 0) return 0;
-  const size_t smem = (2 * kWarpsPerBlock + 2 * (size_t)p.block_buf) * sizeof(float);
-#define BDD_SWEEP(F, M) sweep_kernel<F, M><<<grid, kBlockThreads, smem, stream>>>(p)
+  const size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf);
+  int rc = 0;
+#define BDD_SWEEP(F, M) rc = launch_pdl(sweep_kernel<F, M>, grid, kBlockThreads, smem, stream, p)
   if (forward) {
     if (mode == kUpdate) BDD_SWEEP(true, kUpdate);
     else if (mode == kMessages) BDD_SWEEP(true, kMessages);
@@ -470,7 +794,7 @@ int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStr
     else BDD_SWEEP(false, kFolded);
   }
 #undef BDD_SWEEP
-  return status();
+  return rc ? rc : status();
 }
 
 int sweep_set_smem(size_t bytes) {
@@ -484,10 +808,33 @@ int sweep_set_smem(size_t bytes) {
   return 0;
 }
 
-int reduce_launch(bool recompute, bool bound, const ReduceParams &p, int grid, cudaStream_t stream) {
-  if (recompute && bound) reduce_kernel<true, true><<<grid, kReduceThreads, 0, stream>>>(p);
-  else if (recompute) reduce_kernel<true, false><<<grid, kReduceThreads, 0, stream>>>(p);
-  else reduce_kernel<false, true><<<grid, kReduceThreads, 0, stream>>>(p);
+int iterate_set_smem(size_t bytes) {
+  return cudaFuncSetAttribute((const void *)iterate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes) == cudaSuccess ? 0 : -5;
+}
+
+int pending_launch(bool bound, const PendingParams &p, int grid, cudaStream_t stream) {
+  const int rc = bound ? launch_pdl(pending_kernel<true>, grid, kReduceThreads, 0, stream, p)
+                       : launch_pdl(pending_kernel<false>, grid, kReduceThreads, 0, stream, p);
+  return rc ? rc : status();
+}
+
+int iterate_persistent_max_grid(size_t smem, int *grid) {
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -5;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return -5;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -5;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iterate_kernel, kPersistThreads, smem) != cudaSuccess)
+    return -5;
+  *grid = sms * per_sm;
+  return *grid > 0 ? 0 : -5;
+}
+
+int iterate_persistent_launch(const IterParams &q, int grid, size_t smem, cudaStream_t stream) {
+  void *args[] = {const_cast<IterParams *>(&q)};
+  if (cudaLaunchCooperativeKernel((const void *)iterate_kernel, dim3(grid), dim3(kPersistThreads), args, smem,
+                                  stream) != cudaSuccess)
+    return -5;
   return status();
 }
 
@@ -498,24 +845,20 @@ int init_lambda_launch(const int *occ_var, const int *var_ptr, const float *c, f
   return status();
 }
 
-int share_from_pending_launch(const int *var_ptr, const float *P, float *share, int n,
-                              cudaStream_t stream) {
+int pending_to_slots_launch(const int *var_ptr, const float *P, float *delta_b, int n, cudaStream_t stream) {
   if (n == 0) return 0;
-  share_kernel<<<grid_for(n, 256), 256, 0, stream>>>(var_ptr, P, share, n);
+  pending_to_slots_kernel<<<grid_for(n, 256), 256, 0, stream>>>(var_ptr, P, delta_b, n);
   return status();
 }
 
-int scatter_lambda_launch(const float *lam, const float *share, const int *occ_var,
-                          const long long *occ_csr, float *out, int O, bool fold,
-                          cudaStream_t stream) {
+int scatter_lambda_launch(const float *lam, const float *share_occ, const long long *occ_csr, float *out, int O,
+                          bool fold, cudaStream_t stream) {
   if (O == 0) return 0;
-  scatter_lambda_kernel<<<grid_for(O, 256), 256, 0, stream>>>(lam, share, occ_var, occ_csr, out, O,
-                                                                fold);
+  scatter_lambda_kernel<<<grid_for(O, 256), 256, 0, stream>>>(lam, share_occ, occ_csr, out, O, fold);
   return status();
 }
 
-int gather_lambda_launch(const float *in, const long long *occ_csr, float *lam, int O,
-                         cudaStream_t stream) {
+int gather_lambda_launch(const float *in, const long long *occ_csr, float *lam, int O, cudaStream_t stream) {
   if (O == 0) return 0;
   gather_lambda_kernel<<<grid_for(O, 256), 256, 0, stream>>>(in, occ_csr, lam, O);
   return status();

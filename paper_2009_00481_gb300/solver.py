@@ -17,8 +17,11 @@ class Solver:
     """
 
     def __init__(self, inst, omega: float = 0.5, host_only: bool = False, max_device_bytes: int = 0,
-                 device: int = -1, stream: int = 0):
+                 device: int = -1, stream: int = 0, schedule: int = 1, spin_limit: int = 0):
         opt = B.bdd_default_options()
+        opt.schedule = int(schedule)
+        if spin_limit:
+            opt.spin_limit = int(spin_limit)
         opt.omega = omega
         opt.host_only = int(host_only)
         opt.max_device_bytes = int(max_device_bytes)
@@ -28,7 +31,7 @@ class Solver:
                              inst.c, opt)
         s = B.bdd_sizes(self.h)
         (self.n, self.m, self.nb, self.O, self.N, self.max_depth, self.max_width, self.nnz,
-         self.device_bytes, self.warp_tiles, self.block_tiles, self.launches_per_iter) = map(int, s)
+         self.device_bytes, self.warp_tiles, self.block_tiles, self.schedule) = map(int, s)
 
     def close(self):
         if getattr(self, "h", None):
@@ -57,7 +60,8 @@ class Solver:
         B.bdd_iterate_device(self.h, n_iter, ptr(trace), ptr(lam), ptr(mm0), ptr(mm1), stream)
 
     def iterate_profiled(self, n_iter: int):
-        """Per-kernel summed device ms: [forward sweep, reduction, backward sweep, reduction+bound]."""
+        """Per-kernel summed device ms: [forward sweeps, pending passes, backward sweeps,
+        pending passes with bound]."""
         return B.bdd_iterate_profiled(self.h, n_iter)
 
     def canonical(self) -> dict:

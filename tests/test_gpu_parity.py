@@ -130,13 +130,14 @@ def _trace(s, iters):
     return tr.cpu().numpy()
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("omega", [0.5, 1.0])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_bound_trace_parity(lib, name, omega):
+def test_bound_trace_parity(lib, name, omega, schedule):
     inst = CASES[name]()
     iters = 100
     want = Oracle(inst).run_parallel(iters, omega=omega)
-    got = _trace(solver(inst, omega=omega), iters)
+    got = _trace(solver(inst, omega=omega, schedule=schedule), iters)
     close(got[-1:], want[-1:], LB_TOL)
     close(got[:10], want[:10], LB_TOL)
     scale = np.maximum(1.0, np.abs(got[1:]))
@@ -252,6 +253,43 @@ def test_calls_on_different_streams_are_ordered(lib):
     np.testing.assert_array_equal(tr.cpu().numpy()[-1], lb_b)
 
 
+@pytest.mark.parametrize("name", ["potts_20x20x3", "tomography_16", "tracking_10x40", "random_wide"])
+def test_schedules_agree(lib, name):
+    """The persistent kernel (schedule 0) and the per-phase kernels (schedule 1) run the same
+    arithmetic: multipliers and pending sums are bit-identical; bounds differ at most in the
+    FP64 summation order."""
+    inst = CASES[name]()
+    a, b = solver(inst, schedule=0), solver(inst, schedule=1)
+    assert a.schedule == 0 and b.schedule == 1
+    ta, tb = _trace(a, 30), _trace(b, 30)
+    close(ta, tb, 1e-12)
+    la, pa = a.get_state()
+    lb_, pb = b.get_state()
+    np.testing.assert_array_equal(la, lb_)
+    np.testing.assert_array_equal(pa, pb)
+    # switching schedules mid-run keeps the trajectory
+    tb2 = _trace(b, 5)
+    c = solver(inst, schedule=0)
+    c.set_state(la, pa)
+    close(_trace(c, 5), tb2, 1e-12)
+
+
+def test_barrier_timeout_reports_status(lib):
+    """A grid-barrier wait limited to one poll gives up; the kernel returns, the host call reports
+    BDD_ETIMEOUT, and the device stays usable."""
+    from paper_2009_00481_gb300 import BDDError
+    from paper_2009_00481_gb300.binding import BDD_ETIMEOUT
+    inst = config(1)
+    s = solver(inst, schedule=0, spin_limit=1)
+    with pytest.raises(BDDError) as e:
+        s.iterate(3)
+    assert e.value.code == BDD_ETIMEOUT
+    s.close()
+    ok = solver(inst)
+    want = Oracle(inst).run_parallel(5, omega=0.5)
+    close(_trace(ok, 5), want, LB_TOL)
+
+
 def test_host_iterate_matches_device_trace(lib):
     inst = config(0)
     a, b = solver(inst), solver(inst)
@@ -262,7 +300,7 @@ def test_host_iterate_matches_device_trace(lib):
 
 def test_profiled_iterations_match(lib):
     inst = config(0)
-    a, b = solver(inst), solver(inst)
+    a, b = solver(inst), solver(inst, schedule=1)
     ms = a.iterate_profiled(12)
     assert ms.shape == (4,) and np.all(ms > 0)
     lb_a, _, _, _ = a.iterate(0)
