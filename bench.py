@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", type=int, default=1, help="1 per-phase graphs (default), 0 persistent kernel")
+    ap.add_argument("--batch-count", type=int, default=256, help="instances in the batch workload (--config 4)")
+    ap.add_argument("--no-plain", action="store_true", help="batch workload: skip the one-solver-per-instance loop")
     return ap.parse_args()
 
 
@@ -297,6 +299,132 @@ def ours(args):
         dist.destroy_process_group()
 
 
+def batched(args):
+    """The batch of 256 uneven Potts instances: packed into one solver (one launch chain for all
+    instances) against the plain form (one solver per instance, solved one after another).
+    Prints one JSON line."""
+    import torch
+
+    from instances import potts_batch, potts_batch_member
+    from paper_2009_00481_gb300 import Solver
+
+    k = args.config
+    iters = args.iters or CONFIG_ITERS[k]
+    count = args.batch_count
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    t0 = time.perf_counter()
+    inst = potts_batch(count)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    s = Solver(inst, omega=0.5, stream=stream.cuda_stream, schedule=args.schedule)
+    build_s = time.perf_counter() - t0
+    arcs_per_step = 2 * s.N * iters
+    trace = torch.zeros(iters, dtype=torch.float64, device="cuda")
+
+    def step():
+        s.iterate_device(iters, trace=trace, stream=stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        s.set_costs(inst.c)
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        s.set_costs(inst.c)
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    value = arcs_per_step / (ms / 1e3)
+    bounds = s.bound_parts(inst.row_parts, inst.var_parts)
+
+    # per-phase kernels, timed one by one, for the roofline of the dominant kernel
+    s.set_costs(inst.c)
+    kms = s.iterate_profiled(iters)
+    kinds = ["fwd", "pending", "bwd", "pending_bound"]
+    dom = int(np.argmax(kms))
+    peak, peak_kind = measured_peaks()
+    abytes = algorithmic_bytes(kinds[dom], s.N, s.O, s.n, s.nb)
+    per_launch_ms = kms[dom] / iters
+    achieved = abytes / (per_launch_ms / 1e3) / 1e9
+    iter_bytes = algorithmic_bytes("iteration", s.N, s.O, s.n, s.nb)
+    iter_ms = float(kms.sum() / iters)
+
+    # the oracle on every 32nd instance: parity of the per-instance bounds and the CPU baseline
+    import oracle
+    oracle.build()
+    from oracle import Oracle
+    # every 32nd instance, the three smallest of them (a bounded CPU sample)
+    every = list(range(0, count, max(1, count // 8)))
+    sizes = [potts_batch_member(idx).nnz for idx in every]
+    sample = sorted(every[t] for t in np.argsort(sizes, kind="stable")[:3])
+    cpu_arcs, cpu_s, parity = 0, 0.0, []
+    for idx in sample:
+        member = potts_batch_member(idx)
+        o = Oracle(member)
+        t0 = time.perf_counter()
+        tr = o.run_parallel(iters, omega=0.5)
+        cpu_s += time.perf_counter() - t0
+        cpu_arcs += 2 * o.N * iters
+        want = float(tr[-1])
+        got = float(bounds[idx])
+        parity.append({"instance": idx, "oracle": want, "gpu": got,
+                       "rel_err": abs(got - want) / max(1.0, abs(want))})
+
+    # plain form: one solver per instance, iterated one after another on the same stream
+    plain = None
+    if not args.no_plain:
+        solvers = [Solver(potts_batch_member(idx), omega=0.5, stream=stream.cuda_stream, schedule=args.schedule)
+                   for idx in range(count)]
+        for t in solvers:
+            t.iterate_device(2, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in solvers:
+            t.iterate_device(iters, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {"value": arcs_per_step / (pms / 1e3), "unit": UNIT, "ms": pms,
+                 "form": "256 solvers, one per instance, iterated one after another"}
+        for t in solvers:
+            t.close()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": CONFIG_NAMES[k], "instances": count, "iterations_per_step": iters,
+                   "bdds": s.nb, "nodes": s.N, "arcs": 2 * s.N, "occurrences": s.O, "variables": s.n,
+                   "omega": 0.5, "device_bytes": s.device_bytes,
+                   "l2": f"inputs larger than L2: {iter_bytes / 1e9:.2f} GB moved per iteration",
+                   "generate_s": gen_s, "build_s": build_s, "parallelism": "single"},
+        "roofline": {"bound": "hbm", "kernel": {"fwd": "sweep_kernel<forward>", "bwd": "sweep_kernel<backward>",
+                     "pending": "pending_kernel", "pending_bound": "pending_kernel<bound>"}[kinds[dom]],
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "algorithmic_bytes_per_launch": abytes,
+                     "launch_ms": per_launch_ms,
+                     "iteration": {"algorithmic_bytes": iter_bytes, "ms": iter_ms,
+                                   "achieved_gbs": iter_bytes / (iter_ms / 1e3) / 1e9,
+                                   "frac": iter_bytes / (iter_ms / 1e3) / 1e9 / peak},
+                     "per_phase_kernel_ms_per_iteration": {kd: float(v / iters) for kd, v in zip(kinds, kms)}},
+        "parity_sampled_instances": parity,
+        "cpu_baseline": {"value": cpu_arcs / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"instances {sample} of the batch, {iters} iterations each, FP64 single thread"},
+        "plain_loop": plain,
+        "gpu_launches": args.steps * iters * 4,
+        "schedule": "persistent" if s.schedule == 0 else "per-phase graphs",
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -340,6 +468,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference(args)
+    elif args.config == 4:
+        batched(args)
     else:
         ours(args)
 

@@ -118,6 +118,15 @@ int bdd_iterate_device(bdd_solver *h, int n_iter, double *d_bound_trace, float *
  * double[4]. */
 int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms);
 
+/* Lower bounds of independent sub-instances packed block-diagonally into one solver (rows
+ * [row_off[k], row_off[k+1]) and variables [var_off[k], var_off[k+1]) form part k, with no row
+ * touching another part's variables).  The y-slack bound of the dual derivation (Appendix A.1)
+ * splits over such parts: out[k] = sum of E^j over part k's rows + sum of min(0, P_i) over part
+ * k's variables (min(0, c_i) for variables in no row), in FP64, in a fixed order.
+ *   nparts >= 1; row_off: int64[nparts+1], var_off: int64[nparts+1] (host, ascending, from 0 to
+ *   m and n); out: host double[nparts].  Synchronises. */
+int bdd_bound_parts(bdd_solver *h, int nparts, const long long *row_off, const long long *var_off, double *out);
+
 /* Replaces c and restarts: lambda = c/|J_i|, pending sums 0, one backward pass.  c: float[n],
  * host. */
 int bdd_set_costs(bdd_solver *h, const float *c);

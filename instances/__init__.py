@@ -16,6 +16,7 @@ from .generators import (  # noqa: F401
     tomography,
     tracking,
     potts_batch,
+    potts_batch_member,
     random_ilp,
     config,
     CONFIG_NAMES,

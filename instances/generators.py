@@ -157,6 +157,17 @@ def potts_grid_2label(H: int, W: int, seed: int) -> Instance:
     return potts_mrf(H, W, 2, seed=seed)
 
 
+def potts_batch_member(s: int, side_range=(16, 128), label_range=(2, 8)) -> Instance:
+    """Instance s of the Potts batch on its own (same draws as inside :func:`potts_batch`)."""
+    rng = np.random.default_rng(s)
+    side = int(rng.integers(side_range[0], side_range[1] + 1))
+    L = int(rng.integers(label_range[0], label_range[1] + 1))
+    unary = rng.standard_normal(side * side * L).astype(np.float32)
+    n, row_len, col, val, b, sense, c, E = _potts_arrays(side, side, L, unary, 0.5)
+    return _assemble(f"potts_batch_member_{s}", n, row_len, col, val, b, sense, c,
+                     {"seed": s, "side": side, "L": L, "edges": E})
+
+
 def potts_batch(count: int = 256, side_range=(16, 128), label_range=(2, 8), first_seed: int = 0,
                 stride: int = 1) -> Instance:
     """Block-diagonal packing of independent Potts instances of uneven size.

@@ -22,7 +22,7 @@ EXPORTED = [
     "bdd_default_options", "bdd_build", "bdd_last_failed_row", "bdd_iterate", "bdd_iterate_device",
     "bdd_iterate_profiled",
     "bdd_set_costs", "bdd_sizes", "bdd_export_canonical", "bdd_get_state", "bdd_set_state",
-    "bdd_strerror", "bdd_free", "bdd_lower_bound_noalloc",
+    "bdd_strerror", "bdd_free", "bdd_lower_bound_noalloc", "bdd_bound_parts",
 ]
 
 
@@ -73,6 +73,7 @@ def load(path: str | None = None):
     lib.bdd_free.argtypes = [vp]
     lib.bdd_free.restype = None
     lib.bdd_lower_bound_noalloc.argtypes = [i32, i32, vp, vp, vp, f64, vp, vp]
+    lib.bdd_bound_parts.argtypes = [vp, i32, P(i64), P(i64), P(f64)]
     if path == LIB:
         _lib = lib
     return lib
@@ -196,6 +197,16 @@ def bdd_lower_bound_noalloc(n: int, nb: int, d_E: int, d_P: int, d_deg: int, emp
     _check(load().bdd_lower_bound_noalloc(int(n), int(nb), d_E or None, d_P or None, d_deg or None,
                                           float(empty_const), d_bound or None, stream or None),
            "bdd_lower_bound_noalloc")
+
+
+def bdd_bound_parts(h, row_off, var_off) -> np.ndarray:
+    """FP64 bounds of block-diagonal parts (row / variable offsets, each nparts + 1 long)."""
+    row_off = np.ascontiguousarray(row_off, np.int64)
+    var_off = np.ascontiguousarray(var_off, np.int64)
+    out = np.zeros(len(row_off) - 1, np.float64)
+    _check(load().bdd_bound_parts(h, len(out), _ptr(row_off, C.c_longlong), _ptr(var_off, C.c_longlong),
+                                  _ptr(out, C.c_double)), "bdd_bound_parts")
+    return out
 
 
 def bdd_strerror(code: int) -> str:

@@ -82,6 +82,11 @@ struct bdd_solver {
   float *d_P = nullptr, *d_c = nullptr, *d_share_occ = nullptr;
   int *d_occ_slot = nullptr;
   int *d_bdd_depth = nullptr;
+  int *d_bdd_row = nullptr;        // row of each BDD in sorted order
+  float *d_E_row = nullptr;        // scratch for per-part bounds (lazily allocated)
+  long long *d_part_off = nullptr; // scratch: row and variable offsets of the parts
+  double *d_part_out = nullptr;
+  int part_cap = 0;
   float *d_bdd_E = nullptr;
   int *d_tile_occ0 = nullptr, *d_tile_bdd0 = nullptr, *d_tile_nbdd = nullptr;
   int *d_var_ptr = nullptr, *d_var_occ = nullptr;
@@ -381,6 +386,11 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   RC(h->alloc(&h->d_P, n));
   RC(h->alloc(&h->d_c, n));
   RC(upload(h, &h->d_bdd_depth, L.bdd_depth));
+  {
+    std::vector<int> rows(h->nb);
+    for (long long t = 0; t < h->nb; ++t) rows[t] = h->canon_row[L.bdd_perm[t]];
+    RC(upload(h, &h->d_bdd_row, rows));
+  }
   RC(h->alloc(&h->d_bdd_E, nb));
   RC(upload(h, &h->d_tile_occ0, L.tile_occ0));
   RC(upload(h, &h->d_tile_bdd0, L.tile_bdd0));
@@ -802,6 +812,34 @@ int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending) {
     RC(h->pending(false, s));
   }
   RC(h->sweep(false, kMessages, s));
+  RC(h->end(s));
+  CK(cudaStreamSynchronize(s));
+  return BDD_OK;
+}
+
+int bdd_bound_parts(bdd_solver *h, int nparts, const long long *row_off, const long long *var_off, double *out) {
+  if (!h || nparts < 1 || !row_off || !var_off || !out) return BDD_EINVAL;
+  if (h->host_only) return BDD_ESTATE;
+  if (row_off[0] != 0 || var_off[0] != 0 || row_off[nparts] != h->m || var_off[nparts] != h->n) return BDD_EINVAL;
+  for (int k = 0; k < nparts; ++k)
+    if (row_off[k + 1] < row_off[k] || var_off[k + 1] < var_off[k]) return BDD_EINVAL;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return BDD_ECUDA;
+  cudaStream_t s = h->stream;
+  if (!h->d_E_row) RC(h->alloc(&h->d_E_row, std::max(h->m, 1)));
+  if (nparts > h->part_cap) {
+    RC(h->alloc(&h->d_part_off, 2LL * (nparts + 1)));
+    RC(h->alloc(&h->d_part_out, nparts));
+    h->part_cap = nparts;
+  }
+  RC(h->begin(s));
+  CK(cudaMemcpyAsync(h->d_part_off, row_off, sizeof(long long) * (nparts + 1), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->d_part_off + nparts + 1, var_off, sizeof(long long) * (nparts + 1), cudaMemcpyHostToDevice,
+                     s));
+  if (part_bounds_launch(h->d_bdd_E, h->d_bdd_row, (int)h->nb, h->d_E_row, h->m, h->d_part_off,
+                         h->d_part_off + nparts + 1, nparts, h->d_var_ptr, h->d_P, h->d_c, h->d_part_out, s))
+    return BDD_ECUDA;
+  CK(cudaMemcpyAsync(out, h->d_part_out, sizeof(double) * nparts, cudaMemcpyDeviceToHost, s));
   RC(h->end(s));
   CK(cudaStreamSynchronize(s));
   return BDD_OK;

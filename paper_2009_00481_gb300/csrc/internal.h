@@ -178,6 +178,10 @@ int scatter_lambda_launch(const float *lam, const float *share_occ, const long l
                           int O, bool fold, cudaStream_t stream);
 int gather_lambda_launch(const float *in, const long long *occ_csr, float *lam, int O,
                          cudaStream_t stream);
+// per-part bounds: E scattered to rows, then one block per part sums its rows and variables
+int part_bounds_launch(const float *bdd_E, const int *bdd_row, int nb, float *E_row, int m, const long long *row_off,
+                       const long long *var_off, int nparts, const int *var_ptr, const float *P, const float *c,
+                       double *out, cudaStream_t stream);
 constexpr int kReduceThreads = 256;
 
 }  // namespace bdd

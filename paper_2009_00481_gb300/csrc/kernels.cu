@@ -739,6 +739,30 @@ __global__ void gather_lambda_kernel(const float *__restrict__ in, const long lo
     lam[o] = in[occ_csr[o]];
 }
 
+__global__ void scatter_rows_kernel(const float *__restrict__ bdd_E, const int *__restrict__ bdd_row, int nb,
+                                    float *__restrict__ E_row) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x)
+    E_row[bdd_row[j]] = bdd_E[j];
+}
+
+// one block per part: sum of E over the part's rows plus min(0, P_i) (min(0, c_i) for a variable
+// in no row) over its variables, FP64, strided per thread then a fixed tree
+__global__ void __launch_bounds__(kReduceThreads)
+    part_bound_kernel(const float *__restrict__ E_row, const long long *__restrict__ row_off,
+                      const long long *__restrict__ var_off, const int *__restrict__ var_ptr,
+                      const float *__restrict__ P, const float *__restrict__ c, double *__restrict__ out) {
+  const int k = blockIdx.x;
+  double acc = 0.0;
+  for (long long r = row_off[k] + threadIdx.x; r < row_off[k + 1]; r += blockDim.x) acc += (double)E_row[r];
+  for (long long i = var_off[k] + threadIdx.x; i < var_off[k + 1]; i += blockDim.x) {
+    const float v = var_ptr[i + 1] > var_ptr[i] ? P[i] : c[i];
+    if (v < 0.f) acc += (double)v;
+  }
+  __shared__ double red[kReduceThreads / 32];
+  const double s = block_sum(acc, red, kReduceThreads / 32);
+  if (threadIdx.x == 0) out[k] = s;
+}
+
 // ---------------------------------------------------------------------------------------
 // launch wrappers
 // ---------------------------------------------------------------------------------------
@@ -855,6 +879,15 @@ int scatter_lambda_launch(const float *lam, const float *share_occ, const long l
                           bool fold, cudaStream_t stream) {
   if (O == 0) return 0;
   scatter_lambda_kernel<<<grid_for(O, 256), 256, 0, stream>>>(lam, share_occ, occ_csr, out, O, fold);
+  return status();
+}
+
+int part_bounds_launch(const float *bdd_E, const int *bdd_row, int nb, float *E_row, int m, const long long *row_off,
+                       const long long *var_off, int nparts, const int *var_ptr, const float *P, const float *c,
+                       double *out, cudaStream_t stream) {
+  if (m > 0 && cudaMemsetAsync(E_row, 0, sizeof(float) * m, stream) != cudaSuccess) return -5;
+  if (nb > 0) scatter_rows_kernel<<<grid_for(nb, 256), 256, 0, stream>>>(bdd_E, bdd_row, nb, E_row);
+  part_bound_kernel<<<nparts, kReduceThreads, 0, stream>>>(E_row, row_off, var_off, var_ptr, P, c, out);
   return status();
 }
 

@@ -64,6 +64,10 @@ class Solver:
         pending passes with bound]."""
         return B.bdd_iterate_profiled(self.h, n_iter)
 
+    def bound_parts(self, row_off, var_off):
+        """FP64 bounds of block-diagonal parts of a packed instance."""
+        return B.bdd_bound_parts(self.h, row_off, var_off)
+
     def canonical(self) -> dict:
         return B.bdd_export_canonical(self.h)
 

@@ -365,3 +365,51 @@ def test_max_device_bytes(lib):
     with pytest.raises(BDDError) as e:
         solver(config(1), max_device_bytes=1 << 16)
     assert e.value.code == BDD_ENOMEM
+
+
+# ------------------------------------------------------------------------------------------
+# batches of independent instances packed into one solver
+# ------------------------------------------------------------------------------------------
+
+def _small_batch():
+    from instances import potts_batch, potts_batch_member
+    kw = dict(side_range=(3, 7), label_range=(2, 4))
+    packed = potts_batch(count=5, first_seed=40, **kw)
+    members = [potts_batch_member(40 + k, **kw) for k in range(5)]
+    return packed, members
+
+
+def test_batch_part_bounds_match_members(lib):
+    """Per-instance bounds of a packed batch equal each instance's own oracle bound, and the
+    parts add up to the packed bound."""
+    packed, members = _small_batch()
+    s = solver(packed)
+    tr = _trace(s, 40)
+    parts = s.bound_parts(packed.row_parts, packed.var_parts)
+    want = [Oracle(m).run_parallel(40, omega=0.5)[-1] for m in members]
+    close(parts, want, LB_TOL)
+    assert abs(parts.sum() - tr[-1]) <= 1e-9 * max(1.0, abs(tr[-1]))
+
+
+def test_batch_members_bit_identical_to_separate_solves(lib):
+    """Packing independent instances changes no arithmetic: each member's multipliers after
+    the packed solve equal those of solving the member alone, bit for bit."""
+    packed, members = _small_batch()
+    s = solver(packed)
+    _trace(s, 25)
+    lam, _ = s.get_state()
+    off = packed.row_parts
+    for k, m in enumerate(members):
+        t = solver(m)
+        _trace(t, 25)
+        lm, _ = t.get_state()
+        a, b = int(packed.row_ptr[off[k]]), int(packed.row_ptr[off[k + 1]])
+        np.testing.assert_array_equal(lam[a:b], lm)
+
+
+def test_bound_parts_rejects_bad_offsets(lib):
+    from paper_2009_00481_gb300 import BDDError
+    packed, _ = _small_batch()
+    s = solver(packed)
+    with pytest.raises(BDDError):
+        s.bound_parts([0, 1], [0, packed.n])
