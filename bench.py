@@ -43,8 +43,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", type=int, default=1, help="1 per-phase graphs (default), 0 persistent kernel")
-    ap.add_argument("--batch-count", type=int, default=256, help="instances in the batch workload (--config 4)")
+    ap.add_argument("--batch-count", type=int, default=256, help="instances in the batch workload")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--batch-warmup", type=int, default=2)
     ap.add_argument("--no-plain", action="store_true", help="batch workload: skip the one-solver-per-instance loop")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch workload part of the default line")
     return ap.parse_args()
 
 
@@ -261,6 +264,10 @@ def ours(args):
                "d2h_bytes_per_step": int(d2h), "includes": "bdd_build (host BDD compile + upload) + "
                "bdd_iterate with bound, lambda and min-marginals to host + bdd_free"}
 
+    batch = None
+    if world == 1 and not args.no_batch:
+        batch = run_batched(args, stream, plain=False, n_parity=1)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -289,6 +296,7 @@ def ours(args):
                      "per_phase_kernel_ms_per_iteration": {kd: float(v / iters) for kd, v in zip(kinds, kms)}},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batched": batch,
         "gpu_launches": launches,
         "schedule": "persistent" if s.schedule == 0 else "per-phase graphs",
         "clocks": clocks,
@@ -299,21 +307,18 @@ def ours(args):
         dist.destroy_process_group()
 
 
-def batched(args):
-    """The batch of 256 uneven Potts instances: packed into one solver (one launch chain for all
-    instances) against the plain form (one solver per instance, solved one after another).
-    Prints one JSON line."""
+def run_batched(args, stream, plain: bool, n_parity: int) -> dict:
+    """The batch of 256 uneven Potts instances packed into one solver (one launch chain for all
+    instances): throughput, the roofline of the dominant kernel, per-instance parity with the
+    oracle on a bounded sample, and optionally the plain form (one solver per instance, solved
+    one after another) for comparison."""
     import torch
 
     from instances import potts_batch, potts_batch_member
     from paper_2009_00481_gb300 import Solver
 
-    k = args.config
-    iters = args.iters or CONFIG_ITERS[k]
+    iters = CONFIG_ITERS[4] if args.config != 4 or not args.iters else args.iters
     count = args.batch_count
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
     inst = potts_batch(count)
     gen_s = time.perf_counter() - t0
@@ -326,13 +331,15 @@ def batched(args):
     def step():
         s.iterate_device(iters, trace=trace, stream=stream.cuda_stream)
 
-    for _ in range(args.warmup):
+    warmup = args.batch_warmup
+    steps = args.batch_steps
+    for _ in range(warmup):
         s.set_costs(inst.c)
         step()
     torch.cuda.synchronize()
     sampler = ClockSampler(0)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
         s.set_costs(inst.c)
         evs[i][0].record(stream)
         step()
@@ -340,7 +347,6 @@ def batched(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
-    value = arcs_per_step / (ms / 1e3)
     bounds = s.bound_parts(inst.row_parts, inst.var_parts)
 
     # per-phase kernels, timed one by one, for the roofline of the dominant kernel
@@ -355,30 +361,27 @@ def batched(args):
     iter_bytes = algorithmic_bytes("iteration", s.N, s.O, s.n, s.nb)
     iter_ms = float(kms.sum() / iters)
 
-    # the oracle on every 32nd instance: parity of the per-instance bounds and the CPU baseline
+    # the oracle on a bounded sample of every 32nd instance (the smallest ones): per-instance
+    # parity and the CPU baseline
     import oracle
     oracle.build()
     from oracle import Oracle
-    # every 32nd instance, the three smallest of them (a bounded CPU sample)
     every = list(range(0, count, max(1, count // 8)))
     sizes = [potts_batch_member(idx).nnz for idx in every]
-    sample = sorted(every[t] for t in np.argsort(sizes, kind="stable")[:3])
+    sample = sorted(every[t] for t in np.argsort(sizes, kind="stable")[:n_parity])
     cpu_arcs, cpu_s, parity = 0, 0.0, []
     for idx in sample:
-        member = potts_batch_member(idx)
-        o = Oracle(member)
+        o = Oracle(potts_batch_member(idx))
         t0 = time.perf_counter()
         tr = o.run_parallel(iters, omega=0.5)
         cpu_s += time.perf_counter() - t0
         cpu_arcs += 2 * o.N * iters
-        want = float(tr[-1])
-        got = float(bounds[idx])
+        want, got = float(tr[-1]), float(bounds[idx])
         parity.append({"instance": idx, "oracle": want, "gpu": got,
                        "rel_err": abs(got - want) / max(1.0, abs(want))})
 
-    # plain form: one solver per instance, iterated one after another on the same stream
-    plain = None
-    if not args.no_plain:
+    plain_d = None
+    if plain:
         solvers = [Solver(potts_batch_member(idx), omega=0.5, stream=stream.cuda_stream, schedule=args.schedule)
                    for idx in range(count)]
         for t in solvers:
@@ -391,20 +394,18 @@ def batched(args):
         e1.record(stream)
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1)
-        plain = {"value": arcs_per_step / (pms / 1e3), "unit": UNIT, "ms": pms,
-                 "form": "256 solvers, one per instance, iterated one after another"}
+        plain_d = {"value": arcs_per_step / (pms / 1e3), "unit": UNIT, "ms": pms,
+                   "form": f"{count} solvers, one per instance, iterated one after another"}
         for t in solvers:
             t.close()
-
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": CONFIG_NAMES[k], "instances": count, "iterations_per_step": iters,
+    s.close()
+    return {
+        "value": arcs_per_step / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+        "config": {"workload": CONFIG_NAMES[4], "instances": count, "iterations_per_step": iters,
                    "bdds": s.nb, "nodes": s.N, "arcs": 2 * s.N, "occurrences": s.O, "variables": s.n,
                    "omega": 0.5, "device_bytes": s.device_bytes,
                    "l2": f"inputs larger than L2: {iter_bytes / 1e9:.2f} GB moved per iteration",
-                   "generate_s": gen_s, "build_s": build_s, "parallelism": "single"},
+                   "generate_s": gen_s, "build_s": build_s},
         "roofline": {"bound": "hbm", "kernel": {"fwd": "sweep_kernel<forward>", "bwd": "sweep_kernel<backward>",
                      "pending": "pending_kernel", "pending_bound": "pending_kernel<bound>"}[kinds[dom]],
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -417,11 +418,26 @@ def batched(args):
         "parity_sampled_instances": parity,
         "cpu_baseline": {"value": cpu_arcs / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"instances {sample} of the batch, {iters} iterations each, FP64 single thread"},
-        "plain_loop": plain,
-        "gpu_launches": args.steps * iters * 4,
+        "plain_loop": plain_d,
+        "gpu_launches": steps * iters * 4,
         "schedule": "persistent" if s.schedule == 0 else "per-phase graphs",
         "clocks": clocks,
     }
+
+
+def batched(args):
+    """`--config 4`: the batch workload as the bench line."""
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    b = run_batched(args, stream, plain=not args.no_plain, n_parity=3)
+    out = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": 1, "steps": b["steps"],
+           "warmup": b["warmup"], "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": dict(b["config"], parallelism="single")}
+    out.update({k: b[k] for k in ("roofline", "parity_sampled_instances", "cpu_baseline", "plain_loop",
+                                  "gpu_launches", "schedule", "clocks")})
     print(json.dumps(out), flush=True)
 
 
