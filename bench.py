@@ -76,6 +76,24 @@ def algorithmic_bytes(kind: str, N: int, O: int, n: int, nb: int) -> int:
     raise ValueError(kind)
 
 
+def max_over_ranks(ms: float, world: int, device: str = "cpu") -> float:
+    """Step time of the slowest rank (all ranks call this; needs an initialised process group
+    when world > 1)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_step_per_rank: float, ms_max: float, world: int) -> float:
+    """Whole-job throughput of `world` independent replicas: all ranks' units over the slowest
+    rank's time."""
+    return world * units_per_step_per_rank / (ms_max / 1e3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
@@ -215,12 +233,8 @@ def ours(args):
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * arcs_per_step / (ms / 1e3)
+    ms = max_over_ranks(float(np.mean(step_ms)), world, device="cuda")
+    value = replica_throughput(arcs_per_step, ms, world)
     tr = trace.cpu().numpy()
 
     # roofline of the dominant kernel.  Persistent schedule: the one iteration kernel, timed by
