@@ -57,6 +57,7 @@ def _configure(lib):
     lib.orc_min_marginals.argtypes = [vp, i32, P(f64), P(f64)]
     lib.orc_energies.argtypes = [vp, P(f64)]
     lib.orc_counts.argtypes = [vp, P(f64)]
+    lib.orc_set_alpha.argtypes = [vp, f64]
     return lib
 
 
@@ -131,6 +132,10 @@ class Oracle:
                     occ_width=occ_width, lo=lo, hi=hi, minsum=minsum)
 
     # ---- dual state --------------------------------------------------------------------
+    def set_alpha(self, alpha: float):
+        """Smoothing temperature (0 = min-sum); restarts the dual state."""
+        self.lib.orc_set_alpha(self.h, float(alpha))
+
     def reset(self):
         self.lib.orc_init_dual(self.h)
 

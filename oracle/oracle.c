@@ -31,6 +31,11 @@
  *     form of the dual derivation, Appendix A.1), which equals eq. (D)'s objective when
  *     sum_j lambda^j_i = c_i.
  *   - Solution counts (Appendix C.1, Table 3, counting column).
+ *   - Smoothing (Appendix A.5; Appendix C.1, Table 3, log-sum-exp column): with alpha > 0 every
+ *     minimum above (forward and backward steps, min-marginal aggregation, the y-slack term)
+ *     becomes the soft minimum -alpha log(sum exp(-x / alpha)), evaluated in the -alpha log
+ *     domain with the smaller argument factored out; E^j becomes E^j_alpha and min-marginals
+ *     become marginal log-sum-exp values.  alpha = 0 is the plain min-sum algebra.
  * Readings where the paper is silent: a min-marginal that is +inf (a row that forces x_i)
  * gives the difference 0; a variable in no row contributes min(0, c_i) to the bound; an empty
  * row is dropped when 0 (sense) b holds and is infeasible otherwise.
@@ -94,7 +99,8 @@ typedef struct {
   long long *var_ptr, *var_occ; /* occurrences of each variable in ascending row order */
   int *deg;
   double *c;
-  double empty_const;       /* sum over variables in no row of min(0, c_i) */
+  double empty_const;       /* sum over variables in no row of min(0, c_i) (soft: of agg(0, c_i)) */
+  double alpha;             /* 0: min-sum; > 0: smoothing temperature */
   /* dual state and messages */
   double *lam, *P, *delta, *share, *fm, *bm;
   /* scratch for the definitional dynamic programmes */
@@ -357,6 +363,17 @@ void orc_export(void *vh, int *bdd_row, int *bdd_depth, int *occ_var, long long 
 /* ------------------------------------------------------------------------------------ */
 /* dynamic programmes (Alg. 2 / Alg. 3, eqs. arc-marginal and marginal-aggregation)       */
 /* ------------------------------------------------------------------------------------ */
+/* The aggregation of Table 3: min(a, b) for min-sum; for alpha > 0 the log-sum-exp column in
+ * the -alpha log domain, -alpha log(exp(-a/alpha) + exp(-b/alpha)), written as
+ * min(a, b) - alpha log(1 + exp(-|a - b| / alpha)). */
+static double agg(const oracle_t *h, double a, double b) {
+  if (h->alpha <= 0.0) return a < b ? a : b;
+  if (isinf(a)) return b;
+  if (isinf(b)) return a;
+  double m = a < b ? a : b;
+  return m - h->alpha * log1p(exp(-fabs(a - b) / h->alpha));
+}
+
 /* backward message of the target t of an arc leaving layer o (t is a local id in o+1) */
 static double bval(const oracle_t *h, const double *bm, long long o, int t) {
   if (t == ORC_TOP) return 0.0;
@@ -376,12 +393,12 @@ static void dp_forward(const oracle_t *h, int b, const double *lam, double *fm) 
     for (long long u = h->occ_node0[o - 1]; u < h->occ_node0[o]; ++u) {
       if (h->lo[u] >= 0) {
         long long v = h->occ_node0[o] + h->lo[u];
-        if (fm[u] < fm[v]) fm[v] = fm[u];
+        fm[v] = agg(h, fm[v], fm[u]);
       }
       if (h->hi[u] >= 0) {
         long long v = h->occ_node0[o] + h->hi[u];
         double x = fm[u] + lam[o - 1];
-        if (x < fm[v]) fm[v] = x;
+        fm[v] = agg(h, fm[v], x);
       }
     }
   }
@@ -393,7 +410,7 @@ static void bwd_step(const oracle_t *h, long long o, double lam_o, double *bm) {
     double a0 = bval(h, bm, o, h->lo[u]);
     double a1 = lam_o + bval(h, bm, o, h->hi[u]);
     if (h->hi[u] == ORC_BOT) a1 = INFINITY;
-    bm[u] = a0 < a1 ? a0 : a1;
+    bm[u] = agg(h, a0, a1);
   }
 }
 
@@ -411,11 +428,11 @@ static void aggregate(const oracle_t *h, long long o, double lam_o, const double
   for (long long u = h->occ_node0[o]; u < h->occ_node0[o + 1]; ++u) {
     if (h->lo[u] != ORC_BOT) {
       double x = fm[u] + bval(h, bm, o, h->lo[u]);
-      if (x < a) a = x;
+      a = agg(h, a, x);
     }
     if (h->hi[u] != ORC_BOT) {
       double x = fm[u] + lam_o + bval(h, bm, o, h->hi[u]);
-      if (x < c1) c1 = x;
+      c1 = agg(h, c1, x);
     }
   }
   *m0 = a; *m1 = c1;
@@ -439,7 +456,7 @@ double orc_bound(void *vh) {
   double lb = h->empty_const;
   for (int b = 0; b < h->nb; ++b) lb += energy(h, b, h->lam);
   for (int i = 0; i < h->n; ++i)
-    if (h->deg[i] > 0 && h->P[i] < 0) lb += h->P[i];
+    if (h->deg[i] > 0) lb += agg(h, 0.0, h->P[i]);
   return lb;
 }
 
@@ -464,6 +481,16 @@ void orc_init_dual(void *vh) {
   for (int i = 0; i < h->n; ++i) h->P[i] = 0.0;
   for (int b = 0; b < h->nb; ++b) dp_backward(h, b, h->lam, h->bm);
   for (int t = 0; t < 5; ++t) h->worst[t] = 0.0;
+}
+
+/* Sets the smoothing temperature (0 = min-sum) and restarts the dual state. */
+void orc_set_alpha(void *vh, double alpha) {
+  oracle_t *h = (oracle_t *)vh;
+  h->alpha = alpha > 0.0 ? alpha : 0.0;
+  h->empty_const = 0.0;
+  for (int i = 0; i < h->n; ++i)
+    if (h->deg[i] == 0) h->empty_const += agg(h, 0.0, h->c[i]);
+  orc_init_dual(vh);
 }
 
 void orc_worst(void *vh, double out[5]) {
@@ -511,12 +538,12 @@ static void sweep_forward(oracle_t *h, double omega, int check) {
         for (long long u = h->occ_node0[o - 1]; u < h->occ_node0[o]; ++u) {
           if (h->lo[u] >= 0) {
             long long v = h->occ_node0[o] + h->lo[u];
-            if (h->fm[u] < h->fm[v]) h->fm[v] = h->fm[u];
+            h->fm[v] = agg(h, h->fm[v], h->fm[u]);
           }
           if (h->hi[u] >= 0) {
             long long v = h->occ_node0[o] + h->hi[u];
             double x = h->fm[u] + h->lam[o - 1];
-            if (x < h->fm[v]) h->fm[v] = x;
+            h->fm[v] = agg(h, h->fm[v], x);
           }
         }
       }
@@ -568,7 +595,7 @@ static double bound_after_backward(const oracle_t *h) {
   double lb = h->empty_const;
   for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];
   for (int i = 0; i < h->n; ++i)
-    if (h->deg[i] > 0 && h->P[i] < 0) lb += h->P[i];
+    if (h->deg[i] > 0) lb += agg(h, 0.0, h->P[i]);
   return lb;
 }
 

@@ -26,8 +26,8 @@ MUTANTS = {
     "drop_share": ("        }\n      }\n      h->lam[o] += h->share[h->occ_var[o]];",
                    "        }\n      }\n"),
     # forward update step charges the 1-arc with the wrong layer's multiplier
-    "fwd_index": ("            double x = h->fm[u] + h->lam[o - 1];\n            if (x < h->fm[v]) h->fm[v] = x;\n          }\n        }\n      }\n      h->lam[o]",
-                  "            double x = h->fm[u] + h->lam[o];\n            if (x < h->fm[v]) h->fm[v] = x;\n          }\n        }\n      }\n      h->lam[o]"),
+    "fwd_index": ("            double x = h->fm[u] + h->lam[o - 1];\n            h->fm[v] = agg(h, h->fm[v], x);",
+                  "            double x = h->fm[u] + h->lam[o];\n            h->fm[v] = agg(h, h->fm[v], x);"),
     # BDD builder swaps the 0- and 1-successor
     "swap_arcs": ("iv_push(&Llo[l], c0) || iv_push(&Lhi[l], c1)",
                   "iv_push(&Llo[l], c1) || iv_push(&Lhi[l], c0)"),
@@ -35,7 +35,7 @@ MUTANTS = {
     "bwd_theta": ("double a1 = lam_o + bval(h, bm, o, h->hi[u]);",
                   "double a1 = bval(h, bm, o, h->hi[u]);"),
     # bound forgets the slack term of the y-variables
-    "bound_slack": ("  for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];\n  for (int i = 0; i < h->n; ++i)\n    if (h->deg[i] > 0 && h->P[i] < 0) lb += h->P[i];",
+    "bound_slack": ("  for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];\n  for (int i = 0; i < h->n; ++i)\n    if (h->deg[i] > 0) lb += agg(h, 0.0, h->P[i]);",
                     "  for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];"),
 }
 
