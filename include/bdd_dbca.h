@@ -68,6 +68,12 @@ typedef struct {
                                  cooperative launch. */
   long long spin_limit;       /* polls before a grid-barrier wait gives up (then the call's host
                                  form returns BDD_ETIMEOUT); default 1 << 26 */
+  float alpha;                /* smoothing temperature (Appendix A.5): 0 (default) = min-sum;
+                                 alpha > 0 replaces every minimum of the iteration and of the
+                                 bound by the soft minimum -alpha log sum exp(-x / alpha), so
+                                 the bound is E^j_alpha-based and differentiable.  Smoothed
+                                 solvers need every BDD layer to be at most 32 nodes wide
+                                 (else BDD_ETOOBIG) and run schedule 1. */
 } bdd_options;
 
 void bdd_default_options(bdd_options *opt);
@@ -126,6 +132,18 @@ int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms);
  *   nparts >= 1; row_off: int64[nparts+1], var_off: int64[nparts+1] (host, ascending, from 0 to
  *   m and n); out: host double[nparts].  Synchronises. */
 int bdd_bound_parts(bdd_solver *h, int nparts, const long long *row_off, const long long *var_off, double *out);
+
+/* Smoothed bound as a differentiable function of the costs (Appendix A.5; needs alpha > 0).
+ * bdd_smooth_forward sets c (device float[n]), restarts (lambda = c/|J_i|), runs K iterations
+ * and writes the smoothed bound after them (the y-slack form with every minimum soft) to
+ * d_bound (device double[1]); it keeps a checkpoint of the multipliers and shares of every sweep
+ * (2 K O floats of device memory).  bdd_smooth_backward then writes d_grad_c (device float[n])
+ * = g * d bound / d c, g read from d_gbound (device double[1]), by reverse-mode passes over the
+ * K iterations that recompute each sweep's messages from its checkpoint (hand-written adjoint
+ * kernels).  The backward must follow its forward with no state-changing call in between
+ * (else BDD_ESTATE).  Both enqueue on `stream` (NULL = the solver's stream) and return. */
+int bdd_smooth_forward(bdd_solver *h, int K, const float *d_c, double *d_bound, void *stream);
+int bdd_smooth_backward(bdd_solver *h, const double *d_gbound, float *d_grad_c, void *stream);
 
 /* Replaces c and restarts: lambda = c/|J_i|, pending sums 0, one backward pass.  c: float[n],
  * host. */

@@ -22,14 +22,16 @@ EXPORTED = [
     "bdd_default_options", "bdd_build", "bdd_last_failed_row", "bdd_iterate", "bdd_iterate_device",
     "bdd_iterate_profiled",
     "bdd_set_costs", "bdd_sizes", "bdd_export_canonical", "bdd_get_state", "bdd_set_state",
-    "bdd_strerror", "bdd_free", "bdd_lower_bound_noalloc", "bdd_bound_parts",
+    "bdd_strerror", "bdd_free", "bdd_lower_bound_noalloc", "bdd_bound_parts", "bdd_smooth_forward",
+    "bdd_smooth_backward",
 ]
 
 
 class bdd_options(C.Structure):
     _fields_ = [("omega", C.c_float), ("max_width", C.c_int), ("max_nodes", C.c_longlong),
                 ("max_device_bytes", C.c_longlong), ("host_only", C.c_int), ("device", C.c_int),
-                ("stream", C.c_void_p), ("schedule", C.c_int), ("spin_limit", C.c_longlong)]
+                ("stream", C.c_void_p), ("schedule", C.c_int), ("spin_limit", C.c_longlong),
+                ("alpha", C.c_float)]
 
 
 class BDDError(RuntimeError):
@@ -74,6 +76,8 @@ def load(path: str | None = None):
     lib.bdd_free.restype = None
     lib.bdd_lower_bound_noalloc.argtypes = [i32, i32, vp, vp, vp, f64, vp, vp]
     lib.bdd_bound_parts.argtypes = [vp, i32, P(i64), P(i64), P(f64)]
+    lib.bdd_smooth_forward.argtypes = [vp, i32, vp, vp, vp]
+    lib.bdd_smooth_backward.argtypes = [vp, vp, vp, vp]
     if path == LIB:
         _lib = lib
     return lib
@@ -207,6 +211,18 @@ def bdd_bound_parts(h, row_off, var_off) -> np.ndarray:
     _check(load().bdd_bound_parts(h, len(out), _ptr(row_off, C.c_longlong), _ptr(var_off, C.c_longlong),
                                   _ptr(out, C.c_double)), "bdd_bound_parts")
     return out
+
+
+def bdd_smooth_forward(h, K: int, d_c: int, d_bound: int, stream: int = 0):
+    """Smoothed bound after K iterations from costs c (device pointers as integers)."""
+    _check(load().bdd_smooth_forward(h, int(K), d_c or None, d_bound or None, stream or None),
+           "bdd_smooth_forward")
+
+
+def bdd_smooth_backward(h, d_gbound: int, d_grad_c: int, stream: int = 0):
+    """g * d(smoothed bound)/dc into d_grad_c, for the last bdd_smooth_forward."""
+    _check(load().bdd_smooth_backward(h, d_gbound or None, d_grad_c or None, stream or None),
+           "bdd_smooth_backward")
 
 
 def bdd_strerror(code: int) -> str:

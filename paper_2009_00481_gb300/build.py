@@ -16,14 +16,15 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libbdd_dbca.so")
-SOURCES = ["compile.cpp", "kernels.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["compile.cpp", "kernels.cu", "adjoint.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "internal.h"), os.path.join(INCLUDE, "bdd_dbca.h"),
+    files += [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "device_common.cuh"),
+              os.path.join(INCLUDE, "bdd_dbca.h"),
               os.path.abspath(__file__)]
     return files
 

@@ -1,0 +1,398 @@
+// Reverse-mode adjoints of the smoothed iteration (Appendix A.5), for the gradient of the
+// smoothed bound after K iterations with respect to the costs c.
+//
+// The forward map of one update sweep of one BDD (warp tiles only; T lanes, lane t = node t):
+//   forward sweep, layers l ascending:
+//     fm_l(v)  = softmin over in-arcs (u, v) of fm_{l-1}(u) + theta_uv   (theta = lam''_{l-1} on
+//                1-arcs, 0 on 0-arcs; fm_0(root) = 0)                                  (Alg. 2)
+//     lam'_l   = lam_l + s_l                        (s_l: the pending share)
+//     m0, m1   = softmin over v of fm_l(v) + bmp(lo v),  fm_l(v) + lam'_l + bmp(hi v)
+//     lam''_l  = lam'_l - omega (m1 - m0);  delta_l = omega (m1 - m0)
+//   where bmp are the backward messages of the sweep's starting multipliers (Alg. 3 recursion).
+//   backward sweep, layers l descending: the mirror image, with fmp (forward messages of the
+//   starting multipliers) in the marginals and the new backward messages
+//     bmn_l(v) = softmin(bmn_{l+1}(lo v), lam''_l + bmn_{l+1}(hi v)).
+// The derivative of softmin_k x_k with respect to x_k is exp(-(x_k - softmin)/alpha); every
+// adjoint below is that weight times the adjoint of the soft minimum, pushed or pulled along
+// the same arcs the forward map uses.  Messages and updated multipliers are recomputed from
+// per-sweep checkpoints (multipliers and shares) by the forward kernels before each adjoint.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace bdd {
+namespace {
+
+// softmin weight of an argument x whose soft minimum is m (x >= m up to rounding)
+__device__ __forceinline__ float weight(float x, float m, float inv_alpha) {
+  if (x == inf() || m == inf()) return 0.f;
+  return expf(-(x - m) * inv_alpha);
+}
+
+// message of an arc target: top -> 0, bot / none -> +inf, node -> msg
+__device__ __forceinline__ float target_msg(const float *__restrict__ msg, int t) {
+  if (t >= 0) return msg[t];
+  return t == kTop ? 0.f : inf();
+}
+
+// Push: every lane, as target index tl of the next layer, sums the contributions c0 (along
+// 0-arcs, target lo_rel) and c1 (along 1-arcs, target hi_rel) of the team's source lanes, in
+// source order.
+template <int T>
+__device__ __forceinline__ float team_push(int lo_rel, int hi_rel, float c0, float c1, int tbase, int tl) {
+  float acc = 0.f;
+#pragma unroll
+  for (int s = 0; s < T; ++s) {
+    const int ls = __shfl_sync(kFull, lo_rel, tbase + s);
+    const int hs = __shfl_sync(kFull, hi_rel, tbase + s);
+    const float x0 = __shfl_sync(kFull, c0, tbase + s);
+    const float x1 = __shfl_sync(kFull, c1, tbase + s);
+    if (ls == tl) acc += x0;
+    if (hs == tl) acc += x1;
+  }
+  return acc;
+}
+
+struct Team {
+  int lane, team, tl, tbase, occ0, bdd, depth, lead_depth, maxd;
+};
+
+template <int T>
+__device__ __forceinline__ Team team_of(const SweepParams &p, int tile) {
+  Team m;
+  m.lane = threadIdx.x & 31;
+  m.team = m.lane / T;
+  m.tl = m.lane % T;
+  m.tbase = m.team * T;
+  m.occ0 = p.tile_occ0[tile];
+  m.bdd = p.tile_bdd0[tile] + m.team;
+  const bool valid = m.team < p.tile_nbdd[tile];
+  m.depth = valid ? p.bdd_depth[m.bdd] : 0;
+  m.lead_depth = m.tl == 0 ? m.depth : 0;
+  m.maxd = __reduce_max_sync(kFull, m.depth);
+  return m;
+}
+
+// Adjoint of a forward update sweep.  Descending layers: the node adjoint G of fm_l is pulled
+// from the children (the forward step into layer l+1), the marginal terms are added, and their
+// contributions to the starting backward messages of layer l+1 are pushed into g_node.  Then,
+// ascending, the adjoint of those backward messages runs back through their recursion into the
+// starting multipliers.
+template <int T>
+__device__ void fwd_adjoint_tile(const AdjParams &a, int tile) {
+  const SweepParams &p = a.sp;
+  const Team m = team_of<T>(p, tile);
+  const float ia = p.inv_alpha;
+  float G_next = 0.f, f_next = inf();
+  int node0_next = 0, w_next = 0;
+  for (int l = m.maxd - 1; l >= 0; --l) {
+    const bool active = m.depth > l;
+    const bool nxt = active && l + 1 < m.depth;
+    const int o = m.occ0 + occ_before(m.lead_depth, l) + m.team;
+    int node0 = 0, w = 0;
+    if (active) {
+      node0 = p.occ_node_off[o];
+      w = p.occ_node_off[o + 1] - node0;
+    }
+    const bool has = active && m.tl < w;
+    int2 lh = make_int2(kNone, kNone);
+    float f = inf();
+    if (has) {
+      lh = p.lohi[node0 + m.tl];
+      f = a.msg_new[node0 + m.tl];
+    }
+    const float lam1 = active ? a.lam_s[o] + a.shr_s[o] : 0.f;
+    const float lam2 = active ? a.lam2[o] : 0.f;
+    // pull the adjoint of fm_{l+1} through the forward step from layer l
+    const int lo_loc = nxt && lh.x >= 0 ? lh.x - node0_next : -1;
+    const int hi_loc = nxt && lh.y >= 0 ? lh.y - node0_next : -1;
+    const float Gc0 = __shfl_sync(kFull, G_next, m.tbase + ((lo_loc < 0 ? 0 : lo_loc) & (T - 1)));
+    const float fc0 = __shfl_sync(kFull, f_next, m.tbase + ((lo_loc < 0 ? 0 : lo_loc) & (T - 1)));
+    const float Gc1 = __shfl_sync(kFull, G_next, m.tbase + ((hi_loc < 0 ? 0 : hi_loc) & (T - 1)));
+    const float fc1 = __shfl_sync(kFull, f_next, m.tbase + ((hi_loc < 0 ? 0 : hi_loc) & (T - 1)));
+    float G = 0.f, g_theta = 0.f;
+    if (lo_loc >= 0) G += Gc0 * weight(f, fc0, ia);
+    if (hi_loc >= 0) {
+      g_theta = Gc1 * weight(f + lam2, fc1, ia);
+      G += g_theta;
+    }
+    const float G_lam2 = (active ? a.g_out_lam[o] : 0.f) + team_sum<T>(g_theta);
+    // marginals of layer l and the update
+    const float b0 = has ? target_msg(a.msg_pre, lh.x) : inf();
+    const float b1 = has ? target_msg(a.msg_pre, lh.y) : inf();
+    const float a0 = has ? f + b0 : inf(), a1 = has ? f + lam1 + b1 : inf();
+    const float m0 = team_agg<T, true>(a0, p), m1 = team_agg<T, true>(a1, p);
+    const bool finite = m0 < inf() && m1 < inf();
+    const int slot = active ? p.occ_slot[o] : 0;
+    const float g_delta = active ? a.g_out_delta[slot] : 0.f;
+    const float gd = finite ? p.omega * (g_delta - G_lam2) : 0.f;  // adjoint of m1 - m0
+    const float p0 = weight(a0, m0, ia), p1 = weight(a1, m1, ia);
+    G += -gd * p0 + gd * p1;
+    const float g_lam1 = G_lam2 + gd;  // d m1 / d lam' = 1
+    if (active && m.tl == 0) {
+      a.g_in_lam[o] = g_lam1;
+      a.g_shr[o] = g_lam1;
+    }
+    // contributions to the starting backward messages of layer l + 1
+    const int lo_rel = has && lh.x >= 0 && nxt ? lh.x - node0_next : kNone;
+    const int hi_rel = has && lh.y >= 0 && nxt ? lh.y - node0_next : kNone;
+    const float acc = team_push<T>(lo_rel, hi_rel, -gd * p0, gd * p1, m.tbase, m.tl);
+    if (nxt && m.tl < w_next) a.g_node[node0_next + m.tl] = acc;
+    G_next = has ? G : 0.f;
+    f_next = f;
+    node0_next = node0;
+    w_next = w;
+  }
+  __syncwarp();
+  // the starting backward messages: bmp_l(v) = softmin(bmp_{l+1}(lo), lam_l + bmp_{l+1}(hi)),
+  // adjoints flowing from layer l to layer l + 1
+  float carry = 0.f;
+  for (int l = 0; l < m.maxd; ++l) {
+    const bool active = m.depth > l;
+    const bool nxt = active && l + 1 < m.depth;
+    const int o = m.occ0 + occ_before(m.lead_depth, l) + m.team;
+    int node0 = 0, w = 0, node0n = 0;
+    if (active) {
+      node0 = p.occ_node_off[o];
+      w = p.occ_node_off[o + 1] - node0;
+    }
+    const int ob1 = occ_before(m.lead_depth, l + 1);  // warp-wide: outside the branch
+    if (nxt) node0n = p.occ_node_off[m.occ0 + ob1 + m.team];
+    const bool has = active && m.tl < w;
+    int2 lh = make_int2(kNone, kNone);
+    float bn = inf(), Gb = 0.f;
+    if (has) {
+      lh = p.lohi[node0 + m.tl];
+      bn = a.msg_pre[node0 + m.tl];
+      if (l >= 1) Gb = a.g_node[node0 + m.tl] + carry;
+    }
+    const float lam = active ? a.lam_s[o] : 0.f;
+    const float b0 = has ? target_msg(a.msg_pre, lh.x) : inf();
+    const float b1 = has ? target_msg(a.msg_pre, lh.y) : inf();
+    const float q0 = has ? weight(b0, bn, ia) : 0.f;
+    const float q1 = has ? weight(lam + b1, bn, ia) : 0.f;
+    const float gl = team_sum<T>(Gb * q1);
+    if (active && m.tl == 0) a.g_in_lam[o] += gl;
+    const int lo_rel = has && lh.x >= 0 && nxt ? lh.x - node0n : kNone;
+    const int hi_rel = has && lh.y >= 0 && nxt ? lh.y - node0n : kNone;
+    carry = team_push<T>(lo_rel, hi_rel, Gb * q0, Gb * q1, m.tbase, m.tl);
+  }
+}
+
+// Adjoint of a backward update sweep.  Ascending layers (the reverse of the sweep): the adjoint of
+// the new backward messages of layer l (seeded at the root with gE) runs through the backward
+// step and, with the marginal terms, is pushed to layer l + 1; the marginal terms' adjoints of
+// the starting forward messages go to g_node.  Then, descending, those run back through the
+// forward recursion into the starting multipliers.
+template <int T>
+__device__ void bwd_adjoint_tile(const AdjParams &a, int tile) {
+  const SweepParams &p = a.sp;
+  const Team m = team_of<T>(p, tile);
+  const float ia = p.inv_alpha;
+  float carry = 0.f;
+  for (int l = 0; l < m.maxd; ++l) {
+    const bool active = m.depth > l;
+    const bool nxt = active && l + 1 < m.depth;
+    const int o = m.occ0 + occ_before(m.lead_depth, l) + m.team;
+    int node0 = 0, w = 0, node0n = 0;
+    if (active) {
+      node0 = p.occ_node_off[o];
+      w = p.occ_node_off[o + 1] - node0;
+    }
+    const int ob1 = occ_before(m.lead_depth, l + 1);  // warp-wide: outside the branch
+    if (nxt) node0n = p.occ_node_off[m.occ0 + ob1 + m.team];
+    const bool has = active && m.tl < w;
+    int2 lh = make_int2(kNone, kNone);
+    float fp = inf(), bn = inf(), Gbn = 0.f;
+    if (has) {
+      lh = p.lohi[node0 + m.tl];
+      fp = a.msg_pre[node0 + m.tl];
+      bn = a.msg_new[node0 + m.tl];
+      Gbn = l == 0 ? (m.tl == 0 && a.gE ? (float)*a.gE : 0.f) : carry;
+    }
+    const float lam1 = active ? a.lam_s[o] + a.shr_s[o] : 0.f;
+    const float lam2 = active ? a.lam2[o] : 0.f;
+    const float b0 = has ? target_msg(a.msg_new, lh.x) : inf();
+    const float b1 = has ? target_msg(a.msg_new, lh.y) : inf();
+    // backward step bmn_l = softmin(b0, lam'' + b1)
+    const float q0 = has ? weight(b0, bn, ia) : 0.f;
+    const float q1 = has ? weight(lam2 + b1, bn, ia) : 0.f;
+    const float G_lam2 = (active ? a.g_out_lam[o] : 0.f) + team_sum<T>(Gbn * q1);
+    // marginals and the update
+    const float a0 = has ? fp + b0 : inf(), a1 = has ? fp + lam1 + b1 : inf();
+    const float m0 = team_agg<T, true>(a0, p), m1 = team_agg<T, true>(a1, p);
+    const bool finite = m0 < inf() && m1 < inf();
+    const int slot = active ? p.occ_slot[o] : 0;
+    const float g_delta = active ? a.g_out_delta[slot] : 0.f;
+    const float gd = finite ? p.omega * (g_delta - G_lam2) : 0.f;
+    const float p0 = weight(a0, m0, ia), p1 = weight(a1, m1, ia);
+    if (has) a.g_node[node0 + m.tl] = -gd * p0 + gd * p1;  // adjoint of fmp_l(v), marginal part
+    const float g_lam1 = G_lam2 + gd;
+    if (active && m.tl == 0) {
+      a.g_in_lam[o] = g_lam1;
+      a.g_shr[o] = g_lam1;
+    }
+    const int lo_rel = has && lh.x >= 0 && nxt ? lh.x - node0n : kNone;
+    const int hi_rel = has && lh.y >= 0 && nxt ? lh.y - node0n : kNone;
+    carry = team_push<T>(lo_rel, hi_rel, Gbn * q0 - gd * p0, Gbn * q1 + gd * p1, m.tbase, m.tl);
+  }
+  __syncwarp();
+  // the starting forward messages: fmp_l(v) = softmin over in-arcs of fmp_{l-1}(u) + theta,
+  // adjoints flowing from layer l + 1 back to layer l
+  float G_next = 0.f, f_next = inf();
+  int node0_next = 0;
+  for (int l = m.maxd - 1; l >= 0; --l) {
+    const bool active = m.depth > l;
+    const bool nxt = active && l + 1 < m.depth;
+    const int o = m.occ0 + occ_before(m.lead_depth, l) + m.team;
+    int node0 = 0, w = 0;
+    if (active) {
+      node0 = p.occ_node_off[o];
+      w = p.occ_node_off[o + 1] - node0;
+    }
+    const bool has = active && m.tl < w;
+    int2 lh = make_int2(kNone, kNone);
+    float f = inf(), G = 0.f;
+    if (has) {
+      lh = p.lohi[node0 + m.tl];
+      f = a.msg_pre[node0 + m.tl];
+      G = a.g_node[node0 + m.tl];
+    }
+    const float lam = active ? a.lam_s[o] : 0.f;
+    const int lo_loc = nxt && lh.x >= 0 ? lh.x - node0_next : -1;
+    const int hi_loc = nxt && lh.y >= 0 ? lh.y - node0_next : -1;
+    const float Gc0 = __shfl_sync(kFull, G_next, m.tbase + ((lo_loc < 0 ? 0 : lo_loc) & (T - 1)));
+    const float fc0 = __shfl_sync(kFull, f_next, m.tbase + ((lo_loc < 0 ? 0 : lo_loc) & (T - 1)));
+    const float Gc1 = __shfl_sync(kFull, G_next, m.tbase + ((hi_loc < 0 ? 0 : hi_loc) & (T - 1)));
+    const float fc1 = __shfl_sync(kFull, f_next, m.tbase + ((hi_loc < 0 ? 0 : hi_loc) & (T - 1)));
+    float g_theta = 0.f;
+    if (lo_loc >= 0) G += Gc0 * weight(f, fc0, ia);
+    if (hi_loc >= 0) {
+      g_theta = Gc1 * weight(f + lam, fc1, ia);
+      G += g_theta;
+    }
+    const float gl = team_sum<T>(g_theta);
+    if (active && m.tl == 0) a.g_in_lam[o] += gl;
+    G_next = has ? G : 0.f;
+    f_next = f;
+    node0_next = node0;
+  }
+}
+
+template <bool FWD>
+__device__ __forceinline__ void adjoint_tile(const AdjParams &a, int tile) {
+  int c = 0;
+  while (tile >= a.sp.class_tile_off[c + 1]) ++c;
+  switch (c) {
+#define BDD_ADJ_CASE(C, T)                    \
+  case C:                                     \
+    if (FWD) fwd_adjoint_tile<T>(a, tile);    \
+    else bwd_adjoint_tile<T>(a, tile);        \
+    break;
+    BDD_ADJ_CASE(0, 1)
+    BDD_ADJ_CASE(1, 2)
+    BDD_ADJ_CASE(2, 4)
+    BDD_ADJ_CASE(3, 8)
+    BDD_ADJ_CASE(4, 16)
+    BDD_ADJ_CASE(5, 32)
+#undef BDD_ADJ_CASE
+    default:
+      break;
+  }
+}
+
+}  // namespace
+
+template <bool FWD>
+__global__ void __launch_bounds__(kBlockThreads) sweep_adjoint_kernel(const AdjParams a) {
+  const int tile = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (tile >= a.sp.class_tile_off[kWarpClasses]) return;  // whole warp
+  adjoint_tile<FWD>(a, tile);
+}
+
+// Adjoint of the pending sums: share_o = P_i / |J_i| and P_i = sum of the previous sweep's
+// differences of i, so every slot of i receives (sum over i's occurrences of g_share) / |J_i|.
+__global__ void pending_adjoint_kernel(const int *__restrict__ var_ptr, const int *__restrict__ var_occ,
+                                       const float *__restrict__ g_shr, float *__restrict__ g_delta, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int s = var_ptr[i], e = var_ptr[i + 1];
+    if (e == s) continue;
+    float g = 0.f;
+    for (int k = s; k < e; ++k) g += g_shr[var_occ[k]];
+    g /= (float)(e - s);
+    for (int k = s; k < e; ++k) g_delta[k] = g;
+  }
+}
+
+// Seeds of the bound's adjoint.  The bound adds the soft slack term sl(P_i) = softmin(0, P_i)
+// of every variable in a row (adjoint exp(-(P_i - sl)/alpha) on each slot of i, whose
+// differences form P_i) and sl(c_i) of every variable in no row (adjoint into g_c directly).
+__global__ void bound_seed_kernel(const int *__restrict__ var_ptr, const float *__restrict__ P,
+                                  const float *__restrict__ c, float *__restrict__ g_delta, float *__restrict__ g_c,
+                                  int n, float alpha, const double *__restrict__ g_bound) {
+  const float scale = (float)*g_bound;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int s = var_ptr[i], e = var_ptr[i + 1];
+    const float x = e > s ? P[i] : c[i];
+    const float sl = fminf(x, 0.f) - alpha * log1pf(expf(-fabsf(x) / alpha));
+    const float g = scale * expf(-(x - sl) / alpha);
+    if (e > s) {
+      for (int k = s; k < e; ++k) g_delta[k] = g;
+    } else {
+      g_c[i] = g;
+    }
+  }
+}
+
+// lambda_0 = c_i / |J_i|: g_c_i = (sum over i's occurrences of g_lambda_0) / |J_i|
+__global__ void initial_adjoint_kernel(const int *__restrict__ var_ptr, const int *__restrict__ var_occ,
+                                       const float *__restrict__ g_lam0, float *__restrict__ g_c, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int s = var_ptr[i], e = var_ptr[i + 1];
+    if (e == s) continue;
+    float g = 0.f;
+    for (int k = s; k < e; ++k) g += g_lam0[var_occ[k]];
+    g_c[i] = g / (float)(e - s);
+  }
+}
+
+namespace {
+int grid_of(long long work) {
+  long long g = (work + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
+}
+int launch_status() { return cudaGetLastError() == cudaSuccess ? 0 : -5; }
+}  // namespace
+
+int sweep_adjoint_launch(bool forward, const AdjParams &a, int grid, cudaStream_t stream) {
+  if (grid <= 0) return 0;
+  if (forward)
+    sweep_adjoint_kernel<true><<<grid, kBlockThreads, 0, stream>>>(a);
+  else
+    sweep_adjoint_kernel<false><<<grid, kBlockThreads, 0, stream>>>(a);
+  return launch_status();
+}
+
+int pending_adjoint_launch(const int *var_ptr, const int *var_occ, const float *g_shr, float *g_delta, int n,
+                           cudaStream_t stream) {
+  if (n == 0) return 0;
+  pending_adjoint_kernel<<<grid_of(n), 256, 0, stream>>>(var_ptr, var_occ, g_shr, g_delta, n);
+  return launch_status();
+}
+
+int bound_seed_launch(const int *var_ptr, const float *P, const float *c, float *g_delta, float *g_c, int n,
+                      float alpha, const double *g_bound, cudaStream_t stream) {
+  if (n == 0) return 0;
+  bound_seed_kernel<<<grid_of(n), 256, 0, stream>>>(var_ptr, P, c, g_delta, g_c, n, alpha, g_bound);
+  return launch_status();
+}
+
+int initial_adjoint_launch(const int *var_ptr, const int *var_occ, const float *g_lam0, float *g_c, int n,
+                           cudaStream_t stream) {
+  if (n == 0) return 0;
+  initial_adjoint_kernel<<<grid_of(n), 256, 0, stream>>>(var_ptr, var_occ, g_lam0, g_c, n);
+  return launch_status();
+}
+
+}  // namespace bdd

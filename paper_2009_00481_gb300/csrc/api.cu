@@ -71,6 +71,7 @@ struct bdd_solver {
   // device
   int device = -1;
   float omega = 0.5f;
+  float alpha = 0.f;  // smoothing temperature (0: min-sum)
   cudaStream_t stream = nullptr, cap_stream = nullptr;
   bool own_stream = false;
   long long max_device_bytes = 0, device_bytes = 0;
@@ -106,6 +107,15 @@ struct bdd_solver {
   int grid_sweep = 0, n_warp_blocks = 0, grid_reduce = 1;
   size_t smem = 0, smem_persist = 0;
   cudaGraphExec_t g_many = nullptr, g_one = nullptr;
+  // smoothed bound and its gradient: per-sweep checkpoints and scratch (allocated on first use)
+  int smooth_cap = 0;           // sweeps the checkpoint buffers hold
+  int smooth_K = 0;             // iterations of the recorded forward (0: none)
+  long long state_gen = 0;      // bumped by every call that changes the dual state
+  long long smooth_gen = -1;    // state_gen right after the recorded forward
+  float *ck_lam = nullptr, *ck_shr = nullptr;
+  float *t_lam = nullptr, *t_nodeA = nullptr, *t_nodeB = nullptr, *t_gnode = nullptr;
+  float *t_glam0 = nullptr, *t_glam1 = nullptr, *t_gshr = nullptr, *t_gdelta = nullptr;
+  float *t_delta = nullptr, *t_E = nullptr;
   cudaEvent_t ev_last = nullptr;  // end of the solver's last enqueued work, on whatever stream
 
   ~bdd_solver() {
@@ -156,6 +166,8 @@ struct bdd_solver {
     p.block_buf = block_buf;
     p.block_depth_buf = block_depth_buf;
     p.omega = omega;
+    p.alpha = alpha;
+    p.inv_alpha = alpha > 0.f ? 1.f / alpha : 0.f;
     return p;
   }
 
@@ -175,6 +187,7 @@ struct bdd_solver {
     r.n = n;
     r.nb = (int)nb;
     r.empty_const = empty_const;
+    r.alpha = alpha;
     return r;
   }
 
@@ -416,10 +429,14 @@ bool finite_costs(const float *c, int n) {
   return true;
 }
 
-double empty_constant(const std::vector<int> &deg, const float *c, int n) {
+// sum over variables in no row of the y-slack term min(0, c_i) (its soft minimum for alpha > 0)
+double empty_constant(const std::vector<int> &deg, const float *c, int n, double alpha) {
   double s = 0.0;
-  for (int i = 0; i < n; ++i)
-    if (deg[i] == 0 && c[i] < 0.f) s += (double)c[i];
+  for (int i = 0; i < n; ++i) {
+    if (deg[i] != 0) continue;
+    const double x = c[i], m = x < 0.0 ? x : 0.0;
+    s += alpha > 0.0 ? m - alpha * std::log1p(std::exp(-std::fabs(x) / alpha)) : m;
+  }
   return s;
 }
 
@@ -438,6 +455,7 @@ void bdd_default_options(bdd_options *opt) {
   opt->stream = nullptr;
   opt->schedule = 1;
   opt->spin_limit = 1LL << 26;
+  opt->alpha = 0.f;
 }
 
 int bdd_last_failed_row(void) { return g_failed_row; }
@@ -452,6 +470,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   if (opt_in) opt = *opt_in;
   if (n < 0 || m < 0 || (m > 0 && (!row_ptr || !b || !sense)) || (n > 0 && !c)) return BDD_EINVAL;
   if (!(opt.omega > 0.f && opt.omega <= 1.f) || opt.max_width < 1 || opt.max_nodes < 1) return BDD_EINVAL;
+  if (!(opt.alpha >= 0.f) || !std::isfinite(opt.alpha)) return BDD_EINVAL;
   if (m > 0 && row_ptr[0] != 0) return BDD_EINVAL;
   for (int j = 0; j < m; ++j)
     if (row_ptr[j + 1] < row_ptr[j]) {
@@ -468,7 +487,8 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   h->m = m;
   h->nnz = nnz;
   h->omega = opt.omega;
-  h->schedule = opt.schedule;
+  h->alpha = opt.alpha;
+  h->schedule = opt.alpha > 0.f ? 1 : opt.schedule;  // the persistent kernel runs min-sum only
   h->spin_limit = opt.spin_limit;
   if (opt.schedule < 0 || opt.schedule > 1 || opt.spin_limit < 1) {
     delete h;
@@ -502,7 +522,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   h->var_deg.assign(n, 0);
   for (int v : H.occ_var) h->var_deg[v]++;
   h->c.assign(c, c + n);
-  h->empty_const = empty_constant(h->var_deg, c, n);
+  h->empty_const = empty_constant(h->var_deg, c, n, h->alpha);
   if (h->host_only && !h->host_layout) {
     *out = h;
     return BDD_OK;
@@ -513,6 +533,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   } catch (const std::bad_alloc &) {
     rc = BDD_ENOMEM;
   }
+  if (rc == BDD_OK && h->alpha > 0.f && L.n_block_tiles > 0) rc = BDD_ETOOBIG;  // smoothing: warp tiles only
   if (rc != BDD_OK) {
     delete h;
     return rc;
@@ -574,6 +595,7 @@ int bdd_iterate_device(bdd_solver *h, int n_iter, double *d_bound_trace, float *
     if (!h->g_many && n_iter >= kGraphIters) RC(h->capture(kGraphIters, &h->g_many));
   }
   RC(h->begin(s));
+  if (n_iter > 0) ++h->state_gen;
   if (h->schedule == 0) {
     if (n_iter > 0) RC(h->launch_persistent(n_iter, s));
   } else {
@@ -600,6 +622,7 @@ int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms) {
   for (int t = 0; t < 4; ++t) kernel_ms[t] = 0.0;
   RC(h->ensure_trace(n_iter + 1));
   RC(h->begin(s));
+  ++h->state_gen;
   CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
   const int kBatch = 256;  // iterations per batch of recorded events
   std::vector<cudaEvent_t> ev(5 * kBatch, nullptr);
@@ -667,17 +690,141 @@ int bdd_set_costs(bdd_solver *h, const float *c) {
   if (!h || (h->n > 0 && !c)) return BDD_EINVAL;
   if (!finite_costs(c, h->n)) return BDD_EINVAL;
   h->c.assign(c, c + h->n);
-  h->empty_const = empty_constant(h->var_deg, c, h->n);
+  h->empty_const = empty_constant(h->var_deg, c, h->n, h->alpha);
   if (h->host_only) return BDD_OK;
   DeviceGuard dg(h->device);
   if (!dg.ok) return BDD_ECUDA;
   RC(h->begin(h->stream));
+  ++h->state_gen;
   if (h->n) CK(cudaMemcpyAsync(h->d_c, c, sizeof(float) * h->n, cudaMemcpyHostToDevice, h->stream));
   h->drop_graphs();  // the bound constant is baked into the captured reductions
   RC(h->restart(h->stream));
   RC(h->end(h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return BDD_OK;
+}
+
+int bdd_smooth_forward(bdd_solver *h, int K, const float *d_c, double *d_bound, void *stream) {
+  if (!h || K < 1 || (h->n > 0 && !d_c) || !d_bound) return BDD_EINVAL;
+  if (h->host_only) return BDD_ESTATE;
+  if (!(h->alpha > 0.f)) return BDD_ESTATE;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return BDD_ECUDA;
+  cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+  const long long O = h->O, N = h->N;
+  if (2 * K > h->smooth_cap) {  // checkpoints of every sweep; the old buffers stay owned by allocs
+    RC(h->alloc(&h->ck_lam, 2LL * K * std::max<long long>(O, 1)));
+    RC(h->alloc(&h->ck_shr, 2LL * K * std::max<long long>(O, 1)));
+    h->smooth_cap = 2 * K;
+  }
+  if (!h->t_lam) {
+    RC(h->alloc(&h->t_lam, O));
+    RC(h->alloc(&h->t_nodeA, N));
+    RC(h->alloc(&h->t_nodeB, N));
+    RC(h->alloc(&h->t_gnode, N));
+    RC(h->alloc(&h->t_glam0, O));
+    RC(h->alloc(&h->t_glam1, O));
+    RC(h->alloc(&h->t_gshr, O));
+    RC(h->alloc(&h->t_gdelta, O));
+    RC(h->alloc(&h->t_delta, O));
+    RC(h->alloc(&h->t_E, h->nb));
+  }
+  RC(h->ensure_trace(K + 1));
+  RC(h->begin(s));
+  // costs: on the device for the iteration, on the host for the constant of empty variables
+  std::vector<float> c(h->n);
+  if (h->n) {
+    CK(cudaMemcpyAsync(h->d_c, d_c, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c.data(), d_c, sizeof(float) * h->n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!finite_costs(c.data(), h->n)) return BDD_EINVAL;
+  }
+  h->c = c;
+  h->empty_const = empty_constant(h->var_deg, c.data(), h->n, h->alpha);
+  h->drop_graphs();
+  RC(h->restart(s));
+  CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
+  const size_t ob = sizeof(float) * (size_t)std::max<long long>(O, 1);
+  for (int it = 0; it < K; ++it) {
+    for (int half = 0; half < 2; ++half) {
+      const long long sw = 2LL * it + half;
+      if (O) {
+        CK(cudaMemcpyAsync(h->ck_lam + sw * O, h->d_lam, ob, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(h->ck_shr + sw * O, h->d_share_occ, ob, cudaMemcpyDeviceToDevice, s));
+      }
+      RC(h->sweep(half == 0, kUpdate, s));
+      RC(h->pending(half == 1, s));
+    }
+  }
+  CK(cudaMemcpyAsync(d_bound, h->d_trace + (K - 1), sizeof(double), cudaMemcpyDeviceToDevice, s));
+  ++h->state_gen;
+  h->smooth_gen = h->state_gen;
+  h->smooth_K = K;
+  return h->end(s);
+}
+
+int bdd_smooth_backward(bdd_solver *h, const double *d_gbound, float *d_grad_c, void *stream) {
+  if (!h || !d_gbound || (h->n > 0 && !d_grad_c)) return BDD_EINVAL;
+  if (h->host_only) return BDD_ESTATE;
+  if (h->smooth_K < 1 || h->smooth_gen != h->state_gen) return BDD_ESTATE;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return BDD_ECUDA;
+  cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+  const long long O = h->O;
+  const int K = h->smooth_K;
+  const size_t ob = sizeof(float) * (size_t)std::max<long long>(O, 1);
+  RC(h->begin(s));
+  // seeds: the slack terms of the last pending sums (and of empty variables), E^j of every BDD
+  if (h->n) CK(cudaMemsetAsync(d_grad_c, 0, sizeof(float) * h->n, s));
+  CK(cudaMemsetAsync(h->t_gdelta, 0, ob, s));
+  CK(cudaMemsetAsync(h->t_glam1, 0, ob, s));
+  if (bound_seed_launch(h->d_var_ptr, h->d_P, h->d_c, h->t_gdelta, d_grad_c, h->n, h->alpha, d_gbound, s))
+    return BDD_ECUDA;
+  float *g_next = h->t_glam1, *g_cur = h->t_glam0;  // adjoint of the multipliers after / before a sweep
+  for (long long sw = 2LL * K - 1; sw >= 0; --sw) {
+    const bool fwd = (sw % 2) == 0;
+    const float *lam_s = h->ck_lam + sw * O, *shr_s = h->ck_shr + sw * O;
+    // recompute the sweep from its checkpoint into scratch buffers: starting messages, then the
+    // sweep itself (multipliers, messages), the solver's own state untouched
+    if (O) CK(cudaMemcpyAsync(h->t_lam, lam_s, ob, cudaMemcpyDeviceToDevice, s));
+    SweepParams p = h->sweep_params();
+    p.lam = h->t_lam;
+    p.share_occ = shr_s;
+    p.delta = h->t_delta;
+    p.bdd_E = h->t_E;
+    if (fwd) {
+      p.bm = h->t_nodeA;
+      p.fm = h->t_nodeB;
+      if (sweep_launch(false, kMessages, p, h->grid_sweep, s)) return BDD_ECUDA;
+      if (sweep_launch(true, kUpdate, p, h->grid_sweep, s)) return BDD_ECUDA;
+    } else {
+      p.fm = h->t_nodeA;
+      p.bm = h->t_nodeB;
+      if (sweep_launch(true, kMessages, p, h->grid_sweep, s)) return BDD_ECUDA;
+      if (sweep_launch(false, kUpdate, p, h->grid_sweep, s)) return BDD_ECUDA;
+    }
+    AdjParams a;
+    a.sp = h->sweep_params();
+    a.lam_s = lam_s;
+    a.shr_s = shr_s;
+    a.lam2 = h->t_lam;
+    a.msg_pre = h->t_nodeA;
+    a.msg_new = h->t_nodeB;
+    a.g_out_lam = g_next;
+    a.g_out_delta = h->t_gdelta;
+    a.g_in_lam = g_cur;
+    a.g_shr = h->t_gshr;
+    a.g_node = h->t_gnode;
+    a.gE = sw == 2LL * K - 1 ? d_gbound : nullptr;
+    if (sweep_adjoint_launch(fwd, a, h->n_warp_blocks, s)) return BDD_ECUDA;
+    // the shares of this sweep were formed from the previous sweep's differences
+    if (sw > 0 && pending_adjoint_launch(h->d_var_ptr, h->d_var_occ, h->t_gshr, h->t_gdelta, h->n, s))
+      return BDD_ECUDA;
+    std::swap(g_cur, g_next);
+  }
+  // lambda_0 = c / |J_i|
+  if (initial_adjoint_launch(h->d_var_ptr, h->d_var_occ, g_next, d_grad_c, h->n, s)) return BDD_ECUDA;
+  return h->end(s);
 }
 
 int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]) {
@@ -799,6 +946,7 @@ int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending) {
   cudaStream_t s = h->stream;
   RC(h->ensure_outputs());
   RC(h->begin(s));
+  ++h->state_gen;
   if (h->nnz) CK(cudaMemcpyAsync(h->d_out_lam, lambda, sizeof(float) * h->nnz, cudaMemcpyHostToDevice, s));
   if (h->O && gather_lambda_launch(h->d_out_lam, h->d_occ_csr, h->d_lam, (int)h->O, s)) return BDD_ECUDA;
   if (h->n) {

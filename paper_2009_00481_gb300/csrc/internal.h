@@ -114,6 +114,8 @@ struct SweepParams {
   int block_buf;        // floats per shared-memory layer buffer of a block tile
   int block_depth_buf;  // floats for the per-layer shares of a block tile
   float omega;
+  float alpha;          // smoothing temperature (0: min-sum)
+  float inv_alpha;
 };
 
 // Sweep modes.
@@ -142,6 +144,7 @@ struct PendingParams {
   int n;
   int nb;
   double empty_const;
+  double alpha;  // smoothing temperature of the slack term (0: min-sum)
 };
 
 // Persistent iteration kernel (one cooperative launch runs n_iter iterations).
@@ -161,6 +164,31 @@ struct IterParams {
   double empty_const;
   long long spin_limit;
 };
+
+// Adjoint of one smoothed update sweep (adjoint.cu): checkpointed inputs, recomputed outputs and
+// messages, output adjoints in, input adjoints out.
+struct AdjParams {
+  SweepParams sp;
+  const float *lam_s;        // multipliers at the sweep's start (checkpoint)
+  const float *shr_s;        // shares the sweep added (checkpoint)
+  const float *lam2;         // multipliers after the sweep (recomputed)
+  const float *msg_pre;      // starting backward (forward sweep) / forward (backward sweep) messages
+  const float *msg_new;      // messages the sweep computed: fm (forward) / bm (backward)
+  const float *g_out_lam;    // adjoint of the multipliers after the sweep
+  const float *g_out_delta;  // adjoint of the recorded differences, by slot
+  float *g_in_lam;           // adjoint of the multipliers at the sweep's start
+  float *g_shr;              // adjoint of the shares
+  float *g_node;             // per-node scratch
+  const double *gE;          // adjoint of every BDD's root message (the last backward sweep), or null
+};
+
+int sweep_adjoint_launch(bool forward, const AdjParams &a, int grid, cudaStream_t stream);
+int pending_adjoint_launch(const int *var_ptr, const int *var_occ, const float *g_shr, float *g_delta, int n,
+                           cudaStream_t stream);
+int bound_seed_launch(const int *var_ptr, const float *P, const float *c, float *g_delta, float *g_c, int n,
+                      float alpha, const double *g_bound, cudaStream_t stream);
+int initial_adjoint_launch(const int *var_ptr, const int *var_occ, const float *g_lam0, float *g_c, int n,
+                           cudaStream_t stream);
 
 // Launch wrappers (kernels.cu).  All enqueue on `stream` and return 0 or -5 (launch failure).
 size_t sweep_smem_bytes(int block_buf, int block_depth_buf);

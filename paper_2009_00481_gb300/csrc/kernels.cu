@@ -22,14 +22,11 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "device_common.cuh"
 
 namespace bdd {
 
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
 
 // backward message of an arc target: top -> 0, bot / none -> +inf, node -> bm
 __device__ __forceinline__ float target_bm(const float *__restrict__ bm, int t) {
@@ -50,13 +47,6 @@ __device__ __forceinline__ void atomic_min_f(float *addr, float v) {
     atomicMin(reinterpret_cast<int *>(addr), __float_as_int(v));
   else
     atomicMax(reinterpret_cast<unsigned *>(addr), __float_as_uint(v));
-}
-
-template <int T>
-__device__ __forceinline__ float team_min(float v) {
-#pragma unroll
-  for (int off = T / 2; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, off));
-  return v;
 }
 
 __device__ __forceinline__ float mm_difference(float m0, float m1) {
@@ -121,11 +111,6 @@ __device__ __forceinline__ float slot_sum(const float *__restrict__ d, int s, in
 // with independent coalesced loads before its layers are processed, so the layer recurrence
 // runs on shared memory and registers only.
 // ---------------------------------------------------------------------------------------
-// occurrences of the tile before layer l: sum over the tile's BDDs of min(depth, l)
-__device__ __forceinline__ int occ_before(int lead_depth, int l) {
-  return __reduce_add_sync(kFull, min(lead_depth, l));
-}
-
 template <int MODE>
 __device__ __forceinline__ void stage_occurrences(const SweepParams &p, const Phase &ph, WarpStage &S, int oa,
                                                   int nob, int nox, double &bacc) {
@@ -142,7 +127,7 @@ __device__ __forceinline__ void stage_occurrences(const SweepParams &p, const Ph
   cp_async_wait();
 }
 
-template <int T, int MODE>
+template <int T, int MODE, bool SMOOTH>
 __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &ph, int tile, WarpStage &S,
                                              double &bacc) {
   const int lane = threadIdx.x & 31;
@@ -193,8 +178,8 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
           const float mf = __shfl_sync(kFull, f_prev, tbase + s);
           const int ls = __shfl_sync(kFull, lo_l, tbase + s);
           const int hs = __shfl_sync(kFull, hi_l, tbase + s);
-          if (ls == tl) f = fminf(f, mf);
-          if (hs == tl) f = fminf(f, mf + lam_prev);
+          if (ls == tl) f = agg<SMOOTH>(f, mf, p);
+          if (hs == tl) f = agg<SMOOTH>(f, mf + lam_prev, p);
         }
       }
       int2 lh = make_int2(kNone, kNone);
@@ -207,7 +192,7 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
         // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
         const float a0 = has ? f + staged_bm(S.msg, na, lh.x) : inf();
         const float a1 = has ? f + lam + staged_bm(S.msg, na, lh.y) : inf();
-        const float m0 = team_min<T>(a0), m1 = team_min<T>(a1);
+        const float m0 = team_agg<T, SMOOTH>(a0, p), m1 = team_agg<T, SMOOTH>(a1, p);
         const float dd = p.omega * mm_difference(m0, m1);
         lam -= dd;
         if (active && tl == 0) {
@@ -222,7 +207,7 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
   }
 }
 
-template <int T, int MODE>
+template <int T, int MODE, bool SMOOTH>
 __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase &ph, int tile, WarpStage &S,
                                               double &bacc) {
   const int lane = threadIdx.x & 31;
@@ -273,7 +258,7 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
       const float b0 = lh.x >= 0 ? g0 : (lh.x == kTop ? 0.f : inf());
       const float b1 = lh.y >= 0 ? g1 : (lh.y == kTop ? 0.f : inf());
       if (MODE != kMessages) {
-        const float m0 = team_min<T>(f + b0), m1 = team_min<T>(f + lam + b1);
+        const float m0 = team_agg<T, SMOOTH>(f + b0, p), m1 = team_agg<T, SMOOTH>(f + lam + b1, p);
         if (MODE == kUpdate) {
           const float dd = p.omega * mm_difference(m0, m1);
           lam -= dd;
@@ -288,7 +273,7 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
         }
       }
       // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
-      const float bcur = fminf(b0, lam + b1);
+      const float bcur = agg<SMOOTH>(b0, lam + b1, p);
       if (has) p.bm[node0 + tl] = bcur;
       if (l == 0 && active && tl == 0) {  // E^j(lambda^j) at the root
         p.bdd_E[bdd] = bcur;
@@ -461,7 +446,7 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
   }
 }
 
-template <bool FWD, int MODE>
+template <bool FWD, int MODE, bool SMOOTH>
 __device__ __forceinline__ void warp_tile(const SweepParams &p, const Phase &ph, int tile, WarpStage &S,
                                           double &bacc) {
   int c = 0;
@@ -469,8 +454,8 @@ __device__ __forceinline__ void warp_tile(const SweepParams &p, const Phase &ph,
   switch (c) {
 #define BDD_TEAM_CASE(C, T)                                   \
   case C:                                                     \
-    if (FWD) warp_forward<T, MODE>(p, ph, tile, S, bacc);     \
-    else warp_backward<T, MODE>(p, ph, tile, S, bacc);        \
+    if (FWD) warp_forward<T, MODE, SMOOTH>(p, ph, tile, S, bacc);  \
+    else warp_backward<T, MODE, SMOOTH>(p, ph, tile, S, bacc);     \
     break;
     BDD_TEAM_CASE(0, 1)
     BDD_TEAM_CASE(1, 2)
@@ -501,7 +486,7 @@ __device__ __forceinline__ double block_sum(double v, double *red, int nwarps) {
 // ---------------------------------------------------------------------------------------
 // per-phase kernels
 // ---------------------------------------------------------------------------------------
-template <bool FWD, int MODE>
+template <bool FWD, int MODE, bool SMOOTH>
 __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams p) {
   extern __shared__ __align__(16) float smem[];
   pdl_enter();
@@ -510,8 +495,8 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
   if ((int)blockIdx.x < p.n_warp_blocks) {
     const int tile = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (tile >= p.class_tile_off[kWarpClasses]) return;  // whole warp leaves together
-    warp_tile<FWD, MODE>(p, ph, tile, reinterpret_cast<WarpStage *>(smem)[threadIdx.x >> 5], bacc);
-  } else {
+    warp_tile<FWD, MODE, SMOOTH>(p, ph, tile, reinterpret_cast<WarpStage *>(smem)[threadIdx.x >> 5], bacc);
+  } else if constexpr (!SMOOTH) {  // smoothed solvers have warp tiles only
     const int tile = p.class_tile_off[kWarpClasses] + (blockIdx.x - p.n_warp_blocks);
     if (tile >= p.class_tile_off[kWarpClasses + 1]) return;  // uniform across the block
     const GroupSmem g = group_smem(smem, p);
@@ -520,6 +505,13 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
     else
       block_backward<MODE>(p, ph, tile, g, 0, threadIdx.x, bacc);
   }
+}
+
+// y-slack term of one variable: min(0, P) for min-sum, its soft minimum for alpha > 0 (FP64)
+__device__ __forceinline__ double slack_term(double P, double alpha) {
+  if (alpha <= 0.0) return P < 0.0 ? P : 0.0;
+  const double m = P < 0.0 ? P : 0.0;
+  return m - alpha * log1p(exp(-fabs(P) / alpha));
 }
 
 // Pending sums (the sum in eq. mma-update, deferred): P_i = sum of i's slots in ascending
@@ -556,7 +548,7 @@ __global__ void __launch_bounds__(kReduceThreads) pending_kernel(const PendingPa
     if (i < p.n) {
       bool has;
       const float Pi = pending_var(p.delta, p.var_ptr, p.var_occ, p.P, p.share_occ, i, has);
-      if (BOUND && has && Pi < 0.f) acc += (double)Pi;
+      if (BOUND && has) acc += slack_term((double)Pi, p.alpha);
     }
     if (BOUND && i < p.nb) acc += (double)p.bdd_E[i];
   }
@@ -639,7 +631,7 @@ __device__ __forceinline__ void persistent_phase(const SweepParams &p, float *sm
   const int nwt = p.class_tile_off[kWarpClasses];
   WarpStage &S = reinterpret_cast<WarpStage *>(smem)[warp];
   for (int tile = blockIdx.x * kPersistWarps + warp; tile < nwt; tile += W)
-    warp_tile<FWD, kUpdate>(p, ph, tile, S, bacc);
+    warp_tile<FWD, kUpdate, false>(p, ph, tile, S, bacc);
   const int bt0 = p.class_tile_off[kWarpClasses];
   const int nbt = p.class_tile_off[kWarpClasses + 1] - bt0;
   if (nbt > 0) {
@@ -807,7 +799,9 @@ int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStr
   if (grid <= 0) return 0;
   const size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf);
   int rc = 0;
-#define BDD_SWEEP(F, M) rc = launch_pdl(sweep_kernel<F, M>, grid, kBlockThreads, smem, stream, p)
+#define BDD_SWEEP(F, M)                                                                          \
+  rc = p.alpha > 0.f ? launch_pdl(sweep_kernel<F, M, true>, grid, kBlockThreads, smem, stream, p)    \
+                     : launch_pdl(sweep_kernel<F, M, false>, grid, kBlockThreads, smem, stream, p)
   if (forward) {
     if (mode == kUpdate) BDD_SWEEP(true, kUpdate);
     else if (mode == kMessages) BDD_SWEEP(true, kMessages);
@@ -823,9 +817,12 @@ int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStr
 
 int sweep_set_smem(size_t bytes) {
   const void *fns[] = {
-      (const void *)sweep_kernel<true, kUpdate>,   (const void *)sweep_kernel<true, kMessages>,
-      (const void *)sweep_kernel<true, kFolded>,   (const void *)sweep_kernel<false, kUpdate>,
-      (const void *)sweep_kernel<false, kMessages>, (const void *)sweep_kernel<false, kFolded>};
+      (const void *)sweep_kernel<true, kUpdate, false>,    (const void *)sweep_kernel<true, kMessages, false>,
+      (const void *)sweep_kernel<true, kFolded, false>,    (const void *)sweep_kernel<false, kUpdate, false>,
+      (const void *)sweep_kernel<false, kMessages, false>, (const void *)sweep_kernel<false, kFolded, false>,
+      (const void *)sweep_kernel<true, kUpdate, true>,     (const void *)sweep_kernel<true, kMessages, true>,
+      (const void *)sweep_kernel<true, kFolded, true>,     (const void *)sweep_kernel<false, kUpdate, true>,
+      (const void *)sweep_kernel<false, kMessages, true>,  (const void *)sweep_kernel<false, kFolded, true>};
   for (const void *f : fns)
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
       return -5;

@@ -13,12 +13,15 @@ class Solver:
     """BDDs of a 0-1 ILP on the GPU.
 
     ``inst`` needs attributes n, m, row_ptr, col, val, b, sense, c (CSR form; see
-    ``include/bdd_dbca.h``).  ``omega`` damps the min-marginal difference.
+    ``include/bdd_dbca.h``).  ``omega`` damps the min-marginal difference; ``alpha > 0`` selects
+    the smoothed (log-sum-exp) variant.
     """
 
     def __init__(self, inst, omega: float = 0.5, host_only: bool = False, max_device_bytes: int = 0,
-                 device: int = -1, stream: int = 0, schedule: int = 1, spin_limit: int = 0):
+                 device: int = -1, stream: int = 0, schedule: int = 1, spin_limit: int = 0,
+                 alpha: float = 0.0):
         opt = B.bdd_default_options()
+        opt.alpha = float(alpha)
         opt.schedule = int(schedule)
         if spin_limit:
             opt.spin_limit = int(spin_limit)

@@ -1,0 +1,174 @@
+"""GPU parity of the smoothed (log-sum-exp) variant (Appendix A.5) against the FP64 oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from instances import config, potts_mrf, sparse_matching, tomography, tracking
+from oracle import Oracle
+from tests.test_gpu_parity import LB_TOL, MM_TOL, _trace, close
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "potts_8x8x3": lambda: potts_mrf(8, 8, 3, seed=2),
+    "tracking_10x40": lambda: tracking(frames=10, dets=40, seed=1),
+    "matching_small": lambda: sparse_matching(n_left=60, n_right=50, k=6, n_pairs=800, seed=3),
+}
+
+
+@pytest.fixture(scope="module")
+def lib(cuda_lib):
+    import torch
+    assert torch.cuda.is_available()
+    return cuda_lib
+
+
+def solver(inst, **kw):
+    from paper_2009_00481_gb300 import Solver
+    return Solver(inst, **kw)
+
+
+@pytest.mark.parametrize("alpha", [0.1, 0.5])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_smoothed_trace_parity(lib, name, alpha):
+    inst = CASES[name]()
+    o = Oracle(inst)
+    o.set_alpha(alpha)
+    want = o.run_parallel(60, omega=0.5)
+    got = _trace(solver(inst, alpha=alpha), 60)
+    close(got[-1:], want[-1:], LB_TOL)
+    close(got[:10], want[:10], LB_TOL)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_smoothed_marginals_same_lambda(lib, name):
+    inst = CASES[name]()
+    alpha = 0.2
+    rng = np.random.default_rng(9)
+    lam = rng.normal(0, 1, size=inst.nnz).astype(np.float32)
+    s = solver(inst, alpha=alpha)
+    s.set_state(lam)
+    lb, _, m0, m1 = s.iterate(0, mm=True)
+    o = Oracle(inst)
+    o.set_alpha(alpha)
+    o.set_state(lam.astype(np.float64))
+    e0, e1 = o.min_marginals(fold=True)
+    close(m0, e0, MM_TOL)
+    close(m1, e1, MM_TOL)
+    close([lb], [o.bound()], MM_TOL)
+
+
+def test_small_alpha_recovers_min_sum(lib):
+    inst = config(0)
+    plain = _trace(solver(inst), 40)
+    soft = _trace(solver(inst, alpha=1e-5), 40)
+    close(soft, plain, LB_TOL)
+
+
+def test_smoothing_rejects_wide_bdds(lib):
+    from paper_2009_00481_gb300 import BDDError
+    from paper_2009_00481_gb300.binding import BDD_ETOOBIG
+    with pytest.raises(BDDError) as e:
+        solver(tomography(side=32, seed=1), alpha=0.1)
+    assert e.value.code == BDD_ETOOBIG
+
+
+# ------------------------------------------------------------------------------------------
+# gradient of the smoothed bound (hand-written adjoints) against FP64 central differences
+# ------------------------------------------------------------------------------------------
+
+def _oracle_smoothed_bound(inst, c, alpha, K):
+    import copy
+    j = copy.copy(inst)
+    j.c = np.asarray(c, np.float64)
+    o = Oracle(j)
+    o.set_alpha(alpha)
+    return float(o.run_parallel(K, omega=0.5)[-1])
+
+
+def _gpu_value_and_grad(inst, c, alpha, K):
+    import torch
+    from paper_2009_00481_gb300 import smoothed_bound
+    s = solver(inst, alpha=alpha)
+    ct = torch.tensor(np.asarray(c, np.float32), device="cuda", requires_grad=True)
+    val = smoothed_bound(ct, s, K)
+    val.backward()
+    torch.cuda.synchronize()
+    return float(val.item()), ct.grad.detach().cpu().numpy().astype(np.float64), s
+
+
+@pytest.mark.parametrize("alpha", [0.1, 0.5])
+def test_gradient_matches_oracle_central_differences(lib, alpha):
+    """d(bound)/dc of the smoothed bound after K = 50 iterations on the 5-frame x 20-detection
+    tracking slice: GPU adjoint (FP32) against FP64 central differences of the oracle's bound,
+    on 48 sampled coordinates (plus the bound value itself)."""
+    inst = tracking(frames=5, dets=20, seed=0)
+    K = 50
+    c = inst.c.astype(np.float64)
+    val, grad, _ = _gpu_value_and_grad(inst, c, alpha, K)
+    want = _oracle_smoothed_bound(inst, c, alpha, K)
+    close([val], [want], LB_TOL)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(inst.n, size=48, replace=False)
+    h = 1e-4
+    fd = np.zeros(len(idx))
+    for t, i in enumerate(idx):
+        cp, cm = c.copy(), c.copy()
+        cp[i] += h
+        cm[i] -= h
+        fd[t] = (_oracle_smoothed_bound(inst, cp, alpha, K) - _oracle_smoothed_bound(inst, cm, alpha, K)) / (2 * h)
+    scale = max(1.0, np.abs(fd).max())
+    err = np.abs(grad[idx] - fd) / scale
+    assert err.max() < 5e-3, (err.max(), np.c_[idx, grad[idx], fd][np.argsort(-err)[:5]])
+
+
+def test_gradient_directional_derivative(lib):
+    """The full gradient against a GPU directional difference along a random direction."""
+    inst = potts_mrf(6, 6, 3, seed=5)
+    alpha, K = 0.2, 20
+    c = inst.c.astype(np.float64)
+    val, grad, _ = _gpu_value_and_grad(inst, c, alpha, K)
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=inst.n)
+    eps = 1e-2
+    vp = _oracle_smoothed_bound(inst, c + eps * v, alpha, K)
+    vm = _oracle_smoothed_bound(inst, c - eps * v, alpha, K)
+    dd = (vp - vm) / (2 * eps)
+    assert abs(grad @ v - dd) <= 2e-3 * max(1.0, abs(dd), np.abs(grad) @ np.abs(v))
+
+
+def test_smoothed_forward_small_alpha_recovers_min_sum(lib):
+    """tau -> 0: the smoothed bound after K iterations tends to the min-sum bound."""
+    import torch
+    from paper_2009_00481_gb300 import smoothed_bound
+    inst = potts_mrf(8, 8, 3, seed=6)
+    K = 30
+    plain = _trace(solver(inst), K)[-1]
+    s = solver(inst, alpha=1e-4)
+    ct = torch.tensor(inst.c, device="cuda")
+    val = float(smoothed_bound(ct, s, K).item())
+    close([val], [plain], LB_TOL)
+
+
+def test_backward_needs_matching_forward(lib):
+    import torch
+    from paper_2009_00481_gb300 import BDDError, binding, smoothed_bound
+    from paper_2009_00481_gb300.binding import BDD_ESTATE
+    inst = potts_mrf(4, 4, 2, seed=1)
+    s = solver(inst, alpha=0.3)
+    g = torch.ones((), dtype=torch.float64, device="cuda")
+    out = torch.zeros(inst.n, dtype=torch.float32, device="cuda")
+    with pytest.raises(BDDError) as e:  # no forward yet
+        binding.bdd_smooth_backward(s.h, g.data_ptr(), out.data_ptr())
+    assert e.value.code == BDD_ESTATE
+    ct = torch.tensor(inst.c, device="cuda", requires_grad=True)
+    val = smoothed_bound(ct, s, 5)
+    s.iterate(1)  # changes the state: the recorded forward is stale
+    with pytest.raises(BDDError) as e:
+        val.backward()
+    assert e.value.code == BDD_ESTATE
+    plain = solver(inst)
+    with pytest.raises(BDDError) as e:  # min-sum solvers have no smoothed bound
+        smoothed_bound(ct, plain, 5)
+    assert e.value.code == BDD_ESTATE
