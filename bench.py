@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--batch-warmup", type=int, default=2)
     ap.add_argument("--no-plain", action="store_true", help="batch workload: skip the one-solver-per-instance loop")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch workload part of the default line")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation part of the default line")
+    ap.add_argument("--diff-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -281,6 +283,9 @@ def ours(args):
     batch = None
     if world == 1 and not args.no_batch:
         batch = run_batched(args, stream, plain=False, n_parity=1)
+    diff = None
+    if world == 1 and not args.no_diff:
+        diff = run_differentiation(args, stream)
 
     if rank != 0:
         if world > 1:
@@ -311,6 +316,7 @@ def ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batch,
+        "differentiation": diff,
         "gpu_launches": launches,
         "schedule": "persistent" if s.schedule == 0 else "per-phase graphs",
         "clocks": clocks,
@@ -439,6 +445,106 @@ def run_batched(args, stream, plain: bool, n_parity: int) -> dict:
     }
 
 
+def run_differentiation(args, stream) -> dict:
+    """The differentiation workload (cell-tracking-shaped flow ILP, 50 frames x 200 detections):
+    K = 50 smoothed iterations (tau = 0.1) forward, and forward plus the adjoint giving
+    d(bound)/dc, against K plain iterations on the same instance; smoothed-bound parity with the
+    oracle and a central-difference gradient check on the 5-frame x 20-detection slice."""
+    import torch
+
+    from instances import tracking
+    from paper_2009_00481_gb300 import Solver, binding
+
+    inst = config(3)
+    K, alpha = CONFIG_ITERS[3], 0.1
+    reps = args.diff_steps
+    plain = Solver(inst, omega=0.5, stream=stream.cuda_stream)
+    smooth = Solver(inst, omega=0.5, stream=stream.cuda_stream, alpha=alpha)
+    arcs = 2 * plain.N * K
+    c = torch.tensor(inst.c, device="cuda")
+    bound = torch.zeros((), dtype=torch.float64, device="cuda")
+    gbound = torch.ones((), dtype=torch.float64, device="cuda")
+    grad = torch.zeros(inst.n, dtype=torch.float32, device="cuda")
+    trace = torch.zeros(K, dtype=torch.float64, device="cuda")
+    sp = stream.cuda_stream
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def plain_step():
+        plain.set_costs(inst.c)
+        plain.iterate_device(K, trace=trace, stream=sp)
+
+    ms_plain = timed(plain_step)
+    plain_bound = float(trace[-1].item())
+    ms_fwd = timed(lambda: binding.bdd_smooth_forward(smooth.h, K, c.data_ptr(), bound.data_ptr(), sp))
+
+    def fwd_bwd():
+        binding.bdd_smooth_forward(smooth.h, K, c.data_ptr(), bound.data_ptr(), sp)
+        binding.bdd_smooth_backward(smooth.h, gbound.data_ptr(), grad.data_ptr(), sp)
+
+    ms_fb = timed(fwd_bwd)
+    smooth_bound = float(bound.item())
+
+    import oracle
+    oracle.build()
+    from oracle import Oracle
+    o = Oracle(inst)
+    o.set_alpha(alpha)
+    want = float(o.run_parallel(K, omega=0.5)[-1])
+
+    # gradient check on the slice: 8 coordinates, FP64 central differences of the oracle
+    import copy
+    sl = tracking(frames=5, dets=20, seed=0)
+    ss = Solver(sl, omega=0.5, stream=sp, alpha=alpha)
+    csl = torch.tensor(sl.c, device="cuda")
+    gsl = torch.zeros(sl.n, dtype=torch.float32, device="cuda")
+    binding.bdd_smooth_forward(ss.h, K, csl.data_ptr(), bound.data_ptr(), sp)
+    binding.bdd_smooth_backward(ss.h, gbound.data_ptr(), gsl.data_ptr(), sp)
+    g = gsl.cpu().numpy().astype(np.float64)
+
+    def ob(cv):
+        j = copy.copy(sl)
+        j.c = cv
+        oo = Oracle(j)
+        oo.set_alpha(alpha)
+        return float(oo.run_parallel(K, omega=0.5)[-1])
+
+    idx = np.random.default_rng(0).choice(sl.n, size=8, replace=False)
+    h = 1e-4
+    c0 = sl.c.astype(np.float64)
+    fd = []
+    for i in idx:
+        cp, cm = c0.copy(), c0.copy()
+        cp[i] += h
+        cm[i] -= h
+        fd.append((ob(cp) - ob(cm)) / (2 * h))
+    fd = np.asarray(fd)
+    grad_err = float(np.abs(g[idx] - fd).max() / max(1.0, np.abs(fd).max()))
+    for t in (plain, smooth, ss):
+        t.close()
+    return {
+        "workload": CONFIG_NAMES[3], "iterations": K, "tau": alpha, "nodes": arcs // (2 * K),
+        "plain": {"value": arcs / (ms_plain / 1e3), "unit": UNIT, "ms": ms_plain, "bound": plain_bound},
+        "smoothed_forward": {"value": arcs / (ms_fwd / 1e3), "unit": UNIT, "ms": ms_fwd, "bound": smooth_bound,
+                             "oracle_bound": want, "rel_err": abs(smooth_bound - want) / max(1.0, abs(want))},
+        "smoothed_forward_backward": {"value": arcs / (ms_fb / 1e3), "unit": UNIT, "ms": ms_fb,
+                                      "note": "K smoothed iterations with per-sweep checkpoints, then the "
+                                              "adjoint pass (recomputation + adjoint kernels) giving d(bound)/dc"},
+        "gradient_check": {"slice": "tracking 5 frames x 20 detections", "coordinates": 8,
+                           "max_err_rel_to_max_grad": grad_err, "reference": "FP64 central differences of the oracle"},
+    }
+
+
 def batched(args):
     """`--config 4`: the batch workload as the bench line."""
     import torch
@@ -500,6 +606,12 @@ def main():
         reference(args)
     elif args.config == 4:
         batched(args)
+    elif args.config == 3:
+        import torch
+        torch.cuda.set_device(0)
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        print(json.dumps({"metric": METRIC, "differentiation": run_differentiation(args, stream)}), flush=True)
     else:
         ours(args)
 
