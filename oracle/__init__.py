@@ -42,6 +42,10 @@ def _configure(lib):
     lib.orc_build.restype = vp
     lib.orc_build.argtypes = [i32, i32, P(i64), P(i32), P(i32), P(i32), P(C.c_byte), P(f64),
                               P(i32), P(i32)]
+    lib.orc_build_ordered.restype = vp
+    lib.orc_build_ordered.argtypes = [i32, i32, P(i64), P(i32), P(i32), P(i32), P(C.c_byte),
+                                      P(f64), P(i32), P(i32), P(i32)]
+    lib.orc_set_srmp.argtypes = [vp, i32]
     lib.orc_free.argtypes = [vp]
     lib.orc_sizes.argtypes = [vp, P(i64)]
     lib.orc_export.argtypes = [vp, P(i32), P(i32), P(i32), P(i64), P(i32), P(i32), P(i32), P(i64)]
@@ -84,9 +88,12 @@ class OracleError(RuntimeError):
 
 
 class Oracle:
-    """One instance: BDDs built from the ILP, plus FP64 dual state."""
+    """One instance: BDDs built from the ILP, plus FP64 dual state.
 
-    def __init__(self, inst, lib=None):
+    rank: optional permutation of 0..n-1, the place of each variable in the variable order
+    (Appendix A.3); BDD layers and the sequential schedule follow it.  None = identity."""
+
+    def __init__(self, inst, lib=None, rank=None):
         lib = _load() if lib is None else lib
         self.lib = lib
         self.inst = inst
@@ -97,10 +104,18 @@ class Oracle:
                       np.ascontiguousarray(inst.sense, np.int8),
                       np.ascontiguousarray(inst.c, np.float64)]
         rp, col, val, b, sense, c = self._keep
+        rk = None
+        if rank is not None:
+            rk = np.ascontiguousarray(rank, np.int32)
+            if rk.shape != (inst.n,):
+                raise ValueError("rank must have one entry per variable")
+            self._keep.append(rk)
         st, row = C.c_int(0), C.c_int(0)
-        self.h = lib.orc_build(inst.n, inst.m, _p(rp, C.c_longlong), _p(col, C.c_int),
-                               _p(val, C.c_int), _p(b, C.c_int), _p(sense, C.c_byte),
-                               _p(c, C.c_double), C.byref(st), C.byref(row))
+        self.h = lib.orc_build_ordered(inst.n, inst.m, _p(rp, C.c_longlong), _p(col, C.c_int),
+                                       _p(val, C.c_int), _p(b, C.c_int), _p(sense, C.c_byte),
+                                       _p(c, C.c_double),
+                                       None if rk is None else _p(rk, C.c_int),
+                                       C.byref(st), C.byref(row))
         if not self.h:
             raise OracleError(st.value, row.value)
         s = np.zeros(8, np.int64)
@@ -135,6 +150,11 @@ class Oracle:
     def set_alpha(self, alpha: float):
         """Smoothing temperature (0 = min-sum); restarts the dual state."""
         self.lib.orc_set_alpha(self.h, float(alpha))
+
+    def set_srmp(self, on: bool = True):
+        """SRMP averaging (Appendix A.4) instead of eq. mma-update; restarts the dual state."""
+        self.lib.orc_set_srmp(self.h, int(bool(on)))
+        self.lib.orc_init_dual(self.h)
 
     def reset(self):
         self.lib.orc_init_dual(self.h)

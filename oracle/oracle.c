@@ -36,6 +36,11 @@
  *     becomes the soft minimum -alpha log(sum exp(-x / alpha)), evaluated in the -alpha log
  *     domain with the smaller argument factored out; E^j becomes E^j_alpha and min-marginals
  *     become marginal log-sum-exp values.  alpha = 0 is the plain min-sum algebra.
+ *   - Variable order (Appendix A.3): an optional rank per variable sets the layer order of every
+ *     BDD and the visiting order of Alg. 1 (identity when absent).
+ *   - SRMP averaging (Appendix A.4): optionally, the averaging share of variable i goes only to
+ *     the subproblems that contain a variable after i in the order (forward pass) / before i
+ *     (backward pass), evenly; when there are none, to all of J_i.
  * Readings where the paper is silent: a min-marginal that is +inf (a row that forces x_i)
  * gives the difference 0; a variable in no row contributes min(0, c_i) to the bound; an empty
  * row is dropped when 0 (sense) b holds and is infeasible otherwise.
@@ -101,6 +106,9 @@ typedef struct {
   double *c;
   double empty_const;       /* sum over variables in no row of min(0, c_i) (soft: of agg(0, c_i)) */
   double alpha;             /* 0: min-sum; > 0: smoothing temperature */
+  int srmp;                 /* 0: eq. mma-update averaging; 1: SRMP averaging */
+  int *order;               /* [n] variables in visiting order (Alg. 1) */
+  double *oshare;           /* [O] share each occurrence takes in the next sweep */
   /* dual state and messages */
   double *lam, *P, *delta, *share, *fm, *bm;
   /* scratch for the definitional dynamic programmes */
@@ -118,7 +126,7 @@ void orc_free(void *vh) {
   free(h->lo); free(h->hi); free(h->minsum);
   free(h->var_ptr); free(h->var_occ); free(h->deg); free(h->c);
   free(h->lam); free(h->P); free(h->delta); free(h->share); free(h->fm); free(h->bm);
-  free(h->sfm); free(h->sbm);
+  free(h->sfm); free(h->sbm); free(h->order); free(h->oshare);
   free(h);
 }
 
@@ -127,9 +135,12 @@ void orc_free(void *vh) {
 /* ------------------------------------------------------------------------------------ */
 typedef struct { int col, val; long long pos; } entry_t;
 
+static const int *g_rank;  /* comparator context (the oracle is single-threaded) */
+
 static int cmp_entry(const void *a, const void *b) {
   const entry_t *x = (const entry_t *)a, *y = (const entry_t *)b;
-  return (x->col > y->col) - (x->col < y->col);
+  long long rx = g_rank ? g_rank[x->col] : x->col, ry = g_rank ? g_rank[y->col] : y->col;
+  return (rx > ry) - (rx < ry);
 }
 
 static int sat(long long s, int sense, long long b) {
@@ -240,11 +251,23 @@ done:
 }
 
 /* Builds all BDDs.  status: ORC_* code; failed_row: the row that made it fail (or -1). */
-void *orc_build(int n, int m, const long long *row_ptr, const int *col, const int *val,
-                const int *b, const signed char *sense, const double *c, int *status,
-                int *failed_row) {
+/* rank: NULL (identity) or a permutation of 0..n-1 giving each variable's place in the order */
+void *orc_build_ordered(int n, int m, const long long *row_ptr, const int *col, const int *val,
+                        const int *b, const signed char *sense, const double *c, const int *rank,
+                        int *status, int *failed_row) {
   *status = ORC_OK; *failed_row = -1;
   if (n < 0 || m < 0) { *status = ORC_EINVAL; return NULL; }
+  if (rank) {
+    char *seen = (char *)calloc((size_t)n + 1, 1);
+    int ok = seen != NULL;
+    for (int i = 0; i < n && ok; ++i) {
+      if (rank[i] < 0 || rank[i] >= n || seen[rank[i]]) ok = 0;
+      else seen[rank[i]] = 1;
+    }
+    free(seen);
+    if (!ok) { *status = ORC_EINVAL; return NULL; }
+  }
+  g_rank = rank;
   for (int i = 0; i < n; ++i)
     if (!isfinite(c[i])) { *status = ORC_EINVAL; return NULL; }
   oracle_t *h = (oracle_t *)calloc(1, sizeof(oracle_t));
@@ -280,6 +303,7 @@ void *orc_build(int n, int m, const long long *row_ptr, const int *col, const in
     if (rc != ORC_OK) *failed_row = j;
     free(ent);
   }
+  g_rank = NULL;
   h->bdd_row = bdd_row.p; h->bdd_k = bdd_k.p; h->occ_var = occ_var.p; h->occ_csr = occ_csr.p;
   h->lo = lo.p; h->hi = hi.p; h->minsum = minsum.p;
   h->nb = (int)bdd_row.n; h->O = occ_var.n; h->N = lo.n;
@@ -303,6 +327,10 @@ void *orc_build(int n, int m, const long long *row_ptr, const int *col, const in
   h->bm = (double *)calloc((size_t)N + 1, sizeof(double));
   h->sfm = (double *)calloc((size_t)N + 1, sizeof(double));
   h->sbm = (double *)calloc((size_t)N + 1, sizeof(double));
+  h->order = (int *)malloc((size_t)(n + 1) * sizeof(int));
+  h->oshare = (double *)calloc((size_t)O + 1, sizeof(double));
+  if (!h->order || !h->oshare) { orc_free(h); *status = ORC_ENOMEM; return NULL; }
+  for (int i = 0; i < n; ++i) h->order[rank ? rank[i] : i] = i;
   if (!h->bdd_occ0 || !h->occ_bdd || !h->occ_layer || !h->var_ptr || !h->var_occ || !h->deg ||
       !h->c || !h->lam || !h->delta || !h->P || !h->share || !h->fm || !h->bm || !h->sfm ||
       !h->sbm) {
@@ -336,6 +364,15 @@ void *orc_build(int n, int m, const long long *row_ptr, const int *col, const in
   }
   return h;
 }
+
+void *orc_build(int n, int m, const long long *row_ptr, const int *col, const int *val,
+                const int *b, const signed char *sense, const double *c, int *status,
+                int *failed_row) {
+  return orc_build_ordered(n, m, row_ptr, col, val, b, sense, c, NULL, status, failed_row);
+}
+
+/* 0: the averaging of eq. mma-update; 1: SRMP averaging (Appendix A.4) */
+void orc_set_srmp(void *vh, int srmp) { ((oracle_t *)vh)->srmp = srmp ? 1 : 0; }
 
 void orc_sizes(void *vh, long long out[8]) {
   oracle_t *h = (oracle_t *)vh;
@@ -521,12 +558,34 @@ static void form_pending(oracle_t *h) {
   }
 }
 
-static void take_share(oracle_t *h) {
-  for (int i = 0; i < h->n; ++i) h->share[i] = h->deg[i] ? h->P[i] / h->deg[i] : 0.0;
+/* Is occurrence o among the subproblems that take i's share in a forward (backward) sweep?  For
+ * SRMP: those with a variable after (before) i, i.e. o is not the last (first) layer of its BDD. */
+static int srmp_takes(const oracle_t *h, long long o, int forward) {
+  int l = h->occ_layer[o], k = h->bdd_k[h->occ_bdd[o]];
+  return forward ? l < k - 1 : l > 0;
+}
+
+/* The share each occurrence takes in the next sweep: P_i / |J_i| (eq. mma-update), or for SRMP
+ * P_i / |J_i^>| on J_i^> in a forward sweep (J_i^< backward), all of J_i when that set is empty. */
+static void take_share(oracle_t *h, int forward) {
+  for (int i = 0; i < h->n; ++i) {
+    long long s = h->var_ptr[i], e = h->var_ptr[i + 1];
+    if (e == s) continue;
+    int cnt = 0;
+    if (h->srmp)
+      for (long long t = s; t < e; ++t) cnt += srmp_takes(h, h->var_occ[t], forward);
+    for (long long t = s; t < e; ++t) {
+      long long o = h->var_occ[t];
+      if (!h->srmp || cnt == 0)
+        h->oshare[o] = h->P[i] / (double)(e - s);
+      else
+        h->oshare[o] = srmp_takes(h, o, forward) ? h->P[i] / cnt : 0.0;
+    }
+  }
 }
 
 static void sweep_forward(oracle_t *h, double omega, int check) {
-  take_share(h);
+  take_share(h, 1);
   for (int b = 0; b < h->nb; ++b) {
     long long o0 = h->bdd_occ0[b];
     int k = h->bdd_k[b];
@@ -547,7 +606,7 @@ static void sweep_forward(oracle_t *h, double omega, int check) {
           }
         }
       }
-      h->lam[o] += h->share[h->occ_var[o]];
+      h->lam[o] += h->oshare[o];
       double m0, m1;
       aggregate(h, o, h->lam[o], h->fm, h->bm, &m0, &m1);
       if (check) {
@@ -566,12 +625,12 @@ static void sweep_forward(oracle_t *h, double omega, int check) {
 }
 
 static void sweep_backward(oracle_t *h, double omega, int check) {
-  take_share(h);
+  take_share(h, 0);
   for (int b = 0; b < h->nb; ++b) {
     long long o0 = h->bdd_occ0[b];
     for (int l = h->bdd_k[b] - 1; l >= 0; --l) {
       long long o = o0 + l;
-      h->lam[o] += h->share[h->occ_var[o]];
+      h->lam[o] += h->oshare[o];
       double m0, m1;
       aggregate(h, o, h->lam[o], h->fm, h->bm, &m0, &m1);
       if (check) {
@@ -630,10 +689,14 @@ int orc_run_parallel(void *vh, int iters, double omega, int check, double *trace
 /* ------------------------------------------------------------------------------------ */
 /* schedule S: Alg. 1 with definitional min-marginals                                     */
 /* ------------------------------------------------------------------------------------ */
-static void visit_variable(oracle_t *h, int i, int check, double *m0s, double *m1s) {
+static void visit_variable(oracle_t *h, int i, int forward, int check, double *m0s,
+                           double *m1s) {
   long long s = h->var_ptr[i], e = h->var_ptr[i + 1];
   int J = (int)(e - s);
   if (J == 0) return;
+  int Jt = 0;  /* SRMP: |J_i^>| in a forward pass, |J_i^<| in a backward pass */
+  if (h->srmp)
+    for (long long t = s; t < e; ++t) Jt += srmp_takes(h, h->var_occ[t], forward);
   double S = 0.0, neg = 0.0, before = 0.0;
   int finite = 1;
   for (long long t = s; t < e; ++t) {
@@ -645,9 +708,11 @@ static void visit_variable(oracle_t *h, int i, int check, double *m0s, double *m
     if (d < 0) neg += d;
     if (check) before += energy(h, h->occ_bdd[o], h->lam);
   }
-  for (long long t = s; t < e; ++t) {  /* eq. (mma-update) */
+  for (long long t = s; t < e; ++t) {  /* eq. (mma-update), or eq. (srmp-update) */
     long long o = h->var_occ[t];
-    h->lam[o] += -mm_diff(m0s[t - s], m1s[t - s]) + S / J;
+    double add = S / J;
+    if (h->srmp && Jt > 0) add = srmp_takes(h, o, forward) ? S / Jt : 0.0;
+    h->lam[o] += -mm_diff(m0s[t - s], m1s[t - s]) + add;
   }
   if (check) {
     double after = 0.0;
@@ -672,8 +737,8 @@ int orc_run_sequential(void *vh, int iters, int check, double *trace) {
   for (int i = 0; i < h->n; ++i) h->P[i] = 0.0;
   double prev = orc_bound(h);
   for (int it = 0; it < iters; ++it) {
-    for (int i = 0; i < h->n; ++i) visit_variable(h, i, check, m0s, m1s);
-    for (int i = h->n - 1; i >= 0; --i) visit_variable(h, i, check, m0s, m1s);
+    for (int k = 0; k < h->n; ++k) visit_variable(h, h->order[k], 1, check, m0s, m1s);
+    for (int k = h->n - 1; k >= 0; --k) visit_variable(h, h->order[k], 0, check, m0s, m1s);
     double lb = orc_bound(h);
     if (check) {
       check_invariant(h);

@@ -135,3 +135,107 @@ def potts_map(H, W, L, c) -> float:
             e += float(c[nx + t * L * L + lab[i] * L + lab[j]])
         best = min(best, e)
     return best
+
+
+# ------------------------------------------------------------------------------------------
+# Alg. 1 and the deferred-averaging schedule by enumeration, with a variable order
+# (Appendix A.3) and the SRMP averaging sets (Appendix A.4)
+# ------------------------------------------------------------------------------------------
+
+class EnumDual:
+    """Dual state lambda^j_i per row j and position t (variables of the row in the order given
+    by rank), with min-marginals and energies taken by enumeration of X_j."""
+
+    def __init__(self, inst, rank=None):
+        rank = np.arange(inst.n) if rank is None else np.asarray(rank)
+        self.n = inst.n
+        self.c = inst.c.astype(np.float64)
+        self.rows = []
+        for cols, vals, b, sense in canonical_rows(inst):
+            o = np.argsort(rank[cols], kind="stable")
+            self.rows.append((cols[o], vals[o], b, sense))
+        self.occ = [[] for _ in range(inst.n)]  # per variable: (row, position), rows ascending
+        for j, (cols, _, _, _) in enumerate(self.rows):
+            for t, i in enumerate(cols):
+                self.occ[int(i)].append((j, t))
+        self.order = np.argsort(rank, kind="stable")
+        self.lam = [np.array([self.c[i] / len(self.occ[i]) for i in cols]) for cols, *_ in self.rows]
+        self.P = np.zeros(inst.n)
+
+    def mm(self, j):
+        cols, vals, b, sense = self.rows[j]
+        return min_marginals_enum(vals, b, sense, self.lam[j])
+
+    def bound(self):
+        tot = sum(self.mm(j)[2] for j in range(len(self.rows)))
+        s = np.zeros(self.n)
+        for j, (cols, *_) in enumerate(self.rows):
+            s[cols] += self.lam[j]
+        return tot + np.minimum(0.0, self.c - s).sum()
+
+    def takes(self, j, t, forward):
+        """(j, position t) is in J_i^> (forward) / J_i^< (backward)."""
+        return t < len(self.rows[j][0]) - 1 if forward else t > 0
+
+    def weights(self, i, forward, srmp):
+        """Share of the summed difference that each subproblem of variable i receives."""
+        occ = self.occ[i]
+        if not occ:
+            return []
+        if srmp:
+            mask = [self.takes(j, t, forward) for j, t in occ]
+            if any(mask):
+                return [1.0 / sum(mask) if m else 0.0 for m in mask]
+        return [1.0 / len(occ)] * len(occ)
+
+
+def _diff(m0, m1):
+    return 0.0 if np.isinf(m0) or np.isinf(m1) else m1 - m0
+
+
+def sequential_enum(inst, iters, rank=None, srmp=False):
+    """Alg. 1: forward then backward over the variable order; eq. mma-update, or
+    eq. srmp-update with J_i^> forward and J_i^< backward.  Returns the bound per iteration."""
+    D = EnumDual(inst, rank)
+    trace = []
+    for _ in range(iters):
+        for forward, seq in ((True, D.order), (False, D.order[::-1])):
+            for i in seq:
+                occ = D.occ[int(i)]
+                if not occ:
+                    continue
+                d = []
+                for j, t in occ:
+                    m0, m1, _, _ = D.mm(j)
+                    d.append(_diff(m0[t], m1[t]))
+                S = sum(d)
+                for (j, t), dj, w in zip(occ, d, D.weights(int(i), forward, srmp)):
+                    D.lam[j][t] += -dj + w * S
+        trace.append(D.bound())
+    return np.array(trace)
+
+
+def parallel_enum(inst, iters, omega=0.5, rank=None, srmp=False):
+    """Deferred averaging: every BDD runs its layers in order; the share of the previous sweep's
+    sum P_i is added at the visit, lambda moves by -omega (m1 - m0), P_i = the sum of those
+    moves after the sweep.  Returns the bound after each backward sweep."""
+    D = EnumDual(inst, rank)
+    trace = []
+    for _ in range(iters):
+        for forward in (True, False):
+            share = [np.zeros(len(cols)) for cols, *_ in D.rows]
+            for i in range(D.n):
+                for (j, t), w in zip(D.occ[i], D.weights(i, forward, srmp)):
+                    share[j][t] = w * D.P[i]
+            Pn = np.zeros(D.n)
+            for j, (cols, *_) in enumerate(D.rows):
+                k = len(cols)
+                for t in (range(k) if forward else range(k - 1, -1, -1)):
+                    D.lam[j][t] += share[j][t]
+                    m0, m1, _, _ = D.mm(j)
+                    dlt = omega * _diff(m0[t], m1[t])
+                    D.lam[j][t] -= dlt
+                    Pn[cols[t]] += dlt
+            D.P = Pn
+        trace.append(D.bound())
+    return np.array(trace)

@@ -23,7 +23,7 @@ MUTANTS = {
     "sign": ("return (isinf(m0) || isinf(m1)) ? 0.0 : m1 - m0;",
              "return (isinf(m0) || isinf(m1)) ? 0.0 : m0 - m1;"),
     # deferred averaging share never applied in the forward sweep
-    "drop_share": ("        }\n      }\n      h->lam[o] += h->share[h->occ_var[o]];",
+    "drop_share": ("        }\n      }\n      h->lam[o] += h->oshare[o];",
                    "        }\n      }\n"),
     # forward update step charges the 1-arc with the wrong layer's multiplier
     "fwd_index": ("            double x = h->fm[u] + h->lam[o - 1];\n            h->fm[v] = agg(h, h->fm[v], x);",
@@ -37,6 +37,16 @@ MUTANTS = {
     # bound forgets the slack term of the y-variables
     "bound_slack": ("  for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];\n  for (int i = 0; i < h->n; ++i)\n    if (h->deg[i] > 0) lb += agg(h, 0.0, h->P[i]);",
                     "  for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];"),
+    # SRMP sets of the forward and backward passes swapped (Appendix A.4)
+    "srmp_direction": ("return forward ? l < k - 1 : l > 0;", "return forward ? l > 0 : l < k - 1;"),
+    # SRMP without the fallback to all of J_i when J_i^> (J_i^<) is empty
+    "srmp_no_fallback": ("if (!h->srmp || cnt == 0)", "if (!h->srmp)"),
+    # sequential schedule visits variables in index order whatever the variable order
+    "order_visit": ("visit_variable(h, h->order[k], 1, check, m0s, m1s)",
+                    "visit_variable(h, k, 1, check, m0s, m1s)"),
+    # BDD layers in index order whatever the variable order
+    "order_layers": ("long long rx = g_rank ? g_rank[x->col] : x->col, ry = g_rank ? g_rank[y->col] : y->col;",
+                     "long long rx = x->col, ry = y->col;"),
 }
 
 
@@ -88,6 +98,21 @@ def _pins_hold(lib) -> bool:
             return False
         if tr.max() > opt + 1e-9:
             return False
+    # variable order and SRMP: both schedules against enumeration (Appendix A.3, A.4)
+    for seed in range(2):
+        inst = random_ilp(n=9, m=6, max_row_vars=5, seed=520 + seed)
+        rank = np.random.default_rng(seed).permutation(inst.n)
+        for srmp in (False, True):
+            o = Oracle(inst, lib=lib, rank=rank)
+            if srmp:
+                o.set_srmp()
+            if not np.allclose(o.run_sequential(3), bf.sequential_enum(inst, 3, rank, srmp),
+                               rtol=0, atol=1e-10):
+                return False
+            o.reset()
+            if not np.allclose(o.run_parallel(4, omega=0.5),
+                               bf.parallel_enum(inst, 4, 0.5, rank, srmp), rtol=0, atol=1e-10):
+                return False
     return True
 
 
