@@ -74,6 +74,22 @@ typedef struct {
                                  the bound is E^j_alpha-based and differentiable.  Smoothed
                                  solvers need every BDD layer to be at most 32 nodes wide
                                  (else BDD_ETOOBIG) and run schedule 1. */
+  const int *var_rank;        /* variable order (Appendix A.3): NULL (default) = index order;
+                                 else a host array of n entries, a permutation of 0..n-1, where
+                                 var_rank[i] is the place of variable i.  Every BDD takes its
+                                 row's variables in ascending rank; all inputs and outputs stay
+                                 in CSR / variable index order.  Read by bdd_build only (the
+                                 caller keeps ownership); not a permutation -> BDD_EINVAL.
+                                 bdd_cuthill_mckee computes the paper's choice of order. */
+  int averaging;              /* 0 (default): eq. (mma-update), the pending sum P_i is shared
+                                 evenly over all of J_i.  1: SRMP averaging (Appendix A.4,
+                                 eq. srmp-update): a forward sweep shares P_i evenly over
+                                 J_i^> (subproblems of i with a variable after i in the order,
+                                 i.e. i is not the last layer of the BDD), a backward sweep over
+                                 J_i^< (i not the first layer); an empty set falls back to all of
+                                 J_i.  Under the deferred schedule the set of a sweep applies
+                                 to the shares that sweep adds.  Folded outputs (multipliers and
+                                 min-marginals) add the forward-sweep shares. */
 } bdd_options;
 
 void bdd_default_options(bdd_options *opt);
@@ -184,6 +200,21 @@ int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending);
  * once) race and must be serialised by the caller.  Returns after enqueueing. */
 int bdd_lower_bound_noalloc(int n, int nb, const float *d_E, const float *d_P, const int *d_deg,
                             double empty_const, double *d_bound, void *stream);
+
+/* Variable order by bandwidth reduction (Appendix A.3): the Cuthill-McKee order of the
+ * bipartite variable-constraint graph (one node per variable and per row, an edge per nonzero
+ * coefficient), restricted to the variables.  Host only, no GPU needed.
+ *   n, m, row_ptr, col, val: the constraint matrix in CSR form, as for bdd_build (val may be
+ *     NULL: every stored entry is an edge; else entries with val == 0 are skipped)
+ *   rank: int32[n] output, a permutation of 0..n-1; rank[i] is the place of variable i, ready
+ *     for bdd_options.var_rank.
+ * Each connected component starts at a pseudo-peripheral node of least degree (repeated
+ * breadth-first search), then a breadth-first search that enqueues each node's unvisited
+ * neighbours in ascending degree (ties: ascending index); components follow in the order of
+ * their lowest-index variable; variables in no row come last, in index order.  Deterministic.
+ * Returns BDD_OK, BDD_EINVAL (bad sizes, pointers or column index) or BDD_ENOMEM. */
+int bdd_cuthill_mckee(int n, int m, const long long *row_ptr, const int *col, const int *val,
+                      int *rank);
 
 /* Text for a status code (static storage). */
 const char *bdd_strerror(int code);

@@ -756,15 +756,14 @@ int orc_run_sequential(void *vh, int iters, int check, double *trace) {
 /* ------------------------------------------------------------------------------------ */
 /* state access (arrays indexed by position in the input CSR; zero coefficients get 0)    */
 /* ------------------------------------------------------------------------------------ */
-/* lambda per coefficient; fold != 0 adds the pending share P_i/|J_i|, so that the returned
+/* lambda per coefficient; fold != 0 adds the share the next (forward) sweep would add: P_i/|J_i|,
+ * or with SRMP P_i/|J_i^>| on J_i^> (all of J_i when J_i^> is empty), so that the returned
  * multipliers satisfy sum_j lambda^j_i = c_i. */
 void orc_get_lambda(void *vh, int fold, double *out) {
   oracle_t *h = (oracle_t *)vh;
+  if (fold) take_share(h, 1);
   for (long long t = 0; t < h->nnz; ++t) out[t] = 0.0;
-  for (long long o = 0; o < h->O; ++o) {
-    int i = h->occ_var[o];
-    out[h->occ_csr[o]] = h->lam[o] + (fold ? h->P[i] / h->deg[i] : 0.0);
-  }
+  for (long long o = 0; o < h->O; ++o) out[h->occ_csr[o]] = h->lam[o] + (fold ? h->oshare[o] : 0.0);
 }
 
 void orc_get_pending(void *vh, double *P) {
@@ -781,15 +780,14 @@ void orc_set_state(void *vh, const double *lam, const double *P) {
 }
 
 /* Definitional min-marginals (full forward and backward programmes, then eq.
- * marginal-aggregation) for the current lambda, or lambda + P/|J| when fold != 0. */
+ * marginal-aggregation) for the current lambda, or lambda + the forward sweep's shares (as in
+ * orc_get_lambda) when fold != 0. */
 void orc_min_marginals(void *vh, int fold, double *m0, double *m1) {
   oracle_t *h = (oracle_t *)vh;
   double *lam = (double *)malloc((size_t)(h->O + 1) * sizeof(double));
   if (!lam) return;
-  for (long long o = 0; o < h->O; ++o) {
-    int i = h->occ_var[o];
-    lam[o] = h->lam[o] + (fold ? h->P[i] / h->deg[i] : 0.0);
-  }
+  if (fold) take_share(h, 1);
+  for (long long o = 0; o < h->O; ++o) lam[o] = h->lam[o] + (fold ? h->oshare[o] : 0.0);
   for (long long t = 0; t < h->nnz; ++t) { m0[t] = 0.0; m1[t] = 0.0; }
   for (int b = 0; b < h->nb; ++b) {
     dp_forward(h, b, lam, h->sfm);

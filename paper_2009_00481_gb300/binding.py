@@ -23,7 +23,7 @@ EXPORTED = [
     "bdd_iterate_profiled",
     "bdd_set_costs", "bdd_sizes", "bdd_export_canonical", "bdd_get_state", "bdd_set_state",
     "bdd_strerror", "bdd_free", "bdd_lower_bound_noalloc", "bdd_bound_parts", "bdd_smooth_forward",
-    "bdd_smooth_backward",
+    "bdd_smooth_backward", "bdd_cuthill_mckee",
 ]
 
 
@@ -31,7 +31,7 @@ class bdd_options(C.Structure):
     _fields_ = [("omega", C.c_float), ("max_width", C.c_int), ("max_nodes", C.c_longlong),
                 ("max_device_bytes", C.c_longlong), ("host_only", C.c_int), ("device", C.c_int),
                 ("stream", C.c_void_p), ("schedule", C.c_int), ("spin_limit", C.c_longlong),
-                ("alpha", C.c_float)]
+                ("alpha", C.c_float), ("var_rank", C.POINTER(C.c_int)), ("averaging", C.c_int)]
 
 
 class BDDError(RuntimeError):
@@ -78,6 +78,7 @@ def load(path: str | None = None):
     lib.bdd_bound_parts.argtypes = [vp, i32, P(i64), P(i64), P(f64)]
     lib.bdd_smooth_forward.argtypes = [vp, i32, vp, vp, vp]
     lib.bdd_smooth_backward.argtypes = [vp, vp, vp, vp]
+    lib.bdd_cuthill_mckee.argtypes = [i32, i32, P(i64), P(i32), P(i32), P(i32)]
     if path == LIB:
         _lib = lib
     return lib
@@ -118,6 +119,18 @@ def bdd_build(n, m, row_ptr, col, val, b, sense, c, opt: bdd_options | None = No
     if rc != BDD_OK:
         raise BDDError(rc, "bdd_build", lib.bdd_last_failed_row())
     return h.value
+
+
+def bdd_cuthill_mckee(n, m, row_ptr, col, val=None) -> np.ndarray:
+    """Variable order of the Cuthill-McKee search on the bipartite variable-constraint graph
+    (Appendix A.3): rank[i] = place of variable i."""
+    row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    val = None if val is None else np.ascontiguousarray(val, np.int32)
+    rank = np.zeros(max(int(n), 1), np.int32)
+    _check(load().bdd_cuthill_mckee(int(n), int(m), _ptr(row_ptr, C.c_longlong), _ptr(col, C.c_int),
+                                    _ptr(val, C.c_int), _ptr(rank, C.c_int)), "bdd_cuthill_mckee")
+    return rank[: int(n)]
 
 
 def bdd_last_failed_row() -> int:

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libbdd_dbca.so")
-SOURCES = ["compile.cpp", "kernels.cu", "adjoint.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["compile.cpp", "order.cpp", "kernels.cu", "adjoint.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

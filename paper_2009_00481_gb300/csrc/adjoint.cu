@@ -314,13 +314,23 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_adjoint_kernel(const AdjP
 // Adjoint of the pending sums: share_o = P_i / |J_i| and P_i = sum of the previous sweep's
 // differences of i, so every slot of i receives (sum over i's occurrences of g_share) / |J_i|.
 __global__ void pending_adjoint_kernel(const int *__restrict__ var_ptr, const int *__restrict__ var_occ,
+                                       const unsigned char *__restrict__ slot_dir, int dir,
                                        const float *__restrict__ g_shr, float *__restrict__ g_delta, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int s = var_ptr[i], e = var_ptr[i + 1];
     if (e == s) continue;
+    int cnt = 0;  // SRMP: the slots that took a share (all of them when none is in J_i^dir)
+    if (slot_dir)
+      for (int k = s; k < e; ++k) cnt += (slot_dir[k] & dir) != 0;
     float g = 0.f;
-    for (int k = s; k < e; ++k) g += g_shr[var_occ[k]];
-    g /= (float)(e - s);
+    if (cnt > 0) {
+      for (int k = s; k < e; ++k)
+        if (slot_dir[k] & dir) g += g_shr[var_occ[k]];
+      g /= (float)cnt;
+    } else {
+      for (int k = s; k < e; ++k) g += g_shr[var_occ[k]];
+      g /= (float)(e - s);
+    }
     for (int k = s; k < e; ++k) g_delta[k] = g;
   }
 }
@@ -374,10 +384,10 @@ int sweep_adjoint_launch(bool forward, const AdjParams &a, int grid, cudaStream_
   return launch_status();
 }
 
-int pending_adjoint_launch(const int *var_ptr, const int *var_occ, const float *g_shr, float *g_delta, int n,
-                           cudaStream_t stream) {
+int pending_adjoint_launch(const int *var_ptr, const int *var_occ, const unsigned char *slot_dir, int dir,
+                           const float *g_shr, float *g_delta, int n, cudaStream_t stream) {
   if (n == 0) return 0;
-  pending_adjoint_kernel<<<grid_of(n), 256, 0, stream>>>(var_ptr, var_occ, g_shr, g_delta, n);
+  pending_adjoint_kernel<<<grid_of(n), 256, 0, stream>>>(var_ptr, var_occ, slot_dir, dir, g_shr, g_delta, n);
   return launch_status();
 }
 

@@ -91,6 +91,8 @@ struct bdd_solver {
   float *d_bdd_E = nullptr;
   int *d_tile_occ0 = nullptr, *d_tile_bdd0 = nullptr, *d_tile_nbdd = nullptr;
   int *d_var_ptr = nullptr, *d_var_occ = nullptr;
+  int averaging = 0;                     // 0: eq. mma-update; 1: SRMP (Appendix A.4)
+  unsigned char *d_slot_dir = nullptr;   // SRMP membership bits per slot (averaging == 1)
   // persistent schedule
   int schedule = 1;
   long long spin_limit = 1LL << 26;
@@ -171,8 +173,10 @@ struct bdd_solver {
     return p;
   }
 
-  PendingParams pending_params() const {
+  PendingParams pending_params(int next_dir) const {
     PendingParams r;
+    r.slot_dir = d_slot_dir;
+    r.next_dir = next_dir;
     r.var_ptr = d_var_ptr;
     r.var_occ = d_var_occ;
     r.delta = d_delta;
@@ -206,8 +210,11 @@ struct bdd_solver {
     return sweep_launch(fwd, mode, sweep_params(m0, m1), grid_sweep, s) ? BDD_ECUDA : BDD_OK;
   }
 
-  int pending(bool bound, cudaStream_t s) {
-    return pending_launch(bound, pending_params(), grid_reduce, s) ? BDD_ECUDA : BDD_OK;
+  // pending sums and the shares of the next sweep: a forward sweep follows a bound pass (the
+  // end of an iteration), a backward sweep the pass between the sweeps; `next_dir` overrides
+  int pending(bool bound, cudaStream_t s, int next_dir = 0) {
+    if (!next_dir) next_dir = bound ? kDirForward : kDirBackward;
+    return pending_launch(bound, pending_params(next_dir), grid_reduce, s) ? BDD_ECUDA : BDD_OK;
   }
 
   // one iteration: forward sweep, pending sums, backward sweep, pending sums and bound
@@ -235,6 +242,7 @@ struct bdd_solver {
     q.n = n;
     q.empty_const = empty_const;
     q.spin_limit = spin_limit;
+    q.slot_dir = d_slot_dir;
     CK(cudaMemsetAsync(d_barrier, 0, 2 * sizeof(unsigned), s));
     return iterate_persistent_launch(q, grid_persist, smem_persist, s) ? BDD_ECUDA : BDD_OK;
   }
@@ -375,7 +383,8 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   const long long O = h->O, N = h->N, nb = h->nb, n = h->n;
   const long long ntiles = (long long)L.tile_bdd0.size();
   long long need = (O + 1) * 4 + O * 4 + O * 8 + N * 8 + 2 * N * 4 + 2 * O * 4 + 3 * (long long)n * 4 +
-                   nb * 8 + 3 * ntiles * 4 + (n + 1) * 4 + O * 4 + h->grid_reduce * 8 + 1024 * 8;
+                   nb * 8 + 3 * ntiles * 4 + (n + 1) * 4 + O * 4 + h->grid_reduce * 8 + 1024 * 8 +
+                   (h->averaging == 1 ? O : 0);
   if (h->max_device_bytes > 0 && need > h->max_device_bytes) return BDD_ENOMEM;
 
   RC(upload(h, &h->d_occ_node_off, L.occ_node_off));
@@ -410,6 +419,7 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   RC(upload(h, &h->d_tile_nbdd, L.tile_nbdd));
   RC(upload(h, &h->d_var_ptr, L.var_ptr));
   RC(upload(h, &h->d_var_occ, L.var_occ));
+  if (h->averaging == 1) RC(upload(h, &h->d_slot_dir, L.slot_dir));
   RC(h->alloc(&h->d_partial, h->grid_reduce));
   RC(h->alloc(&h->d_ticket, 1));
   RC(h->alloc(&h->d_iter, 1));
@@ -456,6 +466,8 @@ void bdd_default_options(bdd_options *opt) {
   opt->schedule = 1;
   opt->spin_limit = 1LL << 26;
   opt->alpha = 0.f;
+  opt->var_rank = nullptr;
+  opt->averaging = 0;
 }
 
 int bdd_last_failed_row(void) { return g_failed_row; }
@@ -480,6 +492,20 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   const long long nnz = m ? row_ptr[m] : 0;
   if (nnz > 0 && (!col || !val)) return BDD_EINVAL;
   if (!finite_costs(c, n)) return BDD_EINVAL;
+  if (opt.averaging < 0 || opt.averaging > 1) return BDD_EINVAL;
+  if (opt.var_rank) {  // a permutation of 0..n-1
+    std::vector<char> seen;
+    try {
+      seen.assign(n, 0);
+    } catch (const std::bad_alloc &) {
+      return BDD_ENOMEM;
+    }
+    for (int i = 0; i < n; ++i) {
+      const int r = opt.var_rank[i];
+      if (r < 0 || r >= n || seen[r]) return BDD_EINVAL;
+      seen[r] = 1;
+    }
+  }
 
   bdd_solver *h = new (std::nothrow) bdd_solver();
   if (!h) return BDD_ENOMEM;
@@ -488,6 +514,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   h->nnz = nnz;
   h->omega = opt.omega;
   h->alpha = opt.alpha;
+  h->averaging = opt.averaging;
   h->schedule = opt.alpha > 0.f ? 1 : opt.schedule;  // the persistent kernel runs min-sum only
   h->spin_limit = opt.spin_limit;
   if (opt.schedule < 0 || opt.schedule > 1 || opt.spin_limit < 1) {
@@ -503,7 +530,8 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   h->max_device_bytes = opt.max_device_bytes;
   int failed = -1, rc;
   try {
-    rc = compile_bdds(n, m, row_ptr, col, val, b, sense, opt.max_width, opt.max_nodes, &h->host, &failed);
+    rc = compile_bdds(n, m, row_ptr, col, val, b, sense, opt.var_rank, opt.max_width, opt.max_nodes, &h->host,
+                      &failed);
   } catch (const std::bad_alloc &) {
     rc = BDD_ENOMEM;
   }
@@ -818,7 +846,8 @@ int bdd_smooth_backward(bdd_solver *h, const double *d_gbound, float *d_grad_c, 
     a.gE = sw == 2LL * K - 1 ? d_gbound : nullptr;
     if (sweep_adjoint_launch(fwd, a, h->n_warp_blocks, s)) return BDD_ECUDA;
     // the shares of this sweep were formed from the previous sweep's differences
-    if (sw > 0 && pending_adjoint_launch(h->d_var_ptr, h->d_var_occ, h->t_gshr, h->t_gdelta, h->n, s))
+    if (sw > 0 && pending_adjoint_launch(h->d_var_ptr, h->d_var_occ, h->d_slot_dir,
+                                         fwd ? kDirForward : kDirBackward, h->t_gshr, h->t_gdelta, h->n, s))
       return BDD_ECUDA;
     std::swap(g_cur, g_next);
   }
@@ -957,7 +986,7 @@ int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending) {
     // slots holding P_i in the first slot of i reproduce P exactly; the pending pass then writes
     // the shares (and P again, unchanged)
     if (pending_to_slots_launch(h->d_var_ptr, h->d_P, h->d_delta, h->n, s)) return BDD_ECUDA;
-    RC(h->pending(false, s));
+    RC(h->pending(false, s, kDirForward));  // the shares of the next (forward) sweep
   }
   RC(h->sweep(false, kMessages, s));
   RC(h->end(s));

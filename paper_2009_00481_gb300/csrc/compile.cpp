@@ -76,7 +76,7 @@ inline int key_of(const std::vector<long long> &T, long long s, long long b, int
   return (it != T.end() && *it == r) ? (int)(it - T.begin()) + 1 : 0;
 }
 
-int compile_row(int j, const long long *row_ptr, const int *col, const int *val, int n,
+int compile_row(int j, const long long *row_ptr, const int *col, const int *val, const int *rank, int n,
                 long long b, int sense, int max_width, Scratch &sc, Chunk &out) {
   long long s0 = row_ptr[j], e0 = row_ptr[j + 1];
   if (e0 < s0 || sense < -1 || sense > 1) return BDD_EINVAL;
@@ -85,8 +85,13 @@ int compile_row(int j, const long long *row_ptr, const int *col, const int *val,
     if (col[t] < 0 || col[t] >= n) return BDD_EINVAL;
     if (val[t] != 0) sc.order.push_back((int)(t - s0));
   }
-  std::sort(sc.order.begin(), sc.order.end(),
-            [&](int x, int y) { return col[s0 + x] < col[s0 + y]; });
+  // layer order: ascending place in the variable order (Appendix A.3), index order without one
+  if (rank)
+    std::sort(sc.order.begin(), sc.order.end(),
+              [&](int x, int y) { return rank[col[s0 + x]] < rank[col[s0 + y]]; });
+  else
+    std::sort(sc.order.begin(), sc.order.end(),
+              [&](int x, int y) { return col[s0 + x] < col[s0 + y]; });
   const int k = (int)sc.order.size();
   sc.a.resize(k);
   sc.pos.resize(k);
@@ -159,8 +164,8 @@ int compile_row(int j, const long long *row_ptr, const int *col, const int *val,
 }  // namespace
 
 int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const int *val,
-                 const int *b, const signed char *sense, int max_width, long long max_nodes,
-                 HostBDDs *H, int *failed_row) {
+                 const int *b, const signed char *sense, const int *rank, int max_width,
+                 long long max_nodes, HostBDDs *H, int *failed_row) {
   *failed_row = -1;
   const int rows_per_chunk = 2048;
   const int nchunks = (m + rows_per_chunk - 1) / rows_per_chunk;
@@ -177,7 +182,7 @@ int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const i
       Chunk &ch = chunks[cidx];
       int r0 = cidx * rows_per_chunk, r1 = std::min(m, r0 + rows_per_chunk);
       for (int j = r0; j < r1; ++j) {
-        int rc = compile_row(j, row_ptr, col, val, n, b[j], sense[j], max_width, sc, ch);
+        int rc = compile_row(j, row_ptr, col, val, rank, n, b[j], sense[j], max_width, sc, ch);
         if (rc != BDD_OK) {
           ch.status = rc;
           ch.failed_row = j;
@@ -333,12 +338,17 @@ int build_layout(const HostBDDs &H, Layout *L) {
   for (int i = 0; i < H.n; ++i) L->var_ptr[i + 1] += L->var_ptr[i];
   L->var_occ.assign(O, 0);
   L->occ_slot.assign(O, 0);
+  L->slot_dir.assign(O, 0);
   std::vector<int> fill(L->var_ptr.begin(), L->var_ptr.end() - 1);
-  for (long long co = 0; co < O; ++co) {
-    const int k = fill[H.occ_var[co]]++, o = L->occ_of_canon[co];
-    L->var_occ[k] = o;
-    L->occ_slot[o] = k;
-  }
+  for (long long b = 0; b < nb; ++b)
+    for (long long co = H.bdd_occ0[b]; co < H.bdd_occ0[b + 1]; ++co) {
+      const int k = fill[H.occ_var[co]]++, o = L->occ_of_canon[co];
+      L->var_occ[k] = o;
+      L->occ_slot[o] = k;
+      // SRMP sets (Appendix A.4): in J_i^> unless the last layer, in J_i^< unless the first
+      L->slot_dir[k] = (unsigned char)((co + 1 < H.bdd_occ0[b + 1] ? kDirForward : 0) |
+                                       (co > H.bdd_occ0[b] ? kDirBackward : 0));
+    }
   return BDD_OK;
 }
 

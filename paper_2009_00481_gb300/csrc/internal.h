@@ -35,8 +35,13 @@ struct HostBDDs {
 // Compiles every row (threshold counting over suffix-sum sets; see compile.cpp).
 // Returns a BDD_* status; *failed_row is the row that failed, or -1.
 int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const int *val,
-                 const int *b, const signed char *sense, int max_width, long long max_nodes,
-                 HostBDDs *out, int *failed_row);
+                 const int *b, const signed char *sense, const int *rank, int max_width,
+                 long long max_nodes, HostBDDs *out, int *failed_row);
+
+// SRMP membership bits of a slot (Appendix A.4): the occurrence takes a share in a forward
+// sweep (it is in J_i^>: not the last layer of its BDD) / a backward sweep (J_i^<: not the first).
+constexpr unsigned char kDirForward = 1;
+constexpr unsigned char kDirBackward = 2;
 
 // Team classes of the sweep kernels.  Class c < kWarpClasses: a team of T = 1 << c lanes per
 // BDD (lane t holds node t of the current layer), 32 / T BDDs per warp ("warp tile").
@@ -86,6 +91,7 @@ struct Layout {
   int max_block_width = 0;
   std::vector<int> var_ptr;            // [n+1]
   std::vector<int> var_occ;            // [O] device occurrence of each slot
+  std::vector<unsigned char> slot_dir; // [O] kDirForward / kDirBackward bits of each slot
   std::vector<int> occ_of_canon;       // canonical occurrence -> device occurrence
 };
 
@@ -145,6 +151,8 @@ struct PendingParams {
   int nb;
   double empty_const;
   double alpha;  // smoothing temperature of the slack term (0: min-sum)
+  const unsigned char *slot_dir;  // SRMP membership bits per slot, or null (eq. mma-update)
+  int next_dir;                   // kDirForward / kDirBackward: the sweep the shares are for
 };
 
 // Persistent iteration kernel (one cooperative launch runs n_iter iterations).
@@ -163,6 +171,7 @@ struct IterParams {
   int n;
   double empty_const;
   long long spin_limit;
+  const unsigned char *slot_dir;  // SRMP membership bits per slot, or null (eq. mma-update)
 };
 
 // Adjoint of one smoothed update sweep (adjoint.cu): checkpointed inputs, recomputed outputs and
@@ -183,8 +192,8 @@ struct AdjParams {
 };
 
 int sweep_adjoint_launch(bool forward, const AdjParams &a, int grid, cudaStream_t stream);
-int pending_adjoint_launch(const int *var_ptr, const int *var_occ, const float *g_shr, float *g_delta, int n,
-                           cudaStream_t stream);
+int pending_adjoint_launch(const int *var_ptr, const int *var_occ, const unsigned char *slot_dir, int dir,
+                           const float *g_shr, float *g_delta, int n, cudaStream_t stream);
 int bound_seed_launch(const int *var_ptr, const float *P, const float *c, float *g_delta, float *g_c, int n,
                       float alpha, const double *g_bound, cudaStream_t stream);
 int initial_adjoint_launch(const int *var_ptr, const int *var_occ, const float *g_lam0, float *g_c, int n,

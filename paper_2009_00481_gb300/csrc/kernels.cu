@@ -516,14 +516,26 @@ __device__ __forceinline__ double slack_term(double P, double alpha) {
 
 // Pending sums (the sum in eq. mma-update, deferred): P_i = sum of i's slots in ascending
 // order, stored, and share_i = P_i / |J_i| written to each of i's occurrences for the next sweep.
+// With SRMP bits (Appendix A.4), P_i / |J_i^dir| to the slots in J_i^dir and 0 to the others,
+// unless J_i^dir is empty (then P_i / |J_i| to all).
 __device__ __forceinline__ float pending_var(const float *__restrict__ delta, const int *__restrict__ var_ptr,
                                              const int *__restrict__ var_occ, float *__restrict__ P,
-                                             float *__restrict__ share_occ, int i, bool &has) {
+                                             float *__restrict__ share_occ, int i, bool &has,
+                                             const unsigned char *__restrict__ slot_dir, int dir) {
   const int s = var_ptr[i], e = var_ptr[i + 1];
   has = e > s;
   if (!has) return 0.f;
   const float Pi = slot_sum(delta, s, e);
   P[i] = Pi;
+  if (slot_dir) {
+    int cnt = 0;
+    for (int k = s; k < e; ++k) cnt += (slot_dir[k] & dir) != 0;
+    if (cnt > 0) {
+      const float share = Pi / (float)cnt;
+      for (int k = s; k < e; ++k) share_occ[var_occ[k]] = (slot_dir[k] & dir) ? share : 0.f;
+      return Pi;
+    }
+  }
   const float share = Pi / (float)(e - s);
   for (int k = s; k < e; k += 8) {  // occurrence ids eight at a time, then the stores
     int o[8];
@@ -547,7 +559,7 @@ __global__ void __launch_bounds__(kReduceThreads) pending_kernel(const PendingPa
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < range; i += gridDim.x * blockDim.x) {
     if (i < p.n) {
       bool has;
-      const float Pi = pending_var(p.delta, p.var_ptr, p.var_occ, p.P, p.share_occ, i, has);
+      const float Pi = pending_var(p.delta, p.var_ptr, p.var_occ, p.P, p.share_occ, i, has, p.slot_dir, p.next_dir);
       if (BOUND && has) acc += slack_term((double)Pi, p.alpha);
     }
     if (BOUND && i < p.nb) acc += (double)p.bdd_E[i];
@@ -649,11 +661,11 @@ __device__ __forceinline__ void persistent_phase(const SweepParams &p, float *sm
 }
 
 // pending sums and shares of a grid-stride range of variables; returns sum of min(0, P_i)
-__device__ __forceinline__ double persistent_pending(const IterParams &q) {
+__device__ __forceinline__ double persistent_pending(const IterParams &q, int next_dir) {
   double acc = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q.n; i += gridDim.x * blockDim.x) {
     bool has;
-    const float Pi = pending_var(q.sp.delta, q.var_ptr, q.var_occ, q.P, q.share_occ, i, has);
+    const float Pi = pending_var(q.sp.delta, q.var_ptr, q.var_occ, q.P, q.share_occ, i, has, q.slot_dir, next_dir);
     if (has && Pi < 0.f) acc += (double)Pi;
   }
   return acc;
@@ -682,14 +694,14 @@ __global__ void __launch_bounds__(kPersistThreads, 1) iterate_kernel(const IterP
     persistent_phase<true>(p, smem, bacc);
     if (blockIdx.x == 0 && it > 0) finalize_bound(q, it - 1, red);  // partials of it-1 are final
     if (!grid_barrier(q, failed)) return;
-    persistent_pending(q);
+    persistent_pending(q, kDirBackward);
     if (!grid_barrier(q, failed)) return;
     bacc = 0.0;
     persistent_phase<false>(p, smem, bacc);
     double sum = block_sum(bacc, red, kPersistWarps);
     if (threadIdx.x == 0) q.part[blockIdx.x] = sum;  // E^j part
     if (!grid_barrier(q, failed)) return;
-    sum = block_sum(persistent_pending(q), red, kPersistWarps);
+    sum = block_sum(persistent_pending(q, kDirForward), red, kPersistWarps);
     if (threadIdx.x == 0) q.part[G + blockIdx.x] = sum;  // slack part
     if (!grid_barrier(q, failed)) return;
   }

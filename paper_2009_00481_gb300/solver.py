@@ -14,13 +14,26 @@ class Solver:
 
     ``inst`` needs attributes n, m, row_ptr, col, val, b, sense, c (CSR form; see
     ``include/bdd_dbca.h``).  ``omega`` damps the min-marginal difference; ``alpha > 0`` selects
-    the smoothed (log-sum-exp) variant.
+    the smoothed (log-sum-exp) variant.  ``rank`` (a permutation of 0..n-1, or "cm" for
+    :func:`cuthill_mckee`) sets the variable order of the BDD layers; ``averaging`` 1 selects
+    SRMP averaging instead of eq. mma-update.
     """
 
     def __init__(self, inst, omega: float = 0.5, host_only: bool = False, max_device_bytes: int = 0,
                  device: int = -1, stream: int = 0, schedule: int = 1, spin_limit: int = 0,
-                 alpha: float = 0.0):
+                 alpha: float = 0.0, rank=None, averaging: int = 0):
+        import numpy as np
         opt = B.bdd_default_options()
+        if isinstance(rank, str):
+            if rank != "cm":
+                raise ValueError("rank must be None, 'cm' or a permutation")
+            rank = cuthill_mckee(inst)
+        self.rank = None if rank is None else np.ascontiguousarray(rank, np.int32)
+        if self.rank is not None:
+            if self.rank.shape != (inst.n,):
+                raise ValueError("rank must have one entry per variable")
+            opt.var_rank = self.rank.ctypes.data_as(B.C.POINTER(B.C.c_int))
+        opt.averaging = int(averaging)
         opt.alpha = float(alpha)
         opt.schedule = int(schedule)
         if spin_limit:
@@ -82,3 +95,9 @@ class Solver:
 
     def set_costs(self, c):
         B.bdd_set_costs(self.h, c)
+
+
+def cuthill_mckee(inst):
+    """Variable order of the Cuthill-McKee search on the bipartite variable-constraint graph of
+    ``inst`` (Appendix A.3); rank[i] is the place of variable i."""
+    return B.bdd_cuthill_mckee(inst.n, inst.m, inst.row_ptr, inst.col, inst.val)

@@ -146,3 +146,30 @@ def test_srmp_hand_example():
     assert D.weights(0, True, True) == [1.0, 0.0]
     assert D.weights(0, False, True) == [0.5, 0.5]
     assert D.weights(1, True, True) == [1.0]
+
+
+def test_srmp_fold_keeps_the_invariant():
+    """Folding the forward sweep's SRMP shares into lambda keeps sum_j lambda^j_i = c_i, puts
+    nothing on a last-layer occurrence of a variable that has other occurrences in J_i^>, and
+    equals the plain fold P_i / |J_i| when SRMP is off."""
+    inst = tracking(frames=3, dets=6, seed=3)
+    o = Oracle(inst)
+    o.set_srmp()
+    o.run_parallel(7, omega=0.5)
+    lam, unf, P = o.lam(fold=True), o.lam(fold=False), o.pending()
+    sums = np.zeros(inst.n)
+    np.add.at(sums, inst.col, lam)
+    deg = np.bincount(inst.col[inst.val != 0], minlength=inst.n)
+    np.testing.assert_allclose(sums[deg > 0], inst.c[deg > 0], rtol=0, atol=1e-12)
+    can = o.canonical()
+    last = np.zeros(len(can["occ_var"]), bool)
+    last[np.cumsum(can["bdd_depth"]) - 1] = True
+    first = np.zeros_like(last)
+    first[np.concatenate([[0], np.cumsum(can["bdd_depth"])[:-1]])] = True
+    for occ in np.nonzero(last & ~first)[0]:
+        i = can["occ_var"][occ]
+        if np.any(~last[can["occ_var"] == i]):
+            assert lam[can["occ_csr"][occ]] == unf[can["occ_csr"][occ]]
+    p = Oracle(inst)
+    p.set_state(unf, P)
+    np.testing.assert_allclose(p.lam(fold=True), unf + (P / np.maximum(deg, 1))[inst.col], rtol=0, atol=1e-15)
