@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batch workload part of the default line")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation part of the default line")
     ap.add_argument("--diff-steps", type=int, default=3)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the variable-order / averaging comparison of the default line")
+    ap.add_argument("--variant-iters", type=int, default=300)
+    ap.add_argument("--variants-only", action="store_true", help="print only the order / averaging comparison")
     return ap.parse_args()
 
 
@@ -286,6 +290,9 @@ def ours(args):
     diff = None
     if world == 1 and not args.no_diff:
         diff = run_differentiation(args, stream)
+    variants = None
+    if world == 1 and not args.no_variants:
+        variants = run_variants(args, stream)
 
     if rank != 0:
         if world > 1:
@@ -317,6 +324,7 @@ def ours(args):
         "e2e": e2e,
         "batched": batch,
         "differentiation": diff,
+        "order_and_averaging": variants,
         "gpu_launches": launches,
         "schedule": "persistent" if s.schedule == 0 else "per-phase graphs",
         "clocks": clocks,
@@ -545,6 +553,47 @@ def run_differentiation(args, stream) -> dict:
     }
 
 
+def run_variants(args, stream) -> dict:
+    """Variable order (index vs Cuthill-McKee, Appendix A.3) x averaging (eq. mma-update vs SRMP,
+    Appendix A.4) on the MRF workload (Potts 20x20 grid, 3 labels) and the cell-tracking-shaped
+    flow ILP (50 frames x 200 detections), where the paper reorders variables: bound after
+    --variant-iters iterations, iterations until the bound is within 1e-3 (relative) of the best
+    final bound of the four variants, and device ms per iteration."""
+    import torch
+
+    from paper_2009_00481_gb300 import Solver, cuthill_mckee
+
+    K = args.variant_iters
+    out = {"iterations": K, "target_tol": TTB_TOL}
+    for k in (0, 3):
+        inst = config(k)
+        cm = cuthill_mckee(inst)
+        trace = torch.zeros(K, dtype=torch.float64, device="cuda")
+        res = {}
+        for order, rank in (("index", None), ("cm", cm)):
+            for avg, name in ((0, "mma"), (1, "srmp")):
+                s = Solver(inst, omega=0.5, stream=stream.cuda_stream, rank=rank, averaging=avg)
+                s.iterate_device(K, trace=trace, stream=stream.cuda_stream)  # warm-up (graphs)
+                s.set_costs(inst.c)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                s.iterate_device(K, trace=trace, stream=stream.cuda_stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                res[f"{order}/{name}"] = {"trace": trace.cpu().numpy(), "ms_per_iter": a.elapsed_time(b) / K}
+                s.close()
+        best = max(float(v["trace"][-1]) for v in res.values())
+        target = best - TTB_TOL * abs(best)
+        row = {}
+        for key, v in res.items():
+            hit = np.nonzero(v["trace"] >= target)[0]
+            row[key] = {"bound": float(v["trace"][-1]), "iters_to_target": int(hit[0]) + 1 if hit.size else None,
+                        "ms_per_iter": v["ms_per_iter"]}
+        out[CONFIG_NAMES[k]] = {"best_bound": best, "target": target, "variants": row}
+    return out
+
+
 def batched(args):
     """`--config 4`: the batch workload as the bench line."""
     import torch
@@ -606,6 +655,12 @@ def main():
         reference(args)
     elif args.config == 4:
         batched(args)
+    elif args.variants_only:
+        import torch
+        torch.cuda.set_device(0)
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        print(json.dumps({"metric": METRIC, "order_and_averaging": run_variants(args, stream)}), flush=True)
     elif args.config == 3:
         import torch
         torch.cuda.set_device(0)
