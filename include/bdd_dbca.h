@@ -90,6 +90,15 @@ typedef struct {
                                  J_i.  Under the deferred schedule the set of a sweep applies
                                  to the shares that sweep adds.  Folded outputs (multipliers and
                                  min-marginals) add the forward-sweep shares. */
+  int fused_pending;          /* schedule 1 only.  1: the pending sums are formed inside the
+                                 sweeps (each variable's last visit in a sweep sums its slots and
+                                 writes the next sweep's shares; a forward sweep also reduces
+                                 the previous iteration's bound), two kernels per iteration.
+                                 0: separate pending-sum kernels, four per iteration.  -1
+                                 (default): 0, the faster plan on every workload measured.
+                                 Same arithmetic either way: multipliers and pending sums are
+                                 bit-identical; bounds differ only in the FP64 summation
+                                 order. */
 } bdd_options;
 
 void bdd_default_options(bdd_options *opt);

@@ -31,7 +31,8 @@ class bdd_options(C.Structure):
     _fields_ = [("omega", C.c_float), ("max_width", C.c_int), ("max_nodes", C.c_longlong),
                 ("max_device_bytes", C.c_longlong), ("host_only", C.c_int), ("device", C.c_int),
                 ("stream", C.c_void_p), ("schedule", C.c_int), ("spin_limit", C.c_longlong),
-                ("alpha", C.c_float), ("var_rank", C.POINTER(C.c_int)), ("averaging", C.c_int)]
+                ("alpha", C.c_float), ("var_rank", C.POINTER(C.c_int)), ("averaging", C.c_int),
+                ("fused_pending", C.c_int)]
 
 
 class BDDError(RuntimeError):

@@ -92,7 +92,15 @@ struct bdd_solver {
   int *d_tile_occ0 = nullptr, *d_tile_bdd0 = nullptr, *d_tile_nbdd = nullptr;
   int *d_var_ptr = nullptr, *d_var_occ = nullptr;
   int averaging = 0;                     // 0: eq. mma-update; 1: SRMP (Appendix A.4)
+  bool fused = false;                    // per-phase plan: pending pass fused into the sweeps
+  int fused_opt = -1;                    // bdd_options.fused_pending
+  int *d_cnt = nullptr;                  // [n] fused plan: visits still to come per variable
+  double *d_slk = nullptr;               // [n] fused plan: slack terms of the last backward sweep
+  double *d_fpartial = nullptr;          // fused plan: per-block bound partials
+  unsigned *d_fticket = nullptr;
   unsigned char *d_slot_dir = nullptr;   // SRMP membership bits per slot (averaging == 1)
+  int4 *d_heavy = nullptr;               // variables with more than 8 occurrences: {i, s, e, 0}
+  int n_heavy = 0;
   // persistent schedule
   int schedule = 1;
   long long spin_limit = 1LL << 26;
@@ -146,7 +154,7 @@ struct bdd_solver {
   }
 
   SweepParams sweep_params(float *out_m0 = nullptr, float *out_m1 = nullptr) const {
-    SweepParams p;
+    SweepParams p{};  // value-initialised: no fused pass unless fused_params() sets one
     p.occ_node_off = d_occ_node_off;
     p.occ_csr = d_occ_csr;
     p.lohi = d_lohi;
@@ -173,10 +181,37 @@ struct bdd_solver {
     return p;
   }
 
+  // parameters of the fused plan's update sweeps (bound: reduce the previous iteration's bound at
+  // the start of a forward sweep)
+  SweepParams fused_params(bool bound) const {
+    SweepParams p = sweep_params();
+    FusedParams &z = p.fz;
+    z.cnt = d_cnt;
+    z.occ_var = d_occ_var;
+    z.var_ptr = d_var_ptr;
+    z.var_occ = d_var_occ;
+    z.P = d_P;
+    z.share = d_share_occ;
+    z.slot_dir = d_slot_dir;
+    z.slk = d_slk;
+    z.bound = bound ? 1 : 0;
+    z.partial = d_fpartial;
+    z.ticket = d_fticket;
+    z.iter_ctr = d_iter;
+    z.trace = d_trace;
+    z.trace_cap = trace_cap;
+    z.n = n;
+    z.nb = (int)nb;
+    z.empty_const = empty_const;
+    return p;
+  }
+
   PendingParams pending_params(int next_dir) const {
-    PendingParams r;
+    PendingParams r{};
     r.slot_dir = d_slot_dir;
     r.next_dir = next_dir;
+    r.heavy = d_heavy;
+    r.n_heavy = n_heavy;
     r.var_ptr = d_var_ptr;
     r.var_occ = d_var_occ;
     r.delta = d_delta;
@@ -217,8 +252,16 @@ struct bdd_solver {
     return pending_launch(bound, pending_params(next_dir), grid_reduce, s) ? BDD_ECUDA : BDD_OK;
   }
 
-  // one iteration: forward sweep, pending sums, backward sweep, pending sums and bound
-  int enqueue_iteration(cudaStream_t s) {
+  // one iteration: forward sweep, pending sums, backward sweep, pending sums and bound.  Fused
+  // plan: forward sweep (reducing the previous iteration's bound unless `first`), backward
+  // sweep, and with `last` the bound kernel.
+  int enqueue_iteration(cudaStream_t s, bool first = true, bool last = true) {
+    if (fused) {
+      if (sweep_launch(true, kUpdateFused, fused_params(!first), grid_sweep, s)) return BDD_ECUDA;
+      if (sweep_launch(false, kUpdateFused, fused_params(false), grid_sweep, s)) return BDD_ECUDA;
+      if (last && bound_launch(fused_params(false), grid_reduce, s)) return BDD_ECUDA;
+      return BDD_OK;
+    }
     RC(sweep(true, kUpdate, s));
     RC(pending(false, s));
     RC(sweep(false, kUpdate, s));
@@ -227,7 +270,7 @@ struct bdd_solver {
   }
 
   int launch_persistent(int n_iter, cudaStream_t s) {
-    IterParams q;
+    IterParams q{};
     q.sp = sweep_params();
     q.var_ptr = d_var_ptr;
     q.var_occ = d_var_occ;
@@ -243,6 +286,8 @@ struct bdd_solver {
     q.empty_const = empty_const;
     q.spin_limit = spin_limit;
     q.slot_dir = d_slot_dir;
+    q.heavy = d_heavy;
+    q.n_heavy = n_heavy;
     CK(cudaMemsetAsync(d_barrier, 0, 2 * sizeof(unsigned), s));
     return iterate_persistent_launch(q, grid_persist, smem_persist, s) ? BDD_ECUDA : BDD_OK;
   }
@@ -265,7 +310,7 @@ struct bdd_solver {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = BDD_OK;
-    for (int t = 0; t < iters && rc == BDD_OK; ++t) rc = enqueue_iteration(cap_stream);
+    for (int t = 0; t < iters && rc == BDD_OK; ++t) rc = enqueue_iteration(cap_stream, t == 0, t == iters - 1);
     cudaError_t e = cudaStreamEndCapture(cap_stream, &g);
     if (rc != BDD_OK || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -378,13 +423,17 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
       h->schedule = 1;  // no cooperative launch (or not enough shared memory) on this device
     }
   }
+  // per-phase plan: the pending pass fused into the sweeps only when asked for (measured slower:
+  // a variable's last visit finishes it on one lane, and a warp's tail serialises many such
+  // variables, longer than the separate pending kernel takes)
+  h->fused = h->schedule == 1 && h->fused_opt == 1;
 
   // device memory estimate against the cap, before allocating anything
   const long long O = h->O, N = h->N, nb = h->nb, n = h->n;
   const long long ntiles = (long long)L.tile_bdd0.size();
   long long need = (O + 1) * 4 + O * 4 + O * 8 + N * 8 + 2 * N * 4 + 2 * O * 4 + 3 * (long long)n * 4 +
                    nb * 8 + 3 * ntiles * 4 + (n + 1) * 4 + O * 4 + h->grid_reduce * 8 + 1024 * 8 +
-                   (h->averaging == 1 ? O : 0);
+                   (h->averaging == 1 ? O : 0) + (h->fused ? 12 * n + 8LL * (h->grid_sweep + h->grid_reduce) : 0);
   if (h->max_device_bytes > 0 && need > h->max_device_bytes) return BDD_ENOMEM;
 
   RC(upload(h, &h->d_occ_node_off, L.occ_node_off));
@@ -420,6 +469,21 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   RC(upload(h, &h->d_var_ptr, L.var_ptr));
   RC(upload(h, &h->d_var_occ, L.var_occ));
   if (h->averaging == 1) RC(upload(h, &h->d_slot_dir, L.slot_dir));
+  {
+    std::vector<int4> heavy;
+    for (int i = 0; i < h->n; ++i)
+      if (L.var_ptr[i + 1] - L.var_ptr[i] > 8) heavy.push_back(make_int4(i, L.var_ptr[i], L.var_ptr[i + 1], 0));
+    h->n_heavy = (int)heavy.size();
+    if (!heavy.empty()) RC(upload(h, &h->d_heavy, heavy));
+  }
+  if (h->fused) {
+    RC(upload(h, &h->d_cnt, h->var_deg));
+    RC(h->alloc(&h->d_slk, n));
+    if (n) CK(cudaMemset(h->d_slk, 0, sizeof(double) * n));
+    RC(h->alloc(&h->d_fpartial, std::max(h->grid_sweep, h->grid_reduce)));
+    RC(h->alloc(&h->d_fticket, 1));
+    CK(cudaMemset(h->d_fticket, 0, sizeof(unsigned)));
+  }
   RC(h->alloc(&h->d_partial, h->grid_reduce));
   RC(h->alloc(&h->d_ticket, 1));
   RC(h->alloc(&h->d_iter, 1));
@@ -468,6 +532,7 @@ void bdd_default_options(bdd_options *opt) {
   opt->alpha = 0.f;
   opt->var_rank = nullptr;
   opt->averaging = 0;
+  opt->fused_pending = -1;
 }
 
 int bdd_last_failed_row(void) { return g_failed_row; }
@@ -493,6 +558,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   if (nnz > 0 && (!col || !val)) return BDD_EINVAL;
   if (!finite_costs(c, n)) return BDD_EINVAL;
   if (opt.averaging < 0 || opt.averaging > 1) return BDD_EINVAL;
+  if (opt.fused_pending < -1 || opt.fused_pending > 1) return BDD_EINVAL;
   if (opt.var_rank) {  // a permutation of 0..n-1
     std::vector<char> seen;
     try {
@@ -515,6 +581,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   h->omega = opt.omega;
   h->alpha = opt.alpha;
   h->averaging = opt.averaging;
+  h->fused_opt = opt.fused_pending;
   h->schedule = opt.alpha > 0.f ? 1 : opt.schedule;  // the persistent kernel runs min-sum only
   h->spin_limit = opt.spin_limit;
   if (opt.schedule < 0 || opt.schedule > 1 || opt.spin_limit < 1) {
@@ -662,6 +729,16 @@ int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms) {
     for (int t = 0; t < cnt && rc == BDD_OK; ++t) {
       cudaEvent_t *e = &ev[5 * t];
       if (cudaEventRecord(e[0], s) != cudaSuccess) rc = BDD_ECUDA;
+      if (h->fused) {  // forward sweep, (no separate pending pass), backward sweep, bound
+        if (rc == BDD_OK && sweep_launch(true, kUpdateFused, h->fused_params(false), h->grid_sweep, s)) rc = BDD_ECUDA;
+        if (rc == BDD_OK && cudaEventRecord(e[1], s) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK && cudaEventRecord(e[2], s) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK && sweep_launch(false, kUpdateFused, h->fused_params(false), h->grid_sweep, s)) rc = BDD_ECUDA;
+        if (rc == BDD_OK && cudaEventRecord(e[3], s) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK && bound_launch(h->fused_params(false), h->grid_reduce, s)) rc = BDD_ECUDA;
+        if (rc == BDD_OK && cudaEventRecord(e[4], s) != cudaSuccess) rc = BDD_ECUDA;
+        continue;
+      }
       if (rc == BDD_OK) rc = h->sweep(true, kUpdate, s);
       if (rc == BDD_OK && cudaEventRecord(e[1], s) != cudaSuccess) rc = BDD_ECUDA;
       if (rc == BDD_OK) rc = h->pending(false, s);
@@ -831,7 +908,7 @@ int bdd_smooth_backward(bdd_solver *h, const double *d_gbound, float *d_grad_c, 
       if (sweep_launch(true, kMessages, p, h->grid_sweep, s)) return BDD_ECUDA;
       if (sweep_launch(false, kUpdate, p, h->grid_sweep, s)) return BDD_ECUDA;
     }
-    AdjParams a;
+    AdjParams a{};
     a.sp = h->sweep_params();
     a.lam_s = lam_s;
     a.shr_s = shr_s;

@@ -97,6 +97,31 @@ struct Layout {
 
 int build_layout(const HostBDDs &H, Layout *L);
 
+// Fused pending pass of an update sweep (the per-phase plan without separate pending kernels).
+// At the end of its tile every occurrence counts its variable down; the visit that brings the
+// count to zero is the variable's last in this sweep, so all of its slots are final: it forms
+// P_i, writes the shares of the next sweep and resets the count.  A forward sweep may also
+// reduce the FP64 bound of the previous iteration from the backward sweep's E^j and slack terms.
+struct FusedParams {
+  int *cnt;                       // [n] visits of i still to come in this sweep; null: no fused pass
+  const int *occ_var;             // [O]
+  const int *var_ptr;             // [n + 1]
+  const int *var_occ;             // [O]
+  float *P;                       // [n] pending sums
+  float *share;                   // [O] shares of the next sweep (the sweep's share_occ buffer)
+  const unsigned char *slot_dir;  // SRMP membership bits per slot, or null
+  double *slk;                    // [n] slack term of each variable's pending sum (backward sweeps)
+  int bound;                      // forward sweep: reduce the previous iteration's bound first
+  double *partial;                // [gridDim.x] per-block partial sums of the bound
+  unsigned *ticket;
+  int *iter_ctr;
+  double *trace;
+  int trace_cap;
+  int n;
+  int nb;
+  double empty_const;
+};
+
 // Kernel parameter blocks (passed by value).
 struct SweepParams {
   const int *occ_node_off;
@@ -122,6 +147,7 @@ struct SweepParams {
   float omega;
   float alpha;          // smoothing temperature (0: min-sum)
   float inv_alpha;
+  FusedParams fz;       // fz.cnt == null outside the fused plan
 };
 
 // Sweep modes.
@@ -129,7 +155,9 @@ enum SweepMode : int {
   kUpdate = 0,   // add the pending share, take min-marginals, move lambda, record delta
   kMessages = 1, // messages only (no share, no update); backward form also records E^j
   kFolded = 2,   // messages and min-marginals at lambda + share, nothing stored but messages
+  kUpdateFused = 3,  // kUpdate plus the fused pending pass (SweepParams::fz)
 };
+__host__ __device__ constexpr bool is_update(int mode) { return mode == kUpdate || mode == kUpdateFused; }
 
 // Pending pass: P_i = sum of i's slots, stored; share_i = P_i / |J_i| written to each of i's
 // occurrences; optionally the FP64 y-slack bound sum_j E^j + sum_i min(0, P_i) + empty_const,
@@ -153,6 +181,8 @@ struct PendingParams {
   double alpha;  // smoothing temperature of the slack term (0: min-sum)
   const unsigned char *slot_dir;  // SRMP membership bits per slot, or null (eq. mma-update)
   int next_dir;                   // kDirForward / kDirBackward: the sweep the shares are for
+  const int4 *heavy;              // variables with more than 8 occurrences: {i, first slot, end slot, 0}
+  int n_heavy;                    // (handled by one warp each)
 };
 
 // Persistent iteration kernel (one cooperative launch runs n_iter iterations).
@@ -172,6 +202,8 @@ struct IterParams {
   double empty_const;
   long long spin_limit;
   const unsigned char *slot_dir;  // SRMP membership bits per slot, or null (eq. mma-update)
+  const int4 *heavy;              // as in PendingParams
+  int n_heavy;
 };
 
 // Adjoint of one smoothed update sweep (adjoint.cu): checkpointed inputs, recomputed outputs and
@@ -206,6 +238,8 @@ int sweep_set_smem(size_t bytes);
 int iterate_set_smem(size_t bytes);
 int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStream_t stream);
 int pending_launch(bool bound, const PendingParams &p, int grid, cudaStream_t stream);
+// FP64 bound from the E^j and slack terms of the last fused backward sweep into trace[*iter_ctr]
+int bound_launch(const SweepParams &p, int grid, cudaStream_t stream);
 int iterate_persistent_max_grid(size_t smem, int *grid);
 int iterate_persistent_launch(const IterParams &q, int grid, size_t smem, cudaStream_t stream);
 int init_lambda_launch(const int *occ_var, const int *var_ptr, const float *c, float *lam, int O,

@@ -104,6 +104,171 @@ __device__ __forceinline__ float slot_sum(const float *__restrict__ d, int s, in
   return P;
 }
 
+// y-slack term of one variable: min(0, P) for min-sum, its soft minimum for alpha > 0 (FP64)
+__device__ __forceinline__ double slack_term(double P, double alpha) {
+  if (alpha <= 0.0) return P < 0.0 ? P : 0.0;
+  const double m = P < 0.0 ? P : 0.0;
+  return m - alpha * log1p(exp(-fabs(P) / alpha));
+}
+
+// Pending sums (the sum in eq. mma-update, deferred): P_i = sum of i's slots in ascending
+// order, stored, and share_i = P_i / |J_i| written to each of i's occurrences for the next sweep.
+// With SRMP bits (Appendix A.4), P_i / |J_i^dir| to the slots in J_i^dir and 0 to the others,
+// unless J_i^dir is empty (then P_i / |J_i| to all).
+// FAST > 0: one round of loads for variables with at most FAST occurrences (slots, occurrence
+// ids and SRMP bits together); FAST = 0: slot_sum, then the occurrence ids eight at a time.
+// SKIP_HEAVY: variables with more than 8 occurrences are left to pending_var_warp (has = false).
+template <int FAST, bool SKIP_HEAVY = false>
+__device__ __forceinline__ float pending_var(const float *__restrict__ delta, const int *__restrict__ var_ptr,
+                                             const int *__restrict__ var_occ, float *__restrict__ P,
+                                             float *__restrict__ share_occ, int i, bool &has,
+                                             const unsigned char *__restrict__ slot_dir, int dir) {
+  const int s = var_ptr[i], e = var_ptr[i + 1];
+  has = e > s && (!SKIP_HEAVY || e - s <= 8);
+  if (!has) return 0.f;
+  const int deg = e - s;
+  if (FAST > 0 && deg <= FAST) {
+    constexpr int W = FAST > 0 ? FAST : 1;
+    float v[W];
+    int o[W];
+    unsigned char d[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const bool in = j < deg;
+      v[j] = in ? __ldcg(delta + s + j) : 0.f;
+      o[j] = in ? var_occ[s + j] : -1;
+      d[j] = (in && slot_dir) ? slot_dir[s + j] : 0;
+    }
+    float Pi = 0.f;  // slot order, as slot_sum
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if (j < deg) Pi += v[j];
+    P[i] = Pi;
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) cnt += (d[j] & dir) != 0;
+    const float share = Pi / (float)(cnt > 0 ? cnt : deg);
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if (j < deg) share_occ[o[j]] = (cnt == 0 || (d[j] & dir)) ? share : 0.f;
+    return Pi;
+  }
+  const float Pi = slot_sum(delta, s, e);
+  P[i] = Pi;
+  if (slot_dir) {
+    int cnt = 0;
+    for (int k = s; k < e; ++k) cnt += (slot_dir[k] & dir) != 0;
+    if (cnt > 0) {
+      const float share = Pi / (float)cnt;
+      for (int k = s; k < e; ++k) share_occ[var_occ[k]] = (slot_dir[k] & dir) ? share : 0.f;
+      return Pi;
+    }
+  }
+  const float share = Pi / (float)(e - s);
+  for (int k = s; k < e; k += 8) {  // occurrence ids eight at a time, then the stores
+    int o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o[j] = k + j < e ? var_occ[k + j] : -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (o[j] >= 0) share_occ[o[j]] = share;
+  }
+  return Pi;
+}
+
+// The same pending sum and shares for one variable with many occurrences (slots [s, e)), by a
+// whole warp: slots, occurrence ids and SRMP bits arrive 32 at a time in one round of loads,
+// every lane adds the 32 values in slot order (the additions of slot_sum, so every lane holds
+// the same P_i), and the lanes write the shares.  Warp-uniform arguments.
+__device__ __forceinline__ float pending_var_warp(const float *__restrict__ delta, const int *__restrict__ var_occ,
+                                                  float *__restrict__ P, float *__restrict__ share_occ, int i, int s,
+                                                  int e, const unsigned char *__restrict__ slot_dir, int dir) {
+  const int lane = threadIdx.x & 31;
+  float Pi = 0.f;
+  int cnt = 0, o_first = -1;
+  bool take_first = false;
+  for (int k0 = s; k0 < e; k0 += 32) {
+    const int k = k0 + lane;
+    const bool in = k < e;
+    const float v = in ? __ldcg(delta + k) : 0.f;
+    const bool take = in && slot_dir && (slot_dir[k] & dir);
+    if (k0 == s) {
+      o_first = in ? var_occ[k] : -1;
+      take_first = take;
+    }
+    const int here = e - k0 < 32 ? e - k0 : 32;
+    for (int j = 0; j < here; ++j) Pi += __shfl_sync(kFull, v, j);
+    cnt += __popc(__ballot_sync(kFull, take));
+  }
+  if (lane == 0) P[i] = Pi;
+  const float share = Pi / (float)(cnt > 0 ? cnt : e - s);
+  if (o_first >= 0) share_occ[o_first] = (cnt == 0 || take_first) ? share : 0.f;
+  for (int k = s + 32 + lane; k < e; k += 32)
+    share_occ[var_occ[k]] = (cnt == 0 || (slot_dir[k] & dir)) ? share : 0.f;
+  return Pi;
+}
+
+// Fused pending pass, the part after a variable's last visit: P_i and the next sweep's shares
+// by pending_var (the pending kernel's own arithmetic), the count reset, the slack term.
+template <bool FWD>
+__device__ __forceinline__ void finish_variable(const SweepParams &p, int i) {
+  const FusedParams &z = p.fz;
+  bool has;
+  const float Pi = pending_var<16>(p.delta, z.var_ptr, z.var_occ, z.P, z.share, i, has, z.slot_dir,
+                               FWD ? kDirBackward : kDirForward);
+  z.cnt[i] = z.var_ptr[i + 1] - z.var_ptr[i];
+  if (!FWD) z.slk[i] = slack_term((double)Pi, p.alpha);
+}
+
+// Fused pending pass over the occurrences [o0, o0 + count) of a finished tile, by `nthreads`
+// threads (index t) that have all passed a barrier after the tile's last difference store.
+// Each occurrence counts its variable down (eight atomics in flight per thread); the visit that
+// brings a count to zero is the variable's last in this sweep and finishes it.  `list`
+// (warp tiles: shared memory for 8 * 32 ids) spreads the finished variables evenly over the
+// warp's lanes; without it (block tiles) each thread finishes its own.
+template <bool FWD>
+__device__ __forceinline__ void pending_tail(const SweepParams &p, int o0, int count, int t, int nthreads,
+                                             int *list) {
+  const FusedParams &z = p.fz;
+  __threadfence();  // the tile's difference slots are visible before its counts drop
+  for (int base = 0; base < count; base += 8 * nthreads) {
+    int iv[8], old[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = base + j * nthreads + t;
+      iv[j] = k < count ? z.occ_var[o0 + k] : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) old[j] = iv[j] >= 0 ? atomicSub(z.cnt + iv[j], 1) : 0;
+    int mine = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) mine += old[j] == 1;
+    if (list) {  // warp: exclusive prefix of the lanes' counts, then an even split
+      int incl = mine;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(kFull, incl, off);
+        if (t >= off) incl += u;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      if (total == 0) continue;
+      int pos = incl - mine;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (old[j] == 1) list[pos++] = iv[j];
+      __threadfence();  // every other visit's slots before reading them
+      __syncwarp();
+      for (int q = t; q < total; q += 32) finish_variable<FWD>(p, list[q]);
+      __syncwarp();  // the list is rewritten by the next round
+    } else if (mine) {
+      __threadfence();
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (old[j] == 1) finish_variable<FWD>(p, iv[j]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // warp tiles: T lanes per BDD, 32 / T BDDs per warp.  A tile's slab is contiguous and
 // layer-major, so a window of kWinLayers layers (<= 32 occurrences and <= 32 nodes per layer)
@@ -122,7 +287,7 @@ __device__ __forceinline__ void stage_occurrences(const SweepParams &p, const Ph
       cp_async4(&S.shr[k], &p.share_occ[oa + k]);
     else
       S.shr[k] = 0.f;
-    if (MODE == kUpdate) cp_async4(&S.slot[k], &p.occ_slot[oa + k]);
+    if (is_update(MODE)) cp_async4(&S.slot[k], &p.occ_slot[oa + k]);
   }
   cp_async_wait();
 }
@@ -150,7 +315,7 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
     __syncwarp();
     const int na = S.off[0], nb = S.off[nob];
     for (int k = lane; k < nb - na; k += 32) cp_async8(&S.lohi[k], &p.lohi[na + k]);
-    if (MODE == kUpdate) {
+    if (is_update(MODE)) {
       const int nc = S.off[nox];  // through the layer after the window: the arcs' targets
       for (int k = lane; k < nc - na; k += 32) cp_async4(&S.msg[k], &p.bm[na + k]);
     }
@@ -188,7 +353,7 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
         lh = S.lohi[node0 - na + tl];
       }
       float lam = active ? S.lam[oi] + S.shr[oi] : 0.f;
-      if (MODE == kUpdate) {
+      if (is_update(MODE)) {
         // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
         const float a0 = has ? f + staged_bm(S.msg, na, lh.x) : inf();
         const float a1 = has ? f + lam + staged_bm(S.msg, na, lh.y) : inf();
@@ -204,6 +369,10 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
       lh_prev = lh;
       lam_prev = lam;
     }
+  }
+  if (MODE == kUpdateFused) {
+    __syncwarp();
+    pending_tail<true>(p, occ0, __reduce_add_sync(kFull, lead_depth), lane, 32, S.slot);
   }
 }
 
@@ -259,7 +428,7 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
       const float b1 = lh.y >= 0 ? g1 : (lh.y == kTop ? 0.f : inf());
       if (MODE != kMessages) {
         const float m0 = team_agg<T, SMOOTH>(f + b0, p), m1 = team_agg<T, SMOOTH>(f + lam + b1, p);
-        if (MODE == kUpdate) {
+        if (is_update(MODE)) {
           const float dd = p.omega * mm_difference(m0, m1);
           lam -= dd;
           if (active && tl == 0) {
@@ -282,6 +451,10 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
       b_next = bcur;
       node0_next = node0;
     }
+  }
+  if (MODE == kUpdateFused) {
+    __syncwarp();
+    pending_tail<false>(p, occ0, __reduce_add_sync(kFull, lead_depth), lane, 32, S.slot);
   }
 }
 
@@ -356,13 +529,13 @@ __device__ __forceinline__ void block_forward(const SweepParams &p, const Phase 
     for (int t = gt; t < w; t += kBlockThreads) {
       const float f = cur[t];
       p.fm[node0 + t] = f;
-      if (MODE == kUpdate) {
+      if (is_update(MODE)) {
         const int2 lh = p.lohi[node0 + t];
         a0 = fminf(a0, f + target_bm(p.bm, lh.x));
         a1 = fminf(a1, f + lam + target_bm(p.bm, lh.y));
       }
     }
-    if (MODE == kUpdate) {
+    if (is_update(MODE)) {
       const float2 mm = group_min2(a0, a1, g.red, group, gt);
       const float dd = p.omega * mm_difference(mm.x, mm.y);
       lam -= dd;
@@ -414,7 +587,7 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
         a1 = fminf(a1, f + lam + b1);
       }
       const float2 mm = group_min2(a0, a1, g.red, group, gt);
-      if (MODE == kUpdate) {
+      if (is_update(MODE)) {
         const float dd = p.omega * mm_difference(mm.x, mm.y);
         lam -= dd;
         if (gt == 0) {
@@ -486,10 +659,49 @@ __device__ __forceinline__ double block_sum(double v, double *red, int nwarps) {
 // ---------------------------------------------------------------------------------------
 // per-phase kernels
 // ---------------------------------------------------------------------------------------
+// FP64 bound of the last fused backward sweep: sum_j E^j + sum_i slack_i + empty_const, every
+// thread of the grid taking a grid-stride share, per-block partials finished in block order by
+// the last block to arrive (warp 0 of each block handles the ticket; the other warps go on).
+// Needs every thread of the block; blockDim.x = nthreads.
+__device__ __forceinline__ void fused_bound(const FusedParams &z, const float *__restrict__ bdd_E, int nthreads) {
+  __shared__ double red[kReduceThreads / 32];
+  const int range = z.n > z.nb ? z.n : z.nb;
+  double acc = 0.0;
+  for (int i = blockIdx.x * nthreads + threadIdx.x; i < range; i += gridDim.x * nthreads) {
+    if (i < z.n) acc += z.slk[i];
+    if (i < z.nb) acc += (double)bdd_E[i];
+  }
+  const double blk = block_sum(acc, red, nthreads / 32);
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  unsigned last = 0;
+  if (lane == 0) {
+    z.partial[blockIdx.x] = blk;
+    __threadfence();
+    last = atomicAdd(z.ticket, 1u) == gridDim.x - 1;
+  }
+  if (!__shfl_sync(kFull, last, 0)) return;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned t = lane; t < gridDim.x; t += 32) s += __ldcg(z.partial + t);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+  if (lane == 0) {
+    const int it = *z.iter_ctr;
+    if (it < z.trace_cap) z.trace[it] = s + z.empty_const;
+    *z.iter_ctr = it + 1;
+    *z.ticket = 0u;
+  }
+}
+
 template <bool FWD, int MODE, bool SMOOTH>
 __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams p) {
   extern __shared__ __align__(16) float smem[];
   pdl_enter();
+  if (FWD && MODE == kUpdateFused && p.fz.bound) {  // bound of the previous iteration (fused plan)
+    fused_bound(p.fz, p.bdd_E, kBlockThreads);
+    if (threadIdx.x < 32) __syncwarp();
+  }
   const Phase ph{p.delta};
   double bacc = 0.0;
   if ((int)blockIdx.x < p.n_warp_blocks) {
@@ -504,65 +716,42 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
       block_forward<MODE>(p, ph, tile, g, 0, threadIdx.x, bacc);
     else
       block_backward<MODE>(p, ph, tile, g, 0, threadIdx.x, bacc);
-  }
-}
-
-// y-slack term of one variable: min(0, P) for min-sum, its soft minimum for alpha > 0 (FP64)
-__device__ __forceinline__ double slack_term(double P, double alpha) {
-  if (alpha <= 0.0) return P < 0.0 ? P : 0.0;
-  const double m = P < 0.0 ? P : 0.0;
-  return m - alpha * log1p(exp(-fabs(P) / alpha));
-}
-
-// Pending sums (the sum in eq. mma-update, deferred): P_i = sum of i's slots in ascending
-// order, stored, and share_i = P_i / |J_i| written to each of i's occurrences for the next sweep.
-// With SRMP bits (Appendix A.4), P_i / |J_i^dir| to the slots in J_i^dir and 0 to the others,
-// unless J_i^dir is empty (then P_i / |J_i| to all).
-__device__ __forceinline__ float pending_var(const float *__restrict__ delta, const int *__restrict__ var_ptr,
-                                             const int *__restrict__ var_occ, float *__restrict__ P,
-                                             float *__restrict__ share_occ, int i, bool &has,
-                                             const unsigned char *__restrict__ slot_dir, int dir) {
-  const int s = var_ptr[i], e = var_ptr[i + 1];
-  has = e > s;
-  if (!has) return 0.f;
-  const float Pi = slot_sum(delta, s, e);
-  P[i] = Pi;
-  if (slot_dir) {
-    int cnt = 0;
-    for (int k = s; k < e; ++k) cnt += (slot_dir[k] & dir) != 0;
-    if (cnt > 0) {
-      const float share = Pi / (float)cnt;
-      for (int k = s; k < e; ++k) share_occ[var_occ[k]] = (slot_dir[k] & dir) ? share : 0.f;
-      return Pi;
+    if (MODE == kUpdateFused) {
+      group_sync(0);
+      pending_tail<FWD>(p, p.tile_occ0[tile], p.bdd_depth[p.tile_bdd0[tile]], threadIdx.x, kBlockThreads,
+                        nullptr);
     }
   }
-  const float share = Pi / (float)(e - s);
-  for (int k = s; k < e; k += 8) {  // occurrence ids eight at a time, then the stores
-    int o[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) o[j] = k + j < e ? var_occ[k + j] : -1;
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (o[j] >= 0) share_occ[o[j]] = share;
-  }
-  return Pi;
+}
+
+// the bound of the last iteration of a fused chain (no forward sweep follows to reduce it)
+__global__ void __launch_bounds__(kReduceThreads) bound_kernel(const SweepParams p) {
+  pdl_enter();
+  fused_bound(p.fz, p.bdd_E, kReduceThreads);
 }
 
 // With `bound`, also the FP64 y-slack lower bound sum_j E^j + sum_i min(0, P_i) (+ the constant
 // of variables in no row): per-block partials summed in a fixed order by the last block to
 // finish, written to trace[*iter_ctr].
 template <bool BOUND>
-__global__ void __launch_bounds__(kReduceThreads) pending_kernel(const PendingParams p) {
+__global__ void __launch_bounds__(kReduceThreads, 8) pending_kernel(const PendingParams p) {
   pdl_enter();
   const int range = BOUND ? (p.n > p.nb ? p.n : p.nb) : p.n;
   double acc = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < range; i += gridDim.x * blockDim.x) {
     if (i < p.n) {
       bool has;
-      const float Pi = pending_var(p.delta, p.var_ptr, p.var_occ, p.P, p.share_occ, i, has, p.slot_dir, p.next_dir);
+      const float Pi =
+          pending_var<0, true>(p.delta, p.var_ptr, p.var_occ, p.P, p.share_occ, i, has, p.slot_dir, p.next_dir);
       if (BOUND && has) acc += slack_term((double)Pi, p.alpha);
     }
     if (BOUND && i < p.nb) acc += (double)p.bdd_E[i];
+  }
+  // variables with more than 8 occurrences: one warp each
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < p.n_heavy; w += (gridDim.x * blockDim.x) >> 5) {
+    const int4 hv = p.heavy[w];
+    const float Pi = pending_var_warp(p.delta, p.var_occ, p.P, p.share_occ, hv.x, hv.y, hv.z, p.slot_dir, p.next_dir);
+    if (BOUND && (threadIdx.x & 31) == 0) acc += slack_term((double)Pi, p.alpha);
   }
   if constexpr (BOUND) {
     __shared__ double red[kReduceThreads / 32];
@@ -665,8 +854,14 @@ __device__ __forceinline__ double persistent_pending(const IterParams &q, int ne
   double acc = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q.n; i += gridDim.x * blockDim.x) {
     bool has;
-    const float Pi = pending_var(q.sp.delta, q.var_ptr, q.var_occ, q.P, q.share_occ, i, has, q.slot_dir, next_dir);
+    const float Pi =
+        pending_var<0, true>(q.sp.delta, q.var_ptr, q.var_occ, q.P, q.share_occ, i, has, q.slot_dir, next_dir);
     if (has && Pi < 0.f) acc += (double)Pi;
+  }
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < q.n_heavy; w += (gridDim.x * blockDim.x) >> 5) {
+    const int4 hv = q.heavy[w];
+    const float Pi = pending_var_warp(q.sp.delta, q.var_occ, q.P, q.share_occ, hv.x, hv.y, hv.z, q.slot_dir, next_dir);
+    if ((threadIdx.x & 31) == 0 && Pi < 0.f) acc += (double)Pi;
   }
   return acc;
 }
@@ -816,10 +1011,12 @@ int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStr
                      : launch_pdl(sweep_kernel<F, M, false>, grid, kBlockThreads, smem, stream, p)
   if (forward) {
     if (mode == kUpdate) BDD_SWEEP(true, kUpdate);
+    else if (mode == kUpdateFused) BDD_SWEEP(true, kUpdateFused);
     else if (mode == kMessages) BDD_SWEEP(true, kMessages);
     else BDD_SWEEP(true, kFolded);
   } else {
     if (mode == kUpdate) BDD_SWEEP(false, kUpdate);
+    else if (mode == kUpdateFused) BDD_SWEEP(false, kUpdateFused);
     else if (mode == kMessages) BDD_SWEEP(false, kMessages);
     else BDD_SWEEP(false, kFolded);
   }
@@ -834,7 +1031,9 @@ int sweep_set_smem(size_t bytes) {
       (const void *)sweep_kernel<false, kMessages, false>, (const void *)sweep_kernel<false, kFolded, false>,
       (const void *)sweep_kernel<true, kUpdate, true>,     (const void *)sweep_kernel<true, kMessages, true>,
       (const void *)sweep_kernel<true, kFolded, true>,     (const void *)sweep_kernel<false, kUpdate, true>,
-      (const void *)sweep_kernel<false, kMessages, true>,  (const void *)sweep_kernel<false, kFolded, true>};
+      (const void *)sweep_kernel<false, kMessages, true>,  (const void *)sweep_kernel<false, kFolded, true>,
+      (const void *)sweep_kernel<true, kUpdateFused, false>, (const void *)sweep_kernel<false, kUpdateFused, false>,
+      (const void *)sweep_kernel<true, kUpdateFused, true>,  (const void *)sweep_kernel<false, kUpdateFused, true>};
   for (const void *f : fns)
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
       return -5;
@@ -844,6 +1043,11 @@ int sweep_set_smem(size_t bytes) {
 int iterate_set_smem(size_t bytes) {
   return cudaFuncSetAttribute((const void *)iterate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)bytes) == cudaSuccess ? 0 : -5;
+}
+
+int bound_launch(const SweepParams &p, int grid, cudaStream_t stream) {
+  const int rc = launch_pdl(bound_kernel, grid, kReduceThreads, 0, stream, p);
+  return rc ? rc : status();
 }
 
 int pending_launch(bool bound, const PendingParams &p, int grid, cudaStream_t stream) {

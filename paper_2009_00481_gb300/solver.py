@@ -21,7 +21,7 @@ class Solver:
 
     def __init__(self, inst, omega: float = 0.5, host_only: bool = False, max_device_bytes: int = 0,
                  device: int = -1, stream: int = 0, schedule: int = 1, spin_limit: int = 0,
-                 alpha: float = 0.0, rank=None, averaging: int = 0):
+                 alpha: float = 0.0, rank=None, averaging: int = 0, fused_pending: int = -1):
         import numpy as np
         opt = B.bdd_default_options()
         if isinstance(rank, str):
@@ -34,6 +34,7 @@ class Solver:
                 raise ValueError("rank must have one entry per variable")
             opt.var_rank = self.rank.ctypes.data_as(B.C.POINTER(B.C.c_int))
         opt.averaging = int(averaging)
+        opt.fused_pending = int(fused_pending)
         opt.alpha = float(alpha)
         opt.schedule = int(schedule)
         if spin_limit:
