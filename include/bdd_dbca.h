@@ -45,7 +45,7 @@ enum {
   BDD_ESTATE = -8       /* the call needs device state but the solver was built host-only */
 };
 
-#define BDD_SIZES_LEN 12
+#define BDD_SIZES_LEN 13
 
 /* Options for bdd_build.  Fill with bdd_default_options, then change fields. */
 typedef struct {
@@ -99,6 +99,13 @@ typedef struct {
                                  Same arithmetic either way: multipliers and pending sums are
                                  bit-identical; bounds differ only in the FP64 summation
                                  order. */
+  int staging;                /* warp-tile window staging of the update sweeps.  0: bulk-copy
+                                 (TMA) ring, 4-layer windows, the next window loading while one
+                                 is processed; 1: 8-layer windows in two rounds of cp.async.
+                                 -1 (default): the autotuner times both at build (schedule 1: a
+                                 warm-up and three iterations each, kernel by kernel) and keeps
+                                 the faster per sweep direction.  The variants compute identical
+                                 values; the persistent schedule and other sweeps use 0. */
 } bdd_options;
 
 void bdd_default_options(bdd_options *opt);
@@ -176,7 +183,9 @@ int bdd_set_costs(bdd_solver *h, const float *c);
 
 /* Sizes: out[0] n, [1] m, [2] BDDs, [3] occurrences (nonzeros kept), [4] nodes, [5] max depth,
  * [6] max width, [7] nnz, [8] device bytes held, [9] warp tiles, [10] block tiles,
- * [11] schedule in use (0 persistent, 1 per-phase graphs). */
+ * [11] schedule in use (0 persistent, 1 per-phase graphs), [12] warp-tile staging the autotuner
+ * chose for the update sweeps: bit 0 forward, bit 1 backward (0 bulk-copy ring of 4-layer
+ * windows, 1 8-layer cp.async windows). */
 int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]);
 
 /* Canonical form of the BDDs, read back from the device slabs (or the host copy when built

@@ -16,7 +16,7 @@ from .build import LIB
 
 BDD_OK, BDD_EINVAL, BDD_EINFEASIBLE, BDD_ETOOBIG, BDD_ENOMEM = 0, -1, -2, -3, -4
 BDD_ECUDA, BDD_ETIMEOUT, BDD_EDEVICE, BDD_ESTATE = -5, -6, -7, -8
-BDD_SIZES_LEN = 12
+BDD_SIZES_LEN = 13
 
 EXPORTED = [
     "bdd_default_options", "bdd_build", "bdd_last_failed_row", "bdd_iterate", "bdd_iterate_device",
@@ -32,7 +32,7 @@ class bdd_options(C.Structure):
                 ("max_device_bytes", C.c_longlong), ("host_only", C.c_int), ("device", C.c_int),
                 ("stream", C.c_void_p), ("schedule", C.c_int), ("spin_limit", C.c_longlong),
                 ("alpha", C.c_float), ("var_rank", C.POINTER(C.c_int)), ("averaging", C.c_int),
-                ("fused_pending", C.c_int)]
+                ("fused_pending", C.c_int), ("staging", C.c_int)]
 
 
 class BDDError(RuntimeError):

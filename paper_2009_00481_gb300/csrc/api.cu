@@ -90,8 +90,13 @@ struct bdd_solver {
   int part_cap = 0;
   float *d_bdd_E = nullptr;
   int *d_tile_occ0 = nullptr, *d_tile_bdd0 = nullptr, *d_tile_nbdd = nullptr;
+  int *d_tile_win0 = nullptr;
+  int2 *d_win_node = nullptr;
   int *d_var_ptr = nullptr, *d_var_occ = nullptr;
   int averaging = 0;                     // 0: eq. mma-update; 1: SRMP (Appendix A.4)
+  int stage_fwd = 0, stage_bwd = 0;      // warp-tile staging of the update sweeps (autotuned)
+  int staging_opt = -1;                  // bdd_options.staging
+  float tune_ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // measured ms per sweep [variant][direction]
   bool fused = false;                    // per-phase plan: pending pass fused into the sweeps
   int fused_opt = -1;                    // bdd_options.fused_pending
   int *d_cnt = nullptr;                  // [n] fused plan: visits still to come per variable
@@ -99,8 +104,8 @@ struct bdd_solver {
   double *d_fpartial = nullptr;          // fused plan: per-block bound partials
   unsigned *d_fticket = nullptr;
   unsigned char *d_slot_dir = nullptr;   // SRMP membership bits per slot (averaging == 1)
-  int4 *d_heavy = nullptr;               // variables with more than 8 occurrences: {i, s, e, 0}
-  int n_heavy = 0;
+  int4 *d_heavy = nullptr;               // variables with more than heavy_deg occurrences: {i, s, e, 0}
+  int n_heavy = 0, heavy_deg = 8;
   // persistent schedule
   int schedule = 1;
   long long spin_limit = 1LL << 26;
@@ -139,7 +144,9 @@ struct bdd_solver {
 
   template <class Tp>
   int alloc(Tp **p, long long count) {
-    size_t bytes = (size_t)std::max<long long>(count, 1) * sizeof(Tp);
+    // 16 spare bytes: bulk copies into shared memory read whole 16-byte blocks, up to 15 bytes
+    // past an array's last element
+    size_t bytes = (size_t)std::max<long long>(count, 1) * sizeof(Tp) + 16;
     bytes = (bytes + 255) & ~(size_t)255;
     if (max_device_bytes > 0 && device_bytes + (long long)bytes > max_device_bytes) return BDD_ENOMEM;
     void *q = nullptr;
@@ -167,6 +174,8 @@ struct bdd_solver {
     p.bdd_depth = d_bdd_depth;
     p.bdd_E = d_bdd_E;
     p.tile_occ0 = d_tile_occ0;
+    p.tile_win0 = d_tile_win0;
+    p.win_node = d_win_node;
     p.tile_bdd0 = d_tile_bdd0;
     p.tile_nbdd = d_tile_nbdd;
     p.out_m0 = out_m0;
@@ -177,6 +186,8 @@ struct bdd_solver {
     p.block_depth_buf = block_depth_buf;
     p.omega = omega;
     p.alpha = alpha;
+    p.error = d_error;
+    p.spin_limit = spin_limit;
     p.inv_alpha = alpha > 0.f ? 1.f / alpha : 0.f;
     return p;
   }
@@ -212,6 +223,7 @@ struct bdd_solver {
     r.next_dir = next_dir;
     r.heavy = d_heavy;
     r.n_heavy = n_heavy;
+    r.heavy_deg = heavy_deg;
     r.var_ptr = d_var_ptr;
     r.var_occ = d_var_occ;
     r.delta = d_delta;
@@ -242,7 +254,57 @@ struct bdd_solver {
   }
 
   int sweep(bool fwd, int mode, cudaStream_t s, float *m0 = nullptr, float *m1 = nullptr) {
-    return sweep_launch(fwd, mode, sweep_params(m0, m1), grid_sweep, s) ? BDD_ECUDA : BDD_OK;
+    const int staging = mode == kUpdate ? (fwd ? stage_fwd : stage_bwd) : 0;
+    return sweep_launch(fwd, mode, sweep_params(m0, m1), grid_sweep, s, staging) ? BDD_ECUDA : BDD_OK;
+  }
+
+  // Autotuner: time each warp-tile staging variant of the update sweeps on this instance
+  // (after a warm-up iteration, `reps` iterations launched kernel by kernel between events)
+  // and keep the faster one per direction.  Both variants compute the same values, so the
+  // choice affects time only; the solver is restarted afterwards.
+  int autotune(cudaStream_t s, int reps) {
+    if (n_warp_tiles == 0 || reps < 1) return BDD_OK;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (auto &e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return BDD_ECUDA;
+    float ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [variant][direction]
+    int rc = BDD_OK;
+    for (int v = 0; v < 2 && rc == BDD_OK; ++v) {
+      stage_fwd = stage_bwd = v;
+      rc = restart(s);
+      for (int it = 0; it <= reps && rc == BDD_OK; ++it) {
+        float t0 = 0.f, t1 = 0.f;
+        if (cudaEventRecord(ev[0], s) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK) rc = sweep(true, kUpdate, s);
+        if (rc == BDD_OK && cudaEventRecord(ev[1], s) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK) rc = pending(false, s);
+        if (rc == BDD_OK && cudaEventRecord(ev[2], s) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK && cudaEventSynchronize(ev[2]) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK && cudaEventElapsedTime(&t0, ev[0], ev[1]) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK && cudaEventRecord(ev[0], s) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK) rc = sweep(false, kUpdate, s);
+        if (rc == BDD_OK && cudaEventRecord(ev[1], s) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK) rc = pending(true, s);
+        if (rc == BDD_OK && cudaEventSynchronize(ev[1]) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK && cudaEventElapsedTime(&t1, ev[0], ev[1]) != cudaSuccess) rc = BDD_ECUDA;
+        if (it > 0) {
+          ms[v][0] += t0;
+          ms[v][1] += t1;
+        }
+      }
+    }
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+    if (rc != BDD_OK) {
+      cudaGetLastError();
+      stage_fwd = stage_bwd = 0;
+      return rc;
+    }
+    stage_fwd = ms[1][0] < ms[0][0] ? 1 : 0;
+    stage_bwd = ms[1][1] < ms[0][1] ? 1 : 0;
+    for (int v = 0; v < 2; ++v)
+      for (int d = 0; d < 2; ++d) tune_ms[v][d] = ms[v][d] / reps;
+    return restart(s);
   }
 
   // pending sums and the shares of the next sweep: a forward sweep follows a bound pass (the
@@ -288,6 +350,7 @@ struct bdd_solver {
     q.slot_dir = d_slot_dir;
     q.heavy = d_heavy;
     q.n_heavy = n_heavy;
+    q.heavy_deg = heavy_deg;
     CK(cudaMemsetAsync(d_barrier, 0, 2 * sizeof(unsigned), s));
     return iterate_persistent_launch(q, grid_persist, smem_persist, s) ? BDD_ECUDA : BDD_OK;
   }
@@ -407,7 +470,21 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   h->n_warp_blocks = (L.n_warp_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
   h->grid_sweep = h->n_warp_blocks + L.n_block_tiles;
   const int range = std::max<long long>(h->n, h->nb) > 0 ? (int)std::max<long long>(h->n, h->nb) : 1;
-  h->grid_reduce = std::max(1, std::min((range + kReduceThreads - 1) / kReduceThreads, 152 * 8));
+  // pending passes: a thread per variable (and BDD), plus one warp per variable with more than
+  // heavy_deg occurrences.  heavy_deg: the least of 8, 16, 32, ... that leaves at most 4096 such
+  // variables, so that each gets its own warp (a warp's two rounds of loads beat a thread's
+  // serial batches for few long variables; for many, the extra warps cost more than they save)
+  h->heavy_deg = 8;
+  for (;;) {
+    int cnt = 0;
+    for (int i = 0; i < h->n; ++i) cnt += L.var_ptr[i + 1] - L.var_ptr[i] > h->heavy_deg;
+    if (cnt <= 4096 || h->heavy_deg >= (1 << 20)) break;
+    h->heavy_deg *= 2;
+  }
+  int n_heavy = 0;
+  for (int i = 0; i < h->n; ++i) n_heavy += L.var_ptr[i + 1] - L.var_ptr[i] > h->heavy_deg;
+  const int heavy_blocks = (n_heavy + kReduceThreads / 32 - 1) / (kReduceThreads / 32);
+  h->grid_reduce = std::max(1, std::min(std::max((range + kReduceThreads - 1) / kReduceThreads, heavy_blocks), 152 * 16));
   h->smem = sweep_smem_bytes(h->block_buf, h->block_depth_buf);
   h->smem_persist = persist_smem_bytes(h->block_buf, h->block_depth_buf);
   if (h->smem > 48 * 1024 && sweep_set_smem(h->smem)) return BDD_ECUDA;
@@ -433,7 +510,7 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   const long long ntiles = (long long)L.tile_bdd0.size();
   long long need = (O + 1) * 4 + O * 4 + O * 8 + N * 8 + 2 * N * 4 + 2 * O * 4 + 3 * (long long)n * 4 +
                    nb * 8 + 3 * ntiles * 4 + (n + 1) * 4 + O * 4 + h->grid_reduce * 8 + 1024 * 8 +
-                   (h->averaging == 1 ? O : 0) + (h->fused ? 12 * n + 8LL * (h->grid_sweep + h->grid_reduce) : 0);
+                   (h->averaging == 1 ? O : 0) + 4LL * (long long)(L.tile_win0.size() + L.win_node.size()) + (h->fused ? 12 * n + 8LL * (h->grid_sweep + h->grid_reduce) : 0);
   if (h->max_device_bytes > 0 && need > h->max_device_bytes) return BDD_ENOMEM;
 
   RC(upload(h, &h->d_occ_node_off, L.occ_node_off));
@@ -464,6 +541,12 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   }
   RC(h->alloc(&h->d_bdd_E, nb));
   RC(upload(h, &h->d_tile_occ0, L.tile_occ0));
+  RC(upload(h, &h->d_tile_win0, L.tile_win0));
+  {
+    int *tmp = nullptr;
+    RC(upload(h, &tmp, L.win_node));
+    h->d_win_node = reinterpret_cast<int2 *>(tmp);
+  }
   RC(upload(h, &h->d_tile_bdd0, L.tile_bdd0));
   RC(upload(h, &h->d_tile_nbdd, L.tile_nbdd));
   RC(upload(h, &h->d_var_ptr, L.var_ptr));
@@ -472,7 +555,8 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   {
     std::vector<int4> heavy;
     for (int i = 0; i < h->n; ++i)
-      if (L.var_ptr[i + 1] - L.var_ptr[i] > 8) heavy.push_back(make_int4(i, L.var_ptr[i], L.var_ptr[i + 1], 0));
+      if (L.var_ptr[i + 1] - L.var_ptr[i] > h->heavy_deg)
+        heavy.push_back(make_int4(i, L.var_ptr[i], L.var_ptr[i + 1], 0));
     h->n_heavy = (int)heavy.size();
     if (!heavy.empty()) RC(upload(h, &h->d_heavy, heavy));
   }
@@ -492,6 +576,11 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   RC(h->ensure_trace(1024));
   if (n) CK(cudaMemcpy(h->d_c, c, sizeof(float) * n, cudaMemcpyHostToDevice));
   RC(h->restart(h->stream));
+  if (h->staging_opt >= 0) {
+    h->stage_fwd = h->stage_bwd = h->staging_opt;
+  } else if (h->schedule == 1 && !h->fused) {
+    RC(h->autotune(h->stream, 3));
+  }
   RC(h->end(h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return BDD_OK;
@@ -533,6 +622,7 @@ void bdd_default_options(bdd_options *opt) {
   opt->var_rank = nullptr;
   opt->averaging = 0;
   opt->fused_pending = -1;
+  opt->staging = -1;
 }
 
 int bdd_last_failed_row(void) { return g_failed_row; }
@@ -559,6 +649,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   if (!finite_costs(c, n)) return BDD_EINVAL;
   if (opt.averaging < 0 || opt.averaging > 1) return BDD_EINVAL;
   if (opt.fused_pending < -1 || opt.fused_pending > 1) return BDD_EINVAL;
+  if (opt.staging < -1 || opt.staging > 1) return BDD_EINVAL;
   if (opt.var_rank) {  // a permutation of 0..n-1
     std::vector<char> seen;
     try {
@@ -582,6 +673,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   h->alpha = opt.alpha;
   h->averaging = opt.averaging;
   h->fused_opt = opt.fused_pending;
+  h->staging_opt = h->fused_opt == 1 ? 0 : opt.staging;
   h->schedule = opt.alpha > 0.f ? 1 : opt.schedule;  // the persistent kernel runs min-sum only
   h->spin_limit = opt.spin_limit;
   if (opt.schedule < 0 || opt.schedule > 1 || opt.spin_limit < 1) {
@@ -947,6 +1039,7 @@ int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]) {
   out[9] = h->n_warp_tiles;
   out[10] = h->n_block_tiles;
   out[11] = h->schedule;
+  out[12] = h->stage_fwd | (h->stage_bwd << 1);
   return BDD_OK;
 }
 

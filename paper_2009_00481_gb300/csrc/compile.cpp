@@ -332,6 +332,27 @@ int build_layout(const HostBDDs &H, Layout *L) {
       }
     }
   }
+  // window table of every warp tile: node offsets at layer w * kWinLayers and at layer
+  // min((w + 1) * kWinLayers + 1, maxd), w = 0 .. ceil(maxd / kWinLayers)
+  L->tile_win0.assign(ntiles + 1, 0);
+  L->win_node.clear();
+  for (long long t = 0; t < ntiles; ++t) {
+    L->tile_win0[t] = (int)(L->win_node.size() / 2);
+    if (t >= L->class_tile_off[kWarpClasses]) continue;
+    const int b0 = L->tile_bdd0[t], nt = L->tile_nbdd[t];
+    const int dmax = L->bdd_depth[b0];
+    auto node_at = [&](int layer) {  // first node of `layer` in the tile (tile end for dmax)
+      long long before = 0;
+      for (int q = 0; q < nt; ++q) before += std::min(L->bdd_depth[b0 + q], layer);
+      return L->occ_node_off[L->tile_occ0[t] + before];
+    };
+    const int nwin = (dmax + kWinLayers - 1) / kWinLayers;
+    for (int w = 0; w <= nwin; ++w) {
+      L->win_node.push_back(node_at(std::min(w * kWinLayers, dmax)));
+      L->win_node.push_back(node_at(std::min(w * kWinLayers + kWinLayers + 1, dmax)));
+    }
+  }
+  L->tile_win0[ntiles] = (int)(L->win_node.size() / 2);
   // variable -> occurrences (ascending row, i.e. canonical occurrence order)
   L->var_ptr.assign(H.n + 1, 0);
   for (long long co = 0; co < O; ++co) L->var_ptr[H.occ_var[co] + 1]++;

@@ -57,18 +57,38 @@ constexpr int kMaxBlockTileDepth = 8192;
 
 // Shared-memory stage of one warp: a window of kWinLayers layers of a warp tile (at most 32
 // occurrences and 32 nodes per layer), plus the node offsets and backward messages of the layer
-// after the window.
-constexpr int kWinLayers = 8;
+// after the window.  Each warp has kWarpStages of them (the next window loads while one is
+// processed).
+constexpr int kWinLayers = 4;
+constexpr int kWarpStages = 2;
 constexpr int kWinOcc = 32 * kWinLayers;
 constexpr int kWinNodes = 32 * kWinLayers;
-struct WarpStage {
-  int2 lohi[kWinNodes];
-  float msg[kWinNodes + 32];
-  int off[kWinOcc + 32 + 1];
-  float lam[kWinOcc];
-  float shr[kWinOcc];
-  int slot[kWinOcc];
+// Arrays are filled by bulk copies that start at the 16-byte boundary at or below the window's
+// first element, hence the few spare elements; every array starts 16-byte aligned.
+struct alignas(16) WarpStage {
+  int2 lohi[kWinNodes + 2];
+  float msg[kWinNodes + 32 + 4];
+  int off[kWinOcc + 8];
+  float lam[kWinOcc + 4];
+  float shr[kWinOcc + 4];
+  int slot[kWinOcc + 4];
 };
+
+// The 8-layer window of the cp.async staging variant (one buffer per warp).
+constexpr int kWin8Layers = 8;
+constexpr int kWin8Occ = 32 * kWin8Layers;
+constexpr int kWin8Nodes = 32 * kWin8Layers;
+struct alignas(16) WarpStage8 {
+  int2 lohi[kWin8Nodes];
+  float msg[kWin8Nodes + 32];
+  int off[kWin8Occ + 32 + 1];
+  float lam[kWin8Occ];
+  float shr[kWin8Occ];
+  int slot[kWin8Occ];
+};
+// shared memory of one warp: the larger of the two staging variants
+constexpr size_t kWarpSmemBytes = (kWarpStages * sizeof(WarpStage) > sizeof(WarpStage8) ? kWarpStages * sizeof(WarpStage)
+                                                                                          : sizeof(WarpStage8));
 
 // Device slab layout (host staging copy).  Occurrences are grouped by tile; inside a warp
 // tile they are layer-major (layer l of every tile BDD still alive at l, in tile order; the
@@ -86,6 +106,8 @@ struct Layout {
   std::vector<int> occ_slot;           // [O] slot of the occurrence
   std::vector<int> lohi;               // [2N] interleaved lo, hi
   std::vector<int> tile_occ0, tile_bdd0, tile_nbdd;  // per tile
+  std::vector<int> tile_win0;                        // [ntiles + 1] window table offsets (warp tiles)
+  std::vector<int> win_node;                         // window table, int pairs
   int class_tile_off[kWarpClasses + 2] = {0};        // tiles of class c: [off[c], off[c+1])
   int n_warp_tiles = 0, n_block_tiles = 0;
   int max_block_width = 0;
@@ -136,6 +158,9 @@ struct SweepParams {
   const int *bdd_depth;
   float *bdd_E;
   const int *tile_occ0;
+  const int *tile_win0;     // first window-table entry of each warp tile
+  const int2 *win_node;     // window table: {node at layer w * kWinLayers, node at layer
+                            // min((w + 1) * kWinLayers + 1, maxd)} for w = 0 .. windows
   const int *tile_bdd0;
   const int *tile_nbdd;
   float *out_m0;
@@ -147,6 +172,8 @@ struct SweepParams {
   float omega;
   float alpha;          // smoothing temperature (0: min-sum)
   float inv_alpha;
+  int *error;            // set to BDD_ETIMEOUT if a bounded wait on a shared-memory copy gives up
+  long long spin_limit;  // polls of such a wait: spin_limit / 64 (at least 1)
   FusedParams fz;       // fz.cnt == null outside the fused plan
 };
 
@@ -181,8 +208,9 @@ struct PendingParams {
   double alpha;  // smoothing temperature of the slack term (0: min-sum)
   const unsigned char *slot_dir;  // SRMP membership bits per slot, or null (eq. mma-update)
   int next_dir;                   // kDirForward / kDirBackward: the sweep the shares are for
-  const int4 *heavy;              // variables with more than 8 occurrences: {i, first slot, end slot, 0}
-  int n_heavy;                    // (handled by one warp each)
+  const int4 *heavy;              // variables with more than heavy_deg occurrences: {i, first slot,
+  int n_heavy;                    // end slot, 0}, handled by one warp each
+  int heavy_deg;
 };
 
 // Persistent iteration kernel (one cooperative launch runs n_iter iterations).
@@ -204,6 +232,7 @@ struct IterParams {
   const unsigned char *slot_dir;  // SRMP membership bits per slot, or null (eq. mma-update)
   const int4 *heavy;              // as in PendingParams
   int n_heavy;
+  int heavy_deg;
 };
 
 // Adjoint of one smoothed update sweep (adjoint.cu): checkpointed inputs, recomputed outputs and
@@ -236,7 +265,9 @@ size_t sweep_smem_bytes(int block_buf, int block_depth_buf);
 size_t persist_smem_bytes(int block_buf, int block_depth_buf);
 int sweep_set_smem(size_t bytes);
 int iterate_set_smem(size_t bytes);
-int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStream_t stream);
+// staging: warp-tile window staging of a plain update sweep (0: bulk-copy ring, 1: 8-layer
+// cp.async windows); other modes always use the ring
+int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStream_t stream, int staging = 0);
 int pending_launch(bool bound, const PendingParams &p, int grid, cudaStream_t stream);
 // FP64 bound from the E^j and slack terms of the last fused backward sweep into trace[*iter_ctr]
 int bound_launch(const SweepParams &p, int grid, cudaStream_t stream);

@@ -117,14 +117,15 @@ __device__ __forceinline__ double slack_term(double P, double alpha) {
 // unless J_i^dir is empty (then P_i / |J_i| to all).
 // FAST > 0: one round of loads for variables with at most FAST occurrences (slots, occurrence
 // ids and SRMP bits together); FAST = 0: slot_sum, then the occurrence ids eight at a time.
-// SKIP_HEAVY: variables with more than 8 occurrences are left to pending_var_warp (has = false).
+// SKIP_HEAVY: variables with more than heavy_deg occurrences are left to pending_var_warp
+// (has = false for them).
 template <int FAST, bool SKIP_HEAVY = false>
 __device__ __forceinline__ float pending_var(const float *__restrict__ delta, const int *__restrict__ var_ptr,
                                              const int *__restrict__ var_occ, float *__restrict__ P,
                                              float *__restrict__ share_occ, int i, bool &has,
-                                             const unsigned char *__restrict__ slot_dir, int dir) {
+                                             const unsigned char *__restrict__ slot_dir, int dir, int heavy_deg = 0) {
   const int s = var_ptr[i], e = var_ptr[i + 1];
-  has = e > s && (!SKIP_HEAVY || e - s <= 8);
+  has = e > s && (!SKIP_HEAVY || e - s <= heavy_deg);
   if (!has) return 0.f;
   const int deg = e - s;
   if (FAST > 0 && deg <= FAST) {
@@ -272,12 +273,386 @@ __device__ __forceinline__ void pending_tail(const SweepParams &p, int o0, int c
 // ---------------------------------------------------------------------------------------
 // warp tiles: T lanes per BDD, 32 / T BDDs per warp.  A tile's slab is contiguous and
 // layer-major, so a window of kWinLayers layers (<= 32 occurrences and <= 32 nodes per layer)
-// is one contiguous range of every array.  Each window is staged into the warp's shared memory
-// with independent coalesced loads before its layers are processed, so the layer recurrence
-// runs on shared memory and registers only.
+// is one contiguous range of every array; the tile's window table gives each window's node
+// range without reading the slab first.  Windows are staged into shared memory with cp.async
+// one window ahead of the one being processed (two buffers), so the layer recurrence runs on
+// shared memory and registers while the next window's loads are in flight.  The static part
+// of the first window (node offsets, arcs, slots: written once at build) is staged before the
+// wait on the previous kernel of the chain.
+// ---------------------------------------------------------------------------------------
+// wait for the kernel this launch depends on (programmatic dependent launch); a no-op without one
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// mbarrier and bulk-copy (TMA) primitives.  A window's copies complete on its buffer's
+// mbarrier: one lane posts the expected byte count and issues the copies; every lane waits for
+// the phase with a bounded poll.
+__device__ __forceinline__ unsigned smem_u32(const void *ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
+__device__ __forceinline__ void bar_init(unsigned long long *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void bar_expect(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for phase `parity`; false if it did not complete within the poll limit
+__device__ __forceinline__ bool bar_wait(unsigned long long *bar, unsigned parity, long long limit) {
+  for (long long i = 0; i < limit; ++i)
+    if (bar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// generic-proxy writes to global memory (earlier phases of a persistent launch) before bulk reads
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// A contiguous element range [first, first + n) of an array, widened to whole 16-byte blocks
+// for a bulk copy: the copy starts at a0 and the range's first element lands `shift` elements
+// into the destination.
+struct Range {
+  const char *a0;
+  unsigned bytes;
+  int shift;
+};
+template <int E>
+__device__ __forceinline__ Range range_of(const void *base, long long first, int n) {
+  const char *a = static_cast<const char *>(base) + first * E;
+  const unsigned long long lo = reinterpret_cast<unsigned long long>(a) & ~15ull;
+  const unsigned long long hi = (reinterpret_cast<unsigned long long>(a) + (unsigned long long)n * E + 15ull) & ~15ull;
+  Range r;
+  r.a0 = reinterpret_cast<const char *>(lo);
+  r.bytes = n > 0 ? (unsigned)(hi - lo) : 0u;
+  r.shift = (int)((reinterpret_cast<unsigned long long>(a) - lo) / E);
+  return r;
+}
+
+// Window w of a warp tile: layers [l0, l1), occurrences [ca, cb) (relative to the tile's first),
+// nodes [na, nb); a forward update also reads the backward messages of layer l1, through nc.
+struct Window {
+  int l0, l1, ca, cb, na, nb, nc;
+};
+
+// the tile's window table: entry w = {node at layer w * kWinLayers, node at layer
+// min(w * kWinLayers + kWinLayers + 1, maxd)}; lane w holds entry w for w < 32
+__device__ __forceinline__ int2 win_entry(const SweepParams &p, int win0, int2 tab, int w) {
+  if (w < 32) return make_int2(__shfl_sync(kFull, tab.x, w), __shfl_sync(kFull, tab.y, w));
+  return p.win_node[win0 + w];
+}
+
+__device__ __forceinline__ Window window_of(const SweepParams &p, int win0, int2 tab, int lead_depth, int maxd,
+                                            int w) {
+  Window W;
+  W.l0 = w * kWinLayers;
+  W.l1 = min(W.l0 + kWinLayers, maxd);
+  W.ca = occ_before(lead_depth, W.l0);
+  W.cb = occ_before(lead_depth, W.l1);
+  const int2 e0 = win_entry(p, win0, tab, w), e1 = win_entry(p, win0, tab, w + 1);
+  W.na = e0.x;
+  W.nb = e1.x;
+  W.nc = e0.y;
+  return W;
+}
+
+// The six ranges of a window (static: node offsets, arcs, slots; dynamic: multipliers, shares,
+// messages -- fm for a backward sweep, bm through the extra layer for a forward update)
+struct WindowRanges {
+  Range off, lohi, slot, lam, shr, msg;
+};
+template <bool FWD, int MODE>
+__device__ __forceinline__ WindowRanges ranges_of(const SweepParams &p, int occ0, const Window &W) {
+  const long long oa = occ0 + W.ca;
+  const int nob = W.cb - W.ca;
+  WindowRanges r;
+  r.off = range_of<4>(p.occ_node_off, oa, nob + 1);
+  r.lohi = range_of<8>(p.lohi, W.na, W.nb - W.na);
+  r.slot = range_of<4>(p.occ_slot, oa, is_update(MODE) ? nob : 0);
+  r.lam = range_of<4>(p.lam, oa, nob);
+  r.shr = range_of<4>(p.share_occ, oa, MODE != kMessages ? nob : 0);
+  if (FWD)
+    r.msg = range_of<4>(p.bm, W.na, is_update(MODE) ? W.nc - W.na : 0);
+  else
+    r.msg = range_of<4>(p.fm, W.na, W.nb - W.na);
+  return r;
+}
+
+// Lane 0 issues a window's bulk copies into S on `bar`: with `expect`, first the expected byte
+// count of the whole window; then the static and/or the dynamic copies.
+__device__ __forceinline__ void stage_window(const WindowRanges &r, WarpStage &S, unsigned long long *bar,
+                                             bool expect, bool stat, bool dyn) {
+  if ((threadIdx.x & 31) != 0) return;
+  if (expect)
+    bar_expect(bar, r.off.bytes + r.lohi.bytes + r.slot.bytes + r.lam.bytes + r.shr.bytes + r.msg.bytes);
+  if (stat) {
+    if (r.off.bytes) bulk_copy(S.off, r.off.a0, r.off.bytes, bar);
+    if (r.lohi.bytes) bulk_copy(S.lohi, r.lohi.a0, r.lohi.bytes, bar);
+    if (r.slot.bytes) bulk_copy(S.slot, r.slot.a0, r.slot.bytes, bar);
+  }
+  if (dyn) {
+    if (r.lam.bytes) bulk_copy(S.lam, r.lam.a0, r.lam.bytes, bar);
+    if (r.shr.bytes) bulk_copy(S.shr, r.shr.a0, r.shr.bytes, bar);
+    if (r.msg.bytes) bulk_copy(S.msg, r.msg.a0, r.msg.bytes, bar);
+  }
+}
+
+// Per-warp copy state: two stage buffers, their mbarriers and the parity each waits for next.
+struct StageRing {
+  WarpStage *S;              // [kWarpStages]
+  unsigned long long *bar;   // [kWarpStages]
+  unsigned parity;           // bit b: parity of buffer b's next phase (lane-uniform)
+};
+
+// wait for buffer b's window; on a timeout record BDD_ETIMEOUT and report false (the caller
+// abandons the tile after one more bounded wait for the copies in flight)
+__device__ __forceinline__ bool ring_wait(const SweepParams &p, StageRing &ring, int b) {
+  const long long limit = p.spin_limit / 64 > 0 ? p.spin_limit / 64 : 1;
+  const unsigned par = (ring.parity >> b) & 1u;
+  const bool ok = __all_sync(kFull, bar_wait(&ring.bar[b], par, limit));
+  if (!ok) {
+    if ((threadIdx.x & 31) == 0) atomicExch(p.error, -6);
+    bar_wait(&ring.bar[b], par, limit);
+    return false;
+  }
+  ring.parity ^= 1u << b;
+  return true;
+}
+
+// Tile parameters, depths and the window table (all static, read before the dependency wait).
+struct TileInfo {
+  int occ0, depth, lead_depth, maxd, nw, win0;
+  int2 tab;
+};
+
+template <int T>
+__device__ __forceinline__ TileInfo tile_info(const SweepParams &p, int tile) {
+  const int lane = threadIdx.x & 31;
+  const int team = lane / T, tl = lane % T;
+  TileInfo ti;
+  ti.occ0 = p.tile_occ0[tile];
+  ti.win0 = p.tile_win0[tile];
+  const int bdd = p.tile_bdd0[tile] + team;
+  const bool valid = team < p.tile_nbdd[tile];
+  ti.depth = valid ? p.bdd_depth[bdd] : 0;
+  ti.lead_depth = tl == 0 ? ti.depth : 0;
+  ti.maxd = __reduce_max_sync(kFull, ti.depth);
+  ti.nw = (ti.maxd + kWinLayers - 1) / kWinLayers;
+  ti.tab = lane <= ti.nw ? p.win_node[ti.win0 + lane] : make_int2(0, 0);
+  return ti;
+}
+
+template <int T, int MODE, bool SMOOTH>
+__device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &ph, int tile, StageRing &ring,
+                                             double &bacc) {
+  const int lane = threadIdx.x & 31;
+  const int team = lane / T, tl = lane % T, tbase = team * T;
+  const TileInfo ti = tile_info<T>(p, tile);
+  const int occ0 = ti.occ0, depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd, nw = ti.nw;
+  fence_proxy_async();
+  // window 0 into buffer 0: static part, dependency wait, dynamic part; window 1 into buffer 1
+  Window Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, 0);
+  {
+    const WindowRanges r = ranges_of<true, MODE>(p, occ0, Wn);
+    stage_window(r, ring.S[0], &ring.bar[0], true, true, false);
+    pdl_wait();
+    stage_window(r, ring.S[0], &ring.bar[0], false, false, true);
+  }
+  if (nw > 1) {
+    const Window W1 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, 1);
+    stage_window(ranges_of<true, MODE>(p, occ0, W1), ring.S[1], &ring.bar[1], true, true, true);
+  }
+  float f_prev = inf(), lam_prev = 0.f;
+  int2 lh_prev = make_int2(kNone, kNone);
+  for (int w = 0; w < nw; ++w) {
+    const Window W = Wn;
+    if (w + 1 < nw) Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w + 1);
+    const int b = w & 1;
+    WarpStage &S = ring.S[b];
+    if (!ring_wait(p, ring, b)) return;
+    const WindowRanges r = ranges_of<true, MODE>(p, occ0, W);
+    const int *off = S.off + r.off.shift;
+    const int2 *lohi = S.lohi + r.lohi.shift;
+    const int *slot = S.slot + r.slot.shift;
+    const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
+    const int ca = W.ca, na = W.na, oa = occ0 + ca;
+    for (int l = W.l0; l < W.l1; ++l) {
+      const bool active = depth > l;
+      const int oi = occ_before(lead_depth, l) - ca + team;
+      int node0 = 0, w_l = 0;
+      if (active) {
+        node0 = off[oi];
+        w_l = off[oi + 1] - node0;
+      }
+      const bool has = active && tl < w_l;
+      // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv
+      float f;
+      if (l == 0) {
+        f = 0.f;
+      } else {
+        const int lo_l = lh_prev.x >= 0 ? lh_prev.x - node0 : kNone;
+        const int hi_l = lh_prev.y >= 0 ? lh_prev.y - node0 : kNone;
+        f = inf();
+#pragma unroll
+        for (int s = 0; s < T; ++s) {
+          const float mf = __shfl_sync(kFull, f_prev, tbase + s);
+          const int ls = __shfl_sync(kFull, lo_l, tbase + s);
+          const int hs = __shfl_sync(kFull, hi_l, tbase + s);
+          if (ls == tl) f = agg<SMOOTH>(f, mf, p);
+          if (hs == tl) f = agg<SMOOTH>(f, mf + lam_prev, p);
+        }
+      }
+      int2 lh = make_int2(kNone, kNone);
+      if (has) {
+        p.fm[node0 + tl] = f;
+        lh = lohi[node0 - na + tl];
+      }
+      float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
+      if (is_update(MODE)) {
+        // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
+        const float a0 = has ? f + staged_bm(msg, na, lh.x) : inf();
+        const float a1 = has ? f + lam + staged_bm(msg, na, lh.y) : inf();
+        const float m0 = team_agg<T, SMOOTH>(a0, p), m1 = team_agg<T, SMOOTH>(a1, p);
+        const float dd = p.omega * mm_difference(m0, m1);
+        lam -= dd;
+        if (active && tl == 0) {
+          p.lam[oa + oi] = lam;
+          ph.delta[slot[oi]] = dd;
+        }
+      }
+      f_prev = f;
+      lh_prev = lh;
+      lam_prev = lam;
+    }
+    __syncwarp();  // this buffer is free: stage the window after next into it
+    if (w + 2 < nw) {
+      const Window W2 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w + 2);
+      stage_window(ranges_of<true, MODE>(p, occ0, W2), S, &ring.bar[b], true, true, true);
+    }
+  }
+  if (MODE == kUpdateFused) {
+    __syncwarp();
+    pending_tail<true>(p, occ0, __reduce_add_sync(kFull, lead_depth), lane, 32,
+                       reinterpret_cast<int *>(ring.S[0].lohi));
+  }
+}
+
+template <int T, int MODE, bool SMOOTH>
+__device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase &ph, int tile, StageRing &ring,
+                                              double &bacc) {
+  const int lane = threadIdx.x & 31;
+  const int team = lane / T, tl = lane % T, tbase = team * T;
+  const TileInfo ti = tile_info<T>(p, tile);
+  const int occ0 = ti.occ0, depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd, nw = ti.nw;
+  const int bdd = p.tile_bdd0[tile] + team;
+  fence_proxy_async();
+  // windows from the last to the first; the k-th processed window uses buffer k & 1
+  Window Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, nw - 1);
+  {
+    const WindowRanges r = ranges_of<false, MODE>(p, occ0, Wn);
+    stage_window(r, ring.S[0], &ring.bar[0], true, true, false);
+    pdl_wait();
+    stage_window(r, ring.S[0], &ring.bar[0], false, false, true);
+  }
+  if (nw > 1) {
+    const Window W1 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, nw - 2);
+    stage_window(ranges_of<false, MODE>(p, occ0, W1), ring.S[1], &ring.bar[1], true, true, true);
+  }
+  float b_next = inf();
+  int node0_next = 0;
+  for (int k = 0; k < nw; ++k) {
+    const int w = nw - 1 - k;
+    const Window W = Wn;
+    if (w > 0) Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w - 1);
+    const int b = k & 1;
+    WarpStage &S = ring.S[b];
+    if (!ring_wait(p, ring, b)) return;
+    const WindowRanges r = ranges_of<false, MODE>(p, occ0, W);
+    const int *off = S.off + r.off.shift;
+    const int2 *lohi = S.lohi + r.lohi.shift;
+    const int *slot = S.slot + r.slot.shift;
+    const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
+    const int ca = W.ca, na = W.na, oa = occ0 + ca;
+    for (int l = W.l1 - 1; l >= W.l0; --l) {
+      const bool active = depth > l;
+      const int oi = occ_before(lead_depth, l) - ca + team;
+      int node0 = 0, w_l = 0;
+      if (active) {
+        node0 = off[oi];
+        w_l = off[oi + 1] - node0;
+      }
+      const bool has = active && tl < w_l;
+      int2 lh = make_int2(kNone, kNone);
+      float f = inf();
+      if (has) {
+        lh = lohi[node0 - na + tl];
+        f = msg[node0 - na + tl];
+      }
+      float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
+      // successors' backward messages live on the lanes of this team (layer l + 1)
+      const int s0 = lh.x >= 0 ? lh.x - node0_next : 0;
+      const int s1 = lh.y >= 0 ? lh.y - node0_next : 0;
+      const float g0 = __shfl_sync(kFull, b_next, tbase + (s0 & (T - 1)));
+      const float g1 = __shfl_sync(kFull, b_next, tbase + (s1 & (T - 1)));
+      const float b0 = lh.x >= 0 ? g0 : (lh.x == kTop ? 0.f : inf());
+      const float b1 = lh.y >= 0 ? g1 : (lh.y == kTop ? 0.f : inf());
+      if (MODE != kMessages) {
+        const float m0 = team_agg<T, SMOOTH>(f + b0, p), m1 = team_agg<T, SMOOTH>(f + lam + b1, p);
+        if (is_update(MODE)) {
+          const float dd = p.omega * mm_difference(m0, m1);
+          lam -= dd;
+          if (active && tl == 0) {
+            p.lam[oa + oi] = lam;
+            ph.delta[slot[oi]] = dd;
+          }
+        } else if (active && tl == 0 && p.out_m0) {
+          const long long c = p.occ_csr[oa + oi];
+          p.out_m0[c] = m0;
+          p.out_m1[c] = m1;
+        }
+      }
+      // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
+      const float bcur = agg<SMOOTH>(b0, lam + b1, p);
+      if (has) p.bm[node0 + tl] = bcur;
+      if (l == 0 && active && tl == 0) {  // E^j(lambda^j) at the root
+        p.bdd_E[bdd] = bcur;
+        bacc += (double)bcur;
+      }
+      b_next = bcur;
+      node0_next = node0;
+    }
+    __syncwarp();
+    if (w >= 2) {
+      const Window W2 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w - 2);
+      stage_window(ranges_of<false, MODE>(p, occ0, W2), S, &ring.bar[b], true, true, true);
+    }
+  }
+  if (MODE == kUpdateFused) {
+    __syncwarp();
+    pending_tail<false>(p, occ0, __reduce_add_sync(kFull, lead_depth), lane, 32,
+                        reinterpret_cast<int *>(ring.S[0].lohi));
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// warp tiles, 8-layer windows: each window is staged in two rounds of cp.async (node offsets,
+// multipliers, shares, slots; then arcs and messages over the node range the offsets give) and
+// processed after both have landed.  Fewer instructions per layer than the bulk-copy ring, no
+// overlap of loads with the layer recurrence; the autotuner picks between the two per solver
+// and sweep direction.  Plain updates only.
 // ---------------------------------------------------------------------------------------
 template <int MODE>
-__device__ __forceinline__ void stage_occurrences(const SweepParams &p, const Phase &ph, WarpStage &S, int oa,
+__device__ __forceinline__ void stage_occurrences_w8(const SweepParams &p, const Phase &ph, WarpStage8 &S, int oa,
                                                   int nob, int nox, double &bacc) {
   const int lane = threadIdx.x & 31;
   for (int k = lane; k <= nox; k += 32) cp_async4(&S.off[k], &p.occ_node_off[oa + k]);
@@ -293,7 +668,7 @@ __device__ __forceinline__ void stage_occurrences(const SweepParams &p, const Ph
 }
 
 template <int T, int MODE, bool SMOOTH>
-__device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &ph, int tile, WarpStage &S,
+__device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phase &ph, int tile, WarpStage8 &S,
                                              double &bacc) {
   const int lane = threadIdx.x & 31;
   const int team = lane / T, tl = lane % T, tbase = team * T;
@@ -303,15 +678,16 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
   const int depth = valid ? p.bdd_depth[bdd] : 0;
   const int lead_depth = tl == 0 ? depth : 0;
   const int maxd = __reduce_max_sync(kFull, depth);
+  pdl_wait();
   float f_prev = inf(), lam_prev = 0.f;
   int2 lh_prev = make_int2(kNone, kNone);
-  for (int l0 = 0; l0 < maxd; l0 += kWinLayers) {
-    const int l1 = min(l0 + kWinLayers, maxd);
+  for (int l0 = 0; l0 < maxd; l0 += kWin8Layers) {
+    const int l1 = min(l0 + kWin8Layers, maxd);
     const int ca = occ_before(lead_depth, l0), cb = occ_before(lead_depth, l1);
     const int cx = l1 < maxd ? occ_before(lead_depth, l1 + 1) : cb;
     const int oa = occ0 + ca, nob = cb - ca, nox = cx - ca;
     __syncwarp();  // the previous window is no longer read
-    stage_occurrences<MODE>(p, ph, S, oa, nob, nox, bacc);
+    stage_occurrences_w8<MODE>(p, ph, S, oa, nob, nox, bacc);
     __syncwarp();
     const int na = S.off[0], nb = S.off[nob];
     for (int k = lane; k < nb - na; k += 32) cp_async8(&S.lohi[k], &p.lohi[na + k]);
@@ -370,14 +746,10 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
       lam_prev = lam;
     }
   }
-  if (MODE == kUpdateFused) {
-    __syncwarp();
-    pending_tail<true>(p, occ0, __reduce_add_sync(kFull, lead_depth), lane, 32, S.slot);
-  }
 }
 
 template <int T, int MODE, bool SMOOTH>
-__device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase &ph, int tile, WarpStage &S,
+__device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Phase &ph, int tile, WarpStage8 &S,
                                               double &bacc) {
   const int lane = threadIdx.x & 31;
   const int team = lane / T, tl = lane % T, tbase = team * T;
@@ -387,14 +759,15 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
   const int depth = valid ? p.bdd_depth[bdd] : 0;
   const int lead_depth = tl == 0 ? depth : 0;
   const int maxd = __reduce_max_sync(kFull, depth);
+  pdl_wait();
   float b_next = inf();
   int node0_next = 0;
-  for (int l0 = ((maxd - 1) / kWinLayers) * kWinLayers; l0 >= 0; l0 -= kWinLayers) {
-    const int l1 = min(l0 + kWinLayers, maxd);
+  for (int l0 = ((maxd - 1) / kWin8Layers) * kWin8Layers; l0 >= 0; l0 -= kWin8Layers) {
+    const int l1 = min(l0 + kWin8Layers, maxd);
     const int ca = occ_before(lead_depth, l0), cb = occ_before(lead_depth, l1);
     const int oa = occ0 + ca, nob = cb - ca;
     __syncwarp();
-    stage_occurrences<MODE>(p, ph, S, oa, nob, nob, bacc);
+    stage_occurrences_w8<MODE>(p, ph, S, oa, nob, nob, bacc);
     __syncwarp();
     const int na = S.off[0], nb = S.off[nob];
     for (int k = lane; k < nb - na; k += 32) {
@@ -451,10 +824,6 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
       b_next = bcur;
       node0_next = node0;
     }
-  }
-  if (MODE == kUpdateFused) {
-    __syncwarp();
-    pending_tail<false>(p, occ0, __reduce_add_sync(kFull, lead_depth), lane, 32, S.slot);
   }
 }
 
@@ -619,16 +988,22 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
   }
 }
 
-template <bool FWD, int MODE, bool SMOOTH>
-__device__ __forceinline__ void warp_tile(const SweepParams &p, const Phase &ph, int tile, WarpStage &S,
-                                          double &bacc) {
+// STAGE 0: bulk-copy ring (StageRing); STAGE 1: 8-layer cp.async windows (WarpStage8 at W8)
+template <bool FWD, int MODE, bool SMOOTH, int STAGE = 0>
+__device__ __forceinline__ void warp_tile(const SweepParams &p, const Phase &ph, int tile, StageRing &S,
+                                          double &bacc, WarpStage8 *W8 = nullptr) {
   int c = 0;
   while (tile >= p.class_tile_off[c + 1]) ++c;
   switch (c) {
-#define BDD_TEAM_CASE(C, T)                                   \
-  case C:                                                     \
-    if (FWD) warp_forward<T, MODE, SMOOTH>(p, ph, tile, S, bacc);  \
-    else warp_backward<T, MODE, SMOOTH>(p, ph, tile, S, bacc);     \
+#define BDD_TEAM_CASE(C, T)                                                     \
+  case C:                                                                       \
+    if constexpr (STAGE == 1) {                                                 \
+      if (FWD) warp_forward_w8<T, MODE, SMOOTH>(p, ph, tile, *W8, bacc);       \
+      else warp_backward_w8<T, MODE, SMOOTH>(p, ph, tile, *W8, bacc);          \
+    } else {                                                                    \
+      if (FWD) warp_forward<T, MODE, SMOOTH>(p, ph, tile, S, bacc);             \
+      else warp_backward<T, MODE, SMOOTH>(p, ph, tile, S, bacc);                \
+    }                                                                           \
     break;
     BDD_TEAM_CASE(0, 1)
     BDD_TEAM_CASE(1, 2)
@@ -694,23 +1069,42 @@ __device__ __forceinline__ void fused_bound(const FusedParams &z, const float *_
   }
 }
 
-template <bool FWD, int MODE, bool SMOOTH>
+template <bool FWD, int MODE, bool SMOOTH, int STAGE = 0>
 __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams p) {
   extern __shared__ __align__(16) float smem[];
-  pdl_enter();
+  // the next kernel of the chain may launch now: it reads nothing this one writes before its
+  // own dependency wait.  This kernel reads static data (slab offsets, arcs, slots) before its
+  // wait, and everything a previous kernel writes only after it.
+  pdl_release();
   if (FWD && MODE == kUpdateFused && p.fz.bound) {  // bound of the previous iteration (fused plan)
+    pdl_wait();
     fused_bound(p.fz, p.bdd_E, kBlockThreads);
     if (threadIdx.x < 32) __syncwarp();
   }
   const Phase ph{p.delta};
   double bacc = 0.0;
   if ((int)blockIdx.x < p.n_warp_blocks) {
-    const int tile = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int warp = threadIdx.x >> 5;
+    const int tile = blockIdx.x * kWarpsPerBlock + warp;
     if (tile >= p.class_tile_off[kWarpClasses]) return;  // whole warp leaves together
-    warp_tile<FWD, MODE, SMOOTH>(p, ph, tile, reinterpret_cast<WarpStage *>(smem)[threadIdx.x >> 5], bacc);
+    char *mine = reinterpret_cast<char *>(smem) + (size_t)warp * kWarpSmemBytes;
+    if constexpr (STAGE == 1) {
+      StageRing none{nullptr, nullptr, 0u};
+      warp_tile<FWD, MODE, SMOOTH, 1>(p, ph, tile, none, bacc, reinterpret_cast<WarpStage8 *>(mine));
+    } else {
+      __shared__ unsigned long long bars[kWarpsPerBlock * kWarpStages];
+      if ((threadIdx.x & 31) == 0) {
+        for (int b = 0; b < kWarpStages; ++b) bar_init(&bars[warp * kWarpStages + b]);
+        bar_init_fence();
+      }
+      __syncwarp();
+      StageRing ring{reinterpret_cast<WarpStage *>(mine), &bars[warp * kWarpStages], 0u};
+      warp_tile<FWD, MODE, SMOOTH>(p, ph, tile, ring, bacc);
+    }
   } else if constexpr (!SMOOTH) {  // smoothed solvers have warp tiles only
     const int tile = p.class_tile_off[kWarpClasses] + (blockIdx.x - p.n_warp_blocks);
     if (tile >= p.class_tile_off[kWarpClasses + 1]) return;  // uniform across the block
+    pdl_wait();
     const GroupSmem g = group_smem(smem, p);
     if (FWD)
       block_forward<MODE>(p, ph, tile, g, 0, threadIdx.x, bacc);
@@ -742,12 +1136,13 @@ __global__ void __launch_bounds__(kReduceThreads, 8) pending_kernel(const Pendin
     if (i < p.n) {
       bool has;
       const float Pi =
-          pending_var<0, true>(p.delta, p.var_ptr, p.var_occ, p.P, p.share_occ, i, has, p.slot_dir, p.next_dir);
+          pending_var<0, true>(p.delta, p.var_ptr, p.var_occ, p.P, p.share_occ, i, has, p.slot_dir, p.next_dir,
+                               p.heavy_deg);
       if (BOUND && has) acc += slack_term((double)Pi, p.alpha);
     }
     if (BOUND && i < p.nb) acc += (double)p.bdd_E[i];
   }
-  // variables with more than 8 occurrences: one warp each
+  // variables with more than heavy_deg occurrences: one warp each
   for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < p.n_heavy; w += (gridDim.x * blockDim.x) >> 5) {
     const int4 hv = p.heavy[w];
     const float Pi = pending_var_warp(p.delta, p.var_occ, p.P, p.share_occ, hv.x, hv.y, hv.z, p.slot_dir, p.next_dir);
@@ -825,14 +1220,13 @@ __device__ bool grid_barrier(const IterParams &q, bool &failed) {
 }
 
 template <bool FWD>
-__device__ __forceinline__ void persistent_phase(const SweepParams &p, float *smem, double &bacc) {
+__device__ __forceinline__ void persistent_phase(const SweepParams &p, float *smem, StageRing &ring, double &bacc) {
   const Phase ph{p.delta};
   const int warp = threadIdx.x >> 5;
   const int W = gridDim.x * kPersistWarps;
   const int nwt = p.class_tile_off[kWarpClasses];
-  WarpStage &S = reinterpret_cast<WarpStage *>(smem)[warp];
   for (int tile = blockIdx.x * kPersistWarps + warp; tile < nwt; tile += W)
-    warp_tile<FWD, kUpdate, false>(p, ph, tile, S, bacc);
+    warp_tile<FWD, kUpdate, false>(p, ph, tile, ring, bacc);
   const int bt0 = p.class_tile_off[kWarpClasses];
   const int nbt = p.class_tile_off[kWarpClasses + 1] - bt0;
   if (nbt > 0) {
@@ -855,7 +1249,8 @@ __device__ __forceinline__ double persistent_pending(const IterParams &q, int ne
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q.n; i += gridDim.x * blockDim.x) {
     bool has;
     const float Pi =
-        pending_var<0, true>(q.sp.delta, q.var_ptr, q.var_occ, q.P, q.share_occ, i, has, q.slot_dir, next_dir);
+        pending_var<0, true>(q.sp.delta, q.var_ptr, q.var_occ, q.P, q.share_occ, i, has, q.slot_dir, next_dir,
+                             q.heavy_deg);
     if (has && Pi < 0.f) acc += (double)Pi;
   }
   for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < q.n_heavy; w += (gridDim.x * blockDim.x) >> 5) {
@@ -883,16 +1278,27 @@ __global__ void __launch_bounds__(kPersistThreads, 1) iterate_kernel(const IterP
   __shared__ double red[kPersistWarps];
   const SweepParams &p = q.sp;
   const int G = gridDim.x;
+  // per-warp stage buffers and their mbarriers (static shared memory: the dynamic region is
+  // reused by block tiles)
+  __shared__ unsigned long long bars[kPersistWarps * kWarpStages];
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    for (int b = 0; b < kWarpStages; ++b) bar_init(&bars[warp * kWarpStages + b]);
+    bar_init_fence();
+  }
+  __syncwarp();
+  StageRing ring{reinterpret_cast<WarpStage *>(reinterpret_cast<char *>(smem) + (size_t)warp * kWarpSmemBytes),
+                 &bars[warp * kWarpStages], 0u};
   bool failed = false;
   for (int it = 0; it < q.n_iter; ++it) {
     double bacc = 0.0;
-    persistent_phase<true>(p, smem, bacc);
+    persistent_phase<true>(p, smem, ring, bacc);
     if (blockIdx.x == 0 && it > 0) finalize_bound(q, it - 1, red);  // partials of it-1 are final
     if (!grid_barrier(q, failed)) return;
     persistent_pending(q, kDirBackward);
     if (!grid_barrier(q, failed)) return;
     bacc = 0.0;
-    persistent_phase<false>(p, smem, bacc);
+    persistent_phase<false>(p, smem, ring, bacc);
     double sum = block_sum(bacc, red, kPersistWarps);
     if (threadIdx.x == 0) q.part[blockIdx.x] = sum;  // E^j part
     if (!grid_barrier(q, failed)) return;
@@ -991,21 +1397,30 @@ int launch_pdl(void (*kernel)(Args...), int grid, int block, size_t smem, cudaSt
 }  // namespace
 
 size_t sweep_smem_bytes(int block_buf, int block_depth_buf) {
-  const size_t warp_part = kWarpsPerBlock * sizeof(WarpStage);
+  const size_t warp_part = kWarpsPerBlock * kWarpSmemBytes;
   const size_t group_part = group_floats(block_buf, block_depth_buf) * sizeof(float);
   return warp_part > group_part ? warp_part : group_part;
 }
 
 size_t persist_smem_bytes(int block_buf, int block_depth_buf) {
-  const size_t warp_part = kPersistWarps * sizeof(WarpStage);
+  const size_t warp_part = kPersistWarps * kWarpSmemBytes;
   const size_t group_part = kSubBlocks * group_floats(block_buf, block_depth_buf) * sizeof(float);
   return warp_part > group_part ? warp_part : group_part;
 }
 
-int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStream_t stream) {
+int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStream_t stream, int staging) {
   if (grid <= 0) return 0;
   const size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf);
   int rc = 0;
+  if (mode == kUpdate && staging == 1) {
+    if (p.alpha > 0.f)
+      rc = forward ? launch_pdl(sweep_kernel<true, kUpdate, true, 1>, grid, kBlockThreads, smem, stream, p)
+                   : launch_pdl(sweep_kernel<false, kUpdate, true, 1>, grid, kBlockThreads, smem, stream, p);
+    else
+      rc = forward ? launch_pdl(sweep_kernel<true, kUpdate, false, 1>, grid, kBlockThreads, smem, stream, p)
+                   : launch_pdl(sweep_kernel<false, kUpdate, false, 1>, grid, kBlockThreads, smem, stream, p);
+    return rc ? rc : status();
+  }
 #define BDD_SWEEP(F, M)                                                                          \
   rc = p.alpha > 0.f ? launch_pdl(sweep_kernel<F, M, true>, grid, kBlockThreads, smem, stream, p)    \
                      : launch_pdl(sweep_kernel<F, M, false>, grid, kBlockThreads, smem, stream, p)
@@ -1033,7 +1448,9 @@ int sweep_set_smem(size_t bytes) {
       (const void *)sweep_kernel<true, kFolded, true>,     (const void *)sweep_kernel<false, kUpdate, true>,
       (const void *)sweep_kernel<false, kMessages, true>,  (const void *)sweep_kernel<false, kFolded, true>,
       (const void *)sweep_kernel<true, kUpdateFused, false>, (const void *)sweep_kernel<false, kUpdateFused, false>,
-      (const void *)sweep_kernel<true, kUpdateFused, true>,  (const void *)sweep_kernel<false, kUpdateFused, true>};
+      (const void *)sweep_kernel<true, kUpdateFused, true>,  (const void *)sweep_kernel<false, kUpdateFused, true>,
+      (const void *)sweep_kernel<true, kUpdate, false, 1>,   (const void *)sweep_kernel<false, kUpdate, false, 1>,
+      (const void *)sweep_kernel<true, kUpdate, true, 1>,    (const void *)sweep_kernel<false, kUpdate, true, 1>};
   for (const void *f : fns)
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
       return -5;

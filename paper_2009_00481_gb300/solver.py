@@ -21,7 +21,8 @@ class Solver:
 
     def __init__(self, inst, omega: float = 0.5, host_only: bool = False, max_device_bytes: int = 0,
                  device: int = -1, stream: int = 0, schedule: int = 1, spin_limit: int = 0,
-                 alpha: float = 0.0, rank=None, averaging: int = 0, fused_pending: int = -1):
+                 alpha: float = 0.0, rank=None, averaging: int = 0, fused_pending: int = -1,
+                 staging: int = -1):
         import numpy as np
         opt = B.bdd_default_options()
         if isinstance(rank, str):
@@ -35,6 +36,7 @@ class Solver:
             opt.var_rank = self.rank.ctypes.data_as(B.C.POINTER(B.C.c_int))
         opt.averaging = int(averaging)
         opt.fused_pending = int(fused_pending)
+        opt.staging = int(staging)
         opt.alpha = float(alpha)
         opt.schedule = int(schedule)
         if spin_limit:
@@ -48,7 +50,7 @@ class Solver:
                              inst.c, opt)
         s = B.bdd_sizes(self.h)
         (self.n, self.m, self.nb, self.O, self.N, self.max_depth, self.max_width, self.nnz,
-         self.device_bytes, self.warp_tiles, self.block_tiles, self.schedule) = map(int, s)
+         self.device_bytes, self.warp_tiles, self.block_tiles, self.schedule, self.staging) = map(int, s)
 
     def close(self):
         if getattr(self, "h", None):

@@ -446,3 +446,26 @@ def test_bound_parts_rejects_bad_offsets(lib):
     s = solver(packed)
     with pytest.raises(BDDError):
         s.bound_parts([0, 1], [0, packed.n])
+
+
+@pytest.mark.parametrize("name", ["potts_20x20x3", "matching_small", "tomography_16", "tracking_10x40",
+                                  "random_wide"])
+@pytest.mark.parametrize("variant", ["plain", "smooth", "srmp"])
+def test_staging_variants_bit_identical(lib, name, variant):
+    """The two warp-tile staging variants (bulk-copy ring of 4-layer windows; 8-layer cp.async
+    windows) feed the same arithmetic: bound traces, multipliers and pending sums bit-identical
+    over graphs of 8 iterations plus a ragged tail; the autotuner's choice is one of them."""
+    if variant == "smooth" and name == "tomography_16":
+        pytest.skip("smoothed solvers need layers of at most 32 nodes")
+    inst = CASES[name]()
+    kw = {"plain": {}, "smooth": {"alpha": 0.2}, "srmp": {"averaging": 1, "rank": "cm"}}[variant]
+    a, b = solver(inst, staging=0, **kw), solver(inst, staging=1, **kw)
+    assert a.staging == 0 and b.staging == 3
+    np.testing.assert_array_equal(_trace(a, 19), _trace(b, 19))
+    la, pa = a.get_state()
+    lb_, pb = b.get_state()
+    np.testing.assert_array_equal(la, lb_)
+    np.testing.assert_array_equal(pa, pb)
+    auto = solver(inst, **kw)
+    assert 0 <= auto.staging <= 3
+    np.testing.assert_array_equal(_trace(auto, 19), _trace(solver(inst, staging=0, **kw), 19))
