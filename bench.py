@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", type=int, default=1, help="1 per-phase graphs (default), 0 persistent kernel")
+    ap.add_argument("--staging", type=int, default=-1,
+                    help="warp-tile staging of the update sweeps: -1 autotuned (default), 0 bulk-copy ring, "
+                         "1 8-layer cp.async windows")
     ap.add_argument("--batch-count", type=int, default=256, help="instances in the batch workload")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--batch-warmup", type=int, default=2)
@@ -80,6 +83,52 @@ def algorithmic_bytes(kind: str, N: int, O: int, n: int, nb: int) -> int:
     if kind == "iteration":
         return sum(algorithmic_bytes(k, N, O, n, nb) for k in ("fwd", "pending", "bwd", "pending_bound"))
     raise ValueError(kind)
+
+
+STAGING = {0: "bulk-copy ring, 4-layer windows", 1: "8-layer cp.async windows"}
+
+
+def staging_of(s) -> dict:
+    """Warp-tile staging the solver's autotuner chose for each update sweep."""
+    return {"forward": STAGING[s.staging & 1], "backward": STAGING[(s.staging >> 1) & 1]}
+
+
+def sweep_kernel_name(kind: str, s) -> str:
+    st = staging_of(s)
+    return {"fwd": f"sweep_kernel<forward, update> ({st['forward']})",
+            "bwd": f"sweep_kernel<backward, update> ({st['backward']})",
+            "pending": "pending_kernel", "pending_bound": "pending_kernel<bound>"}[kind]
+
+
+def sources_sha256() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(HERE, "paper_2009_00481_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cpp", ".h", ".cuh")):
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def dram_traffic(workload: str, kernel: str, nodes: int):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, scaled by
+    node count; None when no capture exists or the CUDA sources changed since it was taken."""
+    path = os.path.join(HERE, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want_hash, found = None, None
+    for line in open(path):
+        line = line.strip()
+        if line.startswith("# sources-sha256:"):
+            want_hash = line.split(":", 1)[1].strip()
+        elif line and not line.startswith("#"):
+            parts = [x.strip() for x in line.split("|")]
+            if len(parts) == 4 and parts[0] == workload and parts[1] == kernel:
+                found = int(parts[2]) * nodes / int(parts[3])
+    if found is None or want_hash != sources_sha256():
+        return None
+    return found
 
 
 def max_over_ranks(ms: float, world: int, device: str = "cpu") -> float:
@@ -199,7 +248,7 @@ def ours(args):
     inst = config(k)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    s = Solver(inst, omega=0.5, stream=stream.cuda_stream, schedule=args.schedule)
+    s = Solver(inst, omega=0.5, stream=stream.cuda_stream, schedule=args.schedule, staging=args.staging)
     arcs_per_step = 2 * s.N * iters
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     trace = torch.zeros(iters, dtype=torch.float64, device="cuda")
@@ -258,8 +307,7 @@ def ours(args):
         launches = args.steps
     else:
         dom = int(np.argmax(kms))
-        kernel_name = {"fwd": "sweep_kernel<forward>", "bwd": "sweep_kernel<backward>",
-                       "pending": "pending_kernel", "pending_bound": "pending_kernel<bound>"}[kinds[dom]]
+        kernel_name = sweep_kernel_name(kinds[dom], s)
         abytes = algorithmic_bytes(kinds[dom], s.N, s.O, s.n, s.nb)
         per_launch_ms = kms[dom] / iters
         launches = args.steps * iters * 4
@@ -273,7 +321,7 @@ def ours(args):
         for _ in range(args.e2e_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s2 = Solver(inst, omega=0.5, schedule=args.schedule)
+            s2 = Solver(inst, omega=0.5, schedule=args.schedule, staging=args.staging)
             s2.iterate(iters, lam=True, mm=True)
             s2.close()
             times.append(time.perf_counter() - t0)
@@ -317,7 +365,8 @@ def ours(args):
         "time_to_bound": ttb,
         "roofline": {"bound": "hbm", "kernel": kernel_name,
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": dram_traffic(CONFIG_NAMES[k], kernel_name, s.N) if s.schedule == 1 else None,
                      "algorithmic_bytes_per_launch": abytes, "launch_ms": per_launch_ms,
                      "per_phase_kernel_ms_per_iteration": {kd: float(v / iters) for kd, v in zip(kinds, kms)}},
         "cpu_baseline": cpu,
@@ -327,6 +376,7 @@ def ours(args):
         "order_and_averaging": variants,
         "gpu_launches": launches,
         "schedule": "persistent" if s.schedule == 0 else "per-phase graphs",
+        "staging": staging_of(s),
         "clocks": clocks,
         "wall_s": wall,
     }
@@ -351,7 +401,7 @@ def run_batched(args, stream, plain: bool, n_parity: int) -> dict:
     inst = potts_batch(count)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    s = Solver(inst, omega=0.5, stream=stream.cuda_stream, schedule=args.schedule)
+    s = Solver(inst, omega=0.5, stream=stream.cuda_stream, schedule=args.schedule, staging=args.staging)
     build_s = time.perf_counter() - t0
     arcs_per_step = 2 * s.N * iters
     trace = torch.zeros(iters, dtype=torch.float64, device="cuda")
@@ -434,10 +484,10 @@ def run_batched(args, stream, plain: bool, n_parity: int) -> dict:
                    "omega": 0.5, "device_bytes": s.device_bytes,
                    "l2": f"inputs larger than L2: {iter_bytes / 1e9:.2f} GB moved per iteration",
                    "generate_s": gen_s, "build_s": build_s},
-        "roofline": {"bound": "hbm", "kernel": {"fwd": "sweep_kernel<forward>", "bwd": "sweep_kernel<backward>",
-                     "pending": "pending_kernel", "pending_bound": "pending_kernel<bound>"}[kinds[dom]],
+        "roofline": {"bound": "hbm", "kernel": sweep_kernel_name(kinds[dom], s),
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "algorithmic_bytes_per_launch": abytes,
+                     "frac": achieved / peak,
+                     "traffic": dram_traffic(CONFIG_NAMES[4], sweep_kernel_name(kinds[dom], s), s.N), "algorithmic_bytes_per_launch": abytes,
                      "launch_ms": per_launch_ms,
                      "iteration": {"algorithmic_bytes": iter_bytes, "ms": iter_ms,
                                    "achieved_gbs": iter_bytes / (iter_ms / 1e3) / 1e9,
@@ -449,6 +499,7 @@ def run_batched(args, stream, plain: bool, n_parity: int) -> dict:
         "plain_loop": plain_d,
         "gpu_launches": steps * iters * 4,
         "schedule": "persistent" if s.schedule == 0 else "per-phase graphs",
+        "staging": staging_of(s),
         "clocks": clocks,
     }
 
