@@ -427,6 +427,27 @@ def run_batched(args, stream, plain: bool, n_parity: int) -> dict:
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     bounds = s.bound_parts(inst.row_parts, inst.var_parts)
 
+    # per-instance time to a bound within 1e-3 of the instance's bound after the step's
+    # iterations: an untimed rerun one iteration at a time, every instance's FP64 bound after
+    # each (the reference bounds are the packed solve's own, checked against the oracle on the
+    # sampled instances below)
+    s.set_costs(inst.c)
+    traj = np.zeros((iters, count))
+    for it in range(iters):
+        s.iterate_device(1, stream=stream.cuda_stream)
+        traj[it] = s.bound_parts(inst.row_parts, inst.var_parts)
+    final = traj[-1]
+    hit = traj >= (final - TTB_TOL * np.abs(final))[None, :]
+    first = np.argmax(hit, axis=0) + 1  # hit[-1] is always true
+    ms_iter = ms / iters
+    per_instance = {"reference": "each instance's bound after the step's iterations (packed solve)",
+                    "tolerance": TTB_TOL, "instances": count,
+                    "iterations": {"median": float(np.median(first)), "p90": float(np.percentile(first, 90)),
+                                   "max": int(first.max()), "min": int(first.min())},
+                    "ms": {"median": float(np.median(first)) * ms_iter, "p90": float(np.percentile(first, 90)) * ms_iter,
+                           "max": float(first.max()) * ms_iter},
+                    "final_matches_timed_run": bool(np.array_equal(final, bounds))}
+
     # per-phase kernels, timed one by one, for the roofline of the dominant kernel
     s.set_costs(inst.c)
     kms = s.iterate_profiled(iters)
@@ -494,6 +515,7 @@ def run_batched(args, stream, plain: bool, n_parity: int) -> dict:
                                    "frac": iter_bytes / (iter_ms / 1e3) / 1e9 / peak},
                      "per_phase_kernel_ms_per_iteration": {kd: float(v / iters) for kd, v in zip(kinds, kms)}},
         "parity_sampled_instances": parity,
+        "time_to_bound_per_instance": per_instance,
         "cpu_baseline": {"value": cpu_arcs / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"instances {sample} of the batch, {iters} iterations each, FP64 single thread"},
         "plain_loop": plain_d,
