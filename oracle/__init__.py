@@ -46,6 +46,12 @@ def _configure(lib):
     lib.orc_build_ordered.argtypes = [i32, i32, P(i64), P(i32), P(i32), P(i32), P(C.c_byte),
                                       P(f64), P(i32), P(i32), P(i32)]
     lib.orc_set_srmp.argtypes = [vp, i32]
+    lib.orc_split.restype = i32
+    lib.orc_split.argtypes = [vp, i32, P(i32), f64]
+    lib.orc_npairs.restype = i64
+    lib.orc_npairs.argtypes = [vp]
+    lib.orc_get_copy_duals.argtypes = [vp, P(f64), P(f64)]
+    lib.orc_set_copy_duals.argtypes = [vp, P(f64), P(f64)]
     lib.orc_free.argtypes = [vp]
     lib.orc_sizes.argtypes = [vp, P(i64)]
     lib.orc_export.argtypes = [vp, P(i32), P(i32), P(i32), P(i64), P(i32), P(i32), P(i32), P(i64)]
@@ -155,6 +161,30 @@ class Oracle:
         """SRMP averaging (Appendix A.4) instead of eq. mma-update; restarts the dual state."""
         self.lib.orc_set_srmp(self.h, int(bool(on)))
         self.lib.orc_init_dual(self.h)
+
+    def split(self, cuts, gamma: float = 0.5) -> int:
+        """Sub-BDDs at the interval boundaries `cuts` (ascending places in the variable order;
+        Sec. 6) with copy-arc step size gamma; restarts the dual state.  Returns the number of
+        pieces."""
+        cuts = np.ascontiguousarray(cuts, np.int32)
+        self._keep.append(cuts)
+        nb = self.lib.orc_split(self.h, len(cuts), _p(cuts, C.c_int) if len(cuts) else None, float(gamma))
+        if nb < 0:
+            raise ValueError("bad cuts or gamma")
+        self.nb = nb
+        self.npairs = int(self.lib.orc_npairs(self.h))
+        return nb
+
+    def copy_duals(self):
+        mb = np.zeros(max(self.npairs, 1))
+        mu = np.zeros(max(self.npairs, 1))
+        self.lib.orc_get_copy_duals(self.h, _p(mb, C.c_double), _p(mu, C.c_double))
+        return mb[: self.npairs], mu[: self.npairs]
+
+    def set_copy_duals(self, mu_bar, mu):
+        mb = np.ascontiguousarray(mu_bar, np.float64)
+        m = np.ascontiguousarray(mu, np.float64)
+        self.lib.orc_set_copy_duals(self.h, _p(mb, C.c_double), _p(m, C.c_double))
 
     def reset(self):
         self.lib.orc_init_dual(self.h)

@@ -41,6 +41,16 @@
  *   - SRMP averaging (Appendix A.4): optionally, the averaging share of variable i goes only to
  *     the subproblems that contain a variable after i in the order (forward pass) / before i
  *     (backward pass), evenly; when there are none, to all of J_i.
+ *   - Sub-BDDs and copy arcs (Sec. 6, Def. of sub-BDDs and copy-arcs, the parallel averaging
+ *     algorithm and Prop. 4): optionally the variable order is cut into intervals; every BDD is
+ *     split where its variables cross an interval boundary.  The earlier piece keeps the arcs
+ *     crossing the cut as copy arcs into the top terminal with cost theta + mu_bar; the later
+ *     piece starts at its first layer with several roots, each with initial forward message
+ *     min over its entry arcs of mu (the entry arcs carry no theta).  After every forward sweep
+ *     mu_bar moves by -gamma * delta_fwd + gamma * delta_bwd (delta_fwd: arc-marginal of the copy
+ *     arc minus its minimum over the cut), after every backward sweep mu moves by
+ *     -gamma * delta_bwd + gamma * delta_fwd (delta_bwd: the same on the entry arcs).  Each
+ *     piece is a subproblem of the decomposition (its layers are its occurrences).
  * Readings where the paper is silent: a min-marginal that is +inf (a row that forces x_i)
  * gives the difference 0; a variable in no row contributes min(0, c_i) to the bound; an empty
  * row is dropped when 0 (sense) b holds and is infeasible otherwise.
@@ -53,6 +63,8 @@
 
 #define ORC_TOP (-1)
 #define ORC_BOT (-2)
+/* arc target codes below ORC_COPY0: copy arc k into the top terminal, cost mu_bar[k] */
+#define ORC_COPY0 (-4)
 
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_EINFEASIBLE = -2, ORC_ETOOBIG = -3, ORC_ENOMEM = -4 };
 
@@ -113,6 +125,17 @@ typedef struct {
   double *lam, *P, *delta, *share, *fm, *bm;
   /* scratch for the definitional dynamic programmes */
   double *sfm, *sbm;
+  /* sub-BDDs (Sec. 6): copy-arc pairs grouped by cut, root messages of later pieces */
+  long long npairs;
+  int ncuts;
+  long long *cut_ptr;       /* [ncuts+1] pairs of each cut */
+  long long *pair_u, *pair_w; /* global node of the copy arc's tail (earlier piece), of the
+                                 entry arc's head (later piece's first layer) */
+  long long *pair_occ;      /* occurrence of the tail's layer */
+  int *pair_hi;             /* 1: the original arc is the 1-arc (theta = lambda) */
+  double *mu_bar, *mu, *dfwd, *dbwd;  /* [npairs] */
+  double *root_f;           /* [N] initial forward message of first-layer nodes of each piece */
+  double gamma;
   /* worst check violations seen: [monotone drop, invariant, incremental mm, prop-1 gain,
    * negative gain] */
   double worst[5];
@@ -127,6 +150,8 @@ void orc_free(void *vh) {
   free(h->var_ptr); free(h->var_occ); free(h->deg); free(h->c);
   free(h->lam); free(h->P); free(h->delta); free(h->share); free(h->fm); free(h->bm);
   free(h->sfm); free(h->sbm); free(h->order); free(h->oshare);
+  free(h->cut_ptr); free(h->pair_u); free(h->pair_w); free(h->pair_occ); free(h->pair_hi);
+  free(h->mu_bar); free(h->mu); free(h->dfwd); free(h->dbwd); free(h->root_f);
   free(h);
 }
 
@@ -415,15 +440,20 @@ static double agg(const oracle_t *h, double a, double b) {
 static double bval(const oracle_t *h, const double *bm, long long o, int t) {
   if (t == ORC_TOP) return 0.0;
   if (t == ORC_BOT) return INFINITY;
+  if (t <= ORC_COPY0) return h->mu_bar[ORC_COPY0 - t];
   return bm[h->occ_node0[o + 1] + t];
 }
+
+/* initial forward message of a first-layer node: 0 at the root of a whole BDD or first piece;
+ * for a later piece, the cheapest entry arc (+inf if none enters the node) */
+static double root_msg(const oracle_t *h, long long v) { return h->root_f ? h->root_f[v] : 0.0; }
 
 /* Full forward programme of BDD b into fm: m_fwd(root) = 0, then for every layer the min
  * over in-arcs (each arc relaxed once). */
 static void dp_forward(const oracle_t *h, int b, const double *lam, double *fm) {
   long long o0 = h->bdd_occ0[b];
   int k = h->bdd_k[b];
-  fm[h->occ_node0[o0]] = 0.0;
+  for (long long v = h->occ_node0[o0]; v < h->occ_node0[o0 + 1]; ++v) fm[v] = root_msg(h, v);
   for (int l = 1; l < k; ++l) {
     long long o = o0 + l;
     for (long long v = h->occ_node0[o]; v < h->occ_node0[o + 1]; ++v) fm[v] = INFINITY;
@@ -451,11 +481,21 @@ static void bwd_step(const oracle_t *h, long long o, double lam_o, double *bm) {
   }
 }
 
-/* Full backward programme of BDD b into bm; returns E^j = m_bwd(root). */
+/* E^j from the backward messages of the first layer: m_bwd(root) for a whole BDD, the min over
+ * roots of (initial forward message + m_bwd) for a piece */
+static double piece_energy(const oracle_t *h, int b, const double *bm) {
+  long long o0 = h->bdd_occ0[b];
+  if (!h->root_f) return bm[h->occ_node0[o0]];
+  double e = INFINITY;
+  for (long long v = h->occ_node0[o0]; v < h->occ_node0[o0 + 1]; ++v) e = agg(h, e, h->root_f[v] + bm[v]);
+  return e;
+}
+
+/* Full backward programme of BDD b into bm; returns E^j. */
 static double dp_backward(const oracle_t *h, int b, const double *lam, double *bm) {
   long long o0 = h->bdd_occ0[b];
   for (int l = h->bdd_k[b] - 1; l >= 0; --l) bwd_step(h, o0 + l, lam[o0 + l], bm);
-  return bm[h->occ_node0[o0]];
+  return piece_energy(h, b, bm);
 }
 
 /* min-marginals of occurrence o from fm (its layer) and bm (next layer) */
@@ -516,6 +556,8 @@ void orc_init_dual(void *vh) {
   oracle_t *h = (oracle_t *)vh;
   for (long long o = 0; o < h->O; ++o) h->lam[o] = h->c[h->occ_var[o]] / h->deg[h->occ_var[o]];
   for (int i = 0; i < h->n; ++i) h->P[i] = 0.0;
+  for (long long k = 0; k < h->npairs; ++k) h->mu_bar[k] = h->mu[k] = h->dfwd[k] = h->dbwd[k] = 0.0;
+  for (long long k = 0; k < h->npairs; ++k) h->root_f[h->pair_w[k]] = 0.0;
   for (int b = 0; b < h->nb; ++b) dp_backward(h, b, h->lam, h->bm);
   for (int t = 0; t < 5; ++t) h->worst[t] = 0.0;
 }
@@ -589,7 +631,7 @@ static void sweep_forward(oracle_t *h, double omega, int check) {
   for (int b = 0; b < h->nb; ++b) {
     long long o0 = h->bdd_occ0[b];
     int k = h->bdd_k[b];
-    h->fm[h->occ_node0[o0]] = 0.0;
+    for (long long v = h->occ_node0[o0]; v < h->occ_node0[o0 + 1]; ++v) h->fm[v] = root_msg(h, v);
     for (int l = 0; l < k; ++l) {
       long long o = o0 + l;
       if (l > 0) {  /* Alg. 2 for the nodes of layer l */
@@ -649,10 +691,54 @@ static void sweep_backward(oracle_t *h, double omega, int check) {
   form_pending(h);
 }
 
+/* Copy-arc pair updates (Sec. 6, the parallel averaging algorithm).  After a forward sweep:
+ * m_bar = m_fwd(tail) + theta + mu_bar is the cost of the best path of the earlier piece through
+ * the copy arc; delta_fwd = m_bar - its minimum over the cut (0 where either is infinite) and
+ * mu_bar += -gamma * delta_fwd + gamma * delta_bwd.  After a backward sweep: m = mu + m_bwd(head)
+ * (the entry node's forward message is 0, the entry arc carries no theta); delta_bwd likewise
+ * and mu += -gamma * delta_bwd + gamma * delta_fwd; then every later piece's root message is
+ * the minimum of mu over the entry arcs into it. */
+static double copy_marginal(const oracle_t *h, long long k) {
+  return h->fm[h->pair_u[k]] + (h->pair_hi[k] ? h->lam[h->pair_occ[k]] : 0.0) + h->mu_bar[k];
+}
+
+static double entry_marginal(const oracle_t *h, long long k) { return h->mu[k] + h->bm[h->pair_w[k]]; }
+
+static double cut_delta(double m, double mn) { return (isinf(m) || isinf(mn)) ? 0.0 : m - mn; }
+
+static void cut_forward(oracle_t *h) {
+  for (int c = 0; c < h->ncuts; ++c) {
+    long long s = h->cut_ptr[c], e = h->cut_ptr[c + 1];
+    double mn = INFINITY;
+    for (long long k = s; k < e; ++k) {
+      double m = copy_marginal(h, k);
+      if (m < mn) mn = m;
+    }
+    for (long long k = s; k < e; ++k) h->dfwd[k] = cut_delta(copy_marginal(h, k), mn);
+    for (long long k = s; k < e; ++k) h->mu_bar[k] += -h->gamma * h->dfwd[k] + h->gamma * h->dbwd[k];
+  }
+}
+
+static void cut_backward(oracle_t *h) {
+  for (int c = 0; c < h->ncuts; ++c) {
+    long long s = h->cut_ptr[c], e = h->cut_ptr[c + 1];
+    double mn = INFINITY;
+    for (long long k = s; k < e; ++k) {
+      double m = entry_marginal(h, k);
+      if (m < mn) mn = m;
+    }
+    for (long long k = s; k < e; ++k) h->dbwd[k] = cut_delta(entry_marginal(h, k), mn);
+    for (long long k = s; k < e; ++k) h->mu[k] += -h->gamma * h->dbwd[k] + h->gamma * h->dfwd[k];
+  }
+  for (long long k = 0; k < h->npairs; ++k) h->root_f[h->pair_w[k]] = INFINITY;
+  for (long long k = 0; k < h->npairs; ++k)
+    if (h->mu[k] < h->root_f[h->pair_w[k]]) h->root_f[h->pair_w[k]] = h->mu[k];
+}
+
 /* bound from the current messages: valid right after a backward sweep */
 static double bound_after_backward(const oracle_t *h) {
   double lb = h->empty_const;
-  for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];
+  for (int b = 0; b < h->nb; ++b) lb += piece_energy(h, b, h->bm);
   for (int i = 0; i < h->n; ++i)
     if (h->deg[i] > 0) lb += agg(h, 0.0, h->P[i]);
   return lb;
@@ -666,6 +752,7 @@ int orc_run_parallel(void *vh, int iters, double omega, int check, double *trace
   double prev = check ? orc_bound(h) : 0.0;
   for (int it = 0; it < iters; ++it) {
     sweep_forward(h, omega, check);
+    if (h->ncuts) cut_forward(h);
     if (check) {
       check_invariant(h);
       double lb = orc_bound(h);
@@ -680,6 +767,14 @@ int orc_run_parallel(void *vh, int iters, double omega, int check, double *trace
       note(&h->worst[2], rel(fresh - lb, fresh));
       note(&h->worst[0], rel(prev - fresh, fresh) * (prev > fresh ? 1.0 : 0.0));
       prev = fresh;
+    }
+    if (h->ncuts) {
+      cut_backward(h);
+      if (check) {
+        double after = orc_bound(h);
+        note(&h->worst[0], rel(prev - after, after) * (prev > after ? 1.0 : 0.0));
+        prev = after;
+      }
     }
     if (trace) trace[it] = lb;
   }
@@ -759,6 +854,125 @@ int orc_run_sequential(void *vh, int iters, int check, double *trace) {
 /* lambda per coefficient; fold != 0 adds the share the next (forward) sweep would add: P_i/|J_i|,
  * or with SRMP P_i/|J_i^>| on J_i^> (all of J_i when J_i^> is empty), so that the returned
  * multipliers satisfy sum_j lambda^j_i = c_i. */
+/* Splits every BDD into pieces at the interval boundaries of the variable order (Sec. 6, Def.
+ * of sub-BDDs): cuts[0 .. ncuts) are ascending positions in the order; variable i lies in
+ * interval #{t : cuts[t] <= place of i}.  A BDD is cut between consecutive layers whose
+ * variables lie in different intervals.  gamma: the copy-arc step size.  Call before any
+ * iteration (it restarts the dual state).  Returns the number of pieces, or -1 on bad input. */
+int orc_split(void *vh, int ncuts, const int *cuts, double gamma) {
+  oracle_t *h = (oracle_t *)vh;
+  if (ncuts < 0 || h->ncuts || !(gamma > 0.0 && gamma <= 1.0)) return -1;
+  for (int t = 0; t < ncuts; ++t)
+    if (cuts[t] < 1 || cuts[t] >= h->n || (t > 0 && cuts[t] <= cuts[t - 1])) return -1;
+  int *place = (int *)malloc((size_t)(h->n + 1) * sizeof(int));
+  int *interval = (int *)malloc((size_t)(h->n + 1) * sizeof(int));
+  if (!place || !interval) { free(place); free(interval); return -1; }
+  for (int k = 0; k < h->n; ++k) place[h->order[k]] = k;
+  for (int i = 0; i < h->n; ++i) {
+    int c = 0;
+    while (c < ncuts && cuts[c] <= place[i]) ++c;
+    interval[i] = c;
+  }
+  /* pieces: count, then fill */
+  int npieces = 0;
+  long long npairs = 0;
+  for (int b = 0; b < h->nb; ++b) {
+    long long o0 = h->bdd_occ0[b];
+    ++npieces;
+    for (int l = 1; l < h->bdd_k[b]; ++l)
+      if (interval[h->occ_var[o0 + l]] != interval[h->occ_var[o0 + l - 1]]) {
+        ++npieces;
+        for (long long u = h->occ_node0[o0 + l - 1]; u < h->occ_node0[o0 + l]; ++u)
+          npairs += (h->lo[u] >= 0) + (h->hi[u] >= 0);
+      }
+  }
+  int *row = (int *)malloc((size_t)npieces * sizeof(int));
+  int *kk = (int *)malloc((size_t)npieces * sizeof(int));
+  long long *occ0 = (long long *)malloc((size_t)(npieces + 1) * sizeof(long long));
+  h->cut_ptr = (long long *)malloc((size_t)(npieces + 1) * sizeof(long long));
+  h->pair_u = (long long *)malloc((size_t)(npairs + 1) * sizeof(long long));
+  h->pair_w = (long long *)malloc((size_t)(npairs + 1) * sizeof(long long));
+  h->pair_occ = (long long *)malloc((size_t)(npairs + 1) * sizeof(long long));
+  h->pair_hi = (int *)malloc((size_t)(npairs + 1) * sizeof(int));
+  h->mu_bar = (double *)calloc((size_t)npairs + 1, sizeof(double));
+  h->mu = (double *)calloc((size_t)npairs + 1, sizeof(double));
+  h->dfwd = (double *)calloc((size_t)npairs + 1, sizeof(double));
+  h->dbwd = (double *)calloc((size_t)npairs + 1, sizeof(double));
+  h->root_f = (double *)calloc((size_t)h->N + 1, sizeof(double));
+  if (!row || !kk || !occ0 || !h->cut_ptr || !h->pair_u || !h->pair_w || !h->pair_occ || !h->pair_hi ||
+      !h->mu_bar || !h->mu || !h->dfwd || !h->dbwd || !h->root_f) {
+    free(row); free(kk); free(occ0); free(place); free(interval);
+    return -1;
+  }
+  int p = 0, c = 0;
+  long long k = 0;
+  h->cut_ptr[0] = 0;
+  for (int b = 0; b < h->nb; ++b) {
+    long long o0 = h->bdd_occ0[b];
+    int start = 0;
+    for (int l = 1; l <= h->bdd_k[b]; ++l) {
+      int boundary = l == h->bdd_k[b] ||
+                     interval[h->occ_var[o0 + l]] != interval[h->occ_var[o0 + l - 1]];
+      if (!boundary) continue;
+      row[p] = h->bdd_row[b];
+      kk[p] = l - start;
+      occ0[p] = o0 + start;
+      ++p;
+      if (l < h->bdd_k[b]) {  /* cut between layers l-1 and l: their arcs become copy pairs */
+        long long ot = o0 + l - 1, nw = h->occ_node0[o0 + l];
+        for (long long u = h->occ_node0[ot]; u < h->occ_node0[ot + 1]; ++u)
+          for (int side = 0; side < 2; ++side) {
+            int *t = side ? &h->hi[u] : &h->lo[u];
+            if (*t < 0) continue;
+            h->pair_u[k] = u;
+            h->pair_w[k] = nw + *t;
+            h->pair_occ[k] = ot;
+            h->pair_hi[k] = side;
+            *t = (int)(ORC_COPY0 - k);
+            ++k;
+          }
+        h->cut_ptr[++c] = k;
+      }
+      start = l;
+    }
+  }
+  occ0[p] = h->O;
+  h->ncuts = c;
+  h->npairs = npairs;
+  h->gamma = gamma;
+  free(h->bdd_row); free(h->bdd_k); free(h->bdd_occ0);
+  h->bdd_row = row; h->bdd_k = kk; h->bdd_occ0 = occ0;
+  h->nb = npieces;
+  for (int b = 0; b < h->nb; ++b)
+    for (int l = 0; l < h->bdd_k[b]; ++l) {
+      h->occ_bdd[h->bdd_occ0[b] + l] = b;
+      h->occ_layer[h->bdd_occ0[b] + l] = l;
+    }
+  free(place); free(interval);
+  orc_init_dual(vh);
+  return npieces;
+}
+
+/* Copy-arc duals: mu_bar and mu of every pair, cuts in order (pairs of a cut: tails in node
+ * order, 0-arc before 1-arc). */
+void orc_get_copy_duals(void *vh, double *mu_bar, double *mu) {
+  oracle_t *h = (oracle_t *)vh;
+  for (long long k = 0; k < h->npairs; ++k) { mu_bar[k] = h->mu_bar[k]; mu[k] = h->mu[k]; }
+}
+
+long long orc_npairs(void *vh) { return ((oracle_t *)vh)->npairs; }
+
+/* Sets the copy-arc duals (and the root messages they imply), then recomputes the backward
+ * messages. */
+void orc_set_copy_duals(void *vh, const double *mu_bar, const double *mu) {
+  oracle_t *h = (oracle_t *)vh;
+  for (long long k = 0; k < h->npairs; ++k) { h->mu_bar[k] = mu_bar[k]; h->mu[k] = mu[k]; }
+  for (long long k = 0; k < h->npairs; ++k) h->root_f[h->pair_w[k]] = INFINITY;
+  for (long long k = 0; k < h->npairs; ++k)
+    if (h->mu[k] < h->root_f[h->pair_w[k]]) h->root_f[h->pair_w[k]] = h->mu[k];
+  for (int b = 0; b < h->nb; ++b) dp_backward(h, b, h->lam, h->bm);
+}
+
 void orc_get_lambda(void *vh, int fold, double *out) {
   oracle_t *h = (oracle_t *)vh;
   if (fold) take_share(h, 1);

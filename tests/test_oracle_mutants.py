@@ -35,8 +35,8 @@ MUTANTS = {
     "bwd_theta": ("double a1 = lam_o + bval(h, bm, o, h->hi[u]);",
                   "double a1 = bval(h, bm, o, h->hi[u]);"),
     # bound forgets the slack term of the y-variables
-    "bound_slack": ("  for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];\n  for (int i = 0; i < h->n; ++i)\n    if (h->deg[i] > 0) lb += agg(h, 0.0, h->P[i]);",
-                    "  for (int b = 0; b < h->nb; ++b) lb += h->bm[h->occ_node0[h->bdd_occ0[b]]];"),
+    "bound_slack": ("  for (int b = 0; b < h->nb; ++b) lb += piece_energy(h, b, h->bm);\n  for (int i = 0; i < h->n; ++i)\n    if (h->deg[i] > 0) lb += agg(h, 0.0, h->P[i]);",
+                    "  for (int b = 0; b < h->nb; ++b) lb += piece_energy(h, b, h->bm);"),
     # SRMP sets of the forward and backward passes swapped (Appendix A.4)
     "srmp_direction": ("return forward ? l < k - 1 : l > 0;", "return forward ? l > 0 : l < k - 1;"),
     # SRMP without the fallback to all of J_i when J_i^> (J_i^<) is empty
@@ -49,10 +49,25 @@ MUTANTS = {
                      "long long rx = x->col, ry = y->col;"),
 }
 
+# planted mistakes in the sub-BDD code (Sec. 6), caught by the split battery
+SPLIT_MUTANTS = {
+    # copy-arc update with the wrong sign of delta_fwd
+    "split_sign": ("h->mu_bar[k] += -h->gamma * h->dfwd[k] + h->gamma * h->dbwd[k];",
+                   "h->mu_bar[k] += h->gamma * h->dfwd[k] + h->gamma * h->dbwd[k];"),
+    # later pieces start every root at 0 instead of min mu over the entry arcs
+    "split_root": ("static double root_msg(const oracle_t *h, long long v) { return h->root_f ? h->root_f[v] : 0.0; }",
+                   "static double root_msg(const oracle_t *h, long long v) { (void)v; return h->root_f ? 0.0 : 0.0; }"),
+    # copy arcs into top without their dual
+    "split_copy_cost": ("if (t <= ORC_COPY0) return h->mu_bar[ORC_COPY0 - t];", "if (t <= ORC_COPY0) return 0.0;"),
+    # entry marginal from the forward instead of the backward message of the head
+    "split_entry": ("return h->mu[k] + h->bm[h->pair_w[k]];", "return h->mu[k] + h->fm[h->pair_w[k]];"),
+}
+MUTANTS_ALL = {**MUTANTS, **SPLIT_MUTANTS}
+
 
 def _compile(tmp_path, name):
     src = open(SRC).read()
-    old, new = MUTANTS[name]
+    old, new = MUTANTS_ALL[name]
     assert src.count(old) == 1, f"mutation anchor for {name} not unique"
     path = tmp_path / f"{name}.c"
     path.write_text(src.replace(old, new))
@@ -114,6 +129,52 @@ def _pins_hold(lib) -> bool:
                                bf.parallel_enum(inst, 4, 0.5, rank, srmp), rtol=0, atol=1e-10):
                 return False
     return True
+
+
+def _split_pins_hold(lib) -> bool:
+    """Piece energies by enumeration with random duals, and the split schedule's checks."""
+    from tests.test_oracle_split import _piece_energies_enum
+    rng = np.random.default_rng(3)
+    for t in range(6):
+        k = int(rng.integers(5, 10))
+        vals = rng.integers(1, 4, size=k) * rng.choice([-1, 1], size=k)
+        sense = [SENSE_LE, SENSE_EQ, SENSE_GE][t % 3]
+        b = int(vals @ rng.integers(0, 2, size=k))
+        inst = _from_rows("r", k, [(np.arange(k), vals, b, sense)], np.zeros(k, np.float32))
+        layers = bf.split_bdds(Oracle(inst, lib=lib).canonical())[0]
+        cuts = sorted(rng.choice(np.arange(1, k), size=2, replace=False).tolist())
+        o = Oracle(inst, lib=lib)
+        o.split(cuts)
+        lam = rng.normal(size=k)
+        o.set_state(lam)
+        mb, mu = rng.normal(size=o.npairs), rng.normal(size=o.npairs)
+        o.set_copy_duals(mb, mu)
+        want = _piece_energies_enum(vals, b, sense, lam, cuts, mb, mu, layers)
+        if not np.allclose(o.energies(), want, rtol=0, atol=1e-12):
+            return False
+    for seed in range(3):
+        inst = random_ilp(n=15, m=10, max_row_vars=9, seed=40 + seed)
+        o = Oracle(inst, lib=lib)
+        o.split([5, 10])
+        tr = o.run_parallel(30, omega=0.5, check=True)
+        w = o.worst()
+        if w["incremental_mm"] > 1e-10 or w["invariant"] > 1e-12 or w["monotone_drop"] > 1e-12:
+            return False
+        mb, mu = o.copy_duals()
+        if np.any(mb + mu > 1e-12) or tr.max() > bf.ilp_optimum(inst) + 1e-9:
+            return False
+    return True
+
+
+def test_original_passes_split_battery():
+    from oracle import _load
+    assert _split_pins_hold(_load())
+
+
+@pytest.mark.parametrize("name", sorted(SPLIT_MUTANTS))
+def test_split_mutant_is_caught(tmp_path, name):
+    lib = _compile(tmp_path, name)
+    assert not _split_pins_hold(lib), f"planted mistake '{name}' passed every split pin"
 
 
 def test_original_passes_battery():

@@ -1,0 +1,123 @@
+"""Pins for the oracle's sub-BDDs and copy-arc duals (Sec. 6: sub-BDDs, copy-arcs, the parallel
+averaging algorithm, Prop. 4)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from instances import SENSE_EQ, SENSE_GE, SENSE_LE, potts_mrf, random_ilp, tomography
+from instances.generators import _from_rows
+from oracle import Oracle
+from tests import bruteforce as bf
+
+
+def _pairs_of_cut(layers, l_cut):
+    """Copy pairs of the cut before layer l_cut, in the oracle's order (tails in node order,
+    0-arc before 1-arc): list of (tail, side)."""
+    out = []
+    lay = layers[l_cut - 1]
+    for u in range(len(lay["lo"])):
+        for side, arr in ((0, lay["lo"]), (1, lay["hi"])):
+            if arr[u] >= 0:
+                out.append((u, side))
+    return out
+
+
+def _piece_energies_enum(vals, b, sense, lam, cuts_layers, mu_bar, mu, layers):
+    """Energy of every piece of one row by enumeration: min over feasible x of (mu of the entry
+    pair x uses + sum of lam x over the piece's layers + mu_bar of the exit pair)."""
+    k = len(vals)
+    X = bf.assignments(k)
+    feas = bf.row_feasible(vals, b, sense)
+    bounds = [0] + list(cuts_layers) + [k]
+    pair_index = []  # per cut: dict (tail, side) -> global pair index
+    base = 0
+    for lc in cuts_layers:
+        prs = _pairs_of_cut(layers, lc)
+        pair_index.append({p: base + t for t, p in enumerate(prs)})
+        base += len(prs)
+    E = np.full(len(bounds) - 1, np.inf)
+    for x, ok in zip(X, feas):
+        if not ok:
+            continue
+        acc, path = bf.walk(layers, x)
+        assert acc
+        used = [pair_index[c][(path[lc - 1], int(x[lc - 1]))] for c, lc in enumerate(cuts_layers)]
+        for p in range(len(bounds) - 1):
+            cost = float(np.dot(lam[bounds[p]:bounds[p + 1]], x[bounds[p]:bounds[p + 1]]))
+            if p > 0:
+                cost += mu[used[p - 1]]
+            if p < len(bounds) - 2:
+                cost += mu_bar[used[p]]
+            E[p] = min(E[p], cost)
+    return E
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_piece_energies_match_enumeration(seed):
+    """One row split at one or two random places; random lambda and random copy duals: every
+    piece's energy (multi-root pieces with root messages min mu, copy arcs into top with cost
+    mu_bar) equals the enumeration of the row's feasible points."""
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(4, 11))
+    vals = rng.integers(1, 4, size=k) * rng.choice([-1, 1], size=k)
+    sense = [SENSE_LE, SENSE_EQ, SENSE_GE][seed % 3]
+    b = int(vals @ rng.integers(0, 2, size=k))
+    inst = _from_rows("r", k, [(np.arange(k), vals, b, sense)], np.zeros(k, np.float32))
+    layers = bf.split_bdds(Oracle(inst).canonical())[0]
+    ncut = 1 + seed % 2
+    cuts_layers = sorted(rng.choice(np.arange(1, k), size=ncut, replace=False).tolist())
+    o = Oracle(inst)
+    assert o.split(cuts_layers) == ncut + 1
+    lam = rng.normal(size=k)
+    o.set_state(lam)
+    mb = rng.normal(size=o.npairs)
+    mu = rng.normal(size=o.npairs)
+    o.set_copy_duals(mb, mu)
+    want = _piece_energies_enum(vals, b, sense, lam, cuts_layers, mb, mu, layers)
+    np.testing.assert_allclose(o.energies(), want, rtol=0, atol=1e-12)
+
+
+def test_no_cuts_is_the_unsplit_method():
+    inst = random_ilp(n=16, m=10, max_row_vars=8, seed=5)
+    a, b = Oracle(inst), Oracle(inst)
+    assert b.split([]) == a.nb
+    assert np.array_equal(a.run_parallel(25), b.run_parallel(25))
+
+
+@pytest.mark.parametrize("gamma", [0.5, 1.0])
+@pytest.mark.parametrize("seed", range(6))
+def test_split_schedule_invariants_and_duality(seed, gamma):
+    """With cuts: incremental min-marginals equal the definitional ones of the pieces at every
+    visit, sum_j lambda + P = c, the bound never decreases (Prop. 4 together with the deferred
+    averaging), mu + mu_bar <= 0 for every pair, and every bound is below the ILP optimum."""
+    inst = random_ilp(n=15, m=10, max_row_vars=9, seed=40 + seed)
+    rng = np.random.default_rng(seed)
+    cuts = sorted(rng.choice(np.arange(1, inst.n), size=2, replace=False).tolist())
+    o = Oracle(inst)
+    o.split(cuts, gamma)
+    tr = o.run_parallel(40, omega=0.5, check=True)
+    w = o.worst()
+    assert w["incremental_mm"] < 1e-10 and w["invariant"] < 1e-12 and w["monotone_drop"] < 1e-12
+    mb, mu = o.copy_duals()
+    assert np.all(mb + mu <= 1e-12)
+    assert tr.max() <= bf.ilp_optimum(inst) + 1e-9
+
+
+def test_split_bound_below_unsplit_at_start_and_converges():
+    """The pieces relax the rows (copy constraints dualised): at mu = 0 the split bound is at most
+    the unsplit one; iterating closes most of the gap."""
+    inst = tomography(side=12, seed=3, unary_sigma=0.1)
+    a = Oracle(inst)
+    b = Oracle(inst)
+    b.split([inst.n // 4, inst.n // 2, 3 * inst.n // 4])
+    assert b.bound() <= a.bound() + 1e-9
+    ta, tb = a.run_parallel(300), b.run_parallel(300)
+    assert tb[-1] > tb[0] and (ta[-1] - tb[-1]) < 0.2 * (ta[-1] - tb[0])
+
+
+def test_split_rejects_bad_input():
+    inst = potts_mrf(3, 3, 2, seed=0)
+    for cuts, g in (([0], 0.5), ([3, 3], 0.5), ([inst.n], 0.5), ([2], 0.0), ([2], 1.5)):
+        with pytest.raises(ValueError):
+            Oracle(inst).split(cuts, g)
