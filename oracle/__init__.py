@@ -48,6 +48,8 @@ def _configure(lib):
     lib.orc_set_srmp.argtypes = [vp, i32]
     lib.orc_split.restype = i32
     lib.orc_split.argtypes = [vp, i32, P(i32), f64]
+    lib.orc_split_depth.restype = i32
+    lib.orc_split_depth.argtypes = [vp, i32, f64]
     lib.orc_npairs.restype = i64
     lib.orc_npairs.argtypes = [vp]
     lib.orc_get_copy_duals.argtypes = [vp, P(f64), P(f64)]
@@ -171,6 +173,17 @@ class Oracle:
         nb = self.lib.orc_split(self.h, len(cuts), _p(cuts, C.c_int) if len(cuts) else None, float(gamma))
         if nb < 0:
             raise ValueError("bad cuts or gamma")
+        self.nb = nb
+        self.npairs = int(self.lib.orc_npairs(self.h))
+        return nb
+
+    def split_depth(self, depth: int, gamma: float = 0.5) -> int:
+        """Sub-BDDs of at most `depth` layers: every BDD of k layers is cut before layers
+        floor(t k / q), t = 1 .. q-1, q = ceil(k / depth), with copy-arc step size gamma; restarts
+        the dual state.  Returns the number of pieces."""
+        nb = self.lib.orc_split_depth(self.h, int(depth), float(gamma))
+        if nb < 0:
+            raise ValueError("bad depth or gamma")
         self.nb = nb
         self.npairs = int(self.lib.orc_npairs(self.h))
         return nb

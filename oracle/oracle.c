@@ -50,7 +50,9 @@
  *     mu_bar moves by -gamma * delta_fwd + gamma * delta_bwd (delta_fwd: arc-marginal of the copy
  *     arc minus its minimum over the cut), after every backward sweep mu moves by
  *     -gamma * delta_bwd + gamma * delta_fwd (delta_bwd: the same on the entry arcs).  Each
- *     piece is a subproblem of the decomposition (its layers are its occurrences).
+ *     piece is a subproblem of the decomposition (its layers are its occurrences).  A depth
+ *     split (a reading for deep BDDs) cuts every BDD into pieces of at most D layers instead,
+ *     with the same copy arcs and steps.
  * Readings where the paper is silent: a min-marginal that is +inf (a row that forces x_i)
  * gives the difference 0; a variable in no row contributes min(0, c_i) to the bound; an empty
  * row is dropped when 0 (sense) b holds and is infeasible otherwise.
@@ -851,9 +853,20 @@ int orc_run_sequential(void *vh, int iters, int check, double *trace) {
 /* ------------------------------------------------------------------------------------ */
 /* state access (arrays indexed by position in the input CSR; zero coefficients get 0)    */
 /* ------------------------------------------------------------------------------------ */
-/* lambda per coefficient; fold != 0 adds the share the next (forward) sweep would add: P_i/|J_i|,
- * or with SRMP P_i/|J_i^>| on J_i^> (all of J_i when J_i^> is empty), so that the returned
- * multipliers satisfy sum_j lambda^j_i = c_i. */
+/* Is there a cut between layers l-1 and l of a BDD with first occurrence o0 and k layers?
+ * With intervals (Sec. 6): its two variables lie in different intervals.  With a depth limit D
+ * (interval == NULL; a reading for deep BDDs, below): l is one of floor(t k / q), t = 1 .. q-1,
+ * q = ceil(k / D). */
+static int cut_before(const oracle_t *h, const int *interval, int D, long long o0, int k, int l) {
+  if (interval) return interval[h->occ_var[o0 + l]] != interval[h->occ_var[o0 + l - 1]];
+  int q = (k + D - 1) / D;
+  for (int t = 1; t < q; ++t)
+    if ((long long)t * k / q == l) return 1;
+  return 0;
+}
+
+static int split_core(oracle_t *h, const int *interval, int D, double gamma);
+
 /* Splits every BDD into pieces at the interval boundaries of the variable order (Sec. 6, Def.
  * of sub-BDDs): cuts[0 .. ncuts) are ascending positions in the order; variable i lies in
  * interval #{t : cuts[t] <= place of i}.  A BDD is cut between consecutive layers whose
@@ -873,6 +886,25 @@ int orc_split(void *vh, int ncuts, const int *cuts, double gamma) {
     while (c < ncuts && cuts[c] <= place[i]) ++c;
     interval[i] = c;
   }
+  free(place);
+  int r = split_core(h, interval, 0, gamma);
+  free(interval);
+  return r;
+}
+
+/* Depth split (a reading: Sec. 6 cuts a BDD wherever two consecutive layers fall into
+ * different intervals of one global partition, and neither the copy-arc steps nor Prop. 4's
+ * argument use the partition beyond that, so a cut may sit between any two consecutive layers
+ * of any BDD): every BDD with k > D layers becomes q = ceil(k / D) pieces, cut before layers
+ * floor(t k / q), t = 1 .. q-1, so that no piece has more than D layers.  Returns the number of
+ * pieces, or -1 on bad input. */
+int orc_split_depth(void *vh, int D, double gamma) {
+  oracle_t *h = (oracle_t *)vh;
+  if (D < 1 || h->ncuts || !(gamma > 0.0 && gamma <= 1.0)) return -1;
+  return split_core(h, NULL, D, gamma);
+}
+
+static int split_core(oracle_t *h, const int *interval, int D, double gamma) {
   /* pieces: count, then fill */
   int npieces = 0;
   long long npairs = 0;
@@ -880,7 +912,7 @@ int orc_split(void *vh, int ncuts, const int *cuts, double gamma) {
     long long o0 = h->bdd_occ0[b];
     ++npieces;
     for (int l = 1; l < h->bdd_k[b]; ++l)
-      if (interval[h->occ_var[o0 + l]] != interval[h->occ_var[o0 + l - 1]]) {
+      if (cut_before(h, interval, D, o0, h->bdd_k[b], l)) {
         ++npieces;
         for (long long u = h->occ_node0[o0 + l - 1]; u < h->occ_node0[o0 + l]; ++u)
           npairs += (h->lo[u] >= 0) + (h->hi[u] >= 0);
@@ -901,7 +933,7 @@ int orc_split(void *vh, int ncuts, const int *cuts, double gamma) {
   h->root_f = (double *)calloc((size_t)h->N + 1, sizeof(double));
   if (!row || !kk || !occ0 || !h->cut_ptr || !h->pair_u || !h->pair_w || !h->pair_occ || !h->pair_hi ||
       !h->mu_bar || !h->mu || !h->dfwd || !h->dbwd || !h->root_f) {
-    free(row); free(kk); free(occ0); free(place); free(interval);
+    free(row); free(kk); free(occ0);
     return -1;
   }
   int p = 0, c = 0;
@@ -911,8 +943,7 @@ int orc_split(void *vh, int ncuts, const int *cuts, double gamma) {
     long long o0 = h->bdd_occ0[b];
     int start = 0;
     for (int l = 1; l <= h->bdd_k[b]; ++l) {
-      int boundary = l == h->bdd_k[b] ||
-                     interval[h->occ_var[o0 + l]] != interval[h->occ_var[o0 + l - 1]];
+      int boundary = l == h->bdd_k[b] || cut_before(h, interval, D, o0, h->bdd_k[b], l);
       if (!boundary) continue;
       row[p] = h->bdd_row[b];
       kk[p] = l - start;
@@ -948,8 +979,7 @@ int orc_split(void *vh, int ncuts, const int *cuts, double gamma) {
       h->occ_bdd[h->bdd_occ0[b] + l] = b;
       h->occ_layer[h->bdd_occ0[b] + l] = l;
     }
-  free(place); free(interval);
-  orc_init_dual(vh);
+  orc_init_dual(h);
   return npieces;
 }
 
@@ -973,6 +1003,9 @@ void orc_set_copy_duals(void *vh, const double *mu_bar, const double *mu) {
   for (int b = 0; b < h->nb; ++b) dp_backward(h, b, h->lam, h->bm);
 }
 
+/* lambda per coefficient; fold != 0 adds the share the next (forward) sweep would add: P_i/|J_i|,
+ * or with SRMP P_i/|J_i^>| on J_i^> (all of J_i when J_i^> is empty), so that the returned
+ * multipliers satisfy sum_j lambda^j_i = c_i. */
 void orc_get_lambda(void *vh, int fold, double *out) {
   oracle_t *h = (oracle_t *)vh;
   if (fold) take_share(h, 1);

@@ -61,6 +61,8 @@ SPLIT_MUTANTS = {
     "split_copy_cost": ("if (t <= ORC_COPY0) return h->mu_bar[ORC_COPY0 - t];", "if (t <= ORC_COPY0) return 0.0;"),
     # entry marginal from the forward instead of the backward message of the head
     "split_entry": ("return h->mu[k] + h->bm[h->pair_w[k]];", "return h->mu[k] + h->fm[h->pair_w[k]];"),
+    # depth split with floor(k / D) pieces instead of ceil(k / D)
+    "split_depth_floor": ("int q = (k + D - 1) / D;", "int q = k / D;"),
 }
 MUTANTS_ALL = {**MUTANTS, **SPLIT_MUTANTS}
 
@@ -162,6 +164,16 @@ def _split_pins_hold(lib) -> bool:
             return False
         mb, mu = o.copy_duals()
         if np.any(mb + mu > 1e-12) or tr.max() > bf.ilp_optimum(inst) + 1e-9:
+            return False
+    for D in (2, 3):  # depth split: no piece deeper than D, every piece an honest subproblem
+        inst = random_ilp(n=20, m=12, max_row_vars=11, seed=70 + D, coef=3)
+        o = Oracle(inst, lib=lib)
+        o.split_depth(D)
+        if o.canonical()["bdd_depth"].max() > D:
+            return False
+        tr = o.run_parallel(20, omega=0.5, check=True)
+        w = o.worst()
+        if w["incremental_mm"] > 1e-10 or w["monotone_drop"] > 1e-12 or tr.max() > bf.ilp_optimum(inst) + 1e-9:
             return False
     return True
 

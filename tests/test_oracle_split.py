@@ -121,3 +121,102 @@ def test_split_rejects_bad_input():
     for cuts, g in (([0], 0.5), ([3, 3], 0.5), ([inst.n], 0.5), ([2], 0.0), ([2], 1.5)):
         with pytest.raises(ValueError):
             Oracle(inst).split(cuts, g)
+
+
+def _pieces_by_row(can):
+    """Depths of the pieces of every row, in layer order."""
+    out = {}
+    for r, d in zip(can["bdd_row"], can["bdd_depth"]):
+        out.setdefault(int(r), []).append(int(d))
+    return out
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 5, 8])
+def test_depth_split_structure(D):
+    """Every piece has at most D layers, a row of k layers has ceil(k / D) pieces whose depths
+    differ by at most one and add up to k, and the pieces keep the row's nodes and arcs: every
+    copy code replaces one arc into a node of the next layer, in pair order."""
+    inst = random_ilp(n=24, m=14, max_row_vars=12, seed=90 + D, coef=3)
+    whole = Oracle(inst).canonical()
+    o = Oracle(inst)
+    o.split_depth(D)
+    can = o.canonical()
+    assert can["bdd_depth"].max() <= D
+    k_of_row = dict(zip(whole["bdd_row"].tolist(), whole["bdd_depth"].tolist()))
+    for r, ds in _pieces_by_row(can).items():
+        k = k_of_row[r]
+        assert sum(ds) == k and len(ds) == -(-k // D) and max(ds) - min(ds) <= 1, (r, k, ds)
+    np.testing.assert_array_equal(can["occ_width"], whole["occ_width"])
+    for side in ("lo", "hi"):
+        c = can[side] <= -4
+        assert np.all(whole[side][c] >= 0), "a copy arc replaced an arc into a terminal"
+        np.testing.assert_array_equal(can[side][~c], whole[side][~c])
+    codes = np.sort(np.concatenate([can["lo"][can["lo"] <= -4], can["hi"][can["hi"] <= -4]]))[::-1]
+    np.testing.assert_array_equal(-4 - codes, np.arange(o.npairs))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_depth_split_piece_energies_match_enumeration(seed):
+    """One row cut into pieces of at most D layers; random lambda and copy duals: every piece's
+    energy equals the enumeration of the row's feasible points (cut layers read from the
+    pieces' depths)."""
+    rng = np.random.default_rng(100 + seed)
+    k = int(rng.integers(5, 12))
+    vals = rng.integers(1, 4, size=k) * rng.choice([-1, 1], size=k)
+    sense = [SENSE_LE, SENSE_EQ, SENSE_GE][seed % 3]
+    b = int(vals @ rng.integers(0, 2, size=k))
+    inst = _from_rows("r", k, [(np.arange(k), vals, b, sense)], np.zeros(k, np.float32))
+    layers = bf.split_bdds(Oracle(inst).canonical())[0]
+    D = int(rng.integers(2, k))
+    o = Oracle(inst)
+    o.split_depth(D)
+    depths = o.canonical()["bdd_depth"]
+    cuts_layers = np.cumsum(depths)[:-1].tolist()
+    assert len(cuts_layers) >= 1
+    lam = rng.normal(size=k)
+    o.set_state(lam)
+    mb = rng.normal(size=o.npairs)
+    mu = rng.normal(size=o.npairs)
+    o.set_copy_duals(mb, mu)
+    want = _piece_energies_enum(vals, b, sense, lam, cuts_layers, mb, mu, layers)
+    np.testing.assert_allclose(o.energies(), want, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("D", [2, 4])
+@pytest.mark.parametrize("seed", range(4))
+def test_depth_split_schedule_invariants_and_duality(seed, D):
+    """Depth split: incremental min-marginals equal the definitional ones at every visit, the
+    invariant, a non-decreasing bound (Prop. 4's argument per cut), mu + mu_bar <= 0, weak
+    duality; a depth limit no BDD exceeds changes nothing."""
+    inst = random_ilp(n=15, m=10, max_row_vars=9, seed=60 + seed)
+    o = Oracle(inst)
+    o.split_depth(D)
+    assert o.npairs > 0
+    tr = o.run_parallel(40, omega=0.5, check=True)
+    w = o.worst()
+    assert w["incremental_mm"] < 1e-10 and w["invariant"] < 1e-12 and w["monotone_drop"] < 1e-12
+    mb, mu = o.copy_duals()
+    assert np.all(mb + mu <= 1e-12)
+    assert tr.max() <= bf.ilp_optimum(inst) + 1e-9
+    a, b = Oracle(inst), Oracle(inst)
+    assert b.split_depth(100) == a.nb and b.npairs == 0
+    assert np.array_equal(a.run_parallel(20), b.run_parallel(20))
+
+
+def test_depth_split_closes_the_gap_on_tomography():
+    """Tomography projections (up to 24 layers at side 12) in pieces of at most 6 layers: the
+    bound starts no higher than the unsplit one and iterating closes most of the gap."""
+    inst = tomography(side=12, seed=3, unary_sigma=0.1)
+    a, b = Oracle(inst), Oracle(inst)
+    b.split_depth(6)
+    assert b.canonical()["bdd_depth"].max() <= 6
+    assert b.bound() <= a.bound() + 1e-9
+    ta, tb = a.run_parallel(300), b.run_parallel(300)
+    assert tb[-1] > tb[0] and (ta[-1] - tb[-1]) < 0.2 * (ta[-1] - tb[0])
+
+
+def test_depth_split_rejects_bad_input():
+    inst = potts_mrf(3, 3, 2, seed=0)
+    for D, g in ((0, 0.5), (-1, 0.5), (2, 0.0), (2, 1.5)):
+        with pytest.raises(ValueError):
+            Oracle(inst).split_depth(D, g)
