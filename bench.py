@@ -57,6 +57,11 @@ def parse():
                     help="skip the variable-order / averaging comparison of the default line")
     ap.add_argument("--variant-iters", type=int, default=300)
     ap.add_argument("--variants-only", action="store_true", help="print only the order / averaging comparison")
+    ap.add_argument("--no-split", action="store_true", help="skip the sub-BDD (interval split) comparison")
+    ap.add_argument("--split-only", action="store_true", help="print only the sub-BDD comparison")
+    ap.add_argument("--split-iters", type=int, default=200, help="timed iterations per sub-BDD variant")
+    ap.add_argument("--split-ttb-iters", type=int, default=300,
+                    help="oracle iterations giving the sub-BDD comparison's target bound (the GPU runs 3x)")
     return ap.parse_args()
 
 
@@ -341,6 +346,9 @@ def ours(args):
     variants = None
     if world == 1 and not args.no_variants:
         variants = run_variants(args, stream)
+    split = None
+    if world == 1 and not args.no_split:
+        split = run_split(args, stream)
 
     if rank != 0:
         if world > 1:
@@ -374,6 +382,7 @@ def ours(args):
         "batched": batch,
         "differentiation": diff,
         "order_and_averaging": variants,
+        "sub_bdds": split,
         "gpu_launches": launches,
         "schedule": "persistent" if s.schedule == 0 else "per-phase graphs",
         "staging": staging_of(s),
@@ -667,6 +676,68 @@ def run_variants(args, stream) -> dict:
     return out
 
 
+def run_split(args, stream) -> dict:
+    """Sub-BDDs with copy-arc duals (Sec. 6) on the wide, deep tomography BDDs (64x64 image, 3
+    levels; projections up to 128 layers and 97 nodes wide): the whole BDDs; the variable order
+    cut into k intervals of similar node counts, k = 4, 32, 128 (a row projection covers 192
+    consecutive variables, so only many intervals cut all of them); and the depth split into
+    pieces of at most D = 64, 32, 16, 8 layers.  Per variant: device ms per iteration
+    and arcs/s of the stated workload (zero unaries), the forward / backward sweep kernels' ms,
+    and on the tie-break variant (unaries N(0, 0.01)) the iterations and ms until the bound is
+    within 1e-3 (relative) of the oracle's unsplit bound after --split-ttb-iters iterations, out
+    of three times as many (a split relaxes the rows until the copy duals agree, so it may need
+    more iterations)."""
+    import torch
+
+    from paper_2009_00481_gb300 import Solver
+    from instances import tomography
+
+    K, KT = args.split_iters, args.split_ttb_iters
+    work = config(2)
+    tie = tomography(side=64, seed=0, unary_sigma=0.01)
+    t0 = time.perf_counter()
+    lb_ref, _, _, _ = oracle_run(tie, KT)
+    oracle_s = time.perf_counter() - t0
+    target = lb_ref - TTB_TOL * abs(lb_ref)
+    out = {"workload": CONFIG_NAMES[2], "tie_break_workload": "tomography_64x64x3 with N(0, 0.01) unaries",
+           "iterations_timed": K, "gamma": 0.5, "oracle_unsplit_bound": lb_ref,
+           "oracle_iterations": KT, "oracle_s": oracle_s, "target": target, "variants": {}}
+    trace = torch.zeros(max(K, 3 * KT), dtype=torch.float64, device="cuda")
+    variants = [("whole", {})] + [(f"intervals_{k}", {"split": k}) for k in (4, 32, 128)] + \
+        [(f"depth_{d}", {"split_depth": d}) for d in (64, 32, 16, 8)]
+    for label, kw in variants:
+        row = {}
+        for name, inst, iters in (("stated", work, K), ("tie_break", tie, 3 * KT)):
+            s = Solver(inst, omega=0.5, stream=stream.cuda_stream, **kw)
+            s.iterate_device(min(iters, 16), trace=trace, stream=stream.cuda_stream)  # warm-up (graphs)
+            s.set_costs(inst.c)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            s.iterate_device(iters, trace=trace, stream=stream.cuda_stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms_it = a.elapsed_time(b) / iters
+            tr = trace[:iters].cpu().numpy()
+            if name == "stated":
+                s.set_costs(inst.c)
+                kms = s.iterate_profiled(min(iters, 50)) / min(iters, 50)
+                row.update({"pieces": s.nb, "cuts": s.n_cuts, "copy_pairs": s.npairs,
+                            "max_depth": s.max_depth, "ms_per_iter": ms_it,
+                            "arcs_per_s": 2 * s.N / (ms_it / 1e3),
+                            "kernel_ms_per_iter": {"fwd": float(kms[0]), "pending_and_cut": float(kms[1]),
+                                                   "bwd": float(kms[2]),
+                                                   "pending_bound_and_cut": float(kms[3])}})
+            else:
+                hit = np.nonzero(tr >= target)[0]
+                kh = int(hit[0]) + 1 if hit.size else None
+                row.update({"tie_break_ms_per_iter": ms_it, "tie_break_bound": float(tr[-1]),
+                            "iters_to_target": kh, "ms_to_target": ms_it * kh if kh else None})
+            s.close()
+        out["variants"][label] = row
+    return out
+
+
 def batched(args):
     """`--config 4`: the batch workload as the bench line."""
     import torch
@@ -728,6 +799,12 @@ def main():
         reference(args)
     elif args.config == 4:
         batched(args)
+    elif args.split_only:
+        import torch
+        torch.cuda.set_device(0)
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        print(json.dumps({"metric": METRIC, "sub_bdds": run_split(args, stream)}), flush=True)
     elif args.variants_only:
         import torch
         torch.cuda.set_device(0)

@@ -45,7 +45,7 @@ enum {
   BDD_ESTATE = -8       /* the call needs device state but the solver was built host-only */
 };
 
-#define BDD_SIZES_LEN 13
+#define BDD_SIZES_LEN 16
 
 /* Options for bdd_build.  Fill with bdd_default_options, then change fields. */
 typedef struct {
@@ -106,6 +106,38 @@ typedef struct {
                                  warm-up and three iterations each, kernel by kernel) and keeps
                                  the faster per sweep direction.  The variants compute identical
                                  values; the persistent schedule and other sweeps use 0. */
+  int split_intervals;        /* sub-BDDs (Sec. 6, Def. of sub-BDDs and copy-arcs; the parallel
+                                 min-marginal averaging algorithm).  0 or 1 (default): no split.
+                                 k >= 2: the variable order is cut into at most k intervals
+                                 holding similar node counts (a node counts for its layer's
+                                 variable; the first place whose preceding places hold at least
+                                 t N / k nodes starts interval t + 1).  Every BDD is cut between
+                                 consecutive layers whose variables lie in different intervals;
+                                 each piece is a subproblem of its own (several roots when it
+                                 starts below the BDD's root), the arcs crossing a cut become
+                                 copy-arc pairs: the earlier piece's copy arc into top with
+                                 cost theta + mu_bar, the later piece's entry arc with cost mu
+                                 (the arc's theta stays with the copy arc).  After every forward
+                                 sweep each cut moves mu_bar by -gamma d_fwd + gamma d_bwd, after
+                                 every backward sweep mu by -gamma d_bwd + gamma d_fwd (d: an
+                                 arc-marginal minus its minimum over the cut).  Min-marginals
+                                 and energies then refer to the pieces.  Split solvers run
+                                 schedule 1 without fused pending sums, need alpha = 0
+                                 (else BDD_EINVAL) and refuse bdd_bound_parts. */
+  const int *cuts;            /* explicit cut places instead (n_cuts entries, ascending, in
+                                 [1, n); variable i lies in interval #{t : cuts[t] <= place of
+                                 i}); overrides split_intervals; bad cuts -> BDD_EINVAL.  Read
+                                 by bdd_build only. */
+  int n_cuts;                 /* entries of cuts; default 0 */
+  float gamma;                /* copy-arc step size in (0, 1]; default 0.5 (the paper's choice
+                                 in its experiments, Sec. 7) */
+  int split_depth;            /* depth split instead of intervals: 0 (default) off; D >= 1 cuts
+                                 every BDD of k > D layers into q = ceil(k / D) pieces, before
+                                 layers floor(t k / q), t = 1 .. q-1, with the same copy arcs and
+                                 steps.  This bounds the longest chain of dependent layers a
+                                 sweep walks, which a partition of the variable order does not
+                                 (a BDD over consecutive variables stays whole unless a cut falls
+                                 inside it).  Overrides split_intervals and cuts. */
 } bdd_options;
 
 void bdd_default_options(bdd_options *opt);
@@ -181,11 +213,12 @@ int bdd_smooth_backward(bdd_solver *h, const double *d_gbound, float *d_grad_c, 
  * host. */
 int bdd_set_costs(bdd_solver *h, const float *c);
 
-/* Sizes: out[0] n, [1] m, [2] BDDs, [3] occurrences (nonzeros kept), [4] nodes, [5] max depth,
- * [6] max width, [7] nnz, [8] device bytes held, [9] warp tiles, [10] block tiles,
- * [11] schedule in use (0 persistent, 1 per-phase graphs), [12] warp-tile staging the autotuner
- * chose for the update sweeps: bit 0 forward, bit 1 backward (0 bulk-copy ring of 4-layer
- * windows, 1 8-layer cp.async windows). */
+/* Sizes: out[0] n, [1] m, [2] BDDs (pieces of a split solver), [3] occurrences (nonzeros
+ * kept), [4] nodes, [5] max depth, [6] max width, [7] nnz, [8] device bytes held, [9] warp
+ * tiles, [10] block tiles, [11] schedule in use (0 persistent, 1 per-phase graphs), [12]
+ * warp-tile staging the autotuner chose for the update sweeps: bit 0 forward, bit 1 backward
+ * (0 bulk-copy ring of 4-layer windows, 1 8-layer cp.async windows), [13] cuts of the variable
+ * order, [14] copy-arc pairs, [15] depth limit of a depth split (0: none). */
 int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]);
 
 /* Canonical form of the BDDs, read back from the device slabs (or the host copy when built
@@ -196,6 +229,21 @@ int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]);
  * occ_width [occurrences]; lo, hi [nodes].  occ_csr is the CSR position of the coefficient. */
 int bdd_export_canonical(const bdd_solver *h, int *bdd_row, int *bdd_depth, int *occ_var,
                          long long *occ_csr, int *occ_width, int *lo, int *hi);
+
+/* Cut places of a split solver (Sec. 6): cuts: host int32[out[13] of bdd_sizes]. */
+int bdd_get_cuts(const bdd_solver *h, int *cuts);
+
+/* Copy-arc duals of a split solver (Sec. 6, Def. of copy-arc costs): mu_bar (the copy arc's
+ * dual, earlier piece) and mu (the entry arc's dual, later piece), host float[pairs] each
+ * (out[14] of bdd_sizes; NULL skips one in the get form).  Pairs are in canonical order: the
+ * cuts of BDD 0 (ascending row) by ascending layer, then BDD 1, ...; inside a cut, the tails
+ * in canonical node order, the 0-arc before the 1-arc.  Every mu + mu_bar <= 0 keeps the bound
+ * valid; the iteration keeps it when it starts there (all 0 after bdd_build / bdd_set_costs).
+ * bdd_set_copy_duals also recomputes the root messages (min of mu over a head's entry arcs) and
+ * the backward messages; it leaves the last deltas of the dual steps as they are.  Both
+ * synchronise. */
+int bdd_get_copy_duals(const bdd_solver *h, float *mu_bar, float *mu);
+int bdd_set_copy_duals(bdd_solver *h, const float *mu_bar, const float *mu);
 
 /* Dual state: lambda without the pending share (float[nnz], CSR positions) and the pending
  * sums P_i (float[n]).  bdd_set_state also recomputes the backward messages. */

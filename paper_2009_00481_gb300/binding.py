@@ -16,14 +16,15 @@ from .build import LIB
 
 BDD_OK, BDD_EINVAL, BDD_EINFEASIBLE, BDD_ETOOBIG, BDD_ENOMEM = 0, -1, -2, -3, -4
 BDD_ECUDA, BDD_ETIMEOUT, BDD_EDEVICE, BDD_ESTATE = -5, -6, -7, -8
-BDD_SIZES_LEN = 13
+BDD_SIZES_LEN = 16
 
 EXPORTED = [
     "bdd_default_options", "bdd_build", "bdd_last_failed_row", "bdd_iterate", "bdd_iterate_device",
     "bdd_iterate_profiled",
     "bdd_set_costs", "bdd_sizes", "bdd_export_canonical", "bdd_get_state", "bdd_set_state",
     "bdd_strerror", "bdd_free", "bdd_lower_bound_noalloc", "bdd_bound_parts", "bdd_smooth_forward",
-    "bdd_smooth_backward", "bdd_cuthill_mckee",
+    "bdd_smooth_backward", "bdd_cuthill_mckee", "bdd_get_cuts", "bdd_get_copy_duals",
+    "bdd_set_copy_duals",
 ]
 
 
@@ -32,7 +33,9 @@ class bdd_options(C.Structure):
                 ("max_device_bytes", C.c_longlong), ("host_only", C.c_int), ("device", C.c_int),
                 ("stream", C.c_void_p), ("schedule", C.c_int), ("spin_limit", C.c_longlong),
                 ("alpha", C.c_float), ("var_rank", C.POINTER(C.c_int)), ("averaging", C.c_int),
-                ("fused_pending", C.c_int), ("staging", C.c_int)]
+                ("fused_pending", C.c_int), ("staging", C.c_int), ("split_intervals", C.c_int),
+                ("cuts", C.POINTER(C.c_int)), ("n_cuts", C.c_int), ("gamma", C.c_float),
+                ("split_depth", C.c_int)]
 
 
 class BDDError(RuntimeError):
@@ -80,6 +83,9 @@ def load(path: str | None = None):
     lib.bdd_smooth_forward.argtypes = [vp, i32, vp, vp, vp]
     lib.bdd_smooth_backward.argtypes = [vp, vp, vp, vp]
     lib.bdd_cuthill_mckee.argtypes = [i32, i32, P(i64), P(i32), P(i32), P(i32)]
+    lib.bdd_get_cuts.argtypes = [vp, P(i32)]
+    lib.bdd_get_copy_duals.argtypes = [vp, P(f32), P(f32)]
+    lib.bdd_set_copy_duals.argtypes = [vp, P(f32), P(f32)]
     if path == LIB:
         _lib = lib
     return lib
@@ -206,6 +212,29 @@ def bdd_set_state(h, lam, P=None):
     lam = np.ascontiguousarray(lam, np.float32)
     P = None if P is None else np.ascontiguousarray(P, np.float32)
     _check(load().bdd_set_state(h, _ptr(lam, C.c_float), _ptr(P, C.c_float)), "bdd_set_state")
+
+
+def bdd_get_cuts(h) -> np.ndarray:
+    """Cut places of a split solver (Sec. 6)."""
+    k = int(bdd_sizes(h)[13])
+    cuts = np.zeros(max(k, 1), np.int32)
+    _check(load().bdd_get_cuts(h, _ptr(cuts, C.c_int)), "bdd_get_cuts")
+    return cuts[:k]
+
+
+def bdd_get_copy_duals(h):
+    """(mu_bar, mu) of every copy-arc pair, canonical pair order."""
+    k = int(bdd_sizes(h)[14])
+    mb = np.zeros(max(k, 1), np.float32)
+    mu = np.zeros(max(k, 1), np.float32)
+    _check(load().bdd_get_copy_duals(h, _ptr(mb, C.c_float), _ptr(mu, C.c_float)), "bdd_get_copy_duals")
+    return mb[:k], mu[:k]
+
+
+def bdd_set_copy_duals(h, mu_bar, mu):
+    mb = np.ascontiguousarray(mu_bar, np.float32)
+    m = np.ascontiguousarray(mu, np.float32)
+    _check(load().bdd_set_copy_duals(h, _ptr(mb, C.c_float), _ptr(m, C.c_float)), "bdd_set_copy_duals")
 
 
 def bdd_lower_bound_noalloc(n: int, nb: int, d_E: int, d_P: int, d_deg: int, empty_const: float,

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -131,6 +132,14 @@ struct bdd_solver {
   float *t_lam = nullptr, *t_nodeA = nullptr, *t_nodeB = nullptr, *t_gnode = nullptr;
   float *t_glam0 = nullptr, *t_glam1 = nullptr, *t_gshr = nullptr, *t_gdelta = nullptr;
   float *t_delta = nullptr, *t_E = nullptr;
+  // sub-BDDs (Sec. 6): cuts of the variable order, copy-arc pairs and their duals
+  std::vector<int> cuts;
+  long long npairs = 0, ngroups = 0;
+  float gamma = 0.5f;
+  int split_depth = 0;
+  int4 *d_cut_grp = nullptr, *d_pair = nullptr;
+  int *d_head_node = nullptr, *d_head_ptr = nullptr, *d_head_pair = nullptr;
+  float *d_mu_bar = nullptr, *d_mu = nullptr, *d_dfwd = nullptr, *d_dbwd = nullptr;
   cudaEvent_t ev_last = nullptr;  // end of the solver's last enqueued work, on whatever stream
 
   ~bdd_solver() {
@@ -189,7 +198,34 @@ struct bdd_solver {
     p.error = d_error;
     p.spin_limit = spin_limit;
     p.inv_alpha = alpha > 0.f ? 1.f / alpha : 0.f;
+    p.copy_val = d_mu_bar;
+    p.split = npairs > 0 ? 1 : 0;
     return p;
+  }
+
+  CutParams cut_params() const {
+    CutParams c{};
+    c.grp = d_cut_grp;
+    c.pair = d_pair;
+    c.head_node = d_head_node;
+    c.head_ptr = d_head_ptr;
+    c.head_pair = d_head_pair;
+    c.mu_bar = d_mu_bar;
+    c.mu = d_mu;
+    c.dfwd = d_dfwd;
+    c.dbwd = d_dbwd;
+    c.fm = d_fm;
+    c.bm = d_bm;
+    c.lam = d_lam;
+    c.gamma = gamma;
+    c.ngroups = npairs > 0 ? (int)ngroups : 0;
+    return c;
+  }
+
+  // copy-arc dual step after a sweep (split solvers; nothing otherwise)
+  int cut(bool fwd, cudaStream_t s) {
+    if (npairs == 0) return BDD_OK;
+    return cut_launch(fwd, cut_params(), s) ? BDD_ECUDA : BDD_OK;
   }
 
   // parameters of the fused plan's update sweeps (bound: reduce the previous iteration's bound at
@@ -325,9 +361,11 @@ struct bdd_solver {
       return BDD_OK;
     }
     RC(sweep(true, kUpdate, s));
+    RC(cut(true, s));
     RC(pending(false, s));
     RC(sweep(false, kUpdate, s));
     RC(pending(true, s));
+    RC(cut(false, s));
     return BDD_OK;
   }
 
@@ -410,9 +448,18 @@ struct bdd_solver {
     return BDD_OK;
   }
 
-  // lambda^j_i = c_i/|J_i|, P = 0, then backward messages (and E^j) for that lambda
+  // lambda^j_i = c_i/|J_i|, P = 0, then backward messages (and E^j) for that lambda.  Split
+  // solvers: copy-arc duals and their last deltas 0, so every root message is 0.
   int restart(cudaStream_t s) {
     if (O > 0 && init_lambda_launch(d_occ_var, d_var_ptr, d_c, d_lam, (int)O, s)) return BDD_ECUDA;
+    if (npairs > 0) {
+      const size_t pb = sizeof(float) * (size_t)npairs;
+      CK(cudaMemsetAsync(d_mu_bar, 0, pb, s));
+      CK(cudaMemsetAsync(d_mu, 0, pb, s));
+      CK(cudaMemsetAsync(d_dfwd, 0, pb, s));
+      CK(cudaMemsetAsync(d_dbwd, 0, pb, s));
+      CK(cudaMemsetAsync(d_fm, 0, sizeof(float) * (size_t)std::max<long long>(N, 1), s));
+    }
     CK(cudaMemsetAsync(d_P, 0, sizeof(float) * std::max(n, 1), s));
     CK(cudaMemsetAsync(d_delta, 0, sizeof(float) * std::max<long long>(O, 1), s));
     CK(cudaMemsetAsync(d_share_occ, 0, sizeof(float) * std::max<long long>(O, 1), s));
@@ -444,6 +491,45 @@ struct bdd_solver {
 
 namespace {
 
+// Device tables of the copy-arc pairs (CutParams), from the canonical pairs and the slab layout.
+struct CutTables {
+  std::vector<int4> grp, pair;
+  std::vector<int> head_node, head_ptr, head_pair;
+};
+
+int build_cut_tables(const HostBDDs &H, const Layout &L, const CopyPairs &P, CutTables *T) {
+  const long long G = P.ngroups();
+  T->grp.resize(G);
+  T->pair.resize(P.npairs());
+  T->head_node.clear();
+  T->head_ptr.assign(1, 0);
+  T->head_pair.clear();
+  std::vector<int> cnt;
+  for (long long g = 0; g < G; ++g) {
+    const long long ot = P.tail_occ[g];
+    const int dt = L.occ_of_canon[ot], dh = L.occ_of_canon[ot + 1];
+    const int tail0 = L.occ_node_off[dt], head0 = L.occ_node_off[dh], w = H.occ_width[ot + 1];
+    const long long ps = P.cut_ptr[g], pe = P.cut_ptr[g + 1];
+    const long long hs = (long long)T->head_node.size();
+    if (hs + w > INT_MAX || pe > INT_MAX) return BDD_ETOOBIG;
+    T->grp[g] = make_int4((int)ps, (int)pe, (int)hs, (int)(hs + w));
+    cnt.assign(w, 0);
+    for (long long k = ps; k < pe; ++k) {
+      T->pair[k] = make_int4(tail0 + P.tail[k], head0 + P.head[k], dt, P.side[k]);
+      cnt[P.head[k]]++;
+    }
+    for (int t = 0; t < w; ++t) {
+      T->head_node.push_back(head0 + t);
+      T->head_ptr.push_back(T->head_ptr.back() + cnt[t]);
+    }
+    const size_t base = T->head_pair.size();
+    T->head_pair.resize(base + (size_t)(pe - ps));
+    std::vector<int> fill(T->head_ptr.end() - 1 - w, T->head_ptr.end() - 1);
+    for (long long k = ps; k < pe; ++k) T->head_pair[fill[P.head[k]]++] = (int)k;
+  }
+  return BDD_OK;
+}
+
 template <class Tp>
 int upload(bdd_solver *h, Tp **d, const std::vector<Tp> &v) {
   RC(h->alloc(d, (long long)v.size()));
@@ -451,7 +537,7 @@ int upload(bdd_solver *h, Tp **d, const std::vector<Tp> &v) {
   return BDD_OK;
 }
 
-int setup_device(bdd_solver *h, const Layout &L, const float *c) {
+int setup_device(bdd_solver *h, const Layout &L, const float *c, const CutTables &ct) {
   CK(cudaEventCreateWithFlags(&h->ev_last, cudaEventDisableTiming));
   h->bdd_perm = L.bdd_perm;
   h->tile_occ0 = L.tile_occ0;
@@ -510,7 +596,8 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
   const long long ntiles = (long long)L.tile_bdd0.size();
   long long need = (O + 1) * 4 + O * 4 + O * 8 + N * 8 + 2 * N * 4 + 2 * O * 4 + 3 * (long long)n * 4 +
                    nb * 8 + 3 * ntiles * 4 + (n + 1) * 4 + O * 4 + h->grid_reduce * 8 + 1024 * 8 +
-                   (h->averaging == 1 ? O : 0) + 4LL * (long long)(L.tile_win0.size() + L.win_node.size()) + (h->fused ? 12 * n + 8LL * (h->grid_sweep + h->grid_reduce) : 0);
+                   (h->averaging == 1 ? O : 0) + 4LL * (long long)(L.tile_win0.size() + L.win_node.size()) + (h->fused ? 12 * n + 8LL * (h->grid_sweep + h->grid_reduce) : 0) +
+                   h->npairs * 36 + 16 * h->ngroups + 8LL * (long long)ct.head_node.size();
   if (h->max_device_bytes > 0 && need > h->max_device_bytes) return BDD_ENOMEM;
 
   RC(upload(h, &h->d_occ_node_off, L.occ_node_off));
@@ -568,6 +655,17 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c) {
     RC(h->alloc(&h->d_fticket, 1));
     CK(cudaMemset(h->d_fticket, 0, sizeof(unsigned)));
   }
+  if (h->npairs > 0) {
+    RC(upload(h, &h->d_cut_grp, ct.grp));
+    RC(upload(h, &h->d_pair, ct.pair));
+    RC(upload(h, &h->d_head_node, ct.head_node));
+    RC(upload(h, &h->d_head_ptr, ct.head_ptr));
+    RC(upload(h, &h->d_head_pair, ct.head_pair));
+    RC(h->alloc(&h->d_mu_bar, h->npairs));
+    RC(h->alloc(&h->d_mu, h->npairs));
+    RC(h->alloc(&h->d_dfwd, h->npairs));
+    RC(h->alloc(&h->d_dbwd, h->npairs));
+  }
   RC(h->alloc(&h->d_partial, h->grid_reduce));
   RC(h->alloc(&h->d_ticket, 1));
   RC(h->alloc(&h->d_iter, 1));
@@ -623,6 +721,11 @@ void bdd_default_options(bdd_options *opt) {
   opt->averaging = 0;
   opt->fused_pending = -1;
   opt->staging = -1;
+  opt->split_intervals = 0;
+  opt->cuts = nullptr;
+  opt->n_cuts = 0;
+  opt->gamma = 0.5f;
+  opt->split_depth = 0;
 }
 
 int bdd_last_failed_row(void) { return g_failed_row; }
@@ -650,6 +753,11 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   if (opt.averaging < 0 || opt.averaging > 1) return BDD_EINVAL;
   if (opt.fused_pending < -1 || opt.fused_pending > 1) return BDD_EINVAL;
   if (opt.staging < -1 || opt.staging > 1) return BDD_EINVAL;
+  if (opt.split_intervals < 0 || opt.n_cuts < 0 || (opt.n_cuts > 0 && !opt.cuts) || opt.split_depth < 0)
+    return BDD_EINVAL;
+  if (!(opt.gamma > 0.f && opt.gamma <= 1.f)) return BDD_EINVAL;
+  const bool want_split = opt.split_depth > 0 || opt.n_cuts > 0 || opt.split_intervals >= 2;
+  if (want_split && opt.alpha > 0.f) return BDD_EINVAL;  // sub-BDDs run the min-sum iteration only
   if (opt.var_rank) {  // a permutation of 0..n-1
     std::vector<char> seen;
     try {
@@ -672,9 +780,11 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   h->omega = opt.omega;
   h->alpha = opt.alpha;
   h->averaging = opt.averaging;
-  h->fused_opt = opt.fused_pending;
+  h->fused_opt = want_split ? 0 : opt.fused_pending;  // the copy-arc steps follow whole sweeps
   h->staging_opt = h->fused_opt == 1 ? 0 : opt.staging;
-  h->schedule = opt.alpha > 0.f ? 1 : opt.schedule;  // the persistent kernel runs min-sum only
+  // the persistent kernel runs the plain min-sum iteration only
+  h->schedule = opt.alpha > 0.f || want_split ? 1 : opt.schedule;
+  h->gamma = opt.gamma;
   h->spin_limit = opt.spin_limit;
   if (opt.schedule < 0 || opt.schedule > 1 || opt.spin_limit < 1) {
     delete h;
@@ -700,6 +810,30 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
     return rc;
   }
   HostBDDs &H = h->host;
+  CopyPairs pairs;
+  if (want_split) {
+    std::vector<int> cuts;
+    if (opt.split_depth > 0) {
+      // depth split: no interval cuts
+    } else if (opt.n_cuts > 0) {
+      cuts.assign(opt.cuts, opt.cuts + opt.n_cuts);
+    } else {
+      cuts = balanced_cuts(H, opt.var_rank, opt.split_intervals);
+    }
+    h->split_depth = opt.split_depth;
+    try {
+      rc = split_bdds(H, opt.var_rank, cuts, opt.split_depth, &pairs);
+    } catch (const std::bad_alloc &) {
+      rc = BDD_ENOMEM;
+    }
+    if (rc != BDD_OK) {
+      delete h;
+      return rc;
+    }
+    h->cuts = pairs.cuts;
+    h->npairs = pairs.npairs();
+    h->ngroups = pairs.ngroups();
+  }
   h->nb = H.nb();
   h->O = H.O();
   h->N = H.N();
@@ -721,6 +855,14 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
     rc = BDD_ENOMEM;
   }
   if (rc == BDD_OK && h->alpha > 0.f && L.n_block_tiles > 0) rc = BDD_ETOOBIG;  // smoothing: warp tiles only
+  CutTables ct;
+  if (rc == BDD_OK && h->npairs > 0 && !h->host_layout) {
+    try {
+      rc = build_cut_tables(H, L, pairs, &ct);
+    } catch (const std::bad_alloc &) {
+      rc = BDD_ENOMEM;
+    }
+  }
   if (rc != BDD_OK) {
     delete h;
     return rc;
@@ -759,7 +901,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
       delete h;
       return BDD_ECUDA;
     }
-    rc = setup_device(h, L, c);
+    rc = setup_device(h, L, c, ct);
   }
   if (rc != BDD_OK) {
     delete h;
@@ -833,11 +975,13 @@ int bdd_iterate_profiled(bdd_solver *h, int n_iter, double *kernel_ms) {
       }
       if (rc == BDD_OK) rc = h->sweep(true, kUpdate, s);
       if (rc == BDD_OK && cudaEventRecord(e[1], s) != cudaSuccess) rc = BDD_ECUDA;
+      if (rc == BDD_OK) rc = h->cut(true, s);
       if (rc == BDD_OK) rc = h->pending(false, s);
       if (rc == BDD_OK && cudaEventRecord(e[2], s) != cudaSuccess) rc = BDD_ECUDA;
       if (rc == BDD_OK) rc = h->sweep(false, kUpdate, s);
       if (rc == BDD_OK && cudaEventRecord(e[3], s) != cudaSuccess) rc = BDD_ECUDA;
       if (rc == BDD_OK) rc = h->pending(true, s);
+      if (rc == BDD_OK) rc = h->cut(false, s);
       if (rc == BDD_OK && cudaEventRecord(e[4], s) != cudaSuccess) rc = BDD_ECUDA;
     }
     if (rc == BDD_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = BDD_ECUDA;
@@ -1040,6 +1184,53 @@ int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]) {
   out[10] = h->n_block_tiles;
   out[11] = h->schedule;
   out[12] = h->stage_fwd | (h->stage_bwd << 1);
+  out[13] = (long long)h->cuts.size();
+  out[14] = h->npairs;
+  out[15] = h->split_depth;
+  return BDD_OK;
+}
+
+int bdd_get_cuts(const bdd_solver *h, int *cuts) {
+  if (!h || (!h->cuts.empty() && !cuts)) return BDD_EINVAL;
+  std::copy(h->cuts.begin(), h->cuts.end(), cuts);
+  return BDD_OK;
+}
+
+int bdd_get_copy_duals(const bdd_solver *h_in, float *mu_bar, float *mu) {
+  bdd_solver *h = const_cast<bdd_solver *>(h_in);
+  if (!h) return BDD_EINVAL;
+  if (h->host_only) return BDD_ESTATE;
+  if (h->npairs == 0) return BDD_OK;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return BDD_ECUDA;
+  cudaStream_t s = h->stream;
+  const size_t pb = sizeof(float) * (size_t)h->npairs;
+  RC(h->begin(s));
+  if (mu_bar) CK(cudaMemcpyAsync(mu_bar, h->d_mu_bar, pb, cudaMemcpyDeviceToHost, s));
+  if (mu) CK(cudaMemcpyAsync(mu, h->d_mu, pb, cudaMemcpyDeviceToHost, s));
+  RC(h->end(s));
+  CK(cudaStreamSynchronize(s));
+  return BDD_OK;
+}
+
+int bdd_set_copy_duals(bdd_solver *h, const float *mu_bar, const float *mu) {
+  if (!h || (h->npairs > 0 && (!mu_bar || !mu))) return BDD_EINVAL;
+  if (h->host_only) return BDD_ESTATE;
+  if (h->npairs == 0) return BDD_OK;
+  for (long long k = 0; k < h->npairs; ++k)
+    if (!std::isfinite(mu_bar[k]) || !std::isfinite(mu[k])) return BDD_EINVAL;
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return BDD_ECUDA;
+  cudaStream_t s = h->stream;
+  const size_t pb = sizeof(float) * (size_t)h->npairs;
+  RC(h->begin(s));
+  ++h->state_gen;
+  CK(cudaMemcpyAsync(h->d_mu_bar, mu_bar, pb, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->d_mu, mu, pb, cudaMemcpyHostToDevice, s));
+  if (cut_roots_launch(h->cut_params(), s)) return BDD_ECUDA;
+  RC(h->sweep(false, kMessages, s));
+  RC(h->end(s));
+  CK(cudaStreamSynchronize(s));
   return BDD_OK;
 }
 
@@ -1167,6 +1358,7 @@ int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending) {
 int bdd_bound_parts(bdd_solver *h, int nparts, const long long *row_off, const long long *var_off, double *out) {
   if (!h || nparts < 1 || !row_off || !var_off || !out) return BDD_EINVAL;
   if (h->host_only) return BDD_ESTATE;
+  if (h->npairs > 0) return BDD_EINVAL;  // pieces of one row would share its energy slot
   if (row_off[0] != 0 || var_off[0] != 0 || row_off[nparts] != h->m || var_off[nparts] != h->n) return BDD_EINVAL;
   for (int k = 0; k < nparts; ++k)
     if (row_off[k + 1] < row_off[k] || var_off[k + 1] < var_off[k]) return BDD_EINVAL;

@@ -15,6 +15,12 @@
 //
 // build_layout: turns the canonical BDDs into the tile-grouped, layer-major slabs the sweep
 // kernels read.
+//
+// split_bdds: sub-BDDs (Sec. 6, Def. of sub-BDDs): a BDD whose consecutive layers lie in
+// different intervals of the variable order is cut there; each piece becomes a BDD of its own
+// (several roots when it starts below the original root), and the arcs leaving the last layer
+// before a cut go into the top terminal as copy arcs.  The pieces keep the row's occurrences, so
+// the slab layout, the slots and the outputs need no change.
 #include <algorithm>
 #include <atomic>
 #include <climits>
@@ -370,6 +376,93 @@ int build_layout(const HostBDDs &H, Layout *L) {
       L->slot_dir[k] = (unsigned char)((co + 1 < H.bdd_occ0[b + 1] ? kDirForward : 0) |
                                        (co > H.bdd_occ0[b] ? kDirBackward : 0));
     }
+  return BDD_OK;
+}
+
+std::vector<int> balanced_cuts(const HostBDDs &H, const int *rank, int k) {
+  std::vector<int> cuts;
+  const int n = H.n;
+  const long long N = H.N();
+  if (k < 2 || n < 2 || N == 0) return cuts;
+  std::vector<long long> at(n, 0);  // nodes of the layers of the variable at each place
+  for (long long o = 0; o < H.O(); ++o) {
+    const int i = H.occ_var[o];
+    at[rank ? rank[i] : i] += H.occ_width[o];
+  }
+  long long acc = 0;  // nodes at places before p
+  int t = 1;          // next interval boundary to place, at about t * N / k nodes
+  for (int p = 1; p < n && t < k; ++p) {
+    acc += at[p - 1];
+    if (acc * k >= (long long)t * N) {
+      cuts.push_back(p);
+      while (t < k && acc * k >= (long long)t * N) ++t;
+    }
+  }
+  return cuts;
+}
+
+int split_bdds(HostBDDs &H, const int *rank, const std::vector<int> &cuts, int depth, CopyPairs *P) {
+  const int n = H.n;
+  if (depth < 0 || (depth > 0 && !cuts.empty())) return BDD_EINVAL;
+  for (size_t t = 0; t < cuts.size(); ++t)
+    if (cuts[t] < 1 || cuts[t] >= n || (t > 0 && cuts[t] <= cuts[t - 1])) return BDD_EINVAL;
+  P->cuts = cuts;
+  P->cut_ptr.assign(1, 0);
+  P->tail_occ.clear();
+  P->tail.clear();
+  P->side.clear();
+  P->head.clear();
+  if (cuts.empty() && depth == 0) return BDD_OK;
+  // interval of every variable: the number of cuts at or before its place
+  std::vector<int> interval(depth > 0 ? 0 : n);
+  for (int i = 0; i < (int)interval.size(); ++i) {
+    const int place = rank ? rank[i] : i;
+    interval[i] = (int)(std::upper_bound(cuts.begin(), cuts.end(), place) - cuts.begin());
+  }
+  std::vector<char> cut_at;  // depth split: cut before layer l of the current BDD
+  std::vector<int> row, pdepth;
+  std::vector<long long> occ0;
+  const long long nb = H.nb();
+  for (long long b = 0; b < nb; ++b) {
+    const long long o0 = H.bdd_occ0[b];
+    const int k = H.bdd_depth[b];
+    if (depth > 0) {
+      const int q = (k + depth - 1) / depth;
+      cut_at.assign(k + 1, 0);
+      for (int t = 1; t < q; ++t) cut_at[(long long)t * k / q] = 1;
+    }
+    int start = 0;
+    for (int l = 1; l <= k; ++l) {
+      if (l < k && !(depth > 0 ? cut_at[l] != 0 : interval[H.occ_var[o0 + l]] != interval[H.occ_var[o0 + l - 1]]))
+        continue;
+      row.push_back(H.bdd_row[b]);
+      pdepth.push_back(l - start);
+      occ0.push_back(o0 + start);
+      if (l < k) {  // cut between layers l - 1 and l: every arc between them becomes a pair
+        const long long ot = o0 + l - 1;
+        P->tail_occ.push_back(ot);
+        for (int u = 0; u < H.occ_width[ot]; ++u)
+          for (int side = 0; side < 2; ++side) {
+            int &t = side ? H.hi[H.occ_node0[ot] + u] : H.lo[H.occ_node0[ot] + u];
+            if (t < 0) continue;  // an arc into bot stays one (Def. of sub-BDDs)
+            const long long pk = P->npairs();
+            if (pk > (long long)INT_MAX + kCopy0) return BDD_ETOOBIG;
+            P->tail.push_back(u);
+            P->side.push_back(side);
+            P->head.push_back(t);
+            t = kCopy0 - (int)pk;
+          }
+        P->cut_ptr.push_back(P->npairs());
+      }
+      start = l;
+    }
+  }
+  occ0.push_back(H.O());
+  H.bdd_row = std::move(row);
+  H.bdd_depth = std::move(pdepth);
+  H.bdd_occ0 = std::move(occ0);
+  H.max_depth = 0;
+  for (int d : H.bdd_depth) H.max_depth = std::max(H.max_depth, d);
   return BDD_OK;
 }
 

@@ -12,6 +12,9 @@ namespace bdd {
 constexpr int kTop = -1;   // arc into the true terminal
 constexpr int kBot = -2;   // arc into the false terminal
 constexpr int kNone = -3;  // no arc (lane without a node)
+// Sub-BDDs (Sec. 6): an arc that crosses a cut ends in the top terminal as the copy arc of
+// copy-arc pair k, encoded as kCopy0 - k; its backward message is the pair's dual mu_bar.
+constexpr int kCopy0 = -4;
 
 // Canonical host form of all BDDs (Sec. 5.1, Def. 4): BDDs in ascending row order;
 // occurrences (row j, variable i) BDD-major, layer-minor; nodes BDD-major, layer-major,
@@ -31,6 +34,32 @@ struct HostBDDs {
   long long O() const { return (long long)occ_var.size(); }
   long long N() const { return (long long)lo.size(); }
 };
+
+// Copy-arc pairs of a split (Sec. 6, Def. of sub-BDDs and copy-arcs), in canonical order: cuts
+// of BDD 0 by ascending layer, then BDD 1, ...; inside a cut, tails in node order, the 0-arc
+// before the 1-arc.  Pair k joins the copy arc (tail node of the earlier piece's last layer, into
+// top) with the arc entering the head node of the later piece's first layer.
+struct CopyPairs {
+  std::vector<int> cuts;            // places in the variable order where intervals 2.. start
+  std::vector<long long> cut_ptr;   // [groups + 1] pairs of each cut of a BDD
+  std::vector<long long> tail_occ;  // [groups] canonical occurrence of the tails' layer
+  std::vector<int> tail, side;      // [pairs] tail node id inside that layer; 0-arc / 1-arc
+  std::vector<int> head;            // [pairs] head node id inside the next layer
+  long long npairs() const { return (long long)tail.size(); }
+  long long ngroups() const { return (long long)tail_occ.size(); }
+};
+
+// k - 1 cut places that give every interval of the variable order about N / k nodes (a node
+// counts for the interval of its layer's variable; Sec. 6 chooses the interval endpoints so).
+std::vector<int> balanced_cuts(const HostBDDs &H, const int *rank, int k);
+
+// Splits every BDD of H in place into its sub-BDDs: with depth == 0 at the interval boundaries
+// `cuts` (ascending places in [1, n); rank: the variable order, null = index order), with
+// depth D > 0 into pieces of at most D layers (a BDD of k layers is cut before layers
+// floor(t k / q), t = 1 .. q-1, q = ceil(k / D)).  Each piece becomes a BDD of its own (bdd_row
+// keeps the row); the arcs of the last layer before a cut become copy codes kCopy0 - k.
+// Returns a BDD_* status.
+int split_bdds(HostBDDs &H, const int *rank, const std::vector<int> &cuts, int depth, CopyPairs *P);
 
 // Compiles every row (threshold counting over suffix-sum sets; see compile.cpp).
 // Returns a BDD_* status; *failed_row is the row that failed, or -1.
@@ -172,6 +201,9 @@ struct SweepParams {
   float omega;
   float alpha;          // smoothing temperature (0: min-sum)
   float inv_alpha;
+  const float *copy_val; // sub-BDDs: mu_bar of every copy-arc pair (backward message of kCopy0 - k)
+  int split;             // sub-BDDs: layer-0 forward messages are the root messages held in fm, and
+                         // E^j is the minimum over the first layer of fm + bm
   int *error;            // set to BDD_ETIMEOUT if a bounded wait on a shared-memory copy gives up
   long long spin_limit;  // polls of such a wait: spin_limit / 64 (at least 1)
   FusedParams fz;       // fz.cnt == null outside the fused plan
@@ -259,6 +291,28 @@ int bound_seed_launch(const int *var_ptr, const float *P, const float *c, float 
                       float alpha, const double *g_bound, cudaStream_t stream);
 int initial_adjoint_launch(const int *var_ptr, const int *var_occ, const float *g_lam0, float *g_c, int n,
                            cudaStream_t stream);
+
+// Copy-arc dual updates of a split solver (Sec. 6, parallel min-marginal averaging), one warp per
+// cut of a BDD.  After a forward sweep: m_k = fm(tail) + theta(tail arc) + mu_bar_k, d_fwd =
+// m_k - min over the cut, mu_bar_k += -gamma d_fwd + gamma d_bwd.  After a backward sweep:
+// m_k = mu_k + bm(head), d_bwd likewise, mu_k += -gamma d_bwd + gamma d_fwd, then every head
+// node's root message (in fm) = min of mu over the pairs entering it.
+struct CutParams {
+  const int4 *grp;        // [ngroups] {first pair, end pair, first head, end head}
+  const int4 *pair;       // [npairs] {tail node, head node, tail occurrence, side}
+  const int *head_node;   // [heads] device node of each head
+  const int *head_ptr;    // [heads + 1] pairs entering each head ...
+  const int *head_pair;   // ... listed here
+  float *mu_bar, *mu, *dfwd, *dbwd;  // [npairs]
+  float *fm;
+  const float *bm;
+  const float *lam;
+  float gamma;
+  int ngroups;
+};
+int cut_launch(bool forward, const CutParams &c, cudaStream_t stream);
+// root messages only (after the duals were set): fm(head) = min of mu over its pairs
+int cut_roots_launch(const CutParams &c, cudaStream_t stream);
 
 // Launch wrappers (kernels.cu).  All enqueue on `stream` and return 0 or -5 (launch failure).
 size_t sweep_smem_bytes(int block_buf, int block_depth_buf);

@@ -28,16 +28,21 @@ namespace bdd {
 
 namespace {
 
-// backward message of an arc target: top -> 0, bot / none -> +inf, node -> bm
-__device__ __forceinline__ float target_bm(const float *__restrict__ bm, int t) {
-  if (t >= 0) return bm[t];
-  return t == kTop ? 0.f : inf();
+// backward message of a terminal arc target t < 0: top -> 0, bot / none -> +inf; the copy arc of
+// pair k (t = kCopy0 - k, sub-BDDs of Sec. 6) enters top at cost mu_bar_k
+__device__ __forceinline__ float terminal_bm(const float *__restrict__ copy_val, int t) {
+  if (t == kTop) return 0.f;
+  return t > kCopy0 ? inf() : copy_val[kCopy0 - t];
+}
+
+// backward message of an arc target: node -> bm, else the terminal's
+__device__ __forceinline__ float target_bm(const float *__restrict__ bm, const float *__restrict__ copy_val, int t) {
+  return t >= 0 ? bm[t] : terminal_bm(copy_val, t);
 }
 
 // backward message of an arc target staged at msg[t - base]
-__device__ __forceinline__ float staged_bm(const float *msg, int base, int t) {
-  if (t >= 0) return msg[t - base];
-  return t == kTop ? 0.f : inf();
+__device__ __forceinline__ float staged_bm(const float *msg, const float *__restrict__ copy_val, int base, int t) {
+  return t >= 0 ? msg[t - base] : terminal_bm(copy_val, t);
 }
 
 // atomic minimum on a float in shared memory (non-negative floats order like their int bits,
@@ -497,8 +502,8 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
       const bool has = active && tl < w_l;
       // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv
       float f;
-      if (l == 0) {
-        f = 0.f;
+      if (l == 0) {  // the root, or a piece's roots with their root messages (sub-BDDs)
+        f = p.split && has ? p.fm[node0 + tl] : 0.f;
       } else {
         const int lo_l = lh_prev.x >= 0 ? lh_prev.x - node0 : kNone;
         const int hi_l = lh_prev.y >= 0 ? lh_prev.y - node0 : kNone;
@@ -520,8 +525,8 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
       float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
       if (is_update(MODE)) {
         // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
-        const float a0 = has ? f + staged_bm(msg, na, lh.x) : inf();
-        const float a1 = has ? f + lam + staged_bm(msg, na, lh.y) : inf();
+        const float a0 = has ? f + staged_bm(msg, p.copy_val, na, lh.x) : inf();
+        const float a1 = has ? f + lam + staged_bm(msg, p.copy_val, na, lh.y) : inf();
         const float m0 = team_agg<T, SMOOTH>(a0, p), m1 = team_agg<T, SMOOTH>(a1, p);
         const float dd = p.omega * mm_difference(m0, m1);
         lam -= dd;
@@ -604,8 +609,8 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
       const int s1 = lh.y >= 0 ? lh.y - node0_next : 0;
       const float g0 = __shfl_sync(kFull, b_next, tbase + (s0 & (T - 1)));
       const float g1 = __shfl_sync(kFull, b_next, tbase + (s1 & (T - 1)));
-      const float b0 = lh.x >= 0 ? g0 : (lh.x == kTop ? 0.f : inf());
-      const float b1 = lh.y >= 0 ? g1 : (lh.y == kTop ? 0.f : inf());
+      const float b0 = lh.x >= 0 ? g0 : terminal_bm(p.copy_val, lh.x);
+      const float b1 = lh.y >= 0 ? g1 : terminal_bm(p.copy_val, lh.y);
       if (MODE != kMessages) {
         const float m0 = team_agg<T, SMOOTH>(f + b0, p), m1 = team_agg<T, SMOOTH>(f + lam + b1, p);
         if (is_update(MODE)) {
@@ -624,9 +629,12 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
       // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
       const float bcur = agg<SMOOTH>(b0, lam + b1, p);
       if (has) p.bm[node0 + tl] = bcur;
-      if (l == 0 && active && tl == 0) {  // E^j(lambda^j) at the root
-        p.bdd_E[bdd] = bcur;
-        bacc += (double)bcur;
+      if (l == 0) {  // E^j(lambda^j) at the root; a piece: min over its roots of fm + bm
+        const float e = p.split ? team_agg<T, SMOOTH>(has ? f + bcur : inf(), p) : bcur;
+        if (active && tl == 0) {
+          p.bdd_E[bdd] = e;
+          bacc += (double)e;
+        }
       }
       b_next = bcur;
       node0_next = node0;
@@ -708,8 +716,8 @@ __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phas
       const bool has = active && tl < w;
       // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv
       float f;
-      if (l == 0) {
-        f = 0.f;
+      if (l == 0) {  // the root, or a piece's roots with their root messages (sub-BDDs)
+        f = p.split && has ? p.fm[node0 + tl] : 0.f;
       } else {
         const int lo_l = lh_prev.x >= 0 ? lh_prev.x - node0 : kNone;
         const int hi_l = lh_prev.y >= 0 ? lh_prev.y - node0 : kNone;
@@ -731,8 +739,8 @@ __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phas
       float lam = active ? S.lam[oi] + S.shr[oi] : 0.f;
       if (is_update(MODE)) {
         // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
-        const float a0 = has ? f + staged_bm(S.msg, na, lh.x) : inf();
-        const float a1 = has ? f + lam + staged_bm(S.msg, na, lh.y) : inf();
+        const float a0 = has ? f + staged_bm(S.msg, p.copy_val, na, lh.x) : inf();
+        const float a1 = has ? f + lam + staged_bm(S.msg, p.copy_val, na, lh.y) : inf();
         const float m0 = team_agg<T, SMOOTH>(a0, p), m1 = team_agg<T, SMOOTH>(a1, p);
         const float dd = p.omega * mm_difference(m0, m1);
         lam -= dd;
@@ -797,8 +805,8 @@ __device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Pha
       const int s1 = lh.y >= 0 ? lh.y - node0_next : 0;
       const float g0 = __shfl_sync(kFull, b_next, tbase + (s0 & (T - 1)));
       const float g1 = __shfl_sync(kFull, b_next, tbase + (s1 & (T - 1)));
-      const float b0 = lh.x >= 0 ? g0 : (lh.x == kTop ? 0.f : inf());
-      const float b1 = lh.y >= 0 ? g1 : (lh.y == kTop ? 0.f : inf());
+      const float b0 = lh.x >= 0 ? g0 : terminal_bm(p.copy_val, lh.x);
+      const float b1 = lh.y >= 0 ? g1 : terminal_bm(p.copy_val, lh.y);
       if (MODE != kMessages) {
         const float m0 = team_agg<T, SMOOTH>(f + b0, p), m1 = team_agg<T, SMOOTH>(f + lam + b1, p);
         if (is_update(MODE)) {
@@ -817,9 +825,12 @@ __device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Pha
       // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
       const float bcur = agg<SMOOTH>(b0, lam + b1, p);
       if (has) p.bm[node0 + tl] = bcur;
-      if (l == 0 && active && tl == 0) {  // E^j(lambda^j) at the root
-        p.bdd_E[bdd] = bcur;
-        bacc += (double)bcur;
+      if (l == 0) {  // E^j(lambda^j) at the root; a piece: min over its roots of fm + bm
+        const float e = p.split ? team_agg<T, SMOOTH>(has ? f + bcur : inf(), p) : bcur;
+        if (active && tl == 0) {
+          p.bdd_E[bdd] = e;
+          bacc += (double)e;
+        }
       }
       b_next = bcur;
       node0_next = node0;
@@ -888,7 +899,12 @@ __device__ __forceinline__ void block_forward(const SweepParams &p, const Phase 
   const int depth = p.bdd_depth[bdd];
   float *cur = g.bufA, *nxt = g.bufB;
   stage_group_shares<MODE>(p, occ0, depth, g.shr, gt);
-  if (gt == 0) cur[0] = 0.f;
+  if (p.split) {  // a piece's roots start from their root messages
+    const int n0 = p.occ_node_off[occ0], w0 = p.occ_node_off[occ0 + 1] - n0;
+    for (int t = gt; t < w0; t += kBlockThreads) cur[t] = p.fm[n0 + t];
+  } else if (gt == 0) {
+    cur[0] = 0.f;
+  }
   group_sync(group);
   for (int l = 0; l < depth; ++l) {
     const int o = occ0 + l;
@@ -900,8 +916,8 @@ __device__ __forceinline__ void block_forward(const SweepParams &p, const Phase 
       p.fm[node0 + t] = f;
       if (is_update(MODE)) {
         const int2 lh = p.lohi[node0 + t];
-        a0 = fminf(a0, f + target_bm(p.bm, lh.x));
-        a1 = fminf(a1, f + lam + target_bm(p.bm, lh.y));
+        a0 = fminf(a0, f + target_bm(p.bm, p.copy_val, lh.x));
+        a1 = fminf(a1, f + lam + target_bm(p.bm, p.copy_val, lh.y));
       }
     }
     if (is_update(MODE)) {
@@ -950,8 +966,8 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
       for (int t = gt; t < w; t += kBlockThreads) {
         const int2 lh = p.lohi[node0 + t];
         const float f = p.fm[node0 + t];
-        const float b0 = lh.x >= 0 ? cur[lh.x - next0] : (lh.x == kTop ? 0.f : inf());
-        const float b1 = lh.y >= 0 ? cur[lh.y - next0] : (lh.y == kTop ? 0.f : inf());
+        const float b0 = lh.x >= 0 ? cur[lh.x - next0] : terminal_bm(p.copy_val, lh.x);
+        const float b1 = lh.y >= 0 ? cur[lh.y - next0] : terminal_bm(p.copy_val, lh.y);
         a0 = fminf(a0, f + b0);
         a1 = fminf(a1, f + lam + b1);
       }
@@ -969,16 +985,28 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
         p.out_m1[c] = mm.y;
       }
     }
+    float e = inf();  // a piece's energy: min over its roots of fm + bm
     for (int t = gt; t < w; t += kBlockThreads) {
       const int2 lh = p.lohi[node0 + t];
-      const float b0 = lh.x >= 0 ? cur[lh.x - next0] : (lh.x == kTop ? 0.f : inf());
-      const float b1 = lh.y >= 0 ? cur[lh.y - next0] : (lh.y == kTop ? 0.f : inf());
+      const float b0 = lh.x >= 0 ? cur[lh.x - next0] : terminal_bm(p.copy_val, lh.x);
+      const float b1 = lh.y >= 0 ? cur[lh.y - next0] : terminal_bm(p.copy_val, lh.y);
       const float bcur = fminf(b0, lam + b1);
       p.bm[node0 + t] = bcur;
       nxt[t] = bcur;
-      if (l == 0 && t == 0) {
-        p.bdd_E[bdd] = bcur;
-        bacc += (double)bcur;
+      if (l == 0) {
+        if (p.split) {
+          e = fminf(e, p.fm[node0 + t] + bcur);
+        } else if (t == 0) {
+          p.bdd_E[bdd] = bcur;
+          bacc += (double)bcur;
+        }
+      }
+    }
+    if (l == 0 && p.split) {
+      e = group_min2(e, inf(), g.red, group, gt).x;
+      if (gt == 0) {
+        p.bdd_E[bdd] = e;
+        bacc += (double)e;
       }
     }
     group_sync(group);
@@ -1310,6 +1338,64 @@ __global__ void __launch_bounds__(kPersistThreads, 1) iterate_kernel(const IterP
 }
 
 // ---------------------------------------------------------------------------------------
+// copy-arc pairs of sub-BDDs (Sec. 6, parallel min-marginal averaging)
+// ---------------------------------------------------------------------------------------
+// arc-marginal of pair k's copy arc after a forward sweep (the best path of the earlier piece
+// through it: fm(tail) + theta + mu_bar) or of its entry arc after a backward sweep (the best path
+// of the later piece entering through it: mu + bm(head); the entry arc carries no theta, which
+// stays with the copy arc's layer)
+template <bool FWD>
+__device__ __forceinline__ float cut_marginal(const CutParams &c, int k) {
+  const int4 q = c.pair[k];
+  if (FWD) return c.fm[q.x] + (q.w ? c.lam[q.z] : 0.f) + c.mu_bar[k];
+  return c.mu[k] + c.bm[q.y];
+}
+
+// root messages of a cut's heads: min of mu over the pairs entering each head
+__device__ __forceinline__ void cut_roots(const CutParams &c, int4 G, int lane) {
+  for (int h = G.z + lane; h < G.w; h += 32) {
+    float r = inf();
+    for (int q = c.head_ptr[h]; q < c.head_ptr[h + 1]; ++q) r = fminf(r, c.mu[c.head_pair[q]]);
+    c.fm[c.head_node[h]] = r;
+  }
+}
+
+// one warp per cut of a BDD: delta = marginal - its minimum over the cut (0 where either is
+// +inf), then the gamma-damped dual step, each dual offsetting the other side's last delta
+template <bool FWD>
+__global__ void __launch_bounds__(kBlockThreads) cut_kernel(const CutParams c) {
+  pdl_wait();
+  const int lane = threadIdx.x & 31;
+  const int g = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (g >= c.ngroups) return;
+  const int4 G = c.grp[g];
+  float mn = inf();
+  for (int k = G.x + lane; k < G.y; k += 32) mn = fminf(mn, cut_marginal<FWD>(c, k));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mn = fminf(mn, __shfl_xor_sync(kFull, mn, off));
+  for (int k = G.x + lane; k < G.y; k += 32) {
+    const float m = cut_marginal<FWD>(c, k);
+    const float d = (m < inf() && mn < inf()) ? m - mn : 0.f;
+    if (FWD) {
+      c.dfwd[k] = d;
+      c.mu_bar[k] += -c.gamma * d + c.gamma * c.dbwd[k];
+    } else {
+      c.dbwd[k] = d;
+      c.mu[k] += -c.gamma * d + c.gamma * c.dfwd[k];
+    }
+  }
+  if (!FWD) {
+    __syncwarp();  // the cut's new mu, written by all lanes, before the root messages read them
+    cut_roots(c, G, lane);
+  }
+}
+
+__global__ void __launch_bounds__(kBlockThreads) cut_roots_kernel(const CutParams c) {
+  const int g = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  if (g < c.ngroups) cut_roots(c, c.grp[g], threadIdx.x & 31);
+}
+
+// ---------------------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------------------
 // lambda^j_i = c_i / |J_i| (Alg. 1 initialisation)
@@ -1524,6 +1610,20 @@ int part_bounds_launch(const float *bdd_E, const int *bdd_row, int nb, float *E_
 int gather_lambda_launch(const float *in, const long long *occ_csr, float *lam, int O, cudaStream_t stream) {
   if (O == 0) return 0;
   gather_lambda_kernel<<<grid_for(O, 256), 256, 0, stream>>>(in, occ_csr, lam, O);
+  return status();
+}
+
+int cut_launch(bool forward, const CutParams &c, cudaStream_t stream) {
+  if (c.ngroups <= 0) return 0;
+  const int grid = (c.ngroups + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int rc = forward ? launch_pdl(cut_kernel<true>, grid, kBlockThreads, 0, stream, c)
+                         : launch_pdl(cut_kernel<false>, grid, kBlockThreads, 0, stream, c);
+  return rc ? rc : status();
+}
+
+int cut_roots_launch(const CutParams &c, cudaStream_t stream) {
+  if (c.ngroups <= 0) return 0;
+  cut_roots_kernel<<<(c.ngroups + kWarpsPerBlock - 1) / kWarpsPerBlock, kBlockThreads, 0, stream>>>(c);
   return status();
 }
 

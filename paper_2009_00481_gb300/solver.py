@@ -16,13 +16,16 @@ class Solver:
     ``include/bdd_dbca.h``).  ``omega`` damps the min-marginal difference; ``alpha > 0`` selects
     the smoothed (log-sum-exp) variant.  ``rank`` (a permutation of 0..n-1, or "cm" for
     :func:`cuthill_mckee`) sets the variable order of the BDD layers; ``averaging`` 1 selects
-    SRMP averaging instead of eq. mma-update.
+    SRMP averaging instead of eq. mma-update.  ``split`` (an interval count k >= 2) or ``cuts``
+    (explicit cut places) splits the BDDs into sub-BDDs with copy-arc duals (Sec. 6), step size
+    ``gamma``; ``split_depth`` D >= 1 instead cuts every BDD into pieces of at most D layers.
     """
 
     def __init__(self, inst, omega: float = 0.5, host_only: bool = False, max_device_bytes: int = 0,
                  device: int = -1, stream: int = 0, schedule: int = 1, spin_limit: int = 0,
                  alpha: float = 0.0, rank=None, averaging: int = 0, fused_pending: int = -1,
-                 staging: int = -1):
+                 staging: int = -1, split: int = 0, cuts=None, gamma: float = 0.5,
+                 split_depth: int = 0):
         import numpy as np
         opt = B.bdd_default_options()
         if isinstance(rank, str):
@@ -34,6 +37,13 @@ class Solver:
             if self.rank.shape != (inst.n,):
                 raise ValueError("rank must have one entry per variable")
             opt.var_rank = self.rank.ctypes.data_as(B.C.POINTER(B.C.c_int))
+        self._cuts = None if cuts is None else np.ascontiguousarray(cuts, np.int32)
+        if self._cuts is not None and len(self._cuts):
+            opt.cuts = self._cuts.ctypes.data_as(B.C.POINTER(B.C.c_int))
+            opt.n_cuts = len(self._cuts)
+        opt.split_intervals = int(split)
+        opt.gamma = float(gamma)
+        opt.split_depth = int(split_depth)
         opt.averaging = int(averaging)
         opt.fused_pending = int(fused_pending)
         opt.staging = int(staging)
@@ -50,7 +60,8 @@ class Solver:
                              inst.c, opt)
         s = B.bdd_sizes(self.h)
         (self.n, self.m, self.nb, self.O, self.N, self.max_depth, self.max_width, self.nnz,
-         self.device_bytes, self.warp_tiles, self.block_tiles, self.schedule, self.staging) = map(int, s)
+         self.device_bytes, self.warp_tiles, self.block_tiles, self.schedule, self.staging,
+         self.n_cuts, self.npairs, self.split_depth) = map(int, s)
 
     def close(self):
         if getattr(self, "h", None):
@@ -98,6 +109,17 @@ class Solver:
 
     def set_costs(self, c):
         B.bdd_set_costs(self.h, c)
+
+    def cuts(self):
+        """Cut places of the variable order (split solvers; empty otherwise)."""
+        return B.bdd_get_cuts(self.h)
+
+    def copy_duals(self):
+        """(mu_bar, mu) of the copy-arc pairs (split solvers), canonical pair order."""
+        return B.bdd_get_copy_duals(self.h)
+
+    def set_copy_duals(self, mu_bar, mu):
+        B.bdd_set_copy_duals(self.h, mu_bar, mu)
 
 
 def cuthill_mckee(inst):

@@ -1,0 +1,254 @@
+"""GPU parity of sub-BDDs with copy-arc duals (Sec. 6: sub-BDDs, copy-arcs, the parallel
+min-marginal averaging algorithm, Prop. 4): the CUDA library through its C ABI against the FP64
+oracle's split of the same instance at the same cut places.
+
+Tolerances as in the unsplit parity tests (relative with a floor of 1): pieces read back from
+the device bit-exact; min-marginals and energies of the pieces for the same FP32 multipliers
+and copy duals 1e-5; bound traces of the deferred schedule with the copy-arc steps 1e-4; the
+device bound never drops by more than 1e-5 * |bound|.
+
+Undamped copy-arc steps (gamma = 1) equalise the marginals of a cut after every step, so later
+minima over the cut are decided by rounding and the iteration becomes sensitive to it: on the
+24x24 tomography pieces of 8 layers, relative cost perturbations of 1e-7 move the FP64 oracle's
+own bound after 100 iterations by ~5e-4 (by ~3e-8 at gamma = 0.5).  The bound tolerance after
+many iterations is therefore the larger of 1e-4 and four times the oracle's spread under
+perturbations of the costs by FP32 rounding (2^-24 relative)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from instances import config, random_ilp, sparse_matching, tomography, tracking
+from oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+MM_TOL = 1e-5
+LB_TOL = 1e-4
+MONO_TOL = 1e-5
+KEYS = ["bdd_row", "bdd_depth", "occ_var", "occ_csr", "occ_width", "lo", "hi"]
+
+
+def close(a, b, tol):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    assert np.array_equal(np.isfinite(a), np.isfinite(b)), "infinite entries differ"
+    fin = np.isfinite(a)
+    err = np.abs(a[fin] - b[fin]) / np.maximum(1.0, np.maximum(np.abs(a[fin]), np.abs(b[fin])))
+    assert err.size == 0 or err.max() <= tol, f"max rel err {err.max():.3e} > {tol:.1e}"
+
+
+@pytest.fixture(scope="module")
+def lib(cuda_lib):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return cuda_lib
+
+
+def solver(inst, **kw):
+    from paper_2009_00481_gb300 import Solver
+    return Solver(inst, **kw)
+
+
+def _trace(s, iters):
+    import torch
+    tr = torch.zeros(iters, dtype=torch.float64, device="cuda")
+    s.iterate_device(iters, trace=tr)
+    torch.cuda.synchronize()
+    return tr.cpu().numpy()
+
+
+# name -> (instance, number of intervals, depth limit of the depth split); the tomography case
+# has layers wider than 32 nodes (block tiles), the others run in warp tiles
+CASES = {
+    "potts_20x20x3": (lambda: config(0), 4, 2),
+    "matching_small": (lambda: sparse_matching(n_left=60, n_right=50, k=6, n_pairs=800, seed=3), 4, 3),
+    "tomography_24": (lambda: tomography(side=24, seed=2, unary_sigma=0.05), 3, 8),
+    "tracking_10x40": (lambda: tracking(frames=10, dets=40, seed=1), 4, 4),
+    "random_wide": (lambda: random_ilp(n=60, m=40, max_row_vars=16, seed=11, coef=3), 3, 5),
+}
+MODES = ["intervals", "depth"]
+
+
+def _oracle_for(inst, mode, kw, s, c=None):
+    import copy
+    if c is not None:
+        inst = copy.copy(inst)
+        inst.c = c
+    o = Oracle(inst, rank=kw.get("rank"))
+    if kw.get("averaging") == 1:
+        o.set_srmp(True)
+    if mode == "depth":
+        o.split_depth(s.split_depth, kw.get("gamma", 0.5))
+    else:
+        o.split(s.cuts(), kw.get("gamma", 0.5))
+    return o
+
+
+def _sensitivity(inst, mode, kw, s, iters, reps=3):
+    """Largest relative change of the oracle's bound after `iters` iterations when every cost is
+    scaled by 1 + 2^-24 * N(0, 1)."""
+    base = _oracle_for(inst, mode, kw, s).run_parallel(iters, omega=0.5)[-1]
+    rng = np.random.default_rng(0)
+    dev = 0.0
+    for _ in range(reps):
+        c = np.asarray(inst.c, np.float64) * (1 + 2.0 ** -24 * rng.standard_normal(inst.n))
+        lb = _oracle_for(inst, mode, kw, s, c).run_parallel(iters, omega=0.5)[-1]
+        dev = max(dev, abs(lb - base) / max(1.0, abs(base)))
+    return dev
+
+
+def _pair(name, mode="intervals", **kw):
+    """(instance, GPU solver split into balanced intervals or pieces of bounded depth, oracle
+    split the same way)"""
+    make, k, D = CASES[name]
+    inst = make()
+    o = Oracle(inst, rank=kw.get("rank"))
+    if kw.get("averaging") == 1:
+        o.set_srmp(True)
+    if mode == "depth":
+        s = solver(inst, split_depth=D, **kw)
+        o.split_depth(D, kw.get("gamma", 0.5))
+        assert s.max_depth <= D
+    else:
+        s = solver(inst, split=k, **kw)
+        o.split(s.cuts(), kw.get("gamma", 0.5))
+    assert s.npairs == o.npairs > 0 and s.nb == o.nb
+    return inst, s, o
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_split_slabs_bit_exact(lib, name, mode):
+    inst, s, o = _pair(name, mode)
+    if name == "tomography_24":
+        assert s.block_tiles > 0
+    got, want = s.canonical(), o.canonical()
+    for key in KEYS:
+        np.testing.assert_array_equal(got[key], want[key], err_msg=key)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_split_min_marginals_same_state(lib, name, mode):
+    """Pieces' min-marginals, folded multipliers and the bound for the same multipliers, pending
+    sums and copy duals: exercises multi-root first layers (root messages = min of mu over the
+    entry arcs) and copy arcs into top (cost mu_bar)."""
+    inst, s, o = _pair(name, mode)
+    rng = np.random.default_rng(len(name))
+    lam = rng.normal(0, 1, size=inst.nnz).astype(np.float32)
+    lam[inst.val == 0] = 0
+    P = rng.normal(0, 0.3, size=inst.n).astype(np.float32)
+    mb = rng.normal(0, 0.5, size=s.npairs).astype(np.float32)
+    mu = (-mb - np.abs(rng.normal(0, 0.5, size=s.npairs))).astype(np.float32)
+    s.set_state(lam, P)
+    s.set_copy_duals(mb, mu)
+    o.set_state(lam.astype(np.float64), P.astype(np.float64))
+    o.set_copy_duals(mb.astype(np.float64), mu.astype(np.float64))
+    lb, lam_out, m0, m1 = s.iterate(0, lam=True, mm=True)
+    e0, e1 = o.min_marginals(fold=True)
+    close(m0, e0, MM_TOL)
+    close(m1, e1, MM_TOL)
+    close(lam_out, o.lam(fold=True), 1e-6)
+    close([lb], [o.bound()], MM_TOL)
+    gb, gm = s.copy_duals()
+    np.testing.assert_array_equal(gb, mb)
+    np.testing.assert_array_equal(gm, mu)
+
+
+@pytest.mark.parametrize("staging", [0, 1])
+@pytest.mark.parametrize("gamma", [0.5, 1.0])
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_split_bound_trace_parity(lib, name, mode, gamma, staging):
+    inst, s, o = _pair(name, mode, gamma=gamma, staging=staging)
+    iters = 100
+    want = o.run_parallel(iters, omega=0.5)
+    got = _trace(s, iters)
+    close(got[:10], want[:10], LB_TOL)
+    tol = LB_TOL if gamma < 1.0 else max(LB_TOL, 4 * _sensitivity(inst, mode, {"gamma": gamma}, s, iters))
+    close(got[-1:], want[-1:], tol)
+    scale = np.maximum(1.0, np.abs(got[1:]))
+    assert np.all(np.diff(got) >= -MONO_TOL * scale), "device bound decreased"
+
+
+def test_split_state_after_iterations(lib):
+    """Multipliers, pending sums and copy duals after 60 iterations follow the oracle's; every
+    pair keeps mu + mu_bar <= 0; the folded multipliers of each variable sum to c_i."""
+    inst, s, o = _pair("potts_20x20x3")
+    lb, lam_fold, _, _ = s.iterate(60, lam=True)
+    tr = o.run_parallel(60, omega=0.5)
+    close([lb], [tr[-1]], LB_TOL)
+    lam, P = s.get_state()
+    close(lam, o.lam(fold=False), 2e-4)
+    close(P, o.pending(), 2e-4)
+    mb, mu = s.copy_duals()
+    wb, wm = o.copy_duals()
+    close(mb, wb, 2e-4)
+    close(mu, wm, 2e-4)
+    assert np.all(mb.astype(np.float64) + mu <= 1e-5)
+    sums = np.zeros(inst.n)
+    np.add.at(sums, inst.col, lam_fold.astype(np.float64))
+    close(sums, inst.c, 1e-5)
+
+
+def test_split_srmp_and_order(lib):
+    """Split solvers in a Cuthill-McKee order with SRMP averaging (Appendix A.3, A.4)."""
+    from paper_2009_00481_gb300 import cuthill_mckee
+    make = CASES["tracking_10x40"][0]
+    rank = cuthill_mckee(make())
+    for mode in MODES:
+        inst, s, o = _pair("tracking_10x40", mode, rank=rank, averaging=1)
+        close(_trace(s, 60), o.run_parallel(60, omega=0.5), LB_TOL)
+
+
+def test_split_full_tomography(lib):
+    """64x64 tomography (tie-break unaries) in 4 intervals, 100 iterations.  Row projections
+    cover consecutive variables and stay whole unless a cut falls inside them; column and
+    diagonal projections are cut."""
+    inst = tomography(side=64, seed=0, unary_sigma=0.01)
+    s = solver(inst, split=4)
+    o = Oracle(inst)
+    nb0 = o.nb
+    o.split(s.cuts())
+    assert s.nb == o.nb > nb0 and s.block_tiles > 0
+    close(_trace(s, 100)[-1:], o.run_parallel(100, omega=0.5)[-1:], LB_TOL)
+
+
+def test_depth_split_full_tomography(lib):
+    """64x64 tomography (tie-break unaries), every projection in pieces of at most 32 layers,
+    100 iterations."""
+    inst = tomography(side=64, seed=0, unary_sigma=0.01)
+    s = solver(inst, split_depth=32)
+    o = Oracle(inst)
+    o.split_depth(32)
+    assert s.nb == o.nb and s.max_depth == 32 and s.block_tiles > 0
+    close(_trace(s, 100)[-1:], o.run_parallel(100, omega=0.5)[-1:], LB_TOL)
+
+
+def test_split_restart_and_determinism(lib):
+    """set_costs restarts the copy duals at 0; two solvers give identical traces; the profiled
+    (kernel by kernel) iterations run the same steps as the graphs."""
+    inst, a, o = _pair("random_wide")
+    ta = _trace(a, 30)
+    a.set_costs(inst.c)
+    mb, mu = a.copy_duals()
+    assert np.all(mb == 0) and np.all(mu == 0)
+    np.testing.assert_array_equal(_trace(a, 30), ta)
+    b = solver(inst, split=CASES["random_wide"][1])
+    assert b.npairs == a.npairs
+    b.iterate_profiled(30)
+    la, pa = a.get_state()
+    lb_, pb = b.get_state()
+    np.testing.assert_array_equal(la, lb_)
+    np.testing.assert_array_equal(pa, pb)
+    np.testing.assert_array_equal(a.copy_duals()[0], b.copy_duals()[0])
+
+
+def test_split_refuses_part_bounds(lib):
+    from paper_2009_00481_gb300 import BDDError
+    from paper_2009_00481_gb300.binding import BDD_EINVAL
+    inst, s, _ = _pair("potts_20x20x3")
+    with pytest.raises(BDDError) as e:
+        s.bound_parts([0, inst.m], [0, inst.n])
+    assert e.value.code == BDD_EINVAL
