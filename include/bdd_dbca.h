@@ -103,7 +103,8 @@ typedef struct {
                                  (TMA) ring, 4-layer windows, the next window loading while one
                                  is processed; 1: 8-layer windows in two rounds of cp.async.
                                  -1 (default): the autotuner times both at build (schedule 1: a
-                                 warm-up and three iterations each, kernel by kernel) and keeps
+                                 warm-up and six iterations each, kernel by kernel, the fastest
+                                 launch of each sweep counted) and keeps
                                  the faster per sweep direction.  The variants compute identical
                                  values; the persistent schedule and other sweeps use 0. */
   int split_intervals;        /* sub-BDDs (Sec. 6, Def. of sub-BDDs and copy-arcs; the parallel

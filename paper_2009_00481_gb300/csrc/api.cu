@@ -289,14 +289,25 @@ struct bdd_solver {
     return BDD_OK;
   }
 
-  int sweep(bool fwd, int mode, cudaStream_t s, float *m0 = nullptr, float *m1 = nullptr) {
+  // finish_prev: a forward update sweep that also finishes the previous iteration's deferred bound
+  int sweep(bool fwd, int mode, cudaStream_t s, float *m0 = nullptr, float *m1 = nullptr, bool finish_prev = false) {
     const int staging = mode == kUpdate ? (fwd ? stage_fwd : stage_bwd) : 0;
-    return sweep_launch(fwd, mode, sweep_params(m0, m1), grid_sweep, s, staging) ? BDD_ECUDA : BDD_OK;
+    SweepParams p = sweep_params(m0, m1);
+    if (finish_prev) {
+      p.fin_partial = d_partial;
+      p.fin_nblocks = grid_reduce;
+      p.fin_iter = d_iter;
+      p.fin_trace = d_trace;
+      p.fin_cap = trace_cap;
+      p.fin_const = empty_const;
+    }
+    return sweep_launch(fwd, mode, p, grid_sweep, s, staging) ? BDD_ECUDA : BDD_OK;
   }
 
   // Autotuner: time each warp-tile staging variant of the update sweeps on this instance
-  // (after a warm-up iteration, `reps` iterations launched kernel by kernel between events)
-  // and keep the faster one per direction.  Both variants compute the same values, so the
+  // (after a warm-up iteration, `reps` iterations launched kernel by kernel between events,
+  // the fastest of each sweep kept, which is robust to a stray slow launch) and keep the faster
+  // variant per direction.  Both variants compute the same values, so the
   // choice affects time only; the solver is restarted afterwards.
   int autotune(cudaStream_t s, int reps) {
     if (n_warp_tiles == 0 || reps < 1) return BDD_OK;
@@ -323,10 +334,8 @@ struct bdd_solver {
         if (rc == BDD_OK) rc = pending(true, s);
         if (rc == BDD_OK && cudaEventSynchronize(ev[1]) != cudaSuccess) rc = BDD_ECUDA;
         if (rc == BDD_OK && cudaEventElapsedTime(&t1, ev[0], ev[1]) != cudaSuccess) rc = BDD_ECUDA;
-        if (it > 0) {
-          ms[v][0] += t0;
-          ms[v][1] += t1;
-        }
+        if (it == 1 || (it > 1 && t0 < ms[v][0])) ms[v][0] = t0;
+        if (it == 1 || (it > 1 && t1 < ms[v][1])) ms[v][1] = t1;
       }
     }
     for (auto &e : ev)
@@ -339,15 +348,17 @@ struct bdd_solver {
     stage_fwd = ms[1][0] < ms[0][0] ? 1 : 0;
     stage_bwd = ms[1][1] < ms[0][1] ? 1 : 0;
     for (int v = 0; v < 2; ++v)
-      for (int d = 0; d < 2; ++d) tune_ms[v][d] = ms[v][d] / reps;
+      for (int d = 0; d < 2; ++d) tune_ms[v][d] = ms[v][d];
     return restart(s);
   }
 
   // pending sums and the shares of the next sweep: a forward sweep follows a bound pass (the
   // end of an iteration), a backward sweep the pass between the sweeps; `next_dir` overrides
-  int pending(bool bound, cudaStream_t s, int next_dir = 0) {
+  int pending(bool bound, cudaStream_t s, int next_dir = 0, bool defer = false) {
     if (!next_dir) next_dir = bound ? kDirForward : kDirBackward;
-    return pending_launch(bound, pending_params(next_dir), grid_reduce, s) ? BDD_ECUDA : BDD_OK;
+    PendingParams r = pending_params(next_dir);
+    r.defer = defer ? 1 : 0;
+    return pending_launch(bound, r, grid_reduce, s) ? BDD_ECUDA : BDD_OK;
   }
 
   // one iteration: forward sweep, pending sums, backward sweep, pending sums and bound.  Fused
@@ -360,12 +371,18 @@ struct bdd_solver {
       if (last && bound_launch(fused_params(false), grid_reduce, s)) return BDD_ECUDA;
       return BDD_OK;
     }
-    RC(sweep(true, kUpdate, s));
+    // the bound's per-block partials are summed by the next iteration's forward sweep (off the
+    // chain's critical path), or after the last iteration by a one-warp kernel
+    const bool defer = grid_sweep > 0;
+    RC(sweep(true, kUpdate, s, nullptr, nullptr, defer && !first));
     RC(cut(true, s));
     RC(pending(false, s));
     RC(sweep(false, kUpdate, s));
-    RC(pending(true, s));
+    RC(pending(true, s, 0, defer));
     RC(cut(false, s));
+    if (defer && last &&
+        bound_finish_launch(d_partial, grid_reduce, d_iter, d_trace, trace_cap, empty_const, s))
+      return BDD_ECUDA;
     return BDD_OK;
   }
 
@@ -677,7 +694,7 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c, const CutTables
   if (h->staging_opt >= 0) {
     h->stage_fwd = h->stage_bwd = h->staging_opt;
   } else if (h->schedule == 1 && !h->fused) {
-    RC(h->autotune(h->stream, 3));
+    RC(h->autotune(h->stream, 6));
   }
   RC(h->end(h->stream));
   CK(cudaStreamSynchronize(h->stream));

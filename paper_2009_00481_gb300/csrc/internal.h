@@ -204,6 +204,15 @@ struct SweepParams {
   const float *copy_val; // sub-BDDs: mu_bar of every copy-arc pair (backward message of kCopy0 - k)
   int split;             // sub-BDDs: layer-0 forward messages are the root messages held in fm, and
                          // E^j is the minimum over the first layer of fm + bm
+  // deferred bound of the previous iteration (forward update sweeps of the per-phase plan): the
+  // per-block partials its pending pass left, summed in a fixed order by one warp of the
+  // sweep's last warp block (its shallowest tiles) into fin_trace[*fin_iter]; null: nothing
+  const double *fin_partial;
+  int fin_nblocks;
+  int *fin_iter;
+  double *fin_trace;
+  int fin_cap;
+  double fin_const;
   int *error;            // set to BDD_ETIMEOUT if a bounded wait on a shared-memory copy gives up
   long long spin_limit;  // polls of such a wait: spin_limit / 64 (at least 1)
   FusedParams fz;       // fz.cnt == null outside the fused plan
@@ -240,6 +249,8 @@ struct PendingParams {
   double alpha;  // smoothing temperature of the slack term (0: min-sum)
   const unsigned char *slot_dir;  // SRMP membership bits per slot, or null (eq. mma-update)
   int next_dir;                   // kDirForward / kDirBackward: the sweep the shares are for
+  int defer;                      // bound: leave the per-block partials for the next forward sweep
+                                  // (or bound_finish_launch) instead of finishing them here
   const int4 *heavy;              // variables with more than heavy_deg occurrences: {i, first slot,
   int n_heavy;                    // end slot, 0}, handled by one warp each
   int heavy_deg;
@@ -325,6 +336,9 @@ int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStr
 int pending_launch(bool bound, const PendingParams &p, int grid, cudaStream_t stream);
 // FP64 bound from the E^j and slack terms of the last fused backward sweep into trace[*iter_ctr]
 int bound_launch(const SweepParams &p, int grid, cudaStream_t stream);
+// finishes a deferred bound (partials of a pending pass with defer) into trace[*iter_ctr]
+int bound_finish_launch(const double *partial, int nblocks, int *iter_ctr, double *trace, int cap,
+                        double empty_const, cudaStream_t stream);
 int iterate_persistent_max_grid(size_t smem, int *grid);
 int iterate_persistent_launch(const IterParams &q, int grid, size_t smem, cudaStream_t stream);
 int init_lambda_launch(const int *occ_var, const int *var_ptr, const float *c, float *lam, int O,

@@ -30,19 +30,24 @@ namespace {
 
 // backward message of a terminal arc target t < 0: top -> 0, bot / none -> +inf; the copy arc of
 // pair k (t = kCopy0 - k, sub-BDDs of Sec. 6) enters top at cost mu_bar_k
+// (SPLIT: instantiated for split solvers only, so the unsplit sweeps carry no copy-arc code)
+template <bool SPLIT>
 __device__ __forceinline__ float terminal_bm(const float *__restrict__ copy_val, int t) {
   if (t == kTop) return 0.f;
+  if (!SPLIT) return inf();
   return t > kCopy0 ? inf() : copy_val[kCopy0 - t];
 }
 
 // backward message of an arc target: node -> bm, else the terminal's
+template <bool SPLIT>
 __device__ __forceinline__ float target_bm(const float *__restrict__ bm, const float *__restrict__ copy_val, int t) {
-  return t >= 0 ? bm[t] : terminal_bm(copy_val, t);
+  return t >= 0 ? bm[t] : terminal_bm<SPLIT>(copy_val, t);
 }
 
 // backward message of an arc target staged at msg[t - base]
+template <bool SPLIT>
 __device__ __forceinline__ float staged_bm(const float *msg, const float *__restrict__ copy_val, int base, int t) {
-  return t >= 0 ? msg[t - base] : terminal_bm(copy_val, t);
+  return t >= 0 ? msg[t - base] : terminal_bm<SPLIT>(copy_val, t);
 }
 
 // atomic minimum on a float in shared memory (non-negative floats order like their int bits,
@@ -457,7 +462,7 @@ __device__ __forceinline__ TileInfo tile_info(const SweepParams &p, int tile) {
   return ti;
 }
 
-template <int T, int MODE, bool SMOOTH>
+template <int T, int MODE, bool SMOOTH, bool SPLIT>
 __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &ph, int tile, StageRing &ring,
                                              double &bacc) {
   const int lane = threadIdx.x & 31;
@@ -503,7 +508,7 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
       // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv
       float f;
       if (l == 0) {  // the root, or a piece's roots with their root messages (sub-BDDs)
-        f = p.split && has ? p.fm[node0 + tl] : 0.f;
+        f = SPLIT && has ? p.fm[node0 + tl] : 0.f;
       } else {
         const int lo_l = lh_prev.x >= 0 ? lh_prev.x - node0 : kNone;
         const int hi_l = lh_prev.y >= 0 ? lh_prev.y - node0 : kNone;
@@ -525,8 +530,8 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
       float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
       if (is_update(MODE)) {
         // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
-        const float a0 = has ? f + staged_bm(msg, p.copy_val, na, lh.x) : inf();
-        const float a1 = has ? f + lam + staged_bm(msg, p.copy_val, na, lh.y) : inf();
+        const float a0 = has ? f + staged_bm<SPLIT>(msg, p.copy_val, na, lh.x) : inf();
+        const float a1 = has ? f + lam + staged_bm<SPLIT>(msg, p.copy_val, na, lh.y) : inf();
         const float m0 = team_agg<T, SMOOTH>(a0, p), m1 = team_agg<T, SMOOTH>(a1, p);
         const float dd = p.omega * mm_difference(m0, m1);
         lam -= dd;
@@ -552,7 +557,7 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
   }
 }
 
-template <int T, int MODE, bool SMOOTH>
+template <int T, int MODE, bool SMOOTH, bool SPLIT>
 __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase &ph, int tile, StageRing &ring,
                                               double &bacc) {
   const int lane = threadIdx.x & 31;
@@ -609,8 +614,8 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
       const int s1 = lh.y >= 0 ? lh.y - node0_next : 0;
       const float g0 = __shfl_sync(kFull, b_next, tbase + (s0 & (T - 1)));
       const float g1 = __shfl_sync(kFull, b_next, tbase + (s1 & (T - 1)));
-      const float b0 = lh.x >= 0 ? g0 : terminal_bm(p.copy_val, lh.x);
-      const float b1 = lh.y >= 0 ? g1 : terminal_bm(p.copy_val, lh.y);
+      const float b0 = lh.x >= 0 ? g0 : terminal_bm<SPLIT>(p.copy_val, lh.x);
+      const float b1 = lh.y >= 0 ? g1 : terminal_bm<SPLIT>(p.copy_val, lh.y);
       if (MODE != kMessages) {
         const float m0 = team_agg<T, SMOOTH>(f + b0, p), m1 = team_agg<T, SMOOTH>(f + lam + b1, p);
         if (is_update(MODE)) {
@@ -630,7 +635,7 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
       const float bcur = agg<SMOOTH>(b0, lam + b1, p);
       if (has) p.bm[node0 + tl] = bcur;
       if (l == 0) {  // E^j(lambda^j) at the root; a piece: min over its roots of fm + bm
-        const float e = p.split ? team_agg<T, SMOOTH>(has ? f + bcur : inf(), p) : bcur;
+        const float e = SPLIT ? team_agg<T, SMOOTH>(has ? f + bcur : inf(), p) : bcur;
         if (active && tl == 0) {
           p.bdd_E[bdd] = e;
           bacc += (double)e;
@@ -675,7 +680,7 @@ __device__ __forceinline__ void stage_occurrences_w8(const SweepParams &p, const
   cp_async_wait();
 }
 
-template <int T, int MODE, bool SMOOTH>
+template <int T, int MODE, bool SMOOTH, bool SPLIT>
 __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phase &ph, int tile, WarpStage8 &S,
                                              double &bacc) {
   const int lane = threadIdx.x & 31;
@@ -717,7 +722,7 @@ __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phas
       // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv
       float f;
       if (l == 0) {  // the root, or a piece's roots with their root messages (sub-BDDs)
-        f = p.split && has ? p.fm[node0 + tl] : 0.f;
+        f = SPLIT && has ? p.fm[node0 + tl] : 0.f;
       } else {
         const int lo_l = lh_prev.x >= 0 ? lh_prev.x - node0 : kNone;
         const int hi_l = lh_prev.y >= 0 ? lh_prev.y - node0 : kNone;
@@ -739,8 +744,8 @@ __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phas
       float lam = active ? S.lam[oi] + S.shr[oi] : 0.f;
       if (is_update(MODE)) {
         // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
-        const float a0 = has ? f + staged_bm(S.msg, p.copy_val, na, lh.x) : inf();
-        const float a1 = has ? f + lam + staged_bm(S.msg, p.copy_val, na, lh.y) : inf();
+        const float a0 = has ? f + staged_bm<SPLIT>(S.msg, p.copy_val, na, lh.x) : inf();
+        const float a1 = has ? f + lam + staged_bm<SPLIT>(S.msg, p.copy_val, na, lh.y) : inf();
         const float m0 = team_agg<T, SMOOTH>(a0, p), m1 = team_agg<T, SMOOTH>(a1, p);
         const float dd = p.omega * mm_difference(m0, m1);
         lam -= dd;
@@ -756,7 +761,7 @@ __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phas
   }
 }
 
-template <int T, int MODE, bool SMOOTH>
+template <int T, int MODE, bool SMOOTH, bool SPLIT>
 __device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Phase &ph, int tile, WarpStage8 &S,
                                               double &bacc) {
   const int lane = threadIdx.x & 31;
@@ -805,8 +810,8 @@ __device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Pha
       const int s1 = lh.y >= 0 ? lh.y - node0_next : 0;
       const float g0 = __shfl_sync(kFull, b_next, tbase + (s0 & (T - 1)));
       const float g1 = __shfl_sync(kFull, b_next, tbase + (s1 & (T - 1)));
-      const float b0 = lh.x >= 0 ? g0 : terminal_bm(p.copy_val, lh.x);
-      const float b1 = lh.y >= 0 ? g1 : terminal_bm(p.copy_val, lh.y);
+      const float b0 = lh.x >= 0 ? g0 : terminal_bm<SPLIT>(p.copy_val, lh.x);
+      const float b1 = lh.y >= 0 ? g1 : terminal_bm<SPLIT>(p.copy_val, lh.y);
       if (MODE != kMessages) {
         const float m0 = team_agg<T, SMOOTH>(f + b0, p), m1 = team_agg<T, SMOOTH>(f + lam + b1, p);
         if (is_update(MODE)) {
@@ -826,7 +831,7 @@ __device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Pha
       const float bcur = agg<SMOOTH>(b0, lam + b1, p);
       if (has) p.bm[node0 + tl] = bcur;
       if (l == 0) {  // E^j(lambda^j) at the root; a piece: min over its roots of fm + bm
-        const float e = p.split ? team_agg<T, SMOOTH>(has ? f + bcur : inf(), p) : bcur;
+        const float e = SPLIT ? team_agg<T, SMOOTH>(has ? f + bcur : inf(), p) : bcur;
         if (active && tl == 0) {
           p.bdd_E[bdd] = e;
           bacc += (double)e;
@@ -845,10 +850,11 @@ __device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Pha
 struct GroupSmem {
   float2 *red;  // [kWarpsPerBlock]
   float *bufA, *bufB, *shr;
+  int *off;     // [block_depth_buf + 4] node offsets of the tile's layers (narrow tiles)
 };
 
 __host__ __device__ __forceinline__ size_t group_floats(int block_buf, int block_depth_buf) {
-  return 2 * kWarpsPerBlock + 2 * (size_t)block_buf + block_depth_buf;
+  return 2 * kWarpsPerBlock + 2 * (size_t)block_buf + 2 * (size_t)block_depth_buf + 4;
 }
 
 __device__ __forceinline__ GroupSmem group_smem(float *base, const SweepParams &p) {
@@ -857,6 +863,7 @@ __device__ __forceinline__ GroupSmem group_smem(float *base, const SweepParams &
   g.bufA = base + 2 * kWarpsPerBlock;
   g.bufB = g.bufA + p.block_buf;
   g.shr = g.bufB + p.block_buf;
+  g.off = reinterpret_cast<int *>(g.shr + p.block_depth_buf);
   return g;
 }
 
@@ -891,7 +898,7 @@ __device__ __forceinline__ void stage_group_shares(const SweepParams &p, int occ
   cp_async_wait();
 }
 
-template <int MODE>
+template <int MODE, bool SPLIT>
 __device__ __forceinline__ void block_forward(const SweepParams &p, const Phase &ph, int tile, const GroupSmem &g,
                                               int group, int gt, double &bacc) {
   const int bdd = p.tile_bdd0[tile];
@@ -899,7 +906,7 @@ __device__ __forceinline__ void block_forward(const SweepParams &p, const Phase 
   const int depth = p.bdd_depth[bdd];
   float *cur = g.bufA, *nxt = g.bufB;
   stage_group_shares<MODE>(p, occ0, depth, g.shr, gt);
-  if (p.split) {  // a piece's roots start from their root messages
+  if (SPLIT) {  // a piece's roots start from their root messages
     const int n0 = p.occ_node_off[occ0], w0 = p.occ_node_off[occ0 + 1] - n0;
     for (int t = gt; t < w0; t += kBlockThreads) cur[t] = p.fm[n0 + t];
   } else if (gt == 0) {
@@ -916,8 +923,8 @@ __device__ __forceinline__ void block_forward(const SweepParams &p, const Phase 
       p.fm[node0 + t] = f;
       if (is_update(MODE)) {
         const int2 lh = p.lohi[node0 + t];
-        a0 = fminf(a0, f + target_bm(p.bm, p.copy_val, lh.x));
-        a1 = fminf(a1, f + lam + target_bm(p.bm, p.copy_val, lh.y));
+        a0 = fminf(a0, f + target_bm<SPLIT>(p.bm, p.copy_val, lh.x));
+        a1 = fminf(a1, f + lam + target_bm<SPLIT>(p.bm, p.copy_val, lh.y));
       }
     }
     if (is_update(MODE)) {
@@ -947,7 +954,7 @@ __device__ __forceinline__ void block_forward(const SweepParams &p, const Phase 
   }
 }
 
-template <int MODE>
+template <int MODE, bool SPLIT>
 __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase &ph, int tile, const GroupSmem &g,
                                                int group, int gt, double &bacc) {
   const int bdd = p.tile_bdd0[tile];
@@ -966,8 +973,8 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
       for (int t = gt; t < w; t += kBlockThreads) {
         const int2 lh = p.lohi[node0 + t];
         const float f = p.fm[node0 + t];
-        const float b0 = lh.x >= 0 ? cur[lh.x - next0] : terminal_bm(p.copy_val, lh.x);
-        const float b1 = lh.y >= 0 ? cur[lh.y - next0] : terminal_bm(p.copy_val, lh.y);
+        const float b0 = lh.x >= 0 ? cur[lh.x - next0] : terminal_bm<SPLIT>(p.copy_val, lh.x);
+        const float b1 = lh.y >= 0 ? cur[lh.y - next0] : terminal_bm<SPLIT>(p.copy_val, lh.y);
         a0 = fminf(a0, f + b0);
         a1 = fminf(a1, f + lam + b1);
       }
@@ -988,13 +995,13 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
     float e = inf();  // a piece's energy: min over its roots of fm + bm
     for (int t = gt; t < w; t += kBlockThreads) {
       const int2 lh = p.lohi[node0 + t];
-      const float b0 = lh.x >= 0 ? cur[lh.x - next0] : terminal_bm(p.copy_val, lh.x);
-      const float b1 = lh.y >= 0 ? cur[lh.y - next0] : terminal_bm(p.copy_val, lh.y);
+      const float b0 = lh.x >= 0 ? cur[lh.x - next0] : terminal_bm<SPLIT>(p.copy_val, lh.x);
+      const float b1 = lh.y >= 0 ? cur[lh.y - next0] : terminal_bm<SPLIT>(p.copy_val, lh.y);
       const float bcur = fminf(b0, lam + b1);
       p.bm[node0 + t] = bcur;
       nxt[t] = bcur;
       if (l == 0) {
-        if (p.split) {
+        if (SPLIT) {
           e = fminf(e, p.fm[node0 + t] + bcur);
         } else if (t == 0) {
           p.bdd_E[bdd] = bcur;
@@ -1002,7 +1009,7 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
         }
       }
     }
-    if (l == 0 && p.split) {
+    if (l == 0 && SPLIT) {
       e = group_min2(e, inf(), g.red, group, gt).x;
       if (gt == 0) {
         p.bdd_E[bdd] = e;
@@ -1016,8 +1023,168 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// block tiles whose layers are at most kBlockThreads nodes wide (one node per thread): the
+// tile's node offsets and multipliers (with the shares the sweep adds) are staged in shared
+// memory once, and each thread prefetches its node's arcs two layers ahead and, in a forward
+// update, the backward messages of their targets one layer ahead, so the layer recurrence waits
+// on no global load.  Same arithmetic as block_forward / block_backward.
+// ---------------------------------------------------------------------------------------
+template <int MODE>
+__device__ __forceinline__ void stage_group_layers(const SweepParams &p, int occ0, int depth, const GroupSmem &g,
+                                                   int gt) {
+  for (int l = gt; l <= depth; l += kBlockThreads) g.off[l] = p.occ_node_off[occ0 + l];
+  for (int l = gt; l < depth; l += kBlockThreads)
+    g.shr[l] = p.lam[occ0 + l] + (MODE != kMessages ? p.share_occ[occ0 + l] : 0.f);
+}
+
+// arcs of this thread's node in layer l (none past the last layer or the layer's width)
+__device__ __forceinline__ int2 narrow_arcs(const SweepParams &p, const int *off, int l, int depth, int gt) {
+  if (l >= depth) return make_int2(kNone, kNone);
+  const int node0 = off[l];
+  return gt < off[l + 1] - node0 ? p.lohi[node0 + gt] : make_int2(kNone, kNone);
+}
+
+template <int MODE, bool SPLIT>
+__device__ __forceinline__ void block_forward_narrow(const SweepParams &p, const Phase &ph, int tile,
+                                                     const GroupSmem &g, int group, int gt, double &bacc) {
+  const int bdd = p.tile_bdd0[tile];
+  const int occ0 = p.tile_occ0[tile];
+  const int depth = p.bdd_depth[bdd];
+  float *cur = g.bufA, *nxt = g.bufB;
+  const int *off = g.off;
+  stage_group_layers<MODE>(p, occ0, depth, g, gt);
+  group_sync(group);
+  {  // the root, or a piece's roots with their root messages (sub-BDDs)
+    const int n0 = off[0];
+    if (gt < off[1] - n0) cur[gt] = SPLIT ? p.fm[n0 + gt] : 0.f;
+  }
+  int2 lh = narrow_arcs(p, off, 0, depth, gt), lh1 = narrow_arcs(p, off, 1, depth, gt);
+  float t0 = 0.f, t1 = 0.f;
+  if (is_update(MODE)) {
+    t0 = target_bm<SPLIT>(p.bm, p.copy_val, lh.x);
+    t1 = target_bm<SPLIT>(p.bm, p.copy_val, lh.y);
+  }
+  group_sync(group);
+  for (int l = 0; l < depth; ++l) {
+    // in flight during this layer: the next layer's target messages, the arcs two layers on
+    float u0 = 0.f, u1 = 0.f;
+    if (is_update(MODE) && l + 1 < depth) {
+      u0 = target_bm<SPLIT>(p.bm, p.copy_val, lh1.x);
+      u1 = target_bm<SPLIT>(p.bm, p.copy_val, lh1.y);
+    }
+    const int2 lh2 = narrow_arcs(p, off, l + 2, depth, gt);
+    const int o = occ0 + l;
+    const int node0 = off[l], w = off[l + 1] - node0;
+    const bool has = gt < w;
+    const float f = has ? cur[gt] : inf();
+    if (has) p.fm[node0 + gt] = f;
+    float lam = g.shr[l];
+    const bool more = l + 1 < depth;
+    // nxt was last read before the previous layer's final barrier
+    if (more && gt < off[l + 2] - off[l + 1]) nxt[gt] = inf();
+    if (is_update(MODE)) {
+      const float2 mm = group_min2(has ? f + t0 : inf(), has ? f + lam + t1 : inf(), g.red, group, gt);
+      const float dd = p.omega * mm_difference(mm.x, mm.y);
+      lam -= dd;
+      if (gt == 0) {
+        p.lam[o] = lam;
+        ph.delta[p.occ_slot[o]] = dd;
+      }
+    } else if (more) {
+      group_sync(group);  // the resets of nxt before the pushes
+    }
+    if (more) {
+      const int next0 = off[l + 1];
+      if (lh.x >= 0) atomic_min_f(&nxt[lh.x - next0], f);
+      if (lh.y >= 0) atomic_min_f(&nxt[lh.y - next0], f + lam);
+      group_sync(group);
+      float *tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
+    lh = lh1;
+    lh1 = lh2;
+    t0 = u0;
+    t1 = u1;
+  }
+}
+
+template <int MODE, bool SPLIT>
+__device__ __forceinline__ void block_backward_narrow(const SweepParams &p, const Phase &ph, int tile,
+                                                      const GroupSmem &g, int group, int gt, double &bacc) {
+  const int bdd = p.tile_bdd0[tile];
+  const int occ0 = p.tile_occ0[tile];
+  const int depth = p.bdd_depth[bdd];
+  float *cur = g.bufA, *nxt = g.bufB;  // cur: backward messages of layer l + 1
+  const int *off = g.off;
+  stage_group_layers<MODE>(p, occ0, depth, g, gt);
+  group_sync(group);
+  // this thread's node in layer l: arcs and forward message, prefetched two layers ahead
+  auto node_fm = [&](int l) {
+    if (l < 0) return inf();
+    const int node0 = off[l];
+    return gt < off[l + 1] - node0 ? p.fm[node0 + gt] : inf();
+  };
+  const int last = depth - 1;
+  int2 lh = narrow_arcs(p, off, last, depth, gt), lh1 = last >= 1 ? narrow_arcs(p, off, last - 1, depth, gt)
+                                                                    : make_int2(kNone, kNone);
+  float f = node_fm(last), f1 = node_fm(last - 1);
+  for (int l = last; l >= 0; --l) {
+    const int2 lh2 = l >= 2 ? narrow_arcs(p, off, l - 2, depth, gt) : make_int2(kNone, kNone);
+    const float f2 = node_fm(l - 2);
+    const int o = occ0 + l;
+    const int node0 = off[l], w = off[l + 1] - node0, next0 = off[l + 1];
+    const bool has = gt < w;
+    float lam = g.shr[l];
+    const float b0 = lh.x >= 0 ? cur[lh.x - next0] : terminal_bm<SPLIT>(p.copy_val, lh.x);
+    const float b1 = lh.y >= 0 ? cur[lh.y - next0] : terminal_bm<SPLIT>(p.copy_val, lh.y);
+    if (MODE != kMessages) {
+      const float2 mm = group_min2(has ? f + b0 : inf(), has ? f + lam + b1 : inf(), g.red, group, gt);
+      if (is_update(MODE)) {
+        const float dd = p.omega * mm_difference(mm.x, mm.y);
+        lam -= dd;
+        if (gt == 0) {
+          p.lam[o] = lam;
+          ph.delta[p.occ_slot[o]] = dd;
+        }
+      } else if (gt == 0 && p.out_m0) {
+        const long long c = p.occ_csr[o];
+        p.out_m0[c] = mm.x;
+        p.out_m1[c] = mm.y;
+      }
+    }
+    // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
+    const float bcur = fminf(b0, lam + b1);
+    if (has) {
+      p.bm[node0 + gt] = bcur;
+      nxt[gt] = bcur;
+    }
+    if (l == 0) {  // E^j at the root; a piece: min over its roots of fm + bm
+      if (SPLIT) {
+        const float e = group_min2(has ? f + bcur : inf(), inf(), g.red, group, gt).x;
+        if (gt == 0) {
+          p.bdd_E[bdd] = e;
+          bacc += (double)e;
+        }
+      } else if (gt == 0) {
+        p.bdd_E[bdd] = bcur;
+        bacc += (double)bcur;
+      }
+    }
+    group_sync(group);
+    float *tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    lh = lh1;
+    lh1 = lh2;
+    f = f1;
+    f1 = f2;
+  }
+}
+
 // STAGE 0: bulk-copy ring (StageRing); STAGE 1: 8-layer cp.async windows (WarpStage8 at W8)
-template <bool FWD, int MODE, bool SMOOTH, int STAGE = 0>
+template <bool FWD, int MODE, bool SMOOTH, int STAGE = 0, bool SPLIT = false>
 __device__ __forceinline__ void warp_tile(const SweepParams &p, const Phase &ph, int tile, StageRing &S,
                                           double &bacc, WarpStage8 *W8 = nullptr) {
   int c = 0;
@@ -1026,11 +1193,11 @@ __device__ __forceinline__ void warp_tile(const SweepParams &p, const Phase &ph,
 #define BDD_TEAM_CASE(C, T)                                                     \
   case C:                                                                       \
     if constexpr (STAGE == 1) {                                                 \
-      if (FWD) warp_forward_w8<T, MODE, SMOOTH>(p, ph, tile, *W8, bacc);       \
-      else warp_backward_w8<T, MODE, SMOOTH>(p, ph, tile, *W8, bacc);          \
+      if (FWD) warp_forward_w8<T, MODE, SMOOTH, SPLIT>(p, ph, tile, *W8, bacc); \
+      else warp_backward_w8<T, MODE, SMOOTH, SPLIT>(p, ph, tile, *W8, bacc);    \
     } else {                                                                    \
-      if (FWD) warp_forward<T, MODE, SMOOTH>(p, ph, tile, S, bacc);             \
-      else warp_backward<T, MODE, SMOOTH>(p, ph, tile, S, bacc);                \
+      if (FWD) warp_forward<T, MODE, SMOOTH, SPLIT>(p, ph, tile, S, bacc);       \
+      else warp_backward<T, MODE, SMOOTH, SPLIT>(p, ph, tile, S, bacc);          \
     }                                                                           \
     break;
     BDD_TEAM_CASE(0, 1)
@@ -1042,6 +1209,23 @@ __device__ __forceinline__ void warp_tile(const SweepParams &p, const Phase &ph,
 #undef BDD_TEAM_CASE
     default:
       break;
+  }
+}
+
+// The bound from the per-block partials of a deferred pending pass, by one warp: lane k adds
+// partials k, k + 32, ... in order, then a fixed shuffle tree; lane 0 stores.  The same bits on
+// every run (the order does not depend on timing).
+__device__ __forceinline__ void finish_bound(const double *partial, int nblocks, int *iter_ctr, double *trace,
+                                             int cap, double empty_const) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int k = lane; k < nblocks; k += 32) s += __ldcg(partial + k);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+  if (lane == 0) {
+    const int it = *iter_ctr;
+    if (it < cap) trace[it] = s + empty_const;
+    *iter_ctr = it + 1;
   }
 }
 
@@ -1097,7 +1281,7 @@ __device__ __forceinline__ void fused_bound(const FusedParams &z, const float *_
   }
 }
 
-template <bool FWD, int MODE, bool SMOOTH, int STAGE = 0>
+template <bool FWD, int MODE, bool SMOOTH, int STAGE = 0, bool SPLIT = false>
 __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams p) {
   extern __shared__ __align__(16) float smem[];
   // the next kernel of the chain may launch now: it reads nothing this one writes before its
@@ -1118,7 +1302,7 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
     char *mine = reinterpret_cast<char *>(smem) + (size_t)warp * kWarpSmemBytes;
     if constexpr (STAGE == 1) {
       StageRing none{nullptr, nullptr, 0u};
-      warp_tile<FWD, MODE, SMOOTH, 1>(p, ph, tile, none, bacc, reinterpret_cast<WarpStage8 *>(mine));
+      warp_tile<FWD, MODE, SMOOTH, 1, SPLIT>(p, ph, tile, none, bacc, reinterpret_cast<WarpStage8 *>(mine));
     } else {
       __shared__ unsigned long long bars[kWarpsPerBlock * kWarpStages];
       if ((threadIdx.x & 31) == 0) {
@@ -1127,23 +1311,42 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
       }
       __syncwarp();
       StageRing ring{reinterpret_cast<WarpStage *>(mine), &bars[warp * kWarpStages], 0u};
-      warp_tile<FWD, MODE, SMOOTH>(p, ph, tile, ring, bacc);
+      warp_tile<FWD, MODE, SMOOTH, 0, SPLIT>(p, ph, tile, ring, bacc);
     }
+    // the previous iteration's bound, by warp 0 of the last warp block (its tiles are the
+    // shallowest, so the chain's critical path does not wait for this)
+    if (FWD && p.fin_partial && (int)blockIdx.x == p.n_warp_blocks - 1 && warp == 0)
+      finish_bound(p.fin_partial, p.fin_nblocks, p.fin_iter, p.fin_trace, p.fin_cap, p.fin_const);
   } else if constexpr (!SMOOTH) {  // smoothed solvers have warp tiles only
     const int tile = p.class_tile_off[kWarpClasses] + (blockIdx.x - p.n_warp_blocks);
     if (tile >= p.class_tile_off[kWarpClasses + 1]) return;  // uniform across the block
     pdl_wait();
     const GroupSmem g = group_smem(smem, p);
-    if (FWD)
-      block_forward<MODE>(p, ph, tile, g, 0, threadIdx.x, bacc);
-    else
-      block_backward<MODE>(p, ph, tile, g, 0, threadIdx.x, bacc);
+    if (p.block_buf <= kBlockThreads) {
+      if (FWD)
+        block_forward_narrow<MODE, SPLIT>(p, ph, tile, g, 0, threadIdx.x, bacc);
+      else
+        block_backward_narrow<MODE, SPLIT>(p, ph, tile, g, 0, threadIdx.x, bacc);
+    } else if (FWD) {
+      block_forward<MODE, SPLIT>(p, ph, tile, g, 0, threadIdx.x, bacc);
+    } else {
+      block_backward<MODE, SPLIT>(p, ph, tile, g, 0, threadIdx.x, bacc);
+    }
     if (MODE == kUpdateFused) {
       group_sync(0);
       pending_tail<FWD>(p, p.tile_occ0[tile], p.bdd_depth[p.tile_bdd0[tile]], threadIdx.x, kBlockThreads,
                         nullptr);
     }
+    // no warp tiles: the last block finishes the previous iteration's bound
+    if (FWD && p.fin_partial && p.n_warp_blocks == 0 && blockIdx.x == gridDim.x - 1 && threadIdx.x < 32)
+      finish_bound(p.fin_partial, p.fin_nblocks, p.fin_iter, p.fin_trace, p.fin_cap, p.fin_const);
   }
+}
+
+__global__ void __launch_bounds__(32) bound_finish_kernel(const double *partial, int nblocks, int *iter_ctr,
+                                                          double *trace, int cap, double empty_const) {
+  pdl_enter();
+  finish_bound(partial, nblocks, iter_ctr, trace, cap, empty_const);
 }
 
 // the bound of the last iteration of a fused chain (no forward sweep follows to reduce it)
@@ -1180,6 +1383,10 @@ __global__ void __launch_bounds__(kReduceThreads, 8) pending_kernel(const Pendin
     __shared__ double red[kReduceThreads / 32];
     __shared__ bool last;
     const double blk = block_sum(acc, red, kReduceThreads / 32);
+    if (p.defer) {  // the next forward sweep (or a finishing kernel) sums the partials
+      if (threadIdx.x == 0) p.partial[blockIdx.x] = blk;
+      return;
+    }
     if (threadIdx.x == 0) {
       p.partial[blockIdx.x] = blk;
       __threadfence();
@@ -1263,9 +1470,9 @@ __device__ __forceinline__ void persistent_phase(const SweepParams &p, float *sm
     const GroupSmem g = group_smem(smem + group * group_floats(p.block_buf, p.block_depth_buf), p);
     for (int t = blockIdx.x * kSubBlocks + group; t < nbt; t += gridDim.x * kSubBlocks) {
       if (FWD)
-        block_forward<kUpdate>(p, ph, bt0 + t, g, group, gt, bacc);
+        block_forward<kUpdate, false>(p, ph, bt0 + t, g, group, gt, bacc);
       else
-        block_backward<kUpdate>(p, ph, bt0 + t, g, group, gt, bacc);
+        block_backward<kUpdate, false>(p, ph, bt0 + t, g, group, gt, bacc);
       group_sync(group);
     }
   }
@@ -1498,6 +1705,21 @@ int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStr
   if (grid <= 0) return 0;
   const size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf);
   int rc = 0;
+  if (p.split) {  // sub-BDDs: min-sum only, no fused pending pass
+    if (p.alpha > 0.f || mode == kUpdateFused) return -5;
+    if (mode == kUpdate && staging == 1)
+      rc = forward ? launch_pdl(sweep_kernel<true, kUpdate, false, 1, true>, grid, kBlockThreads, smem, stream, p)
+                   : launch_pdl(sweep_kernel<false, kUpdate, false, 1, true>, grid, kBlockThreads, smem, stream, p);
+#define BDD_SPLIT_SWEEP(F, M) rc = launch_pdl(sweep_kernel<F, M, false, 0, true>, grid, kBlockThreads, smem, stream, p)
+    else if (forward && mode == kUpdate) BDD_SPLIT_SWEEP(true, kUpdate);
+    else if (forward && mode == kMessages) BDD_SPLIT_SWEEP(true, kMessages);
+    else if (forward) BDD_SPLIT_SWEEP(true, kFolded);
+    else if (mode == kUpdate) BDD_SPLIT_SWEEP(false, kUpdate);
+    else if (mode == kMessages) BDD_SPLIT_SWEEP(false, kMessages);
+    else BDD_SPLIT_SWEEP(false, kFolded);
+#undef BDD_SPLIT_SWEEP
+    return rc ? rc : status();
+  }
   if (mode == kUpdate && staging == 1) {
     if (p.alpha > 0.f)
       rc = forward ? launch_pdl(sweep_kernel<true, kUpdate, true, 1>, grid, kBlockThreads, smem, stream, p)
@@ -1536,7 +1758,11 @@ int sweep_set_smem(size_t bytes) {
       (const void *)sweep_kernel<true, kUpdateFused, false>, (const void *)sweep_kernel<false, kUpdateFused, false>,
       (const void *)sweep_kernel<true, kUpdateFused, true>,  (const void *)sweep_kernel<false, kUpdateFused, true>,
       (const void *)sweep_kernel<true, kUpdate, false, 1>,   (const void *)sweep_kernel<false, kUpdate, false, 1>,
-      (const void *)sweep_kernel<true, kUpdate, true, 1>,    (const void *)sweep_kernel<false, kUpdate, true, 1>};
+      (const void *)sweep_kernel<true, kUpdate, true, 1>,    (const void *)sweep_kernel<false, kUpdate, true, 1>,
+      (const void *)sweep_kernel<true, kUpdate, false, 0, true>,   (const void *)sweep_kernel<false, kUpdate, false, 0, true>,
+      (const void *)sweep_kernel<true, kMessages, false, 0, true>, (const void *)sweep_kernel<false, kMessages, false, 0, true>,
+      (const void *)sweep_kernel<true, kFolded, false, 0, true>,   (const void *)sweep_kernel<false, kFolded, false, 0, true>,
+      (const void *)sweep_kernel<true, kUpdate, false, 1, true>,   (const void *)sweep_kernel<false, kUpdate, false, 1, true>};
   for (const void *f : fns)
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
       return -5;
@@ -1550,6 +1776,13 @@ int iterate_set_smem(size_t bytes) {
 
 int bound_launch(const SweepParams &p, int grid, cudaStream_t stream) {
   const int rc = launch_pdl(bound_kernel, grid, kReduceThreads, 0, stream, p);
+  return rc ? rc : status();
+}
+
+int bound_finish_launch(const double *partial, int nblocks, int *iter_ctr, double *trace, int cap,
+                        double empty_const, cudaStream_t stream) {
+  const int rc = launch_pdl(bound_finish_kernel, 1, 32, 0, stream, partial, nblocks, iter_ctr, trace, cap,
+                            empty_const);
   return rc ? rc : status();
 }
 
