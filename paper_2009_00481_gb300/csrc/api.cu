@@ -311,31 +311,34 @@ struct bdd_solver {
   // choice affects time only; the solver is restarted afterwards.
   int autotune(cudaStream_t s, int reps) {
     if (n_warp_tiles == 0 || reps < 1) return BDD_OK;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    for (auto &e : ev)
-      if (cudaEventCreate(&e) != cudaSuccess) return BDD_ECUDA;
-    float ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [variant][direction]
+    // events around each sweep of every iteration, read after one synchronisation per variant
+    std::vector<cudaEvent_t> ev(4 * (reps + 1), nullptr);
     int rc = BDD_OK;
+    for (auto &e : ev)
+      if (rc == BDD_OK && cudaEventCreate(&e) != cudaSuccess) rc = BDD_ECUDA;
+    float ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [variant][direction]: fastest launch
     for (int v = 0; v < 2 && rc == BDD_OK; ++v) {
       stage_fwd = stage_bwd = v;
       rc = restart(s);
       for (int it = 0; it <= reps && rc == BDD_OK; ++it) {
-        float t0 = 0.f, t1 = 0.f;
-        if (cudaEventRecord(ev[0], s) != cudaSuccess) rc = BDD_ECUDA;
+        cudaEvent_t *e = &ev[4 * it];
+        if (cudaEventRecord(e[0], s) != cudaSuccess) rc = BDD_ECUDA;
         if (rc == BDD_OK) rc = sweep(true, kUpdate, s);
-        if (rc == BDD_OK && cudaEventRecord(ev[1], s) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK && cudaEventRecord(e[1], s) != cudaSuccess) rc = BDD_ECUDA;
         if (rc == BDD_OK) rc = pending(false, s);
-        if (rc == BDD_OK && cudaEventRecord(ev[2], s) != cudaSuccess) rc = BDD_ECUDA;
-        if (rc == BDD_OK && cudaEventSynchronize(ev[2]) != cudaSuccess) rc = BDD_ECUDA;
-        if (rc == BDD_OK && cudaEventElapsedTime(&t0, ev[0], ev[1]) != cudaSuccess) rc = BDD_ECUDA;
-        if (rc == BDD_OK && cudaEventRecord(ev[0], s) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK && cudaEventRecord(e[2], s) != cudaSuccess) rc = BDD_ECUDA;
         if (rc == BDD_OK) rc = sweep(false, kUpdate, s);
-        if (rc == BDD_OK && cudaEventRecord(ev[1], s) != cudaSuccess) rc = BDD_ECUDA;
+        if (rc == BDD_OK && cudaEventRecord(e[3], s) != cudaSuccess) rc = BDD_ECUDA;
         if (rc == BDD_OK) rc = pending(true, s);
-        if (rc == BDD_OK && cudaEventSynchronize(ev[1]) != cudaSuccess) rc = BDD_ECUDA;
-        if (rc == BDD_OK && cudaEventElapsedTime(&t1, ev[0], ev[1]) != cudaSuccess) rc = BDD_ECUDA;
-        if (it == 1 || (it > 1 && t0 < ms[v][0])) ms[v][0] = t0;
-        if (it == 1 || (it > 1 && t1 < ms[v][1])) ms[v][1] = t1;
+      }
+      if (rc == BDD_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = BDD_ECUDA;
+      for (int it = 1; it <= reps && rc == BDD_OK; ++it) {  // iteration 0 warms up
+        const cudaEvent_t *e = &ev[4 * it];
+        float t0 = 0.f, t1 = 0.f;
+        if (cudaEventElapsedTime(&t0, e[0], e[1]) != cudaSuccess || cudaEventElapsedTime(&t1, e[2], e[3]) != cudaSuccess)
+          rc = BDD_ECUDA;
+        if (it == 1 || t0 < ms[v][0]) ms[v][0] = t0;
+        if (it == 1 || t1 < ms[v][1]) ms[v][1] = t1;
       }
     }
     for (auto &e : ev)

@@ -658,25 +658,35 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
 }
 
 // ---------------------------------------------------------------------------------------
-// warp tiles, 8-layer windows: each window is staged in two rounds of cp.async (node offsets,
-// multipliers, shares, slots; then arcs and messages over the node range the offsets give) and
-// processed after both have landed.  Fewer instructions per layer than the bulk-copy ring, no
-// overlap of loads with the layer recurrence; the autotuner picks between the two per solver
-// and sweep direction.  Plain updates only.
+// warp tiles, 8-layer windows: each window is staged in one round of cp.async (node offsets,
+// slots and arcs, then multipliers, shares and messages; the tile's window table gives the
+// window's node range) and processed once it has landed.  The first window's static part (node
+// offsets, slots, arcs: written once at build) is issued before the wait on the previous kernel.
+// Fewer instructions per layer than the bulk-copy ring, no overlap of loads with the layer
+// recurrence; the autotuner picks between the two per solver and sweep direction.  Update
+// sweeps only.
 // ---------------------------------------------------------------------------------------
+// One window: node offsets of occurrences [oa, oa + nox], slots and multipliers / shares of
+// [oa, oa + nob), arcs of nodes [na, nb), messages of nodes [na, nm) (bm through the layer after
+// the window for a forward update, fm for a backward sweep).  `first`: the launch's first
+// window, whose static part goes out before the dependency wait.
 template <int MODE>
-__device__ __forceinline__ void stage_occurrences_w8(const SweepParams &p, const Phase &ph, WarpStage8 &S, int oa,
-                                                  int nob, int nox, double &bacc) {
+__device__ __forceinline__ void stage_window_w8(const SweepParams &p, WarpStage8 &S, int oa, int nob, int nox,
+                                                int na, int nb, const float *msg_src, int nm, bool first) {
   const int lane = threadIdx.x & 31;
   for (int k = lane; k <= nox; k += 32) cp_async4(&S.off[k], &p.occ_node_off[oa + k]);
+  if (is_update(MODE))
+    for (int k = lane; k < nob; k += 32) cp_async4(&S.slot[k], &p.occ_slot[oa + k]);
+  for (int k = lane; k < nb - na; k += 32) cp_async8(&S.lohi[k], &p.lohi[na + k]);
+  if (first) pdl_wait();
   for (int k = lane; k < nob; k += 32) {
     cp_async4(&S.lam[k], &p.lam[oa + k]);
     if (MODE != kMessages)
       cp_async4(&S.shr[k], &p.share_occ[oa + k]);
     else
       S.shr[k] = 0.f;
-    if (is_update(MODE)) cp_async4(&S.slot[k], &p.occ_slot[oa + k]);
   }
+  for (int k = lane; k < nm - na; k += 32) cp_async4(&S.msg[k], &msg_src[na + k]);
   cp_async_wait();
 }
 
@@ -685,13 +695,8 @@ __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phas
                                              double &bacc) {
   const int lane = threadIdx.x & 31;
   const int team = lane / T, tl = lane % T, tbase = team * T;
-  const int occ0 = p.tile_occ0[tile];
-  const int bdd = p.tile_bdd0[tile] + team;
-  const bool valid = team < p.tile_nbdd[tile];
-  const int depth = valid ? p.bdd_depth[bdd] : 0;
-  const int lead_depth = tl == 0 ? depth : 0;
-  const int maxd = __reduce_max_sync(kFull, depth);
-  pdl_wait();
+  const TileInfo ti = tile_info<T>(p, tile);
+  const int occ0 = ti.occ0, depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd;
   float f_prev = inf(), lam_prev = 0.f;
   int2 lh_prev = make_int2(kNone, kNone);
   for (int l0 = 0; l0 < maxd; l0 += kWin8Layers) {
@@ -699,16 +704,14 @@ __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phas
     const int ca = occ_before(lead_depth, l0), cb = occ_before(lead_depth, l1);
     const int cx = l1 < maxd ? occ_before(lead_depth, l1 + 1) : cb;
     const int oa = occ0 + ca, nob = cb - ca, nox = cx - ca;
+    // node range of the window from the 4-layer window table: nodes at layers l0 and l1, and
+    // (a forward update reads the arcs' targets) at layer min(l0 + 9, maxd)
+    const int w4 = l0 / kWinLayers;
+    const int na = win_entry(p, ti.win0, ti.tab, w4).x;
+    const int nb = win_entry(p, ti.win0, ti.tab, min(w4 + 2, ti.nw)).x;
+    const int nc = win_entry(p, ti.win0, ti.tab, w4 + 1).y;
     __syncwarp();  // the previous window is no longer read
-    stage_occurrences_w8<MODE>(p, ph, S, oa, nob, nox, bacc);
-    __syncwarp();
-    const int na = S.off[0], nb = S.off[nob];
-    for (int k = lane; k < nb - na; k += 32) cp_async8(&S.lohi[k], &p.lohi[na + k]);
-    if (is_update(MODE)) {
-      const int nc = S.off[nox];  // through the layer after the window: the arcs' targets
-      for (int k = lane; k < nc - na; k += 32) cp_async4(&S.msg[k], &p.bm[na + k]);
-    }
-    cp_async_wait();
+    stage_window_w8<MODE>(p, S, oa, nob, nox, na, nb, p.bm, is_update(MODE) ? nc : na, l0 == 0);
     __syncwarp();
     for (int l = l0; l < l1; ++l) {
       const bool active = depth > l;
@@ -766,28 +769,21 @@ __device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Pha
                                               double &bacc) {
   const int lane = threadIdx.x & 31;
   const int team = lane / T, tl = lane % T, tbase = team * T;
-  const int occ0 = p.tile_occ0[tile];
+  const TileInfo ti = tile_info<T>(p, tile);
+  const int occ0 = ti.occ0, depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd;
   const int bdd = p.tile_bdd0[tile] + team;
-  const bool valid = team < p.tile_nbdd[tile];
-  const int depth = valid ? p.bdd_depth[bdd] : 0;
-  const int lead_depth = tl == 0 ? depth : 0;
-  const int maxd = __reduce_max_sync(kFull, depth);
-  pdl_wait();
   float b_next = inf();
   int node0_next = 0;
-  for (int l0 = ((maxd - 1) / kWin8Layers) * kWin8Layers; l0 >= 0; l0 -= kWin8Layers) {
+  const int ltop = ((maxd - 1) / kWin8Layers) * kWin8Layers;
+  for (int l0 = ltop; l0 >= 0; l0 -= kWin8Layers) {
     const int l1 = min(l0 + kWin8Layers, maxd);
     const int ca = occ_before(lead_depth, l0), cb = occ_before(lead_depth, l1);
     const int oa = occ0 + ca, nob = cb - ca;
+    const int w4 = l0 / kWinLayers;
+    const int na = win_entry(p, ti.win0, ti.tab, w4).x;
+    const int nb = win_entry(p, ti.win0, ti.tab, min(w4 + 2, ti.nw)).x;
     __syncwarp();
-    stage_occurrences_w8<MODE>(p, ph, S, oa, nob, nob, bacc);
-    __syncwarp();
-    const int na = S.off[0], nb = S.off[nob];
-    for (int k = lane; k < nb - na; k += 32) {
-      cp_async8(&S.lohi[k], &p.lohi[na + k]);
-      cp_async4(&S.msg[k], &p.fm[na + k]);
-    }
-    cp_async_wait();
+    stage_window_w8<MODE>(p, S, oa, nob, nob, na, nb, p.fm, nb, l0 == ltop);
     __syncwarp();
     for (int l = l1 - 1; l >= l0; --l) {
       const bool active = depth > l;
