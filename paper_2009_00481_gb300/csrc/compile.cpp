@@ -23,8 +23,11 @@
 // the slab layout, the slots and the outputs need no change.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <climits>
+#include <condition_variable>
 #include <cstring>
+#include <mutex>
 #include <thread>
 
 #include "bdd_dbca.h"
@@ -169,26 +172,119 @@ int compile_row(int j, const long long *row_ptr, const int *col, const int *val,
 
 }  // namespace
 
+namespace {
+
+// Host worker threads of parallel_for.  A job is published by bumping an atomic generation;
+// workers spin on it for a short while after each job (the calls of one build come in quick
+// succession), then sleep on a condition variable.  Each takes chunks of the job from a shared
+// atomic cursor and checks out when none are left; the caller works too and returns once every
+// worker has checked out, so a job's fields never change under a worker.
+class HostPool {
+ public:
+  static HostPool &get() {
+    static HostPool pool;
+    return pool;
+  }
+  bool run(long long n, long long grain, const std::function<void(long long, long long)> &body) {
+    std::unique_lock<std::mutex> busy(job_mu_, std::try_to_lock);
+    if (!busy.owns_lock() || workers_.empty()) return false;
+    body_ = &body;
+    n_ = n;
+    grain_ = grain;
+    next_.store(0, std::memory_order_relaxed);
+    active_.store((int)workers_.size(), std::memory_order_relaxed);
+    {
+      std::lock_guard<std::mutex> lk(mu_);  // a worker about to sleep sees the new generation
+      gen_.fetch_add(1, std::memory_order_release);
+    }
+    cv_.notify_all();
+    work();
+    while (active_.load(std::memory_order_acquire) != 0) std::this_thread::yield();
+    body_ = nullptr;
+    return true;
+  }
+
+ private:
+  HostPool() {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int extra = (int)std::min(hw ? hw : 1u, 64u) - 1;
+    for (int t = 0; t < extra; ++t) workers_.emplace_back([this] { loop(); });
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_.store(true);
+      gen_.fetch_add(1, std::memory_order_release);
+    }
+    cv_.notify_all();
+    for (auto &w : workers_) w.join();
+  }
+  void work() {
+    for (;;) {
+      const long long b = next_.fetch_add(grain_, std::memory_order_relaxed);
+      if (b >= n_) break;
+      (*body_)(b, std::min(n_, b + grain_));
+    }
+  }
+  void loop() {
+    unsigned long long seen = 0;
+    for (;;) {
+      const auto t0 = std::chrono::steady_clock::now();
+      unsigned spins = 0;
+      while (gen_.load(std::memory_order_acquire) == seen) {
+        if ((++spins & 255) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(500)) {
+          std::unique_lock<std::mutex> lk(mu_);
+          cv_.wait(lk, [&] { return gen_.load(std::memory_order_acquire) != seen; });
+        }
+      }
+      seen = gen_.load(std::memory_order_acquire);
+      if (stop_.load()) return;
+      work();
+      active_.fetch_sub(1, std::memory_order_release);
+    }
+  }
+  std::vector<std::thread> workers_;
+  std::mutex job_mu_, mu_;
+  std::condition_variable cv_;
+  const std::function<void(long long, long long)> *body_ = nullptr;
+  long long n_ = 0, grain_ = 1;
+  std::atomic<long long> next_{0};
+  std::atomic<int> active_{0};
+  std::atomic<unsigned long long> gen_{0};
+  std::atomic<bool> stop_{false};
+};
+
+}  // namespace
+
+void parallel_for(long long n, long long grain, const std::function<void(long long, long long)> &body) {
+  if (n <= 0) return;
+  grain = std::max(1LL, grain);
+  if (n <= grain || !HostPool::get().run(n, grain, body)) body(0, n);
+}
+
+namespace {
+
+template <class Tp>
+void copy_into(std::vector<Tp> &out, size_t off, const std::vector<Tp> &v) {
+  if (!v.empty()) std::memcpy(out.data() + off, v.data(), v.size() * sizeof(Tp));
+}
+
+}  // namespace
+
 int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const int *val,
                  const int *b, const signed char *sense, const int *rank, int max_width,
                  long long max_nodes, HostBDDs *H, int *failed_row) {
   *failed_row = -1;
-  const int rows_per_chunk = 2048;
+  const int rows_per_chunk = 512;
   const int nchunks = (m + rows_per_chunk - 1) / rows_per_chunk;
   std::vector<Chunk> chunks(nchunks);
-  std::atomic<int> next(0);
-  unsigned hw = std::thread::hardware_concurrency();
-  int nthreads = (int)std::max(1u, std::min(hw ? hw : 1u, 64u));
-  nthreads = std::min(nthreads, std::max(1, nchunks));
-  auto worker = [&]() {
+  parallel_for(nchunks, 1, [&](long long c0, long long c1) {
     Scratch sc;
-    for (;;) {
-      int cidx = next.fetch_add(1);
-      if (cidx >= nchunks) break;
+    for (long long cidx = c0; cidx < c1; ++cidx) {
       Chunk &ch = chunks[cidx];
-      int r0 = cidx * rows_per_chunk, r1 = std::min(m, r0 + rows_per_chunk);
+      const int r0 = (int)cidx * rows_per_chunk, r1 = std::min(m, r0 + rows_per_chunk);
       for (int j = r0; j < r1; ++j) {
-        int rc = compile_row(j, row_ptr, col, val, rank, n, b[j], sense[j], max_width, sc, ch);
+        const int rc = compile_row(j, row_ptr, col, val, rank, n, b[j], sense[j], max_width, sc, ch);
         if (rc != BDD_OK) {
           ch.status = rc;
           ch.failed_row = j;
@@ -196,44 +292,47 @@ int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const i
         }
       }
     }
-  };
-  std::vector<std::thread> pool;
-  for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
-  worker();
-  for (auto &th : pool) th.join();
+  });
   for (auto &ch : chunks)
     if (ch.status != BDD_OK) {
       *failed_row = ch.failed_row;
       return ch.status;
     }
-  // concatenate in row order
+  // concatenate in row order (each chunk's part copied in parallel)
   size_t nb = 0, O = 0, N = 0;
-  for (auto &ch : chunks) {
-    nb += ch.bdd_row.size();
-    O += ch.occ_var.size();
-    N += ch.lo.size();
+  std::vector<size_t> off_b(nchunks), off_o(nchunks), off_n(nchunks);
+  for (int c = 0; c < nchunks; ++c) {
+    off_b[c] = nb;
+    off_o[c] = O;
+    off_n[c] = N;
+    nb += chunks[c].bdd_row.size();
+    O += chunks[c].occ_var.size();
+    N += chunks[c].lo.size();
   }
   if ((long long)N > max_nodes || N >= (size_t)INT_MAX || O >= (size_t)INT_MAX) return BDD_ETOOBIG;
   H->n = n;
   H->m = m;
   H->nnz = m ? row_ptr[m] : 0;
-  H->bdd_row.reserve(nb);
-  H->bdd_depth.reserve(nb);
-  H->occ_var.reserve(O);
-  H->occ_csr.reserve(O);
-  H->occ_width.reserve(O);
-  H->lo.reserve(N);
-  H->hi.reserve(N);
-  for (auto &ch : chunks) {
-    H->bdd_row.insert(H->bdd_row.end(), ch.bdd_row.begin(), ch.bdd_row.end());
-    H->bdd_depth.insert(H->bdd_depth.end(), ch.bdd_depth.begin(), ch.bdd_depth.end());
-    H->occ_var.insert(H->occ_var.end(), ch.occ_var.begin(), ch.occ_var.end());
-    H->occ_csr.insert(H->occ_csr.end(), ch.occ_csr.begin(), ch.occ_csr.end());
-    H->occ_width.insert(H->occ_width.end(), ch.occ_width.begin(), ch.occ_width.end());
-    H->lo.insert(H->lo.end(), ch.lo.begin(), ch.lo.end());
-    H->hi.insert(H->hi.end(), ch.hi.begin(), ch.hi.end());
-    ch = Chunk();  // release the chunk's memory as soon as it is copied
-  }
+  H->bdd_row.resize(nb);
+  H->bdd_depth.resize(nb);
+  H->occ_var.resize(O);
+  H->occ_csr.resize(O);
+  H->occ_width.resize(O);
+  H->lo.resize(N);
+  H->hi.resize(N);
+  parallel_for(nchunks, 1, [&](long long c0, long long c1) {
+    for (long long c = c0; c < c1; ++c) {
+      const Chunk &ch = chunks[c];
+      copy_into(H->bdd_row, off_b[c], ch.bdd_row);
+      copy_into(H->bdd_depth, off_b[c], ch.bdd_depth);
+      copy_into(H->occ_var, off_o[c], ch.occ_var);
+      copy_into(H->occ_csr, off_o[c], ch.occ_csr);
+      copy_into(H->occ_width, off_o[c], ch.occ_width);
+      copy_into(H->lo, off_n[c], ch.lo);
+      copy_into(H->hi, off_n[c], ch.hi);
+    }
+  });
+  chunks.clear();
   H->bdd_occ0.assign(nb + 1, 0);
   for (size_t t = 0; t < nb; ++t) {
     H->bdd_occ0[t + 1] = H->bdd_occ0[t] + H->bdd_depth[t];
@@ -291,7 +390,8 @@ int build_layout(const HostBDDs &H, Layout *L) {
   L->class_tile_off[kWarpClasses + 1] = (int)L->tile_bdd0.size();
   L->n_warp_tiles = L->class_tile_off[kWarpClasses];
   L->n_block_tiles = L->class_tile_off[kWarpClasses + 1] - L->class_tile_off[kWarpClasses];
-  // occurrences and nodes in tile order
+  // occurrences and nodes in tile order: per-tile counts and their prefix sums, then every tile
+  // filled on its own (a tile's slab is one contiguous range)
   const long long ntiles = (long long)L->tile_bdd0.size();
   L->tile_occ0.resize(ntiles);
   L->occ_of_canon.assign(O, -1);
@@ -299,45 +399,67 @@ int build_layout(const HostBDDs &H, Layout *L) {
   L->occ_var.assign(O, 0);
   L->occ_csr.assign(O, 0);
   std::vector<long long> node_of_canon_occ(O, 0);  // device first node of each canonical occurrence
-  long long dev_o = 0, dev_node = 0;
-  L->max_block_width = 0;
-  for (long long t = 0; t < ntiles; ++t) {
-    L->tile_occ0[t] = (int)dev_o;
-    const int b0 = L->tile_bdd0[t], nt = L->tile_nbdd[t];
-    const int dmax = L->bdd_depth[b0];  // first BDD of a tile is the deepest
-    for (int l = 0; l < dmax; ++l) {
+  std::vector<long long> tile_node0(ntiles + 1, 0);
+  {
+    long long o = 0, v = 0;
+    for (long long t = 0; t < ntiles; ++t) {
+      L->tile_occ0[t] = (int)o;
+      tile_node0[t] = v;
+      const int b0 = L->tile_bdd0[t], nt = L->tile_nbdd[t];
       for (int q = 0; q < nt; ++q) {
         const int cb = L->bdd_perm[b0 + q];
-        if (H.bdd_depth[cb] <= l) break;  // depths are non-increasing inside the tile
-        const long long co = H.bdd_occ0[cb] + l;
-        L->occ_of_canon[co] = (int)dev_o;
-        L->occ_node_off[dev_o] = (int)dev_node;
-        L->occ_var[dev_o] = H.occ_var[co];
-        L->occ_csr[dev_o] = H.occ_csr[co];
-        node_of_canon_occ[co] = dev_node;
-        dev_node += H.occ_width[co];
-        if (cls[cb] == kWarpClasses) L->max_block_width = std::max(L->max_block_width, H.occ_width[co]);
-        ++dev_o;
+        o += H.bdd_depth[cb];
+        v += H.occ_node0[H.bdd_occ0[cb + 1]] - H.occ_node0[H.bdd_occ0[cb]];
       }
     }
+    tile_node0[ntiles] = v;
+    if (o != O || v != N) return BDD_EINVAL;
   }
-  L->occ_node_off[O] = (int)dev_node;
-  if (dev_o != O || dev_node != N) return BDD_EINVAL;
+  parallel_for(ntiles, 64, [&](long long t0, long long t1) {
+    for (long long t = t0; t < t1; ++t) {
+      long long dev_o = L->tile_occ0[t], dev_node = tile_node0[t];
+      const int b0 = L->tile_bdd0[t], nt = L->tile_nbdd[t];
+      const int dmax = L->bdd_depth[b0];  // first BDD of a tile is the deepest
+      for (int l = 0; l < dmax; ++l) {
+        for (int q = 0; q < nt; ++q) {
+          const int cb = L->bdd_perm[b0 + q];
+          if (H.bdd_depth[cb] <= l) break;  // depths are non-increasing inside the tile
+          const long long co = H.bdd_occ0[cb] + l;
+          L->occ_of_canon[co] = (int)dev_o;
+          L->occ_node_off[dev_o] = (int)dev_node;
+          L->occ_var[dev_o] = H.occ_var[co];
+          L->occ_csr[dev_o] = H.occ_csr[co];
+          node_of_canon_occ[co] = dev_node;
+          dev_node += H.occ_width[co];
+          ++dev_o;
+        }
+      }
+    }
+  });
+  L->occ_node_off[O] = (int)N;
+  L->max_block_width = 0;  // widest layer of a block tile
+  for (long long t = L->class_tile_off[kWarpClasses]; t < ntiles; ++t) {
+    const int cb = L->bdd_perm[L->tile_bdd0[t]];
+    for (long long co = H.bdd_occ0[cb]; co < H.bdd_occ0[cb + 1]; ++co)
+      L->max_block_width = std::max(L->max_block_width, H.occ_width[co]);
+  }
   // successors as global device node ids
   L->lohi.assign(2 * N, 0);
-  for (long long b = 0; b < nb; ++b) {
-    for (long long co = H.bdd_occ0[b]; co < H.bdd_occ0[b + 1]; ++co) {
-      const bool last = co + 1 == H.bdd_occ0[b + 1];
-      const long long next0 = last ? 0 : node_of_canon_occ[co + 1];
-      const long long d0 = node_of_canon_occ[co];
-      for (int q = 0; q < H.occ_width[co]; ++q) {
-        const long long cn = H.occ_node0[co] + q;
-        const int lo = H.lo[cn], hi = H.hi[cn];
-        L->lohi[2 * (d0 + q)] = lo >= 0 ? (int)(next0 + lo) : lo;
-        L->lohi[2 * (d0 + q) + 1] = hi >= 0 ? (int)(next0 + hi) : hi;
+  parallel_for(nb, 256, [&](long long b0, long long b1) {
+    for (long long b = b0; b < b1; ++b) {
+      for (long long co = H.bdd_occ0[b]; co < H.bdd_occ0[b + 1]; ++co) {
+        const bool last = co + 1 == H.bdd_occ0[b + 1];
+        const long long next0 = last ? 0 : node_of_canon_occ[co + 1];
+        const long long d0 = node_of_canon_occ[co];
+        for (int q = 0; q < H.occ_width[co]; ++q) {
+          const long long cn = H.occ_node0[co] + q;
+          const int lo = H.lo[cn], hi = H.hi[cn];
+          L->lohi[2 * (d0 + q)] = lo >= 0 ? (int)(next0 + lo) : lo;
+          L->lohi[2 * (d0 + q) + 1] = hi >= 0 ? (int)(next0 + hi) : hi;
+        }
       }
     }
-  }
+  });
   // window table of every warp tile: node offsets at layer w * kWinLayers and at layer
   // min((w + 1) * kWinLayers + 1, maxd), w = 0 .. ceil(maxd / kWinLayers)
   L->tile_win0.assign(ntiles + 1, 0);

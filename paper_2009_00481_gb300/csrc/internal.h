@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 namespace bdd {
@@ -60,6 +61,12 @@ std::vector<int> balanced_cuts(const HostBDDs &H, const int *rank, int k);
 // keeps the row); the arcs of the last layer before a cut become copy codes kCopy0 - k.
 // Returns a BDD_* status.
 int split_bdds(HostBDDs &H, const int *rank, const std::vector<int> &cuts, int depth, CopyPairs *P);
+
+// Runs body(begin, end) over [0, n) in chunks of `grain` items, on the library's host worker
+// threads (created on first use, one per hardware thread but the caller's, kept until the
+// process exits) together with the calling thread.  One job runs on the workers at a time; a
+// call that finds them busy (a solver being built on another host thread) runs inline.
+void parallel_for(long long n, long long grain, const std::function<void(long long, long long)> &body);
 
 // Compiles every row (threshold counting over suffix-sum sets; see compile.cpp).
 // Returns a BDD_* status; *failed_row is the row that failed, or -1.
