@@ -252,3 +252,36 @@ def test_split_refuses_part_bounds(lib):
     with pytest.raises(BDDError) as e:
         s.bound_parts([0, inst.m], [0, inst.n])
     assert e.value.code == BDD_EINVAL
+
+
+def test_split_wide_block_tiles(lib):
+    """Layers wider than 128 nodes take the general block-tile path (several nodes per thread):
+    a 300-variable cardinality row in pieces of at most 60 layers, plus narrow rows, against the
+    oracle's split; pieces bit-exact, bound trace and same-state min-marginals."""
+    from instances.generators import _from_rows
+    from instances import SENSE_LE
+    rng = np.random.default_rng(3)
+    rows = [(np.arange(300), np.ones(300), 149, SENSE_LE)]
+    for k in [2, 3, 5, 9, 17, 33, 40, 70]:
+        cols = np.sort(rng.choice(300, size=k, replace=False))
+        rows.append((cols, np.ones(k), k // 2, SENSE_LE))
+    inst = _from_rows("wide", 300, rows, rng.normal(size=300).astype(np.float32))
+    s = solver(inst, split_depth=60)
+    o = Oracle(inst)
+    o.split_depth(60)
+    assert s.block_tiles >= 1 and s.max_width > 128 and s.npairs == o.npairs > 0
+    got, want = s.canonical(), o.canonical()
+    for key in KEYS:
+        np.testing.assert_array_equal(got[key], want[key], err_msg=key)
+    close(_trace(s, 40), o.run_parallel(40, omega=0.5), LB_TOL)
+    lam = rng.normal(0, 1, size=inst.nnz).astype(np.float32)
+    mb = rng.normal(0, 0.5, size=s.npairs).astype(np.float32)
+    mu = (-mb - np.abs(rng.normal(0, 0.5, size=s.npairs))).astype(np.float32)
+    s.set_state(lam)
+    s.set_copy_duals(mb, mu)
+    o.set_state(lam.astype(np.float64))
+    o.set_copy_duals(mb.astype(np.float64), mu.astype(np.float64))
+    _, _, m0, m1 = s.iterate(0, mm=True)
+    e0, e1 = o.min_marginals(fold=True)
+    close(m0, e0, MM_TOL)
+    close(m1, e1, MM_TOL)
