@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--schedule", type=int, default=1, help="1 per-phase graphs (default), 0 persistent kernel")
     ap.add_argument("--staging", type=int, default=-1,
                     help="warp-tile staging of the update sweeps: -1 autotuned (default), 0 bulk-copy ring, "
-                         "1 8-layer cp.async windows")
+                         "1 8-layer cp.async windows, 2 the same double-buffered")
     ap.add_argument("--batch-count", type=int, default=256, help="instances in the batch workload")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--batch-warmup", type=int, default=2)
@@ -90,12 +90,13 @@ def algorithmic_bytes(kind: str, N: int, O: int, n: int, nb: int) -> int:
     raise ValueError(kind)
 
 
-STAGING = {0: "bulk-copy ring, 4-layer windows", 1: "8-layer cp.async windows"}
+STAGING = {0: "bulk-copy ring, 4-layer windows", 1: "8-layer cp.async windows",
+           2: "double-buffered 8-layer cp.async windows"}
 
 
 def staging_of(s) -> dict:
     """Warp-tile staging the solver's autotuner chose for each update sweep."""
-    return {"forward": STAGING[s.staging & 1], "backward": STAGING[(s.staging >> 1) & 1]}
+    return {"forward": STAGING[s.staging & 3], "backward": STAGING[(s.staging >> 2) & 3]}
 
 
 def sweep_kernel_name(kind: str, s) -> str:

@@ -101,11 +101,13 @@ typedef struct {
                                  order. */
   int staging;                /* warp-tile window staging of the update sweeps.  0: bulk-copy
                                  (TMA) ring, 4-layer windows, the next window loading while one
-                                 is processed; 1: 8-layer windows in two rounds of cp.async.
-                                 -1 (default): the autotuner times both at build (schedule 1: a
-                                 warm-up and six iterations each, kernel by kernel, the fastest
-                                 launch of each sweep counted) and keeps
-                                 the faster per sweep direction.  The variants compute identical
+                                 is processed; 1: 8-layer windows, each loaded by cp.async in one
+                                 round and then processed; 2: the same with two buffers per warp,
+                                 the next window loading while one is processed (twice the shared
+                                 memory of 1).  -1 (default): the autotuner times all three at
+                                 build (schedule 1: a warm-up and six iterations each, kernel by
+                                 kernel, the fastest launch of each sweep counted) and keeps the
+                                 fastest per sweep direction.  The variants compute identical
                                  values; the persistent schedule and other sweeps use 0. */
   int split_intervals;        /* sub-BDDs (Sec. 6, Def. of sub-BDDs and copy-arcs; the parallel
                                  min-marginal averaging algorithm).  0 or 1 (default): no split.
@@ -217,9 +219,10 @@ int bdd_set_costs(bdd_solver *h, const float *c);
 /* Sizes: out[0] n, [1] m, [2] BDDs (pieces of a split solver), [3] occurrences (nonzeros
  * kept), [4] nodes, [5] max depth, [6] max width, [7] nnz, [8] device bytes held, [9] warp
  * tiles, [10] block tiles, [11] schedule in use (0 persistent, 1 per-phase graphs), [12]
- * warp-tile staging the autotuner chose for the update sweeps: bit 0 forward, bit 1 backward
- * (0 bulk-copy ring of 4-layer windows, 1 8-layer cp.async windows), [13] cuts of the variable
- * order, [14] copy-arc pairs, [15] depth limit of a depth split (0: none). */
+ * warp-tile staging the autotuner chose for the update sweeps: bits 0-1 forward, bits 2-3 backward
+ * (0 bulk-copy ring of 4-layer windows, 1 8-layer cp.async windows, 2 the same
+ * double-buffered), [13] cuts of the variable order, [14] copy-arc pairs, [15] depth limit of a
+ * depth split (0: none). */
 int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]);
 
 /* Canonical form of the BDDs, read back from the device slabs (or the host copy when built

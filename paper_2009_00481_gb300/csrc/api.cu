@@ -97,7 +97,7 @@ struct bdd_solver {
   int averaging = 0;                     // 0: eq. mma-update; 1: SRMP (Appendix A.4)
   int stage_fwd = 0, stage_bwd = 0;      // warp-tile staging of the update sweeps (autotuned)
   int staging_opt = -1;                  // bdd_options.staging
-  float tune_ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // measured ms per sweep [variant][direction]
+  float tune_ms[kStagings][2] = {};      // measured ms per sweep [variant][direction]
   bool fused = false;                    // per-phase plan: pending pass fused into the sweeps
   int fused_opt = -1;                    // bdd_options.fused_pending
   int *d_cnt = nullptr;                  // [n] fused plan: visits still to come per variable
@@ -316,8 +316,8 @@ struct bdd_solver {
     int rc = BDD_OK;
     for (auto &e : ev)
       if (rc == BDD_OK && cudaEventCreate(&e) != cudaSuccess) rc = BDD_ECUDA;
-    float ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [variant][direction]: fastest launch
-    for (int v = 0; v < 2 && rc == BDD_OK; ++v) {
+    float ms[kStagings][2] = {};  // [variant][direction]: fastest launch
+    for (int v = 0; v < kStagings && rc == BDD_OK; ++v) {
       stage_fwd = stage_bwd = v;
       rc = restart(s);
       for (int it = 0; it <= reps && rc == BDD_OK; ++it) {
@@ -348,9 +348,12 @@ struct bdd_solver {
       stage_fwd = stage_bwd = 0;
       return rc;
     }
-    stage_fwd = ms[1][0] < ms[0][0] ? 1 : 0;
-    stage_bwd = ms[1][1] < ms[0][1] ? 1 : 0;
-    for (int v = 0; v < 2; ++v)
+    stage_fwd = stage_bwd = 0;
+    for (int v = 1; v < kStagings; ++v) {
+      if (ms[v][0] < ms[stage_fwd][0]) stage_fwd = v;
+      if (ms[v][1] < ms[stage_bwd][1]) stage_bwd = v;
+    }
+    for (int v = 0; v < kStagings; ++v)
       for (int d = 0; d < 2; ++d) tune_ms[v][d] = ms[v][d];
     return restart(s);
   }
@@ -591,7 +594,9 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c, const CutTables
   for (int i = 0; i < h->n; ++i) n_heavy += L.var_ptr[i + 1] - L.var_ptr[i] > h->heavy_deg;
   const int heavy_blocks = (n_heavy + kReduceThreads / 32 - 1) / (kReduceThreads / 32);
   h->grid_reduce = std::max(1, std::min(std::max((range + kReduceThreads - 1) / kReduceThreads, heavy_blocks), 152 * 16));
-  h->smem = sweep_smem_bytes(h->block_buf, h->block_depth_buf);
+  // the largest dynamic shared memory any staging variant's sweep launch asks for
+  h->smem = std::max(sweep_smem_bytes(h->block_buf, h->block_depth_buf, 0),
+                     sweep_smem_bytes(h->block_buf, h->block_depth_buf, 2));
   h->smem_persist = persist_smem_bytes(h->block_buf, h->block_depth_buf);
   if (h->smem > 48 * 1024 && sweep_set_smem(h->smem)) return BDD_ECUDA;
   if (h->schedule == 0) {
@@ -772,7 +777,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   if (!finite_costs(c, n)) return BDD_EINVAL;
   if (opt.averaging < 0 || opt.averaging > 1) return BDD_EINVAL;
   if (opt.fused_pending < -1 || opt.fused_pending > 1) return BDD_EINVAL;
-  if (opt.staging < -1 || opt.staging > 1) return BDD_EINVAL;
+  if (opt.staging < -1 || opt.staging >= kStagings) return BDD_EINVAL;
   if (opt.split_intervals < 0 || opt.n_cuts < 0 || (opt.n_cuts > 0 && !opt.cuts) || opt.split_depth < 0)
     return BDD_EINVAL;
   if (!(opt.gamma > 0.f && opt.gamma <= 1.f)) return BDD_EINVAL;
@@ -1203,7 +1208,7 @@ int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]) {
   out[9] = h->n_warp_tiles;
   out[10] = h->n_block_tiles;
   out[11] = h->schedule;
-  out[12] = h->stage_fwd | (h->stage_bwd << 1);
+  out[12] = h->stage_fwd | (h->stage_bwd << 2);
   out[13] = (long long)h->cuts.size();
   out[14] = h->npairs;
   out[15] = h->split_depth;

@@ -122,9 +122,13 @@ struct alignas(16) WarpStage8 {
   float shr[kWin8Occ];
   int slot[kWin8Occ];
 };
-// shared memory of one warp: the larger of the two staging variants
+// shared memory of one warp: the larger of the bulk-copy ring and one 8-layer window (staging
+// variants 0 and 1); two 8-layer windows for the double-buffered variant 2, whose launches get
+// their own shared-memory size
 constexpr size_t kWarpSmemBytes = (kWarpStages * sizeof(WarpStage) > sizeof(WarpStage8) ? kWarpStages * sizeof(WarpStage)
                                                                                           : sizeof(WarpStage8));
+constexpr size_t kWarpSmemBytes2 = 2 * sizeof(WarpStage8);
+constexpr int kStagings = 3;  // warp-tile staging variants of the update sweeps
 
 // Device slab layout (host staging copy).  Occurrences are grouped by tile; inside a warp
 // tile they are layer-major (layer l of every tile BDD still alive at l, in tile order; the
@@ -333,12 +337,12 @@ int cut_launch(bool forward, const CutParams &c, cudaStream_t stream);
 int cut_roots_launch(const CutParams &c, cudaStream_t stream);
 
 // Launch wrappers (kernels.cu).  All enqueue on `stream` and return 0 or -5 (launch failure).
-size_t sweep_smem_bytes(int block_buf, int block_depth_buf);
+size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging = 0);
 size_t persist_smem_bytes(int block_buf, int block_depth_buf);
 int sweep_set_smem(size_t bytes);
 int iterate_set_smem(size_t bytes);
 // staging: warp-tile window staging of a plain update sweep (0: bulk-copy ring, 1: 8-layer
-// cp.async windows); other modes always use the ring
+// cp.async windows, 2: the same double-buffered); other modes always use the ring
 int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStream_t stream, int staging = 0);
 int pending_launch(bool bound, const PendingParams &p, int grid, cudaStream_t stream);
 // FP64 bound from the E^j and slack terms of the last fused backward sweep into trace[*iter_ctr]

@@ -77,6 +77,10 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Programmatic dependent launch: the per-phase kernels are launched so that the next kernel of
 // the chain may start while this one drains; each kernel waits here for its predecessor to
@@ -121,6 +125,33 @@ __device__ __forceinline__ double slack_term(double P, double alpha) {
   return m - alpha * log1p(exp(-fabs(P) / alpha));
 }
 
+// the general path of pending_var for slots [s, e) of variable i
+__device__ __forceinline__ float pending_tail_sum(const float *__restrict__ delta, const int *__restrict__ var_occ,
+                                                  float *__restrict__ P, float *__restrict__ share_occ, int i, int s,
+                                                  int e, const unsigned char *__restrict__ slot_dir, int dir) {
+  const float Pi = slot_sum(delta, s, e);
+  P[i] = Pi;
+  if (slot_dir) {
+    int cnt = 0;
+    for (int k = s; k < e; ++k) cnt += (slot_dir[k] & dir) != 0;
+    if (cnt > 0) {
+      const float share = Pi / (float)cnt;
+      for (int k = s; k < e; ++k) share_occ[var_occ[k]] = (slot_dir[k] & dir) ? share : 0.f;
+      return Pi;
+    }
+  }
+  const float share = Pi / (float)(e - s);
+  for (int k = s; k < e; k += 8) {  // occurrence ids eight at a time, then the stores
+    int o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o[j] = k + j < e ? var_occ[k + j] : -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (o[j] >= 0) share_occ[o[j]] = share;
+  }
+  return Pi;
+}
+
 // Pending sums (the sum in eq. mma-update, deferred): P_i = sum of i's slots in ascending
 // order, stored, and share_i = P_i / |J_i| written to each of i's occurrences for the next sweep.
 // With SRMP bits (Appendix A.4), P_i / |J_i^dir| to the slots in J_i^dir and 0 to the others,
@@ -129,12 +160,12 @@ __device__ __forceinline__ double slack_term(double P, double alpha) {
 // ids and SRMP bits together); FAST = 0: slot_sum, then the occurrence ids eight at a time.
 // SKIP_HEAVY: variables with more than heavy_deg occurrences are left to pending_var_warp
 // (has = false for them).
+// (pending_var_se: the same for a variable whose slot range [s, e) the caller has loaded)
 template <int FAST, bool SKIP_HEAVY = false>
-__device__ __forceinline__ float pending_var(const float *__restrict__ delta, const int *__restrict__ var_ptr,
-                                             const int *__restrict__ var_occ, float *__restrict__ P,
-                                             float *__restrict__ share_occ, int i, bool &has,
-                                             const unsigned char *__restrict__ slot_dir, int dir, int heavy_deg = 0) {
-  const int s = var_ptr[i], e = var_ptr[i + 1];
+__device__ __forceinline__ float pending_var_se(const float *__restrict__ delta, const int *__restrict__ var_occ,
+                                                float *__restrict__ P, float *__restrict__ share_occ, int i, int s,
+                                                int e, bool &has, const unsigned char *__restrict__ slot_dir, int dir,
+                                                int heavy_deg = 0) {
   has = e > s && (!SKIP_HEAVY || e - s <= heavy_deg);
   if (!has) return 0.f;
   const int deg = e - s;
@@ -164,27 +195,16 @@ __device__ __forceinline__ float pending_var(const float *__restrict__ delta, co
       if (j < deg) share_occ[o[j]] = (cnt == 0 || (d[j] & dir)) ? share : 0.f;
     return Pi;
   }
-  const float Pi = slot_sum(delta, s, e);
-  P[i] = Pi;
-  if (slot_dir) {
-    int cnt = 0;
-    for (int k = s; k < e; ++k) cnt += (slot_dir[k] & dir) != 0;
-    if (cnt > 0) {
-      const float share = Pi / (float)cnt;
-      for (int k = s; k < e; ++k) share_occ[var_occ[k]] = (slot_dir[k] & dir) ? share : 0.f;
-      return Pi;
-    }
-  }
-  const float share = Pi / (float)(e - s);
-  for (int k = s; k < e; k += 8) {  // occurrence ids eight at a time, then the stores
-    int o[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) o[j] = k + j < e ? var_occ[k + j] : -1;
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (o[j] >= 0) share_occ[o[j]] = share;
-  }
-  return Pi;
+  return pending_tail_sum(delta, var_occ, P, share_occ, i, s, e, slot_dir, dir);
+}
+
+template <int FAST, bool SKIP_HEAVY = false>
+__device__ __forceinline__ float pending_var(const float *__restrict__ delta, const int *__restrict__ var_ptr,
+                                             const int *__restrict__ var_occ, float *__restrict__ P,
+                                             float *__restrict__ share_occ, int i, bool &has,
+                                             const unsigned char *__restrict__ slot_dir, int dir, int heavy_deg = 0) {
+  return pending_var_se<FAST, SKIP_HEAVY>(delta, var_occ, P, share_occ, i, var_ptr[i], var_ptr[i + 1], has, slot_dir,
+                                          dir, heavy_deg);
 }
 
 // The same pending sum and shares for one variable with many occurrences (slots [s, e)), by a
@@ -671,7 +691,7 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
 // the window for a forward update, fm for a backward sweep).  `first`: the launch's first
 // window, whose static part goes out before the dependency wait.
 template <int MODE>
-__device__ __forceinline__ void stage_window_w8(const SweepParams &p, WarpStage8 &S, int oa, int nob, int nox,
+__device__ __forceinline__ void issue_window_w8(const SweepParams &p, WarpStage8 &S, int oa, int nob, int nox,
                                                 int na, int nb, const float *msg_src, int nm, bool first) {
   const int lane = threadIdx.x & 31;
   for (int k = lane; k <= nox; k += 32) cp_async4(&S.off[k], &p.occ_node_off[oa + k]);
@@ -687,33 +707,73 @@ __device__ __forceinline__ void stage_window_w8(const SweepParams &p, WarpStage8
       S.shr[k] = 0.f;
   }
   for (int k = lane; k < nm - na; k += 32) cp_async4(&S.msg[k], &msg_src[na + k]);
+}
+
+template <int MODE>
+__device__ __forceinline__ void stage_window_w8(const SweepParams &p, WarpStage8 &S, int oa, int nob, int nox,
+                                                int na, int nb, const float *msg_src, int nm, bool first) {
+  issue_window_w8<MODE>(p, S, oa, nob, nox, na, nb, msg_src, nm, first);
   cp_async_wait();
 }
 
-template <int T, int MODE, bool SMOOTH, bool SPLIT>
-__device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phase &ph, int tile, WarpStage8 &S,
+// Geometry of 8-layer window k of a warp tile: layers [l0, l1), occurrences [ca, cb) relative to
+// the tile (cx: through the layer after the window), nodes [na, nb) and, for a forward update,
+// through the layer after the window, nc.  Node ranges come from the tile's 4-layer window table.
+// Warp-collective (every lane calls it with the same k).
+struct Win8 {
+  int l0, l1, ca, oa, nob, nox, na, nb, nc;
+};
+__device__ __forceinline__ Win8 win8_of(const SweepParams &p, const TileInfo &ti, int lead_depth, int k) {
+  Win8 g;
+  g.l0 = k * kWin8Layers;
+  g.l1 = min(g.l0 + kWin8Layers, ti.maxd);
+  g.ca = occ_before(lead_depth, g.l0);
+  const int cb = occ_before(lead_depth, g.l1);
+  const int cx = g.l1 < ti.maxd ? occ_before(lead_depth, g.l1 + 1) : cb;
+  g.oa = ti.occ0 + g.ca;
+  g.nob = cb - g.ca;
+  g.nox = cx - g.ca;
+  const int w4 = g.l0 / kWinLayers;
+  g.na = win_entry(p, ti.win0, ti.tab, w4).x;
+  g.nb = win_entry(p, ti.win0, ti.tab, min(w4 + 2, ti.nw)).x;
+  g.nc = win_entry(p, ti.win0, ti.tab, w4 + 1).y;  // node at layer min(l0 + 9, maxd)
+  return g;
+}
+
+// NBUF = 1: each window is loaded, then processed (staging variant 1).  NBUF = 2: two buffers per
+// warp, window k + 1's copies in flight (one cp.async group per window) while window k is
+// processed (staging variant 2).
+template <int T, int MODE, bool SMOOTH, bool SPLIT, int NBUF>
+__device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phase &ph, int tile, WarpStage8 *SB,
                                              double &bacc) {
   const int lane = threadIdx.x & 31;
   const int team = lane / T, tl = lane % T, tbase = team * T;
   const TileInfo ti = tile_info<T>(p, tile);
-  const int occ0 = ti.occ0, depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd;
+  const int depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd;
+  const int nwin = (maxd + kWin8Layers - 1) / kWin8Layers;
   float f_prev = inf(), lam_prev = 0.f;
   int2 lh_prev = make_int2(kNone, kNone);
-  for (int l0 = 0; l0 < maxd; l0 += kWin8Layers) {
-    const int l1 = min(l0 + kWin8Layers, maxd);
-    const int ca = occ_before(lead_depth, l0), cb = occ_before(lead_depth, l1);
-    const int cx = l1 < maxd ? occ_before(lead_depth, l1 + 1) : cb;
-    const int oa = occ0 + ca, nob = cb - ca, nox = cx - ca;
-    // node range of the window from the 4-layer window table: nodes at layers l0 and l1, and
-    // (a forward update reads the arcs' targets) at layer min(l0 + 9, maxd)
-    const int w4 = l0 / kWinLayers;
-    const int na = win_entry(p, ti.win0, ti.tab, w4).x;
-    const int nb = win_entry(p, ti.win0, ti.tab, min(w4 + 2, ti.nw)).x;
-    const int nc = win_entry(p, ti.win0, ti.tab, w4 + 1).y;
-    __syncwarp();  // the previous window is no longer read
-    stage_window_w8<MODE>(p, S, oa, nob, nox, na, nb, p.bm, is_update(MODE) ? nc : na, l0 == 0);
+  auto issue = [&](WarpStage8 &S, const Win8 &g, bool first) {
+    issue_window_w8<MODE>(p, S, g.oa, g.nob, g.nox, g.na, g.nb, p.bm, is_update(MODE) ? g.nc : g.na, first);
+  };
+  if (NBUF == 2) {
+    issue(SB[0], win8_of(p, ti, lead_depth, 0), true);
+    cp_async_commit();
+    if (nwin > 1) issue(SB[1], win8_of(p, ti, lead_depth, 1), false);
+    cp_async_commit();  // (an empty group when there is no second window)
+  }
+  for (int k = 0; k < nwin; ++k) {
+    const Win8 g = win8_of(p, ti, lead_depth, k);
+    WarpStage8 &S = SB[NBUF == 2 ? (k & 1) : 0];
+    if (NBUF == 1) {
+      __syncwarp();  // the previous window is no longer read
+      stage_window_w8<MODE>(p, S, g.oa, g.nob, g.nox, g.na, g.nb, p.bm, is_update(MODE) ? g.nc : g.na, k == 0);
+    } else {
+      cp_async_wait_group<1>();  // window k has landed (window k + 1 may still be in flight)
+    }
     __syncwarp();
-    for (int l = l0; l < l1; ++l) {
+    const int ca = g.ca, oa = g.oa, na = g.na;
+    for (int l = g.l0; l < g.l1; ++l) {
       const bool active = depth > l;
       const int oi = occ_before(lead_depth, l) - ca + team;
       int node0 = 0, w = 0;
@@ -761,31 +821,48 @@ __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phas
       lh_prev = lh;
       lam_prev = lam;
     }
+    if (NBUF == 2) {
+      __syncwarp();  // this buffer is free: window k + 2 goes into it
+      if (k + 2 < nwin) issue(S, win8_of(p, ti, lead_depth, k + 2), false);
+      cp_async_commit();
+    }
   }
 }
 
-template <int T, int MODE, bool SMOOTH, bool SPLIT>
-__device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Phase &ph, int tile, WarpStage8 &S,
+template <int T, int MODE, bool SMOOTH, bool SPLIT, int NBUF>
+__device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Phase &ph, int tile, WarpStage8 *SB,
                                               double &bacc) {
   const int lane = threadIdx.x & 31;
   const int team = lane / T, tl = lane % T, tbase = team * T;
   const TileInfo ti = tile_info<T>(p, tile);
-  const int occ0 = ti.occ0, depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd;
+  const int depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd;
   const int bdd = p.tile_bdd0[tile] + team;
+  const int nwin = (maxd + kWin8Layers - 1) / kWin8Layers;
   float b_next = inf();
   int node0_next = 0;
-  const int ltop = ((maxd - 1) / kWin8Layers) * kWin8Layers;
-  for (int l0 = ltop; l0 >= 0; l0 -= kWin8Layers) {
-    const int l1 = min(l0 + kWin8Layers, maxd);
-    const int ca = occ_before(lead_depth, l0), cb = occ_before(lead_depth, l1);
-    const int oa = occ0 + ca, nob = cb - ca;
-    const int w4 = l0 / kWinLayers;
-    const int na = win_entry(p, ti.win0, ti.tab, w4).x;
-    const int nb = win_entry(p, ti.win0, ti.tab, min(w4 + 2, ti.nw)).x;
+  // windows from the last to the first; the j-th processed window uses buffer j & 1
+  auto issue = [&](WarpStage8 &S, const Win8 &g, bool first) {
+    issue_window_w8<MODE>(p, S, g.oa, g.nob, g.nob, g.na, g.nb, p.fm, g.nb, first);
+  };
+  if (NBUF == 2) {
+    issue(SB[0], win8_of(p, ti, lead_depth, nwin - 1), true);
+    cp_async_commit();
+    if (nwin > 1) issue(SB[1], win8_of(p, ti, lead_depth, nwin - 2), false);
+    cp_async_commit();
+  }
+  for (int j = 0; j < nwin; ++j) {
+    const int k = nwin - 1 - j;
+    const Win8 g = win8_of(p, ti, lead_depth, k);
+    WarpStage8 &S = SB[NBUF == 2 ? (j & 1) : 0];
+    if (NBUF == 1) {
+      __syncwarp();
+      stage_window_w8<MODE>(p, S, g.oa, g.nob, g.nob, g.na, g.nb, p.fm, g.nb, j == 0);
+    } else {
+      cp_async_wait_group<1>();
+    }
     __syncwarp();
-    stage_window_w8<MODE>(p, S, oa, nob, nob, na, nb, p.fm, nb, l0 == ltop);
-    __syncwarp();
-    for (int l = l1 - 1; l >= l0; --l) {
+    const int ca = g.ca, oa = g.oa, na = g.na;
+    for (int l = g.l1 - 1; l >= g.l0; --l) {
       const bool active = depth > l;
       const int oi = occ_before(lead_depth, l) - ca + team;
       int node0 = 0, w = 0;
@@ -835,6 +912,11 @@ __device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Pha
       }
       b_next = bcur;
       node0_next = node0;
+    }
+    if (NBUF == 2) {
+      __syncwarp();
+      if (j + 2 < nwin) issue(S, win8_of(p, ti, lead_depth, k - 2), false);
+      cp_async_commit();
     }
   }
 }
@@ -1179,7 +1261,8 @@ __device__ __forceinline__ void block_backward_narrow(const SweepParams &p, cons
   }
 }
 
-// STAGE 0: bulk-copy ring (StageRing); STAGE 1: 8-layer cp.async windows (WarpStage8 at W8)
+// STAGE 0: bulk-copy ring (StageRing); STAGE 1: 8-layer cp.async windows (WarpStage8 at W8);
+// STAGE 2: two 8-layer windows per warp, the next loading while one is processed (W8[0..1])
 template <bool FWD, int MODE, bool SMOOTH, int STAGE = 0, bool SPLIT = false>
 __device__ __forceinline__ void warp_tile(const SweepParams &p, const Phase &ph, int tile, StageRing &S,
                                           double &bacc, WarpStage8 *W8 = nullptr) {
@@ -1188,9 +1271,9 @@ __device__ __forceinline__ void warp_tile(const SweepParams &p, const Phase &ph,
   switch (c) {
 #define BDD_TEAM_CASE(C, T)                                                     \
   case C:                                                                       \
-    if constexpr (STAGE == 1) {                                                 \
-      if (FWD) warp_forward_w8<T, MODE, SMOOTH, SPLIT>(p, ph, tile, *W8, bacc); \
-      else warp_backward_w8<T, MODE, SMOOTH, SPLIT>(p, ph, tile, *W8, bacc);    \
+    if constexpr (STAGE >= 1) {                                                 \
+      if (FWD) warp_forward_w8<T, MODE, SMOOTH, SPLIT, STAGE>(p, ph, tile, W8, bacc); \
+      else warp_backward_w8<T, MODE, SMOOTH, SPLIT, STAGE>(p, ph, tile, W8, bacc);    \
     } else {                                                                    \
       if (FWD) warp_forward<T, MODE, SMOOTH, SPLIT>(p, ph, tile, S, bacc);       \
       else warp_backward<T, MODE, SMOOTH, SPLIT>(p, ph, tile, S, bacc);          \
@@ -1295,10 +1378,10 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
     const int warp = threadIdx.x >> 5;
     const int tile = blockIdx.x * kWarpsPerBlock + warp;
     if (tile >= p.class_tile_off[kWarpClasses]) return;  // whole warp leaves together
-    char *mine = reinterpret_cast<char *>(smem) + (size_t)warp * kWarpSmemBytes;
-    if constexpr (STAGE == 1) {
+    char *mine = reinterpret_cast<char *>(smem) + (size_t)warp * (STAGE == 2 ? kWarpSmemBytes2 : kWarpSmemBytes);
+    if constexpr (STAGE >= 1) {
       StageRing none{nullptr, nullptr, 0u};
-      warp_tile<FWD, MODE, SMOOTH, 1, SPLIT>(p, ph, tile, none, bacc, reinterpret_cast<WarpStage8 *>(mine));
+      warp_tile<FWD, MODE, SMOOTH, STAGE, SPLIT>(p, ph, tile, none, bacc, reinterpret_cast<WarpStage8 *>(mine));
     } else {
       __shared__ unsigned long long bars[kWarpsPerBlock * kWarpStages];
       if ((threadIdx.x & 31) == 0) {
@@ -1356,15 +1439,23 @@ __global__ void __launch_bounds__(kReduceThreads) bound_kernel(const SweepParams
 // finish, written to trace[*iter_ctr].
 template <bool BOUND>
 __global__ void __launch_bounds__(kReduceThreads, 8) pending_kernel(const PendingParams p) {
+  // the first variable's slot range is static: load it before waiting for the sweep that writes
+  // the slots, so its round trip overlaps that sweep's tail
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  int s0 = 0, e0 = 0;
+  if (i0 < p.n) {
+    s0 = p.var_ptr[i0];
+    e0 = p.var_ptr[i0 + 1];
+  }
   pdl_enter();
   const int range = BOUND ? (p.n > p.nb ? p.n : p.nb) : p.n;
   double acc = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < range; i += gridDim.x * blockDim.x) {
+  for (int i = i0; i < range; i += gridDim.x * blockDim.x) {
     if (i < p.n) {
       bool has;
-      const float Pi =
-          pending_var<0, true>(p.delta, p.var_ptr, p.var_occ, p.P, p.share_occ, i, has, p.slot_dir, p.next_dir,
-                               p.heavy_deg);
+      const int s = i == i0 ? s0 : p.var_ptr[i], e = i == i0 ? e0 : p.var_ptr[i + 1];
+      const float Pi = pending_var_se<0, true>(p.delta, p.var_occ, p.P, p.share_occ, i, s, e, has, p.slot_dir,
+                                               p.next_dir, p.heavy_deg);
       if (BOUND && has) acc += slack_term((double)Pi, p.alpha);
     }
     if (BOUND && i < p.nb) acc += (double)p.bdd_E[i];
@@ -1685,8 +1776,8 @@ int launch_pdl(void (*kernel)(Args...), int grid, int block, size_t smem, cudaSt
 }
 }  // namespace
 
-size_t sweep_smem_bytes(int block_buf, int block_depth_buf) {
-  const size_t warp_part = kWarpsPerBlock * kWarpSmemBytes;
+size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging) {
+  const size_t warp_part = kWarpsPerBlock * (staging == 2 ? kWarpSmemBytes2 : kWarpSmemBytes);
   const size_t group_part = group_floats(block_buf, block_depth_buf) * sizeof(float);
   return warp_part > group_part ? warp_part : group_part;
 }
@@ -1699,13 +1790,17 @@ size_t persist_smem_bytes(int block_buf, int block_depth_buf) {
 
 int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStream_t stream, int staging) {
   if (grid <= 0) return 0;
-  const size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf);
+  if (mode != kUpdate) staging = 0;
+  const size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf, staging);
   int rc = 0;
   if (p.split) {  // sub-BDDs: min-sum only, no fused pending pass
     if (p.alpha > 0.f || mode == kUpdateFused) return -5;
-    if (mode == kUpdate && staging == 1)
+    if (staging == 1)
       rc = forward ? launch_pdl(sweep_kernel<true, kUpdate, false, 1, true>, grid, kBlockThreads, smem, stream, p)
                    : launch_pdl(sweep_kernel<false, kUpdate, false, 1, true>, grid, kBlockThreads, smem, stream, p);
+    else if (staging == 2)
+      rc = forward ? launch_pdl(sweep_kernel<true, kUpdate, false, 2, true>, grid, kBlockThreads, smem, stream, p)
+                   : launch_pdl(sweep_kernel<false, kUpdate, false, 2, true>, grid, kBlockThreads, smem, stream, p);
 #define BDD_SPLIT_SWEEP(F, M) rc = launch_pdl(sweep_kernel<F, M, false, 0, true>, grid, kBlockThreads, smem, stream, p)
     else if (forward && mode == kUpdate) BDD_SPLIT_SWEEP(true, kUpdate);
     else if (forward && mode == kMessages) BDD_SPLIT_SWEEP(true, kMessages);
@@ -1723,6 +1818,15 @@ int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStr
     else
       rc = forward ? launch_pdl(sweep_kernel<true, kUpdate, false, 1>, grid, kBlockThreads, smem, stream, p)
                    : launch_pdl(sweep_kernel<false, kUpdate, false, 1>, grid, kBlockThreads, smem, stream, p);
+    return rc ? rc : status();
+  }
+  if (mode == kUpdate && staging == 2) {
+    if (p.alpha > 0.f)
+      rc = forward ? launch_pdl(sweep_kernel<true, kUpdate, true, 2>, grid, kBlockThreads, smem, stream, p)
+                   : launch_pdl(sweep_kernel<false, kUpdate, true, 2>, grid, kBlockThreads, smem, stream, p);
+    else
+      rc = forward ? launch_pdl(sweep_kernel<true, kUpdate, false, 2>, grid, kBlockThreads, smem, stream, p)
+                   : launch_pdl(sweep_kernel<false, kUpdate, false, 2>, grid, kBlockThreads, smem, stream, p);
     return rc ? rc : status();
   }
 #define BDD_SWEEP(F, M)                                                                          \
@@ -1758,7 +1862,10 @@ int sweep_set_smem(size_t bytes) {
       (const void *)sweep_kernel<true, kUpdate, false, 0, true>,   (const void *)sweep_kernel<false, kUpdate, false, 0, true>,
       (const void *)sweep_kernel<true, kMessages, false, 0, true>, (const void *)sweep_kernel<false, kMessages, false, 0, true>,
       (const void *)sweep_kernel<true, kFolded, false, 0, true>,   (const void *)sweep_kernel<false, kFolded, false, 0, true>,
-      (const void *)sweep_kernel<true, kUpdate, false, 1, true>,   (const void *)sweep_kernel<false, kUpdate, false, 1, true>};
+      (const void *)sweep_kernel<true, kUpdate, false, 1, true>,   (const void *)sweep_kernel<false, kUpdate, false, 1, true>,
+      (const void *)sweep_kernel<true, kUpdate, false, 2>,         (const void *)sweep_kernel<false, kUpdate, false, 2>,
+      (const void *)sweep_kernel<true, kUpdate, true, 2>,          (const void *)sweep_kernel<false, kUpdate, true, 2>,
+      (const void *)sweep_kernel<true, kUpdate, false, 2, true>,   (const void *)sweep_kernel<false, kUpdate, false, 2, true>};
   for (const void *f : fns)
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
       return -5;

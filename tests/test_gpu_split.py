@@ -156,7 +156,7 @@ def test_split_min_marginals_same_state(lib, name, mode):
     np.testing.assert_array_equal(gm, mu)
 
 
-@pytest.mark.parametrize("staging", [0, 1])
+@pytest.mark.parametrize("staging", [0, 1, 2])
 @pytest.mark.parametrize("gamma", [0.5, 1.0])
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("name", sorted(CASES))
