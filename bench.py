@@ -73,6 +73,13 @@ def dist_env():
 # ------------------------------------------------------------------------------------------
 # algorithmic bytes per kernel launch (minimum traffic of the slab layout)
 # ------------------------------------------------------------------------------------------
+def graph_launches(iters: int) -> int:
+    """Kernels the per-phase schedule launches for `iters` iterations: four per iteration (two
+    sweeps, two pending passes), plus the one-warp kernel that finishes the last bound of each
+    captured chain (chains of 8 iterations, then single iterations)."""
+    return 4 * iters + iters // 8 + iters % 8
+
+
 def algorithmic_bytes(kind: str, N: int, O: int, n: int, nb: int) -> int:
     if kind in ("fwd", "bwd"):
         # per node: lo/hi 8 B, fm 4 B, bm 4 B; per occurrence: node offset 4, lambda read+write
@@ -316,7 +323,7 @@ def ours(args):
         kernel_name = sweep_kernel_name(kinds[dom], s)
         abytes = algorithmic_bytes(kinds[dom], s.N, s.O, s.n, s.nb)
         per_launch_ms = kms[dom] / iters
-        launches = args.steps * iters * 4
+        launches = args.steps * graph_launches(iters)
     achieved = abytes / (per_launch_ms / 1e3) / 1e9
 
     # end to end through the C ABI with host buffers: build (host compile + upload), iterate,
@@ -529,7 +536,7 @@ def run_batched(args, stream, plain: bool, n_parity: int) -> dict:
         "cpu_baseline": {"value": cpu_arcs / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"instances {sample} of the batch, {iters} iterations each, FP64 single thread"},
         "plain_loop": plain_d,
-        "gpu_launches": steps * iters * 4,
+        "gpu_launches": steps * graph_launches(iters),
         "schedule": "persistent" if s.schedule == 0 else "per-phase graphs",
         "staging": staging_of(s),
         "clocks": clocks,
