@@ -107,7 +107,8 @@ typedef struct {
                                  memory of 1).  -1 (default): the autotuner times all three at
                                  build (schedule 1: a warm-up and six iterations each, kernel by
                                  kernel, the fastest launch of each sweep counted) and keeps the
-                                 fastest per sweep direction.  The variants compute identical
+                                 fastest per sweep direction (a higher-numbered variant must be
+                                 at least 5 % faster than a lower one).  The variants compute identical
                                  values; the persistent schedule and other sweeps use 0. */
   int split_intervals;        /* sub-BDDs (Sec. 6, Def. of sub-BDDs and copy-arcs; the parallel
                                  min-marginal averaging algorithm).  0 or 1 (default): no split.

@@ -48,6 +48,7 @@ struct DeviceGuard {
   } while (0)
 
 constexpr int kGraphIters = 8;  // iterations per captured graph
+constexpr float kTuneMargin = 0.05f;  // autotuner: required gain of a later staging variant
 
 }  // namespace
 
@@ -348,10 +349,14 @@ struct bdd_solver {
       stage_fwd = stage_bwd = 0;
       return rc;
     }
+    // a later variant (larger shared-memory footprint, fewer resident warps) replaces the choice
+    // only when it is at least kTuneMargin faster: launches timed one by one miss how a variant
+    // shares the SMs with its neighbours inside the captured graphs, and near-ties flipped
+    // between builds
     stage_fwd = stage_bwd = 0;
     for (int v = 1; v < kStagings; ++v) {
-      if (ms[v][0] < ms[stage_fwd][0]) stage_fwd = v;
-      if (ms[v][1] < ms[stage_bwd][1]) stage_bwd = v;
+      if (ms[v][0] < (1.f - kTuneMargin) * ms[stage_fwd][0]) stage_fwd = v;
+      if (ms[v][1] < (1.f - kTuneMargin) * ms[stage_bwd][1]) stage_bwd = v;
     }
     for (int v = 0; v < kStagings; ++v)
       for (int d = 0; d < 2; ++d) tune_ms[v][d] = ms[v][d];
