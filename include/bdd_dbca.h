@@ -242,11 +242,12 @@ int bdd_get_cuts(const bdd_solver *h, int *cuts);
  * dual, earlier piece) and mu (the entry arc's dual, later piece), host float[pairs] each
  * (out[14] of bdd_sizes; NULL skips one in the get form).  Pairs are in canonical order: the
  * cuts of BDD 0 (ascending row) by ascending layer, then BDD 1, ...; inside a cut, the tails
- * in canonical node order, the 0-arc before the 1-arc.  Every mu + mu_bar <= 0 keeps the bound
- * valid; the iteration keeps it when it starts there (all 0 after bdd_build / bdd_set_costs).
+ * in canonical node order, the 0-arc before the 1-arc.  The bound is valid while every
+ * mu + mu_bar <= 0.  From the all-zero duals of bdd_build / bdd_set_costs the iteration keeps
+ * that: after a forward step each pair's sum is -gamma d_fwd, after a backward step -gamma d_bwd.
  * bdd_set_copy_duals also recomputes the root messages (min of mu over a head's entry arcs) and
- * the backward messages; it leaves the last deltas of the dual steps as they are.  Both
- * synchronise. */
+ * the backward messages; it leaves the last deltas of the dual steps as they are, so duals set
+ * by hand need not keep the sums nonpositive.  Both synchronise. */
 int bdd_get_copy_duals(const bdd_solver *h, float *mu_bar, float *mu);
 int bdd_set_copy_duals(bdd_solver *h, const float *mu_bar, const float *mu);
 
