@@ -285,3 +285,26 @@ def test_split_wide_block_tiles(lib):
     e0, e1 = o.min_marginals(fold=True)
     close(m0, e0, MM_TOL)
     close(m1, e1, MM_TOL)
+
+
+def test_depth_split_single_layer_pieces(lib):
+    """The degenerate depth split D = 1: every layer is a piece of its own (roots from the root
+    messages, arcs into top through copy pairs); bound trace against the oracle."""
+    inst = random_ilp(n=40, m=25, max_row_vars=10, seed=21, coef=3)
+    s = solver(inst, split_depth=1)
+    o = Oracle(inst)
+    o.split_depth(1)
+    assert s.max_depth == 1 and s.nb == o.nb == s.O and s.npairs == o.npairs > 0
+    close(_trace(s, 60), o.run_parallel(60, omega=0.5), LB_TOL)
+
+
+def test_set_copy_duals_rejects_non_finite(lib):
+    from paper_2009_00481_gb300 import BDDError
+    from paper_2009_00481_gb300.binding import BDD_EINVAL
+    inst, s, _ = _pair("random_wide")
+    mb = np.zeros(s.npairs, np.float32)
+    mu = np.zeros(s.npairs, np.float32)
+    mu[0] = np.inf
+    with pytest.raises(BDDError) as e:
+        s.set_copy_duals(mb, mu)
+    assert e.value.code == BDD_EINVAL

@@ -220,3 +220,30 @@ def test_depth_split_rejects_bad_input():
     for D, g in ((0, 0.5), (-1, 0.5), (2, 0.0), (2, 1.5)):
         with pytest.raises(ValueError):
             Oracle(inst).split_depth(D, g)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_split_with_srmp_keeps_the_checks(seed):
+    """SRMP averaging (Appendix A.4) on pieces: a piece's first and last layers define its J_i^<
+    and J_i^> membership.  Incremental min-marginals equal the definitional ones, the invariant
+    and monotonicity hold, and the bound stays below the ILP optimum."""
+    inst = random_ilp(n=15, m=10, max_row_vars=9, seed=80 + seed)
+    o = Oracle(inst)
+    o.set_srmp(True)
+    o.split_depth(3)
+    tr = o.run_parallel(30, omega=0.5, check=True)
+    w = o.worst()
+    assert w["incremental_mm"] < 1e-10 and w["invariant"] < 1e-12 and w["monotone_drop"] < 1e-12
+    assert tr.max() <= bf.ilp_optimum(inst) + 1e-9
+
+
+def test_copy_dual_sums_after_each_step():
+    """From zero duals, after the forward copy step every pair's mu + mu_bar is -gamma times a
+    nonnegative difference (so it never turns positive), and after the backward step too."""
+    inst = random_ilp(n=14, m=9, max_row_vars=9, seed=91)
+    o = Oracle(inst)
+    o.split_depth(3, 0.5)
+    for _ in range(15):
+        o.run_parallel(1, omega=0.5)
+        mb, mu = o.copy_duals()
+        assert np.all(mb + mu <= 1e-12)
