@@ -30,6 +30,8 @@
 #include <mutex>
 #include <thread>
 
+#include <unistd.h>
+
 #include "bdd_dbca.h"
 #include "internal.h"
 
@@ -178,14 +180,17 @@ namespace {
 // workers spin on it for a short while after each job (the calls of one build come in quick
 // succession), then sleep on a condition variable.  Each takes chunks of the job from a shared
 // atomic cursor and checks out when none are left; the caller works too and returns once every
-// worker has checked out, so a job's fields never change under a worker.
+// worker has checked out, so a job's fields never change under a worker.  The pool lives until
+// the process exits and is never destroyed (its idle threads end with the process).  A child
+// forked after the pool was made has none of its threads, so there every job runs inline.
 class HostPool {
  public:
   static HostPool &get() {
-    static HostPool pool;
-    return pool;
+    static HostPool *pool = new HostPool();
+    return *pool;
   }
   bool run(long long n, long long grain, const std::function<void(long long, long long)> &body) {
+    if (getpid() != owner_) return false;  // a forked child: the workers exist only in the parent
     std::unique_lock<std::mutex> busy(job_mu_, std::try_to_lock);
     if (!busy.owns_lock() || workers_.empty()) return false;
     body_ = &body;
@@ -210,15 +215,6 @@ class HostPool {
     const int extra = (int)std::min(hw ? hw : 1u, 64u) - 1;
     for (int t = 0; t < extra; ++t) workers_.emplace_back([this] { loop(); });
   }
-  ~HostPool() {
-    {
-      std::lock_guard<std::mutex> lk(mu_);
-      stop_.store(true);
-      gen_.fetch_add(1, std::memory_order_release);
-    }
-    cv_.notify_all();
-    for (auto &w : workers_) w.join();
-  }
   void work() {
     for (;;) {
       const long long b = next_.fetch_add(grain_, std::memory_order_relaxed);
@@ -238,11 +234,11 @@ class HostPool {
         }
       }
       seen = gen_.load(std::memory_order_acquire);
-      if (stop_.load()) return;
       work();
       active_.fetch_sub(1, std::memory_order_release);
     }
   }
+  const pid_t owner_ = getpid();
   std::vector<std::thread> workers_;
   std::mutex job_mu_, mu_;
   std::condition_variable cv_;
@@ -251,7 +247,6 @@ class HostPool {
   std::atomic<long long> next_{0};
   std::atomic<int> active_{0};
   std::atomic<unsigned long long> gen_{0};
-  std::atomic<bool> stop_{false};
 };
 
 }  // namespace

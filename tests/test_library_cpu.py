@@ -122,3 +122,34 @@ def test_host_only_refuses_device_calls(cuda_lib):
     with pytest.raises(BDDError) as e:
         s.get_state()
     assert e.value.code == BDD_ESTATE
+
+
+@pytest.mark.filterwarnings("ignore::DeprecationWarning")
+def test_build_in_a_forked_child(cuda_lib):
+    """The host compiler's worker threads live in the process that made them: a child forked
+    after a build (e.g. a fork-started data-loader worker) compiles on its own thread and does
+    not wait for workers it does not have."""
+    import os
+    import time
+    from paper_2009_00481_gb300 import Solver
+    inst = config(1)
+    Solver(inst, host_only=1)  # the pool exists in this process now
+    pid = os.fork()
+    if pid == 0:  # child: build again and report
+        code = 1
+        try:
+            s = Solver(inst, host_only=2)
+            code = 0 if s.N == Oracle(inst).N else 1
+        finally:
+            os._exit(code)
+    deadline = time.time() + 60
+    while True:
+        done, status = os.waitpid(pid, os.WNOHANG)
+        if done:
+            break
+        if time.time() > deadline:
+            os.kill(pid, 9)
+            os.waitpid(pid, 0)
+            raise AssertionError("the forked child's build did not finish")
+        time.sleep(0.05)
+    assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0
