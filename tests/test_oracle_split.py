@@ -247,3 +247,45 @@ def test_copy_dual_sums_after_each_step():
         o.run_parallel(1, omega=0.5)
         mb, mu = o.copy_duals()
         assert np.all(mb + mu <= 1e-12)
+
+
+def test_fig2_worked_example():
+    """Sec. 6, Figure 2: the split of Figure 1's BDD has two pieces and three copy-arc pairs, in
+    the arcs the figure draws; the figure's marked path (x1 = 0, x3 = 1, x7 = 0) crosses the cut
+    through the pair it marks, so with that pair's duals made cheap the piece energies add up to
+    the path's cost."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fig2_split.json")))
+    fig1 = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fig1_bdd.json")))["row"]
+    n = fig1["n"]
+    inst = _from_rows("fig1", n, [(np.array(fig1["cols"]), np.array(fig1["vals"]), fig1["b"], fig1["sense"])],
+                      np.zeros(n, np.float32))
+    o = Oracle(inst)
+    assert o.split([g["cut_place"]]) == 2
+    assert o.npairs == len(g["pair_heads"])
+    can = o.canonical()
+    want_lo = [v for p in g["pieces"] for lay in p["layers"] for v in lay["lo"]]
+    want_hi = [v for p in g["pieces"] for lay in p["layers"] for v in lay["hi"]]
+    np.testing.assert_array_equal(can["lo"], want_lo)
+    np.testing.assert_array_equal(can["hi"], want_hi)
+    np.testing.assert_array_equal(can["bdd_depth"], [len(p["layers"]) for p in g["pieces"]])
+    np.testing.assert_array_equal(can["occ_var"], [lay["var"] for p in g["pieces"] for lay in p["layers"]])
+    # only the marked pair (abar_2, a_2) is cheap on both sides; lambda charges x3 alone.  The
+    # earlier piece's best path is then the figure's x1 = 0, x3 = 1 through abar_2 (cost 1), the
+    # later piece's enters through a_2 and takes x7 = 0 (cost 0): the marked paths of Figure 2
+    lam = np.zeros(3)
+    lam[1] = 1.0
+    o.set_state(lam)
+    mb = np.full(o.npairs, 5.0)
+    mu = np.full(o.npairs, 5.0)
+    mb[g["marked_pair"]] = 0.0
+    mu[g["marked_pair"]] = 0.0
+    o.set_copy_duals(mb, mu)
+    E = o.energies()
+    np.testing.assert_allclose(E, [1.0, 0.0], rtol=0, atol=1e-12)
+    # a dearer marked pair moves both energies by its duals: the path is still the only cheap one
+    mb[g["marked_pair"]] = 0.5
+    mu[g["marked_pair"]] = -0.5
+    o.set_copy_duals(mb, mu)
+    np.testing.assert_allclose(o.energies(), [1.5, -0.5], rtol=0, atol=1e-12)

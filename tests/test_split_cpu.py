@@ -144,3 +144,25 @@ def test_depth_split_full_tomography_shape(cuda_lib):
     o = Oracle(inst)
     o.split_depth(32)
     assert (o.nb, o.npairs) == (s.nb, s.npairs)
+
+
+def test_fig2_worked_example_library(cuda_lib):
+    """The library's split of Figure 1's BDD at the cut of Figure 2 (Sec. 6) gives the pieces and
+    copy arcs of the golden fixture, bit for bit (host compile and host slab layout)."""
+    import json
+    import os
+    from instances.generators import _from_rows
+    from paper_2009_00481_gb300 import Solver
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    g = json.load(open(os.path.join(here, "fig2_split.json")))
+    row = json.load(open(os.path.join(here, "fig1_bdd.json")))["row"]
+    n = row["n"]
+    inst = _from_rows("fig1", n, [(np.array(row["cols"]), np.array(row["vals"]), row["b"], row["sense"])],
+                      np.zeros(n, np.float32))
+    for host_only in (1, 2):
+        s = Solver(inst, host_only=host_only, cuts=[g["cut_place"]])
+        assert (s.nb, s.npairs) == (2, len(g["pair_heads"]))
+        can = s.canonical()
+        np.testing.assert_array_equal(can["lo"], [v for p in g["pieces"] for lay in p["layers"] for v in lay["lo"]])
+        np.testing.assert_array_equal(can["hi"], [v for p in g["pieces"] for lay in p["layers"] for v in lay["hi"]])
+        np.testing.assert_array_equal(can["bdd_depth"], [len(p["layers"]) for p in g["pieces"]])
