@@ -47,3 +47,22 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.replica_throughput(10.0, 2.0, 1) == pytest.approx(5000.0)
+
+
+def test_bench_bookkeeping():
+    """Kernels per step of the per-phase schedule (four per iteration plus the kernel that
+    finishes the last bound of each captured chain of 8 or 1 iterations), the staging decode of
+    bdd_sizes' out[12] (two bits per sweep direction) and the algorithmic bytes of an iteration."""
+    import bench
+    assert bench.graph_launches(500) == 4 * 500 + 62 + 4
+    assert bench.graph_launches(8) == 33 and bench.graph_launches(1) == 5
+    for f in range(3):
+        for b in range(3):
+            class S:
+                staging = f | (b << 2)
+            st = bench.staging_of(S)
+            assert st == {"forward": bench.STAGING[f], "backward": bench.STAGING[b]}
+    N, O, n, nb = 1000, 700, 300, 90
+    # the sum of the per-kernel figures: two sweeps (16 N + 24 O + 4 / 8 nb), two pending passes
+    # (8 n + 12 O, the bound one + 4 nb)
+    assert bench.algorithmic_bytes("iteration", N, O, n, nb) == 32 * N + 72 * O + 16 * n + 16 * nb
