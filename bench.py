@@ -71,7 +71,8 @@ def dist_env():
 
 
 # ------------------------------------------------------------------------------------------
-# algorithmic bytes per kernel launch (minimum traffic of the slab layout)
+# algorithmic bytes per kernel launch (minimum traffic of the slab layout: every array a kernel
+# needs, touched once)
 # ------------------------------------------------------------------------------------------
 def graph_launches(iters: int) -> int:
     """Kernels the per-phase schedule launches for `iters` iterations: four per iteration (two
@@ -180,7 +181,8 @@ class ClockSampler:
 
     def __init__(self, device_index: int):
         self.proc = None
-        self.path = os.path.join(HERE, "gpurun_out", f"clocks_rank{device_index}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"bdd_bench_clocks_rank{device_index}.csv")
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         try:
             self.f = open(self.path, "w")
