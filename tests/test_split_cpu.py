@@ -166,3 +166,25 @@ def test_fig2_worked_example_library(cuda_lib):
         np.testing.assert_array_equal(can["lo"], [v for p in g["pieces"] for lay in p["layers"] for v in lay["lo"]])
         np.testing.assert_array_equal(can["hi"], [v for p in g["pieces"] for lay in p["layers"] for v in lay["hi"]])
         np.testing.assert_array_equal(can["bdd_depth"], [len(p["layers"]) for p in g["pieces"]])
+
+
+def test_split_abi_errors_on_host(cuda_lib):
+    """Calls of the sub-BDD ABI on host-only solvers: cut places readable, copy duals need device
+    state (BDD_ESTATE), missing arrays refused (BDD_EINVAL); an unsplit solver reports no cuts
+    and no pairs."""
+    from paper_2009_00481_gb300 import BDDError, Solver
+    from paper_2009_00481_gb300 import binding as B
+    inst = WORKLOADS["random"]()
+    s = Solver(inst, host_only=1, split=3)
+    cuts = s.cuts()
+    assert len(cuts) == s.n_cuts >= 1 and s.npairs > 0
+    with pytest.raises(BDDError) as e:
+        s.copy_duals()
+    assert e.value.code == B.BDD_ESTATE
+    lib = B.load()
+    assert lib.bdd_set_copy_duals(s.h, None, None) == B.BDD_EINVAL
+    assert lib.bdd_get_cuts(s.h, None) == B.BDD_EINVAL
+    plain = Solver(inst, host_only=1)
+    assert plain.n_cuts == 0 and plain.npairs == 0 and plain.split_depth == 0
+    assert len(plain.cuts()) == 0
+    assert lib.bdd_get_cuts(plain.h, None) == B.BDD_OK
