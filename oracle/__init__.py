@@ -70,6 +70,8 @@ def _configure(lib):
     lib.orc_energies.argtypes = [vp, P(f64)]
     lib.orc_counts.argtypes = [vp, P(f64)]
     lib.orc_set_alpha.argtypes = [vp, f64]
+    lib.orc_smooth_gradient.argtypes = [vp, i32, f64, P(f64), P(f64)]
+    lib.orc_smooth_gradient.restype = i32
     return lib
 
 
@@ -240,6 +242,17 @@ class Oracle:
         else:
             P = np.ascontiguousarray(P, np.float64)
             self.lib.orc_set_state(self.h, _p(lam, C.c_double), _p(P, C.c_double))
+
+    def smooth_gradient(self, K: int, omega: float = 0.5):
+        """Smoothed bound after K iterations of the deferred schedule from lambda = c/|J_i| and
+        its gradient d bound / d c (FP64 reverse mode over the recorded iterations; needs
+        set_alpha(alpha > 0) first).  Leaves the dual state after K iterations."""
+        lb = np.zeros(1, np.float64)
+        g = np.zeros(max(self.n, 1), np.float64)
+        rc = self.lib.orc_smooth_gradient(self.h, int(K), float(omega), _p(lb, C.c_double), _p(g, C.c_double))
+        if rc:
+            raise OracleError(rc, -1)
+        return float(lb[0]), g[: self.n]
 
     def min_marginals(self, fold: bool = True):
         m0 = np.zeros(max(self.nnz, 1), np.float64)

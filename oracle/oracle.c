@@ -784,6 +784,227 @@ int orc_run_parallel(void *vh, int iters, double omega, int check, double *trace
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* derivative of the smoothed bound after K iterations of schedule P (Appendix A.5)       */
+/* ------------------------------------------------------------------------------------ */
+/* With alpha > 0 every aggregation is the soft minimum z = -alpha log sum_k exp(-x_k / alpha),
+ * a smooth function of its arguments with dz/dx_k = exp(-(x_k - z) / alpha) (the Gibbs weight of
+ * term k; 0 for x_k = +inf).  The bound after K iterations of schedule P is then a composition
+ * of smooth steps of the costs c (lambda_0 = c_i/|J_i|, the initial backward programme, 2K
+ * sweeps with their pending sums, the y-slack term), so reverse-mode differentiation gives
+ * d bound / d c exactly: the forward run below keeps the inputs and outputs of every sweep,
+ * and each step is then reversed in the opposite order.  Plain reverse-mode, no
+ * recomputation tricks: a tape of (2K + 1) (O + n) + (2K + 1) N doubles. */
+
+static double gibbs(const oracle_t *h, double x, double z) { return isinf(x) ? 0.0 : exp(-(x - z) / h->alpha); }
+
+/* weight of P_i in the share occurrence o takes in a forward (backward) sweep (take_share) */
+static double share_weight(const oracle_t *h, long long o, int forward) {
+  int i = h->occ_var[o];
+  long long s = h->var_ptr[i], e = h->var_ptr[i + 1];
+  if (!h->srmp) return 1.0 / (double)(e - s);
+  int cnt = 0;
+  for (long long t = s; t < e; ++t) cnt += srmp_takes(h, h->var_occ[t], forward);
+  if (cnt == 0) return 1.0 / (double)(e - s);
+  return srmp_takes(h, o, forward) ? 1.0 / (double)cnt : 0.0;
+}
+
+/* Reverse of the backward update step b(u) = agg(b(lo u), lam_o + b(hi u)) of the nodes of
+ * occurrence o, given the adjoints gb of those nodes: adds to gb of the next layer and to
+ * *glam.  bm holds the messages of both layers. */
+static void bwd_step_adjoint(const oracle_t *h, long long o, double lam_o, const double *bm, double *gb,
+                             double *glam) {
+  long long n1 = h->occ_node0[o + 1];
+  for (long long u = h->occ_node0[o]; u < h->occ_node0[o + 1]; ++u) {
+    double g = gb[u];
+    if (g == 0.0) continue;
+    double a0 = bval(h, bm, o, h->lo[u]);
+    double a1 = h->hi[u] == ORC_BOT ? INFINITY : lam_o + bval(h, bm, o, h->hi[u]);
+    double w0 = gibbs(h, a0, bm[u]), w1 = gibbs(h, a1, bm[u]);
+    if (h->lo[u] >= 0) gb[n1 + h->lo[u]] += g * w0;
+    if (h->hi[u] >= 0) gb[n1 + h->hi[u]] += g * w1;
+    *glam += g * w1;
+  }
+}
+
+/* Reverse of eq. marginal-aggregation for occurrence o (m0, m1 from fm of its layer and bm of
+ * the next) followed by d = omega (m1 - m0): given gd, adds to gfm of the layer's nodes, gbm of
+ * the next layer's nodes and *gmu (the multiplier the 1-arcs carry). */
+static void marginal_adjoint(const oracle_t *h, long long o, double mu, const double *fm, const double *bm,
+                             double omega, double gd, double *gfm, double *gbm, double *gmu) {
+  double m0, m1;
+  aggregate(h, o, mu, fm, bm, &m0, &m1);
+  if (isinf(m0) || isinf(m1) || gd == 0.0) return;  /* d = 0 there (reading r3): no dependence */
+  double g1 = omega * gd, g0 = -omega * gd;
+  long long n1 = h->occ_node0[o + 1];
+  for (long long u = h->occ_node0[o]; u < h->occ_node0[o + 1]; ++u) {
+    if (h->lo[u] != ORC_BOT) {
+      double w = gibbs(h, fm[u] + bval(h, bm, o, h->lo[u]), m0);
+      gfm[u] += g0 * w;
+      if (h->lo[u] >= 0) gbm[n1 + h->lo[u]] += g0 * w;
+    }
+    if (h->hi[u] != ORC_BOT) {
+      double w = gibbs(h, fm[u] + mu + bval(h, bm, o, h->hi[u]), m1);
+      gfm[u] += g1 * w;
+      *gmu += g1 * w;
+      if (h->hi[u] >= 0) gbm[n1 + h->hi[u]] += g1 * w;
+    }
+  }
+}
+
+/* Smoothed bound after K >= 0 iterations of schedule P from lambda_0 = c_i/|J_i| (the value
+ * orc_run_parallel's trace ends with), and its gradient with respect to c, both FP64.  Needs
+ * alpha > 0 and no copy-arc pairs.  Leaves the dual state after K iterations.  Returns 0, or
+ * ORC_EINVAL / ORC_ENOMEM. */
+int orc_smooth_gradient(void *vh, int K, double omega, double *bound, double *grad_c) {
+  oracle_t *h = (oracle_t *)vh;
+  if (!(h->alpha > 0.0) || h->npairs > 0 || K < 0) return ORC_EINVAL;
+  const long long O = h->O, N = h->N, S = 2LL * K;
+  const int n = h->n;
+  /* tape: multipliers and pending sums at the start of sweep s (s = 2K: the end state), the
+   * messages after the initial backward programme and after every sweep */
+  double *lam_t = (double *)malloc((size_t)((S + 1) * O + 1) * sizeof(double));
+  double *P_t = (double *)malloc((size_t)((S + 1) * n + 1) * sizeof(double));
+  double *msg_t = (double *)malloc((size_t)((S + 1) * N + 1) * sizeof(double));
+  double *glam = (double *)calloc((size_t)O + 1, sizeof(double));   /* adjoint of lambda */
+  double *gdel = (double *)calloc((size_t)O + 1, sizeof(double));   /* adjoint of delta */
+  double *gshr = (double *)calloc((size_t)O + 1, sizeof(double));   /* adjoint of the shares */
+  double *gP = (double *)calloc((size_t)n + 1, sizeof(double));     /* adjoint of P */
+  double *gin = (double *)calloc((size_t)N + 1, sizeof(double));    /* adjoint of the messages a sweep reads */
+  double *gout = (double *)calloc((size_t)N + 1, sizeof(double));   /* adjoint of the messages a sweep writes */
+  double *wf = (double *)malloc((size_t)(O + 1) * sizeof(double));
+  double *wb = (double *)malloc((size_t)(O + 1) * sizeof(double));
+  if (!lam_t || !P_t || !msg_t || !glam || !gdel || !gshr || !gP || !gin || !gout || !wf || !wb) {
+    free(lam_t); free(P_t); free(msg_t); free(glam); free(gdel); free(gshr); free(gP); free(gin);
+    free(gout); free(wf); free(wb);
+    return ORC_ENOMEM;
+  }
+  for (long long o = 0; o < O; ++o) { wf[o] = share_weight(h, o, 1); wb[o] = share_weight(h, o, 0); }
+
+  /* ---- forward run (the oracle's own schedule P), taping every sweep's inputs ---- */
+  orc_init_dual(h);  /* lambda_0 = c/|J_i|, P = 0, initial backward programme into bm */
+  memcpy(msg_t, h->bm, (size_t)N * sizeof(double));
+  for (long long s = 0; s < S; ++s) {
+    memcpy(lam_t + s * O, h->lam, (size_t)O * sizeof(double));
+    memcpy(P_t + s * n, h->P, (size_t)n * sizeof(double));
+    if (s % 2 == 0) {
+      sweep_forward(h, omega, 0);
+      memcpy(msg_t + (s + 1) * N, h->fm, (size_t)N * sizeof(double));
+    } else {
+      sweep_backward(h, omega, 0);
+      memcpy(msg_t + (s + 1) * N, h->bm, (size_t)N * sizeof(double));
+    }
+  }
+  memcpy(lam_t + S * O, h->lam, (size_t)O * sizeof(double));
+  memcpy(P_t + S * n, h->P, (size_t)n * sizeof(double));
+  /* the bound: the energies from the last backward messages (the initial programme's for K =
+   * 0) plus the soft y-slack terms */
+  const double *bm_last = msg_t + S * N;
+  double lb = h->empty_const;
+  for (int b = 0; b < h->nb; ++b) lb += piece_energy(h, b, bm_last);
+  for (int i = 0; i < n; ++i)
+    if (h->deg[i] > 0) lb += agg(h, 0.0, P_t[S * n + i]);
+  *bound = lb;
+
+  /* ---- reverse ---- */
+  for (int i = 0; i < n; ++i) grad_c[i] = 0.0;
+  /* d bound: 1 on every root's backward message; the slack term's Gibbs weight on P_i; for a
+   * variable in no row, the weight of c_i in agg(0, c_i) */
+  for (int b = 0; b < h->nb; ++b) gout[h->occ_node0[h->bdd_occ0[b]]] += 1.0;
+  for (int i = 0; i < n; ++i) {
+    if (h->deg[i] > 0) {
+      double P = P_t[S * n + i];
+      gP[i] = gibbs(h, P, agg(h, 0.0, P));
+    } else {
+      grad_c[i] = gibbs(h, h->c[i], agg(h, 0.0, h->c[i]));
+    }
+  }
+  /* gout holds the adjoint of the messages the last sweep wrote (bm); glam of the end state is 0 */
+  for (long long s = S - 1; s >= 0; --s) {
+    const int forward = s % 2 == 0;
+    const double *lam0 = lam_t + s * O, *lam1 = lam_t + (s + 1) * O;  /* before / after the sweep */
+    const double *Pin = P_t + s * n;
+    const double *mout = msg_t + (s + 1) * N;   /* fm (forward) / bm (backward) written */
+    const double *min = msg_t + s * N;          /* bm (forward) / fm (backward) read */
+    const double *w = forward ? wf : wb;
+    /* pending sums after the sweep: P_i = sum of its deltas */
+    for (int i = 0; i < n; ++i)
+      for (long long t = h->var_ptr[i]; t < h->var_ptr[i + 1]; ++t) gdel[h->var_occ[t]] += gP[i];
+    for (int i = 0; i < n; ++i) gP[i] = 0.0;
+    for (long long v = 0; v < N; ++v) gin[v] = 0.0;
+    for (long long o = 0; o < O; ++o) gshr[o] = 0.0;
+    /* glam: adjoint of lambda after the sweep (lam1); becomes the adjoint before it (lam0) */
+    for (int b = 0; b < h->nb; ++b) {
+      long long o0 = h->bdd_occ0[b];
+      int k = h->bdd_k[b];
+      if (forward) {
+        /* layers in reverse: lam1 = mu - d, d = omega (m1 - m0) from fm (this sweep) and bm (read),
+         * then fm of the layer from the previous layer (Alg. 2) */
+        for (int l = k - 1; l >= 0; --l) {
+          long long o = o0 + l;
+          double mu = lam0[o] + w[o] * Pin[h->occ_var[o]];
+          double gmu = glam[o];
+          double gd = gdel[o] - glam[o];
+          marginal_adjoint(h, o, mu, mout, min, omega, gd, gout, gin, &gmu);
+          glam[o] = gmu;   /* lambda before the sweep enters mu with weight 1 */
+          gshr[o] = gmu;
+          if (l > 0) {     /* fm(v) = agg over arcs u -> v of fm(u) + theta, theta = lam1 on 1-arcs */
+            long long ol = o - 1;
+            long long nl = h->occ_node0[o];
+            for (long long u = h->occ_node0[ol]; u < h->occ_node0[o]; ++u) {
+              if (h->lo[u] >= 0) {
+                long long v = nl + h->lo[u];
+                gout[u] += gout[v] * gibbs(h, mout[u], mout[v]);
+              }
+              if (h->hi[u] >= 0) {
+                long long v = nl + h->hi[u];
+                double wt = gout[v] * gibbs(h, mout[u] + lam1[ol], mout[v]);
+                gout[u] += wt;
+                glam[ol] += wt;  /* adjoint of lam1 of the previous layer (processed next) */
+              }
+            }
+          }
+        }
+      } else {
+        /* layers in reverse of the backward order (first to last): bm of the layer (Alg. 3 with
+         * lam1), then lam1 = mu - d, d from fm (read) and bm of the next layer (written) */
+        for (int l = 0; l < k; ++l) {
+          long long o = o0 + l;
+          double mu = lam0[o] + w[o] * Pin[h->occ_var[o]];
+          double gl1 = glam[o];
+          bwd_step_adjoint(h, o, lam1[o], mout, gout, &gl1);
+          double gmu = gl1;
+          double gd = gdel[o] - gl1;
+          marginal_adjoint(h, o, mu, min, mout, omega, gd, gin, gout, &gmu);
+          glam[o] = gmu;
+          gshr[o] = gmu;
+        }
+      }
+    }
+    for (long long o = 0; o < O; ++o) gdel[o] = 0.0;
+    /* the shares came from the pending sums before the sweep */
+    for (long long o = 0; o < O; ++o) gP[h->occ_var[o]] += w[o] * gshr[o];
+    /* messages read by this sweep were written by the previous one */
+    memcpy(gout, gin, (size_t)N * sizeof(double));
+  }
+  /* gout: adjoint of the initial backward programme's messages (with lambda_0); P_0 = 0 is a
+   * constant, so gP is dropped */
+  for (int b = 0; b < h->nb; ++b) {
+    long long o0 = h->bdd_occ0[b];
+    for (int l = 0; l < h->bdd_k[b]; ++l) {
+      long long o = o0 + l;
+      double g = 0.0;
+      bwd_step_adjoint(h, o, lam_t[o], msg_t, gout, &g);
+      glam[o] += g;
+    }
+  }
+  /* lambda_0 = c_i / |J_i| */
+  for (long long o = 0; o < O; ++o) grad_c[h->occ_var[o]] += glam[o] / (double)h->deg[h->occ_var[o]];
+  free(lam_t); free(P_t); free(msg_t); free(glam); free(gdel); free(gshr); free(gP); free(gin);
+  free(gout); free(wf); free(wb);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* schedule S: Alg. 1 with definitional min-marginals                                     */
 /* ------------------------------------------------------------------------------------ */
 static void visit_variable(oracle_t *h, int i, int forward, int check, double *m0s,

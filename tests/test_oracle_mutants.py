@@ -64,7 +64,23 @@ SPLIT_MUTANTS = {
     # depth split with floor(k / D) pieces instead of ceil(k / D)
     "split_depth_floor": ("int q = (k + D - 1) / D;", "int q = k / D;"),
 }
-MUTANTS_ALL = {**MUTANTS, **SPLIT_MUTANTS}
+# planted mistakes in the reverse-mode gradient of the smoothed bound, caught by the gradient
+# battery (central differences and the Gibbs marginals at zero iterations)
+GRAD_MUTANTS = {
+    # the 1-arc multiplier of the previous layer gets no adjoint from the forward messages
+    "grad_fwd_theta": ("                glam[ol] += wt;  /* adjoint of lam1 of the previous layer (processed next) */\n",
+                       "\n"),
+    # d = omega (m1 - m0) reversed with the wrong sign
+    "grad_sign": ("double g1 = omega * gd, g0 = -omega * gd;", "double g1 = -omega * gd, g0 = omega * gd;"),
+    # the share weight 1/|J_i| dropped on the way back to the pending sums
+    "grad_share": ("gP[h->occ_var[o]] += w[o] * gshr[o];", "gP[h->occ_var[o]] += gshr[o];"),
+    # lambda_0 = c_i / |J_i| reversed without the division
+    "grad_init": ("grad_c[h->occ_var[o]] += glam[o] / (double)h->deg[h->occ_var[o]];",
+                  "grad_c[h->occ_var[o]] += glam[o];"),
+    # the recorded deltas get no adjoint from the pending sums they form
+    "grad_pending": ("gdel[h->var_occ[t]] += gP[i];", "(void)t;"),
+}
+MUTANTS_ALL = {**MUTANTS, **SPLIT_MUTANTS, **GRAD_MUTANTS}
 
 
 def _compile(tmp_path, name):
@@ -198,3 +214,29 @@ def test_original_passes_battery():
 def test_mutant_is_caught(tmp_path, name):
     lib = _compile(tmp_path, name)
     assert not _pins_hold(lib), f"planted mistake '{name}' passed every pin"
+
+
+def _grad_pins_hold(lib) -> bool:
+    """The gradient battery of tests/test_oracle_smooth.py on small cases: every coordinate
+    against central differences, and the Gibbs marginals at zero iterations."""
+    from tests.test_oracle_smooth import GRAD_CASES, _central_differences, _oracle_gradient
+    for name in ("tracking_3x6", "random_ilp"):
+        inst = GRAD_CASES[name]()
+        for K, srmp in ((1, False), (4, True)):
+            _, g = _oracle_gradient(inst, 0.3, K, srmp, lib=lib)
+            fd = _central_differences(inst, 0.3, K, srmp, lib=lib)
+            if np.abs(g - fd).max() > 1e-6 * max(1.0, np.abs(fd).max()):
+                return False
+    return True
+
+
+def test_original_passes_gradient_battery():
+    from oracle import _load
+    assert _grad_pins_hold(_load())
+
+
+@pytest.mark.parametrize("name", sorted(GRAD_MUTANTS))
+def test_gradient_mutant_is_caught(tmp_path, name):
+    lib = _compile(tmp_path, name)
+    assert not _grad_pins_hold(lib), f"planted mistake '{name}' passed every gradient pin"
+
