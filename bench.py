@@ -589,8 +589,8 @@ def run_differentiation(args, stream) -> dict:
     ms_fwd = timed(lambda: binding.bdd_smooth_forward(smooth.h, K, c.data_ptr(), bound.data_ptr(), sp))
 
     def fwd_bwd():
-        binding.bdd_smooth_forward(smooth.h, K, c.data_ptr(), bound.data_ptr(), sp)
-        binding.bdd_smooth_backward(smooth.h, gbound.data_ptr(), grad.data_ptr(), sp)
+        gen = binding.bdd_smooth_forward(smooth.h, K, c.data_ptr(), bound.data_ptr(), sp)
+        binding.bdd_smooth_backward(smooth.h, gen, gbound.data_ptr(), grad.data_ptr(), sp)
 
     ms_fb = timed(fwd_bwd)
     smooth_bound = float(bound.item())
@@ -608,8 +608,8 @@ def run_differentiation(args, stream) -> dict:
     ss = Solver(sl, omega=0.5, stream=sp, alpha=alpha)
     csl = torch.tensor(sl.c, device="cuda")
     gsl = torch.zeros(sl.n, dtype=torch.float32, device="cuda")
-    binding.bdd_smooth_forward(ss.h, K, csl.data_ptr(), bound.data_ptr(), sp)
-    binding.bdd_smooth_backward(ss.h, gbound.data_ptr(), gsl.data_ptr(), sp)
+    gen = binding.bdd_smooth_forward(ss.h, K, csl.data_ptr(), bound.data_ptr(), sp)
+    binding.bdd_smooth_backward(ss.h, gen, gbound.data_ptr(), gsl.data_ptr(), sp)
     g = gsl.cpu().numpy().astype(np.float64)
 
     def ob(cv):

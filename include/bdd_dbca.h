@@ -42,7 +42,8 @@ enum {
   BDD_ECUDA = -5,       /* a CUDA runtime call failed (no device, launch failure, ...) */
   BDD_ETIMEOUT = -6,    /* reserved: a bounded device-side wait gave up */
   BDD_EDEVICE = -7,     /* a device-side check failed */
-  BDD_ESTATE = -8       /* the call needs device state but the solver was built host-only */
+  BDD_ESTATE = -8       /* the call needs device state but the solver was built host-only, or a
+                           smoothed backward has no matching forward */
 };
 
 #define BDD_SIZES_LEN 16
@@ -205,13 +206,19 @@ int bdd_bound_parts(bdd_solver *h, int nparts, const long long *row_off, const l
  * bdd_smooth_forward sets c (device float[n]), restarts (lambda = c/|J_i|), runs K iterations
  * and writes the smoothed bound after them (the y-slack form with every minimum soft) to
  * d_bound (device double[1]); it keeps a checkpoint of the multipliers and shares of every sweep
- * (2 K O floats of device memory).  bdd_smooth_backward then writes d_grad_c (device float[n])
+ * (2 K O floats of device memory) and stores the forward's generation number in *generation
+ * (host; NULL skips it).  bdd_smooth_backward then writes d_grad_c (device float[n])
  * = g * d bound / d c, g read from d_gbound (device double[1]), by reverse-mode passes over the
  * K iterations that recompute each sweep's messages from its checkpoint (hand-written adjoint
- * kernels).  The backward must follow its forward with no state-changing call in between
- * (else BDD_ESTATE).  Both enqueue on `stream` (NULL = the solver's stream) and return. */
-int bdd_smooth_forward(bdd_solver *h, int K, const float *d_c, double *d_bound, void *stream);
-int bdd_smooth_backward(bdd_solver *h, const double *d_gbound, float *d_grad_c, void *stream);
+ * kernels).  `generation` names the forward whose gradient is wanted: it must be the value that
+ * forward returned, it must be the solver's last forward, and no state-changing call may come
+ * in between; otherwise BDD_ESTATE (so two forwards on one solver feeding one loss cannot take
+ * the second one's checkpoints for the first one's gradient).  Both enqueue on `stream` (NULL =
+ * the solver's stream) and return. */
+int bdd_smooth_forward(bdd_solver *h, int K, const float *d_c, double *d_bound, long long *generation,
+                       void *stream);
+int bdd_smooth_backward(bdd_solver *h, long long generation, const double *d_gbound, float *d_grad_c,
+                        void *stream);
 
 /* Replaces c and restarts: lambda = c/|J_i|, pending sums 0, one backward pass.  c: float[n],
  * host. */

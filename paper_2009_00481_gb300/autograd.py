@@ -23,7 +23,7 @@ class SmoothedBound(torch.autograd.Function):
             raise ValueError("costs must be a CUDA tensor")
         c32 = c.detach().to(torch.float32).contiguous()
         bound = torch.empty((), dtype=torch.float64, device=c.device)
-        B.bdd_smooth_forward(solver.h, K, c32.data_ptr(), bound.data_ptr(), _stream_ptr())
+        ctx.generation = B.bdd_smooth_forward(solver.h, K, c32.data_ptr(), bound.data_ptr(), _stream_ptr())
         ctx.solver = solver
         ctx.c_dtype = c.dtype
         ctx.keep = c32
@@ -33,7 +33,9 @@ class SmoothedBound(torch.autograd.Function):
     def backward(ctx, g):
         g64 = g.detach().to(torch.float64).contiguous().reshape(())
         grad = torch.empty(ctx.keep.shape, dtype=torch.float32, device=ctx.keep.device)
-        B.bdd_smooth_backward(ctx.solver.h, g64.data_ptr(), grad.data_ptr(), _stream_ptr())
+        # the checkpoints must still be this forward's (a later forward on the same solver
+        # replaces them: the library then refuses with BDD_ESTATE)
+        B.bdd_smooth_backward(ctx.solver.h, ctx.generation, g64.data_ptr(), grad.data_ptr(), _stream_ptr())
         return grad.to(ctx.c_dtype), None, None
 
 

@@ -80,8 +80,8 @@ def load(path: str | None = None):
     lib.bdd_free.restype = None
     lib.bdd_lower_bound_noalloc.argtypes = [i32, i32, vp, vp, vp, f64, vp, vp]
     lib.bdd_bound_parts.argtypes = [vp, i32, P(i64), P(i64), P(f64)]
-    lib.bdd_smooth_forward.argtypes = [vp, i32, vp, vp, vp]
-    lib.bdd_smooth_backward.argtypes = [vp, vp, vp, vp]
+    lib.bdd_smooth_forward.argtypes = [vp, i32, vp, vp, P(i64), vp]
+    lib.bdd_smooth_backward.argtypes = [vp, i64, vp, vp, vp]
     lib.bdd_cuthill_mckee.argtypes = [i32, i32, P(i64), P(i32), P(i32), P(i32)]
     lib.bdd_get_cuts.argtypes = [vp, P(i32)]
     lib.bdd_get_copy_duals.argtypes = [vp, P(f32), P(f32)]
@@ -256,15 +256,19 @@ def bdd_bound_parts(h, row_off, var_off) -> np.ndarray:
     return out
 
 
-def bdd_smooth_forward(h, K: int, d_c: int, d_bound: int, stream: int = 0):
-    """Smoothed bound after K iterations from costs c (device pointers as integers)."""
-    _check(load().bdd_smooth_forward(h, int(K), d_c or None, d_bound or None, stream or None),
+def bdd_smooth_forward(h, K: int, d_c: int, d_bound: int, stream: int = 0) -> int:
+    """Smoothed bound after K iterations from costs c (device pointers as integers).  Returns
+    the forward's generation number, which bdd_smooth_backward needs."""
+    gen = C.c_longlong(-1)
+    _check(load().bdd_smooth_forward(h, int(K), d_c or None, d_bound or None, C.byref(gen), stream or None),
            "bdd_smooth_forward")
+    return int(gen.value)
 
 
-def bdd_smooth_backward(h, d_gbound: int, d_grad_c: int, stream: int = 0):
-    """g * d(smoothed bound)/dc into d_grad_c, for the last bdd_smooth_forward."""
-    _check(load().bdd_smooth_backward(h, d_gbound or None, d_grad_c or None, stream or None),
+def bdd_smooth_backward(h, generation: int, d_gbound: int, d_grad_c: int, stream: int = 0):
+    """g * d(smoothed bound)/dc into d_grad_c for the forward that returned `generation`
+    (BDDError with BDD_ESTATE if it is no longer the solver's last forward)."""
+    _check(load().bdd_smooth_backward(h, int(generation), d_gbound or None, d_grad_c or None, stream or None),
            "bdd_smooth_backward")
 
 

@@ -197,7 +197,6 @@ struct bdd_solver {
     p.omega = omega;
     p.alpha = alpha;
     p.error = d_error;
-    p.spin_limit = spin_limit;
     p.inv_alpha = alpha > 0.f ? 1.f / alpha : 0.f;
     p.copy_val = d_mu_bar;
     p.split = npairs > 0 ? 1 : 0;
@@ -1075,7 +1074,8 @@ int bdd_set_costs(bdd_solver *h, const float *c) {
   return BDD_OK;
 }
 
-int bdd_smooth_forward(bdd_solver *h, int K, const float *d_c, double *d_bound, void *stream) {
+int bdd_smooth_forward(bdd_solver *h, int K, const float *d_c, double *d_bound, long long *generation,
+                       void *stream) {
   if (!h || K < 1 || (h->n > 0 && !d_c) || !d_bound) return BDD_EINVAL;
   if (h->host_only) return BDD_ESTATE;
   if (!(h->alpha > 0.f)) return BDD_ESTATE;
@@ -1131,13 +1131,16 @@ int bdd_smooth_forward(bdd_solver *h, int K, const float *d_c, double *d_bound, 
   ++h->state_gen;
   h->smooth_gen = h->state_gen;
   h->smooth_K = K;
+  if (generation) *generation = h->smooth_gen;
   return h->end(s);
 }
 
-int bdd_smooth_backward(bdd_solver *h, const double *d_gbound, float *d_grad_c, void *stream) {
+int bdd_smooth_backward(bdd_solver *h, long long generation, const double *d_gbound, float *d_grad_c,
+                        void *stream) {
   if (!h || !d_gbound || (h->n > 0 && !d_grad_c)) return BDD_EINVAL;
   if (h->host_only) return BDD_ESTATE;
-  if (h->smooth_K < 1 || h->smooth_gen != h->state_gen) return BDD_ESTATE;
+  // the checkpoints belong to the last forward, and only while nothing has changed the state since
+  if (h->smooth_K < 1 || h->smooth_gen != h->state_gen || generation != h->smooth_gen) return BDD_ESTATE;
   DeviceGuard dg(h->device);
   if (!dg.ok) return BDD_ECUDA;
   cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
@@ -1424,7 +1427,7 @@ const char *bdd_strerror(int code) {
     case BDD_ECUDA: return "CUDA runtime error";
     case BDD_ETIMEOUT: return "device-side wait gave up";
     case BDD_EDEVICE: return "device-side check failed";
-    case BDD_ESTATE: return "solver was built host-only";
+    case BDD_ESTATE: return "call not valid in the solver's state (host-only solver, or no matching smoothed forward)";
     default: return "unknown status";
   }
 }

@@ -225,7 +225,7 @@ struct SweepParams {
   int fin_cap;
   double fin_const;
   int *error;            // set to BDD_ETIMEOUT if a bounded wait on a shared-memory copy gives up
-  long long spin_limit;  // polls of such a wait: spin_limit / 64 (at least 1)
+                         // (a fixed time limit, kRingWaitNs in kernels.cu)
   FusedParams fz;       // fz.cnt == null outside the fused plan
 };
 

@@ -334,12 +334,24 @@ __device__ __forceinline__ bool bar_try_wait(unsigned long long *bar, unsigned p
       : "memory");
   return ok != 0;
 }
-// bounded wait for phase `parity`; false if it did not complete within the poll limit
-__device__ __forceinline__ bool bar_wait(unsigned long long *bar, unsigned parity, long long limit) {
-  for (long long i = 0; i < limit; ++i)
-    if (bar_try_wait(bar, parity)) return true;
-  return false;
+// the GPU's global nanosecond timer
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
+// bounded wait for phase `parity`; false if it did not complete within `ns` nanoseconds
+__device__ __forceinline__ bool bar_wait_ns(unsigned long long *bar, unsigned parity, unsigned long long ns) {
+  if (bar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!bar_try_wait(bar, parity))
+    if (global_ns() - t0 > ns) return false;
+  return true;
+}
+// Time limit of a wait on a window's bulk copies.  Copies that were issued always complete, in
+// microseconds, so this limit only guards against a fault elsewhere; it is independent of
+// bdd_options.spin_limit (the grid-barrier poll limit).
+constexpr unsigned long long kRingWaitNs = 2000000000ull;
 __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_u32(dst)),
@@ -348,6 +360,8 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned b
 }
 // generic-proxy writes to global memory (earlier phases of a persistent launch) before bulk reads
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+// generic-proxy writes to this block's shared memory before bulk copies (async proxy) into it
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // A contiguous element range [first, first + n) of an array, widened to whole 16-byte blocks
 // for a bulk copy: the copy starts at a0 and the range's first element lands `shift` elements
@@ -418,11 +432,24 @@ __device__ __forceinline__ WindowRanges ranges_of(const SweepParams &p, int occ0
   return r;
 }
 
-// Lane 0 issues a window's bulk copies into S on `bar`: with `expect`, first the expected byte
-// count of the whole window; then the static and/or the dynamic copies.
-__device__ __forceinline__ void stage_window(const WindowRanges &r, WarpStage &S, unsigned long long *bar,
-                                             bool expect, bool stat, bool dyn) {
+// Per-warp copy state: two stage buffers, their mbarriers, the parity each waits for next, and
+// which buffers have copies issued that no wait has consumed yet.
+struct StageRing {
+  WarpStage *S;              // [kWarpStages]
+  unsigned long long *bar;   // [kWarpStages]
+  unsigned parity;           // bit b: parity of buffer b's next phase (lane-uniform)
+  unsigned busy;             // bit b: a window was issued into buffer b and not yet waited for
+};
+
+// Lane 0 issues a window's bulk copies into buffer b: with `expect`, first the expected byte
+// count of the whole window; then the static and/or the dynamic copies.  Warp-collective (every
+// lane keeps the same ring state).
+__device__ __forceinline__ void stage_window(const WindowRanges &r, StageRing &ring, int b, bool expect, bool stat,
+                                             bool dyn) {
+  if (expect) ring.busy |= 1u << b;
   if ((threadIdx.x & 31) != 0) return;
+  WarpStage &S = ring.S[b];
+  unsigned long long *bar = &ring.bar[b];
   if (expect)
     bar_expect(bar, r.off.bytes + r.lohi.bytes + r.slot.bytes + r.lam.bytes + r.shr.bytes + r.msg.bytes);
   if (stat) {
@@ -437,26 +464,30 @@ __device__ __forceinline__ void stage_window(const WindowRanges &r, WarpStage &S
   }
 }
 
-// Per-warp copy state: two stage buffers, their mbarriers and the parity each waits for next.
-struct StageRing {
-  WarpStage *S;              // [kWarpStages]
-  unsigned long long *bar;   // [kWarpStages]
-  unsigned parity;           // bit b: parity of buffer b's next phase (lane-uniform)
-};
-
-// wait for buffer b's window; on a timeout record BDD_ETIMEOUT and report false (the caller
-// abandons the tile after one more bounded wait for the copies in flight)
-__device__ __forceinline__ bool ring_wait(const SweepParams &p, StageRing &ring, int b) {
-  const long long limit = p.spin_limit / 64 > 0 ? p.spin_limit / 64 : 1;
-  const unsigned par = (ring.parity >> b) & 1u;
-  const bool ok = __all_sync(kFull, bar_wait(&ring.bar[b], par, limit));
-  if (!ok) {
-    if ((threadIdx.x & 31) == 0) atomicExch(p.error, -6);
-    bar_wait(&ring.bar[b], par, limit);
-    return false;
+// Waits (bounded) for every window still in flight in the ring, so that no copy lands in this
+// warp's shared memory after it stops using the ring.
+__device__ __forceinline__ void ring_drain(StageRing &ring) {
+  for (int b = 0; b < kWarpStages; ++b) {
+    if (!((ring.busy >> b) & 1u)) continue;
+    const unsigned par = (ring.parity >> b) & 1u;
+    if (__all_sync(kFull, bar_wait_ns(&ring.bar[b], par, kRingWaitNs))) ring.parity ^= 1u << b;
   }
-  ring.parity ^= 1u << b;
-  return true;
+  ring.busy = 0u;
+}
+
+// wait for buffer b's window; on a timeout record BDD_ETIMEOUT, drain the copies this warp
+// still has in flight and report false (the caller abandons the tile, and a persistent launch
+// takes no further tile)
+__device__ __forceinline__ bool ring_wait(const SweepParams &p, StageRing &ring, int b) {
+  const unsigned par = (ring.parity >> b) & 1u;
+  if (__all_sync(kFull, bar_wait_ns(&ring.bar[b], par, kRingWaitNs))) {
+    ring.parity ^= 1u << b;
+    ring.busy &= ~(1u << b);
+    return true;
+  }
+  if ((threadIdx.x & 31) == 0) atomicExch(p.error, -6);
+  ring_drain(ring);
+  return false;
 }
 
 // Tile parameters, depths and the window table (all static, read before the dependency wait).
@@ -494,13 +525,13 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
   Window Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, 0);
   {
     const WindowRanges r = ranges_of<true, MODE>(p, occ0, Wn);
-    stage_window(r, ring.S[0], &ring.bar[0], true, true, false);
+    stage_window(r, ring, 0, true, true, false);
     pdl_wait();
-    stage_window(r, ring.S[0], &ring.bar[0], false, false, true);
+    stage_window(r, ring, 0, false, false, true);
   }
   if (nw > 1) {
     const Window W1 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, 1);
-    stage_window(ranges_of<true, MODE>(p, occ0, W1), ring.S[1], &ring.bar[1], true, true, true);
+    stage_window(ranges_of<true, MODE>(p, occ0, W1), ring, 1, true, true, true);
   }
   float f_prev = inf(), lam_prev = 0.f;
   int2 lh_prev = make_int2(kNone, kNone);
@@ -567,13 +598,16 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
     __syncwarp();  // this buffer is free: stage the window after next into it
     if (w + 2 < nw) {
       const Window W2 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w + 2);
-      stage_window(ranges_of<true, MODE>(p, occ0, W2), S, &ring.bar[b], true, true, true);
+      stage_window(ranges_of<true, MODE>(p, occ0, W2), ring, b, true, true, true);
     }
   }
   if (MODE == kUpdateFused) {
     __syncwarp();
     pending_tail<true>(p, occ0, __reduce_add_sync(kFull, lead_depth), lane, 32,
                        reinterpret_cast<int *>(ring.S[0].lohi));
+    // the list was written through the generic proxy into a buffer that bulk copies fill
+    fence_proxy_async_smem();
+    __syncwarp();
   }
 }
 
@@ -590,13 +624,13 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
   Window Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, nw - 1);
   {
     const WindowRanges r = ranges_of<false, MODE>(p, occ0, Wn);
-    stage_window(r, ring.S[0], &ring.bar[0], true, true, false);
+    stage_window(r, ring, 0, true, true, false);
     pdl_wait();
-    stage_window(r, ring.S[0], &ring.bar[0], false, false, true);
+    stage_window(r, ring, 0, false, false, true);
   }
   if (nw > 1) {
     const Window W1 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, nw - 2);
-    stage_window(ranges_of<false, MODE>(p, occ0, W1), ring.S[1], &ring.bar[1], true, true, true);
+    stage_window(ranges_of<false, MODE>(p, occ0, W1), ring, 1, true, true, true);
   }
   float b_next = inf();
   int node0_next = 0;
@@ -667,13 +701,16 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
     __syncwarp();
     if (w >= 2) {
       const Window W2 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w - 2);
-      stage_window(ranges_of<false, MODE>(p, occ0, W2), S, &ring.bar[b], true, true, true);
+      stage_window(ranges_of<false, MODE>(p, occ0, W2), ring, b, true, true, true);
     }
   }
   if (MODE == kUpdateFused) {
     __syncwarp();
     pending_tail<false>(p, occ0, __reduce_add_sync(kFull, lead_depth), lane, 32,
                         reinterpret_cast<int *>(ring.S[0].lohi));
+    // the list was written through the generic proxy into a buffer that bulk copies fill
+    fence_proxy_async_smem();
+    __syncwarp();
   }
 }
 
@@ -1380,7 +1417,7 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
     if (tile >= p.class_tile_off[kWarpClasses]) return;  // whole warp leaves together
     char *mine = reinterpret_cast<char *>(smem) + (size_t)warp * (STAGE == 2 ? kWarpSmemBytes2 : kWarpSmemBytes);
     if constexpr (STAGE >= 1) {
-      StageRing none{nullptr, nullptr, 0u};
+      StageRing none{nullptr, nullptr, 0u, 0u};
       warp_tile<FWD, MODE, SMOOTH, STAGE, SPLIT>(p, ph, tile, none, bacc, reinterpret_cast<WarpStage8 *>(mine));
     } else {
       __shared__ unsigned long long bars[kWarpsPerBlock * kWarpStages];
@@ -1389,7 +1426,7 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
         bar_init_fence();
       }
       __syncwarp();
-      StageRing ring{reinterpret_cast<WarpStage *>(mine), &bars[warp * kWarpStages], 0u};
+      StageRing ring{reinterpret_cast<WarpStage *>(mine), &bars[warp * kWarpStages], 0u, 0u};
       warp_tile<FWD, MODE, SMOOTH, 0, SPLIT>(p, ph, tile, ring, bacc);
     }
     // the previous iteration's bound, by warp 0 of the last warp block (its tiles are the
@@ -1547,8 +1584,12 @@ __device__ __forceinline__ void persistent_phase(const SweepParams &p, float *sm
   const int warp = threadIdx.x >> 5;
   const int W = gridDim.x * kPersistWarps;
   const int nwt = p.class_tile_off[kWarpClasses];
-  for (int tile = blockIdx.x * kPersistWarps + warp; tile < nwt; tile += W)
+  for (int tile = blockIdx.x * kPersistWarps + warp; tile < nwt; tile += W) {
+    // a wait of this launch gave up: its ring may be out of step, so take no further tile (the
+    // next grid barrier sees the error and ends the launch)
+    if (*reinterpret_cast<volatile int *>(p.error) != 0) break;
     warp_tile<FWD, kUpdate, false>(p, ph, tile, ring, bacc);
+  }
   const int bt0 = p.class_tile_off[kWarpClasses];
   const int nbt = p.class_tile_off[kWarpClasses + 1] - bt0;
   if (nbt > 0) {
@@ -1562,6 +1603,10 @@ __device__ __forceinline__ void persistent_phase(const SweepParams &p, float *sm
         block_backward<kUpdate, false>(p, ph, bt0 + t, g, group, gt, bacc);
       group_sync(group);
     }
+    // the group buffers were written through the generic proxy; the next phase's bulk copies
+    // (async proxy) write the same shared memory: order the two
+    fence_proxy_async_smem();
+    __syncthreads();
   }
 }
 
@@ -1610,7 +1655,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) iterate_kernel(const IterP
   }
   __syncwarp();
   StageRing ring{reinterpret_cast<WarpStage *>(reinterpret_cast<char *>(smem) + (size_t)warp * kWarpSmemBytes),
-                 &bars[warp * kWarpStages], 0u};
+                 &bars[warp * kWarpStages], 0u, 0u};
   bool failed = false;
   for (int it = 0; it < q.n_iter; ++it) {
     double bacc = 0.0;
