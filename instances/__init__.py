@@ -17,6 +17,7 @@ from .generators import (  # noqa: F401
     tracking,
     potts_batch,
     potts_batch_member,
+    potts_batch_shape,
     random_ilp,
     config,
     CONFIG_NAMES,

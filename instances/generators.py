@@ -157,6 +157,15 @@ def potts_grid_2label(H: int, W: int, seed: int) -> Instance:
     return potts_mrf(H, W, 2, seed=seed)
 
 
+def potts_batch_shape(s: int, side_range=(16, 128), label_range=(2, 8)):
+    """(side, labels) that instance s of the Potts batch draws (the first two draws of
+    ``default_rng(s)``), without generating its costs."""
+    rng = np.random.default_rng(s)
+    side = int(rng.integers(side_range[0], side_range[1] + 1))
+    L = int(rng.integers(label_range[0], label_range[1] + 1))
+    return side, L
+
+
 def potts_batch_member(s: int, side_range=(16, 128), label_range=(2, 8)) -> Instance:
     """Instance s of the Potts batch on its own (same draws as inside :func:`potts_batch`)."""
     rng = np.random.default_rng(s)
@@ -169,18 +178,20 @@ def potts_batch_member(s: int, side_range=(16, 128), label_range=(2, 8)) -> Inst
 
 
 def potts_batch(count: int = 256, side_range=(16, 128), label_range=(2, 8), first_seed: int = 0,
-                stride: int = 1) -> Instance:
+                stride: int = 1, seeds=None) -> Instance:
     """Block-diagonal packing of independent Potts instances of uneven size.
 
-    Instance s (s = first_seed + k*stride) draws side ~ U{side_range}, labels ~ U{label_range}
-    and its costs as in :func:`potts_mrf`, all from ``default_rng(s)``.
+    Instance s (s = first_seed + k*stride, or the listed `seeds`) draws side ~ U{side_range},
+    labels ~ U{label_range} and its costs as in :func:`potts_mrf`, all from ``default_rng(s)``.
     """
     cols, vals, bs, senses, cs, lens = [], [], [], [], [], []
     var_parts, row_parts = [0], [0]
     voff = 0
     sizes = []
+    seed_list = list(seeds) if seeds is not None else [first_seed + k * stride for k in range(count)]
+    count = len(seed_list)
     for k in range(count):
-        s = first_seed + k * stride
+        s = seed_list[k]
         rng = np.random.default_rng(s)
         side = int(rng.integers(side_range[0], side_range[1] + 1))
         L = int(rng.integers(label_range[0], label_range[1] + 1))
