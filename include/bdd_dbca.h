@@ -46,7 +46,7 @@ enum {
                            smoothed backward has no matching forward */
 };
 
-#define BDD_SIZES_LEN 16
+#define BDD_SIZES_LEN 17
 
 /* Options for bdd_build.  Fill with bdd_default_options, then change fields. */
 typedef struct {
@@ -143,6 +143,13 @@ typedef struct {
                                  sweep walks, which a partition of the variable order does not
                                  (a BDD over consecutive variables stays whole unless a cut falls
                                  inside it).  Overrides split_intervals and cuts. */
+  int lanes;                  /* BDDs whose layers have at most two nodes: 1 = lane tiles (one
+                                 lane per BDD holds both nodes of a layer, 32 BDDs per warp, no
+                                 shuffles or team reductions); 0 = two-lane teams (16 BDDs per
+                                 warp).  Same values bit for bit.  Lane tiles need a plain
+                                 solver (alpha = 0, no split, separate pending kernels, schedule
+                                 1), else BDD_EINVAL.  -1 (default): lane tiles on plain
+                                 solvers, teams otherwise. */
 } bdd_options;
 
 void bdd_default_options(bdd_options *opt);
@@ -230,7 +237,7 @@ int bdd_set_costs(bdd_solver *h, const float *c);
  * warp-tile staging the autotuner chose for the update sweeps: bits 0-1 forward, bits 2-3 backward
  * (0 bulk-copy ring of 4-layer windows, 1 8-layer cp.async windows, 2 the same
  * double-buffered), [13] cuts of the variable order, [14] copy-arc pairs, [15] depth limit of a
- * depth split (0: none). */
+ * depth split (0: none), [16] 1 if BDDs of width <= 2 run as lane tiles (bdd_options.lanes). */
 int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]);
 
 /* Canonical form of the BDDs, read back from the device slabs (or the host copy when built

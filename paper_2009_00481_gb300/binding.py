@@ -16,7 +16,7 @@ from .build import LIB
 
 BDD_OK, BDD_EINVAL, BDD_EINFEASIBLE, BDD_ETOOBIG, BDD_ENOMEM = 0, -1, -2, -3, -4
 BDD_ECUDA, BDD_ETIMEOUT, BDD_EDEVICE, BDD_ESTATE = -5, -6, -7, -8
-BDD_SIZES_LEN = 16
+BDD_SIZES_LEN = 17
 
 EXPORTED = [
     "bdd_default_options", "bdd_build", "bdd_last_failed_row", "bdd_iterate", "bdd_iterate_device",
@@ -35,7 +35,7 @@ class bdd_options(C.Structure):
                 ("alpha", C.c_float), ("var_rank", C.POINTER(C.c_int)), ("averaging", C.c_int),
                 ("fused_pending", C.c_int), ("staging", C.c_int), ("split_intervals", C.c_int),
                 ("cuts", C.POINTER(C.c_int)), ("n_cuts", C.c_int), ("gamma", C.c_float),
-                ("split_depth", C.c_int)]
+                ("split_depth", C.c_int), ("lanes", C.c_int)]
 
 
 class BDDError(RuntimeError):

@@ -96,6 +96,7 @@ struct bdd_solver {
   int2 *d_win_node = nullptr;
   int *d_var_ptr = nullptr, *d_var_occ = nullptr;
   int averaging = 0;                     // 0: eq. mma-update; 1: SRMP (Appendix A.4)
+  bool lanes2 = false;                   // BDDs of width <= 2 run as lane tiles
   int stage_fwd = 0, stage_bwd = 0;      // warp-tile staging of the update sweeps (autotuned)
   int staging_opt = -1;                  // bdd_options.staging
   float tune_ms[kStagings][2] = {};      // measured ms per sweep [variant][direction]
@@ -192,6 +193,7 @@ struct bdd_solver {
     p.out_m1 = out_m1;
     for (int c = 0; c < kWarpClasses + 2; ++c) p.class_tile_off[c] = class_tile_off[c];
     p.n_warp_blocks = n_warp_blocks;
+    p.lanes2 = lanes2 ? 1 : 0;
     p.block_buf = block_buf;
     p.block_depth_buf = block_depth_buf;
     p.omega = omega;
@@ -599,8 +601,8 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c, const CutTables
   const int heavy_blocks = (n_heavy + kReduceThreads / 32 - 1) / (kReduceThreads / 32);
   h->grid_reduce = std::max(1, std::min(std::max((range + kReduceThreads - 1) / kReduceThreads, heavy_blocks), 152 * 16));
   // the largest dynamic shared memory any staging variant's sweep launch asks for
-  h->smem = std::max(sweep_smem_bytes(h->block_buf, h->block_depth_buf, 0),
-                     sweep_smem_bytes(h->block_buf, h->block_depth_buf, 2));
+  h->smem = std::max(sweep_smem_bytes(h->block_buf, h->block_depth_buf, 0, h->lanes2),
+                     sweep_smem_bytes(h->block_buf, h->block_depth_buf, 2, h->lanes2));
   h->smem_persist = persist_smem_bytes(h->block_buf, h->block_depth_buf);
   if (h->smem > 48 * 1024 && sweep_set_smem(h->smem)) return BDD_ECUDA;
   if (h->schedule == 0) {
@@ -755,6 +757,7 @@ void bdd_default_options(bdd_options *opt) {
   opt->n_cuts = 0;
   opt->gamma = 0.5f;
   opt->split_depth = 0;
+  opt->lanes = -1;
 }
 
 int bdd_last_failed_row(void) { return g_failed_row; }
@@ -787,6 +790,11 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   if (!(opt.gamma > 0.f && opt.gamma <= 1.f)) return BDD_EINVAL;
   const bool want_split = opt.split_depth > 0 || opt.n_cuts > 0 || opt.split_intervals >= 2;
   if (want_split && opt.alpha > 0.f) return BDD_EINVAL;  // sub-BDDs run the min-sum iteration only
+  if (opt.lanes < -1 || opt.lanes > 1) return BDD_EINVAL;
+  // lane tiles run the plain min-sum sweeps of the per-phase schedule only
+  const bool plain = opt.alpha == 0.f && !want_split && opt.fused_pending != 1 && opt.schedule == 1;
+  if (opt.lanes == 1 && !plain) return BDD_EINVAL;
+  const bool lanes2 = opt.lanes == 1 || (opt.lanes == -1 && plain);
   if (opt.var_rank) {  // a permutation of 0..n-1
     std::vector<char> seen;
     try {
@@ -814,6 +822,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   // the persistent kernel runs the plain min-sum iteration only
   h->schedule = opt.alpha > 0.f || want_split ? 1 : opt.schedule;
   h->gamma = opt.gamma;
+  h->lanes2 = lanes2;
   h->spin_limit = opt.spin_limit;
   if (opt.schedule < 0 || opt.schedule > 1 || opt.spin_limit < 1) {
     delete h;
@@ -879,7 +888,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   }
   Layout L;
   try {
-    rc = build_layout(H, &L);
+    rc = build_layout(H, &L, h->lanes2);
   } catch (const std::bad_alloc &) {
     rc = BDD_ENOMEM;
   }
@@ -1220,6 +1229,7 @@ int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]) {
   out[13] = (long long)h->cuts.size();
   out[14] = h->npairs;
   out[15] = h->split_depth;
+  out[16] = h->lanes2 ? 1 : 0;
   return BDD_OK;
 }
 

@@ -341,8 +341,9 @@ int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const i
   return BDD_OK;
 }
 
-int build_layout(const HostBDDs &H, Layout *L) {
+int build_layout(const HostBDDs &H, Layout *L, bool lanes2) {
   const long long nb = H.nb(), O = H.O(), N = H.N();
+  L->lanes2 = lanes2;
   // class of each BDD from its widest layer
   std::vector<int> cls(nb);
   for (long long b = 0; b < nb; ++b) {
@@ -350,6 +351,7 @@ int build_layout(const HostBDDs &H, Layout *L) {
     for (long long o = H.bdd_occ0[b]; o < H.bdd_occ0[b + 1]; ++o) w = std::max(w, H.occ_width[o]);
     int c = 0;
     while ((1 << c) < w && c < kWarpClasses) ++c;
+    if (lanes2 && w <= 2) c = 0;  // lane tiles: one lane holds both nodes of a layer
     if (w > 32) c = kWarpClasses;
     if (c == kWarpClasses && w > kMaxBlockTileWidth) return BDD_ETOOBIG;
     cls[b] = c;

@@ -128,6 +128,21 @@ struct alignas(16) WarpStage8 {
 constexpr size_t kWarpSmemBytes = (kWarpStages * sizeof(WarpStage) > sizeof(WarpStage8) ? kWarpStages * sizeof(WarpStage)
                                                                                           : sizeof(WarpStage8));
 constexpr size_t kWarpSmemBytes2 = 2 * sizeof(WarpStage8);
+
+// Lane tiles (layouts built with lanes2): BDDs whose layers have at most two nodes, one lane per
+// BDD, 32 BDDs per tile (warp class 0).  A window holds kWinLayers layers of up to 64 nodes each
+// (plus the layer after it for the backward messages of a forward update); two per warp, filled
+// by the bulk-copy ring.
+constexpr int kLaneWinNodes = 64 * kWinLayers;
+struct alignas(16) LaneStage {
+  int2 lohi[kLaneWinNodes + 2];
+  float msg[kLaneWinNodes + 64 + 4];
+  int off[kWinOcc + 8];
+  float lam[kWinOcc + 4];
+  float shr[kWinOcc + 4];
+  int slot[kWinOcc + 4];
+};
+constexpr size_t kLaneSmemBytes = kWarpStages * sizeof(LaneStage);
 constexpr int kStagings = 3;  // warp-tile staging variants of the update sweeps
 
 // Device slab layout (host staging copy).  Occurrences are grouped by tile; inside a warp
@@ -149,6 +164,7 @@ struct Layout {
   std::vector<int> tile_win0;                        // [ntiles + 1] window table offsets (warp tiles)
   std::vector<int> win_node;                         // window table, int pairs
   int class_tile_off[kWarpClasses + 2] = {0};        // tiles of class c: [off[c], off[c+1])
+  bool lanes2 = false;                               // class 0 = lane tiles of width <= 2
   int n_warp_tiles = 0, n_block_tiles = 0;
   int max_block_width = 0;
   std::vector<int> var_ptr;            // [n+1]
@@ -157,7 +173,9 @@ struct Layout {
   std::vector<int> occ_of_canon;       // canonical occurrence -> device occurrence
 };
 
-int build_layout(const HostBDDs &H, Layout *L);
+// lanes2: BDDs of width <= 2 form the lane tiles of class 0 (32 BDDs per tile, one lane each);
+// otherwise class c holds the BDDs whose widest layer needs a team of 2^c lanes.
+int build_layout(const HostBDDs &H, Layout *L, bool lanes2 = false);
 
 // Fused pending pass of an update sweep (the per-phase plan without separate pending kernels).
 // At the end of its tile every occurrence counts its variable down; the visit that brings the
@@ -207,6 +225,8 @@ struct SweepParams {
   float *out_m1;
   int class_tile_off[kWarpClasses + 2];
   int n_warp_blocks;
+  int lanes2;           // class-0 tiles are lane tiles (one lane per BDD of width <= 2)
+  int warp_smem;        // bytes of dynamic shared memory per warp of a warp block
   int block_buf;        // floats per shared-memory layer buffer of a block tile
   int block_depth_buf;  // floats for the per-layer shares of a block tile
   float omega;
@@ -337,7 +357,8 @@ int cut_launch(bool forward, const CutParams &c, cudaStream_t stream);
 int cut_roots_launch(const CutParams &c, cudaStream_t stream);
 
 // Launch wrappers (kernels.cu).  All enqueue on `stream` and return 0 or -5 (launch failure).
-size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging = 0);
+size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging = 0, bool lanes2 = false);
+size_t sweep_warp_smem(int staging, bool lanes2);
 size_t persist_smem_bytes(int block_buf, int block_depth_buf);
 int sweep_set_smem(size_t bytes);
 int iterate_set_smem(size_t bytes);

@@ -125,6 +125,16 @@ __device__ __forceinline__ double slack_term(double P, double alpha) {
   return m - alpha * log1p(exp(-fabs(P) / alpha));
 }
 
+// acc += the y-slack term of P.  For min-sum the term is min(0, P): only a negative P adds
+// anything, and the comparison is made in FP32 (exact), so a nonnegative P costs no FP64
+// instruction (this part's FP64 throughput is a small fraction of its FP32 throughput).
+__device__ __forceinline__ void add_slack(double &acc, float P, double alpha) {
+  if (alpha > 0.0)
+    acc += slack_term((double)P, alpha);
+  else if (P < 0.f)
+    acc += (double)P;
+}
+
 // the general path of pending_var for slots [s, e) of variable i
 __device__ __forceinline__ float pending_tail_sum(const float *__restrict__ delta, const int *__restrict__ var_occ,
                                                   float *__restrict__ P, float *__restrict__ share_occ, int i, int s,
@@ -434,21 +444,24 @@ __device__ __forceinline__ WindowRanges ranges_of(const SweepParams &p, int occ0
 
 // Per-warp copy state: two stage buffers, their mbarriers, the parity each waits for next, and
 // which buffers have copies issued that no wait has consumed yet.
-struct StageRing {
-  WarpStage *S;              // [kWarpStages]
+template <class Stage>
+struct StageRingT {
+  Stage *S;                  // [kWarpStages]
   unsigned long long *bar;   // [kWarpStages]
   unsigned parity;           // bit b: parity of buffer b's next phase (lane-uniform)
   unsigned busy;             // bit b: a window was issued into buffer b and not yet waited for
 };
+using StageRing = StageRingT<WarpStage>;
 
 // Lane 0 issues a window's bulk copies into buffer b: with `expect`, first the expected byte
 // count of the whole window; then the static and/or the dynamic copies.  Warp-collective (every
 // lane keeps the same ring state).
-__device__ __forceinline__ void stage_window(const WindowRanges &r, StageRing &ring, int b, bool expect, bool stat,
-                                             bool dyn) {
+template <class Stage>
+__device__ __forceinline__ void stage_window(const WindowRanges &r, StageRingT<Stage> &ring, int b, bool expect,
+                                             bool stat, bool dyn) {
   if (expect) ring.busy |= 1u << b;
   if ((threadIdx.x & 31) != 0) return;
-  WarpStage &S = ring.S[b];
+  Stage &S = ring.S[b];
   unsigned long long *bar = &ring.bar[b];
   if (expect)
     bar_expect(bar, r.off.bytes + r.lohi.bytes + r.slot.bytes + r.lam.bytes + r.shr.bytes + r.msg.bytes);
@@ -466,7 +479,8 @@ __device__ __forceinline__ void stage_window(const WindowRanges &r, StageRing &r
 
 // Waits (bounded) for every window still in flight in the ring, so that no copy lands in this
 // warp's shared memory after it stops using the ring.
-__device__ __forceinline__ void ring_drain(StageRing &ring) {
+template <class Stage>
+__device__ __forceinline__ void ring_drain(StageRingT<Stage> &ring) {
   for (int b = 0; b < kWarpStages; ++b) {
     if (!((ring.busy >> b) & 1u)) continue;
     const unsigned par = (ring.parity >> b) & 1u;
@@ -478,7 +492,8 @@ __device__ __forceinline__ void ring_drain(StageRing &ring) {
 // wait for buffer b's window; on a timeout record BDD_ETIMEOUT, drain the copies this warp
 // still has in flight and report false (the caller abandons the tile, and a persistent launch
 // takes no further tile)
-__device__ __forceinline__ bool ring_wait(const SweepParams &p, StageRing &ring, int b) {
+template <class Stage>
+__device__ __forceinline__ bool ring_wait(const SweepParams &p, StageRingT<Stage> &ring, int b) {
   const unsigned par = (ring.parity >> b) & 1u;
   if (__all_sync(kFull, bar_wait_ns(&ring.bar[b], par, kRingWaitNs))) {
     ring.parity ^= 1u << b;
@@ -711,6 +726,209 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
     // the list was written through the generic proxy into a buffer that bulk copies fill
     fence_proxy_async_smem();
     __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// lane tiles: one lane per BDD whose layers have at most two nodes, 32 BDDs per warp (the slab
+// of a warp tile of 32 one-lane teams).  A lane keeps both nodes of its BDD's current layer in
+// registers, so the forward push, the min-marginals and the backward pull need no shuffles and
+// no team reductions; windows of kWinLayers layers (up to 64 nodes each) are staged by the
+// bulk-copy ring as for warp tiles.  The arithmetic is that of a two-lane team, operation for
+// operation and in the same order, so the results equal the team layout's bit for bit.
+// ---------------------------------------------------------------------------------------
+using LaneRing = StageRingT<LaneStage>;
+
+// forward message of node t of a layer (Alg. 2) from the two nodes of the previous layer
+// (messages pf0, pf1; arcs r0, r1 as ids relative to this layer's first node, kNone for none;
+// 1-arc cost plam), relaxed in the order of the team path: node 0 before node 1, 0-arc first
+__device__ __forceinline__ float lane_push(int t, float pf0, int2 r0, float pf1, int2 r1, float plam) {
+  float f = inf();
+  if (r0.x == t) f = fminf(f, pf0);
+  if (r0.y == t) f = fminf(f, pf0 + plam);
+  if (r1.x == t) f = fminf(f, pf1);
+  if (r1.y == t) f = fminf(f, pf1 + plam);
+  return f;
+}
+
+__device__ __forceinline__ int2 rel_arcs(int2 lh, int node0) {
+  return make_int2(lh.x >= 0 ? lh.x - node0 : kNone, lh.y >= 0 ? lh.y - node0 : kNone);
+}
+
+template <int MODE>
+__device__ __forceinline__ void lane_forward(const SweepParams &p, const Phase &ph, int tile, LaneRing &ring) {
+  const int lane = threadIdx.x & 31;
+  const TileInfo ti = tile_info<1>(p, tile);
+  const int occ0 = ti.occ0, depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd, nw = ti.nw;
+  fence_proxy_async();
+  Window Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, 0);
+  {
+    const WindowRanges r = ranges_of<true, MODE>(p, occ0, Wn);
+    stage_window(r, ring, 0, true, true, false);
+    pdl_wait();
+    stage_window(r, ring, 0, false, false, true);
+  }
+  if (nw > 1) {
+    const Window W1 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, 1);
+    stage_window(ranges_of<true, MODE>(p, occ0, W1), ring, 1, true, true, true);
+  }
+  float pf0 = 0.f, pf1 = 0.f, plam = 0.f;
+  int2 plh0 = make_int2(kNone, kNone), plh1 = make_int2(kNone, kNone);
+  for (int w = 0; w < nw; ++w) {
+    const Window W = Wn;
+    if (w + 1 < nw) Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w + 1);
+    const int b = w & 1;
+    LaneStage &S = ring.S[b];
+    if (!ring_wait(p, ring, b)) return;
+    const WindowRanges r = ranges_of<true, MODE>(p, occ0, W);
+    const int *off = S.off + r.off.shift;
+    const int2 *lohi = S.lohi + r.lohi.shift;
+    const int *slot = S.slot + r.slot.shift;
+    const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
+    const int ca = W.ca, na = W.na, oa = occ0 + ca;
+    for (int l = W.l0; l < W.l1; ++l) {
+      const bool active = depth > l;
+      const int oi = occ_before(lead_depth, l) - ca + lane;
+      int node0 = 0, wl = 0;
+      if (active) {
+        node0 = off[oi];
+        wl = off[oi + 1] - node0;
+      }
+      // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv, for both nodes
+      float f0 = 0.f, f1 = 0.f;  // the root (layer 0)
+      if (l > 0) {
+        const int2 r0 = rel_arcs(plh0, node0), r1 = rel_arcs(plh1, node0);
+        f0 = lane_push(0, pf0, r0, pf1, r1, plam);
+        f1 = lane_push(1, pf0, r0, pf1, r1, plam);
+      }
+      int2 lh0 = make_int2(kNone, kNone), lh1 = make_int2(kNone, kNone);
+      if (wl > 0) {
+        p.fm[node0] = f0;
+        lh0 = lohi[node0 - na];
+      }
+      if (wl > 1) {
+        p.fm[node0 + 1] = f1;
+        lh1 = lohi[node0 - na + 1];
+      }
+      float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
+      if (is_update(MODE)) {
+        // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
+        const float a00 = wl > 0 ? f0 + staged_bm<false>(msg, p.copy_val, na, lh0.x) : inf();
+        const float a01 = wl > 1 ? f1 + staged_bm<false>(msg, p.copy_val, na, lh1.x) : inf();
+        const float a10 = wl > 0 ? f0 + lam + staged_bm<false>(msg, p.copy_val, na, lh0.y) : inf();
+        const float a11 = wl > 1 ? f1 + lam + staged_bm<false>(msg, p.copy_val, na, lh1.y) : inf();
+        const float m0 = fminf(a00, a01), m1 = fminf(a10, a11);
+        const float dd = p.omega * mm_difference(m0, m1);
+        lam -= dd;
+        if (active) {
+          p.lam[oa + oi] = lam;
+          ph.delta[slot[oi]] = dd;
+        }
+      }
+      pf0 = f0;
+      pf1 = f1;
+      plh0 = lh0;
+      plh1 = lh1;
+      plam = lam;
+    }
+    __syncwarp();  // this buffer is free: stage the window after next into it
+    if (w + 2 < nw) {
+      const Window W2 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w + 2);
+      stage_window(ranges_of<true, MODE>(p, occ0, W2), ring, b, true, true, true);
+    }
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void lane_backward(const SweepParams &p, const Phase &ph, int tile, LaneRing &ring,
+                                              double &bacc) {
+  const int lane = threadIdx.x & 31;
+  const TileInfo ti = tile_info<1>(p, tile);
+  const int occ0 = ti.occ0, depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd, nw = ti.nw;
+  const int bdd = p.tile_bdd0[tile] + lane;
+  fence_proxy_async();
+  Window Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, nw - 1);
+  {
+    const WindowRanges r = ranges_of<false, MODE>(p, occ0, Wn);
+    stage_window(r, ring, 0, true, true, false);
+    pdl_wait();
+    stage_window(r, ring, 0, false, false, true);
+  }
+  if (nw > 1) {
+    const Window W1 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, nw - 2);
+    stage_window(ranges_of<false, MODE>(p, occ0, W1), ring, 1, true, true, true);
+  }
+  float bn0 = inf(), bn1 = inf();  // backward messages of the next layer's two nodes
+  int node0_next = 0;
+  for (int k = 0; k < nw; ++k) {
+    const int w = nw - 1 - k;
+    const Window W = Wn;
+    if (w > 0) Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w - 1);
+    const int b = k & 1;
+    LaneStage &S = ring.S[b];
+    if (!ring_wait(p, ring, b)) return;
+    const WindowRanges r = ranges_of<false, MODE>(p, occ0, W);
+    const int *off = S.off + r.off.shift;
+    const int2 *lohi = S.lohi + r.lohi.shift;
+    const int *slot = S.slot + r.slot.shift;
+    const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
+    const int ca = W.ca, na = W.na, oa = occ0 + ca;
+    for (int l = W.l1 - 1; l >= W.l0; --l) {
+      const bool active = depth > l;
+      const int oi = occ_before(lead_depth, l) - ca + lane;
+      int node0 = 0, wl = 0;
+      if (active) {
+        node0 = off[oi];
+        wl = off[oi + 1] - node0;
+      }
+      int2 lh0 = make_int2(kNone, kNone), lh1 = make_int2(kNone, kNone);
+      float f0 = inf(), f1 = inf();
+      if (wl > 0) {
+        lh0 = lohi[node0 - na];
+        f0 = msg[node0 - na];
+      }
+      if (wl > 1) {
+        lh1 = lohi[node0 - na + 1];
+        f1 = msg[node0 - na + 1];
+      }
+      float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
+      // successors' backward messages: the next layer's nodes, held by this lane
+      auto pull = [&](int t) {
+        return t >= 0 ? (((t - node0_next) & 1) == 0 ? bn0 : bn1) : terminal_bm<false>(p.copy_val, t);
+      };
+      const float b00 = pull(lh0.x), b01 = pull(lh0.y), b10 = pull(lh1.x), b11 = pull(lh1.y);
+      if (MODE != kMessages) {
+        const float m0 = fminf(f0 + b00, f1 + b10), m1 = fminf(f0 + lam + b01, f1 + lam + b11);
+        if (is_update(MODE)) {
+          const float dd = p.omega * mm_difference(m0, m1);
+          lam -= dd;
+          if (active) {
+            p.lam[oa + oi] = lam;
+            ph.delta[slot[oi]] = dd;
+          }
+        } else if (active && p.out_m0) {
+          const long long c = p.occ_csr[oa + oi];
+          p.out_m0[c] = m0;
+          p.out_m1[c] = m1;
+        }
+      }
+      // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
+      const float bc0 = fminf(b00, lam + b01), bc1 = fminf(b10, lam + b11);
+      if (wl > 0) p.bm[node0] = bc0;
+      if (wl > 1) p.bm[node0 + 1] = bc1;
+      if (l == 0 && active) {  // E^j(lambda^j) at the root
+        p.bdd_E[bdd] = bc0;
+        bacc += (double)bc0;
+      }
+      bn0 = bc0;
+      bn1 = bc1;
+      node0_next = node0;
+    }
+    __syncwarp();
+    if (w >= 2) {
+      const Window W2 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w - 2);
+      stage_window(ranges_of<false, MODE>(p, occ0, W2), ring, b, true, true, true);
+    }
   }
 }
 
@@ -1415,19 +1633,34 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
     const int warp = threadIdx.x >> 5;
     const int tile = blockIdx.x * kWarpsPerBlock + warp;
     if (tile >= p.class_tile_off[kWarpClasses]) return;  // whole warp leaves together
-    char *mine = reinterpret_cast<char *>(smem) + (size_t)warp * (STAGE == 2 ? kWarpSmemBytes2 : kWarpSmemBytes);
-    if constexpr (STAGE >= 1) {
-      StageRing none{nullptr, nullptr, 0u, 0u};
-      warp_tile<FWD, MODE, SMOOTH, STAGE, SPLIT>(p, ph, tile, none, bacc, reinterpret_cast<WarpStage8 *>(mine));
-    } else {
-      __shared__ unsigned long long bars[kWarpsPerBlock * kWarpStages];
+    char *mine = reinterpret_cast<char *>(smem) + (size_t)warp * p.warp_smem;
+    __shared__ unsigned long long bars[kWarpsPerBlock * kWarpStages];
+    constexpr bool kLanes = !SMOOTH && !SPLIT && MODE != kUpdateFused;
+    const bool lane_tile = kLanes && p.lanes2 && tile < p.class_tile_off[1];
+    if (lane_tile || STAGE == 0) {
       if ((threadIdx.x & 31) == 0) {
         for (int b = 0; b < kWarpStages; ++b) bar_init(&bars[warp * kWarpStages + b]);
         bar_init_fence();
       }
       __syncwarp();
-      StageRing ring{reinterpret_cast<WarpStage *>(mine), &bars[warp * kWarpStages], 0u, 0u};
-      warp_tile<FWD, MODE, SMOOTH, 0, SPLIT>(p, ph, tile, ring, bacc);
+    }
+    if constexpr (kLanes) {
+      if (lane_tile) {
+        LaneRing ring{reinterpret_cast<LaneStage *>(mine), &bars[warp * kWarpStages], 0u, 0u};
+        if (FWD)
+          lane_forward<MODE>(p, ph, tile, ring);
+        else
+          lane_backward<MODE>(p, ph, tile, ring, bacc);
+      }
+    }
+    if (!lane_tile) {
+      if constexpr (STAGE >= 1) {
+        StageRing none{nullptr, nullptr, 0u, 0u};
+        warp_tile<FWD, MODE, SMOOTH, STAGE, SPLIT>(p, ph, tile, none, bacc, reinterpret_cast<WarpStage8 *>(mine));
+      } else {
+        StageRing ring{reinterpret_cast<WarpStage *>(mine), &bars[warp * kWarpStages], 0u, 0u};
+        warp_tile<FWD, MODE, SMOOTH, 0, SPLIT>(p, ph, tile, ring, bacc);
+      }
     }
     // the previous iteration's bound, by warp 0 of the last warp block (its tiles are the
     // shallowest, so the chain's critical path does not wait for this)
@@ -1493,7 +1726,7 @@ __global__ void __launch_bounds__(kReduceThreads, 8) pending_kernel(const Pendin
       const int s = i == i0 ? s0 : p.var_ptr[i], e = i == i0 ? e0 : p.var_ptr[i + 1];
       const float Pi = pending_var_se<0, true>(p.delta, p.var_occ, p.P, p.share_occ, i, s, e, has, p.slot_dir,
                                                p.next_dir, p.heavy_deg);
-      if (BOUND && has) acc += slack_term((double)Pi, p.alpha);
+      if (BOUND && has) add_slack(acc, Pi, p.alpha);
     }
     if (BOUND && i < p.nb) acc += (double)p.bdd_E[i];
   }
@@ -1501,7 +1734,7 @@ __global__ void __launch_bounds__(kReduceThreads, 8) pending_kernel(const Pendin
   for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < p.n_heavy; w += (gridDim.x * blockDim.x) >> 5) {
     const int4 hv = p.heavy[w];
     const float Pi = pending_var_warp(p.delta, p.var_occ, p.P, p.share_occ, hv.x, hv.y, hv.z, p.slot_dir, p.next_dir);
-    if (BOUND && (threadIdx.x & 31) == 0) acc += slack_term((double)Pi, p.alpha);
+    if (BOUND && (threadIdx.x & 31) == 0) add_slack(acc, Pi, p.alpha);
   }
   if constexpr (BOUND) {
     __shared__ double red[kReduceThreads / 32];
@@ -1821,8 +2054,13 @@ int launch_pdl(void (*kernel)(Args...), int grid, int block, size_t smem, cudaSt
 }
 }  // namespace
 
-size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging) {
-  const size_t warp_part = kWarpsPerBlock * (staging == 2 ? kWarpSmemBytes2 : kWarpSmemBytes);
+size_t sweep_warp_smem(int staging, bool lanes2) {
+  const size_t st = staging == 2 ? kWarpSmemBytes2 : kWarpSmemBytes;
+  return lanes2 && kLaneSmemBytes > st ? kLaneSmemBytes : st;
+}
+
+size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging, bool lanes2) {
+  const size_t warp_part = kWarpsPerBlock * sweep_warp_smem(staging, lanes2);
   const size_t group_part = group_floats(block_buf, block_depth_buf) * sizeof(float);
   return warp_part > group_part ? warp_part : group_part;
 }
@@ -1833,10 +2071,13 @@ size_t persist_smem_bytes(int block_buf, int block_depth_buf) {
   return warp_part > group_part ? warp_part : group_part;
 }
 
-int sweep_launch(bool forward, int mode, const SweepParams &p, int grid, cudaStream_t stream, int staging) {
+int sweep_launch(bool forward, int mode, const SweepParams &p_in, int grid, cudaStream_t stream, int staging) {
   if (grid <= 0) return 0;
   if (mode != kUpdate) staging = 0;
-  const size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf, staging);
+  SweepParams p = p_in;
+  if (p.lanes2 && (p.alpha > 0.f || p.split || mode == kUpdateFused)) return -5;  // lane tiles: plain min-sum
+  p.warp_smem = (int)sweep_warp_smem(staging, p.lanes2 != 0);
+  const size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf, staging, p.lanes2 != 0);
   int rc = 0;
   if (p.split) {  // sub-BDDs: min-sum only, no fused pending pass
     if (p.alpha > 0.f || mode == kUpdateFused) return -5;

@@ -19,13 +19,15 @@ class Solver:
     SRMP averaging instead of eq. mma-update.  ``split`` (an interval count k >= 2) or ``cuts``
     (explicit cut places) splits the BDDs into sub-BDDs with copy-arc duals (Sec. 6), step size
     ``gamma``; ``split_depth`` D >= 1 instead cuts every BDD into pieces of at most D layers.
+    ``lanes``: 1 lane tiles for BDDs of width <= 2 (one lane per BDD), 0 two-lane teams, -1
+    (default) lane tiles on plain solvers.
     """
 
     def __init__(self, inst, omega: float = 0.5, host_only: bool = False, max_device_bytes: int = 0,
                  device: int = -1, stream: int = 0, schedule: int = 1, spin_limit: int = 0,
                  alpha: float = 0.0, rank=None, averaging: int = 0, fused_pending: int = -1,
                  staging: int = -1, split: int = 0, cuts=None, gamma: float = 0.5,
-                 split_depth: int = 0):
+                 split_depth: int = 0, lanes: int = -1):
         import numpy as np
         opt = B.bdd_default_options()
         if isinstance(rank, str):
@@ -44,6 +46,7 @@ class Solver:
         opt.split_intervals = int(split)
         opt.gamma = float(gamma)
         opt.split_depth = int(split_depth)
+        opt.lanes = int(lanes)
         opt.averaging = int(averaging)
         opt.fused_pending = int(fused_pending)
         opt.staging = int(staging)
@@ -61,7 +64,7 @@ class Solver:
         s = B.bdd_sizes(self.h)
         (self.n, self.m, self.nb, self.O, self.N, self.max_depth, self.max_width, self.nnz,
          self.device_bytes, self.warp_tiles, self.block_tiles, self.schedule, self.staging,
-         self.n_cuts, self.npairs, self.split_depth) = map(int, s)
+         self.n_cuts, self.npairs, self.split_depth, self.lanes) = map(int, s)
 
     def close(self):
         if getattr(self, "h", None):

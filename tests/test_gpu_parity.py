@@ -504,3 +504,47 @@ def test_staging_variants_bit_identical(lib, name, variant):
     auto = solver(inst, **kw)
     assert (auto.staging & 3) <= 2 and (auto.staging >> 2) <= 2
     np.testing.assert_array_equal(_trace(auto, 19), _trace(solver(inst, staging=0, **kw), 19))
+
+
+# ------------------------------------------------------------------------------------------
+# lane tiles (one lane per BDD of width <= 2) against two-lane teams
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["potts_20x20x3", "matching_300x300", "matching_small", "tracking_10x40",
+                                  "random_wide", "tomography_16"])
+def test_lane_tiles_bit_identical_to_teams(lib, name):
+    """BDDs whose layers have at most two nodes run one per lane (32 per warp) or as two-lane
+    teams (16 per warp): the same operations in the same order, so bound traces, multipliers,
+    pending sums and min-marginals are bit-identical, over 8-iteration graphs plus a ragged tail
+    and for every staging variant of the other classes."""
+    inst = CASES[name]()
+    teams = solver(inst, lanes=0)
+    assert teams.lanes == 0
+    t_ref = _trace(teams, 19)
+    l_ref, p_ref = teams.get_state()
+    _, lam_ref, m0_ref, m1_ref = teams.iterate(0, lam=True, mm=True)
+    for staging in (-1, 0, 1, 2):
+        lanes = solver(inst, lanes=1, staging=staging)
+        assert lanes.lanes == 1
+        np.testing.assert_array_equal(_trace(lanes, 19), t_ref)
+        la, pa = lanes.get_state()
+        np.testing.assert_array_equal(la, l_ref)
+        np.testing.assert_array_equal(pa, p_ref)
+        _, lam_l, m0_l, m1_l = lanes.iterate(0, lam=True, mm=True)
+        np.testing.assert_array_equal(lam_l, lam_ref)
+        np.testing.assert_array_equal(m0_l, m0_ref)
+        np.testing.assert_array_equal(m1_l, m1_ref)
+
+
+def test_lane_tiles_default_and_refusals(lib):
+    """Plain solvers default to lane tiles; smoothed, split, fused and persistent solvers keep
+    the team layout, and asking them for lane tiles is refused."""
+    from paper_2009_00481_gb300 import BDDError
+    from paper_2009_00481_gb300.binding import BDD_EINVAL
+    inst = CASES["potts_20x20x3"]()
+    assert solver(inst).lanes == 1
+    for kw in ({"alpha": 0.2}, {"split_depth": 2}, {"fused_pending": 1}, {"schedule": 0}):
+        assert solver(inst, **kw).lanes == 0
+        with pytest.raises(BDDError) as e:
+            solver(inst, lanes=1, **kw)
+        assert e.value.code == BDD_EINVAL
