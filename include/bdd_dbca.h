@@ -148,9 +148,29 @@ typedef struct {
                                  shuffles or team reductions); 0 = two-lane teams (16 BDDs per
                                  warp).  Same values bit for bit.  Lane tiles need a plain
                                  solver (alpha = 0, no split, separate pending kernels, schedule
-                                 1), else BDD_EINVAL.  -1 (default): lane tiles on plain
-                                 solvers, teams otherwise. */
+                                 1), else BDD_EINVAL.  -1 (default): the layout tuner decides
+                                 per key on plain solvers (see tune_layout); lane tiles on plain
+                                 solvers when the tuner is off; teams otherwise. */
+  int tune_layout;            /* layout tuner (plain solvers only, else BDD_EINVAL for 1): a BDD's
+                                 key is its natural width class c (the smallest team of 2^c lanes
+                                 >= its widest layer, c <= 5; 6 = wider than 32, block tiles) and
+                                 its depth bucket (<= 8, <= 32, <= 128, longer), key = 4 c +
+                                 bucket.  For every key holding at least 1 % of the nodes (and
+                                 4096) the tuner times two tile classes on a probe of that key's
+                                 BDDs (all of them, or every k-th one above 16 Mi nodes) in a
+                                 throwaway device solver -- for widths <= 2 two-lane teams against
+                                 lane tiles, for c = 2..5 teams of 2^c against 2^(c+1) lanes (a
+                                 block tile after 32) -- and keeps the alternative only when it
+                                 is at least 5 % faster (fastest forward plus fastest backward
+                                 sweep of three timed iterations).  -1 (default) / 1: on, 0: off.
+                                 bdd_layout_table reports the choice. */
+  const int *layout_classes;  /* explicit table instead of the tuner (plain solvers only):
+                                 kLayoutKeys = 28 entries, -1 = default, 0..5 a team of 2^c lanes,
+                                 6 a block tile, 7 lane tiles (widths <= 2 only); a class too
+                                 narrow for its key -> BDD_EINVAL.  Read by bdd_build only. */
 } bdd_options;
+
+#define BDD_LAYOUT_KEYS 28
 
 void bdd_default_options(bdd_options *opt);
 
@@ -239,6 +259,18 @@ int bdd_set_costs(bdd_solver *h, const float *c);
  * double-buffered), [13] cuts of the variable order, [14] copy-arc pairs, [15] depth limit of a
  * depth split (0: none), [16] 1 if BDDs of width <= 2 run as lane tiles (bdd_options.lanes). */
 int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]);
+
+/* Status a device error word maps to (no counterpart in the paper): 0 -> BDD_OK; -7 (an index
+ * check of the checked build failed) -> BDD_EDEVICE; any other value (a bounded device-side wait
+ * gave up) -> BDD_ETIMEOUT.  Host only; the calls that read the word use this mapping. */
+int bdd_status_of_device_word(int word);
+
+/* Tile class of every layout key (see bdd_options.tune_layout), no counterpart in the paper:
+ * nodes[k] nodes of the solver's BDDs with key k, cls[k] the class they run in (-1 none, 0..5
+ * a team of 2^c lanes, 6 block tiles, 7 lane tiles), ms (NULL skips it) [2k], [2k + 1]: the
+ * tuner's probe time of the default and the alternative class (-1: not probed).  Arrays of
+ * BDD_LAYOUT_KEYS (2 BDD_LAYOUT_KEYS for ms), host. */
+int bdd_layout_table(const bdd_solver *h, long long *nodes, int *cls, float *ms);
 
 /* Canonical form of the BDDs, read back from the device slabs (or the host copy when built
  * host_only): BDDs in ascending row order; occurrences BDD-major, layer-minor; nodes

@@ -12,11 +12,12 @@ import os
 
 import numpy as np
 
-from .build import LIB
+from .build import LIB, LIB_CHECKED
 
 BDD_OK, BDD_EINVAL, BDD_EINFEASIBLE, BDD_ETOOBIG, BDD_ENOMEM = 0, -1, -2, -3, -4
 BDD_ECUDA, BDD_ETIMEOUT, BDD_EDEVICE, BDD_ESTATE = -5, -6, -7, -8
 BDD_SIZES_LEN = 17
+BDD_LAYOUT_KEYS = 28
 
 EXPORTED = [
     "bdd_default_options", "bdd_build", "bdd_last_failed_row", "bdd_iterate", "bdd_iterate_device",
@@ -24,7 +25,7 @@ EXPORTED = [
     "bdd_set_costs", "bdd_sizes", "bdd_export_canonical", "bdd_get_state", "bdd_set_state",
     "bdd_strerror", "bdd_free", "bdd_lower_bound_noalloc", "bdd_bound_parts", "bdd_smooth_forward",
     "bdd_smooth_backward", "bdd_cuthill_mckee", "bdd_get_cuts", "bdd_get_copy_duals",
-    "bdd_set_copy_duals",
+    "bdd_set_copy_duals", "bdd_layout_table", "bdd_status_of_device_word",
 ]
 
 
@@ -35,7 +36,8 @@ class bdd_options(C.Structure):
                 ("alpha", C.c_float), ("var_rank", C.POINTER(C.c_int)), ("averaging", C.c_int),
                 ("fused_pending", C.c_int), ("staging", C.c_int), ("split_intervals", C.c_int),
                 ("cuts", C.POINTER(C.c_int)), ("n_cuts", C.c_int), ("gamma", C.c_float),
-                ("split_depth", C.c_int), ("lanes", C.c_int)]
+                ("split_depth", C.c_int), ("lanes", C.c_int), ("tune_layout", C.c_int),
+                ("layout_classes", C.POINTER(C.c_int))]
 
 
 class BDDError(RuntimeError):
@@ -50,12 +52,19 @@ class BDDError(RuntimeError):
 _lib = None
 
 
+def default_library() -> str:
+    """The library this process uses: the checked build (index checks in the sweep kernels
+    that report BDD_EDEVICE) when the environment sets BDD_DBCA_CHECKED=1, else the normal one."""
+    return LIB_CHECKED if os.environ.get("BDD_DBCA_CHECKED") == "1" else LIB
+
+
 def load(path: str | None = None):
     """Load the CUDA library (raises if it has not been built)."""
     global _lib
     if _lib is not None and path is None:
         return _lib
-    path = path or LIB
+    default = path is None
+    path = path or default_library()
     if not os.path.exists(path):
         raise ImportError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
     lib = C.CDLL(path)
@@ -86,7 +95,9 @@ def load(path: str | None = None):
     lib.bdd_get_cuts.argtypes = [vp, P(i32)]
     lib.bdd_get_copy_duals.argtypes = [vp, P(f32), P(f32)]
     lib.bdd_set_copy_duals.argtypes = [vp, P(f32), P(f32)]
-    if path == LIB:
+    lib.bdd_layout_table.argtypes = [vp, P(i64), P(i32), P(f32)]
+    lib.bdd_status_of_device_word.argtypes = [i32]
+    if default:
         _lib = lib
     return lib
 
@@ -220,6 +231,18 @@ def bdd_get_cuts(h) -> np.ndarray:
     cuts = np.zeros(max(k, 1), np.int32)
     _check(load().bdd_get_cuts(h, _ptr(cuts, C.c_int)), "bdd_get_cuts")
     return cuts[:k]
+
+
+def bdd_layout_table(h) -> dict:
+    """Tile class of every layout key (natural width class c x depth bucket: key = 4 c + bucket):
+    nodes, class (-1 none, 0..5 team of 2^c lanes, 6 block, 7 lane tiles) and the tuner's probe
+    ms of the default and the alternative (-1: not probed)."""
+    nodes = np.zeros(BDD_LAYOUT_KEYS, np.int64)
+    cls = np.zeros(BDD_LAYOUT_KEYS, np.int32)
+    ms = np.zeros(2 * BDD_LAYOUT_KEYS, np.float32)
+    _check(load().bdd_layout_table(h, _ptr(nodes, C.c_longlong), _ptr(cls, C.c_int), _ptr(ms, C.c_float)),
+           "bdd_layout_table")
+    return {"nodes": nodes, "cls": cls, "ms": ms.reshape(BDD_LAYOUT_KEYS, 2)}
 
 
 def bdd_get_copy_duals(h):

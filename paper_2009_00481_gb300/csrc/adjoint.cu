@@ -1,7 +1,8 @@
 // Reverse-mode adjoints of the smoothed iteration (Appendix A.5), for the gradient of the
 // smoothed bound after K iterations with respect to the costs c.
 //
-// The forward map of one update sweep of one BDD (warp tiles only; T lanes, lane t = node t):
+// The forward map of one update sweep of one BDD (warp tiles: T lanes, lane t = node t; block
+// tiles of at most 128 nodes per layer: thread t = node t):
 //   forward sweep, layers l ascending:
 //     fm_l(v)  = softmin over in-arcs (u, v) of fm_{l-1}(u) + theta_uv   (theta = lam''_{l-1} on
 //                1-arcs, 0 on 0-arcs; fm_0(root) = 0)                                  (Alg. 2)
@@ -280,6 +281,231 @@ __device__ void bwd_adjoint_tile(const AdjParams &a, int tile) {
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// block tiles (one 128-thread block per BDD of at most kBlockThreads nodes per layer, thread t =
+// node t): the same adjoints as the warp tiles, with the team shuffles replaced by shared-memory
+// exchanges.  A push along the arcs of layer l into layer l + 1 becomes a pull: node c of layer
+// l + 1 sums the contributions of the nodes of layer l whose arcs enter it, in node order (0-arc
+// before 1-arc), so the sums do not depend on timing.  Reductions over a layer go warp by warp
+// and then over the warps in order; the soft minima of a layer are the forward sweep's
+// group_agg2 reduction (the same order, so the same values).
+// ---------------------------------------------------------------------------------------
+struct BlockAdjSmem {
+  float G[kBlockThreads];   // adjoints of layer l + 1's nodes (pull from children)
+  float F[kBlockThreads];   // their messages
+  int2 arcs[kBlockThreads]; // arcs of layer l
+  float c0[kBlockThreads], c1[kBlockThreads];  // contributions along the 0- and 1-arcs
+  float red[kWarpsPerBlock];
+  float2 red2[kWarpsPerBlock];
+};
+
+// sum over the block, the same value on every thread (warp sums, then the warps in order)
+__device__ __forceinline__ float block_sum_f(float v, float *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = team_sum<32>(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  float r = red[0];
+#pragma unroll
+  for (int t = 1; t < kWarpsPerBlock; ++t) r += red[t];
+  __syncthreads();
+  return r;
+}
+
+// soft minima of a and b over the block (group_agg2 of the sweeps, the same order)
+__device__ __forceinline__ float2 block_softmin2(float a, float b, const SweepParams &p, float2 *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  a = team_agg<32, true>(a, p);
+  b = team_agg<32, true>(b, p);
+  if (lane == 0) red[warp] = make_float2(a, b);
+  __syncthreads();
+  float2 r = red[0];
+#pragma unroll
+  for (int t = 1; t < kWarpsPerBlock; ++t) {
+    r.x = soft_min(r.x, red[t].x, p.alpha, p.inv_alpha);
+    r.y = soft_min(r.y, red[t].y, p.alpha, p.inv_alpha);
+  }
+  __syncthreads();
+  return r;
+}
+
+// node c (< w_next) of layer l + 1, starting at node0n: the sum of the contributions along the
+// arcs of layer l's w nodes that enter it (S.arcs, S.c0, S.c1 filled before a barrier)
+__device__ __forceinline__ float pull_sum(const BlockAdjSmem &S, int w, int node0n, int c) {
+  const int v = node0n + c;
+  float acc = 0.f;
+  for (int u = 0; u < w; ++u) {
+    const int2 q = S.arcs[u];
+    if (q.x == v) acc += S.c0[u];
+    if (q.y == v) acc += S.c1[u];
+  }
+  return acc;
+}
+
+__device__ void fwd_adjoint_block(const AdjParams &a, int tile, BlockAdjSmem &S) {
+  const SweepParams &p = a.sp;
+  const float ia = p.inv_alpha;
+  const int gt = threadIdx.x;
+  const int bdd = p.tile_bdd0[tile], occ0 = p.tile_occ0[tile], depth = p.bdd_depth[bdd];
+  // descending layers: adjoint of fm_l pulled from the children, the marginal terms, their
+  // contributions to the starting backward messages of layer l + 1 (g_node)
+  for (int l = depth - 1; l >= 0; --l) {
+    const int o = occ0 + l;
+    const int node0 = p.occ_node_off[o], w = p.occ_node_off[o + 1] - node0;
+    const bool nxt = l + 1 < depth;
+    const int node0n = node0 + w, wn = nxt ? p.occ_node_off[o + 2] - node0n : 0;
+    const bool has = gt < w;
+    int2 lh = make_int2(kNone, kNone);
+    float f = inf();
+    if (has) {
+      lh = p.lohi[node0 + gt];
+      f = a.msg_new[node0 + gt];
+    }
+    const float lam1 = a.lam_s[o] + a.shr_s[o], lam2 = a.lam2[o];
+    float G = 0.f, g_theta = 0.f;
+    if (has && nxt) {  // S.G, S.F: layer l + 1 (written at the end of the previous step)
+      if (lh.x >= 0) G += S.G[lh.x - node0n] * weight(f, S.F[lh.x - node0n], ia);
+      if (lh.y >= 0) {
+        g_theta = S.G[lh.y - node0n] * weight(f + lam2, S.F[lh.y - node0n], ia);
+        G += g_theta;
+      }
+    }
+    const float G_lam2 = a.g_out_lam[o] + block_sum_f(g_theta, S.red);
+    const float b0 = has ? target_msg(a.msg_pre, lh.x) : inf();
+    const float b1 = has ? target_msg(a.msg_pre, lh.y) : inf();
+    const float a0 = has ? f + b0 : inf(), a1 = has ? f + lam1 + b1 : inf();
+    const float2 mm = block_softmin2(a0, a1, p, S.red2);
+    const bool finite = mm.x < inf() && mm.y < inf();
+    const float gd = finite ? p.omega * (a.g_out_delta[p.occ_slot[o]] - G_lam2) : 0.f;
+    const float p0 = weight(a0, mm.x, ia), p1 = weight(a1, mm.y, ia);
+    G += -gd * p0 + gd * p1;
+    if (gt == 0) {
+      a.g_in_lam[o] = G_lam2 + gd;
+      a.g_shr[o] = G_lam2 + gd;
+    }
+    if (gt < kBlockThreads) {
+      S.arcs[gt] = nxt ? lh : make_int2(kNone, kNone);
+      S.c0[gt] = -gd * p0;
+      S.c1[gt] = gd * p1;
+    }
+    __syncthreads();
+    if (gt < wn) a.g_node[node0n + gt] = pull_sum(S, w, node0n, gt);
+    __syncthreads();  // S.G / S.F of layer l + 1 no longer read
+    S.G[gt] = has ? G : 0.f;
+    S.F[gt] = f;
+    __syncthreads();
+  }
+  // ascending layers: the starting backward messages bmp_l(v) = softmin(bmp_{l+1}(lo),
+  // lam_l + bmp_{l+1}(hi)), adjoints flowing from layer l to layer l + 1
+  float carry = 0.f;
+  for (int l = 0; l < depth; ++l) {
+    const int o = occ0 + l;
+    const int node0 = p.occ_node_off[o], w = p.occ_node_off[o + 1] - node0;
+    const bool nxt = l + 1 < depth;
+    const int node0n = node0 + w, wn = nxt ? p.occ_node_off[o + 2] - node0n : 0;
+    const bool has = gt < w;
+    int2 lh = make_int2(kNone, kNone);
+    float bn = inf(), Gb = 0.f;
+    if (has) {
+      lh = p.lohi[node0 + gt];
+      bn = a.msg_pre[node0 + gt];
+      if (l >= 1) Gb = a.g_node[node0 + gt] + carry;
+    }
+    const float lam = a.lam_s[o];
+    const float b0 = has ? target_msg(a.msg_pre, lh.x) : inf();
+    const float b1 = has ? target_msg(a.msg_pre, lh.y) : inf();
+    const float q0 = has ? weight(b0, bn, ia) : 0.f;
+    const float q1 = has ? weight(lam + b1, bn, ia) : 0.f;
+    const float gl = block_sum_f(Gb * q1, S.red);
+    if (gt == 0) a.g_in_lam[o] += gl;
+    S.arcs[gt] = nxt ? lh : make_int2(kNone, kNone);
+    S.c0[gt] = Gb * q0;
+    S.c1[gt] = Gb * q1;
+    __syncthreads();
+    carry = gt < wn ? pull_sum(S, w, node0n, gt) : 0.f;
+    __syncthreads();
+  }
+}
+
+__device__ void bwd_adjoint_block(const AdjParams &a, int tile, BlockAdjSmem &S) {
+  const SweepParams &p = a.sp;
+  const float ia = p.inv_alpha;
+  const int gt = threadIdx.x;
+  const int bdd = p.tile_bdd0[tile], occ0 = p.tile_occ0[tile], depth = p.bdd_depth[bdd];
+  // ascending layers (the reverse of the sweep): the adjoint of bmn_l (seeded at the root with
+  // gE) through the backward step and, with the marginal terms, on to layer l + 1; the marginal
+  // terms' adjoints of the starting forward messages go to g_node
+  float carry = 0.f;
+  for (int l = 0; l < depth; ++l) {
+    const int o = occ0 + l;
+    const int node0 = p.occ_node_off[o], w = p.occ_node_off[o + 1] - node0;
+    const bool nxt = l + 1 < depth;
+    const int node0n = node0 + w, wn = nxt ? p.occ_node_off[o + 2] - node0n : 0;
+    const bool has = gt < w;
+    int2 lh = make_int2(kNone, kNone);
+    float fp = inf(), bn = inf(), Gbn = 0.f;
+    if (has) {
+      lh = p.lohi[node0 + gt];
+      fp = a.msg_pre[node0 + gt];
+      bn = a.msg_new[node0 + gt];
+      Gbn = l == 0 ? (gt == 0 && a.gE ? (float)*a.gE : 0.f) : carry;
+    }
+    const float lam1 = a.lam_s[o] + a.shr_s[o], lam2 = a.lam2[o];
+    const float b0 = has ? target_msg(a.msg_new, lh.x) : inf();
+    const float b1 = has ? target_msg(a.msg_new, lh.y) : inf();
+    const float q0 = has ? weight(b0, bn, ia) : 0.f;
+    const float q1 = has ? weight(lam2 + b1, bn, ia) : 0.f;
+    const float G_lam2 = a.g_out_lam[o] + block_sum_f(Gbn * q1, S.red);
+    const float a0 = has ? fp + b0 : inf(), a1 = has ? fp + lam1 + b1 : inf();
+    const float2 mm = block_softmin2(a0, a1, p, S.red2);
+    const bool finite = mm.x < inf() && mm.y < inf();
+    const float gd = finite ? p.omega * (a.g_out_delta[p.occ_slot[o]] - G_lam2) : 0.f;
+    const float p0 = weight(a0, mm.x, ia), p1 = weight(a1, mm.y, ia);
+    if (has) a.g_node[node0 + gt] = -gd * p0 + gd * p1;
+    if (gt == 0) {
+      a.g_in_lam[o] = G_lam2 + gd;
+      a.g_shr[o] = G_lam2 + gd;
+    }
+    S.arcs[gt] = nxt ? lh : make_int2(kNone, kNone);
+    S.c0[gt] = Gbn * q0 - gd * p0;
+    S.c1[gt] = Gbn * q1 + gd * p1;
+    __syncthreads();
+    carry = gt < wn ? pull_sum(S, w, node0n, gt) : 0.f;
+    __syncthreads();
+  }
+  // descending layers: the starting forward messages fmp_l(v) = softmin over in-arcs of
+  // fmp_{l-1}(u) + theta, adjoints flowing from layer l + 1 back to layer l
+  for (int l = depth - 1; l >= 0; --l) {
+    const int o = occ0 + l;
+    const int node0 = p.occ_node_off[o], w = p.occ_node_off[o + 1] - node0;
+    const bool nxt = l + 1 < depth;
+    const int node0n = node0 + w;
+    const bool has = gt < w;
+    int2 lh = make_int2(kNone, kNone);
+    float f = inf(), G = 0.f;
+    if (has) {
+      lh = p.lohi[node0 + gt];
+      f = a.msg_pre[node0 + gt];
+      G = a.g_node[node0 + gt];
+    }
+    const float lam = a.lam_s[o];
+    float g_theta = 0.f;
+    if (has && nxt) {
+      if (lh.x >= 0) G += S.G[lh.x - node0n] * weight(f, S.F[lh.x - node0n], ia);
+      if (lh.y >= 0) {
+        g_theta = S.G[lh.y - node0n] * weight(f + lam, S.F[lh.y - node0n], ia);
+        G += g_theta;
+      }
+    }
+    const float gl = block_sum_f(g_theta, S.red);
+    if (gt == 0) a.g_in_lam[o] += gl;
+    __syncthreads();  // S.G / S.F of layer l + 1 no longer read
+    S.G[gt] = has ? G : 0.f;
+    S.F[gt] = f;
+    __syncthreads();
+  }
+}
+
 template <bool FWD>
 __device__ __forceinline__ void adjoint_tile(const AdjParams &a, int tile) {
   int c = 0;
@@ -306,9 +532,20 @@ __device__ __forceinline__ void adjoint_tile(const AdjParams &a, int tile) {
 
 template <bool FWD>
 __global__ void __launch_bounds__(kBlockThreads) sweep_adjoint_kernel(const AdjParams a) {
-  const int tile = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  if (tile >= a.sp.class_tile_off[kWarpClasses]) return;  // whole warp
-  adjoint_tile<FWD>(a, tile);
+  if ((int)blockIdx.x < a.sp.n_warp_blocks) {
+    const int tile = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (tile >= a.sp.class_tile_off[kWarpClasses]) return;  // whole warp
+    adjoint_tile<FWD>(a, tile);
+    return;
+  }
+  // block tiles: one block per BDD (smoothed solvers: layers of at most kBlockThreads nodes)
+  const int tile = a.sp.class_tile_off[kWarpClasses] + ((int)blockIdx.x - a.sp.n_warp_blocks);
+  if (tile >= a.sp.class_tile_off[kWarpClasses + 1]) return;  // uniform across the block
+  __shared__ BlockAdjSmem S;
+  if (FWD)
+    fwd_adjoint_block(a, tile, S);
+  else
+    bwd_adjoint_block(a, tile, S);
 }
 
 // Adjoint of the pending sums: share_o = P_i / |J_i| and P_i = sum of the previous sweep's

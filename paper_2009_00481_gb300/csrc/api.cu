@@ -96,7 +96,12 @@ struct bdd_solver {
   int2 *d_win_node = nullptr;
   int *d_var_ptr = nullptr, *d_var_occ = nullptr;
   int averaging = 0;                     // 0: eq. mma-update; 1: SRMP (Appendix A.4)
-  bool lanes2 = false;                   // BDDs of width <= 2 run as lane tiles
+  bool lanes2 = false;                   // BDDs of width <= 2 may run as lane tiles
+  // layout tuner: tile class of every key (-1: default), nodes per key, probe ms of the default
+  // and the alternative candidate (-1: not probed)
+  int key_class[kLayoutKeys];
+  long long key_nodes[kLayoutKeys];
+  float key_ms[kLayoutKeys][2];
   int stage_fwd = 0, stage_bwd = 0;      // warp-tile staging of the update sweeps (autotuned)
   int staging_opt = -1;                  // bdd_options.staging
   float tune_ms[kStagings][2] = {};      // measured ms per sweep [variant][direction]
@@ -131,7 +136,7 @@ struct bdd_solver {
   long long state_gen = 0;      // bumped by every call that changes the dual state
   long long smooth_gen = -1;    // state_gen right after the recorded forward
   float *ck_lam = nullptr, *ck_shr = nullptr;
-  float *t_lam = nullptr, *t_nodeA = nullptr, *t_nodeB = nullptr, *t_gnode = nullptr;
+  float *t_nodeA = nullptr, *t_nodeB = nullptr, *t_gnode = nullptr;
   float *t_glam0 = nullptr, *t_glam1 = nullptr, *t_gshr = nullptr, *t_gdelta = nullptr;
   float *t_delta = nullptr, *t_E = nullptr;
   // sub-BDDs (Sec. 6): cuts of the variable order, copy-arc pairs and their duals
@@ -143,6 +148,14 @@ struct bdd_solver {
   int *d_head_node = nullptr, *d_head_ptr = nullptr, *d_head_pair = nullptr;
   float *d_mu_bar = nullptr, *d_mu = nullptr, *d_dfwd = nullptr, *d_dbwd = nullptr;
   cudaEvent_t ev_last = nullptr;  // end of the solver's last enqueued work, on whatever stream
+
+  bdd_solver() {
+    for (int k = 0; k < kLayoutKeys; ++k) {
+      key_class[k] = -1;
+      key_nodes[k] = 0;
+      key_ms[k][0] = key_ms[k][1] = -1.f;
+    }
+  }
 
   ~bdd_solver() {
     if (ev_last) cudaEventDestroy(ev_last);
@@ -199,6 +212,10 @@ struct bdd_solver {
     p.omega = omega;
     p.alpha = alpha;
     p.error = d_error;
+    p.n_nodes = N;
+    p.n_occ = O;
+    p.n_csr = nnz;
+    p.n_bdd = nb;
     p.inv_alpha = alpha > 0.f ? 1.f / alpha : 0.f;
     p.copy_val = d_mu_bar;
     p.split = npairs > 0 ? 1 : 0;
@@ -422,7 +439,8 @@ struct bdd_solver {
     return iterate_persistent_launch(q, grid_persist, smem_persist, s) ? BDD_ECUDA : BDD_OK;
   }
 
-  // a grid-barrier wait of an earlier launch gave up: report once, then clear
+  // a device-side wait of an earlier launch gave up, or (checked build) an index check failed:
+  // report once, then clear
   int take_device_error(cudaStream_t s) {
     if (!d_error) return BDD_OK;
     int err = 0;
@@ -431,9 +449,8 @@ struct bdd_solver {
     if (err != 0) {
       CK(cudaMemsetAsync(d_error, 0, sizeof(int), s));
       CK(cudaStreamSynchronize(s));
-      return BDD_ETIMEOUT;
     }
-    return BDD_OK;
+    return bdd_status_of_device_word(err);
   }
 
   int capture(int iters, cudaGraphExec_t *out) {
@@ -601,8 +618,8 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c, const CutTables
   const int heavy_blocks = (n_heavy + kReduceThreads / 32 - 1) / (kReduceThreads / 32);
   h->grid_reduce = std::max(1, std::min(std::max((range + kReduceThreads - 1) / kReduceThreads, heavy_blocks), 152 * 16));
   // the largest dynamic shared memory any staging variant's sweep launch asks for
-  h->smem = std::max(sweep_smem_bytes(h->block_buf, h->block_depth_buf, 0, h->lanes2),
-                     sweep_smem_bytes(h->block_buf, h->block_depth_buf, 2, h->lanes2));
+  h->smem = std::max(sweep_smem_bytes(h->block_buf, h->block_depth_buf, 0, h->lanes2, h->alpha > 0.f),
+                     sweep_smem_bytes(h->block_buf, h->block_depth_buf, 2, h->lanes2, h->alpha > 0.f));
   h->smem_persist = persist_smem_bytes(h->block_buf, h->block_depth_buf);
   if (h->smem > 48 * 1024 && sweep_set_smem(h->smem)) return BDD_ECUDA;
   if (h->schedule == 0) {
@@ -715,6 +732,163 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c, const CutTables
   return BDD_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Layout tuner.  Each key (a BDD's natural width class and its depth bucket) has up to two tile
+// classes its BDDs can run in: lane tiles or two-lane teams for widths <= 2; a team of 2^c or of
+// 2^(c+1) lanes (a block tile after 32) for wider ones.  For every key holding enough nodes the
+// candidates are timed on a probe: the key's BDDs alone (every k-th one when they hold more than
+// kProbeCap nodes, so the probe still fills the GPU many times over), each occurrence its own
+// variable, built into a throwaway device solver; the update sweeps of a warm-up iteration and
+// three more are timed kernel by kernel, and the fastest forward plus the fastest backward
+// launch count.  The alternative replaces the default only when it is kTuneMargin faster.
+// ---------------------------------------------------------------------------------------
+constexpr long long kProbeCap = 16LL << 20;  // nodes of a probe
+constexpr long long kProbeMin = 4096;        // keys with fewer nodes keep the default
+
+long long bdd_nodes(const HostBDDs &H, long long b) {
+  return H.occ_node0[H.bdd_occ0[b + 1]] - H.occ_node0[H.bdd_occ0[b]];
+}
+
+int bdd_width(const HostBDDs &H, long long b) {
+  int w = 0;
+  for (long long o = H.bdd_occ0[b]; o < H.bdd_occ0[b + 1]; ++o) w = std::max(w, H.occ_width[o]);
+  return w;
+}
+
+HostBDDs probe_instance(const HostBDDs &H, int key, long long key_nodes) {
+  HostBDDs P;
+  const long long step = std::max(1LL, (key_nodes + kProbeCap - 1) / kProbeCap);
+  long long seen = 0;
+  P.bdd_occ0.push_back(0);
+  P.occ_node0.push_back(0);
+  for (long long b = 0; b < H.nb(); ++b) {
+    if (layout_key(bdd_width(H, b), H.bdd_depth[b]) != key) continue;
+    if (seen++ % step) continue;
+    P.bdd_row.push_back((int)P.bdd_row.size());
+    P.bdd_depth.push_back(H.bdd_depth[b]);
+    P.max_depth = std::max(P.max_depth, H.bdd_depth[b]);
+    for (long long o = H.bdd_occ0[b]; o < H.bdd_occ0[b + 1]; ++o) {
+      const int w = H.occ_width[o];
+      P.occ_var.push_back((int)P.occ_var.size());
+      P.occ_csr.push_back((long long)P.occ_csr.size());
+      P.occ_width.push_back(w);
+      P.max_width = std::max(P.max_width, w);
+      for (long long v = H.occ_node0[o]; v < H.occ_node0[o + 1]; ++v) {
+        P.lo.push_back(H.lo[v]);
+        P.hi.push_back(H.hi[v]);
+      }
+      P.occ_node0.push_back((long long)P.lo.size());
+    }
+    P.bdd_occ0.push_back((long long)P.occ_var.size());
+  }
+  P.n = (int)P.occ_var.size();
+  P.m = (int)P.bdd_row.size();
+  P.nnz = P.n;
+  return P;
+}
+
+// ms of one forward plus one backward update sweep of the probe in the given layout (-1: failed)
+float probe_time(const HostBDDs &P, bool lanes2, const int *class_of_key) {
+  bdd_solver *h = new (std::nothrow) bdd_solver();
+  if (!h) return -1.f;
+  h->n = P.n;
+  h->m = P.m;
+  h->nnz = P.nnz;
+  h->nb = P.nb();
+  h->O = P.O();
+  h->N = P.N();
+  h->max_depth = P.max_depth;
+  h->max_width = P.max_width;
+  h->lanes2 = lanes2;
+  h->staging_opt = 0;
+  h->schedule = 1;
+  h->canon_row = P.bdd_row;
+  h->var_deg.assign(P.n, 1);
+  h->c.assign(P.n, 0.f);
+  float ms = -1.f;
+  Layout L;
+  int rc = build_layout(P, &L, lanes2, class_of_key);
+  if (rc == BDD_OK && cudaGetDevice(&h->device) != cudaSuccess) rc = BDD_ECUDA;
+  if (rc == BDD_OK && cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) rc = BDD_ECUDA;
+  if (rc == BDD_OK) h->own_stream = true;
+  if (rc == BDD_OK && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) rc = BDD_ECUDA;
+  if (rc == BDD_OK) rc = setup_device(h, L, h->c.data(), CutTables());
+  cudaEvent_t ev[16] = {};
+  for (auto &e : ev)
+    if (rc == BDD_OK && cudaEventCreate(&e) != cudaSuccess) rc = BDD_ECUDA;
+  const cudaStream_t s = h->stream;
+  for (int it = 0; it < 4 && rc == BDD_OK; ++it) {
+    cudaEvent_t *e = &ev[4 * it];
+    if (cudaEventRecord(e[0], s) != cudaSuccess) rc = BDD_ECUDA;
+    if (rc == BDD_OK) rc = h->sweep(true, kUpdate, s);
+    if (rc == BDD_OK && cudaEventRecord(e[1], s) != cudaSuccess) rc = BDD_ECUDA;
+    if (rc == BDD_OK) rc = h->pending(false, s);
+    if (rc == BDD_OK && cudaEventRecord(e[2], s) != cudaSuccess) rc = BDD_ECUDA;
+    if (rc == BDD_OK) rc = h->sweep(false, kUpdate, s);
+    if (rc == BDD_OK && cudaEventRecord(e[3], s) != cudaSuccess) rc = BDD_ECUDA;
+    if (rc == BDD_OK) rc = h->pending(true, s);
+  }
+  if (rc == BDD_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = BDD_ECUDA;
+  float fwd = -1.f, bwd = -1.f;
+  for (int it = 1; it < 4 && rc == BDD_OK; ++it) {  // iteration 0 warms up
+    float t0 = 0.f, t1 = 0.f;
+    if (cudaEventElapsedTime(&t0, ev[4 * it], ev[4 * it + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t1, ev[4 * it + 2], ev[4 * it + 3]) != cudaSuccess)
+      rc = BDD_ECUDA;
+    if (fwd < 0.f || t0 < fwd) fwd = t0;
+    if (bwd < 0.f || t1 < bwd) bwd = t1;
+  }
+  if (rc == BDD_OK) ms = fwd + bwd;
+  for (auto &e : ev)
+    if (e) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete h;
+  return ms;
+}
+
+// Chooses the tile class of every key of a plain solver's BDDs (see above).  allow_lanes: lane
+// tiles are a candidate for widths <= 2 (-1 tuned, 0 never, 1 always).  Fills h->key_*, sets
+// h->lanes2; returns a BDD_* status.
+int tune_layout(bdd_solver *h, const HostBDDs &H, int allow_lanes) {
+  for (long long b = 0; b < H.nb(); ++b) h->key_nodes[layout_key(bdd_width(H, b), H.bdd_depth[b])] += bdd_nodes(H, b);
+  const long long min_nodes = std::max(kProbeMin, H.N() / 100);
+  bool any_lane = false;
+  for (int k = 0; k < kLayoutKeys; ++k) {
+    if (h->key_nodes[k] == 0) continue;
+    const int wc = k / kDepthBuckets;
+    if (wc == kWarpClasses) continue;  // block tiles: no alternative
+    // candidates: [default, alternative]; for widths <= 2 the teams of two lanes (class 1) and
+    // the lane tiles (class 0 with lanes2)
+    const bool narrow = wc <= 1;
+    if (narrow && allow_lanes == 1) {
+      h->key_class[k] = 0;
+      any_lane = true;
+      continue;
+    }
+    if (narrow && allow_lanes == 0) continue;
+    const int cand[2] = {narrow ? 1 : wc, narrow ? 0 : wc + 1};
+    if (h->key_nodes[k] < min_nodes) {
+      h->key_class[k] = cand[0];
+      continue;
+    }
+    HostBDDs P = probe_instance(H, k, h->key_nodes[k]);
+    for (int t = 0; t < 2; ++t) {
+      int table[kLayoutKeys];
+      for (int q = 0; q < kLayoutKeys; ++q) table[q] = -1;
+      table[k] = cand[t];
+      h->key_ms[k][t] = probe_time(P, narrow && t == 1, table);
+      if (h->key_ms[k][t] < 0.f) return BDD_ECUDA;
+    }
+    const bool alt = h->key_ms[k][1] < (1.f - kTuneMargin) * h->key_ms[k][0];
+    h->key_class[k] = cand[alt ? 1 : 0];
+    if (narrow && alt) any_lane = true;
+  }
+  h->lanes2 = any_lane;
+  if (!any_lane)  // no lane tiles: widths <= 2 keep their natural classes (width 1 in class 0)
+    for (int k = 0; k < 2 * kDepthBuckets; ++k) h->key_class[k] = -1;
+  return BDD_OK;
+}
+
 bool finite_costs(const float *c, int n) {
   for (int i = 0; i < n; ++i)
     if (!std::isfinite(c[i])) return false;
@@ -758,6 +932,8 @@ void bdd_default_options(bdd_options *opt) {
   opt->gamma = 0.5f;
   opt->split_depth = 0;
   opt->lanes = -1;
+  opt->tune_layout = -1;
+  opt->layout_classes = nullptr;
 }
 
 int bdd_last_failed_row(void) { return g_failed_row; }
@@ -790,11 +966,21 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   if (!(opt.gamma > 0.f && opt.gamma <= 1.f)) return BDD_EINVAL;
   const bool want_split = opt.split_depth > 0 || opt.n_cuts > 0 || opt.split_intervals >= 2;
   if (want_split && opt.alpha > 0.f) return BDD_EINVAL;  // sub-BDDs run the min-sum iteration only
-  if (opt.lanes < -1 || opt.lanes > 1) return BDD_EINVAL;
-  // lane tiles run the plain min-sum sweeps of the per-phase schedule only
+  if (opt.lanes < -1 || opt.lanes > 1 || opt.tune_layout < -1 || opt.tune_layout > 1) return BDD_EINVAL;
+  // lane tiles and the layout tuner: the plain min-sum sweeps of the per-phase schedule only
   const bool plain = opt.alpha == 0.f && !want_split && opt.fused_pending != 1 && opt.schedule == 1;
-  if (opt.lanes == 1 && !plain) return BDD_EINVAL;
-  const bool lanes2 = opt.lanes == 1 || (opt.lanes == -1 && plain);
+  if ((opt.lanes == 1 || opt.tune_layout == 1 || opt.layout_classes) && !plain) return BDD_EINVAL;
+  bool lanes2 = opt.lanes == 1 || (opt.lanes == -1 && plain);
+  if (opt.layout_classes) {  // explicit table: 7 = lane tiles (widths <= 2), else a tile class
+    lanes2 = false;
+    for (int k = 0; k < kLayoutKeys; ++k) {
+      const int c = opt.layout_classes[k];
+      if (c < -1 || c > kWarpClasses + 1 || (c == kWarpClasses + 1 && k >= 2 * kDepthBuckets)) return BDD_EINVAL;
+      if (c == kWarpClasses + 1) lanes2 = true;
+    }
+    if (lanes2 && opt.lanes == 0) return BDD_EINVAL;
+  }
+  const bool tune = plain && !opt.layout_classes && opt.tune_layout != 0 && !opt.host_only;
   if (opt.var_rank) {  // a permutation of 0..n-1
     std::vector<char> seen;
     try {
@@ -886,13 +1072,39 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
     *out = h;
     return BDD_OK;
   }
+  // tile class of every layout key: explicit, tuned on the device, or the defaults
+  bool keyed = false;
+  if (opt.layout_classes) {
+    for (int k = 0; k < kLayoutKeys; ++k) {
+      const int c = opt.layout_classes[k];
+      h->key_class[k] = c == kWarpClasses + 1 ? 0 : c;
+    }
+    for (long long b = 0; b < H.nb(); ++b) h->key_nodes[layout_key(bdd_width(H, b), H.bdd_depth[b])] += bdd_nodes(H, b);
+    keyed = true;
+  } else if (tune) {
+    DeviceGuard dg(opt.device);
+    rc = dg.ok ? BDD_OK : BDD_ECUDA;
+    try {
+      if (rc == BDD_OK) rc = tune_layout(h, H, opt.lanes);
+    } catch (const std::bad_alloc &) {
+      rc = BDD_ENOMEM;
+    }
+    if (rc != BDD_OK) {
+      delete h;
+      return rc;
+    }
+    keyed = true;
+  } else {
+    for (long long b = 0; b < H.nb(); ++b) h->key_nodes[layout_key(bdd_width(H, b), H.bdd_depth[b])] += bdd_nodes(H, b);
+  }
   Layout L;
   try {
-    rc = build_layout(H, &L, h->lanes2);
+    rc = build_layout(H, &L, h->lanes2, keyed ? h->key_class : nullptr);
   } catch (const std::bad_alloc &) {
     rc = BDD_ENOMEM;
   }
-  if (rc == BDD_OK && h->alpha > 0.f && L.n_block_tiles > 0) rc = BDD_ETOOBIG;  // smoothing: warp tiles only
+  // smoothing: warp tiles and block tiles of at most kBlockThreads nodes per layer
+  if (rc == BDD_OK && h->alpha > 0.f && L.n_block_tiles > 0 && L.max_block_width > kBlockThreads) rc = BDD_ETOOBIG;
   CutTables ct;
   if (rc == BDD_OK && h->npairs > 0 && !h->host_layout) {
     try {
@@ -1097,8 +1309,7 @@ int bdd_smooth_forward(bdd_solver *h, int K, const float *d_c, double *d_bound, 
     RC(h->alloc(&h->ck_shr, 2LL * K * std::max<long long>(O, 1)));
     h->smooth_cap = 2 * K;
   }
-  if (!h->t_lam) {
-    RC(h->alloc(&h->t_lam, O));
+  if (!h->t_nodeA) {
     RC(h->alloc(&h->t_nodeA, N));
     RC(h->alloc(&h->t_nodeB, N));
     RC(h->alloc(&h->t_gnode, N));
@@ -1164,47 +1375,56 @@ int bdd_smooth_backward(bdd_solver *h, long long generation, const double *d_gbo
   if (bound_seed_launch(h->d_var_ptr, h->d_P, h->d_c, h->t_gdelta, d_grad_c, h->n, h->alpha, d_gbound, s))
     return BDD_ECUDA;
   float *g_next = h->t_glam1, *g_cur = h->t_glam0;  // adjoint of the multipliers after / before a sweep
+  // Every sweep's inputs are its checkpointed multipliers and shares and its starting messages
+  // (the backward messages of those multipliers for a forward sweep, the forward messages for a
+  // backward sweep); its outputs are the multipliers at the next checkpoint and the messages it
+  // writes, which are exactly the next sweep's starting messages.  Walking the sweeps in
+  // reverse, each step therefore recomputes only its starting messages (one messages-only
+  // sweep from the checkpoint into a scratch buffer) and takes its outputs from the step before:
+  // the last sweep's from the solver's final state.
+  float *bufs[2] = {h->t_nodeA, h->t_nodeB};
+  int xb = 0;
+  const float *msg_new = h->d_bm, *lam2 = h->d_lam;
   for (long long sw = 2LL * K - 1; sw >= 0; --sw) {
     const bool fwd = (sw % 2) == 0;
     const float *lam_s = h->ck_lam + sw * O, *shr_s = h->ck_shr + sw * O;
-    // recompute the sweep from its checkpoint into scratch buffers: starting messages, then the
-    // sweep itself (multipliers, messages), the solver's own state untouched
-    if (O) CK(cudaMemcpyAsync(h->t_lam, lam_s, ob, cudaMemcpyDeviceToDevice, s));
+    float *pre = bufs[xb];
     SweepParams p = h->sweep_params();
-    p.lam = h->t_lam;
+    p.lam = const_cast<float *>(lam_s);  // a messages-only sweep reads the multipliers, never writes them
     p.share_occ = shr_s;
     p.delta = h->t_delta;
     p.bdd_E = h->t_E;
-    if (fwd) {
-      p.bm = h->t_nodeA;
-      p.fm = h->t_nodeB;
+    if (fwd) {  // backward messages of the checkpoint (reads fm without using it)
+      p.bm = pre;
+      p.fm = const_cast<float *>(msg_new);
       if (sweep_launch(false, kMessages, p, h->grid_sweep, s)) return BDD_ECUDA;
-      if (sweep_launch(true, kUpdate, p, h->grid_sweep, s)) return BDD_ECUDA;
-    } else {
-      p.fm = h->t_nodeA;
-      p.bm = h->t_nodeB;
+    } else {    // forward messages of the checkpoint
+      p.fm = pre;
+      p.bm = const_cast<float *>(msg_new);
       if (sweep_launch(true, kMessages, p, h->grid_sweep, s)) return BDD_ECUDA;
-      if (sweep_launch(false, kUpdate, p, h->grid_sweep, s)) return BDD_ECUDA;
     }
     AdjParams a{};
     a.sp = h->sweep_params();
     a.lam_s = lam_s;
     a.shr_s = shr_s;
-    a.lam2 = h->t_lam;
-    a.msg_pre = h->t_nodeA;
-    a.msg_new = h->t_nodeB;
+    a.lam2 = lam2;
+    a.msg_pre = pre;
+    a.msg_new = msg_new;
     a.g_out_lam = g_next;
     a.g_out_delta = h->t_gdelta;
     a.g_in_lam = g_cur;
     a.g_shr = h->t_gshr;
     a.g_node = h->t_gnode;
     a.gE = sw == 2LL * K - 1 ? d_gbound : nullptr;
-    if (sweep_adjoint_launch(fwd, a, h->n_warp_blocks, s)) return BDD_ECUDA;
+    if (sweep_adjoint_launch(fwd, a, h->grid_sweep, s)) return BDD_ECUDA;
     // the shares of this sweep were formed from the previous sweep's differences
     if (sw > 0 && pending_adjoint_launch(h->d_var_ptr, h->d_var_occ, h->d_slot_dir,
                                          fwd ? kDirForward : kDirBackward, h->t_gshr, h->t_gdelta, h->n, s))
       return BDD_ECUDA;
     std::swap(g_cur, g_next);
+    msg_new = pre;  // this sweep's starting messages are the previous sweep's outputs
+    lam2 = lam_s;
+    xb ^= 1;
   }
   // lambda_0 = c / |J_i|
   if (initial_adjoint_launch(h->d_var_ptr, h->d_var_occ, g_next, d_grad_c, h->n, s)) return BDD_ECUDA;
@@ -1230,6 +1450,23 @@ int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]) {
   out[14] = h->npairs;
   out[15] = h->split_depth;
   out[16] = h->lanes2 ? 1 : 0;
+  return BDD_OK;
+}
+
+int bdd_layout_table(const bdd_solver *h, long long *nodes, int *cls, float *ms) {
+  if (!h || !nodes || !cls) return BDD_EINVAL;
+  for (int k = 0; k < kLayoutKeys; ++k) {
+    const int wc = k / kDepthBuckets;
+    nodes[k] = h->key_nodes[k];
+    int c = h->key_class[k];
+    if (c < 0) c = h->lanes2 && wc <= 1 ? 0 : wc;  // the default
+    if (h->lanes2 && wc <= 1 && c == 0) c = kWarpClasses + 1;  // lane tiles
+    cls[k] = h->key_nodes[k] > 0 ? c : -1;
+    if (ms) {
+      ms[2 * k] = h->key_ms[k][0];
+      ms[2 * k + 1] = h->key_ms[k][1];
+    }
+  }
   return BDD_OK;
 }
 
@@ -1425,6 +1662,11 @@ int bdd_bound_parts(bdd_solver *h, int nparts, const long long *row_off, const l
   RC(h->end(s));
   CK(cudaStreamSynchronize(s));
   return BDD_OK;
+}
+
+int bdd_status_of_device_word(int word) {
+  if (word == 0) return BDD_OK;
+  return word == BDD_EDEVICE ? BDD_EDEVICE : BDD_ETIMEOUT;
 }
 
 const char *bdd_strerror(int code) {

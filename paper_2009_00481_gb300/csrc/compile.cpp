@@ -341,19 +341,24 @@ int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const i
   return BDD_OK;
 }
 
-int build_layout(const HostBDDs &H, Layout *L, bool lanes2) {
+int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_key) {
   const long long nb = H.nb(), O = H.O(), N = H.N();
   L->lanes2 = lanes2;
-  // class of each BDD from its widest layer
+  // class of each BDD: its key's entry in the table, else the default for its widest layer
   std::vector<int> cls(nb);
   for (long long b = 0; b < nb; ++b) {
     int w = 0;
     for (long long o = H.bdd_occ0[b]; o < H.bdd_occ0[b + 1]; ++o) w = std::max(w, H.occ_width[o]);
-    int c = 0;
-    while ((1 << c) < w && c < kWarpClasses) ++c;
-    if (lanes2 && w <= 2) c = 0;  // lane tiles: one lane holds both nodes of a layer
-    if (w > 32) c = kWarpClasses;
+    int c = natural_class(w);
     if (c == kWarpClasses && w > kMaxBlockTileWidth) return BDD_ETOOBIG;
+    if (lanes2 && w <= 2) c = 0;  // lane tiles: one lane holds both nodes of a layer
+    const int want = class_of_key ? class_of_key[layout_key(w, H.bdd_depth[b])] : -1;
+    if (want >= 0) {
+      const bool fits = want == kWarpClasses ? w <= kMaxBlockTileWidth
+                                             : want < kWarpClasses && ((1 << want) >= w || (want == 0 && lanes2 && w <= 2));
+      if (!fits) return BDD_EINVAL;
+      c = want;
+    }
     cls[b] = c;
   }
   // stable counting sort by (class, depth descending); ties keep ascending row order

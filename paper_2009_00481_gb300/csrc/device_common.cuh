@@ -7,6 +7,27 @@ namespace bdd {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Index checks of the checked build (compiled with -DBDD_CHECKED; see build.py): an index
+// outside [0, n) records BDD_EDEVICE (-7) in the error word and is replaced by 0, so the access
+// it guards stays inside its array and the host call reports the failure.  In the normal build
+// the macros are the index itself and nothing is checked.
+#ifdef BDD_CHECKED
+__device__ __forceinline__ long long checked_index(int *err, long long i, long long n) {
+  if (i < 0 || i >= n) {
+    atomicExch(err, -7);
+    return 0;
+  }
+  return i;
+}
+#define BDD_IN(p, i, n) checked_index((p).error, (i), (n))
+#else
+#define BDD_IN(p, i, n) (i)
+#endif
+#define BDD_NODE(p, i) BDD_IN(p, i, (p).n_nodes)
+#define BDD_OCC(p, i) BDD_IN(p, i, (p).n_occ)
+#define BDD_CSR(p, i) BDD_IN(p, i, (p).n_csr)
+#define BDD_BDD(p, i) BDD_IN(p, i, (p).n_bdd)
+
 __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
 
 template <int T>

@@ -173,9 +173,26 @@ struct Layout {
   std::vector<int> occ_of_canon;       // canonical occurrence -> device occurrence
 };
 
-// lanes2: BDDs of width <= 2 form the lane tiles of class 0 (32 BDDs per tile, one lane each);
-// otherwise class c holds the BDDs whose widest layer needs a team of 2^c lanes.
-int build_layout(const HostBDDs &H, Layout *L, bool lanes2 = false);
+// Keys of the layout tuner: a BDD's natural class (the smallest team of 2^c >= its widest
+// layer, c < kWarpClasses; kWarpClasses for block tiles) and its depth bucket (<= 8, <= 32,
+// <= 128, longer).
+constexpr int kDepthBuckets = 4;
+constexpr int kLayoutKeys = (kWarpClasses + 1) * kDepthBuckets;
+inline int natural_class(int width) {
+  if (width > 32) return kWarpClasses;
+  int c = 0;
+  while ((1 << c) < width) ++c;
+  return c;
+}
+inline int depth_bucket(int depth) { return depth <= 8 ? 0 : depth <= 32 ? 1 : depth <= 128 ? 2 : 3; }
+inline int layout_key(int width, int depth) { return natural_class(width) * kDepthBuckets + depth_bucket(depth); }
+
+// lanes2: BDDs of width <= 2 may form the lane tiles of class 0 (32 BDDs per tile, one lane
+// each).  class_of_key (kLayoutKeys entries, or null): the class each key's BDDs go to, -1 for
+// the default (class 0 = lane tiles for width <= 2 when lanes2, else the natural class).  A
+// class must fit the key: a team of 2^c >= the width, a block tile, or lane tiles (width <= 2,
+// lanes2).  Returns BDD_EINVAL otherwise.
+int build_layout(const HostBDDs &H, Layout *L, bool lanes2 = false, const int *class_of_key = nullptr);
 
 // Fused pending pass of an update sweep (the per-phase plan without separate pending kernels).
 // At the end of its tile every occurrence counts its variable down; the visit that brings the
@@ -245,7 +262,9 @@ struct SweepParams {
   int fin_cap;
   double fin_const;
   int *error;            // set to BDD_ETIMEOUT if a bounded wait on a shared-memory copy gives up
-                         // (a fixed time limit, kRingWaitNs in kernels.cu)
+                         // (a fixed time limit, kRingWaitNs in kernels.cu); to BDD_EDEVICE by a
+                         // failed index check of the checked build
+  long long n_nodes, n_occ, n_csr, n_bdd;  // array extents for the checked build's index checks
   FusedParams fz;       // fz.cnt == null outside the fused plan
 };
 
@@ -357,7 +376,8 @@ int cut_launch(bool forward, const CutParams &c, cudaStream_t stream);
 int cut_roots_launch(const CutParams &c, cudaStream_t stream);
 
 // Launch wrappers (kernels.cu).  All enqueue on `stream` and return 0 or -5 (launch failure).
-size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging = 0, bool lanes2 = false);
+size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging = 0, bool lanes2 = false,
+                        bool smooth = false);
 size_t sweep_warp_smem(int staging, bool lanes2);
 size_t persist_smem_bytes(int block_buf, int block_depth_buf);
 int sweep_set_smem(size_t bytes);

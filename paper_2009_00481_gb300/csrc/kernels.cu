@@ -567,14 +567,14 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
       const int oi = occ_before(lead_depth, l) - ca + team;
       int node0 = 0, w_l = 0;
       if (active) {
-        node0 = off[oi];
-        w_l = off[oi + 1] - node0;
+        node0 = off[BDD_IN(p, oi, W.cb - W.ca)];
+        w_l = off[BDD_IN(p, oi + 1, W.cb - W.ca + 1)] - node0;
       }
       const bool has = active && tl < w_l;
       // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv
       float f;
       if (l == 0) {  // the root, or a piece's roots with their root messages (sub-BDDs)
-        f = SPLIT && has ? p.fm[node0 + tl] : 0.f;
+        f = SPLIT && has ? p.fm[BDD_NODE(p, node0 + tl)] : 0.f;
       } else {
         const int lo_l = lh_prev.x >= 0 ? lh_prev.x - node0 : kNone;
         const int hi_l = lh_prev.y >= 0 ? lh_prev.y - node0 : kNone;
@@ -590,8 +590,8 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
       }
       int2 lh = make_int2(kNone, kNone);
       if (has) {
-        p.fm[node0 + tl] = f;
-        lh = lohi[node0 - na + tl];
+        p.fm[BDD_NODE(p, node0 + tl)] = f;
+        lh = lohi[BDD_IN(p, node0 - na + tl, W.nb - W.na)];
       }
       float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
       if (is_update(MODE)) {
@@ -602,8 +602,8 @@ __device__ __forceinline__ void warp_forward(const SweepParams &p, const Phase &
         const float dd = p.omega * mm_difference(m0, m1);
         lam -= dd;
         if (active && tl == 0) {
-          p.lam[oa + oi] = lam;
-          ph.delta[slot[oi]] = dd;
+          p.lam[BDD_OCC(p, oa + oi)] = lam;
+          ph.delta[BDD_OCC(p, slot[oi])] = dd;
         }
       }
       f_prev = f;
@@ -667,15 +667,15 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
       const int oi = occ_before(lead_depth, l) - ca + team;
       int node0 = 0, w_l = 0;
       if (active) {
-        node0 = off[oi];
-        w_l = off[oi + 1] - node0;
+        node0 = off[BDD_IN(p, oi, W.cb - W.ca)];
+        w_l = off[BDD_IN(p, oi + 1, W.cb - W.ca + 1)] - node0;
       }
       const bool has = active && tl < w_l;
       int2 lh = make_int2(kNone, kNone);
       float f = inf();
       if (has) {
-        lh = lohi[node0 - na + tl];
-        f = msg[node0 - na + tl];
+        lh = lohi[BDD_IN(p, node0 - na + tl, W.nb - W.na)];
+        f = msg[BDD_IN(p, node0 - na + tl, W.nb - W.na)];
       }
       float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
       // successors' backward messages live on the lanes of this team (layer l + 1)
@@ -691,22 +691,22 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
           const float dd = p.omega * mm_difference(m0, m1);
           lam -= dd;
           if (active && tl == 0) {
-            p.lam[oa + oi] = lam;
-            ph.delta[slot[oi]] = dd;
+            p.lam[BDD_OCC(p, oa + oi)] = lam;
+            ph.delta[BDD_OCC(p, slot[oi])] = dd;
           }
         } else if (active && tl == 0 && p.out_m0) {
           const long long c = p.occ_csr[oa + oi];
-          p.out_m0[c] = m0;
-          p.out_m1[c] = m1;
+          p.out_m0[BDD_CSR(p, c)] = m0;
+          p.out_m1[BDD_CSR(p, c)] = m1;
         }
       }
       // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
       const float bcur = agg<SMOOTH>(b0, lam + b1, p);
-      if (has) p.bm[node0 + tl] = bcur;
+      if (has) p.bm[BDD_NODE(p, node0 + tl)] = bcur;
       if (l == 0) {  // E^j(lambda^j) at the root; a piece: min over its roots of fm + bm
         const float e = SPLIT ? team_agg<T, SMOOTH>(has ? f + bcur : inf(), p) : bcur;
         if (active && tl == 0) {
-          p.bdd_E[bdd] = e;
+          p.bdd_E[BDD_BDD(p, bdd)] = e;
           bacc += (double)e;
         }
       }
@@ -791,8 +791,8 @@ __device__ __forceinline__ void lane_forward(const SweepParams &p, const Phase &
       const int oi = occ_before(lead_depth, l) - ca + lane;
       int node0 = 0, wl = 0;
       if (active) {
-        node0 = off[oi];
-        wl = off[oi + 1] - node0;
+        node0 = off[BDD_IN(p, oi, W.cb - W.ca)];
+        wl = off[BDD_IN(p, oi + 1, W.cb - W.ca + 1)] - node0;
       }
       // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv, for both nodes
       float f0 = 0.f, f1 = 0.f;  // the root (layer 0)
@@ -803,12 +803,12 @@ __device__ __forceinline__ void lane_forward(const SweepParams &p, const Phase &
       }
       int2 lh0 = make_int2(kNone, kNone), lh1 = make_int2(kNone, kNone);
       if (wl > 0) {
-        p.fm[node0] = f0;
-        lh0 = lohi[node0 - na];
+        p.fm[BDD_NODE(p, node0)] = f0;
+        lh0 = lohi[BDD_IN(p, node0 - na, W.nb - W.na)];
       }
       if (wl > 1) {
-        p.fm[node0 + 1] = f1;
-        lh1 = lohi[node0 - na + 1];
+        p.fm[BDD_NODE(p, node0 + 1)] = f1;
+        lh1 = lohi[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
       }
       float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
       if (is_update(MODE)) {
@@ -821,8 +821,8 @@ __device__ __forceinline__ void lane_forward(const SweepParams &p, const Phase &
         const float dd = p.omega * mm_difference(m0, m1);
         lam -= dd;
         if (active) {
-          p.lam[oa + oi] = lam;
-          ph.delta[slot[oi]] = dd;
+          p.lam[BDD_OCC(p, oa + oi)] = lam;
+          ph.delta[BDD_OCC(p, slot[oi])] = dd;
         }
       }
       pf0 = f0;
@@ -878,18 +878,18 @@ __device__ __forceinline__ void lane_backward(const SweepParams &p, const Phase 
       const int oi = occ_before(lead_depth, l) - ca + lane;
       int node0 = 0, wl = 0;
       if (active) {
-        node0 = off[oi];
-        wl = off[oi + 1] - node0;
+        node0 = off[BDD_IN(p, oi, W.cb - W.ca)];
+        wl = off[BDD_IN(p, oi + 1, W.cb - W.ca + 1)] - node0;
       }
       int2 lh0 = make_int2(kNone, kNone), lh1 = make_int2(kNone, kNone);
       float f0 = inf(), f1 = inf();
       if (wl > 0) {
-        lh0 = lohi[node0 - na];
-        f0 = msg[node0 - na];
+        lh0 = lohi[BDD_IN(p, node0 - na, W.nb - W.na)];
+        f0 = msg[BDD_IN(p, node0 - na, W.nb - W.na)];
       }
       if (wl > 1) {
-        lh1 = lohi[node0 - na + 1];
-        f1 = msg[node0 - na + 1];
+        lh1 = lohi[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
+        f1 = msg[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
       }
       float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
       // successors' backward messages: the next layer's nodes, held by this lane
@@ -903,21 +903,21 @@ __device__ __forceinline__ void lane_backward(const SweepParams &p, const Phase 
           const float dd = p.omega * mm_difference(m0, m1);
           lam -= dd;
           if (active) {
-            p.lam[oa + oi] = lam;
-            ph.delta[slot[oi]] = dd;
+            p.lam[BDD_OCC(p, oa + oi)] = lam;
+            ph.delta[BDD_OCC(p, slot[oi])] = dd;
           }
         } else if (active && p.out_m0) {
           const long long c = p.occ_csr[oa + oi];
-          p.out_m0[c] = m0;
-          p.out_m1[c] = m1;
+          p.out_m0[BDD_CSR(p, c)] = m0;
+          p.out_m1[BDD_CSR(p, c)] = m1;
         }
       }
       // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
       const float bc0 = fminf(b00, lam + b01), bc1 = fminf(b10, lam + b11);
-      if (wl > 0) p.bm[node0] = bc0;
-      if (wl > 1) p.bm[node0 + 1] = bc1;
+      if (wl > 0) p.bm[BDD_NODE(p, node0)] = bc0;
+      if (wl > 1) p.bm[BDD_NODE(p, node0 + 1)] = bc1;
       if (l == 0 && active) {  // E^j(lambda^j) at the root
-        p.bdd_E[bdd] = bc0;
+        p.bdd_E[BDD_BDD(p, bdd)] = bc0;
         bacc += (double)bc0;
       }
       bn0 = bc0;
@@ -1033,14 +1033,14 @@ __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phas
       const int oi = occ_before(lead_depth, l) - ca + team;
       int node0 = 0, w = 0;
       if (active) {
-        node0 = S.off[oi];
-        w = S.off[oi + 1] - node0;
+        node0 = S.off[BDD_IN(p, oi, g.nob)];
+        w = S.off[BDD_IN(p, oi + 1, g.nox + 1)] - node0;
       }
       const bool has = active && tl < w;
       // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv
       float f;
       if (l == 0) {  // the root, or a piece's roots with their root messages (sub-BDDs)
-        f = SPLIT && has ? p.fm[node0 + tl] : 0.f;
+        f = SPLIT && has ? p.fm[BDD_NODE(p, node0 + tl)] : 0.f;
       } else {
         const int lo_l = lh_prev.x >= 0 ? lh_prev.x - node0 : kNone;
         const int hi_l = lh_prev.y >= 0 ? lh_prev.y - node0 : kNone;
@@ -1056,8 +1056,8 @@ __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phas
       }
       int2 lh = make_int2(kNone, kNone);
       if (has) {
-        p.fm[node0 + tl] = f;
-        lh = S.lohi[node0 - na + tl];
+        p.fm[BDD_NODE(p, node0 + tl)] = f;
+        lh = S.lohi[BDD_IN(p, node0 - na + tl, g.nb - g.na)];
       }
       float lam = active ? S.lam[oi] + S.shr[oi] : 0.f;
       if (is_update(MODE)) {
@@ -1068,8 +1068,8 @@ __device__ __forceinline__ void warp_forward_w8(const SweepParams &p, const Phas
         const float dd = p.omega * mm_difference(m0, m1);
         lam -= dd;
         if (active && tl == 0) {
-          p.lam[oa + oi] = lam;
-          ph.delta[S.slot[oi]] = dd;
+          p.lam[BDD_OCC(p, oa + oi)] = lam;
+          ph.delta[BDD_OCC(p, S.slot[oi])] = dd;
         }
       }
       f_prev = f;
@@ -1122,15 +1122,15 @@ __device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Pha
       const int oi = occ_before(lead_depth, l) - ca + team;
       int node0 = 0, w = 0;
       if (active) {
-        node0 = S.off[oi];
-        w = S.off[oi + 1] - node0;
+        node0 = S.off[BDD_IN(p, oi, g.nob)];
+        w = S.off[BDD_IN(p, oi + 1, g.nox + 1)] - node0;
       }
       const bool has = active && tl < w;
       int2 lh = make_int2(kNone, kNone);
       float f = inf();
       if (has) {
-        lh = S.lohi[node0 - na + tl];
-        f = S.msg[node0 - na + tl];
+        lh = S.lohi[BDD_IN(p, node0 - na + tl, g.nb - g.na)];
+        f = S.msg[BDD_IN(p, node0 - na + tl, g.nb - g.na)];
       }
       float lam = active ? S.lam[oi] + S.shr[oi] : 0.f;
       // successors' backward messages live on the lanes of this team (layer l + 1)
@@ -1146,22 +1146,22 @@ __device__ __forceinline__ void warp_backward_w8(const SweepParams &p, const Pha
           const float dd = p.omega * mm_difference(m0, m1);
           lam -= dd;
           if (active && tl == 0) {
-            p.lam[oa + oi] = lam;
-            ph.delta[S.slot[oi]] = dd;
+            p.lam[BDD_OCC(p, oa + oi)] = lam;
+            ph.delta[BDD_OCC(p, S.slot[oi])] = dd;
           }
         } else if (active && tl == 0 && p.out_m0) {
           const long long c = p.occ_csr[oa + oi];
-          p.out_m0[c] = m0;
-          p.out_m1[c] = m1;
+          p.out_m0[BDD_CSR(p, c)] = m0;
+          p.out_m1[BDD_CSR(p, c)] = m1;
         }
       }
       // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
       const float bcur = agg<SMOOTH>(b0, lam + b1, p);
-      if (has) p.bm[node0 + tl] = bcur;
+      if (has) p.bm[BDD_NODE(p, node0 + tl)] = bcur;
       if (l == 0) {  // E^j(lambda^j) at the root; a piece: min over its roots of fm + bm
         const float e = SPLIT ? team_agg<T, SMOOTH>(has ? f + bcur : inf(), p) : bcur;
         if (active && tl == 0) {
-          p.bdd_E[bdd] = e;
+          p.bdd_E[BDD_BDD(p, bdd)] = e;
           bacc += (double)e;
         }
       }
@@ -1184,10 +1184,13 @@ struct GroupSmem {
   float2 *red;  // [kWarpsPerBlock]
   float *bufA, *bufB, *shr;
   int *off;     // [block_depth_buf + 4] node offsets of the tile's layers (narrow tiles)
+  int2 *arcs;   // [block_buf] arcs of the current layer (smoothed narrow tiles), else null
 };
 
-__host__ __device__ __forceinline__ size_t group_floats(int block_buf, int block_depth_buf) {
-  return 2 * kWarpsPerBlock + 2 * (size_t)block_buf + 2 * (size_t)block_depth_buf + 4;
+// floats of shared memory of one block-tile group; `smooth` adds the arcs of a layer
+__host__ __device__ __forceinline__ size_t group_floats(int block_buf, int block_depth_buf, bool smooth = false) {
+  return 2 * kWarpsPerBlock + 2 * (size_t)block_buf + 2 * (size_t)block_depth_buf + 4 +
+         (smooth ? 2 * (size_t)block_buf : 0);
 }
 
 __device__ __forceinline__ GroupSmem group_smem(float *base, const SweepParams &p) {
@@ -1197,6 +1200,7 @@ __device__ __forceinline__ GroupSmem group_smem(float *base, const SweepParams &
   g.bufB = g.bufA + p.block_buf;
   g.shr = g.bufB + p.block_buf;
   g.off = reinterpret_cast<int *>(g.shr + p.block_depth_buf);
+  g.arcs = p.alpha > 0.f ? reinterpret_cast<int2 *>(g.off + p.block_depth_buf + 4) : nullptr;
   return g;
 }
 
@@ -1214,6 +1218,26 @@ __device__ __forceinline__ float2 group_min2(float a, float b, float2 *red, int 
   for (int t = 1; t < kWarpsPerBlock; ++t) {
     r.x = fminf(r.x, red[t].x);
     r.y = fminf(r.y, red[t].y);
+  }
+  group_sync(group);  // red may be reused right after
+  return r;
+}
+
+// the same reduction with the soft minimum (smoothed solvers): each warp's butterfly keeps its
+// first lane's value, then the warps' values in warp order, so every thread gets the same bits
+template <bool SMOOTH>
+__device__ __forceinline__ float2 group_agg2(float a, float b, const SweepParams &p, float2 *red, int group, int gt) {
+  if (!SMOOTH) return group_min2(a, b, red, group, gt);
+  const int lane = gt & 31, warp = gt >> 5;
+  a = team_agg<32, true>(a, p);
+  b = team_agg<32, true>(b, p);
+  if (lane == 0) red[warp] = make_float2(a, b);
+  group_sync(group);
+  float2 r = red[0];
+#pragma unroll
+  for (int t = 1; t < kWarpsPerBlock; ++t) {
+    r.x = soft_min(r.x, red[t].x, p.alpha, p.inv_alpha);
+    r.y = soft_min(r.y, red[t].y, p.alpha, p.inv_alpha);
   }
   group_sync(group);  // red may be reused right after
   return r;
@@ -1253,9 +1277,9 @@ __device__ __forceinline__ void block_forward(const SweepParams &p, const Phase 
     float a0 = inf(), a1 = inf();
     for (int t = gt; t < w; t += kBlockThreads) {
       const float f = cur[t];
-      p.fm[node0 + t] = f;
+      p.fm[BDD_NODE(p, node0 + t)] = f;
       if (is_update(MODE)) {
-        const int2 lh = p.lohi[node0 + t];
+        const int2 lh = p.lohi[BDD_NODE(p, node0 + t)];
         a0 = fminf(a0, f + target_bm<SPLIT>(p.bm, p.copy_val, lh.x));
         a1 = fminf(a1, f + lam + target_bm<SPLIT>(p.bm, p.copy_val, lh.y));
       }
@@ -1265,8 +1289,8 @@ __device__ __forceinline__ void block_forward(const SweepParams &p, const Phase 
       const float dd = p.omega * mm_difference(mm.x, mm.y);
       lam -= dd;
       if (gt == 0) {
-        p.lam[o] = lam;
-        ph.delta[p.occ_slot[o]] = dd;
+        p.lam[BDD_OCC(p, o)] = lam;
+        ph.delta[BDD_OCC(p, p.occ_slot[o])] = dd;
       }
     }
     if (l + 1 < depth) {
@@ -1275,7 +1299,7 @@ __device__ __forceinline__ void block_forward(const SweepParams &p, const Phase 
       group_sync(group);
       for (int t = gt; t < w; t += kBlockThreads) {
         const float f = cur[t];
-        const int2 lh = p.lohi[node0 + t];
+        const int2 lh = p.lohi[BDD_NODE(p, node0 + t)];
         if (lh.x >= 0) atomic_min_f(&nxt[lh.x - next0], f);
         if (lh.y >= 0) atomic_min_f(&nxt[lh.y - next0], f + lam);
       }
@@ -1304,8 +1328,8 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
     if (MODE != kMessages) {
       float a0 = inf(), a1 = inf();
       for (int t = gt; t < w; t += kBlockThreads) {
-        const int2 lh = p.lohi[node0 + t];
-        const float f = p.fm[node0 + t];
+        const int2 lh = p.lohi[BDD_NODE(p, node0 + t)];
+        const float f = p.fm[BDD_NODE(p, node0 + t)];
         const float b0 = lh.x >= 0 ? cur[lh.x - next0] : terminal_bm<SPLIT>(p.copy_val, lh.x);
         const float b1 = lh.y >= 0 ? cur[lh.y - next0] : terminal_bm<SPLIT>(p.copy_val, lh.y);
         a0 = fminf(a0, f + b0);
@@ -1316,28 +1340,28 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
         const float dd = p.omega * mm_difference(mm.x, mm.y);
         lam -= dd;
         if (gt == 0) {
-          p.lam[o] = lam;
-          ph.delta[p.occ_slot[o]] = dd;
+          p.lam[BDD_OCC(p, o)] = lam;
+          ph.delta[BDD_OCC(p, p.occ_slot[o])] = dd;
         }
       } else if (gt == 0 && p.out_m0) {
         const long long c = p.occ_csr[o];
-        p.out_m0[c] = mm.x;
-        p.out_m1[c] = mm.y;
+        p.out_m0[BDD_CSR(p, c)] = mm.x;
+        p.out_m1[BDD_CSR(p, c)] = mm.y;
       }
     }
     float e = inf();  // a piece's energy: min over its roots of fm + bm
     for (int t = gt; t < w; t += kBlockThreads) {
-      const int2 lh = p.lohi[node0 + t];
+      const int2 lh = p.lohi[BDD_NODE(p, node0 + t)];
       const float b0 = lh.x >= 0 ? cur[lh.x - next0] : terminal_bm<SPLIT>(p.copy_val, lh.x);
       const float b1 = lh.y >= 0 ? cur[lh.y - next0] : terminal_bm<SPLIT>(p.copy_val, lh.y);
       const float bcur = fminf(b0, lam + b1);
-      p.bm[node0 + t] = bcur;
+      p.bm[BDD_NODE(p, node0 + t)] = bcur;
       nxt[t] = bcur;
       if (l == 0) {
         if (SPLIT) {
           e = fminf(e, p.fm[node0 + t] + bcur);
         } else if (t == 0) {
-          p.bdd_E[bdd] = bcur;
+          p.bdd_E[BDD_BDD(p, bdd)] = bcur;
           bacc += (double)bcur;
         }
       }
@@ -1345,7 +1369,7 @@ __device__ __forceinline__ void block_backward(const SweepParams &p, const Phase
     if (l == 0 && SPLIT) {
       e = group_min2(e, inf(), g.red, group, gt).x;
       if (gt == 0) {
-        p.bdd_E[bdd] = e;
+        p.bdd_E[BDD_BDD(p, bdd)] = e;
         bacc += (double)e;
       }
     }
@@ -1378,7 +1402,10 @@ __device__ __forceinline__ int2 narrow_arcs(const SweepParams &p, const int *off
   return gt < off[l + 1] - node0 ? p.lohi[node0 + gt] : make_int2(kNone, kNone);
 }
 
-template <int MODE, bool SPLIT>
+// SMOOTH: the forward step pulls instead of pushing -- node v of layer l + 1 aggregates its
+// in-arcs scanning the nodes of layer l in order, 0-arc before 1-arc (the soft minimum is not
+// associative in floating point, so a fixed order replaces the atomic minimum)
+template <int MODE, bool SPLIT, bool SMOOTH = false>
 __device__ __forceinline__ void block_forward_narrow(const SweepParams &p, const Phase &ph, int tile,
                                                      const GroupSmem &g, int group, int gt, double &bacc) {
   const int bdd = p.tile_bdd0[tile];
@@ -1411,26 +1438,40 @@ __device__ __forceinline__ void block_forward_narrow(const SweepParams &p, const
     const int node0 = off[l], w = off[l + 1] - node0;
     const bool has = gt < w;
     const float f = has ? cur[gt] : inf();
-    if (has) p.fm[node0 + gt] = f;
+    if (has) p.fm[BDD_NODE(p, node0 + gt)] = f;
+    if (SMOOTH && gt < p.block_buf) g.arcs[gt] = lh;  // read by the pull after the next barrier
     float lam = g.shr[l];
     const bool more = l + 1 < depth;
     // nxt was last read before the previous layer's final barrier
     if (more && gt < off[l + 2] - off[l + 1]) nxt[gt] = inf();
     if (is_update(MODE)) {
-      const float2 mm = group_min2(has ? f + t0 : inf(), has ? f + lam + t1 : inf(), g.red, group, gt);
+      const float2 mm = group_agg2<SMOOTH>(has ? f + t0 : inf(), has ? f + lam + t1 : inf(), p, g.red, group, gt);
       const float dd = p.omega * mm_difference(mm.x, mm.y);
       lam -= dd;
       if (gt == 0) {
-        p.lam[o] = lam;
-        ph.delta[p.occ_slot[o]] = dd;
+        p.lam[BDD_OCC(p, o)] = lam;
+        ph.delta[BDD_OCC(p, p.occ_slot[o])] = dd;
       }
     } else if (more) {
       group_sync(group);  // the resets of nxt before the pushes
     }
     if (more) {
       const int next0 = off[l + 1];
-      if (lh.x >= 0) atomic_min_f(&nxt[lh.x - next0], f);
-      if (lh.y >= 0) atomic_min_f(&nxt[lh.y - next0], f + lam);
+      if (SMOOTH) {
+        if (gt < off[l + 2] - next0) {
+          const int v = next0 + gt;
+          float acc = inf();
+          for (int u = 0; u < w; ++u) {
+            const int2 a = g.arcs[u];
+            if (a.x == v) acc = soft_min(acc, cur[u], p.alpha, p.inv_alpha);
+            if (a.y == v) acc = soft_min(acc, cur[u] + lam, p.alpha, p.inv_alpha);
+          }
+          nxt[gt] = acc;
+        }
+      } else {
+        if (lh.x >= 0) atomic_min_f(&nxt[lh.x - next0], f);
+        if (lh.y >= 0) atomic_min_f(&nxt[lh.y - next0], f + lam);
+      }
       group_sync(group);
       float *tmp = cur;
       cur = nxt;
@@ -1443,7 +1484,7 @@ __device__ __forceinline__ void block_forward_narrow(const SweepParams &p, const
   }
 }
 
-template <int MODE, bool SPLIT>
+template <int MODE, bool SPLIT, bool SMOOTH = false>
 __device__ __forceinline__ void block_backward_narrow(const SweepParams &p, const Phase &ph, int tile,
                                                       const GroupSmem &g, int group, int gt, double &bacc) {
   const int bdd = p.tile_bdd0[tile];
@@ -1473,35 +1514,35 @@ __device__ __forceinline__ void block_backward_narrow(const SweepParams &p, cons
     const float b0 = lh.x >= 0 ? cur[lh.x - next0] : terminal_bm<SPLIT>(p.copy_val, lh.x);
     const float b1 = lh.y >= 0 ? cur[lh.y - next0] : terminal_bm<SPLIT>(p.copy_val, lh.y);
     if (MODE != kMessages) {
-      const float2 mm = group_min2(has ? f + b0 : inf(), has ? f + lam + b1 : inf(), g.red, group, gt);
+      const float2 mm = group_agg2<SMOOTH>(has ? f + b0 : inf(), has ? f + lam + b1 : inf(), p, g.red, group, gt);
       if (is_update(MODE)) {
         const float dd = p.omega * mm_difference(mm.x, mm.y);
         lam -= dd;
         if (gt == 0) {
-          p.lam[o] = lam;
-          ph.delta[p.occ_slot[o]] = dd;
+          p.lam[BDD_OCC(p, o)] = lam;
+          ph.delta[BDD_OCC(p, p.occ_slot[o])] = dd;
         }
       } else if (gt == 0 && p.out_m0) {
         const long long c = p.occ_csr[o];
-        p.out_m0[c] = mm.x;
-        p.out_m1[c] = mm.y;
+        p.out_m0[BDD_CSR(p, c)] = mm.x;
+        p.out_m1[BDD_CSR(p, c)] = mm.y;
       }
     }
     // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
-    const float bcur = fminf(b0, lam + b1);
+    const float bcur = agg<SMOOTH>(b0, lam + b1, p);
     if (has) {
-      p.bm[node0 + gt] = bcur;
+      p.bm[BDD_NODE(p, node0 + gt)] = bcur;
       nxt[gt] = bcur;
     }
     if (l == 0) {  // E^j at the root; a piece: min over its roots of fm + bm
       if (SPLIT) {
         const float e = group_min2(has ? f + bcur : inf(), inf(), g.red, group, gt).x;
         if (gt == 0) {
-          p.bdd_E[bdd] = e;
+          p.bdd_E[BDD_BDD(p, bdd)] = e;
           bacc += (double)e;
         }
       } else if (gt == 0) {
-        p.bdd_E[bdd] = bcur;
+        p.bdd_E[BDD_BDD(p, bdd)] = bcur;
         bacc += (double)bcur;
       }
     }
@@ -1666,20 +1707,21 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
     // shallowest, so the chain's critical path does not wait for this)
     if (FWD && p.fin_partial && (int)blockIdx.x == p.n_warp_blocks - 1 && warp == 0)
       finish_bound(p.fin_partial, p.fin_nblocks, p.fin_iter, p.fin_trace, p.fin_cap, p.fin_const);
-  } else if constexpr (!SMOOTH) {  // smoothed solvers have warp tiles only
+  } else {  // block tiles (smoothed solvers: layers of at most kBlockThreads nodes only)
     const int tile = p.class_tile_off[kWarpClasses] + (blockIdx.x - p.n_warp_blocks);
     if (tile >= p.class_tile_off[kWarpClasses + 1]) return;  // uniform across the block
     pdl_wait();
     const GroupSmem g = group_smem(smem, p);
     if (p.block_buf <= kBlockThreads) {
       if (FWD)
-        block_forward_narrow<MODE, SPLIT>(p, ph, tile, g, 0, threadIdx.x, bacc);
+        block_forward_narrow<MODE, SPLIT, SMOOTH>(p, ph, tile, g, 0, threadIdx.x, bacc);
       else
-        block_backward_narrow<MODE, SPLIT>(p, ph, tile, g, 0, threadIdx.x, bacc);
-    } else if (FWD) {
-      block_forward<MODE, SPLIT>(p, ph, tile, g, 0, threadIdx.x, bacc);
-    } else {
-      block_backward<MODE, SPLIT>(p, ph, tile, g, 0, threadIdx.x, bacc);
+        block_backward_narrow<MODE, SPLIT, SMOOTH>(p, ph, tile, g, 0, threadIdx.x, bacc);
+    } else if constexpr (!SMOOTH) {
+      if (FWD)
+        block_forward<MODE, SPLIT>(p, ph, tile, g, 0, threadIdx.x, bacc);
+      else
+        block_backward<MODE, SPLIT>(p, ph, tile, g, 0, threadIdx.x, bacc);
     }
     if (MODE == kUpdateFused) {
       group_sync(0);
@@ -1719,16 +1761,28 @@ __global__ void __launch_bounds__(kReduceThreads, 8) pending_kernel(const Pendin
   }
   pdl_enter();
   const int range = BOUND ? (p.n > p.nb ? p.n : p.nb) : p.n;
+  const int stride = gridDim.x * blockDim.x;
   double acc = 0.0;
-  for (int i = i0; i < range; i += gridDim.x * blockDim.x) {
+  int s = s0, e = e0;
+  for (int i = i0; i < range; i += stride) {
+    // the next variable's slot range goes out before this variable's slots are loaded, so the
+    // two round trips overlap; a variable of at most 8 occurrences then loads its differences,
+    // occurrence ids and SRMP bits in one round
+    const int inext = i + stride;
+    int sn = 0, en = 0;
+    if (inext < p.n) {
+      sn = p.var_ptr[inext];
+      en = p.var_ptr[inext + 1];
+    }
     if (i < p.n) {
       bool has;
-      const int s = i == i0 ? s0 : p.var_ptr[i], e = i == i0 ? e0 : p.var_ptr[i + 1];
-      const float Pi = pending_var_se<0, true>(p.delta, p.var_occ, p.P, p.share_occ, i, s, e, has, p.slot_dir,
+      const float Pi = pending_var_se<8, true>(p.delta, p.var_occ, p.P, p.share_occ, i, s, e, has, p.slot_dir,
                                                p.next_dir, p.heavy_deg);
       if (BOUND && has) add_slack(acc, Pi, p.alpha);
     }
     if (BOUND && i < p.nb) acc += (double)p.bdd_E[i];
+    s = sn;
+    e = en;
   }
   // variables with more than heavy_deg occurrences: one warp each
   for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < p.n_heavy; w += (gridDim.x * blockDim.x) >> 5) {
@@ -2059,9 +2113,9 @@ size_t sweep_warp_smem(int staging, bool lanes2) {
   return lanes2 && kLaneSmemBytes > st ? kLaneSmemBytes : st;
 }
 
-size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging, bool lanes2) {
+size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging, bool lanes2, bool smooth) {
   const size_t warp_part = kWarpsPerBlock * sweep_warp_smem(staging, lanes2);
-  const size_t group_part = group_floats(block_buf, block_depth_buf) * sizeof(float);
+  const size_t group_part = group_floats(block_buf, block_depth_buf, smooth) * sizeof(float);
   return warp_part > group_part ? warp_part : group_part;
 }
 
@@ -2077,7 +2131,7 @@ int sweep_launch(bool forward, int mode, const SweepParams &p_in, int grid, cuda
   SweepParams p = p_in;
   if (p.lanes2 && (p.alpha > 0.f || p.split || mode == kUpdateFused)) return -5;  // lane tiles: plain min-sum
   p.warp_smem = (int)sweep_warp_smem(staging, p.lanes2 != 0);
-  const size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf, staging, p.lanes2 != 0);
+  const size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf, staging, p.lanes2 != 0, p.alpha > 0.f);
   int rc = 0;
   if (p.split) {  // sub-BDDs: min-sum only, no fused pending pass
     if (p.alpha > 0.f || mode == kUpdateFused) return -5;

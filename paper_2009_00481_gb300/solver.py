@@ -20,14 +20,15 @@ class Solver:
     (explicit cut places) splits the BDDs into sub-BDDs with copy-arc duals (Sec. 6), step size
     ``gamma``; ``split_depth`` D >= 1 instead cuts every BDD into pieces of at most D layers.
     ``lanes``: 1 lane tiles for BDDs of width <= 2 (one lane per BDD), 0 two-lane teams, -1
-    (default) lane tiles on plain solvers.
+    (default) the layout tuner decides (``tune_layout``; ``layout_classes`` gives the table
+    explicitly, see :meth:`layout_table`).
     """
 
     def __init__(self, inst, omega: float = 0.5, host_only: bool = False, max_device_bytes: int = 0,
                  device: int = -1, stream: int = 0, schedule: int = 1, spin_limit: int = 0,
                  alpha: float = 0.0, rank=None, averaging: int = 0, fused_pending: int = -1,
                  staging: int = -1, split: int = 0, cuts=None, gamma: float = 0.5,
-                 split_depth: int = 0, lanes: int = -1):
+                 split_depth: int = 0, lanes: int = -1, tune_layout: int = -1, layout_classes=None):
         import numpy as np
         opt = B.bdd_default_options()
         if isinstance(rank, str):
@@ -47,6 +48,12 @@ class Solver:
         opt.gamma = float(gamma)
         opt.split_depth = int(split_depth)
         opt.lanes = int(lanes)
+        opt.tune_layout = int(tune_layout)
+        self._layout = None if layout_classes is None else np.ascontiguousarray(layout_classes, np.int32)
+        if self._layout is not None:
+            if self._layout.shape != (B.BDD_LAYOUT_KEYS,):
+                raise ValueError("layout_classes needs one entry per layout key")
+            opt.layout_classes = self._layout.ctypes.data_as(B.C.POINTER(B.C.c_int))
         opt.averaging = int(averaging)
         opt.fused_pending = int(fused_pending)
         opt.staging = int(staging)
@@ -112,6 +119,10 @@ class Solver:
 
     def set_costs(self, c):
         B.bdd_set_costs(self.h, c)
+
+    def layout_table(self) -> dict:
+        """Tile class of every layout key and the tuner's probe times."""
+        return B.bdd_layout_table(self.h)
 
     def cuts(self):
         """Cut places of the variable order (split solvers; empty otherwise)."""

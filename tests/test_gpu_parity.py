@@ -362,8 +362,6 @@ def test_fused_pending_matches_separate_kernels(lib, name, variant):
     up to the FP64 summation order, for 8-iteration graphs plus a ragged tail of 3."""
     inst = CASES[name]()
     kw = {"plain": {}, "srmp": {"averaging": 1}, "smooth": {"alpha": 0.2}, "cm": {"rank": "cm"}}[variant]
-    if variant == "smooth" and name == "tomography_16":
-        pytest.skip("smoothed solvers need layers of at most 32 nodes")
     a, b = solver(inst, fused_pending=1, **kw), solver(inst, fused_pending=0, **kw)
     ta, tb = _trace(a, 19), _trace(b, 19)
     close(ta, tb, 1e-12)
@@ -487,8 +485,6 @@ def test_staging_variants_bit_identical(lib, name, variant):
     windows, single- and double-buffered) feed the same arithmetic: bound traces, multipliers and
     pending sums bit-identical over graphs of 8 iterations plus a ragged tail; the autotuner's
     choice is one of them."""
-    if variant == "smooth" and name == "tomography_16":
-        pytest.skip("smoothed solvers need layers of at most 32 nodes")
     inst = CASES[name]()
     kw = {"plain": {}, "smooth": {"alpha": 0.2}, "srmp": {"averaging": 1, "rank": "cm"}}[variant]
     a, b, c = solver(inst, staging=0, **kw), solver(inst, staging=1, **kw), solver(inst, staging=2, **kw)
@@ -537,14 +533,56 @@ def test_lane_tiles_bit_identical_to_teams(lib, name):
 
 
 def test_lane_tiles_default_and_refusals(lib):
-    """Plain solvers default to lane tiles; smoothed, split, fused and persistent solvers keep
-    the team layout, and asking them for lane tiles is refused."""
+    """Plain solvers without the layout tuner default to lane tiles (with it, lane tiles are one
+    of its choices); smoothed, split, fused and persistent solvers keep the team layout, and
+    asking them for lane tiles is refused."""
     from paper_2009_00481_gb300 import BDDError
     from paper_2009_00481_gb300.binding import BDD_EINVAL
     inst = CASES["potts_20x20x3"]()
-    assert solver(inst).lanes == 1
+    assert solver(inst, tune_layout=0).lanes == 1
     for kw in ({"alpha": 0.2}, {"split_depth": 2}, {"fused_pending": 1}, {"schedule": 0}):
         assert solver(inst, **kw).lanes == 0
         with pytest.raises(BDDError) as e:
             solver(inst, lanes=1, **kw)
         assert e.value.code == BDD_EINVAL
+
+
+# ------------------------------------------------------------------------------------------
+# the layout tuner: every table it may pick computes the same values
+# ------------------------------------------------------------------------------------------
+
+def _layout_tables():
+    up, blk = [-1] * 28, [-1] * 28
+    for k in range(28):
+        c = k // 4
+        if c <= 1:
+            up[k], blk[k] = 7, 1
+        elif c < 6:
+            up[k], blk[k] = c + 1, 6
+    return {"lanes_and_wider_teams": up, "teams_and_blocks": blk}
+
+
+@pytest.mark.parametrize("name", ["potts_20x20x3", "matching_small", "tomography_16", "tracking_10x40",
+                                  "random_wide"])
+def test_layout_tuner_choices_bit_identical(lib, name):
+    """The tuned layout and every alternative tile-class table (lane tiles or two-lane teams for
+    widths <= 2, teams of 2^c or 2^(c+1) lanes, block tiles) give bit-identical bound traces,
+    multipliers, pending sums and min-marginals; the tuned solver reports a class for every key
+    that has nodes."""
+    inst = CASES[name]()
+    ref = solver(inst, tune_layout=0, lanes=0)
+    t_ref = _trace(ref, 19)
+    l_ref, p_ref = ref.get_state()
+    _, _, m0_ref, m1_ref = ref.iterate(0, mm=True)
+    tuned = solver(inst)
+    rep = tuned.layout_table()
+    assert np.all((rep["cls"] >= 0) == (rep["nodes"] > 0))
+    others = [tuned] + [solver(inst, layout_classes=np.asarray(t, np.int32)) for t in _layout_tables().values()]
+    for s in others:
+        np.testing.assert_array_equal(_trace(s, 19), t_ref)
+        la, pa = s.get_state()
+        np.testing.assert_array_equal(la, l_ref)
+        np.testing.assert_array_equal(pa, p_ref)
+        _, _, m0, m1 = s.iterate(0, mm=True)
+        np.testing.assert_array_equal(m0, m0_ref)
+        np.testing.assert_array_equal(m1, m1_ref)

@@ -14,6 +14,10 @@ CASES = {
     "potts_8x8x3": lambda: potts_mrf(8, 8, 3, seed=2),
     "tracking_10x40": lambda: tracking(frames=10, dets=40, seed=1),
     "matching_small": lambda: sparse_matching(n_left=60, n_right=50, k=6, n_pairs=800, seed=3),
+    # tomography (the paper smooths its tomography runs, Sec. 7): the 16x16 projections fit warp
+    # tiles (up to 25 nodes per layer), the 24x24 ones need block tiles (up to 36)
+    "tomography_16": lambda: tomography(side=16, seed=1, unary_sigma=0.05),
+    "tomography_24": lambda: tomography(side=24, seed=2, unary_sigma=0.05),
 }
 
 
@@ -65,12 +69,58 @@ def test_small_alpha_recovers_min_sum(lib):
     close(soft, plain, LB_TOL)
 
 
-def test_smoothing_rejects_wide_bdds(lib):
+def test_smoothing_block_tiles_and_width_limit(lib):
+    """Smoothed solvers run block tiles of at most 128 nodes per layer (tomography projections);
+    a row with layers over 128 nodes is refused."""
     from paper_2009_00481_gb300 import BDDError
     from paper_2009_00481_gb300.binding import BDD_ETOOBIG
+    from tests.test_gpu_parity import _wide_rows_instance
+    s = solver(tomography(side=32, seed=1), alpha=0.1)
+    assert s.block_tiles > 0 and 32 < s.max_width <= 128
     with pytest.raises(BDDError) as e:
-        solver(tomography(side=32, seed=1), alpha=0.1)
+        solver(_wide_rows_instance(), alpha=0.1)
     assert e.value.code == BDD_ETOOBIG
+
+
+def test_smoothed_marginals_same_lambda_full_tomography(lib):
+    """Same-multiplier smoothed marginals on the full 64x64 tomography (block tiles of 33..97
+    nodes per layer), element by element."""
+    inst = config(2)
+    alpha = 0.05
+    rng = np.random.default_rng(4)
+    lam = rng.normal(0, 1, size=inst.nnz).astype(np.float32)
+    lam[inst.val == 0] = 0
+    P = rng.normal(0, 0.5, size=inst.n).astype(np.float32)
+    s = solver(inst, alpha=alpha)
+    assert s.block_tiles > 0
+    s.set_state(lam, P)
+    lb, _, m0, m1 = s.iterate(0, mm=True)
+    o = Oracle(inst)
+    o.set_alpha(alpha)
+    o.set_state(lam.astype(np.float64), P.astype(np.float64))
+    e0, e1 = o.min_marginals(fold=True)
+    close(m0, e0, MM_TOL)
+    close(m1, e1, MM_TOL)
+    close([lb], [o.bound()], MM_TOL)
+
+
+@pytest.mark.parametrize("alpha", [0.1, 0.5])
+def test_gradient_block_tiles_matches_oracle_gradient(lib, alpha):
+    """The adjoint of block tiles: d(bound)/dc after K = 20 smoothed iterations on a 24x24
+    tomography with unary costs (projection layers up to 36 nodes wide), every coordinate
+    against the oracle's FP64 reverse-mode gradient."""
+    inst = tomography(side=24, seed=2, unary_sigma=0.2)
+    K = 20
+    s0 = solver(inst, alpha=alpha)
+    assert s0.block_tiles > 0
+    val, grad, _ = _gpu_value_and_grad(inst, inst.c.astype(np.float64), alpha, K)
+    o = Oracle(inst)
+    o.set_alpha(alpha)
+    want_val, want = o.smooth_gradient(K, omega=0.5)
+    close([val], [want_val], LB_TOL)
+    scale = max(1.0, np.abs(want).max())
+    err = np.abs(grad - want) / scale
+    assert err.max() <= 1e-4, err.max()
 
 
 # ------------------------------------------------------------------------------------------

@@ -153,3 +153,96 @@ def test_build_in_a_forked_child(cuda_lib):
             raise AssertionError("the forked child's build did not finish")
         time.sleep(0.05)
     assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0
+
+
+def _tables():
+    """Layout tables that move every key to another valid tile class: lane tiles for widths <= 2
+    and teams twice as wide above; two-lane teams for widths <= 2 and block tiles for every
+    wider key; the defaults."""
+    up = [-1] * 28
+    blk = [-1] * 28
+    for k in range(28):
+        c = k // 4
+        if c <= 1:
+            up[k] = 7
+            blk[k] = 1
+        elif c < 6:
+            up[k] = c + 1
+            blk[k] = 6
+    return {"lanes_and_wider_teams": up, "teams_and_blocks": blk, "defaults": [-1] * 28}
+
+
+@pytest.mark.parametrize("which", ["potts", "tomography_small", "tracking", "random"])
+@pytest.mark.parametrize("table", sorted(_tables()))
+def test_layout_tables_keep_canonical_form(cuda_lib, which, table):
+    """Every tile-class table the layout tuner may pick gives slabs whose canonical read-back is
+    the oracle's BDDs, bit for bit (host layout, no GPU); the reported table matches."""
+    from paper_2009_00481_gb300 import Solver
+    inst = {"potts": lambda: config(0), "tomography_small": lambda: tomography(side=12, seed=3, unary_sigma=0.1),
+            "tracking": lambda: tracking(frames=8, dets=30, seed=2),
+            "random": lambda: random_ilp(n=40, m=30, max_row_vars=14, seed=5, coef=3)}[which]()
+    tab = np.asarray(_tables()[table], np.int32)
+    s = Solver(inst, host_only=2, layout_classes=tab)
+    want = Oracle(inst).canonical()
+    got = s.canonical()
+    for key in ["bdd_row", "bdd_depth", "occ_var", "occ_csr", "occ_width", "lo", "hi"]:
+        np.testing.assert_array_equal(got[key], want[key], err_msg=key)
+    rep = s.layout_table()
+    assert rep["nodes"].sum() == s.N
+    for k in range(28):
+        if rep["nodes"][k] == 0:
+            assert rep["cls"][k] == -1
+        elif tab[k] >= 0:
+            assert rep["cls"][k] == tab[k]
+    assert s.lanes == int(table == "lanes_and_wider_teams")
+
+
+def test_layout_table_rejects_narrow_classes(cuda_lib):
+    from paper_2009_00481_gb300 import BDDError, Solver
+    from paper_2009_00481_gb300.binding import BDD_EINVAL
+    inst = tomography(side=12, seed=3, unary_sigma=0.1)
+    bad = np.full(28, -1, np.int32)
+    bad[3 * 4: 4 * 4] = 2  # widths 5..8 in teams of 4 lanes
+    with pytest.raises(BDDError) as e:
+        Solver(inst, host_only=2, layout_classes=bad)
+    assert e.value.code == BDD_EINVAL
+    lanes_wide = np.full(28, -1, np.int32)
+    lanes_wide[8:12] = 7  # lane tiles are for widths <= 2 only
+    with pytest.raises(BDDError) as e:
+        Solver(inst, host_only=2, layout_classes=lanes_wide)
+    assert e.value.code == BDD_EINVAL
+    with pytest.raises(BDDError) as e:  # explicit tables are for plain solvers
+        Solver(inst, host_only=2, layout_classes=np.full(28, -1, np.int32), alpha=0.1)
+    assert e.value.code == BDD_EINVAL
+
+
+def test_device_error_word_mapping(cuda_lib):
+    """A device error word maps to a status on the host: 0 ok, -7 (an index check of the checked
+    build failed) BDD_EDEVICE, anything else (a bounded device-side wait gave up) BDD_ETIMEOUT."""
+    from paper_2009_00481_gb300.binding import BDD_EDEVICE, BDD_ETIMEOUT, BDD_OK
+    f = cuda_lib.bdd_status_of_device_word
+    assert f(0) == BDD_OK
+    assert f(-7) == BDD_EDEVICE
+    assert f(-6) == BDD_ETIMEOUT and f(1) == BDD_ETIMEOUT and f(-1) == BDD_ETIMEOUT
+
+
+def test_checked_library_exports_the_same_symbols(cuda_lib):
+    """The checked build (-DBDD_CHECKED sweep kernels) loads without a GPU and exports the same
+    C ABI; BDD_DBCA_CHECKED=1 selects it as the process's library."""
+    import ctypes
+    from paper_2009_00481_gb300 import binding
+    from paper_2009_00481_gb300.build import LIB_CHECKED
+    lib = ctypes.CDLL(LIB_CHECKED)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    old = os.environ.get("BDD_DBCA_CHECKED")
+    try:
+        os.environ["BDD_DBCA_CHECKED"] = "1"
+        assert binding.default_library() == LIB_CHECKED
+        os.environ["BDD_DBCA_CHECKED"] = "0"
+        assert binding.default_library() == binding.LIB
+    finally:
+        if old is None:
+            os.environ.pop("BDD_DBCA_CHECKED", None)
+        else:
+            os.environ["BDD_DBCA_CHECKED"] = old
