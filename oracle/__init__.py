@@ -24,16 +24,22 @@ TOP, BOT = -1, -2
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle (plain C11, no FMA contraction so x86 and Arm agree bit for bit)."""
-    if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
-        return _OUT
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    tmp = _OUT + f".tmp{os.getpid()}"
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
+
+
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle (plain C11, no FMA contraction so x86 and Arm agree bit for bit).
+    omp: the OpenMP build (schedule P's loops over BDDs and variables on all host cores, the
+    same results bit for bit), used only as the benchmark's second CPU baseline."""
+    out = _OUT_OMP if omp else _OUT
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                           "-o", tmp, _SRC, "-lm"])
-    os.replace(tmp, _OUT)
-    return _OUT
+                           *(["-fopenmp"] if omp else []), "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, out)
+    return out
 
 
 def _configure(lib):
@@ -80,6 +86,17 @@ def _load():
     if _lib is None:
         _lib = _configure(C.CDLL(build()))
     return _lib
+
+
+_lib_omp = None
+
+
+def load_omp():
+    """The OpenMP build (all host cores; see build)."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = _configure(C.CDLL(build(omp=True)))
+    return _lib_omp
 
 
 def load_variant(path: str):

@@ -53,6 +53,11 @@
  *     piece is a subproblem of the decomposition (its layers are its occurrences).  A depth
  *     split (a reading for deep BDDs) cuts every BDD into pieces of at most D layers instead,
  *     with the same copy arcs and steps.
+ * Threads: the tests, the package smoke check and the oracle the benchmark times as the CPU
+ * baseline use the single-threaded build.  Built with -fopenmp (the benchmark's second CPU
+ * baseline, all host cores), the loops of schedule P over BDDs and over variables run in
+ * parallel; each BDD and each variable is still computed by the same operations in the same
+ * order, so that build's results equal the single-threaded build's bit for bit.
  * Readings where the paper is silent: a min-marginal that is +inf (a row that forces x_i)
  * gives the difference 0; a variable in no row contributes min(0, c_i) to the bound; an empty
  * row is dropped when 0 (sense) b holds and is infeasible otherwise.
@@ -595,6 +600,7 @@ static void check_invariant(oracle_t *h) {
 }
 
 static void form_pending(oracle_t *h) {
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < h->n; ++i) {
     double s = 0.0;
     for (long long t = h->var_ptr[i]; t < h->var_ptr[i + 1]; ++t) s += h->delta[h->var_occ[t]];
@@ -612,6 +618,7 @@ static int srmp_takes(const oracle_t *h, long long o, int forward) {
 /* The share each occurrence takes in the next sweep: P_i / |J_i| (eq. mma-update), or for SRMP
  * P_i / |J_i^>| on J_i^> in a forward sweep (J_i^< backward), all of J_i when that set is empty. */
 static void take_share(oracle_t *h, int forward) {
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < h->n; ++i) {
     long long s = h->var_ptr[i], e = h->var_ptr[i + 1];
     if (e == s) continue;
@@ -630,6 +637,7 @@ static void take_share(oracle_t *h, int forward) {
 
 static void sweep_forward(oracle_t *h, double omega, int check) {
   take_share(h, 1);
+#pragma omp parallel for schedule(dynamic, 64) if (!check)
   for (int b = 0; b < h->nb; ++b) {
     long long o0 = h->bdd_occ0[b];
     int k = h->bdd_k[b];
@@ -670,6 +678,7 @@ static void sweep_forward(oracle_t *h, double omega, int check) {
 
 static void sweep_backward(oracle_t *h, double omega, int check) {
   take_share(h, 0);
+#pragma omp parallel for schedule(dynamic, 64) if (!check)
   for (int b = 0; b < h->nb; ++b) {
     long long o0 = h->bdd_occ0[b];
     for (int l = h->bdd_k[b] - 1; l >= 0; --l) {

@@ -295,3 +295,22 @@ def test_tomography_short_diagonals_force_variables():
     tr = o.run_parallel(20, omega=0.5, check=True)
     w = o.worst()
     assert w["monotone_drop"] < 1e-12 and w["invariant"] < 1e-12 and w["incremental_mm"] < 1e-10
+
+
+def test_openmp_build_is_bit_identical():
+    """The oracle's OpenMP build (the benchmark's second CPU baseline) runs schedule P's loops
+    over BDDs and variables on all host cores and gives the single-threaded build's results bit
+    for bit (traces, multipliers, pending sums), with and without SRMP."""
+    import numpy as np
+
+    from instances import config, tracking
+    from oracle import Oracle, load_omp
+    for inst in (config(0), tracking(frames=6, dets=30, seed=4)):
+        for srmp in (False, True):
+            a, b = Oracle(inst), Oracle(inst, lib=load_omp())
+            if srmp:
+                a.set_srmp(True)
+                b.set_srmp(True)
+            np.testing.assert_array_equal(a.run_parallel(25, omega=0.5), b.run_parallel(25, omega=0.5))
+            np.testing.assert_array_equal(a.lam(fold=False), b.lam(fold=False))
+            np.testing.assert_array_equal(a.pending(), b.pending())
