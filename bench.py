@@ -66,6 +66,8 @@ def parse(argv=None):
     ap.add_argument("--variant-iters", type=int, default=300)
     ap.add_argument("--variants-only", action="store_true", help="print only the order / averaging comparison")
     ap.add_argument("--split-only", action="store_true", help="print only the sub-BDD comparison")
+    ap.add_argument("--smoothed-only", action="store_true",
+                    help="print only the smoothed bound with its adjoint (tracking 50x200, K = 50)")
     ap.add_argument("--split-iters", type=int, default=200, help="timed iterations per sub-BDD variant")
     ap.add_argument("--split-ttb-iters", type=int, default=300,
                     help="oracle iterations giving the sub-BDD comparison's target bound (the GPU runs 3x)")
@@ -494,13 +496,14 @@ def run_batch(args):
     if world == 1 and not args.no_plain:
         plain = run_plain_loop(args, torch, stream, iters)
 
-    forms = None
-    if world == 1 and not args.no_forms:
-        forms = run_forms(args, torch, stream, pool)
-
     cpu, ttb = None, None
     if pool is not None:
         cpu, ttb = batch_reference(pool, sample, iters, finals, traj if world == 1 else None, ms / iters, plain)
+
+    forms = None
+    if world == 1 and not args.no_forms:
+        forms = run_forms(args, torch, stream, pool)
+    if pool is not None:
         pool.close()
 
     out = {
@@ -655,7 +658,37 @@ def run_forms(args, torch, stream, pool):
         out[f"plain_{CONFIG_NAMES[k]}"] = row
         s.close()
 
-    # smoothed with the adjoint (tracking 50x200, tau = 0.1, K = 50)
+    out.update(run_smoothed(args, torch, stream, pool))
+    if pool is not None:  # the oracle's OpenMP build on all host cores, after the pool is done
+        for k in (0, 1, 2, 3):
+            row = out[f"plain_{CONFIG_NAMES[k]}"]
+            try:
+                sec, cores = oracle_omp_seconds(k)
+                row.update({"oracle_omp_s": sec, "oracle_omp_value": 2 * row["nodes"] * CONFIG_ITERS[k] / sec,
+                            "oracle_omp_cores": cores})
+            except Exception as e:  # no OpenMP runtime on this host
+                row["oracle_omp"] = f"unavailable: {e}"
+    return out
+
+
+def oracle_omp_seconds(k: int):
+    """Seconds of the oracle's OpenMP build (schedule P's loops over BDDs and variables on all
+    host cores; the same results bit for bit) for workload k's iterations, and the cores used."""
+    from instances import tomography
+    from oracle import Oracle, load_omp
+    inst = tomography(side=64, seed=0, unary_sigma=0.01) if k == 2 else config(k)
+    o = Oracle(inst, lib=load_omp())
+    t0 = time.perf_counter()
+    o.run_parallel(CONFIG_ITERS[k], omega=0.5)
+    return time.perf_counter() - t0, int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_smoothed(args, torch, stream, pool, reps: int = 3) -> dict:
+    """The smoothed bound with its adjoint (tracking 50x200, tau = 0.1, K = 50): forward and
+    forward + adjoint ms, and the iterations and ms to 1e-3 of the oracle's smoothed bound."""
+    from paper_2009_00481_gb300 import Solver, binding
+
+    out = {}
     inst = config(3)
     K = CONFIG_ITERS[3]
     sm = Solver(inst, omega=0.5, stream=stream.cuda_stream, alpha=SMOOTH_TAU)
@@ -669,7 +702,7 @@ def run_forms(args, torch, stream, pool):
     grad = torch.zeros(inst.n, dtype=torch.float32, device="cuda")
     sp = stream.cuda_stream
 
-    def timed(fn, reps=3):
+    def timed(fn):
         for _ in range(2):
             fn()
         torch.cuda.synchronize()
@@ -932,6 +965,14 @@ def main():
         key = "sub_bdds" if args.split_only else "order_and_averaging"
         res = run_split(args, stream) if args.split_only else run_variants(args, stream)
         print(json.dumps({"metric": METRIC, key: res}), flush=True)
+        return
+    if args.smoothed_only:
+        import torch
+        torch.cuda.set_device(0)
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        print(json.dumps({"metric": METRIC, "smoothed": run_smoothed(args, torch, stream, None, reps=args.steps)}),
+              flush=True)
         return
     if args.config == 4:
         run_batch(args)
