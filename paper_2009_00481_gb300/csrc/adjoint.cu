@@ -75,6 +75,30 @@ __device__ __forceinline__ Team team_of(const SweepParams &p, int tile) {
   return m;
 }
 
+// Per-layer values of a warp team's BDD (its occurrence, node range, multipliers and slot),
+// loaded one layer ahead of their use so that a layer waits on one round of dependent loads
+// (arcs and messages of its nodes) instead of three.  Warp-collective: every lane calls it with
+// the same l.
+struct LayerVals {
+  int o, node0, w, slot;
+  float lam_s, shr_s, lam2;
+};
+
+template <int T>
+__device__ __forceinline__ LayerVals layer_vals(const AdjParams &a, const Team &m, int l) {
+  LayerVals v{};
+  v.o = m.occ0 + occ_before(m.lead_depth, l) + m.team;
+  if (l >= 0 && m.depth > l) {
+    v.node0 = a.sp.occ_node_off[v.o];
+    v.w = a.sp.occ_node_off[v.o + 1] - v.node0;
+    v.lam_s = a.lam_s[v.o];
+    v.shr_s = a.shr_s[v.o];
+    v.lam2 = a.lam2[v.o];
+    v.slot = a.sp.occ_slot[v.o];
+  }
+  return v;
+}
+
 // Adjoint of a forward update sweep.  Descending layers: the node adjoint G of fm_l is pulled
 // from the children (the forward step into layer l+1), the marginal terms are added, and their
 // contributions to the starting backward messages of layer l+1 are pushed into g_node.  Then,
@@ -87,15 +111,14 @@ __device__ void fwd_adjoint_tile(const AdjParams &a, int tile) {
   const float ia = p.inv_alpha;
   float G_next = 0.f, f_next = inf();
   int node0_next = 0, w_next = 0;
+  LayerVals ahead = layer_vals<T>(a, m, m.maxd - 1);
   for (int l = m.maxd - 1; l >= 0; --l) {
+    const LayerVals v = ahead;
+    ahead = layer_vals<T>(a, m, l - 1);  // in flight during this layer
     const bool active = m.depth > l;
     const bool nxt = active && l + 1 < m.depth;
-    const int o = m.occ0 + occ_before(m.lead_depth, l) + m.team;
-    int node0 = 0, w = 0;
-    if (active) {
-      node0 = p.occ_node_off[o];
-      w = p.occ_node_off[o + 1] - node0;
-    }
+    const int o = v.o;
+    const int node0 = active ? v.node0 : 0, w = active ? v.w : 0;
     const bool has = active && m.tl < w;
     int2 lh = make_int2(kNone, kNone);
     float f = inf();
@@ -103,8 +126,8 @@ __device__ void fwd_adjoint_tile(const AdjParams &a, int tile) {
       lh = p.lohi[node0 + m.tl];
       f = a.msg_new[node0 + m.tl];
     }
-    const float lam1 = active ? a.lam_s[o] + a.shr_s[o] : 0.f;
-    const float lam2 = active ? a.lam2[o] : 0.f;
+    const float lam1 = active ? v.lam_s + v.shr_s : 0.f;
+    const float lam2 = active ? v.lam2 : 0.f;
     // pull the adjoint of fm_{l+1} through the forward step from layer l
     const int lo_loc = nxt && lh.x >= 0 ? lh.x - node0_next : -1;
     const int hi_loc = nxt && lh.y >= 0 ? lh.y - node0_next : -1;
@@ -125,8 +148,7 @@ __device__ void fwd_adjoint_tile(const AdjParams &a, int tile) {
     const float a0 = has ? f + b0 : inf(), a1 = has ? f + lam1 + b1 : inf();
     const float m0 = team_agg<T, true>(a0, p), m1 = team_agg<T, true>(a1, p);
     const bool finite = m0 < inf() && m1 < inf();
-    const int slot = active ? p.occ_slot[o] : 0;
-    const float g_delta = active ? a.g_out_delta[slot] : 0.f;
+    const float g_delta = active ? a.g_out_delta[v.slot] : 0.f;
     const float gd = finite ? p.omega * (g_delta - G_lam2) : 0.f;  // adjoint of m1 - m0
     const float p0 = weight(a0, m0, ia), p1 = weight(a1, m1, ia);
     G += -gd * p0 + gd * p1;
@@ -149,17 +171,15 @@ __device__ void fwd_adjoint_tile(const AdjParams &a, int tile) {
   // the starting backward messages: bmp_l(v) = softmin(bmp_{l+1}(lo), lam_l + bmp_{l+1}(hi)),
   // adjoints flowing from layer l to layer l + 1
   float carry = 0.f;
+  ahead = layer_vals<T>(a, m, 0);
   for (int l = 0; l < m.maxd; ++l) {
+    const LayerVals v = ahead;
+    ahead = layer_vals<T>(a, m, l + 1);  // the next layer: in flight, and its first node
     const bool active = m.depth > l;
     const bool nxt = active && l + 1 < m.depth;
-    const int o = m.occ0 + occ_before(m.lead_depth, l) + m.team;
-    int node0 = 0, w = 0, node0n = 0;
-    if (active) {
-      node0 = p.occ_node_off[o];
-      w = p.occ_node_off[o + 1] - node0;
-    }
-    const int ob1 = occ_before(m.lead_depth, l + 1);  // warp-wide: outside the branch
-    if (nxt) node0n = p.occ_node_off[m.occ0 + ob1 + m.team];
+    const int o = v.o;
+    const int node0 = active ? v.node0 : 0, w = active ? v.w : 0;
+    const int node0n = nxt ? ahead.node0 : 0;
     const bool has = active && m.tl < w;
     int2 lh = make_int2(kNone, kNone);
     float bn = inf(), Gb = 0.f;
@@ -168,7 +188,7 @@ __device__ void fwd_adjoint_tile(const AdjParams &a, int tile) {
       bn = a.msg_pre[node0 + m.tl];
       if (l >= 1) Gb = a.g_node[node0 + m.tl] + carry;
     }
-    const float lam = active ? a.lam_s[o] : 0.f;
+    const float lam = active ? v.lam_s : 0.f;
     const float b0 = has ? target_msg(a.msg_pre, lh.x) : inf();
     const float b1 = has ? target_msg(a.msg_pre, lh.y) : inf();
     const float q0 = has ? weight(b0, bn, ia) : 0.f;
@@ -192,17 +212,15 @@ __device__ void bwd_adjoint_tile(const AdjParams &a, int tile) {
   const Team m = team_of<T>(p, tile);
   const float ia = p.inv_alpha;
   float carry = 0.f;
+  LayerVals ahead = layer_vals<T>(a, m, 0);
   for (int l = 0; l < m.maxd; ++l) {
+    const LayerVals v = ahead;
+    ahead = layer_vals<T>(a, m, l + 1);  // the next layer: in flight, and its first node
     const bool active = m.depth > l;
     const bool nxt = active && l + 1 < m.depth;
-    const int o = m.occ0 + occ_before(m.lead_depth, l) + m.team;
-    int node0 = 0, w = 0, node0n = 0;
-    if (active) {
-      node0 = p.occ_node_off[o];
-      w = p.occ_node_off[o + 1] - node0;
-    }
-    const int ob1 = occ_before(m.lead_depth, l + 1);  // warp-wide: outside the branch
-    if (nxt) node0n = p.occ_node_off[m.occ0 + ob1 + m.team];
+    const int o = v.o;
+    const int node0 = active ? v.node0 : 0, w = active ? v.w : 0;
+    const int node0n = nxt ? ahead.node0 : 0;
     const bool has = active && m.tl < w;
     int2 lh = make_int2(kNone, kNone);
     float fp = inf(), bn = inf(), Gbn = 0.f;
@@ -212,8 +230,8 @@ __device__ void bwd_adjoint_tile(const AdjParams &a, int tile) {
       bn = a.msg_new[node0 + m.tl];
       Gbn = l == 0 ? (m.tl == 0 && a.gE ? (float)*a.gE : 0.f) : carry;
     }
-    const float lam1 = active ? a.lam_s[o] + a.shr_s[o] : 0.f;
-    const float lam2 = active ? a.lam2[o] : 0.f;
+    const float lam1 = active ? v.lam_s + v.shr_s : 0.f;
+    const float lam2 = active ? v.lam2 : 0.f;
     const float b0 = has ? target_msg(a.msg_new, lh.x) : inf();
     const float b1 = has ? target_msg(a.msg_new, lh.y) : inf();
     // backward step bmn_l = softmin(b0, lam'' + b1)
@@ -224,8 +242,7 @@ __device__ void bwd_adjoint_tile(const AdjParams &a, int tile) {
     const float a0 = has ? fp + b0 : inf(), a1 = has ? fp + lam1 + b1 : inf();
     const float m0 = team_agg<T, true>(a0, p), m1 = team_agg<T, true>(a1, p);
     const bool finite = m0 < inf() && m1 < inf();
-    const int slot = active ? p.occ_slot[o] : 0;
-    const float g_delta = active ? a.g_out_delta[slot] : 0.f;
+    const float g_delta = active ? a.g_out_delta[v.slot] : 0.f;
     const float gd = finite ? p.omega * (g_delta - G_lam2) : 0.f;
     const float p0 = weight(a0, m0, ia), p1 = weight(a1, m1, ia);
     if (has) a.g_node[node0 + m.tl] = -gd * p0 + gd * p1;  // adjoint of fmp_l(v), marginal part
@@ -243,15 +260,14 @@ __device__ void bwd_adjoint_tile(const AdjParams &a, int tile) {
   // adjoints flowing from layer l + 1 back to layer l
   float G_next = 0.f, f_next = inf();
   int node0_next = 0;
+  ahead = layer_vals<T>(a, m, m.maxd - 1);
   for (int l = m.maxd - 1; l >= 0; --l) {
+    const LayerVals v = ahead;
+    ahead = layer_vals<T>(a, m, l - 1);  // in flight during this layer
     const bool active = m.depth > l;
     const bool nxt = active && l + 1 < m.depth;
-    const int o = m.occ0 + occ_before(m.lead_depth, l) + m.team;
-    int node0 = 0, w = 0;
-    if (active) {
-      node0 = p.occ_node_off[o];
-      w = p.occ_node_off[o + 1] - node0;
-    }
+    const int o = v.o;
+    const int node0 = active ? v.node0 : 0, w = active ? v.w : 0;
     const bool has = active && m.tl < w;
     int2 lh = make_int2(kNone, kNone);
     float f = inf(), G = 0.f;
@@ -260,7 +276,7 @@ __device__ void bwd_adjoint_tile(const AdjParams &a, int tile) {
       f = a.msg_pre[node0 + m.tl];
       G = a.g_node[node0 + m.tl];
     }
-    const float lam = active ? a.lam_s[o] : 0.f;
+    const float lam = active ? v.lam_s : 0.f;
     const int lo_loc = nxt && lh.x >= 0 ? lh.x - node0_next : -1;
     const int hi_loc = nxt && lh.y >= 0 ? lh.y - node0_next : -1;
     const float Gc0 = __shfl_sync(kFull, G_next, m.tbase + ((lo_loc < 0 ? 0 : lo_loc) & (T - 1)));

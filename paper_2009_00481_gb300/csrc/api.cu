@@ -6,6 +6,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -62,9 +63,9 @@ struct bdd_solver {
   bool host_layout = false;      // host_only == 2: the slab layout is kept in host memory
   Layout layout;
   // host metadata of the device layout
-  std::vector<int> bdd_perm;     // sorted position -> canonical BDD index
-  std::vector<int> canon_row;    // canonical BDD index -> row
-  std::vector<int> tile_occ0, tile_bdd0, tile_nbdd;
+  hvec<int> bdd_perm;     // sorted position -> canonical BDD index
+  hvec<int> canon_row;    // canonical BDD index -> row
+  hvec<int> tile_occ0, tile_bdd0, tile_nbdd;
   int class_tile_off[kWarpClasses + 2] = {0};
   int n_warp_tiles = 0, n_block_tiles = 0, block_buf = 0;
   std::vector<int> var_deg;
@@ -576,8 +577,8 @@ int build_cut_tables(const HostBDDs &H, const Layout &L, const CopyPairs &P, Cut
   return BDD_OK;
 }
 
-template <class Tp>
-int upload(bdd_solver *h, Tp **d, const std::vector<Tp> &v) {
+template <class Tp, class A>
+int upload(bdd_solver *h, Tp **d, const std::vector<Tp, A> &v) {
   RC(h->alloc(d, (long long)v.size()));
   if (!v.empty()) CK(cudaMemcpy(*d, v.data(), v.size() * sizeof(Tp), cudaMemcpyHostToDevice));
   return BDD_OK;
@@ -606,15 +607,25 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c, const CutTables
   // heavy_deg occurrences.  heavy_deg: the least of 8, 16, 32, ... that leaves at most 4096 such
   // variables, so that each gets its own warp (a warp's two rounds of loads beat a thread's
   // serial batches for few long variables; for many, the extra warps cost more than they save)
-  h->heavy_deg = 8;
-  for (;;) {
-    int cnt = 0;
-    for (int i = 0; i < h->n; ++i) cnt += L.var_ptr[i + 1] - L.var_ptr[i] > h->heavy_deg;
-    if (cnt <= 4096 || h->heavy_deg >= (1 << 20)) break;
-    h->heavy_deg *= 2;
+  // (one parallel pass: variables above 8 * 2^t occurrences, for every t)
+  constexpr int kDegSteps = 18;
+  long long above[kDegSteps] = {};
+  {
+    std::mutex mu;
+    parallel_for(h->n, 1 << 16, [&](long long a, long long e) {
+      long long loc[kDegSteps] = {};
+      for (long long i = a; i < e; ++i) {
+        const int d = L.var_ptr[i + 1] - L.var_ptr[i];
+        for (int t = 0; t < kDegSteps && d > (8 << t); ++t) ++loc[t];
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      for (int t = 0; t < kDegSteps; ++t) above[t] += loc[t];
+    });
   }
-  int n_heavy = 0;
-  for (int i = 0; i < h->n; ++i) n_heavy += L.var_ptr[i + 1] - L.var_ptr[i] > h->heavy_deg;
+  int step = 0;
+  while (step + 1 < kDegSteps && above[step] > 4096) ++step;
+  h->heavy_deg = 8 << step;
+  const int n_heavy = (int)above[step];
   const int heavy_blocks = (n_heavy + kReduceThreads / 32 - 1) / (kReduceThreads / 32);
   h->grid_reduce = std::max(1, std::min(std::max((range + kReduceThreads - 1) / kReduceThreads, heavy_blocks), 152 * 16));
   // the largest dynamic shared memory any staging variant's sweep launch asks for
@@ -689,7 +700,7 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c, const CutTables
   if (h->averaging == 1) RC(upload(h, &h->d_slot_dir, L.slot_dir));
   {
     std::vector<int4> heavy;
-    for (int i = 0; i < h->n; ++i)
+    for (int i = 0; i < h->n && n_heavy > 0; ++i)
       if (L.var_ptr[i + 1] - L.var_ptr[i] > h->heavy_deg)
         heavy.push_back(make_int4(i, L.var_ptr[i], L.var_ptr[i + 1], 0));
     h->n_heavy = (int)heavy.size();
@@ -755,14 +766,25 @@ int bdd_width(const HostBDDs &H, long long b) {
   return w;
 }
 
-HostBDDs probe_instance(const HostBDDs &H, int key, long long key_nodes) {
+// layout key of every BDD, and the nodes per key (both in parallel)
+std::vector<unsigned char> bdd_keys(const HostBDDs &H, long long key_nodes[kLayoutKeys]) {
+  std::vector<unsigned char> key(H.nb());
+  parallel_for(H.nb(), 4096, [&](long long b0, long long b1) {
+    for (long long b = b0; b < b1; ++b) key[b] = (unsigned char)layout_key(bdd_width(H, b), H.bdd_depth[b]);
+  });
+  for (int k = 0; k < kLayoutKeys; ++k) key_nodes[k] = 0;
+  for (long long b = 0; b < H.nb(); ++b) key_nodes[key[b]] += bdd_nodes(H, b);
+  return key;
+}
+
+HostBDDs probe_instance(const HostBDDs &H, const std::vector<unsigned char> &keys, int key, long long key_nodes) {
   HostBDDs P;
   const long long step = std::max(1LL, (key_nodes + kProbeCap - 1) / kProbeCap);
   long long seen = 0;
   P.bdd_occ0.push_back(0);
   P.occ_node0.push_back(0);
   for (long long b = 0; b < H.nb(); ++b) {
-    if (layout_key(bdd_width(H, b), H.bdd_depth[b]) != key) continue;
+    if (keys[b] != key) continue;
     if (seen++ % step) continue;
     P.bdd_row.push_back((int)P.bdd_row.size());
     P.bdd_depth.push_back(H.bdd_depth[b]);
@@ -850,7 +872,7 @@ float probe_time(const HostBDDs &P, bool lanes2, const int *class_of_key) {
 // tiles are a candidate for widths <= 2 (-1 tuned, 0 never, 1 always).  Fills h->key_*, sets
 // h->lanes2; returns a BDD_* status.
 int tune_layout(bdd_solver *h, const HostBDDs &H, int allow_lanes) {
-  for (long long b = 0; b < H.nb(); ++b) h->key_nodes[layout_key(bdd_width(H, b), H.bdd_depth[b])] += bdd_nodes(H, b);
+  const std::vector<unsigned char> keys = bdd_keys(H, h->key_nodes);
   const long long min_nodes = std::max(kProbeMin, H.N() / 100);
   bool any_lane = false;
   for (int k = 0; k < kLayoutKeys; ++k) {
@@ -871,7 +893,7 @@ int tune_layout(bdd_solver *h, const HostBDDs &H, int allow_lanes) {
       h->key_class[k] = cand[0];
       continue;
     }
-    HostBDDs P = probe_instance(H, k, h->key_nodes[k]);
+    HostBDDs P = probe_instance(H, keys, k, h->key_nodes[k]);
     for (int t = 0; t < 2; ++t) {
       int table[kLayoutKeys];
       for (int q = 0; q < kLayoutKeys; ++q) table[q] = -1;
@@ -1065,7 +1087,12 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   h->max_width = H.max_width;
   h->canon_row = H.bdd_row;
   h->var_deg.assign(n, 0);
-  for (int v : H.occ_var) h->var_deg[v]++;
+  {
+    int *deg = h->var_deg.data();
+    parallel_for(H.O(), 1 << 16, [&](long long a, long long e) {
+      for (long long o = a; o < e; ++o) __atomic_fetch_add(&deg[H.occ_var[o]], 1, __ATOMIC_RELAXED);
+    });
+  }
   h->c.assign(c, c + n);
   h->empty_const = empty_constant(h->var_deg, c, n, h->alpha);
   if (h->host_only && !h->host_layout) {
@@ -1079,7 +1106,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
       const int c = opt.layout_classes[k];
       h->key_class[k] = c == kWarpClasses + 1 ? 0 : c;
     }
-    for (long long b = 0; b < H.nb(); ++b) h->key_nodes[layout_key(bdd_width(H, b), H.bdd_depth[b])] += bdd_nodes(H, b);
+    bdd_keys(H, h->key_nodes);
     keyed = true;
   } else if (tune) {
     DeviceGuard dg(opt.device);
@@ -1095,7 +1122,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
     }
     keyed = true;
   } else {
-    for (long long b = 0; b < H.nb(); ++b) h->key_nodes[layout_key(bdd_width(H, b), H.bdd_depth[b])] += bdd_nodes(H, b);
+    bdd_keys(H, h->key_nodes);
   }
   Layout L;
   try {
@@ -1530,8 +1557,8 @@ int bdd_export_canonical(const bdd_solver *h, int *bdd_row, int *bdd_depth, int 
   }
   // read the slabs back (from the device, or the host copy of the layout) and undo the tiles
   const long long O = h->O, N = h->N, nb = h->nb;
-  std::vector<int> off(O + 1), var(O), depth(nb), lohi(2 * N);
-  std::vector<long long> csr(O);
+  hvec<int> off(O + 1), var(O), depth(nb), lohi(2 * N);
+  hvec<long long> csr(O);
   if (h->host_layout) {
     const Layout &L = h->layout;
     off = L.occ_node_off;

@@ -259,9 +259,46 @@ void parallel_for(long long n, long long grain, const std::function<void(long lo
 
 namespace {
 
-template <class Tp>
-void copy_into(std::vector<Tp> &out, size_t off, const std::vector<Tp> &v) {
+template <class V, class Tp>
+void copy_into(V &out, size_t off, const std::vector<Tp> &v) {
   if (!v.empty()) std::memcpy(out.data() + off, v.data(), v.size() * sizeof(Tp));
+}
+
+// out[0] = 0, out[k + 1] = out[k] + in[k] for k < n (out has n + 1 entries), in three passes:
+// the sums of fixed blocks in parallel, their prefix, then every block's prefix in parallel
+// (the same result as the serial loop); returns the largest in[k] through *max_in.
+template <class In>
+void parallel_prefix(const In *in, long long n, long long *out, In *max_in) {
+  constexpr long long kBlock = 1 << 16;
+  const long long nblk = (n + kBlock - 1) / kBlock;
+  std::vector<long long> sum(nblk + 1, 0);
+  std::vector<In> mx(nblk, In(0));
+  parallel_for(nblk, 1, [&](long long b0, long long b1) {
+    for (long long b = b0; b < b1; ++b) {
+      long long acc = 0;
+      In m = In(0);
+      for (long long k = b * kBlock; k < std::min(n, (b + 1) * kBlock); ++k) {
+        acc += in[k];
+        m = std::max(m, in[k]);
+      }
+      sum[b + 1] = acc;
+      mx[b] = m;
+    }
+  });
+  for (long long b = 0; b < nblk; ++b) sum[b + 1] += sum[b];
+  out[0] = 0;
+  parallel_for(nblk, 1, [&](long long b0, long long b1) {
+    for (long long b = b0; b < b1; ++b) {
+      long long acc = sum[b];
+      for (long long k = b * kBlock; k < std::min(n, (b + 1) * kBlock); ++k) {
+        acc += in[k];
+        out[k + 1] = acc;
+      }
+    }
+  });
+  In m = In(0);
+  for (long long b = 0; b < nblk; ++b) m = std::max(m, mx[b]);
+  if (max_in) *max_in = m;
 }
 
 }  // namespace
@@ -328,16 +365,10 @@ int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const i
     }
   });
   chunks.clear();
-  H->bdd_occ0.assign(nb + 1, 0);
-  for (size_t t = 0; t < nb; ++t) {
-    H->bdd_occ0[t + 1] = H->bdd_occ0[t] + H->bdd_depth[t];
-    H->max_depth = std::max(H->max_depth, H->bdd_depth[t]);
-  }
-  H->occ_node0.assign(O + 1, 0);
-  for (size_t o = 0; o < O; ++o) {
-    H->occ_node0[o + 1] = H->occ_node0[o] + H->occ_width[o];
-    H->max_width = std::max(H->max_width, H->occ_width[o]);
-  }
+  H->bdd_occ0.resize(nb + 1);
+  H->occ_node0.resize(O + 1);
+  parallel_prefix(H->bdd_depth.data(), (long long)nb, H->bdd_occ0.data(), &H->max_depth);
+  parallel_prefix(H->occ_width.data(), (long long)O, H->occ_node0.data(), &H->max_width);
   return BDD_OK;
 }
 
@@ -346,21 +377,25 @@ int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_
   L->lanes2 = lanes2;
   // class of each BDD: its key's entry in the table, else the default for its widest layer
   std::vector<int> cls(nb);
-  for (long long b = 0; b < nb; ++b) {
-    int w = 0;
-    for (long long o = H.bdd_occ0[b]; o < H.bdd_occ0[b + 1]; ++o) w = std::max(w, H.occ_width[o]);
-    int c = natural_class(w);
-    if (c == kWarpClasses && w > kMaxBlockTileWidth) return BDD_ETOOBIG;
-    if (lanes2 && w <= 2) c = 0;  // lane tiles: one lane holds both nodes of a layer
-    const int want = class_of_key ? class_of_key[layout_key(w, H.bdd_depth[b])] : -1;
-    if (want >= 0) {
-      const bool fits = want == kWarpClasses ? w <= kMaxBlockTileWidth
-                                             : want < kWarpClasses && ((1 << want) >= w || (want == 0 && lanes2 && w <= 2));
-      if (!fits) return BDD_EINVAL;
-      c = want;
+  std::atomic<int> bad{BDD_OK};
+  parallel_for(nb, 4096, [&](long long b0, long long b1) {
+    for (long long b = b0; b < b1; ++b) {
+      int w = 0;
+      for (long long o = H.bdd_occ0[b]; o < H.bdd_occ0[b + 1]; ++o) w = std::max(w, H.occ_width[o]);
+      int c = natural_class(w);
+      if (c == kWarpClasses && w > kMaxBlockTileWidth) bad.store(BDD_ETOOBIG);
+      if (lanes2 && w <= 2) c = 0;  // lane tiles: one lane holds both nodes of a layer
+      const int want = class_of_key ? class_of_key[layout_key(w, H.bdd_depth[b])] : -1;
+      if (want >= 0) {
+        const bool fits = want == kWarpClasses ? w <= kMaxBlockTileWidth
+                                               : want < kWarpClasses && ((1 << want) >= w || (want == 0 && lanes2 && w <= 2));
+        if (!fits) bad.store(BDD_EINVAL);
+        c = want;
+      }
+      cls[b] = c;
     }
-    cls[b] = c;
-  }
+  });
+  if (bad.load() != BDD_OK) return bad.load();
   // stable counting sort by (class, depth descending); ties keep ascending row order
   const int D = H.max_depth;
   const int nkeys = (kWarpClasses + 1) * (D + 1);
@@ -368,11 +403,13 @@ int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_
   auto key = [&](long long b) { return cls[b] * (D + 1) + (D - H.bdd_depth[b]); };
   for (long long b = 0; b < nb; ++b) cnt[key(b) + 1]++;
   for (int t = 0; t < nkeys; ++t) cnt[t + 1] += cnt[t];
-  L->bdd_perm.assign(nb, 0);
+  L->bdd_perm.resize(nb);
   for (long long b = 0; b < nb; ++b) L->bdd_perm[cnt[key(b)]++] = (int)b;
   L->n_sorted = (int)nb;
   L->bdd_depth.resize(nb);
-  for (long long s = 0; s < nb; ++s) L->bdd_depth[s] = H.bdd_depth[L->bdd_perm[s]];
+  parallel_for(nb, 1 << 14, [&](long long s0, long long s1) {
+    for (long long t = s0; t < s1; ++t) L->bdd_depth[t] = H.bdd_depth[L->bdd_perm[t]];
+  });
   // tiles
   L->tile_occ0.clear();
   L->tile_bdd0.clear();
@@ -396,11 +433,12 @@ int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_
   // filled on its own (a tile's slab is one contiguous range)
   const long long ntiles = (long long)L->tile_bdd0.size();
   L->tile_occ0.resize(ntiles);
-  L->occ_of_canon.assign(O, -1);
-  L->occ_node_off.assign(O + 1, 0);
-  L->occ_var.assign(O, 0);
-  L->occ_csr.assign(O, 0);
-  std::vector<long long> node_of_canon_occ(O, 0);  // device first node of each canonical occurrence
+  // (every entry of these is written below, each tile's by one parallel task)
+  L->occ_of_canon.resize(O);
+  L->occ_node_off.resize(O + 1);
+  L->occ_var.resize(O);
+  L->occ_csr.resize(O);
+  hvec<long long> node_of_canon_occ(O);  // device first node of each canonical occurrence
   std::vector<long long> tile_node0(ntiles + 1, 0);
   {
     long long o = 0, v = 0;
@@ -446,7 +484,7 @@ int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_
       L->max_block_width = std::max(L->max_block_width, H.occ_width[co]);
   }
   // successors as global device node ids
-  L->lohi.assign(2 * N, 0);
+  L->lohi.resize(2 * N);  // every node's pair is written below
   parallel_for(nb, 256, [&](long long b0, long long b1) {
     for (long long b = b0; b < b1; ++b) {
       for (long long co = H.bdd_occ0[b]; co < H.bdd_occ0[b + 1]; ++co) {
@@ -463,43 +501,84 @@ int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_
     }
   });
   // window table of every warp tile: node offsets at layer w * kWinLayers and at layer
-  // min((w + 1) * kWinLayers + 1, maxd), w = 0 .. ceil(maxd / kWinLayers)
+  // min((w + 1) * kWinLayers + 1, maxd), w = 0 .. ceil(maxd / kWinLayers); entry counts first,
+  // then every tile's entries filled on their own
   L->tile_win0.assign(ntiles + 1, 0);
-  L->win_node.clear();
   for (long long t = 0; t < ntiles; ++t) {
-    L->tile_win0[t] = (int)(L->win_node.size() / 2);
-    if (t >= L->class_tile_off[kWarpClasses]) continue;
-    const int b0 = L->tile_bdd0[t], nt = L->tile_nbdd[t];
-    const int dmax = L->bdd_depth[b0];
-    auto node_at = [&](int layer) {  // first node of `layer` in the tile (tile end for dmax)
-      long long before = 0;
-      for (int q = 0; q < nt; ++q) before += std::min(L->bdd_depth[b0 + q], layer);
-      return L->occ_node_off[L->tile_occ0[t] + before];
-    };
-    const int nwin = (dmax + kWinLayers - 1) / kWinLayers;
-    for (int w = 0; w <= nwin; ++w) {
-      L->win_node.push_back(node_at(std::min(w * kWinLayers, dmax)));
-      L->win_node.push_back(node_at(std::min(w * kWinLayers + kWinLayers + 1, dmax)));
-    }
+    const int dmax = L->bdd_depth[L->tile_bdd0[t]];
+    const int entries = t < L->class_tile_off[kWarpClasses] ? (dmax + kWinLayers - 1) / kWinLayers + 1 : 0;
+    L->tile_win0[t + 1] = L->tile_win0[t] + entries;
   }
-  L->tile_win0[ntiles] = (int)(L->win_node.size() / 2);
-  // variable -> occurrences (ascending row, i.e. canonical occurrence order)
-  L->var_ptr.assign(H.n + 1, 0);
-  for (long long co = 0; co < O; ++co) L->var_ptr[H.occ_var[co] + 1]++;
-  for (int i = 0; i < H.n; ++i) L->var_ptr[i + 1] += L->var_ptr[i];
-  L->var_occ.assign(O, 0);
-  L->occ_slot.assign(O, 0);
-  L->slot_dir.assign(O, 0);
-  std::vector<int> fill(L->var_ptr.begin(), L->var_ptr.end() - 1);
-  for (long long b = 0; b < nb; ++b)
-    for (long long co = H.bdd_occ0[b]; co < H.bdd_occ0[b + 1]; ++co) {
-      const int k = fill[H.occ_var[co]]++, o = L->occ_of_canon[co];
-      L->var_occ[k] = o;
-      L->occ_slot[o] = k;
-      // SRMP sets (Appendix A.4): in J_i^> unless the last layer, in J_i^< unless the first
-      L->slot_dir[k] = (unsigned char)((co + 1 < H.bdd_occ0[b + 1] ? kDirForward : 0) |
-                                       (co > H.bdd_occ0[b] ? kDirBackward : 0));
+  L->win_node.resize(2 * (size_t)L->tile_win0[ntiles]);
+  parallel_for(L->class_tile_off[kWarpClasses], 256, [&](long long t0, long long t1) {
+    for (long long t = t0; t < t1; ++t) {
+      const int b0 = L->tile_bdd0[t], nt = L->tile_nbdd[t];
+      const int dmax = L->bdd_depth[b0];
+      auto node_at = [&](int layer) {  // first node of `layer` in the tile (tile end for dmax)
+        long long before = 0;
+        for (int q = 0; q < nt; ++q) before += std::min(L->bdd_depth[b0 + q], layer);
+        return L->occ_node_off[L->tile_occ0[t] + before];
+      };
+      const int nwin = (dmax + kWinLayers - 1) / kWinLayers;
+      int *out = L->win_node.data() + 2 * (size_t)L->tile_win0[t];
+      for (int w = 0; w <= nwin; ++w) {
+        out[2 * w] = node_at(std::min(w * kWinLayers, dmax));
+        out[2 * w + 1] = node_at(std::min(w * kWinLayers + kWinLayers + 1, dmax));
+      }
     }
+  });
+  // variable -> occurrences (ascending row, i.e. canonical occurrence order): degrees by atomic
+  // counts, slots claimed in any order, then each variable's slots sorted by canonical
+  // occurrence; SRMP sets (Appendix A.4): in J_i^> unless the last layer, in J_i^< unless the
+  // first
+  const int n = H.n;
+  std::vector<int> vcnt(n + 1, 0);
+  parallel_for(O, 1 << 16, [&](long long a, long long e) {
+    for (long long co = a; co < e; ++co) __atomic_fetch_add(&vcnt[H.occ_var[co]], 1, __ATOMIC_RELAXED);
+  });
+  std::vector<long long> ptr(n + 1);
+  parallel_prefix(vcnt.data(), (long long)n, ptr.data(), (int *)nullptr);
+  L->var_ptr.resize(n + 1);
+  parallel_for(n + 1, 1 << 16, [&](long long a, long long e) {
+    for (long long i = a; i < e; ++i) {
+      L->var_ptr[i] = (int)ptr[i];
+      if (i < n) vcnt[i] = 0;
+    }
+  });
+  hvec<unsigned char> dir_canon(O);
+  parallel_for(nb, 4096, [&](long long b0, long long b1) {
+    for (long long b = b0; b < b1; ++b)
+      for (long long co = H.bdd_occ0[b]; co < H.bdd_occ0[b + 1]; ++co)
+        dir_canon[co] = (unsigned char)((co + 1 < H.bdd_occ0[b + 1] ? kDirForward : 0) |
+                                        (co > H.bdd_occ0[b] ? kDirBackward : 0));
+  });
+  hvec<int> slot_canon(O);
+  parallel_for(O, 1 << 16, [&](long long a, long long e) {
+    for (long long co = a; co < e; ++co) {
+      const int i = H.occ_var[co];
+      slot_canon[L->var_ptr[i] + __atomic_fetch_add(&vcnt[i], 1, __ATOMIC_RELAXED)] = (int)co;
+    }
+  });
+  L->var_occ.resize(O);
+  L->occ_slot.resize(O);
+  L->slot_dir.resize(O);
+  parallel_for(n, 1 << 14, [&](long long a, long long e) {
+    for (long long i = a; i < e; ++i) {
+      int *s0 = slot_canon.data() + L->var_ptr[i], *s1 = slot_canon.data() + L->var_ptr[i + 1];
+      if (s1 - s0 <= 32) {  // insertion sort of a short list
+        for (int *x = s0 + 1; x < s1; ++x)
+          for (int *y = x; y > s0 && y[-1] > y[0]; --y) std::swap(y[-1], y[0]);
+      } else {
+        std::sort(s0, s1);
+      }
+      for (int k = L->var_ptr[i]; k < L->var_ptr[i + 1]; ++k) {
+        const int co = slot_canon[k], o = L->occ_of_canon[co];
+        L->var_occ[k] = o;
+        L->occ_slot[o] = k;
+        L->slot_dir[k] = dir_canon[co];
+      }
+    }
+  });
   return BDD_OK;
 }
 
@@ -544,8 +623,8 @@ int split_bdds(HostBDDs &H, const int *rank, const std::vector<int> &cuts, int d
     interval[i] = (int)(std::upper_bound(cuts.begin(), cuts.end(), place) - cuts.begin());
   }
   std::vector<char> cut_at;  // depth split: cut before layer l of the current BDD
-  std::vector<int> row, pdepth;
-  std::vector<long long> occ0;
+  hvec<int> row, pdepth;
+  hvec<long long> occ0;
   const long long nb = H.nb();
   for (long long b = 0; b < nb; ++b) {
     const long long o0 = H.bdd_occ0[b];

@@ -4,11 +4,42 @@
 
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 #include <functional>
+#include <memory>
+#include <utility>
 #include <vector>
 
 namespace bdd {
+
+// Host arrays of the compiled BDDs and of the slab layout: std::vector with an allocator whose
+// resize leaves new elements uninitialised (value-initialisation is skipped), so the multi-GB
+// arrays are first written -- and their pages first touched -- by the parallel loops that fill
+// them instead of being zeroed by one thread beforehand.  Code that needs a value writes it.
+template <class T>
+struct UninitAlloc {
+  using value_type = T;
+  UninitAlloc() = default;
+  template <class U>
+  UninitAlloc(const UninitAlloc<U> &) {}
+  T *allocate(std::size_t n) { return std::allocator<T>().allocate(n); }
+  void deallocate(T *p, std::size_t n) { std::allocator<T>().deallocate(p, n); }
+  template <class U>
+  void construct(U *p) noexcept {
+    ::new (static_cast<void *>(p)) U;  // default-initialisation: nothing for arithmetic types
+  }
+  template <class U, class... A>
+  void construct(U *p, A &&...a) {
+    ::new (static_cast<void *>(p)) U(std::forward<A>(a)...);
+  }
+  template <class U>
+  bool operator==(const UninitAlloc<U> &) const { return true; }
+  template <class U>
+  bool operator!=(const UninitAlloc<U> &) const { return false; }
+};
+template <class T>
+using hvec = std::vector<T, UninitAlloc<T>>;
 
 constexpr int kTop = -1;   // arc into the true terminal
 constexpr int kBot = -2;   // arc into the false terminal
@@ -23,13 +54,13 @@ constexpr int kCopy0 = -4;
 struct HostBDDs {
   int n = 0, m = 0;
   long long nnz = 0;
-  std::vector<int> bdd_row, bdd_depth;
-  std::vector<long long> bdd_occ0;   // [nb+1]
-  std::vector<int> occ_var;          // [O]
-  std::vector<long long> occ_csr;    // [O]
-  std::vector<int> occ_width;        // [O]
-  std::vector<long long> occ_node0;  // [O+1]
-  std::vector<int> lo, hi;           // [N]
+  hvec<int> bdd_row, bdd_depth;
+  hvec<long long> bdd_occ0;   // [nb+1]
+  hvec<int> occ_var;          // [O]
+  hvec<long long> occ_csr;    // [O]
+  hvec<int> occ_width;        // [O]
+  hvec<long long> occ_node0;  // [O+1]
+  hvec<int> lo, hi;           // [N]
   int max_depth = 0, max_width = 0;
   long long nb() const { return (long long)bdd_row.size(); }
   long long O() const { return (long long)occ_var.size(); }
@@ -153,24 +184,24 @@ constexpr int kStagings = 3;  // warp-tile staging variants of the update sweeps
 // the occurrences of variable i in ascending row order.
 struct Layout {
   int n_sorted = 0;                    // BDDs in sorted (device) order
-  std::vector<int> bdd_perm;           // sorted position -> canonical BDD index
-  std::vector<int> bdd_depth;          // [nb] sorted order
-  std::vector<int> occ_node_off;       // [O+1]
-  std::vector<int> occ_var;            // [O]
-  std::vector<long long> occ_csr;      // [O]
-  std::vector<int> occ_slot;           // [O] slot of the occurrence
-  std::vector<int> lohi;               // [2N] interleaved lo, hi
-  std::vector<int> tile_occ0, tile_bdd0, tile_nbdd;  // per tile
-  std::vector<int> tile_win0;                        // [ntiles + 1] window table offsets (warp tiles)
-  std::vector<int> win_node;                         // window table, int pairs
+  hvec<int> bdd_perm;           // sorted position -> canonical BDD index
+  hvec<int> bdd_depth;          // [nb] sorted order
+  hvec<int> occ_node_off;       // [O+1]
+  hvec<int> occ_var;            // [O]
+  hvec<long long> occ_csr;      // [O]
+  hvec<int> occ_slot;           // [O] slot of the occurrence
+  hvec<int> lohi;               // [2N] interleaved lo, hi
+  hvec<int> tile_occ0, tile_bdd0, tile_nbdd;  // per tile
+  hvec<int> tile_win0;                        // [ntiles + 1] window table offsets (warp tiles)
+  hvec<int> win_node;                         // window table, int pairs
   int class_tile_off[kWarpClasses + 2] = {0};        // tiles of class c: [off[c], off[c+1])
   bool lanes2 = false;                               // class 0 = lane tiles of width <= 2
   int n_warp_tiles = 0, n_block_tiles = 0;
   int max_block_width = 0;
-  std::vector<int> var_ptr;            // [n+1]
-  std::vector<int> var_occ;            // [O] device occurrence of each slot
-  std::vector<unsigned char> slot_dir; // [O] kDirForward / kDirBackward bits of each slot
-  std::vector<int> occ_of_canon;       // canonical occurrence -> device occurrence
+  hvec<int> var_ptr;            // [n+1]
+  hvec<int> var_occ;            // [O] device occurrence of each slot
+  hvec<unsigned char> slot_dir; // [O] kDirForward / kDirBackward bits of each slot
+  hvec<int> occ_of_canon;       // canonical occurrence -> device occurrence
 };
 
 // Keys of the layout tuner: a BDD's natural class (the smallest team of 2^c >= its widest
