@@ -129,6 +129,7 @@ struct bdd_solver {
   int trace_cap = 0;
   float *d_out_lam = nullptr, *d_out_m0 = nullptr, *d_out_m1 = nullptr;
   int grid_sweep = 0, n_warp_blocks = 0, grid_reduce = 1;
+  int lane_run = 1, n_lane_warps = 0;  // lane tiles per warp; warps that take lane tiles
   size_t smem = 0, smem_persist = 0;
   cudaGraphExec_t g_many = nullptr, g_one = nullptr;
   // smoothed bound and its gradient: per-sweep checkpoints and scratch (allocated on first use)
@@ -208,6 +209,8 @@ struct bdd_solver {
     for (int c = 0; c < kWarpClasses + 2; ++c) p.class_tile_off[c] = class_tile_off[c];
     p.n_warp_blocks = n_warp_blocks;
     p.lanes2 = lanes2 ? 1 : 0;
+    p.lane_run = lane_run;
+    p.n_lane_warps = n_lane_warps;
     p.block_buf = block_buf;
     p.block_depth_buf = block_depth_buf;
     p.omega = omega;
@@ -600,7 +603,22 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c, const CutTables
       dmax = std::max(dmax, L.bdd_depth[L.tile_bdd0[t]]);
     h->block_depth_buf = ((dmax + 3) / 4) * 4;
   }
-  h->n_warp_blocks = (L.n_warp_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  // lane tiles go out in runs of consecutive tiles per warp, as long runs as leave every SM at
+  // least four warps' worth of runs per resident warp slot (about 128 warps per SM), at most
+  // kLaneRunMax; the other warp tiles one per warp after them
+  long long warp_units = L.n_warp_tiles;
+  h->lane_run = 1;
+  h->n_lane_warps = 0;
+  if (h->lanes2) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return BDD_ECUDA;
+    const long long nlt = L.class_tile_off[1];
+    h->lane_run = (int)std::max<long long>(1, std::min<long long>(kLaneRunMax, nlt / (128LL * std::max(1, nsm))));
+    h->n_lane_warps = (int)((nlt + h->lane_run - 1) / h->lane_run);
+    warp_units = h->n_lane_warps + (L.n_warp_tiles - nlt);
+  }
+  h->n_warp_blocks = (int)((warp_units + kWarpsPerBlock - 1) / kWarpsPerBlock);
   h->grid_sweep = h->n_warp_blocks + L.n_block_tiles;
   const int range = std::max<long long>(h->n, h->nb) > 0 ? (int)std::max<long long>(h->n, h->nb) : 1;
   // pending passes: a thread per variable (and BDD), plus one warp per variable with more than

@@ -163,7 +163,9 @@ constexpr size_t kWarpSmemBytes2 = 2 * sizeof(WarpStage8);
 // Lane tiles (layouts built with lanes2): BDDs whose layers have at most two nodes, one lane per
 // BDD, 32 BDDs per tile (warp class 0).  A window holds kWinLayers layers of up to 64 nodes each
 // (plus the layer after it for the backward messages of a forward update); two per warp, filled
-// by the bulk-copy ring.
+// by the bulk-copy ring.  A warp takes a run of up to kLaneRunMax consecutive lane tiles and
+// streams their windows through its two buffers.
+constexpr int kLaneRunMax = 32;  // lane tiles per warp: one tile's scalars per lane
 constexpr int kLaneWinNodes = 64 * kWinLayers;
 struct alignas(16) LaneStage {
   int2 lohi[kLaneWinNodes + 2];
@@ -274,6 +276,8 @@ struct SweepParams {
   int class_tile_off[kWarpClasses + 2];
   int n_warp_blocks;
   int lanes2;           // class-0 tiles are lane tiles (one lane per BDD of width <= 2)
+  int lane_run;         // lane tiles per warp (consecutive, at most kLaneRunMax)
+  int n_lane_warps;     // warps that take lane tiles: ceil(lane tiles / lane_run)
   int warp_smem;        // bytes of dynamic shared memory per warp of a warp block
   int block_buf;        // floats per shared-memory layer buffer of a block tile
   int block_depth_buf;  // floats for the per-layer shares of a block tile

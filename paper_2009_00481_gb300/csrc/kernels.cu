@@ -758,180 +758,289 @@ __device__ __forceinline__ int2 rel_arcs(int2 lh, int node0) {
   return make_int2(lh.x >= 0 ? lh.x - node0 : kNone, lh.y >= 0 ? lh.y - node0 : kNone);
 }
 
-template <int MODE>
-__device__ __forceinline__ void lane_forward(const SweepParams &p, const Phase &ph, int tile, LaneRing &ring) {
+// A lane run: consecutive lane tiles [t0, t1) of one warp (at most 32), streamed through the
+// ring as one sequence of windows (a tile's windows in sweep order, then the next tile's), so
+// that the copies of a tile's first windows overlap the previous tile's last ones.  Lane i holds
+// the scalars of tile t0 + i (loaded once); a tile's BDD depths and window table are loaded
+// while the tile before it is staged, so no tile waits on its own parameters.
+struct LaneRunScalars {
+  int occ0, win0, win1, bdd0, nbdd;  // of tile t0 + lane (win1: the next tile's first entry)
+};
+struct LanePre {  // depth of this lane's BDD and window-table entry `lane` of one tile
+  int depth;
+  int2 tab;
+};
+struct LaneCursor {  // the next window to stage: window w of `tile` (tile == t1: none left)
+  int tile, w, bdd0;
+  TileInfo ti;
+  LanePre pre;  // of tile + 1
+};
+// one staged window and what its processing needs
+struct LaneJob {
+  Window W;
+  int occ0, depth, bdd0;
+};
+
+__device__ __forceinline__ LaneRunScalars lane_run_scalars(const SweepParams &p, int t0, int t1) {
+  const int t = t0 + (threadIdx.x & 31);
+  LaneRunScalars s{0, 0, 0, 0, 0};
+  if (t < t1) {
+    s.occ0 = p.tile_occ0[t];
+    s.win0 = p.tile_win0[t];
+    s.win1 = p.tile_win0[t + 1];
+    s.bdd0 = p.tile_bdd0[t];
+    s.nbdd = p.tile_nbdd[t];
+  }
+  return s;
+}
+
+// issues the loads of tile t's depths and window table (tile t of the run: i = t - t0 < 32)
+__device__ __forceinline__ LanePre lane_pre(const SweepParams &p, const LaneRunScalars &s, int i, bool valid) {
   const int lane = threadIdx.x & 31;
-  const TileInfo ti = tile_info<1>(p, tile);
-  const int occ0 = ti.occ0, depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd, nw = ti.nw;
-  fence_proxy_async();
-  Window Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, 0);
-  {
-    const WindowRanges r = ranges_of<true, MODE>(p, occ0, Wn);
-    stage_window(r, ring, 0, true, true, false);
-    pdl_wait();
-    stage_window(r, ring, 0, false, false, true);
+  const int win0 = __shfl_sync(kFull, s.win0, i & 31), nent = __shfl_sync(kFull, s.win1, i & 31) - win0;
+  const int bdd0 = __shfl_sync(kFull, s.bdd0, i & 31), nbdd = __shfl_sync(kFull, s.nbdd, i & 31);
+  LanePre q{0, make_int2(0, 0)};
+  if (valid && lane < nbdd) q.depth = p.bdd_depth[bdd0 + lane];
+  if (valid && lane < nent) q.tab = p.win_node[win0 + lane];
+  return q;
+}
+
+// tile_info<1> of tile t0 + i from its prefetched depths and window table
+__device__ __forceinline__ TileInfo lane_info(const LaneRunScalars &s, int i, const LanePre &q) {
+  TileInfo ti;
+  ti.occ0 = __shfl_sync(kFull, s.occ0, i & 31);
+  ti.win0 = __shfl_sync(kFull, s.win0, i & 31);
+  ti.depth = q.depth;
+  ti.lead_depth = q.depth;
+  ti.maxd = __reduce_max_sync(kFull, q.depth);
+  ti.nw = (ti.maxd + kWinLayers - 1) / kWinLayers;
+  ti.tab = q.tab;
+  return ti;
+}
+
+// enter tile c.tile (< t1): its parameters from the prefetch, then the next tile's prefetch
+template <bool FWD>
+__device__ __forceinline__ void lane_enter(const SweepParams &p, const LaneRunScalars &s, int t0, int t1,
+                                           LaneCursor &c) {
+  const int i = c.tile - t0;
+  c.ti = lane_info(s, i, c.pre);
+  c.bdd0 = __shfl_sync(kFull, s.bdd0, i & 31);
+  c.w = FWD ? 0 : c.ti.nw - 1;
+  c.pre = lane_pre(p, s, i + 1, c.tile + 1 < t1);
+}
+
+// the window after c's in stream order; skips tiles without layers
+template <bool FWD>
+__device__ __forceinline__ void lane_step(const SweepParams &p, const LaneRunScalars &s, int t0, int t1,
+                                          LaneCursor &c) {
+  if (FWD ? c.w + 1 < c.ti.nw : c.w > 0) {
+    c.w += FWD ? 1 : -1;
+    return;
   }
-  if (nw > 1) {
-    const Window W1 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, 1);
-    stage_window(ranges_of<true, MODE>(p, occ0, W1), ring, 1, true, true, true);
+  while (++c.tile < t1) {
+    lane_enter<FWD>(p, s, t0, t1, c);
+    if (c.ti.nw > 0) break;
   }
-  float pf0 = 0.f, pf1 = 0.f, plam = 0.f;
-  int2 plh0 = make_int2(kNone, kNone), plh1 = make_int2(kNone, kNone);
-  for (int w = 0; w < nw; ++w) {
-    const Window W = Wn;
-    if (w + 1 < nw) Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w + 1);
-    const int b = w & 1;
-    LaneStage &S = ring.S[b];
-    if (!ring_wait(p, ring, b)) return;
-    const WindowRanges r = ranges_of<true, MODE>(p, occ0, W);
-    const int *off = S.off + r.off.shift;
-    const int2 *lohi = S.lohi + r.lohi.shift;
-    const int *slot = S.slot + r.slot.shift;
-    const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
-    const int ca = W.ca, na = W.na, oa = occ0 + ca;
-    for (int l = W.l0; l < W.l1; ++l) {
-      const bool active = depth > l;
-      const int oi = occ_before(lead_depth, l) - ca + lane;
-      int node0 = 0, wl = 0;
+}
+
+template <bool FWD>
+__device__ __forceinline__ void lane_start(const SweepParams &p, const LaneRunScalars &s, int t0, int t1,
+                                           LaneCursor &c) {
+  c.tile = t0;
+  c.pre = lane_pre(p, s, 0, true);
+  for (; c.tile < t1; ++c.tile) {
+    lane_enter<FWD>(p, s, t0, t1, c);
+    if (c.ti.nw > 0) break;
+  }
+}
+
+__device__ __forceinline__ LaneJob lane_job(const SweepParams &p, const LaneCursor &c) {
+  LaneJob j;
+  j.W = window_of(p, c.ti.win0, c.ti.tab, c.ti.lead_depth, c.ti.maxd, c.w);
+  j.occ0 = c.ti.occ0;
+  j.depth = c.ti.depth;
+  j.bdd0 = c.bdd0;
+  return j;
+}
+
+// forward recurrence state carried from layer to layer: the previous layer's two messages, arcs
+// and 1-arc cost
+struct LaneFwd {
+  float pf0, pf1, plam;
+  int2 plh0, plh1;
+};
+
+template <int MODE>
+__device__ __forceinline__ void lane_forward_window(const SweepParams &p, const Phase &ph, const LaneJob &j,
+                                                    const LaneStage &S, LaneFwd &st) {
+  const int lane = threadIdx.x & 31;
+  const Window &W = j.W;
+  const WindowRanges r = ranges_of<true, MODE>(p, j.occ0, W);
+  const int *off = S.off + r.off.shift;
+  const int2 *lohi = S.lohi + r.lohi.shift;
+  const int *slot = S.slot + r.slot.shift;
+  const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
+  const int ca = W.ca, na = W.na, oa = j.occ0 + ca;
+  for (int l = W.l0; l < W.l1; ++l) {
+    const bool active = j.depth > l;
+    const int oi = occ_before(j.depth, l) - ca + lane;
+    int node0 = 0, wl = 0;
+    if (active) {
+      node0 = off[BDD_IN(p, oi, W.cb - W.ca)];
+      wl = off[BDD_IN(p, oi + 1, W.cb - W.ca + 1)] - node0;
+    }
+    // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv, for both nodes
+    float f0 = 0.f, f1 = 0.f;  // the root (layer 0)
+    if (l > 0) {
+      const int2 r0 = rel_arcs(st.plh0, node0), r1 = rel_arcs(st.plh1, node0);
+      f0 = lane_push(0, st.pf0, r0, st.pf1, r1, st.plam);
+      f1 = lane_push(1, st.pf0, r0, st.pf1, r1, st.plam);
+    }
+    int2 lh0 = make_int2(kNone, kNone), lh1 = make_int2(kNone, kNone);
+    if (wl > 0) {
+      p.fm[BDD_NODE(p, node0)] = f0;
+      lh0 = lohi[BDD_IN(p, node0 - na, W.nb - W.na)];
+    }
+    if (wl > 1) {
+      p.fm[BDD_NODE(p, node0 + 1)] = f1;
+      lh1 = lohi[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
+    }
+    float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
+    if (is_update(MODE)) {
+      // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
+      const float a00 = wl > 0 ? f0 + staged_bm<false>(msg, p.copy_val, na, lh0.x) : inf();
+      const float a01 = wl > 1 ? f1 + staged_bm<false>(msg, p.copy_val, na, lh1.x) : inf();
+      const float a10 = wl > 0 ? f0 + lam + staged_bm<false>(msg, p.copy_val, na, lh0.y) : inf();
+      const float a11 = wl > 1 ? f1 + lam + staged_bm<false>(msg, p.copy_val, na, lh1.y) : inf();
+      const float m0 = fminf(a00, a01), m1 = fminf(a10, a11);
+      const float dd = p.omega * mm_difference(m0, m1);
+      lam -= dd;
       if (active) {
-        node0 = off[BDD_IN(p, oi, W.cb - W.ca)];
-        wl = off[BDD_IN(p, oi + 1, W.cb - W.ca + 1)] - node0;
+        p.lam[BDD_OCC(p, oa + oi)] = lam;
+        ph.delta[BDD_OCC(p, slot[oi])] = dd;
       }
-      // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv, for both nodes
-      float f0 = 0.f, f1 = 0.f;  // the root (layer 0)
-      if (l > 0) {
-        const int2 r0 = rel_arcs(plh0, node0), r1 = rel_arcs(plh1, node0);
-        f0 = lane_push(0, pf0, r0, pf1, r1, plam);
-        f1 = lane_push(1, pf0, r0, pf1, r1, plam);
-      }
-      int2 lh0 = make_int2(kNone, kNone), lh1 = make_int2(kNone, kNone);
-      if (wl > 0) {
-        p.fm[BDD_NODE(p, node0)] = f0;
-        lh0 = lohi[BDD_IN(p, node0 - na, W.nb - W.na)];
-      }
-      if (wl > 1) {
-        p.fm[BDD_NODE(p, node0 + 1)] = f1;
-        lh1 = lohi[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
-      }
-      float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
+    }
+    st.pf0 = f0;
+    st.pf1 = f1;
+    st.plh0 = lh0;
+    st.plh1 = lh1;
+    st.plam = lam;
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void lane_backward_window(const SweepParams &p, const Phase &ph, const LaneJob &j,
+                                                     const LaneStage &S, float &bn0, float &bn1, int &node0_next,
+                                                     double &bacc) {
+  const int lane = threadIdx.x & 31;
+  const Window &W = j.W;
+  const WindowRanges r = ranges_of<false, MODE>(p, j.occ0, W);
+  const int *off = S.off + r.off.shift;
+  const int2 *lohi = S.lohi + r.lohi.shift;
+  const int *slot = S.slot + r.slot.shift;
+  const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
+  const int ca = W.ca, na = W.na, oa = j.occ0 + ca;
+  for (int l = W.l1 - 1; l >= W.l0; --l) {
+    const bool active = j.depth > l;
+    const int oi = occ_before(j.depth, l) - ca + lane;
+    int node0 = 0, wl = 0;
+    if (active) {
+      node0 = off[BDD_IN(p, oi, W.cb - W.ca)];
+      wl = off[BDD_IN(p, oi + 1, W.cb - W.ca + 1)] - node0;
+    }
+    int2 lh0 = make_int2(kNone, kNone), lh1 = make_int2(kNone, kNone);
+    float f0 = inf(), f1 = inf();
+    if (wl > 0) {
+      lh0 = lohi[BDD_IN(p, node0 - na, W.nb - W.na)];
+      f0 = msg[BDD_IN(p, node0 - na, W.nb - W.na)];
+    }
+    if (wl > 1) {
+      lh1 = lohi[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
+      f1 = msg[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
+    }
+    float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
+    // successors' backward messages: the next layer's nodes, held by this lane (a BDD's last
+    // layer has terminal arcs only, so nothing is read from the previous BDD of the lane)
+    auto pull = [&](int t) {
+      return t >= 0 ? (((t - node0_next) & 1) == 0 ? bn0 : bn1) : terminal_bm<false>(p.copy_val, t);
+    };
+    const float b00 = pull(lh0.x), b01 = pull(lh0.y), b10 = pull(lh1.x), b11 = pull(lh1.y);
+    if (MODE != kMessages) {
+      const float m0 = fminf(f0 + b00, f1 + b10), m1 = fminf(f0 + lam + b01, f1 + lam + b11);
       if (is_update(MODE)) {
-        // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
-        const float a00 = wl > 0 ? f0 + staged_bm<false>(msg, p.copy_val, na, lh0.x) : inf();
-        const float a01 = wl > 1 ? f1 + staged_bm<false>(msg, p.copy_val, na, lh1.x) : inf();
-        const float a10 = wl > 0 ? f0 + lam + staged_bm<false>(msg, p.copy_val, na, lh0.y) : inf();
-        const float a11 = wl > 1 ? f1 + lam + staged_bm<false>(msg, p.copy_val, na, lh1.y) : inf();
-        const float m0 = fminf(a00, a01), m1 = fminf(a10, a11);
         const float dd = p.omega * mm_difference(m0, m1);
         lam -= dd;
         if (active) {
           p.lam[BDD_OCC(p, oa + oi)] = lam;
           ph.delta[BDD_OCC(p, slot[oi])] = dd;
         }
+      } else if (active && p.out_m0) {
+        const long long c = p.occ_csr[oa + oi];
+        p.out_m0[BDD_CSR(p, c)] = m0;
+        p.out_m1[BDD_CSR(p, c)] = m1;
       }
-      pf0 = f0;
-      pf1 = f1;
-      plh0 = lh0;
-      plh1 = lh1;
-      plam = lam;
     }
-    __syncwarp();  // this buffer is free: stage the window after next into it
-    if (w + 2 < nw) {
-      const Window W2 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w + 2);
-      stage_window(ranges_of<true, MODE>(p, occ0, W2), ring, b, true, true, true);
+    // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
+    const float bc0 = fminf(b00, lam + b01), bc1 = fminf(b10, lam + b11);
+    if (wl > 0) p.bm[BDD_NODE(p, node0)] = bc0;
+    if (wl > 1) p.bm[BDD_NODE(p, node0 + 1)] = bc1;
+    if (l == 0 && active) {  // E^j(lambda^j) at the root
+      p.bdd_E[BDD_BDD(p, j.bdd0 + lane)] = bc0;
+      bacc += (double)bc0;
     }
+    bn0 = bc0;
+    bn1 = bc1;
+    node0_next = node0;
   }
 }
 
-template <int MODE>
-__device__ __forceinline__ void lane_backward(const SweepParams &p, const Phase &ph, int tile, LaneRing &ring,
-                                              double &bacc) {
-  const int lane = threadIdx.x & 31;
-  const TileInfo ti = tile_info<1>(p, tile);
-  const int occ0 = ti.occ0, depth = ti.depth, lead_depth = ti.lead_depth, maxd = ti.maxd, nw = ti.nw;
-  const int bdd = p.tile_bdd0[tile] + lane;
+// The run's window stream: stage the first two windows (the first one's static part before the
+// dependency wait), then process window k from buffer k & 1 and stage window k + 2 into it.
+template <bool FWD, int MODE>
+__device__ __forceinline__ void lane_run(const SweepParams &p, const Phase &ph, int t0, int t1, LaneRing &ring,
+                                         double &bacc) {
   fence_proxy_async();
-  Window Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, nw - 1);
+  const LaneRunScalars s = lane_run_scalars(p, t0, t1);
+  LaneCursor c;
+  lane_start<FWD>(p, s, t0, t1, c);
+  if (c.tile >= t1) return;
+  LaneJob cur = lane_job(p, c);
   {
-    const WindowRanges r = ranges_of<false, MODE>(p, occ0, Wn);
+    const WindowRanges r = ranges_of<FWD, MODE>(p, cur.occ0, cur.W);
     stage_window(r, ring, 0, true, true, false);
     pdl_wait();
     stage_window(r, ring, 0, false, false, true);
   }
-  if (nw > 1) {
-    const Window W1 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, nw - 2);
-    stage_window(ranges_of<false, MODE>(p, occ0, W1), ring, 1, true, true, true);
+  lane_step<FWD>(p, s, t0, t1, c);
+  bool have_next = c.tile < t1;
+  LaneJob next = cur;
+  if (have_next) {
+    next = lane_job(p, c);
+    stage_window(ranges_of<FWD, MODE>(p, next.occ0, next.W), ring, 1, true, true, true);
+    lane_step<FWD>(p, s, t0, t1, c);
   }
+  LaneFwd st{0.f, 0.f, 0.f, make_int2(kNone, kNone), make_int2(kNone, kNone)};
   float bn0 = inf(), bn1 = inf();  // backward messages of the next layer's two nodes
   int node0_next = 0;
-  for (int k = 0; k < nw; ++k) {
-    const int w = nw - 1 - k;
-    const Window W = Wn;
-    if (w > 0) Wn = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w - 1);
+  for (int k = 0;; ++k) {
     const int b = k & 1;
-    LaneStage &S = ring.S[b];
     if (!ring_wait(p, ring, b)) return;
-    const WindowRanges r = ranges_of<false, MODE>(p, occ0, W);
-    const int *off = S.off + r.off.shift;
-    const int2 *lohi = S.lohi + r.lohi.shift;
-    const int *slot = S.slot + r.slot.shift;
-    const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
-    const int ca = W.ca, na = W.na, oa = occ0 + ca;
-    for (int l = W.l1 - 1; l >= W.l0; --l) {
-      const bool active = depth > l;
-      const int oi = occ_before(lead_depth, l) - ca + lane;
-      int node0 = 0, wl = 0;
-      if (active) {
-        node0 = off[BDD_IN(p, oi, W.cb - W.ca)];
-        wl = off[BDD_IN(p, oi + 1, W.cb - W.ca + 1)] - node0;
-      }
-      int2 lh0 = make_int2(kNone, kNone), lh1 = make_int2(kNone, kNone);
-      float f0 = inf(), f1 = inf();
-      if (wl > 0) {
-        lh0 = lohi[BDD_IN(p, node0 - na, W.nb - W.na)];
-        f0 = msg[BDD_IN(p, node0 - na, W.nb - W.na)];
-      }
-      if (wl > 1) {
-        lh1 = lohi[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
-        f1 = msg[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
-      }
-      float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
-      // successors' backward messages: the next layer's nodes, held by this lane
-      auto pull = [&](int t) {
-        return t >= 0 ? (((t - node0_next) & 1) == 0 ? bn0 : bn1) : terminal_bm<false>(p.copy_val, t);
-      };
-      const float b00 = pull(lh0.x), b01 = pull(lh0.y), b10 = pull(lh1.x), b11 = pull(lh1.y);
-      if (MODE != kMessages) {
-        const float m0 = fminf(f0 + b00, f1 + b10), m1 = fminf(f0 + lam + b01, f1 + lam + b11);
-        if (is_update(MODE)) {
-          const float dd = p.omega * mm_difference(m0, m1);
-          lam -= dd;
-          if (active) {
-            p.lam[BDD_OCC(p, oa + oi)] = lam;
-            ph.delta[BDD_OCC(p, slot[oi])] = dd;
-          }
-        } else if (active && p.out_m0) {
-          const long long c = p.occ_csr[oa + oi];
-          p.out_m0[BDD_CSR(p, c)] = m0;
-          p.out_m1[BDD_CSR(p, c)] = m1;
-        }
-      }
-      // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
-      const float bc0 = fminf(b00, lam + b01), bc1 = fminf(b10, lam + b11);
-      if (wl > 0) p.bm[BDD_NODE(p, node0)] = bc0;
-      if (wl > 1) p.bm[BDD_NODE(p, node0 + 1)] = bc1;
-      if (l == 0 && active) {  // E^j(lambda^j) at the root
-        p.bdd_E[BDD_BDD(p, bdd)] = bc0;
-        bacc += (double)bc0;
-      }
-      bn0 = bc0;
-      bn1 = bc1;
-      node0_next = node0;
+    if (FWD)
+      lane_forward_window<MODE>(p, ph, cur, ring.S[b], st);
+    else
+      lane_backward_window<MODE>(p, ph, cur, ring.S[b], bn0, bn1, node0_next, bacc);
+    __syncwarp();  // this buffer is free: stage the window after next into it
+    const bool have_after = c.tile < t1;
+    LaneJob after = next;
+    if (have_after) {
+      after = lane_job(p, c);
+      stage_window(ranges_of<FWD, MODE>(p, after.occ0, after.W), ring, b, true, true, true);
+      lane_step<FWD>(p, s, t0, t1, c);
     }
-    __syncwarp();
-    if (w >= 2) {
-      const Window W2 = window_of(p, ti.win0, ti.tab, lead_depth, maxd, w - 2);
-      stage_window(ranges_of<false, MODE>(p, occ0, W2), ring, b, true, true, true);
-    }
+    if (!have_next) break;
+    cur = next;
+    next = after;
+    have_next = have_after;
   }
 }
 
@@ -1675,12 +1784,16 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
   double bacc = 0.0;
   if ((int)blockIdx.x < p.n_warp_blocks) {
     const int warp = threadIdx.x >> 5;
-    const int tile = blockIdx.x * kWarpsPerBlock + warp;
+    constexpr bool kLanes = !SMOOTH && !SPLIT && MODE != kUpdateFused;
+    // with lane tiles, warps [0, n_lane_warps) take runs of lane_run consecutive lane tiles and
+    // the warps after them one other warp tile each
+    const int wi = blockIdx.x * kWarpsPerBlock + warp;
+    const bool lanes = kLanes && p.lanes2;
+    const bool lane_tile = lanes && wi < p.n_lane_warps;
+    const int tile = !lanes ? wi : lane_tile ? wi * p.lane_run : wi - p.n_lane_warps + p.class_tile_off[1];
     if (tile >= p.class_tile_off[kWarpClasses]) return;  // whole warp leaves together
     char *mine = reinterpret_cast<char *>(smem) + (size_t)warp * p.warp_smem;
     __shared__ unsigned long long bars[kWarpsPerBlock * kWarpStages];
-    constexpr bool kLanes = !SMOOTH && !SPLIT && MODE != kUpdateFused;
-    const bool lane_tile = kLanes && p.lanes2 && tile < p.class_tile_off[1];
     if (lane_tile || STAGE == 0) {
       if ((threadIdx.x & 31) == 0) {
         for (int b = 0; b < kWarpStages; ++b) bar_init(&bars[warp * kWarpStages + b]);
@@ -1691,10 +1804,7 @@ __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams 
     if constexpr (kLanes) {
       if (lane_tile) {
         LaneRing ring{reinterpret_cast<LaneStage *>(mine), &bars[warp * kWarpStages], 0u, 0u};
-        if (FWD)
-          lane_forward<MODE>(p, ph, tile, ring);
-        else
-          lane_backward<MODE>(p, ph, tile, ring, bacc);
+        lane_run<FWD, MODE>(p, ph, tile, min(tile + p.lane_run, p.class_tile_off[1]), ring, bacc);
       }
     }
     if (!lane_tile) {
