@@ -165,7 +165,7 @@ constexpr size_t kWarpSmemBytes2 = 2 * sizeof(WarpStage8);
 // (plus the layer after it for the backward messages of a forward update); two per warp, filled
 // by the bulk-copy ring.  A warp takes a run of up to kLaneRunMax consecutive lane tiles and
 // streams their windows through its two buffers.
-constexpr int kLaneRunMax = 32;  // lane tiles per warp: one tile's scalars per lane
+constexpr int kLaneRunMax = 4;  // lane tiles per warp (longer runs measured no faster)
 constexpr int kLaneWinNodes = 64 * kWinLayers;
 struct alignas(16) LaneStage {
   int2 lohi[kLaneWinNodes + 2];
@@ -301,6 +301,7 @@ struct SweepParams {
                          // failed index check of the checked build
   long long n_nodes, n_occ, n_csr, n_bdd;  // array extents for the checked build's index checks
   FusedParams fz;       // fz.cnt == null outside the fused plan
+  int pdl_early;        // 1: let the next kernel launch when this one starts; 0: as blocks exit
 };
 
 // Sweep modes.
@@ -339,6 +340,7 @@ struct PendingParams {
   const int4 *heavy;              // variables with more than heavy_deg occurrences: {i, first slot,
   int n_heavy;                    // end slot, 0}, handled by one warp each
   int heavy_deg;
+  int pdl_early;                  // as in SweepParams
 };
 
 // Persistent iteration kernel (one cooperative launch runs n_iter iterations).
@@ -414,6 +416,7 @@ int cut_roots_launch(const CutParams &c, cudaStream_t stream);
 size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging = 0, bool lanes2 = false,
                         bool smooth = false);
 size_t sweep_warp_smem(int staging, bool lanes2);
+int sweep_resident_blocks(size_t smem, int *blocks);  // blocks of a sweep launch per SM
 size_t persist_smem_bytes(int block_buf, int block_depth_buf);
 int sweep_set_smem(size_t bytes);
 int iterate_set_smem(size_t bytes);

@@ -758,11 +758,12 @@ __device__ __forceinline__ int2 rel_arcs(int2 lh, int node0) {
   return make_int2(lh.x >= 0 ? lh.x - node0 : kNone, lh.y >= 0 ? lh.y - node0 : kNone);
 }
 
-// A lane run: consecutive lane tiles [t0, t1) of one warp (at most 32), streamed through the
+// A lane run: consecutive lane tiles [t0, t1) of one warp (at most kLaneRunMax), streamed through the
 // ring as one sequence of windows (a tile's windows in sweep order, then the next tile's), so
 // that the copies of a tile's first windows overlap the previous tile's last ones.  Lane i holds
 // the scalars of tile t0 + i (loaded once); a tile's BDD depths and window table are loaded
 // while the tile before it is staged, so no tile waits on its own parameters.
+static_assert(kLaneRunMax <= 32, "a lane run keeps one tile's scalars per lane");
 struct LaneRunScalars {
   int occ0, win0, win1, bdd0, nbdd;  // of tile t0 + lane (win1: the next tile's first entry)
 };
@@ -1771,10 +1772,11 @@ __device__ __forceinline__ void fused_bound(const FusedParams &z, const float *_
 template <bool FWD, int MODE, bool SMOOTH, int STAGE = 0, bool SPLIT = false>
 __global__ void __launch_bounds__(kBlockThreads) sweep_kernel(const SweepParams p) {
   extern __shared__ __align__(16) float smem[];
-  // the next kernel of the chain may launch now: it reads nothing this one writes before its
-  // own dependency wait.  This kernel reads static data (slab offsets, arcs, slots) before its
-  // wait, and everything a previous kernel writes only after it.
-  pdl_release();
+  // the next kernel of the chain may launch now (small grids; else as this one's blocks exit):
+  // it reads nothing this one writes before its own dependency wait.  This kernel reads static
+  // data (slab offsets, arcs, slots) before its wait, and everything a previous kernel writes
+  // only after it.
+  if (p.pdl_early) pdl_release();
   if (FWD && MODE == kUpdateFused && p.fz.bound) {  // bound of the previous iteration (fused plan)
     pdl_wait();
     fused_bound(p.fz, p.bdd_E, kBlockThreads);
@@ -1874,7 +1876,8 @@ __global__ void __launch_bounds__(kReduceThreads, 8) pending_kernel(const Pendin
     s = p.var_ptr[i0];
     e = p.var_ptr[i0 + 1];
   }
-  pdl_enter();
+  pdl_wait();
+  if (p.pdl_early) pdl_release();
   const int range = BOUND ? (p.n > p.nb ? p.n : p.nb) : p.n;
   const int stride = gridDim.x * blockDim.x;
   double acc = 0.0;
@@ -2223,6 +2226,13 @@ int launch_pdl(void (*kernel)(Args...), int grid, int block, size_t smem, cudaSt
 size_t sweep_warp_smem(int staging, bool lanes2) {
   const size_t st = staging == 2 ? kWarpSmemBytes2 : kWarpSmemBytes;
   return lanes2 && kLaneSmemBytes > st ? kLaneSmemBytes : st;
+}
+
+int sweep_resident_blocks(size_t smem, int *blocks) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, sweep_kernel<true, kUpdate, false, 0, false>,
+                                                       kBlockThreads, smem) == cudaSuccess
+             ? 0
+             : -5;
 }
 
 size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging, bool lanes2, bool smooth) {
