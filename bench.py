@@ -97,11 +97,12 @@ def algorithmic_bytes(kind: str, N: int, O: int, n: int, nb: int) -> int:
         # sweep)
         return 16 * N + 24 * O + (4 if kind == "fwd" else 8) * nb
     if kind == "pending":
-        # per variable: slot range 4, P write 4; per slot: difference 4, occurrence id 4,
-        # share write 4
-        return 8 * n + 12 * O
+        # per variable: slot range 4 (P is stored by the bound pass only); per slot: difference
+        # 4, occurrence id 4, share write 4
+        return 4 * n + 12 * O
     if kind == "pending_bound":
-        return algorithmic_bytes("pending", N, O, n, nb) + 4 * nb
+        # and P write 4 per variable, root value 4 per BDD
+        return algorithmic_bytes("pending", N, O, n, nb) + 4 * n + 4 * nb
     if kind == "iteration":
         return sum(algorithmic_bytes(k, N, O, n, nb) for k in ("fwd", "pending", "bwd", "pending_bound"))
     raise ValueError(kind)

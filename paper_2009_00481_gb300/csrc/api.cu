@@ -1683,7 +1683,7 @@ int bdd_set_state(bdd_solver *h, const float *lambda, const float *pending) {
     else
       CK(cudaMemsetAsync(h->d_P, 0, sizeof(float) * h->n, s));
     // slots holding P_i in the first slot of i reproduce P exactly; the pending pass then writes
-    // the shares (and P again, unchanged)
+    // the shares
     if (pending_to_slots_launch(h->d_var_ptr, h->d_P, h->d_delta, h->n, s)) return BDD_ECUDA;
     RC(h->pending(false, s, kDirForward));  // the shares of the next (forward) sweep
   }

@@ -127,15 +127,41 @@ __device__ __forceinline__ double slack_term(float P, float alpha) {
   return (double)(m - alpha * log1pf(expf(-fabsf(P) / alpha)));
 }
 
-// acc += the y-slack term of P.  For min-sum the term is min(0, P): only a negative P adds
-// anything, and the comparison is made in FP32 (exact), so a nonnegative P costs no FP64
-// instruction (this part's FP64 throughput is a small fraction of its FP32 throughput).
+// A thread's share of the bound: FP32 terms summed without FP64 arithmetic per term (this
+// part's FP64 rate is 1/64 of its FP32 rate, and a pending pass with one FP64 add per variable
+// and per BDD ran 0.2 ms longer per pass on the 256-instance Potts batch).  Terms of magnitude
+// below 2^100 go into hi with Knuth's TwoSum, whose exact rounding error goes into lo; the
+// others (and infinities, NaN) straight into lo, where they dwarf the rounding errors (and
+// propagate as an FP64 sum would).  Otherwise hi + lo is the sum of the terms up to the
+// roundings of the additions into lo: an error below k^2 * 2^-48 of the summed magnitudes for
+// k terms (about 3e-10 for the few hundred terms a thread takes), far below the FP32 rounding
+// of the terms themselves.  The threads' values are then summed in FP64.
+struct BoundSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    if (!(fabsf(x) < 0x1p100f)) {
+      lo += x;
+      return;
+    }
+    const float t = hi + x;
+    const float xv = t - hi;  // TwoSum: t + err = hi + x exactly
+    const float err = (hi - (t - xv)) + (x - xv);
+    hi = t;
+    lo += err;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// the y-slack term of P: min(0, P) for min-sum (only a negative P adds anything), its soft
+// minimum for alpha > 0, in FP32 either way
 template <bool SMOOTH>
-__device__ __forceinline__ void add_slack(double &acc, float P, double alpha) {
-  if (SMOOTH)
-    acc += slack_term(P, (float)alpha);
-  else if (P < 0.f)
-    acc += (double)P;
+__device__ __forceinline__ void add_slack(BoundSum &acc, float P, float alpha) {
+  if (SMOOTH) {
+    const float m = fminf(P, 0.f);
+    acc.add(m - alpha * log1pf(expf(-fabsf(P) / alpha)));
+  } else if (P < 0.f) {
+    acc.add(P);
+  }
 }
 
 // the general path of pending_var for slots [s, e) of variable i
@@ -143,7 +169,7 @@ __device__ __forceinline__ float pending_tail_sum(const float *__restrict__ delt
                                                   float *__restrict__ P, float *__restrict__ share_occ, int i, int s,
                                                   int e, const unsigned char *__restrict__ slot_dir, int dir) {
   const float Pi = slot_sum(delta, s, e);
-  P[i] = Pi;
+  if (P) P[i] = Pi;
   if (slot_dir) {
     int cnt = 0;
     for (int k = s; k < e; ++k) cnt += (slot_dir[k] & dir) != 0;
@@ -166,7 +192,8 @@ __device__ __forceinline__ float pending_tail_sum(const float *__restrict__ delt
 }
 
 // Pending sums (the sum in eq. mma-update, deferred): P_i = sum of i's slots in ascending
-// order, stored, and share_i = P_i / |J_i| written to each of i's occurrences for the next sweep.
+// order, stored (unless P is null), and share_i = P_i / |J_i| written to each of i's occurrences
+// for the next sweep.
 // With SRMP bits (Appendix A.4), P_i / |J_i^dir| to the slots in J_i^dir and 0 to the others,
 // unless J_i^dir is empty (then P_i / |J_i| to all).
 // FAST > 0: one round of loads for variables with at most FAST occurrences (slots, occurrence
@@ -198,7 +225,7 @@ __device__ __forceinline__ float pending_var_se(const float *__restrict__ delta,
 #pragma unroll
     for (int j = 0; j < W; ++j)
       if (j < deg) Pi += v[j];
-    P[i] = Pi;
+    if (P) P[i] = Pi;
     int cnt = 0;
 #pragma unroll
     for (int j = 0; j < W; ++j) cnt += (d[j] & dir) != 0;
@@ -244,7 +271,7 @@ __device__ __forceinline__ float pending_var_warp(const float *__restrict__ delt
     for (int j = 0; j < here; ++j) Pi += __shfl_sync(kFull, v, j);
     cnt += __popc(__ballot_sync(kFull, take));
   }
-  if (lane == 0) P[i] = Pi;
+  if (lane == 0 && P) P[i] = Pi;
   const float share = Pi / (float)(cnt > 0 ? cnt : e - s);
   if (o_first >= 0) share_occ[o_first] = (cnt == 0 || take_first) ? share : 0.f;
   for (int k = s + 32 + lane; k < e; k += 32)
@@ -1880,7 +1907,11 @@ __global__ void __launch_bounds__(kReduceThreads, 8) pending_kernel(const Pendin
   if (p.pdl_early) pdl_release();
   const int range = BOUND ? (p.n > p.nb ? p.n : p.nb) : p.n;
   const int stride = gridDim.x * blockDim.x;
-  double acc = 0.0;
+  // P_i is stored by the bound pass only: the pass between the sweeps of an iteration would
+  // store values that the bound pass of the same iteration overwrites before anything reads them
+  float *const P = BOUND ? p.P : nullptr;
+  const float alpha = (float)p.alpha;
+  BoundSum acc;
   for (int i = i0; i < range; i += stride) {
     // the next variable's slot range goes out before this variable's slots are loaded, so the
     // two round trips overlap (measured on the Potts batch: 0.93 -> 0.86 ms per pass)
@@ -1891,24 +1922,24 @@ __global__ void __launch_bounds__(kReduceThreads, 8) pending_kernel(const Pendin
     }
     if (i < p.n) {
       bool has;
-      const float Pi = pending_var_se<0, true>(p.delta, p.var_occ, p.P, p.share_occ, i, s, e, has, p.slot_dir,
+      const float Pi = pending_var_se<0, true>(p.delta, p.var_occ, P, p.share_occ, i, s, e, has, p.slot_dir,
                                                p.next_dir, p.heavy_deg);
-      if (BOUND && has) add_slack<SMOOTH>(acc, Pi, p.alpha);
+      if (BOUND && has) add_slack<SMOOTH>(acc, Pi, alpha);
     }
-    if (BOUND && i < p.nb) acc += (double)p.bdd_E[i];
+    if (BOUND && i < p.nb) acc.add(p.bdd_E[i]);
     s = sn;
     e = en;
   }
   // variables with more than heavy_deg occurrences: one warp each
   for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < p.n_heavy; w += (gridDim.x * blockDim.x) >> 5) {
     const int4 hv = p.heavy[w];
-    const float Pi = pending_var_warp(p.delta, p.var_occ, p.P, p.share_occ, hv.x, hv.y, hv.z, p.slot_dir, p.next_dir);
-    if (BOUND && (threadIdx.x & 31) == 0) add_slack<SMOOTH>(acc, Pi, p.alpha);
+    const float Pi = pending_var_warp(p.delta, p.var_occ, P, p.share_occ, hv.x, hv.y, hv.z, p.slot_dir, p.next_dir);
+    if (BOUND && (threadIdx.x & 31) == 0) add_slack<SMOOTH>(acc, Pi, alpha);
   }
   if constexpr (BOUND) {
     __shared__ double red[kReduceThreads / 32];
     __shared__ bool last;
-    const double blk = block_sum(acc, red, kReduceThreads / 32);
+    const double blk = block_sum(acc.value(), red, kReduceThreads / 32);
     if (p.defer) {  // the next forward sweep (or a finishing kernel) sums the partials
       if (threadIdx.x == 0) p.partial[blockIdx.x] = blk;
       return;

@@ -65,8 +65,8 @@ def test_bench_bookkeeping():
             assert st == {"forward": bench.STAGING[f], "backward": bench.STAGING[b]}
     N, O, n, nb = 1000, 700, 300, 90
     # the sum of the per-kernel figures: two sweeps (16 N + 24 O + 4 / 8 nb), two pending passes
-    # (8 n + 12 O, the bound one + 4 nb)
-    assert bench.algorithmic_bytes("iteration", N, O, n, nb) == 32 * N + 72 * O + 16 * n + 16 * nb
+    # (4 n + 12 O; the bound one also stores P, + 4 n, and reads the root values, + 4 nb)
+    assert bench.algorithmic_bytes("iteration", N, O, n, nb) == 32 * N + 72 * O + 12 * n + 16 * nb
 
 
 def test_partition_covers_batch_once_and_balances():
