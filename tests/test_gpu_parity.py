@@ -311,6 +311,43 @@ def test_schedules_agree(lib, name):
     close(_trace(c, 5), tb2, 1e-12)
 
 
+def _mixed_degree_instance(seed=5):
+    """At-most-one rows of four over variables of three kinds: 6000 of degree about 12 (more than
+    4096 above 8, so the heavy-variable threshold is 16), 6000 of degree about 2, and 12 of
+    degree about 60 (heavy: one warp each)."""
+    rng = np.random.default_rng(seed)
+    n = 12000
+    need = np.concatenate([np.full(6000, 12), np.full(6000, 2)])
+    need[rng.choice(n, size=12, replace=False)] = 60
+    pool = np.repeat(np.arange(n), need)
+    rng.shuffle(pool)
+    rows = []
+    for g in range(0, len(pool) - 3, 4):
+        cols = np.unique(pool[g:g + 4])
+        rows.append((cols, np.ones(len(cols)), 1, SENSE_LE))
+    c = rng.standard_normal(n).astype(np.float32)
+    return _from_rows("mixed_degrees", n, rows, c)
+
+
+@pytest.mark.parametrize("averaging", [0, 1])
+def test_pending_mixed_degrees_match_persistent(lib, averaging):
+    """The per-phase pending pass (one thread per variable with the next slot range loaded
+    ahead, variables above the heavy threshold one warp each, the threshold chosen from the
+    degree histogram) gives the multipliers and pending sums of the persistent kernel's pass bit
+    for bit, with and without SRMP, on a mix of light, medium and heavy variables."""
+    inst = _mixed_degree_instance()
+    deg = np.bincount(inst.col, minlength=inst.n)
+    assert (deg > 16).sum() >= 12 and (deg > 8).sum() > 4096
+    a = solver(inst, schedule=0, averaging=averaging)
+    b = solver(inst, schedule=1, averaging=averaging)
+    assert a.schedule == 0 and b.schedule == 1
+    close(_trace(a, 12), _trace(b, 12), 1e-12)
+    la, pa = a.get_state()
+    lb_, pb = b.get_state()
+    np.testing.assert_array_equal(la, lb_)
+    np.testing.assert_array_equal(pa, pb)
+
+
 def test_barrier_timeout_reports_status(lib):
     """A grid-barrier wait limited to one poll gives up; the kernel returns, the host call reports
     BDD_ETIMEOUT, and the device stays usable."""
