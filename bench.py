@@ -119,9 +119,12 @@ def staging_of(s) -> dict:
 
 
 def sweep_kernel_name(kind: str, s) -> str:
+    """The sweep kernel as the solver runs it: lane tiles (if its layout has them) and the
+    staging of its other warp tiles."""
     st = staging_of(s)
-    return {"fwd": f"sweep_kernel<forward, update> ({st['forward']})",
-            "bwd": f"sweep_kernel<backward, update> ({st['backward']})",
+    lanes = "lane tiles + " if getattr(s, "lanes", 0) else ""
+    return {"fwd": f"sweep_kernel<forward, update> ({lanes}{st['forward']})",
+            "bwd": f"sweep_kernel<backward, update> ({lanes}{st['backward']})",
             "pending": "pending_kernel", "pending_bound": "pending_kernel<bound>"}[kind]
 
 
