@@ -168,6 +168,16 @@ typedef struct {
                                  kLayoutKeys = 28 entries, -1 = default, 0..5 a team of 2^c lanes,
                                  6 a block tile, 7 lane tiles (widths <= 2 only); a class too
                                  narrow for its key -> BDD_EINVAL.  Read by bdd_build only. */
+  int smooth_messages;        /* smoothed solvers: whether bdd_smooth_forward keeps the messages
+                                 every sweep wrote (and the initial backward messages), (2 K + 1)
+                                 N floats, so that bdd_smooth_backward reads each sweep's
+                                 starting messages instead of recomputing them with one
+                                 messages-only sweep per reversed sweep.  1: keep them
+                                 (BDD_ENOMEM if they cannot be allocated); 0: recompute; -1
+                                 (default): keep them when they fit in a quarter of the free
+                                 device memory and in max_device_bytes, else recompute.  The
+                                 gradient is the same either way (the recomputation repeats
+                                 the forward's arithmetic). */
 } bdd_options;
 
 #define BDD_LAYOUT_KEYS 28
@@ -233,11 +243,13 @@ int bdd_bound_parts(bdd_solver *h, int nparts, const long long *row_off, const l
  * bdd_smooth_forward sets c (device float[n]), restarts (lambda = c/|J_i|), runs K iterations
  * and writes the smoothed bound after them (the y-slack form with every minimum soft) to
  * d_bound (device double[1]); it keeps a checkpoint of the multipliers and shares of every sweep
- * (2 K O floats of device memory) and stores the forward's generation number in *generation
- * (host; NULL skips it).  bdd_smooth_backward then writes d_grad_c (device float[n])
- * = g * d bound / d c, g read from d_gbound (device double[1]), by reverse-mode passes over the
- * K iterations that recompute each sweep's messages from its checkpoint (hand-written adjoint
- * kernels).  `generation` names the forward whose gradient is wanted: it must be the value that
+ * (2 K O floats of device memory), and of the messages every sweep wrote unless
+ * bdd_options.smooth_messages says otherwise ((2 K + 1) N floats), and stores the forward's
+ * generation number in *generation (host; NULL skips it).  bdd_smooth_backward then writes
+ * d_grad_c (device float[n]) = g * d bound / d c, g read from d_gbound (device double[1]), by
+ * reverse-mode passes over the K iterations (hand-written adjoint kernels) that take each
+ * sweep's messages from those checkpoints, or recompute them from the multipliers' checkpoint
+ * when the messages were not kept.  `generation` names the forward whose gradient is wanted: it must be the value that
  * forward returned, it must be the solver's last forward, and no state-changing call may come
  * in between; otherwise BDD_ESTATE (so two forwards on one solver feeding one loss cannot take
  * the second one's checkpoints for the first one's gradient).  Both enqueue on `stream` (NULL =

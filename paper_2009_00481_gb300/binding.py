@@ -37,7 +37,7 @@ class bdd_options(C.Structure):
                 ("fused_pending", C.c_int), ("staging", C.c_int), ("split_intervals", C.c_int),
                 ("cuts", C.POINTER(C.c_int)), ("n_cuts", C.c_int), ("gamma", C.c_float),
                 ("split_depth", C.c_int), ("lanes", C.c_int), ("tune_layout", C.c_int),
-                ("layout_classes", C.POINTER(C.c_int))]
+                ("layout_classes", C.POINTER(C.c_int)), ("smooth_messages", C.c_int)]
 
 
 class BDDError(RuntimeError):

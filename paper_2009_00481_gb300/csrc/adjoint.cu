@@ -99,6 +99,48 @@ __device__ __forceinline__ LayerVals layer_vals(const AdjParams &a, const Team &
   return v;
 }
 
+// The loads of one layer of a warp team's BDD, in three stages that a loop issues for three
+// consecutive layers ahead of their use: the layer's per-occurrence values (their addresses need
+// no load), the lane's node (its arcs, two per-node values, and the adjoints of the layer's
+// outputs), and the messages of the node's arc targets (their addresses are the arcs).  A layer's
+// step then waits on no load it issued: the arcs were loaded two layers earlier, the target
+// messages one layer earlier.  Only the timing of the loads differs from loading each value where
+// it is used; the arithmetic and its order are unchanged.
+struct Ahead {
+  LayerVals v;
+  int2 lh;       // the node's arcs (kNone for a lane without a node)
+  float x, y;    // two per-node values (which arrays depends on the loop); 0 without a node
+  float gl, gd;  // adjoints of the updated multiplier (by occurrence) and of the difference (by slot)
+  float b0, b1;  // messages of the 0- and 1-arc targets (target_msg)
+};
+
+// node stage of layer l: X and Y are read at the lane's node if Y_ok (Y may be null); with outs,
+// the adjoints of the layer's outputs; with IN, g_in_lam at the layer's occurrence (into gl)
+template <int T>
+__device__ __forceinline__ void ahead_node(Ahead &q, const AdjParams &a, const Team &m, int l, const float *X,
+                                           const float *Y, bool y_ok, bool outs, bool in = false) {
+  const bool active = l >= 0 && m.depth > l;
+  const bool has = active && m.tl < q.v.w;
+  const int nd = q.v.node0 + m.tl;
+  q.lh = make_int2(kNone, kNone);
+  q.x = q.y = q.gl = q.gd = 0.f;
+  if (has) {
+    q.lh = a.sp.lohi[nd];
+    q.x = X[nd];
+    if (Y && y_ok) q.y = Y[nd];
+  }
+  if (active && outs) {
+    q.gl = a.g_out_lam[q.v.o];
+    q.gd = a.g_out_delta[q.v.slot];
+  }
+  if (active && in && m.tl == 0) q.gl = a.g_in_lam[q.v.o];
+}
+
+__device__ __forceinline__ void ahead_targets(Ahead &q, const float *msg) {
+  q.b0 = target_msg(msg, q.lh.x);  // kNone: +inf, as for a lane without a node
+  q.b1 = target_msg(msg, q.lh.y);
+}
+
 // Adjoint of a forward update sweep.  Descending layers: the node adjoint G of fm_l is pulled
 // from the children (the forward step into layer l+1), the marginal terms are added, and their
 // contributions to the starting backward messages of layer l+1 are pushed into g_node.  Then,
@@ -111,21 +153,29 @@ __device__ void fwd_adjoint_tile(const AdjParams &a, int tile) {
   const float ia = p.inv_alpha;
   float G_next = 0.f, f_next = inf();
   int node0_next = 0, w_next = 0;
-  LayerVals ahead = layer_vals<T>(a, m, m.maxd - 1);
+  // c: layer l (all stages), n1: layer l - 1 (node stage), n2: layer l - 2 (layer values)
+  Ahead c, n1, n2;
+  c.v = layer_vals<T>(a, m, m.maxd - 1);
+  ahead_node<T>(c, a, m, m.maxd - 1, a.msg_new, nullptr, false, true);
+  ahead_targets(c, a.msg_pre);
+  n1.v = layer_vals<T>(a, m, m.maxd - 2);
+  ahead_node<T>(n1, a, m, m.maxd - 2, a.msg_new, nullptr, false, true);
+  n2.v = layer_vals<T>(a, m, m.maxd - 3);
   for (int l = m.maxd - 1; l >= 0; --l) {
-    const LayerVals v = ahead;
-    ahead = layer_vals<T>(a, m, l - 1);  // in flight during this layer
+    const Ahead q = c;
+    c = n1;
+    ahead_targets(c, a.msg_pre);
+    n1 = n2;
+    ahead_node<T>(n1, a, m, l - 2, a.msg_new, nullptr, false, true);
+    n2.v = layer_vals<T>(a, m, l - 3);
+    const LayerVals &v = q.v;
     const bool active = m.depth > l;
     const bool nxt = active && l + 1 < m.depth;
     const int o = v.o;
     const int node0 = active ? v.node0 : 0, w = active ? v.w : 0;
     const bool has = active && m.tl < w;
-    int2 lh = make_int2(kNone, kNone);
-    float f = inf();
-    if (has) {
-      lh = p.lohi[node0 + m.tl];
-      f = a.msg_new[node0 + m.tl];
-    }
+    const int2 lh = q.lh;
+    const float f = has ? q.x : inf();
     const float lam1 = active ? v.lam_s + v.shr_s : 0.f;
     const float lam2 = active ? v.lam2 : 0.f;
     // pull the adjoint of fm_{l+1} through the forward step from layer l
@@ -141,15 +191,14 @@ __device__ void fwd_adjoint_tile(const AdjParams &a, int tile) {
       g_theta = Gc1 * weight(f + lam2, fc1, ia);
       G += g_theta;
     }
-    const float G_lam2 = (active ? a.g_out_lam[o] : 0.f) + team_sum<T>(g_theta);
+    const float G_lam2 = q.gl + team_sum<T>(g_theta);
     // marginals of layer l and the update
-    const float b0 = has ? target_msg(a.msg_pre, lh.x) : inf();
-    const float b1 = has ? target_msg(a.msg_pre, lh.y) : inf();
+    const float b0 = has ? q.b0 : inf();
+    const float b1 = has ? q.b1 : inf();
     const float a0 = has ? f + b0 : inf(), a1 = has ? f + lam1 + b1 : inf();
     const float m0 = team_agg<T, true>(a0, p), m1 = team_agg<T, true>(a1, p);
     const bool finite = m0 < inf() && m1 < inf();
-    const float g_delta = active ? a.g_out_delta[v.slot] : 0.f;
-    const float gd = finite ? p.omega * (g_delta - G_lam2) : 0.f;  // adjoint of m1 - m0
+    const float gd = finite ? p.omega * (q.gd - G_lam2) : 0.f;  // adjoint of m1 - m0
     const float p0 = weight(a0, m0, ia), p1 = weight(a1, m1, ia);
     G += -gd * p0 + gd * p1;
     const float g_lam1 = G_lam2 + gd;  // d m1 / d lam' = 1
@@ -169,32 +218,39 @@ __device__ void fwd_adjoint_tile(const AdjParams &a, int tile) {
   }
   __syncwarp();
   // the starting backward messages: bmp_l(v) = softmin(bmp_{l+1}(lo), lam_l + bmp_{l+1}(hi)),
-  // adjoints flowing from layer l to layer l + 1
+  // adjoints flowing from layer l to layer l + 1.  Node values: x = bmp (msg_pre), y = g_node
+  // (written above by the same lane), gl = g_in_lam (written above).
   float carry = 0.f;
-  ahead = layer_vals<T>(a, m, 0);
+  c.v = layer_vals<T>(a, m, 0);
+  ahead_node<T>(c, a, m, 0, a.msg_pre, a.g_node, false, false, true);
+  ahead_targets(c, a.msg_pre);
+  n1.v = layer_vals<T>(a, m, 1);
+  ahead_node<T>(n1, a, m, 1, a.msg_pre, a.g_node, true, false, true);
+  n2.v = layer_vals<T>(a, m, 2);
   for (int l = 0; l < m.maxd; ++l) {
-    const LayerVals v = ahead;
-    ahead = layer_vals<T>(a, m, l + 1);  // the next layer: in flight, and its first node
+    const Ahead q = c;
+    c = n1;  // the next layer: its node stage arrived, its targets in flight
+    ahead_targets(c, a.msg_pre);
+    n1 = n2;
+    ahead_node<T>(n1, a, m, l + 2, a.msg_pre, a.g_node, true, false, true);
+    n2.v = layer_vals<T>(a, m, l + 3);
+    const LayerVals &v = q.v;
     const bool active = m.depth > l;
     const bool nxt = active && l + 1 < m.depth;
     const int o = v.o;
-    const int node0 = active ? v.node0 : 0, w = active ? v.w : 0;
-    const int node0n = nxt ? ahead.node0 : 0;
+    const int w = active ? v.w : 0;
+    const int node0n = nxt ? c.v.node0 : 0;
     const bool has = active && m.tl < w;
-    int2 lh = make_int2(kNone, kNone);
-    float bn = inf(), Gb = 0.f;
-    if (has) {
-      lh = p.lohi[node0 + m.tl];
-      bn = a.msg_pre[node0 + m.tl];
-      if (l >= 1) Gb = a.g_node[node0 + m.tl] + carry;
-    }
+    const int2 lh = q.lh;
+    const float bn = has ? q.x : inf();
+    const float Gb = has && l >= 1 ? q.y + carry : 0.f;
     const float lam = active ? v.lam_s : 0.f;
-    const float b0 = has ? target_msg(a.msg_pre, lh.x) : inf();
-    const float b1 = has ? target_msg(a.msg_pre, lh.y) : inf();
+    const float b0 = has ? q.b0 : inf();
+    const float b1 = has ? q.b1 : inf();
     const float q0 = has ? weight(b0, bn, ia) : 0.f;
     const float q1 = has ? weight(lam + b1, bn, ia) : 0.f;
     const float gl = team_sum<T>(Gb * q1);
-    if (active && m.tl == 0) a.g_in_lam[o] += gl;
+    if (active && m.tl == 0) a.g_in_lam[o] = q.gl + gl;
     const int lo_rel = has && lh.x >= 0 && nxt ? lh.x - node0n : kNone;
     const int hi_rel = has && lh.y >= 0 && nxt ? lh.y - node0n : kNone;
     carry = team_push<T>(lo_rel, hi_rel, Gb * q0, Gb * q1, m.tbase, m.tl);
@@ -212,38 +268,45 @@ __device__ void bwd_adjoint_tile(const AdjParams &a, int tile) {
   const Team m = team_of<T>(p, tile);
   const float ia = p.inv_alpha;
   float carry = 0.f;
-  LayerVals ahead = layer_vals<T>(a, m, 0);
+  const float gE = m.tl == 0 && a.gE ? (float)*a.gE : 0.f;
+  // node values: x = fmp (msg_pre), y = bmn (msg_new); targets from msg_new
+  Ahead c, n1, n2;
+  c.v = layer_vals<T>(a, m, 0);
+  ahead_node<T>(c, a, m, 0, a.msg_pre, a.msg_new, true, true);
+  ahead_targets(c, a.msg_new);
+  n1.v = layer_vals<T>(a, m, 1);
+  ahead_node<T>(n1, a, m, 1, a.msg_pre, a.msg_new, true, true);
+  n2.v = layer_vals<T>(a, m, 2);
   for (int l = 0; l < m.maxd; ++l) {
-    const LayerVals v = ahead;
-    ahead = layer_vals<T>(a, m, l + 1);  // the next layer: in flight, and its first node
+    const Ahead q = c;
+    c = n1;  // the next layer: its node stage arrived, its targets in flight
+    ahead_targets(c, a.msg_new);
+    n1 = n2;
+    ahead_node<T>(n1, a, m, l + 2, a.msg_pre, a.msg_new, true, true);
+    n2.v = layer_vals<T>(a, m, l + 3);
+    const LayerVals &v = q.v;
     const bool active = m.depth > l;
     const bool nxt = active && l + 1 < m.depth;
     const int o = v.o;
     const int node0 = active ? v.node0 : 0, w = active ? v.w : 0;
-    const int node0n = nxt ? ahead.node0 : 0;
+    const int node0n = nxt ? c.v.node0 : 0;
     const bool has = active && m.tl < w;
-    int2 lh = make_int2(kNone, kNone);
-    float fp = inf(), bn = inf(), Gbn = 0.f;
-    if (has) {
-      lh = p.lohi[node0 + m.tl];
-      fp = a.msg_pre[node0 + m.tl];
-      bn = a.msg_new[node0 + m.tl];
-      Gbn = l == 0 ? (m.tl == 0 && a.gE ? (float)*a.gE : 0.f) : carry;
-    }
+    const int2 lh = q.lh;
+    const float fp = has ? q.x : inf(), bn = has ? q.y : inf();
+    const float Gbn = has ? (l == 0 ? gE : carry) : 0.f;
     const float lam1 = active ? v.lam_s + v.shr_s : 0.f;
     const float lam2 = active ? v.lam2 : 0.f;
-    const float b0 = has ? target_msg(a.msg_new, lh.x) : inf();
-    const float b1 = has ? target_msg(a.msg_new, lh.y) : inf();
+    const float b0 = has ? q.b0 : inf();
+    const float b1 = has ? q.b1 : inf();
     // backward step bmn_l = softmin(b0, lam'' + b1)
     const float q0 = has ? weight(b0, bn, ia) : 0.f;
     const float q1 = has ? weight(lam2 + b1, bn, ia) : 0.f;
-    const float G_lam2 = (active ? a.g_out_lam[o] : 0.f) + team_sum<T>(Gbn * q1);
+    const float G_lam2 = q.gl + team_sum<T>(Gbn * q1);
     // marginals and the update
     const float a0 = has ? fp + b0 : inf(), a1 = has ? fp + lam1 + b1 : inf();
     const float m0 = team_agg<T, true>(a0, p), m1 = team_agg<T, true>(a1, p);
     const bool finite = m0 < inf() && m1 < inf();
-    const float g_delta = active ? a.g_out_delta[v.slot] : 0.f;
-    const float gd = finite ? p.omega * (g_delta - G_lam2) : 0.f;
+    const float gd = finite ? p.omega * (q.gd - G_lam2) : 0.f;
     const float p0 = weight(a0, m0, ia), p1 = weight(a1, m1, ia);
     if (has) a.g_node[node0 + m.tl] = -gd * p0 + gd * p1;  // adjoint of fmp_l(v), marginal part
     const float g_lam1 = G_lam2 + gd;
@@ -257,25 +320,27 @@ __device__ void bwd_adjoint_tile(const AdjParams &a, int tile) {
   }
   __syncwarp();
   // the starting forward messages: fmp_l(v) = softmin over in-arcs of fmp_{l-1}(u) + theta,
-  // adjoints flowing from layer l + 1 back to layer l
+  // adjoints flowing from layer l + 1 back to layer l.  Node values: x = fmp, y = g_node (written
+  // above by the same lane), gl = g_in_lam (written above); no target messages.
   float G_next = 0.f, f_next = inf();
   int node0_next = 0;
-  ahead = layer_vals<T>(a, m, m.maxd - 1);
+  c.v = layer_vals<T>(a, m, m.maxd - 1);
+  ahead_node<T>(c, a, m, m.maxd - 1, a.msg_pre, a.g_node, true, false, true);
+  n1.v = layer_vals<T>(a, m, m.maxd - 2);
   for (int l = m.maxd - 1; l >= 0; --l) {
-    const LayerVals v = ahead;
-    ahead = layer_vals<T>(a, m, l - 1);  // in flight during this layer
+    const Ahead q = c;
+    c = n1;
+    ahead_node<T>(c, a, m, l - 1, a.msg_pre, a.g_node, true, false, true);
+    n1.v = layer_vals<T>(a, m, l - 2);
+    const LayerVals &v = q.v;
     const bool active = m.depth > l;
     const bool nxt = active && l + 1 < m.depth;
     const int o = v.o;
     const int node0 = active ? v.node0 : 0, w = active ? v.w : 0;
     const bool has = active && m.tl < w;
-    int2 lh = make_int2(kNone, kNone);
-    float f = inf(), G = 0.f;
-    if (has) {
-      lh = p.lohi[node0 + m.tl];
-      f = a.msg_pre[node0 + m.tl];
-      G = a.g_node[node0 + m.tl];
-    }
+    const int2 lh = q.lh;
+    const float f = has ? q.x : inf();
+    float G = has ? q.y : 0.f;
     const float lam = active ? v.lam_s : 0.f;
     const int lo_loc = nxt && lh.x >= 0 ? lh.x - node0_next : -1;
     const int hi_loc = nxt && lh.y >= 0 ? lh.y - node0_next : -1;
@@ -290,7 +355,7 @@ __device__ void bwd_adjoint_tile(const AdjParams &a, int tile) {
       G += g_theta;
     }
     const float gl = team_sum<T>(g_theta);
-    if (active && m.tl == 0) a.g_in_lam[o] += gl;
+    if (active && m.tl == 0) a.g_in_lam[o] = q.gl + gl;
     G_next = has ? G : 0.f;
     f_next = f;
     node0_next = node0;

@@ -139,6 +139,10 @@ struct bdd_solver {
   long long state_gen = 0;      // bumped by every call that changes the dual state
   long long smooth_gen = -1;    // state_gen right after the recorded forward
   float *ck_lam = nullptr, *ck_shr = nullptr;
+  int smooth_messages = -1;     // bdd_options.smooth_messages
+  float *ck_msg = nullptr;      // messages before the first sweep and after every sweep
+  int msg_cap = 0;              // message checkpoints ck_msg holds
+  bool smooth_msgs = false;     // the recorded forward kept its messages in ck_msg
   float *t_nodeA = nullptr, *t_nodeB = nullptr, *t_gnode = nullptr;
   float *t_glam0 = nullptr, *t_glam1 = nullptr, *t_gshr = nullptr, *t_gdelta = nullptr;
   float *t_delta = nullptr, *t_E = nullptr;
@@ -987,6 +991,7 @@ void bdd_default_options(bdd_options *opt) {
   opt->lanes = -1;
   opt->tune_layout = -1;
   opt->layout_classes = nullptr;
+  opt->smooth_messages = -1;
 }
 
 int bdd_last_failed_row(void) { return g_failed_row; }
@@ -1055,6 +1060,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   h->nnz = nnz;
   h->omega = opt.omega;
   h->alpha = opt.alpha;
+  h->smooth_messages = opt.smooth_messages;
   h->averaging = opt.averaging;
   h->fused_opt = want_split ? 0 : opt.fused_pending;  // the copy-arc steps follow whole sweeps
   h->staging_opt = h->fused_opt == 1 ? 0 : opt.staging;
@@ -1379,6 +1385,27 @@ int bdd_smooth_forward(bdd_solver *h, int K, const float *d_c, double *d_bound, 
     RC(h->alloc(&h->t_E, h->nb));
   }
   RC(h->ensure_trace(K + 1));
+  // the messages before the first sweep and after every sweep, when kept: the backward then
+  // reads each sweep's starting and final messages instead of recomputing the starting ones
+  h->smooth_msgs = false;
+  if (h->smooth_messages != 0 && N > 0) {
+    const long long count = (2LL * K + 1) * N;
+    if (2 * K + 1 <= h->msg_cap) {
+      h->smooth_msgs = true;
+    } else {
+      size_t free_b = 0, total_b = 0;
+      const bool fits = h->smooth_messages == 1 ||
+                        (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+                         (size_t)count * sizeof(float) <= free_b / 4);
+      const int arc = fits ? h->alloc(&h->ck_msg, count) : BDD_ENOMEM;
+      if (arc == BDD_OK) {
+        h->msg_cap = 2 * K + 1;
+        h->smooth_msgs = true;
+      } else if (h->smooth_messages == 1) {
+        return arc;
+      }
+    }
+  }
   RC(h->begin(s));
   // costs: on the device for the iteration, on the host for the constant of empty variables
   std::vector<float> c(h->n);
@@ -1394,6 +1421,8 @@ int bdd_smooth_forward(bdd_solver *h, int K, const float *d_c, double *d_bound, 
   RC(h->restart(s));
   CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), s));
   const size_t ob = sizeof(float) * (size_t)std::max<long long>(O, 1);
+  const size_t nbytes = sizeof(float) * (size_t)N;
+  if (h->smooth_msgs) CK(cudaMemcpyAsync(h->ck_msg, h->d_bm, nbytes, cudaMemcpyDeviceToDevice, s));
   for (int it = 0; it < K; ++it) {
     for (int half = 0; half < 2; ++half) {
       const long long sw = 2LL * it + half;
@@ -1402,6 +1431,9 @@ int bdd_smooth_forward(bdd_solver *h, int K, const float *d_c, double *d_bound, 
         CK(cudaMemcpyAsync(h->ck_shr + sw * O, h->d_share_occ, ob, cudaMemcpyDeviceToDevice, s));
       }
       RC(h->sweep(half == 0, kUpdate, s));
+      if (h->smooth_msgs)
+        CK(cudaMemcpyAsync(h->ck_msg + (sw + 1) * N, half == 0 ? h->d_fm : h->d_bm, nbytes,
+                           cudaMemcpyDeviceToDevice, s));
       RC(h->pending(half == 1, s));
     }
   }
@@ -1439,20 +1471,25 @@ int bdd_smooth_backward(bdd_solver *h, long long generation, const double *d_gbo
   // writes, which are exactly the next sweep's starting messages.  Walking the sweeps in
   // reverse, each step therefore recomputes only its starting messages (one messages-only
   // sweep from the checkpoint into a scratch buffer) and takes its outputs from the step before:
-  // the last sweep's from the solver's final state.
+  // the last sweep's from the solver's final state.  When the forward kept every sweep's
+  // messages, nothing is recomputed: sweep sw started from message checkpoint sw and wrote
+  // checkpoint sw + 1.
   float *bufs[2] = {h->t_nodeA, h->t_nodeB};
   int xb = 0;
+  const long long N = h->N;
   const float *msg_new = h->d_bm, *lam2 = h->d_lam;
   for (long long sw = 2LL * K - 1; sw >= 0; --sw) {
     const bool fwd = (sw % 2) == 0;
     const float *lam_s = h->ck_lam + sw * O, *shr_s = h->ck_shr + sw * O;
-    float *pre = bufs[xb];
+    float *pre = h->smooth_msgs ? h->ck_msg + sw * N : bufs[xb];
     SweepParams p = h->sweep_params();
     p.lam = const_cast<float *>(lam_s);  // a messages-only sweep reads the multipliers, never writes them
     p.share_occ = shr_s;
     p.delta = h->t_delta;
     p.bdd_E = h->t_E;
-    if (fwd) {  // backward messages of the checkpoint (reads fm without using it)
+    if (h->smooth_msgs) {
+      // kept by the forward
+    } else if (fwd) {  // backward messages of the checkpoint (reads fm without using it)
       p.bm = pre;
       p.fm = const_cast<float *>(msg_new);
       if (sweep_launch(false, kMessages, p, h->grid_sweep, s)) return BDD_ECUDA;

@@ -21,14 +21,17 @@ class Solver:
     ``gamma``; ``split_depth`` D >= 1 instead cuts every BDD into pieces of at most D layers.
     ``lanes``: 1 lane tiles for BDDs of width <= 2 (one lane per BDD), 0 two-lane teams, -1
     (default) the layout tuner decides (``tune_layout``; ``layout_classes`` gives the table
-    explicitly, see :meth:`layout_table`).
+    explicitly, see :meth:`layout_table`).  ``smooth_messages``: whether the smoothed forward keeps
+    every sweep's messages for the gradient (1), recomputes them there (0), or keeps them when
+    they fit (-1, default).
     """
 
     def __init__(self, inst, omega: float = 0.5, host_only: bool = False, max_device_bytes: int = 0,
                  device: int = -1, stream: int = 0, schedule: int = 1, spin_limit: int = 0,
                  alpha: float = 0.0, rank=None, averaging: int = 0, fused_pending: int = -1,
                  staging: int = -1, split: int = 0, cuts=None, gamma: float = 0.5,
-                 split_depth: int = 0, lanes: int = -1, tune_layout: int = -1, layout_classes=None):
+                 split_depth: int = 0, lanes: int = -1, tune_layout: int = -1, layout_classes=None,
+                 smooth_messages: int = -1):
         import numpy as np
         opt = B.bdd_default_options()
         if isinstance(rank, str):
@@ -58,6 +61,7 @@ class Solver:
         opt.fused_pending = int(fused_pending)
         opt.staging = int(staging)
         opt.alpha = float(alpha)
+        opt.smooth_messages = int(smooth_messages)
         opt.schedule = int(schedule)
         if spin_limit:
             opt.spin_limit = int(spin_limit)

@@ -171,6 +171,41 @@ def test_gradient_matches_oracle_gradient(lib, alpha, srmp):
                                                  want[np.argsort(-err)[:5]]])
 
 
+@pytest.mark.parametrize("name", ["tracking_5x20", "tomography_24"])
+def test_gradient_kept_messages_match_recomputed(lib, name):
+    """The backward either reads the messages the forward kept or recomputes them from the
+    multipliers' checkpoints (bdd_options.smooth_messages): the same bound and the same gradient
+    (to 1e-6 of its scale), on warp tiles (tracking) and block tiles (tomography); keeping them
+    holds (2K + 1) N more floats of device memory."""
+    import torch
+    from paper_2009_00481_gb300 import binding as B, smoothed_bound
+    inst = tracking(frames=5, dets=20, seed=0) if name == "tracking_5x20" else \
+        tomography(side=24, seed=2, unary_sigma=0.2)
+    K, alpha = 12, 0.1
+    out, grown = {}, {}
+    for keep in (0, 1):
+        s = solver(inst, alpha=alpha, smooth_messages=keep)
+        before = int(B.bdd_sizes(s.h)[8])
+        for rep in range(2):  # the second forward reuses the buffers
+            ct = torch.tensor(inst.c.astype(np.float32), device="cuda", requires_grad=True)
+            val = smoothed_bound(ct, s, K)
+            val.backward()
+            torch.cuda.synchronize()
+            out[keep, rep] = (float(val.item()), ct.grad.detach().cpu().numpy().astype(np.float64))
+        grown[keep] = int(B.bdd_sizes(s.h)[8]) - before
+        n_nodes = s.N
+        s.close()
+    extra = grown[1] - grown[0]
+    assert 4 * (2 * K + 1) * n_nodes <= extra <= 4 * (2 * K + 1) * n_nodes + 512, (grown, n_nodes)
+    (v0, g0), (v1, g1) = out[0, 0], out[1, 0]
+    assert v0 == v1
+    scale = max(1.0, np.abs(g0).max())
+    assert np.abs(g1 - g0).max() <= 1e-6 * scale, np.abs(g1 - g0).max()
+    for keep in (0, 1):
+        assert out[keep, 1][0] == out[keep, 0][0]
+        np.testing.assert_array_equal(out[keep, 1][1], out[keep, 0][1])
+
+
 @pytest.mark.parametrize("alpha", [0.1, 0.5])
 def test_gradient_matches_oracle_central_differences(lib, alpha):
     """The same gradient against FP64 central differences of the oracle's bound on 16 sampled
