@@ -341,6 +341,10 @@ struct bdd_solver {
   // choice affects time only; the solver is restarted afterwards.
   int autotune(cudaStream_t s, int reps) {
     if (n_warp_tiles == 0 || reps < 1) return BDD_OK;
+    // lane tiles stream their windows through the bulk-copy ring whatever the staging variant:
+    // when they are all the warp tiles, every variant runs the same code and there is nothing
+    // to time
+    if (lanes2 && class_tile_off[1] == class_tile_off[kWarpClasses]) return BDD_OK;
     // events around each sweep of every iteration, read after one synchronisation per variant
     std::vector<cudaEvent_t> ev(4 * (reps + 1), nullptr);
     int rc = BDD_OK;
