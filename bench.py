@@ -90,12 +90,16 @@ def graph_launches(iters: int) -> int:
     return 4 * iters + iters // 8 + iters % 8
 
 
-def algorithmic_bytes(kind: str, N: int, O: int, n: int, nb: int) -> int:
+def algorithmic_bytes(kind: str, N: int, O: int, n: int, nb: int, lane_N: int = 0, lane_O: int = 0) -> int:
+    """Bytes a kernel must move once per launch; lane_N / lane_O: nodes and occurrences of the
+    lane tiles (bdd_sizes [18] / [17]), whose arcs are one byte per occurrence."""
     if kind in ("fwd", "bwd"):
-        # per node: lo/hi 8 B, fm 4 B, bm 4 B; per occurrence: node offset 4, lambda read+write
-        # 8, share 4, slot 4, difference write 4; per BDD: depth (+ root value on the backward
-        # sweep)
-        return 16 * N + 24 * O + (4 if kind == "fwd" else 8) * nb
+        # warp teams and block tiles, per node: lo/hi 8 B, fm 4 B, bm 4 B; per occurrence: node
+        # offset 4, lambda read+write 8, share 4, slot 4, difference write 4.  Lane tiles, per
+        # node: fm 4, bm 4; per occurrence: lane code 1, lambda 8, share 4, slot 4, difference 4.
+        # Per BDD: depth (+ root value on the backward sweep)
+        tN, tO = N - lane_N, O - lane_O
+        return 16 * tN + 24 * tO + 8 * lane_N + 21 * lane_O + (4 if kind == "fwd" else 8) * nb
     if kind == "pending":
         # per variable: slot range 4 (P is stored by the bound pass only); per slot: difference
         # 4, occurrence id 4, share write 4
@@ -104,8 +108,13 @@ def algorithmic_bytes(kind: str, N: int, O: int, n: int, nb: int) -> int:
         # and P write 4 per variable, root value 4 per BDD
         return algorithmic_bytes("pending", N, O, n, nb) + 4 * n + 4 * nb
     if kind == "iteration":
-        return sum(algorithmic_bytes(k, N, O, n, nb) for k in ("fwd", "pending", "bwd", "pending_bound"))
+        return sum(algorithmic_bytes(k, N, O, n, nb, lane_N, lane_O) for k in ("fwd", "pending", "bwd", "pending_bound"))
     raise ValueError(kind)
+
+
+def solver_bytes(kind: str, s) -> int:
+    """algorithmic_bytes of a solver's layout."""
+    return algorithmic_bytes(kind, s.N, s.O, s.n, s.nb, getattr(s, "lane_N", 0), getattr(s, "lane_O", 0))
 
 
 STAGING = {0: "bulk-copy ring, 4-layer windows", 1: "8-layer cp.async windows",
@@ -373,10 +382,10 @@ def timed_steps(torch, s, inst, iters, steps, warmup, stream, trace):
 def roofline_of(s, iters, kms, peak, peak_kind, workload, label=None):
     """Roofline of the dominant per-phase kernel from the kernel-by-kernel event timings."""
     dom = int(np.argmax(kms))
-    abytes = algorithmic_bytes(KINDS[dom], s.N, s.O, s.n, s.nb)
+    abytes = solver_bytes(KINDS[dom], s)
     per_launch_ms = float(kms[dom] / iters)
     achieved = abytes / (per_launch_ms / 1e3) / 1e9
-    iter_bytes = algorithmic_bytes("iteration", s.N, s.O, s.n, s.nb)
+    iter_bytes = solver_bytes("iteration", s)
     iter_ms = float(kms.sum() / iters)
     name = sweep_kernel_name(KINDS[dom], s)
     out = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
@@ -520,7 +529,7 @@ def run_batch(args):
                    "arcs_all_ranks": arcs_all / iters, "occurrences": s.O, "variables": s.n, "omega": 0.5,
                    "device_bytes": s.device_bytes,
                    "l2": "inputs larger than L2 (no flush): "
-                         f"{algorithmic_bytes('iteration', s.N, s.O, s.n, s.nb) / 1e9:.1f} GB moved per iteration",
+                         f"{solver_bytes('iteration', s) / 1e9:.1f} GB moved per iteration",
                    "generate_s": gen_s, "build_s": build_s,
                    "parallelism": f"instances split over {world} ranks, no exchange" if world > 1 else "single"},
         "roofline": roof,
@@ -647,7 +656,7 @@ def run_forms(args, torch, stream, pool):
         trace = torch.zeros(iters, dtype=torch.float64, device="cuda")
         ms = timed_steps(torch, s, inst, iters, 3, 2, stream, trace)
         tr = trace.cpu().numpy()
-        ib = algorithmic_bytes("iteration", s.N, s.O, s.n, s.nb)
+        ib = solver_bytes("iteration", s)
         row = {"workload": CONFIG_NAMES[k] + (" (unaries N(0, 0.01))" if k == 2 else ""), "iterations": iters,
                "nodes": s.N, "ms": ms, "value": 2 * s.N * iters / (ms / 1e3), "unit": UNIT,
                "hbm_frac": ib * iters / (ms / 1e3) / 1e9 / peak,

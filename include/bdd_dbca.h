@@ -46,7 +46,7 @@ enum {
                            smoothed backward has no matching forward */
 };
 
-#define BDD_SIZES_LEN 17
+#define BDD_SIZES_LEN 19
 
 /* Options for bdd_build.  Fill with bdd_default_options, then change fields. */
 typedef struct {
@@ -269,7 +269,9 @@ int bdd_set_costs(bdd_solver *h, const float *c);
  * warp-tile staging the autotuner chose for the update sweeps: bits 0-1 forward, bits 2-3 backward
  * (0 bulk-copy ring of 4-layer windows, 1 8-layer cp.async windows, 2 the same
  * double-buffered), [13] cuts of the variable order, [14] copy-arc pairs, [15] depth limit of a
- * depth split (0: none), [16] 1 if BDDs of width <= 2 run as lane tiles (bdd_options.lanes). */
+ * depth split (0: none), [16] 1 if BDDs of width <= 2 run as lane tiles (bdd_options.lanes),
+ * [17] occurrences and [18] nodes of the lane tiles (their sweeps read one byte of arcs per
+ * occurrence instead of a node offset per occurrence and a successor pair per node). */
 int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]);
 
 /* Status a device error word maps to (no counterpart in the paper): 0 -> BDD_OK; -7 (an index

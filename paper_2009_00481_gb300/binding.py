@@ -16,7 +16,7 @@ from .build import LIB, LIB_CHECKED
 
 BDD_OK, BDD_EINVAL, BDD_EINFEASIBLE, BDD_ETOOBIG, BDD_ENOMEM = 0, -1, -2, -3, -4
 BDD_ECUDA, BDD_ETIMEOUT, BDD_EDEVICE, BDD_ESTATE = -5, -6, -7, -8
-BDD_SIZES_LEN = 17
+BDD_SIZES_LEN = 19
 BDD_LAYOUT_KEYS = 28
 
 EXPORTED = [

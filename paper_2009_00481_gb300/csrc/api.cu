@@ -82,6 +82,8 @@ struct bdd_solver {
   int *d_occ_node_off = nullptr, *d_occ_var = nullptr;
   long long *d_occ_csr = nullptr;
   int2 *d_lohi = nullptr;
+  unsigned char *d_lane_code = nullptr;  // lane tiles: arcs of a layer in one byte per occurrence
+  long long lane_O = 0, lane_N = 0;      // occurrences and nodes of the lane tiles
   float *d_fm = nullptr, *d_bm = nullptr, *d_lam = nullptr, *d_delta = nullptr;
   float *d_P = nullptr, *d_c = nullptr, *d_share_occ = nullptr;
   int *d_occ_slot = nullptr;
@@ -196,6 +198,7 @@ struct bdd_solver {
     p.occ_node_off = d_occ_node_off;
     p.occ_csr = d_occ_csr;
     p.lohi = d_lohi;
+    p.lane_code = d_lane_code;
     p.fm = d_fm;
     p.bm = d_bm;
     p.lam = d_lam;
@@ -694,7 +697,7 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c, const CutTables
   const long long ntiles = (long long)L.tile_bdd0.size();
   long long need = (O + 1) * 4 + O * 4 + O * 8 + N * 8 + 2 * N * 4 + 2 * O * 4 + 3 * (long long)n * 4 +
                    nb * 8 + 3 * ntiles * 4 + (n + 1) * 4 + O * 4 + h->grid_reduce * 8 + 1024 * 8 +
-                   (h->averaging == 1 ? O : 0) + 4LL * (long long)(L.tile_win0.size() + L.win_node.size()) + (h->fused ? 12 * n + 8LL * (h->grid_sweep + h->grid_reduce) : 0) +
+                   (h->averaging == 1 ? O : 0) + (h->lanes2 ? O + kLaneCodePad : 0) + 4LL * (long long)(L.tile_win0.size() + L.win_node.size()) + (h->fused ? 12 * n + 8LL * (h->grid_sweep + h->grid_reduce) : 0) +
                    h->npairs * 36 + 16 * h->ngroups + 8LL * (long long)ct.head_node.size();
   if (h->max_device_bytes > 0 && need > h->max_device_bytes) return BDD_ENOMEM;
 
@@ -707,6 +710,7 @@ int setup_device(bdd_solver *h, const Layout &L, const float *c, const CutTables
     RC(upload(h, &tmp, L.lohi));
     h->d_lohi = reinterpret_cast<int2 *>(tmp);
   }
+  if (h->lanes2) RC(upload(h, &h->d_lane_code, L.lane_code));
   RC(h->alloc(&h->d_fm, N));
   RC(h->alloc(&h->d_bm, N));
   RC(h->alloc(&h->d_lam, O));
@@ -1171,6 +1175,11 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   } catch (const std::bad_alloc &) {
     rc = BDD_ENOMEM;
   }
+  if (rc == BDD_OK && h->lanes2) {  // lane tiles come first: their occurrences and nodes too
+    const int nlt = L.class_tile_off[1];
+    h->lane_O = nlt < (int)L.tile_occ0.size() ? L.tile_occ0[nlt] : H.O();
+    h->lane_N = L.occ_node_off[h->lane_O];
+  }
   // smoothing: warp tiles and block tiles of at most kBlockThreads nodes per layer
   if (rc == BDD_OK && h->alpha > 0.f && L.n_block_tiles > 0 && L.max_block_width > kBlockThreads) rc = BDD_ETOOBIG;
   CutTables ct;
@@ -1549,6 +1558,8 @@ int bdd_sizes(const bdd_solver *h, long long out[BDD_SIZES_LEN]) {
   out[14] = h->npairs;
   out[15] = h->split_depth;
   out[16] = h->lanes2 ? 1 : 0;
+  out[17] = h->lane_O;
+  out[18] = h->lane_N;
   return BDD_OK;
 }
 
@@ -1631,6 +1642,7 @@ int bdd_export_canonical(const bdd_solver *h, int *bdd_row, int *bdd_depth, int 
   const long long O = h->O, N = h->N, nb = h->nb;
   hvec<int> off(O + 1), var(O), depth(nb), lohi(2 * N);
   hvec<long long> csr(O);
+  hvec<unsigned char> code(h->lanes2 ? O : 0);
   if (h->host_layout) {
     const Layout &L = h->layout;
     off = L.occ_node_off;
@@ -1638,6 +1650,7 @@ int bdd_export_canonical(const bdd_solver *h, int *bdd_row, int *bdd_depth, int 
     csr = L.occ_csr;
     depth = L.bdd_depth;
     lohi = L.lohi;
+    if (h->lanes2) std::copy(L.lane_code.begin(), L.lane_code.begin() + O, code.begin());
   } else {
     DeviceGuard dg(h->device);
     if (!dg.ok) return BDD_ECUDA;
@@ -1649,6 +1662,7 @@ int bdd_export_canonical(const bdd_solver *h, int *bdd_row, int *bdd_depth, int 
     }
     if (nb) CK(cudaMemcpy(depth.data(), h->d_bdd_depth, sizeof(int) * nb, cudaMemcpyDeviceToHost));
     if (N) CK(cudaMemcpy(lohi.data(), h->d_lohi, sizeof(int) * 2 * N, cudaMemcpyDeviceToHost));
+    if (h->lanes2 && O) CK(cudaMemcpy(code.data(), h->d_lane_code, O, cudaMemcpyDeviceToHost));
   }
   // device occurrence of (sorted BDD s, layer l), by the tile rule the kernels use
   std::vector<std::vector<int>> occ_of(nb);
@@ -1658,6 +1672,31 @@ int bdd_export_canonical(const bdd_solver *h, int *bdd_row, int *bdd_depth, int 
     for (int q = 0; q < nt; ++q) occ_of[b0 + q].assign(depth[b0 + q], -1);
     for (int l = 0; l < depth[b0]; ++l)
       for (int q = 0; q < nt && depth[b0 + q] > l; ++q) occ_of[b0 + q][l] = o++;
+  }
+  // lane tiles: the sweeps read only the lane codes there, so they must give the slabs' node
+  // offsets (the layer's nodes BDD by BDD from the tile's running node count) and arcs
+  if (h->lanes2) {
+    const int n_lane_tiles = h->class_tile_off[1];
+    for (int t = 0; t < n_lane_tiles; ++t) {
+      const int b0 = h->tile_bdd0[t], nt = h->tile_nbdd[t];
+      if (nt < 1 || nt > 32) return BDD_EDEVICE;
+      long long node = off[h->tile_occ0[t]];
+      for (int l = 0; l < depth[b0]; ++l)
+        for (int q = 0; q < nt && depth[b0 + q] > l; ++q) {
+          const int o = occ_of[b0 + q][l];
+          const unsigned c = code[o];
+          const int w = (c >> 4) == (kLaneNoNode1 >> 4) ? 1 : 2;
+          if (off[o] != node || off[o + 1] - off[o] != w) return BDD_EDEVICE;
+          const long long next0 = l + 1 < depth[b0 + q] ? off[occ_of[b0 + q][l + 1]] : 0;
+          for (int k = 0; k < w; ++k)
+            for (int a = 0; a < 2; ++a) {
+              const int g = lohi[2 * (off[o] + k) + a];
+              const unsigned want = g >= 0 ? (unsigned)(g - next0) : g == kTop ? kLaneTop : kLaneBot;
+              if (want > kLaneBot || ((c >> (4 * k + 2 * a)) & 3u) != want) return BDD_EDEVICE;
+            }
+          node += w;
+        }
+    }
   }
   std::vector<int> sorted_of_canon(nb);
   for (long long s = 0; s < nb; ++s) sorted_of_canon[h->bdd_perm[s]] = (int)s;

@@ -455,11 +455,16 @@ int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_
     tile_node0[ntiles] = v;
     if (o != O || v != N) return BDD_EINVAL;
   }
+  // lane codes (see LaneStage): both nodes' arcs of a lane-tile layer in one byte, 0 elsewhere
+  L->lane_code.resize(O + kLaneCodePad);
+  const long long n_lane_tiles = lanes2 ? L->class_tile_off[1] : 0;
+  auto lane_arc = [](int x) -> unsigned { return x >= 0 ? (unsigned)x : x == kTop ? kLaneTop : kLaneBot; };
   parallel_for(ntiles, 64, [&](long long t0, long long t1) {
     for (long long t = t0; t < t1; ++t) {
       long long dev_o = L->tile_occ0[t], dev_node = tile_node0[t];
       const int b0 = L->tile_bdd0[t], nt = L->tile_nbdd[t];
       const int dmax = L->bdd_depth[b0];  // first BDD of a tile is the deepest
+      const bool lane_tile = t < n_lane_tiles;
       for (int l = 0; l < dmax; ++l) {
         for (int q = 0; q < nt; ++q) {
           const int cb = L->bdd_perm[b0 + q];
@@ -469,6 +474,19 @@ int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_
           L->occ_node_off[dev_o] = (int)dev_node;
           L->occ_var[dev_o] = H.occ_var[co];
           L->occ_csr[dev_o] = H.occ_csr[co];
+          unsigned code = 0;
+          if (lane_tile) {  // widths <= 2, so a non-terminal successor is node 0 or 1
+            const long long cn = H.occ_node0[co];
+            code = lane_arc(H.lo[cn]) | lane_arc(H.hi[cn]) << 2;
+            if (H.occ_width[co] == 2) {
+              const unsigned c1 = lane_arc(H.lo[cn + 1]) | lane_arc(H.hi[cn + 1]) << 2;
+              if (c1 == (kLaneNoNode1 >> 4)) bad.store(BDD_EINVAL);  // a node without a path to top
+              code |= c1 << 4;
+            } else {
+              code |= kLaneNoNode1;
+            }
+          }
+          L->lane_code[dev_o] = (unsigned char)code;
           node_of_canon_occ[co] = dev_node;
           dev_node += H.occ_width[co];
           ++dev_o;
@@ -476,6 +494,8 @@ int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_
       }
     }
   });
+  if (bad.load() != BDD_OK) return bad.load();
+  for (int k = 0; k < kLaneCodePad; ++k) L->lane_code[O + k] = 0;
   L->occ_node_off[O] = (int)N;
   L->max_block_width = 0;  // widest layer of a block tile
   for (long long t = L->class_tile_off[kWarpClasses]; t < ntiles; ++t) {

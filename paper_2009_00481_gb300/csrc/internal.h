@@ -165,15 +165,24 @@ constexpr size_t kWarpSmemBytes2 = 2 * sizeof(WarpStage8);
 // (plus the layer after it for the backward messages of a forward update); two per warp, filled
 // by the bulk-copy ring.  A warp takes a run of up to kLaneRunMax consecutive lane tiles and
 // streams their windows through its two buffers.
+//
+// The arcs of a lane tile's layer are one byte per occurrence (lane code) instead of node
+// offsets and an int2 per node: bits 4t..4t+1 hold the 0-arc and bits 4t+2..4t+3 the 1-arc of
+// node t (t = 0, 1), each as 0 or 1 (that node of the BDD's next layer), kLaneTop or kLaneBot.  A layer with one node has node 1's arcs both kLaneBot, which no
+// node of a reduced BDD has (every node has a path to the true terminal).  A layer's nodes follow
+// the tile's layer-major order (BDD by BDD, the BDDs alive at the layer being a prefix of the
+// tile), so the kernels find a lane's first node from the widths of the lanes before it.
 constexpr int kLaneRunMax = 4;  // lane tiles per warp (longer runs measured no faster)
 constexpr int kLaneWinNodes = 64 * kWinLayers;
+constexpr unsigned kLaneTop = 2, kLaneBot = 3;
+constexpr unsigned kLaneNoNode1 = 0xF0u;  // node 1's arcs of a one-node layer: both kLaneBot
+constexpr int kLaneCodePad = 64;          // spare codes after the last occurrence (read, unused)
 struct alignas(16) LaneStage {
-  int2 lohi[kLaneWinNodes + 2];
   float msg[kLaneWinNodes + 64 + 4];
-  int off[kWinOcc + 8];
   float lam[kWinOcc + 4];
   float shr[kWinOcc + 4];
   int slot[kWinOcc + 4];
+  unsigned char code[kWinOcc + 32 + 16];  // the window's occurrences and the layer after it
 };
 constexpr size_t kLaneSmemBytes = kWarpStages * sizeof(LaneStage);
 constexpr int kStagings = 3;  // warp-tile staging variants of the update sweeps
@@ -193,6 +202,7 @@ struct Layout {
   hvec<long long> occ_csr;      // [O]
   hvec<int> occ_slot;           // [O] slot of the occurrence
   hvec<int> lohi;               // [2N] interleaved lo, hi
+  hvec<unsigned char> lane_code;  // [O + kLaneCodePad] arcs of lane-tile layers (0 elsewhere)
   hvec<int> tile_occ0, tile_bdd0, tile_nbdd;  // per tile
   hvec<int> tile_win0;                        // [ntiles + 1] window table offsets (warp tiles)
   hvec<int> win_node;                         // window table, int pairs
@@ -257,6 +267,7 @@ struct SweepParams {
   const int *occ_node_off;
   const long long *occ_csr;
   const int2 *lohi;
+  const unsigned char *lane_code;  // lane tiles: one byte of arcs per occurrence (see LaneStage)
   float *fm;
   float *bm;
   float *lam;

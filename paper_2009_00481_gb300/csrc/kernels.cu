@@ -764,25 +764,70 @@ __device__ __forceinline__ void warp_backward(const SweepParams &p, const Phase 
 // of a warp tile of 32 one-lane teams).  A lane keeps both nodes of its BDD's current layer in
 // registers, so the forward push, the min-marginals and the backward pull need no shuffles and
 // no team reductions; windows of kWinLayers layers (up to 64 nodes each) are staged by the
-// bulk-copy ring as for warp tiles.  The arithmetic is that of a two-lane team, operation for
-// operation and in the same order, so the results equal the team layout's bit for bit.
+// bulk-copy ring as for warp tiles.  A layer's arcs come from its lane code (one byte per
+// occurrence, see LaneStage) instead of node offsets and a pair of node indices per node: the
+// lane's first node is the layer's first node plus the nodes of the lanes before it (a ballot of
+// the two-node layers), its successors are node 0 or 1 of its next layer or a terminal.  The
+// arithmetic is that of a two-lane team, operation for operation and in the same order, so the
+// results equal the team layout's bit for bit.
 // ---------------------------------------------------------------------------------------
 using LaneRing = StageRingT<LaneStage>;
 
+// the arc a of node t in a lane code (a = 0: 0-arc, 1: 1-arc): 0 or 1, kLaneTop or kLaneBot
+__device__ __forceinline__ unsigned lane_arc(unsigned code, int t, int a) { return (code >> (4 * t + 2 * a)) & 3u; }
+__device__ __forceinline__ bool lane_two_nodes(unsigned code) { return (code >> 4) != (kLaneNoNode1 >> 4); }
+
 // forward message of node t of a layer (Alg. 2) from the two nodes of the previous layer
-// (messages pf0, pf1; arcs r0, r1 as ids relative to this layer's first node, kNone for none;
-// 1-arc cost plam), relaxed in the order of the team path: node 0 before node 1, 0-arc first
-__device__ __forceinline__ float lane_push(int t, float pf0, int2 r0, float pf1, int2 r1, float plam) {
+// (messages pf0, pf1; their arcs in the lane code pc; 1-arc cost plam), relaxed in the order of
+// the team path: node 0 before node 1, 0-arc first
+__device__ __forceinline__ float lane_push(unsigned t, float pf0, float pf1, unsigned pc, float plam) {
   float f = inf();
-  if (r0.x == t) f = fminf(f, pf0);
-  if (r0.y == t) f = fminf(f, pf0 + plam);
-  if (r1.x == t) f = fminf(f, pf1);
-  if (r1.y == t) f = fminf(f, pf1 + plam);
+  if (lane_arc(pc, 0, 0) == t) f = fminf(f, pf0);
+  if (lane_arc(pc, 0, 1) == t) f = fminf(f, pf0 + plam);
+  if (lane_arc(pc, 1, 0) == t) f = fminf(f, pf1);
+  if (lane_arc(pc, 1, 1) == t) f = fminf(f, pf1 + plam);
   return f;
 }
 
-__device__ __forceinline__ int2 rel_arcs(int2 lh, int node0) {
-  return make_int2(lh.x >= 0 ? lh.x - node0 : kNone, lh.y >= 0 ? lh.y - node0 : kNone);
+// The five ranges of a lane-tile window: the lane codes of its occurrences and of the layer after
+// it (static; the code array carries kLaneCodePad spare entries), slots (static), multipliers,
+// shares and messages (dynamic, as for warp tiles)
+struct LaneRanges {
+  Range code, slot, lam, shr, msg;
+};
+template <bool FWD, int MODE>
+__device__ __forceinline__ LaneRanges lane_ranges_of(const SweepParams &p, int occ0, const Window &W) {
+  const long long oa = occ0 + W.ca;
+  const int nob = W.cb - W.ca;
+  LaneRanges r;
+  r.code = range_of<1>(p.lane_code, oa, nob + 32);
+  r.slot = range_of<4>(p.occ_slot, oa, is_update(MODE) ? nob : 0);
+  r.lam = range_of<4>(p.lam, oa, nob);
+  r.shr = range_of<4>(p.share_occ, oa, MODE != kMessages ? nob : 0);
+  if (FWD)
+    r.msg = range_of<4>(p.bm, W.na, is_update(MODE) ? W.nc - W.na : 0);
+  else
+    r.msg = range_of<4>(p.fm, W.na, W.nb - W.na);
+  return r;
+}
+
+// stage_window for a lane-tile window
+__device__ __forceinline__ void stage_lane_window(const LaneRanges &r, LaneRing &ring, int b, bool expect, bool stat,
+                                                  bool dyn) {
+  if (expect) ring.busy |= 1u << b;
+  if ((threadIdx.x & 31) != 0) return;
+  LaneStage &S = ring.S[b];
+  unsigned long long *bar = &ring.bar[b];
+  if (expect) bar_expect(bar, r.code.bytes + r.slot.bytes + r.lam.bytes + r.shr.bytes + r.msg.bytes);
+  if (stat) {
+    if (r.code.bytes) bulk_copy(S.code, r.code.a0, r.code.bytes, bar);
+    if (r.slot.bytes) bulk_copy(S.slot, r.slot.a0, r.slot.bytes, bar);
+  }
+  if (dyn) {
+    if (r.lam.bytes) bulk_copy(S.lam, r.lam.a0, r.lam.bytes, bar);
+    if (r.shr.bytes) bulk_copy(S.shr, r.shr.a0, r.shr.bytes, bar);
+    if (r.msg.bytes) bulk_copy(S.msg, r.msg.a0, r.msg.bytes, bar);
+  }
 }
 
 // A lane run: consecutive lane tiles [t0, t1) of one warp (at most kLaneRunMax), streamed through the
@@ -895,51 +940,55 @@ __device__ __forceinline__ LaneJob lane_job(const SweepParams &p, const LaneCurs
 // and 1-arc cost
 struct LaneFwd {
   float pf0, pf1, plam;
-  int2 plh0, plh1;
+  unsigned pcode;  // the previous layer's lane code (no arcs for a lane without that layer)
 };
 
 template <int MODE>
 __device__ __forceinline__ void lane_forward_window(const SweepParams &p, const Phase &ph, const LaneJob &j,
                                                     const LaneStage &S, LaneFwd &st) {
   const int lane = threadIdx.x & 31;
+  const unsigned before = (1u << lane) - 1u;  // the lanes before this one
   const Window &W = j.W;
-  const WindowRanges r = ranges_of<true, MODE>(p, j.occ0, W);
-  const int *off = S.off + r.off.shift;
-  const int2 *lohi = S.lohi + r.lohi.shift;
+  const LaneRanges r = lane_ranges_of<true, MODE>(p, j.occ0, W);
+  const unsigned char *code = S.code + r.code.shift;
   const int *slot = S.slot + r.slot.shift;
   const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
   const int ca = W.ca, na = W.na, oa = j.occ0 + ca;
+  [[maybe_unused]] const int ncode = W.cb - W.ca + 32;  // staged codes: the window's occurrences and the next layer's
+  int first = na;                      // the layer's first node (the window's first, then onwards)
   for (int l = W.l0; l < W.l1; ++l) {
     const bool active = j.depth > l;
     const int oi = occ_before(j.depth, l) - ca + lane;
-    int node0 = 0, wl = 0;
-    if (active) {
-      node0 = off[BDD_IN(p, oi, W.cb - W.ca)];
-      wl = off[BDD_IN(p, oi + 1, W.cb - W.ca + 1)] - node0;
-    }
+    const unsigned c = active ? code[BDD_IN(p, oi, ncode)] : 0xFFu;
+    const bool two = active && lane_two_nodes(c);
+    const int wl = active ? (two ? 2 : 1) : 0;
+    const unsigned twos = __ballot_sync(kFull, two);
+    const int node0 = first + lane + __popc(twos & before);  // the alive lanes are a prefix
+    const int layer_nodes = __popc(__ballot_sync(kFull, active)) + __popc(twos);
     // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv, for both nodes
     float f0 = 0.f, f1 = 0.f;  // the root (layer 0)
     if (l > 0) {
-      const int2 r0 = rel_arcs(st.plh0, node0), r1 = rel_arcs(st.plh1, node0);
-      f0 = lane_push(0, st.pf0, r0, st.pf1, r1, st.plam);
-      f1 = lane_push(1, st.pf0, r0, st.pf1, r1, st.plam);
+      f0 = lane_push(0u, st.pf0, st.pf1, st.pcode, st.plam);
+      f1 = lane_push(1u, st.pf0, st.pf1, st.pcode, st.plam);
     }
-    int2 lh0 = make_int2(kNone, kNone), lh1 = make_int2(kNone, kNone);
-    if (wl > 0) {
-      p.fm[BDD_NODE(p, node0)] = f0;
-      lh0 = lohi[BDD_IN(p, node0 - na, W.nb - W.na)];
-    }
-    if (wl > 1) {
-      p.fm[BDD_NODE(p, node0 + 1)] = f1;
-      lh1 = lohi[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
-    }
+    if (wl > 0) p.fm[BDD_NODE(p, node0)] = f0;
+    if (wl > 1) p.fm[BDD_NODE(p, node0 + 1)] = f1;
     float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
     if (is_update(MODE)) {
+      // the first node of this BDD's next layer, from that layer's codes (staged with the window)
+      const bool active_n = j.depth > l + 1;
+      const int oin = occ_before(j.depth, l + 1) - ca + lane;
+      const unsigned cn = active_n ? code[BDD_IN(p, oin, ncode)] : 0xFFu;
+      const unsigned twos_n = __ballot_sync(kFull, active_n && lane_two_nodes(cn));
+      const int next0 = first + layer_nodes + lane + __popc(twos_n & before) - na;  // in the staged messages
+      auto bm_of = [&](unsigned a) {
+        return a < 2u ? msg[BDD_IN(p, next0 + (int)a, W.nc - na)] : a == kLaneTop ? 0.f : inf();
+      };
       // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
-      const float a00 = wl > 0 ? f0 + staged_bm<false>(msg, p.copy_val, na, lh0.x) : inf();
-      const float a01 = wl > 1 ? f1 + staged_bm<false>(msg, p.copy_val, na, lh1.x) : inf();
-      const float a10 = wl > 0 ? f0 + lam + staged_bm<false>(msg, p.copy_val, na, lh0.y) : inf();
-      const float a11 = wl > 1 ? f1 + lam + staged_bm<false>(msg, p.copy_val, na, lh1.y) : inf();
+      const float a00 = wl > 0 ? f0 + bm_of(lane_arc(c, 0, 0)) : inf();
+      const float a01 = wl > 1 ? f1 + bm_of(lane_arc(c, 1, 0)) : inf();
+      const float a10 = wl > 0 ? f0 + lam + bm_of(lane_arc(c, 0, 1)) : inf();
+      const float a11 = wl > 1 ? f1 + lam + bm_of(lane_arc(c, 1, 1)) : inf();
       const float m0 = fminf(a00, a01), m1 = fminf(a10, a11);
       const float dd = p.omega * mm_difference(m0, m1);
       lam -= dd;
@@ -950,49 +999,43 @@ __device__ __forceinline__ void lane_forward_window(const SweepParams &p, const 
     }
     st.pf0 = f0;
     st.pf1 = f1;
-    st.plh0 = lh0;
-    st.plh1 = lh1;
+    st.pcode = c;  // 0xFF (all arcs to the false terminal) for a lane without this layer
     st.plam = lam;
+    first += layer_nodes;
   }
 }
 
 template <int MODE>
 __device__ __forceinline__ void lane_backward_window(const SweepParams &p, const Phase &ph, const LaneJob &j,
-                                                     const LaneStage &S, float &bn0, float &bn1, int &node0_next,
-                                                     double &bacc) {
+                                                     const LaneStage &S, float &bn0, float &bn1, double &bacc) {
   const int lane = threadIdx.x & 31;
+  const unsigned before = (1u << lane) - 1u;
   const Window &W = j.W;
-  const WindowRanges r = ranges_of<false, MODE>(p, j.occ0, W);
-  const int *off = S.off + r.off.shift;
-  const int2 *lohi = S.lohi + r.lohi.shift;
+  const LaneRanges r = lane_ranges_of<false, MODE>(p, j.occ0, W);
+  const unsigned char *code = S.code + r.code.shift;
   const int *slot = S.slot + r.slot.shift;
   const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
   const int ca = W.ca, na = W.na, oa = j.occ0 + ca;
+  [[maybe_unused]] const int ncode = W.cb - W.ca + 32;
+  int end = W.nb;  // one past the layer's last node (the window's end, then downwards)
   for (int l = W.l1 - 1; l >= W.l0; --l) {
     const bool active = j.depth > l;
     const int oi = occ_before(j.depth, l) - ca + lane;
-    int node0 = 0, wl = 0;
-    if (active) {
-      node0 = off[BDD_IN(p, oi, W.cb - W.ca)];
-      wl = off[BDD_IN(p, oi + 1, W.cb - W.ca + 1)] - node0;
-    }
-    int2 lh0 = make_int2(kNone, kNone), lh1 = make_int2(kNone, kNone);
+    const unsigned c = active ? code[BDD_IN(p, oi, ncode)] : 0xFFu;
+    const bool two = active && lane_two_nodes(c);
+    const int wl = active ? (two ? 2 : 1) : 0;
+    const unsigned twos = __ballot_sync(kFull, two);
+    end -= __popc(__ballot_sync(kFull, active)) + __popc(twos);  // now the layer's first node
+    const int node0 = end + lane + __popc(twos & before);
     float f0 = inf(), f1 = inf();
-    if (wl > 0) {
-      lh0 = lohi[BDD_IN(p, node0 - na, W.nb - W.na)];
-      f0 = msg[BDD_IN(p, node0 - na, W.nb - W.na)];
-    }
-    if (wl > 1) {
-      lh1 = lohi[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
-      f1 = msg[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
-    }
+    if (wl > 0) f0 = msg[BDD_IN(p, node0 - na, W.nb - W.na)];
+    if (wl > 1) f1 = msg[BDD_IN(p, node0 - na + 1, W.nb - W.na)];
     float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
     // successors' backward messages: the next layer's nodes, held by this lane (a BDD's last
     // layer has terminal arcs only, so nothing is read from the previous BDD of the lane)
-    auto pull = [&](int t) {
-      return t >= 0 ? (((t - node0_next) & 1) == 0 ? bn0 : bn1) : terminal_bm<false>(p.copy_val, t);
-    };
-    const float b00 = pull(lh0.x), b01 = pull(lh0.y), b10 = pull(lh1.x), b11 = pull(lh1.y);
+    auto pull = [&](unsigned a) { return a == 0u ? bn0 : a == 1u ? bn1 : a == kLaneTop ? 0.f : inf(); };
+    const float b00 = pull(lane_arc(c, 0, 0)), b01 = pull(lane_arc(c, 0, 1));
+    const float b10 = pull(lane_arc(c, 1, 0)), b11 = pull(lane_arc(c, 1, 1));
     if (MODE != kMessages) {
       const float m0 = fminf(f0 + b00, f1 + b10), m1 = fminf(f0 + lam + b01, f1 + lam + b11);
       if (is_update(MODE)) {
@@ -1003,9 +1046,9 @@ __device__ __forceinline__ void lane_backward_window(const SweepParams &p, const
           ph.delta[BDD_OCC(p, slot[oi])] = dd;
         }
       } else if (active && p.out_m0) {
-        const long long c = p.occ_csr[oa + oi];
-        p.out_m0[BDD_CSR(p, c)] = m0;
-        p.out_m1[BDD_CSR(p, c)] = m1;
+        const long long csr = p.occ_csr[oa + oi];
+        p.out_m0[BDD_CSR(p, csr)] = m0;
+        p.out_m1[BDD_CSR(p, csr)] = m1;
       }
     }
     // Alg. 3: m_bwd(v) = min(m_bwd(v0) + 0, m_bwd(v1) + lambda)
@@ -1018,7 +1061,6 @@ __device__ __forceinline__ void lane_backward_window(const SweepParams &p, const
     }
     bn0 = bc0;
     bn1 = bc1;
-    node0_next = node0;
   }
 }
 
@@ -1034,35 +1076,34 @@ __device__ __forceinline__ void lane_run(const SweepParams &p, const Phase &ph, 
   if (c.tile >= t1) return;
   LaneJob cur = lane_job(p, c);
   {
-    const WindowRanges r = ranges_of<FWD, MODE>(p, cur.occ0, cur.W);
-    stage_window(r, ring, 0, true, true, false);
+    const LaneRanges r = lane_ranges_of<FWD, MODE>(p, cur.occ0, cur.W);
+    stage_lane_window(r, ring, 0, true, true, false);
     pdl_wait();
-    stage_window(r, ring, 0, false, false, true);
+    stage_lane_window(r, ring, 0, false, false, true);
   }
   lane_step<FWD>(p, s, t0, t1, c);
   bool have_next = c.tile < t1;
   LaneJob next = cur;
   if (have_next) {
     next = lane_job(p, c);
-    stage_window(ranges_of<FWD, MODE>(p, next.occ0, next.W), ring, 1, true, true, true);
+    stage_lane_window(lane_ranges_of<FWD, MODE>(p, next.occ0, next.W), ring, 1, true, true, true);
     lane_step<FWD>(p, s, t0, t1, c);
   }
-  LaneFwd st{0.f, 0.f, 0.f, make_int2(kNone, kNone), make_int2(kNone, kNone)};
+  LaneFwd st{0.f, 0.f, 0.f, 0xFFu};
   float bn0 = inf(), bn1 = inf();  // backward messages of the next layer's two nodes
-  int node0_next = 0;
   for (int k = 0;; ++k) {
     const int b = k & 1;
     if (!ring_wait(p, ring, b)) return;
     if (FWD)
       lane_forward_window<MODE>(p, ph, cur, ring.S[b], st);
     else
-      lane_backward_window<MODE>(p, ph, cur, ring.S[b], bn0, bn1, node0_next, bacc);
+      lane_backward_window<MODE>(p, ph, cur, ring.S[b], bn0, bn1, bacc);
     __syncwarp();  // this buffer is free: stage the window after next into it
     const bool have_after = c.tile < t1;
     LaneJob after = next;
     if (have_after) {
       after = lane_job(p, c);
-      stage_window(ranges_of<FWD, MODE>(p, after.occ0, after.W), ring, b, true, true, true);
+      stage_lane_window(lane_ranges_of<FWD, MODE>(p, after.occ0, after.W), ring, b, true, true, true);
       lane_step<FWD>(p, s, t0, t1, c);
     }
     if (!have_next) break;

@@ -75,7 +75,7 @@ class Solver:
         s = B.bdd_sizes(self.h)
         (self.n, self.m, self.nb, self.O, self.N, self.max_depth, self.max_width, self.nnz,
          self.device_bytes, self.warp_tiles, self.block_tiles, self.schedule, self.staging,
-         self.n_cuts, self.npairs, self.split_depth, self.lanes) = map(int, s)
+         self.n_cuts, self.npairs, self.split_depth, self.lanes, self.lane_O, self.lane_N) = map(int, s)
 
     def close(self):
         if getattr(self, "h", None):

@@ -67,6 +67,10 @@ def test_bench_bookkeeping():
     # the sum of the per-kernel figures: two sweeps (16 N + 24 O + 4 / 8 nb), two pending passes
     # (4 n + 12 O; the bound one also stores P, + 4 n, and reads the root values, + 4 nb)
     assert bench.algorithmic_bytes("iteration", N, O, n, nb) == 32 * N + 72 * O + 12 * n + 16 * nb
+    # lane tiles: one byte of arcs per occurrence, no node offsets or successor pairs
+    assert bench.algorithmic_bytes("fwd", N, O, n, nb, N, O) == 8 * N + 21 * O + 4 * nb
+    assert bench.algorithmic_bytes("iteration", N, O, n, nb, N // 2, O // 3) == \
+        32 * N + 72 * O + 12 * n + 16 * nb - 2 * (8 * (N // 2) + 3 * (O // 3))
 
 
 def test_partition_covers_batch_once_and_balances():
