@@ -795,21 +795,40 @@ __device__ __forceinline__ float lane_push(unsigned t, float pf0, float pf1, uns
 struct LaneRanges {
   Range code, slot, lam, shr, msg;
 };
-template <bool FWD, int MODE>
-__device__ __forceinline__ LaneRanges lane_ranges_of(const SweepParams &p, int occ0, const Window &W) {
-  const long long oa = occ0 + W.ca;
-  const int nob = W.cb - W.ca;
-  LaneRanges r;
-  r.code = range_of<1>(p.lane_code, oa, nob + 32);
-  r.slot = range_of<4>(p.occ_slot, oa, is_update(MODE) ? nob : 0);
-  r.lam = range_of<4>(p.lam, oa, nob);
-  r.shr = range_of<4>(p.share_occ, oa, MODE != kMessages ? nob : 0);
-  if (FWD)
-    r.msg = range_of<4>(p.bm, W.na, is_update(MODE) ? W.nc - W.na : 0);
-  else
-    r.msg = range_of<4>(p.fm, W.na, W.nb - W.na);
+// A range of E-byte elements [first, first + n) of an array whose start is 16-byte aligned (every
+// device array comes from cudaMalloc), widened to whole 16-byte blocks: the block boundaries
+// follow from the element indices alone, in 32-bit arithmetic, and the first element lands
+// first mod (16 / E) elements into the destination.
+template <int E>
+__device__ __forceinline__ Range aligned_range(const void *base, unsigned first, unsigned n) {
+  constexpr unsigned B = 16 / E;  // elements per 16-byte block
+  const unsigned lo = first & ~(B - 1), hi = (first + n + B - 1) & ~(B - 1);
+  Range r;
+  r.a0 = static_cast<const char *>(base) + (size_t)lo * E;
+  r.bytes = n > 0 ? (hi - lo) * E : 0u;
+  r.shift = (int)(first - lo);
   return r;
 }
+template <bool FWD, int MODE>
+__device__ __forceinline__ LaneRanges lane_ranges_of(const SweepParams &p, int occ0, const Window &W) {
+  const unsigned oa = (unsigned)(occ0 + W.ca), nob = (unsigned)(W.cb - W.ca);
+  LaneRanges r;
+  r.code = aligned_range<1>(p.lane_code, oa, nob + 32);
+  r.slot = aligned_range<4>(p.occ_slot, oa, is_update(MODE) ? nob : 0u);
+  r.lam = aligned_range<4>(p.lam, oa, nob);
+  r.shr = aligned_range<4>(p.share_occ, oa, MODE != kMessages ? nob : 0u);
+  if (FWD)
+    r.msg = aligned_range<4>(p.bm, (unsigned)W.na, is_update(MODE) ? (unsigned)(W.nc - W.na) : 0u);
+  else
+    r.msg = aligned_range<4>(p.fm, (unsigned)W.na, (unsigned)(W.nb - W.na));
+  return r;
+}
+// where a lane-tile window's first occurrence, code and message sit in its stage (the shifts of
+// lane_ranges_of, without the ranges)
+struct LaneShifts {
+  int occ, code, msg;
+};
+__device__ __forceinline__ LaneShifts lane_shifts(int oa, int na) { return {oa & 3, oa & 15, na & 3}; }
 
 // stage_window for a lane-tile window
 __device__ __forceinline__ void stage_lane_window(const LaneRanges &r, LaneRing &ring, int b, bool expect, bool stat,
@@ -949,22 +968,32 @@ __device__ __forceinline__ void lane_forward_window(const SweepParams &p, const 
   const int lane = threadIdx.x & 31;
   const unsigned before = (1u << lane) - 1u;  // the lanes before this one
   const Window &W = j.W;
-  const LaneRanges r = lane_ranges_of<true, MODE>(p, j.occ0, W);
-  const unsigned char *code = S.code + r.code.shift;
-  const int *slot = S.slot + r.slot.shift;
-  const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
+  const LaneShifts sh = lane_shifts(j.occ0 + W.ca, W.na);
+  const unsigned char *code = S.code + sh.code;
+  const int *slot = S.slot + sh.occ;
+  const float *lamw = S.lam + sh.occ, *shr = S.shr + sh.occ, *msg = S.msg + sh.msg;
   const int ca = W.ca, na = W.na, oa = j.occ0 + ca;
   [[maybe_unused]] const int ncode = W.cb - W.ca + 32;  // staged codes: the window's occurrences and the next layer's
   int first = na;                      // the layer's first node (the window's first, then onwards)
+  // layer l's occurrences before it in the tile (ob), this lane's code and the two-node lanes;
+  // each layer's are taken from the step before, which decodes the layer after it
+  int ob = ca;
+  unsigned c = j.depth > W.l0 ? code[BDD_IN(p, lane, ncode)] : 0xFFu;
+  unsigned twos = __ballot_sync(kFull, j.depth > W.l0 && lane_two_nodes(c));
   for (int l = W.l0; l < W.l1; ++l) {
     const bool active = j.depth > l;
-    const int oi = occ_before(j.depth, l) - ca + lane;
-    const unsigned c = active ? code[BDD_IN(p, oi, ncode)] : 0xFFu;
+    const int oi = ob - ca + lane;
     const bool two = active && lane_two_nodes(c);
     const int wl = active ? (two ? 2 : 1) : 0;
-    const unsigned twos = __ballot_sync(kFull, two);
     const int node0 = first + lane + __popc(twos & before);  // the alive lanes are a prefix
-    const int layer_nodes = __popc(__ballot_sync(kFull, active)) + __popc(twos);
+    const int ob_n = occ_before(j.depth, l + 1);
+    const int layer_nodes = (ob_n - ob) + __popc(twos);  // alive lanes + their second nodes
+    // the next layer's codes (staged with the window)
+    const bool active_n = j.depth > l + 1;
+    const int oin = ob_n - ca + lane;
+    const unsigned cn = active_n ? code[BDD_IN(p, oin, ncode)] : 0xFFu;
+    const bool two_n = active_n && lane_two_nodes(cn);
+    const unsigned twos_n = __ballot_sync(kFull, two_n);
     // Alg. 2: m_fwd(v) = min over in-arcs (u, v) of m_fwd(u) + theta_uv, for both nodes
     float f0 = 0.f, f1 = 0.f;  // the root (layer 0)
     if (l > 0) {
@@ -975,15 +1004,12 @@ __device__ __forceinline__ void lane_forward_window(const SweepParams &p, const 
     if (wl > 1) p.fm[BDD_NODE(p, node0 + 1)] = f1;
     float lam = active ? lamw[oi] + (MODE != kMessages ? shr[oi] : 0.f) : 0.f;
     if (is_update(MODE)) {
-      // the first node of this BDD's next layer, from that layer's codes (staged with the window)
-      const bool active_n = j.depth > l + 1;
-      const int oin = occ_before(j.depth, l + 1) - ca + lane;
-      const unsigned cn = active_n ? code[BDD_IN(p, oin, ncode)] : 0xFFu;
-      const unsigned twos_n = __ballot_sync(kFull, active_n && lane_two_nodes(cn));
-      const int next0 = first + layer_nodes + lane + __popc(twos_n & before) - na;  // in the staged messages
-      auto bm_of = [&](unsigned a) {
-        return a < 2u ? msg[BDD_IN(p, next0 + (int)a, W.nc - na)] : a == kLaneTop ? 0.f : inf();
-      };
+      // the backward messages of this BDD's next layer (staged with the window): node 0 if the
+      // BDD has that layer, node 1 if the layer has two nodes -- the only nodes its arcs reach
+      const int next0 = first + layer_nodes + lane + __popc(twos_n & before) - na;
+      const float bn0 = active_n ? msg[BDD_IN(p, next0, W.nc - na)] : inf();
+      const float bn1 = two_n ? msg[BDD_IN(p, next0 + 1, W.nc - na)] : inf();
+      auto bm_of = [&](unsigned a) { return a == 0u ? bn0 : a == 1u ? bn1 : a == kLaneTop ? 0.f : inf(); };
       // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
       const float a00 = wl > 0 ? f0 + bm_of(lane_arc(c, 0, 0)) : inf();
       const float a01 = wl > 1 ? f1 + bm_of(lane_arc(c, 1, 0)) : inf();
@@ -1002,6 +1028,9 @@ __device__ __forceinline__ void lane_forward_window(const SweepParams &p, const 
     st.pcode = c;  // 0xFF (all arcs to the false terminal) for a lane without this layer
     st.plam = lam;
     first += layer_nodes;
+    ob = ob_n;
+    c = cn;
+    twos = twos_n;
   }
 }
 
@@ -1011,21 +1040,24 @@ __device__ __forceinline__ void lane_backward_window(const SweepParams &p, const
   const int lane = threadIdx.x & 31;
   const unsigned before = (1u << lane) - 1u;
   const Window &W = j.W;
-  const LaneRanges r = lane_ranges_of<false, MODE>(p, j.occ0, W);
-  const unsigned char *code = S.code + r.code.shift;
-  const int *slot = S.slot + r.slot.shift;
-  const float *lamw = S.lam + r.lam.shift, *shr = S.shr + r.shr.shift, *msg = S.msg + r.msg.shift;
+  const LaneShifts sh = lane_shifts(j.occ0 + W.ca, W.na);
+  const unsigned char *code = S.code + sh.code;
+  const int *slot = S.slot + sh.occ;
+  const float *lamw = S.lam + sh.occ, *shr = S.shr + sh.occ, *msg = S.msg + sh.msg;
   const int ca = W.ca, na = W.na, oa = j.occ0 + ca;
   [[maybe_unused]] const int ncode = W.cb - W.ca + 32;
   int end = W.nb;  // one past the layer's last node (the window's end, then downwards)
+  int ob_n = W.cb;  // occurrences of the tile before layer l + 1
   for (int l = W.l1 - 1; l >= W.l0; --l) {
     const bool active = j.depth > l;
-    const int oi = occ_before(j.depth, l) - ca + lane;
+    const int ob = occ_before(j.depth, l);
+    const int oi = ob - ca + lane;
     const unsigned c = active ? code[BDD_IN(p, oi, ncode)] : 0xFFu;
     const bool two = active && lane_two_nodes(c);
     const int wl = active ? (two ? 2 : 1) : 0;
     const unsigned twos = __ballot_sync(kFull, two);
-    end -= __popc(__ballot_sync(kFull, active)) + __popc(twos);  // now the layer's first node
+    end -= (ob_n - ob) + __popc(twos);  // alive lanes + their second nodes: now the layer's first node
+    ob_n = ob;
     const int node0 = end + lane + __popc(twos & before);
     float f0 = inf(), f1 = inf();
     if (wl > 0) f0 = msg[BDD_IN(p, node0 - na, W.nb - W.na)];
@@ -2318,6 +2350,13 @@ size_t sweep_smem_bytes(int block_buf, int block_depth_buf, int staging, bool la
   return warp_part > group_part ? warp_part : group_part;
 }
 
+// the same for a layout whose warp tiles are all lane tiles (min-sum sweeps)
+size_t lane_only_smem_bytes(int block_buf, int block_depth_buf) {
+  const size_t warp_part = kWarpsPerBlock * kLaneSmemBytes;
+  const size_t group_part = group_floats(block_buf, block_depth_buf, false) * sizeof(float);
+  return warp_part > group_part ? warp_part : group_part;
+}
+
 size_t persist_smem_bytes(int block_buf, int block_depth_buf) {
   const size_t warp_part = kPersistWarps * kWarpSmemBytes;
   const size_t group_part = kSubBlocks * group_floats(block_buf, block_depth_buf) * sizeof(float);
@@ -2329,8 +2368,16 @@ int sweep_launch(bool forward, int mode, const SweepParams &p_in, int grid, cuda
   if (mode != kUpdate) staging = 0;
   SweepParams p = p_in;
   if (p.lanes2 && (p.alpha > 0.f || p.split || mode == kUpdateFused)) return -5;  // lane tiles: plain min-sum
-  p.warp_smem = (int)sweep_warp_smem(staging, p.lanes2 != 0);
-  const size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf, staging, p.lanes2 != 0, p.alpha > 0.f);
+  if (p.lanes2 && (reinterpret_cast<uintptr_t>(p.lane_code) | reinterpret_cast<uintptr_t>(p.occ_slot) |
+                   reinterpret_cast<uintptr_t>(p.lam) | reinterpret_cast<uintptr_t>(p.share_occ) |
+                   reinterpret_cast<uintptr_t>(p.fm) | reinterpret_cast<uintptr_t>(p.bm)) & 15u)
+    return -5;  // lane-tile windows find their staged elements from 16-byte aligned array starts
+  // a layout whose warp tiles are all lane tiles needs only the lane ring's shared memory, so
+  // more blocks fit on an SM
+  const bool lane_only = p.lanes2 && p.class_tile_off[1] == p.class_tile_off[kWarpClasses];
+  p.warp_smem = lane_only ? (int)kLaneSmemBytes : (int)sweep_warp_smem(staging, p.lanes2 != 0);
+  size_t smem = sweep_smem_bytes(p.block_buf, p.block_depth_buf, staging, p.lanes2 != 0, p.alpha > 0.f);
+  if (lane_only) smem = lane_only_smem_bytes(p.block_buf, p.block_depth_buf);
   int rc = 0;
   if (p.split) {  // sub-BDDs: min-sum only, no fused pending pass
     if (p.alpha > 0.f || mode == kUpdateFused) return -5;
