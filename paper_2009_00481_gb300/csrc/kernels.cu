@@ -1010,11 +1010,13 @@ __device__ __forceinline__ void lane_forward_window(const SweepParams &p, const 
       const float bn0 = active_n ? msg[BDD_IN(p, next0, W.nc - na)] : inf();
       const float bn1 = two_n ? msg[BDD_IN(p, next0 + 1, W.nc - na)] : inf();
       auto bm_of = [&](unsigned a) { return a == 0u ? bn0 : a == 1u ? bn1 : a == kLaneTop ? 0.f : inf(); };
-      // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step
-      const float a00 = wl > 0 ? f0 + bm_of(lane_arc(c, 0, 0)) : inf();
-      const float a01 = wl > 1 ? f1 + bm_of(lane_arc(c, 1, 0)) : inf();
-      const float a10 = wl > 0 ? f0 + lam + bm_of(lane_arc(c, 0, 1)) : inf();
-      const float a11 = wl > 1 ? f1 + lam + bm_of(lane_arc(c, 1, 1)) : inf();
+      // eqs. arc-marginal / marginal-aggregation, then the damped eq. mma-update step.  A node
+      // the layer does not have (node 1 of a one-node layer, both nodes of a lane without the
+      // layer) has both arcs to the false terminal, so its terms are +inf without a test.
+      const float a00 = f0 + bm_of(lane_arc(c, 0, 0));
+      const float a01 = f1 + bm_of(lane_arc(c, 1, 0));
+      const float a10 = f0 + lam + bm_of(lane_arc(c, 0, 1));
+      const float a11 = f1 + lam + bm_of(lane_arc(c, 1, 1));
       const float m0 = fminf(a00, a01), m1 = fminf(a10, a11);
       const float dd = p.omega * mm_difference(m0, m1);
       lam -= dd;
