@@ -1171,7 +1171,7 @@ int bdd_build(int n, int m, const long long *row_ptr, const int *col, const int 
   }
   Layout L;
   try {
-    rc = build_layout(H, &L, h->lanes2, keyed ? h->key_class : nullptr);
+    rc = build_layout(H, &L, h->lanes2, keyed ? h->key_class : nullptr, h->var_deg.data());
   } catch (const std::bad_alloc &) {
     rc = BDD_ENOMEM;
   }

@@ -43,6 +43,7 @@ constexpr long long kSumCap = 1LL << 22;  // largest suffix / prefix sum set per
 struct Scratch {
   std::vector<int> order;
   std::vector<long long> a, pos;
+  std::vector<long long> tlo, thi, slo, shi;  // unit rows: the sum sets as integer ranges
   std::vector<int> cols;
   std::vector<std::vector<long long>> T, S, rep;
   std::vector<std::vector<int>> id_of_key;
@@ -87,6 +88,74 @@ inline int key_of(const std::vector<long long> &T, long long s, long long b, int
   return (it != T.end() && *it == r) ? (int)(it - T.begin()) + 1 : 0;
 }
 
+// key_of for a set T that holds every integer of [lo, hi]: the same counts and positions without
+// a search
+inline int key_of_range(long long lo, long long hi, long long s, long long b, int sense) {
+  const long long r = b - s, m = hi - lo + 1;
+  if (sense < 0) return (int)(r < lo ? 0 : r >= hi ? m : r - lo + 1);
+  if (sense > 0) return (int)(r > hi ? 0 : r <= lo ? m : hi - r + 1);
+  return (r >= lo && r <= hi) ? (int)(r - lo + 1) : 0;
+}
+
+// compile_row for a row whose coefficients (in layer order, sc.a) are all +1 or -1.  Then every
+// suffix-sum set T_l and every reachable prefix-sum set S_l holds all integers between its least
+// and greatest element (adding 0 or +-1 to a set of consecutive integers keeps them consecutive),
+// so the sets are kept as ranges and keys come from key_of_range.  The nodes, their order, the
+// arcs and the checks (in the same order) are those of the general path.
+int compile_unit_row(int j, long long b, int sense, int max_width, int k, Scratch &sc, Chunk &out) {
+  sc.tlo.resize(k + 1);
+  sc.thi.resize(k + 1);
+  sc.slo.resize(k);
+  sc.shi.resize(k);
+  sc.tlo[k] = sc.thi[k] = 0;
+  for (int l = k - 1; l >= 0; --l) {
+    sc.tlo[l] = sc.tlo[l + 1] + std::min(sc.a[l], 0LL);
+    sc.thi[l] = sc.thi[l + 1] + std::max(sc.a[l], 0LL);
+    if (sc.thi[l] - sc.tlo[l] + 1 > kSumCap) return BDD_ETOOBIG;
+  }
+  sc.slo[0] = sc.shi[0] = 0;
+  for (int l = 0; l + 1 < k; ++l) {
+    sc.slo[l + 1] = sc.slo[l] + std::min(sc.a[l], 0LL);
+    sc.shi[l + 1] = sc.shi[l] + std::max(sc.a[l], 0LL);
+    if (sc.shi[l + 1] - sc.slo[l + 1] + 1 > kSumCap) return BDD_ETOOBIG;
+  }
+  for (int l = 0; l < k; ++l) {
+    std::vector<int> &ids = sc.id_of_key[l];
+    ids.assign(sc.thi[l] - sc.tlo[l] + 2, -1);
+    sc.rep[l].clear();
+    for (long long s = sc.slo[l]; s <= sc.shi[l]; ++s) {
+      const int key = key_of_range(sc.tlo[l], sc.thi[l], s, b, sense);
+      if (key == 0 || ids[key] >= 0) continue;
+      ids[key] = (int)sc.rep[l].size();
+      sc.rep[l].push_back(s);
+    }
+    if (sc.rep[l].empty()) return BDD_EINFEASIBLE;
+    if ((long long)sc.rep[l].size() > max_width) return BDD_ETOOBIG;
+  }
+  out.bdd_row.push_back(j);
+  out.bdd_depth.push_back(k);
+  for (int l = 0; l < k; ++l) {
+    out.occ_var.push_back(sc.cols[l]);
+    out.occ_csr.push_back(sc.pos[l]);
+    out.occ_width.push_back((int)sc.rep[l].size());
+    for (long long s : sc.rep[l]) {
+      int lo, hi;
+      if (l == k - 1) {
+        lo = sat(s, sense, b) ? kTop : kBot;
+        hi = sat(s + sc.a[l], sense, b) ? kTop : kBot;
+      } else {
+        const int k0 = key_of_range(sc.tlo[l + 1], sc.thi[l + 1], s, b, sense);
+        const int k1 = key_of_range(sc.tlo[l + 1], sc.thi[l + 1], s + sc.a[l], b, sense);
+        lo = k0 ? sc.id_of_key[l + 1][k0] : kBot;
+        hi = k1 ? sc.id_of_key[l + 1][k1] : kBot;
+      }
+      out.lo.push_back(lo);
+      out.hi.push_back(hi);
+    }
+  }
+  return BDD_OK;
+}
+
 int compile_row(int j, const long long *row_ptr, const int *col, const int *val, const int *rank, int n,
                 long long b, int sense, int max_width, Scratch &sc, Chunk &out) {
   long long s0 = row_ptr[j], e0 = row_ptr[j + 1];
@@ -121,6 +190,9 @@ int compile_row(int j, const long long *row_ptr, const int *col, const int *val,
     sc.rep.resize(k + 1);
     sc.id_of_key.resize(k + 1);
   }
+  bool unit = true;
+  for (int l = 0; l < k && unit; ++l) unit = sc.a[l] == 1 || sc.a[l] == -1;
+  if (unit) return compile_unit_row(j, b, sense, max_width, k, sc, out);
   // suffix sums T_l (l = k .. 0)
   sc.T[k].assign(1, 0);
   for (int l = k - 1; l >= 0; --l) {
@@ -372,7 +444,7 @@ int compile_bdds(int n, int m, const long long *row_ptr, const int *col, const i
   return BDD_OK;
 }
 
-int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_key) {
+int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_key, const int *var_deg) {
   const long long nb = H.nb(), O = H.O(), N = H.N();
   L->lanes2 = lanes2;
   // class of each BDD: its key's entry in the table, else the default for its widest layer
@@ -547,17 +619,20 @@ int build_layout(const HostBDDs &H, Layout *L, bool lanes2, const int *class_of_
       }
     }
   });
-  // variable -> occurrences (ascending row, i.e. canonical occurrence order): degrees by atomic
-  // counts, slots claimed in any order, then each variable's slots sorted by canonical
-  // occurrence; SRMP sets (Appendix A.4): in J_i^> unless the last layer, in J_i^< unless the
-  // first
+  // variable -> occurrences (ascending row, i.e. canonical occurrence order): degrees (the
+  // caller's, else atomic counts), slots claimed in any order, then each variable's slots sorted
+  // by canonical occurrence; SRMP sets (Appendix A.4): in J_i^> unless the last layer, in J_i^<
+  // unless the first
   const int n = H.n;
   std::vector<int> vcnt(n + 1, 0);
-  parallel_for(O, 1 << 16, [&](long long a, long long e) {
-    for (long long co = a; co < e; ++co) __atomic_fetch_add(&vcnt[H.occ_var[co]], 1, __ATOMIC_RELAXED);
-  });
+  if (!var_deg) {
+    parallel_for(O, 1 << 16, [&](long long a, long long e) {
+      for (long long co = a; co < e; ++co) __atomic_fetch_add(&vcnt[H.occ_var[co]], 1, __ATOMIC_RELAXED);
+    });
+    var_deg = vcnt.data();
+  }
   std::vector<long long> ptr(n + 1);
-  parallel_prefix(vcnt.data(), (long long)n, ptr.data(), (int *)nullptr);
+  parallel_prefix(var_deg, (long long)n, ptr.data(), (int *)nullptr);
   L->var_ptr.resize(n + 1);
   parallel_for(n + 1, 1 << 16, [&](long long a, long long e) {
     for (long long i = a; i < e; ++i) {

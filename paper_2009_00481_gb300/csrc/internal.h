@@ -234,8 +234,10 @@ inline int layout_key(int width, int depth) { return natural_class(width) * kDep
 // each).  class_of_key (kLayoutKeys entries, or null): the class each key's BDDs go to, -1 for
 // the default (class 0 = lane tiles for width <= 2 when lanes2, else the natural class).  A
 // class must fit the key: a team of 2^c >= the width, a block tile, or lane tiles (width <= 2,
-// lanes2).  Returns BDD_EINVAL otherwise.
-int build_layout(const HostBDDs &H, Layout *L, bool lanes2 = false, const int *class_of_key = nullptr);
+// lanes2).  Returns BDD_EINVAL otherwise.  var_deg (H.n entries, or null): the number of
+// occurrences of every variable in H.occ_var, if the caller has counted them already.
+int build_layout(const HostBDDs &H, Layout *L, bool lanes2 = false, const int *class_of_key = nullptr,
+                 const int *var_deg = nullptr);
 
 // Fused pending pass of an update sweep (the per-phase plan without separate pending kernels).
 // At the end of its tile every occurrence counts its variable down; the visit that brings the

@@ -73,6 +73,25 @@ def test_compiler_bit_exact_random(cuda_lib, seed):
     _assert_same(inst, 1 + seed % 2)
 
 
+@pytest.mark.parametrize("seed", range(20))
+def test_compiler_bit_exact_unit_rows(cuda_lib, seed):
+    """Rows with coefficients +-1 only (the library compiles them from integer ranges instead of
+    sorted sum sets): canonical arrays equal the oracle's for every sense, including rows with
+    no feasible completion of some partial sums and one-variable rows."""
+    inst = random_ilp(n=40, m=40, max_row_vars=16, seed=900 + seed, coef=1)
+    _assert_same(inst, 1 + seed % 2)
+
+
+def test_compiler_unit_rows_mixed_with_general_rows(cuda_lib):
+    """+-1 rows and rows with larger coefficients in one instance, every sense: both paths of
+    the compiler, the same canonical arrays as the oracle."""
+    rows = [([0, 1, 2, 3], [1, -1, 1, 1], 1, 0), ([1, 2, 4], [2, -3, 1], 0, 1),
+            ([0, 3, 4, 5], [-1, -1, 1, 1], 0, -1), ([2, 5], [1, 1], 1, 1), ([5], [-1], -1, 0)]
+    inst = _from_rows("mixed", 6, rows, np.random.default_rng(5).normal(size=6))
+    for host_only in (1, 2):
+        _assert_same(inst, host_only)
+
+
 def test_layout_classes(cuda_lib):
     """Potts rows have width <= 2 (warp tiles of 16 BDDs); tomography projections are wider than
     32 nodes (one block per BDD)."""
